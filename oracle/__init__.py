@@ -1,0 +1,246 @@
+"""FP64 CPU oracle for the diffuse-radiation ray-tracing scheme of Tanaka et al.
+(2014) -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this package.  The product path (``paper_1410_0763_gb300``)
+never imports it and shares no code with it.  The arithmetic lives in
+``oracle.c`` (plain C, FP64); this module only compiles it with gcc and
+marshals numpy arrays through ctypes.
+
+Every function cites the passage of the paper it follows; see ``oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import sys
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into a shared library (gcc, -O2, OpenMP when present)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-D_GNU_SOURCE", _SRC, "-o", tmp, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class SweepCfg(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("nside", C.c_int),
+                ("tie_tol", C.c_double), ("field_form", C.c_int), ("nthreads", C.c_int)]
+
+
+class Chem(C.Structure):
+    _fields_ = [("alphaA", C.c_double), ("alphaB", C.c_double), ("gcoll", C.c_double),
+                ("sigma0", C.c_double), ("h", C.c_double), ("nu0", C.c_double),
+                ("dnu", C.c_double), ("dx", C.c_double)]
+
+
+_D = C.POINTER(C.c_double)
+_L = C.POINTER(C.c_long)
+
+
+def _lib_handle():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            lib = C.CDLL(path)
+            lib.orc_n_dirs.argtypes = [C.c_int]
+            lib.orc_healpix_dirs.argtypes = [C.c_int, _D]
+            lib.orc_sweep_dir.argtypes = [C.POINTER(SweepCfg), _D, _D, C.c_int, _D, _D]
+            lib.orc_sweep_range.argtypes = [C.POINTER(SweepCfg), _D, _D, C.c_int, C.c_int, _D]
+            lib.orc_sweep_range.restype = C.c_long
+            lib.orc_sweep.argtypes = [C.POINTER(SweepCfg), _D, _D, _D, _D]
+            lib.orc_sweep.restype = C.c_long
+            lib.orc_lattice.argtypes = [C.POINTER(SweepCfg), C.c_int, _L, C.POINTER(C.c_int), _D]
+            lib.orc_trace_ray.argtypes = [C.POINTER(SweepCfg), _D, _D, C.c_int, C.c_long, C.c_long,
+                                          _L, _D, _D, C.c_int, _D]
+            lib.orc_jin_cells.argtypes = [C.POINTER(SweepCfg), _D, _D, _L, C.c_int, _D]
+            lib.orc_band_integral.argtypes = [C.c_double] * 4
+            lib.orc_band_integral.restype = C.c_double
+            lib.orc_point_sources.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _D, _D, C.c_int,
+                                              _D, _D, C.c_double, C.c_int, _D]
+            lib.orc_balance_eq.argtypes = [C.c_long, _D, C.c_double, C.c_double, _D, _D]
+            lib.orc_iterate.argtypes = [C.POINTER(SweepCfg), C.POINTER(Chem), _D, C.c_int, _D, _D,
+                                        C.c_double, C.c_int, _D, _D, C.POINTER(C.c_int)]
+            _lib = lib
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def default_threads() -> int:
+    return max(1, min(os.cpu_count() or 1, 64))
+
+
+def _cfg(shape, nside, field_form=0, tie_tol=1e-12, nthreads=None) -> SweepCfg:
+    nz, ny, nx = shape
+    return SweepCfg(nx, ny, nz, nside, tie_tol, int(field_form),
+                    default_threads() if nthreads is None else int(nthreads))
+
+
+def n_dirs(nside: int) -> int:
+    return 12 * nside * nside
+
+
+def healpix_dirs(nside: int) -> np.ndarray:
+    """HEALPix RING pixel centres as unit vectors, shape (12 nside^2, 3)."""
+    out = np.empty((n_dirs(nside), 3))
+    if _lib_handle().orc_healpix_dirs(nside, _dp(out)) != 0:
+        raise ValueError("nside must be >= 1")
+    return out
+
+
+def sweep(kappa, src, nside, field_form=0, tie_tol=1e-12, nthreads=None):
+    """Full sweep (Sec. 2.2).  kappa, src: [z][y][x].  Returns (J_in, J, n_w_zero)."""
+    k, s = _f64(kappa), _f64(src)
+    jin = np.empty_like(k)
+    j = np.empty_like(k)
+    cfg = _cfg(k.shape, nside, field_form, tie_tol, nthreads)
+    nz = _lib_handle().orc_sweep(C.byref(cfg), _dp(k), _dp(s), _dp(jin), _dp(j))
+    if nz < 0:
+        raise MemoryError("oracle sweep: allocation failed")
+    return jin, j, int(nz)
+
+
+def sweep_range(kappa, src, nside, d0, d1, field_form=0, tie_tol=1e-12, nthreads=None):
+    """Sum over directions d0..d1-1 (RING order) of Ibar^{ave,in}, not divided by N_d."""
+    k, s = _f64(kappa), _f64(src)
+    acc = np.empty_like(k)
+    cfg = _cfg(k.shape, nside, field_form, tie_tol, nthreads)
+    nz = _lib_handle().orc_sweep_range(C.byref(cfg), _dp(k), _dp(s), int(d0), int(d1), _dp(acc))
+    if nz < 0:
+        raise MemoryError("oracle sweep: allocation failed")
+    return acc, int(nz)
+
+
+def sweep_dir(kappa, src, nside, d, field_form=0, tie_tol=1e-12):
+    """Per-cell A (sum ds*Ibar_in) and W (sum ds) of one direction."""
+    k, s = _f64(kappa), _f64(src)
+    A = np.empty_like(k)
+    W = np.empty_like(k)
+    cfg = _cfg(k.shape, nside, field_form, tie_tol, 1)
+    if _lib_handle().orc_sweep_dir(C.byref(cfg), _dp(k), _dp(s), int(d), _dp(A), _dp(W)) != 0:
+        raise ValueError("bad direction index")
+    return A, W
+
+
+def lattice(shape, nside, d, tie_tol=1e-12):
+    """(jlo, jhi, klo, khi), (a, b, c, sign_a), (qb, qc, |n_a|) of direction d."""
+    r = np.zeros(4, dtype=np.int64)
+    ax = (C.c_int * 4)()
+    q = np.zeros(3)
+    cfg = _cfg(shape, nside, 0, tie_tol, 1)
+    if _lib_handle().orc_lattice(C.byref(cfg), int(d), r.ctypes.data_as(_L), ax, _dp(q)) != 0:
+        raise ValueError("bad direction index")
+    return tuple(int(v) for v in r), tuple(ax), tuple(q)
+
+
+def trace_ray(kappa, src, nside, d, j, k, field_form=0, tie_tol=1e-12, maxseg=100000):
+    """Segments (cell, ds, I_in) of lattice ray (j, k) of direction d, and the exit intensity."""
+    kk, s = _f64(kappa), _f64(src)
+    cells = np.zeros(maxseg, dtype=np.int64)
+    ds = np.zeros(maxseg)
+    iin = np.zeros(maxseg)
+    iex = C.c_double(0.0)
+    cfg = _cfg(kk.shape, nside, field_form, tie_tol, 1)
+    n = _lib_handle().orc_trace_ray(C.byref(cfg), _dp(kk), _dp(s), int(d), int(j), int(k),
+                                    cells.ctypes.data_as(_L), _dp(ds), _dp(iin), maxseg,
+                                    C.byref(iex))
+    if n < 0 or n > maxseg:
+        raise ValueError("trace_ray failed")
+    return cells[:n].copy(), ds[:n].copy(), iin[:n].copy(), iex.value
+
+
+def jin_cells(kappa, src, nside, cells, field_form=0, tie_tol=1e-12, nthreads=None):
+    """J^in at the given flat cell indices, computed one cell at a time."""
+    k, s = _f64(kappa), _f64(src)
+    c = np.ascontiguousarray(np.asarray(cells, dtype=np.int64))
+    out = np.empty(c.shape[0])
+    cfg = _cfg(k.shape, nside, field_form, tie_tol, nthreads)
+    bad = _lib_handle().orc_jin_cells(C.byref(cfg), _dp(k), _dp(s), c.ctypes.data_as(_L),
+                                      int(c.shape[0]), _dp(out))
+    if bad:
+        raise RuntimeError(f"{bad} (cell, direction) pairs with no ray")
+    return out
+
+
+def band_integral(sigma0, h, nu0, nu1) -> float:
+    """int_{nu0}^{nu1} sigma(nu)/(h nu) dnu for sigma = sigma0 (nu/nu0)^-3 (Eq. gamma_diff)."""
+    return float(_lib_handle().orc_band_integral(sigma0, h, nu0, nu1))
+
+
+def point_sources(kappa_bins, sigma_bins, pos, Q, dx, nthreads=None):
+    """Photon-conserving point-source rate per neutral atom (App. A).
+
+    kappa_bins: [bins][z][y][x] (per cell width); sigma_bins: [bins] cm^2;
+    pos: [nsrc][3] in cell widths (x, y, z); Q: [nsrc][bins] photons/s.
+    """
+    kb = _f64(kappa_bins)
+    if kb.ndim == 3:
+        kb = kb[None]
+    nb, nz, ny, nx = kb.shape
+    sg = _f64(sigma_bins).reshape(nb)
+    p = _f64(pos).reshape(-1, 3)
+    q = _f64(Q).reshape(p.shape[0], nb)
+    out = np.empty((nz, ny, nx))
+    _lib_handle().orc_point_sources(nx, ny, nz, nb, _dp(kb), _dp(sg), p.shape[0], _dp(p), _dp(q),
+                                    float(dx), default_threads() if nthreads is None else nthreads,
+                                    _dp(out))
+    return out
+
+
+def balance_eq(nH, alphaB, gcoll, g):
+    """Equilibrium neutral fraction y (App. B, dt -> infinity)."""
+    n = _f64(nH)
+    gg = _f64(g)
+    y = np.empty_like(n)
+    _lib_handle().orc_balance_eq(n.size, _dp(n), float(alphaB), float(gcoll), _dp(gg), _dp(y))
+    return y
+
+
+def iterate(nH, nside, chem: dict, pos, Q, y0, tol=1e-6, max_iter=200, nthreads=None):
+    """RT / balance fixed-point iteration (App. D).  Returns (y, iters, residuals, converged)."""
+    n = _f64(nH)
+    y = _f64(y0).copy()
+    p = _f64(pos).reshape(-1, 3)
+    q = _f64(Q).reshape(p.shape[0])
+    hist = np.zeros(max_iter)
+    it = C.c_int(0)
+    ch = Chem(chem["alphaA"], chem["alphaB"], chem["gcoll"], chem["sigma0"], chem["h"],
+              chem["nu0"], chem["dnu"], chem["dx"])
+    cfg = _cfg(n.shape, nside, 1, 1e-12, nthreads)
+    rc = _lib_handle().orc_iterate(C.byref(cfg), C.byref(ch), _dp(n), p.shape[0], _dp(p), _dp(q),
+                                   float(tol), int(max_iter), _dp(y), _dp(hist), C.byref(it))
+    if rc < 0:
+        raise MemoryError("oracle iterate: allocation failed")
+    return y, it.value, hist[: it.value].copy(), rc == 0
+
+
+if __name__ == "__main__":  # pragma: no cover
+    print(build(force="--force" in sys.argv))

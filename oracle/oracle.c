@@ -1,0 +1,679 @@
+/*
+ * oracle.c -- plain FP64 CPU oracle for the diffuse-radiation ray-tracing
+ * scheme of Tanaka, Yoshikawa, Okamoto & Hasegawa (2014), "A new ray-tracing
+ * scheme for 3D diffuse radiation transfer on highly parallel architectures".
+ *
+ * TEST INFRASTRUCTURE.  This library exists only to check the CUDA path.  Only
+ * the test suite, the package smoke check and the benchmark's CPU-baseline leg
+ * may load it.  It shares no code, header, table or constant with the CUDA
+ * library; both sides receive the same seeded inputs and physical constants
+ * from their caller.
+ *
+ * What it computes, in the paper's order:
+ *   - directions: HEALPix RING pixel centres (Sec. 2.3; Gorski et al. 2005,
+ *     Sec. 4, pixel-to-angle relations of the RING scheme);
+ *   - the parallel-ray family of each direction (Sec. 2.2, Fig. parallel_ray;
+ *     reading: a unit lattice of lines on planes normal to the dominant axis,
+ *     offset to cell centres), each line marched cell by cell from where it
+ *     enters the box with vacuum intensity;
+ *   - the per-segment transfer step, Eq. (rt); the path-averaged incoming
+ *     intensity of a segment (the equation after Eq. (rt)); the Delta-tau
+ *     weighted cell average, Eqs. (path_averaged_intensity) and
+ *     (averaged_intensity); the angle average, Eq. (mean_intensity) and the
+ *     definition of J^in that follows it;
+ *   - the photo-ionization rate of the diffuse field, Eq. (gamma_diff);
+ *   - point sources by long characteristics with the photon-conserving rate
+ *     of App. A, Eq. (pc_gamma), with the absorbed count taken as in minus
+ *     out (App. A prints out minus in; the sign is a typo);
+ *   - the hydrogen ionization balance of App. B in its dt -> infinity
+ *     (equilibrium) limit, and the RT/balance fixed-point iteration of App. D
+ *     with the electron-density convergence test.
+ *
+ * Everything is FP64.  Summations run in a fixed order (directions in RING
+ * order, rays in lattice order, sources in index order), so the oracle is
+ * deterministic for a given thread count and bit-identical across thread
+ * counts (directions are computed in parallel but added in RING order).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* Crossing parameters closer than this (in cell widths along the dominant
+ * axis) are one crossing: a ray through an edge or a corner steps across all
+ * the planes it meets there at once, and no zero-length segment is emitted. */
+#define ORC_TIE 1e-12
+
+/* ------------------------------------------------------------------------ */
+/* Directions: HEALPix RING scheme, pixel index -> unit vector.              */
+/* Gorski et al. (2005), Sec. 4: north polar cap, equatorial belt, south    */
+/* polar cap; ring index i, pixel-in-ring index j, z = cos(theta), phi.      */
+/* ------------------------------------------------------------------------ */
+int orc_n_dirs(int nside) { return 12 * nside * nside; }
+
+void orc_healpix_vec(int nside, long p, double v[3])
+{
+    const double ns = (double)nside;
+    const long npix = 12L * nside * nside;
+    const long ncap = 2L * nside * (nside - 1);
+    double z, phi;
+    if (p < ncap) {
+        double ph = 0.5 * (double)(p + 1);
+        long i = (long)floor(sqrt(ph - sqrt(floor(ph)))) + 1;
+        long j = p + 1 - 2 * i * (i - 1);
+        z = 1.0 - (double)(i * i) / (3.0 * ns * ns);
+        phi = M_PI / (2.0 * (double)i) * ((double)j - 0.5);
+    } else if (p < npix - ncap) {
+        long q = p - ncap;
+        long i = q / (4 * nside) + nside;
+        long j = q % (4 * nside) + 1;
+        long s = (i - nside + 1) % 2;
+        z = 4.0 / 3.0 - 2.0 * (double)i / (3.0 * ns);
+        phi = M_PI / (2.0 * ns) * ((double)j - 0.5 * (double)s);
+    } else {
+        double ph = 0.5 * (double)(npix - p);
+        long i = (long)floor(sqrt(ph - sqrt(floor(ph)))) + 1;
+        long j = 4 * i + 1 - (npix - p - 2 * i * (i - 1));
+        z = -1.0 + (double)(i * i) / (3.0 * ns * ns);
+        phi = M_PI / (2.0 * (double)i) * ((double)j - 0.5);
+    }
+    double st = sqrt((1.0 - z) * (1.0 + z));
+    v[0] = st * cos(phi);
+    v[1] = st * sin(phi);
+    v[2] = z;
+}
+
+int orc_healpix_dirs(int nside, double *out)
+{
+    if (nside < 1) return -1;
+    long n = orc_n_dirs(nside);
+    for (long p = 0; p < n; p++) orc_healpix_vec(nside, p, out + 3 * p);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Frame of one direction.  a = dominant axis (the lowest index among the    */
+/* components within tie_tol of the largest magnitude), b < c the other two. */
+/* The rays are the lines X_a = upwind + sa*u, X_b = j + 1/2 + qb*u,         */
+/* X_c = k + 1/2 + qc*u with integer (j, k), u the distance along a from the */
+/* upwind a-face, qb = n_b/|n_a|, qc = n_c/|n_a| (clamped to [-1, 1]); the   */
+/* path length of a piece of ray is du / |n_a|.                              */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int dims[3];          /* nx, ny, nz */
+    int a, b, c;          /* axes */
+    int sa;               /* sign of n_a */
+    double na, qb, qc;
+    int Na, Nb, Nc;
+} frame_t;
+
+static double clamp1(double q) { return q > 1.0 ? 1.0 : (q < -1.0 ? -1.0 : q); }
+
+static void frame_of(const int dims[3], const double n[3], double tie_tol, frame_t *f)
+{
+    double m = fabs(n[0]);
+    if (fabs(n[1]) > m) m = fabs(n[1]);
+    if (fabs(n[2]) > m) m = fabs(n[2]);
+    int a = 0;
+    for (int i = 0; i < 3; i++)
+        if (fabs(n[i]) >= m - tie_tol * m) { a = i; break; }
+    f->a = a;
+    f->b = (a == 0) ? 1 : 0;
+    f->c = (a == 2) ? 1 : 2;
+    f->sa = n[a] >= 0.0 ? 1 : -1;
+    f->na = fabs(n[a]);
+    f->qb = clamp1(n[f->b] / f->na);
+    f->qc = clamp1(n[f->c] / f->na);
+    for (int i = 0; i < 3; i++) f->dims[i] = dims[i];
+    f->Na = dims[a];
+    f->Nb = dims[f->b];
+    f->Nc = dims[f->c];
+}
+
+/* Range of u over which the ray (j, k) is inside the open box. */
+static int ray_u_range(const frame_t *f, long j, long k, double *u0, double *u1)
+{
+    double lo = 0.0, hi = (double)f->Na;
+    double xb0 = (double)j + 0.5, xc0 = (double)k + 0.5;
+    const double q[2] = {f->qb, f->qc};
+    const double x0[2] = {xb0, xc0};
+    const int N[2] = {f->Nb, f->Nc};
+    for (int t = 0; t < 2; t++) {
+        if (q[t] == 0.0) {
+            if (!(x0[t] > 0.0 && x0[t] < (double)N[t])) return 0;
+            continue;
+        }
+        double ua = (0.0 - x0[t]) / q[t];
+        double ub = ((double)N[t] - x0[t]) / q[t];
+        if (ua > ub) { double s = ua; ua = ub; ub = s; }
+        if (ua > lo) lo = ua;
+        if (ub < hi) hi = ub;
+    }
+    if (hi - lo <= ORC_TIE) return 0;
+    *u0 = lo;
+    *u1 = hi;
+    return 1;
+}
+
+/* Lattice index range that can contain rays meeting the box (generous). */
+static void lattice_range(const frame_t *f, long *jlo, long *jhi, long *klo, long *khi)
+{
+    double sb = f->qb * f->Na, sc = f->qc * f->Na;
+    *jlo = (long)floor(-0.5 - (sb > 0 ? sb : 0.0)) - 1;
+    *jhi = (long)ceil((double)f->Nb - 0.5 - (sb < 0 ? sb : 0.0)) + 1;
+    *klo = (long)floor(-0.5 - (sc > 0 ? sc : 0.0)) - 1;
+    *khi = (long)ceil((double)f->Nc - 0.5 - (sc < 0 ? sc : 0.0)) + 1;
+}
+
+static long cell_index(const frame_t *f, long ia, long ib, long ic)
+{
+    long x[3];
+    x[f->a] = ia;
+    x[f->b] = ib;
+    x[f->c] = ic;
+    return (x[2] * f->dims[1] + x[1]) * f->dims[0] + x[0];
+}
+
+static long clampl(long v, long lo, long hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* phi(x) = (1 - e^-x)/x with phi(0) = 1: the path-averaged attenuation of a
+ * segment of optical depth x (Sec. 2.2, the equation after Eq. (rt)). */
+static double phi_of(double x) { return x > 0.0 ? -expm1(-x) / x : 1.0; }
+
+/* March one ray from where it enters the box to where it leaves.  For each
+ * segment (a maximal piece inside one cell, length > 0) the callback receives
+ * the cell index and the path length ds, in order along n. */
+typedef void (*seg_fn)(void *ctx, long cell, double ds);
+
+static int march_ray(const frame_t *f, long j, long k, seg_fn fn, void *ctx)
+{
+    double u0, u1;
+    if (!ray_u_range(f, j, k, &u0, &u1)) return 0;
+    const double xb0 = (double)j + 0.5, xc0 = (double)k + 0.5;
+    const double q[2] = {f->qb, f->qc};
+    const double x0[2] = {xb0, xc0};
+    /* next crossing parameter per axis: a-planes sit at integer u */
+    double pa = floor(u0 + ORC_TIE) + 1.0;
+    double plane[2], un[2];
+    for (int t = 0; t < 2; t++) {
+        double x = x0[t] + q[t] * u0;
+        if (q[t] > 0.0) {
+            plane[t] = floor(x + ORC_TIE) + 1.0;
+            un[t] = (plane[t] - x0[t]) / q[t];
+        } else if (q[t] < 0.0) {
+            plane[t] = ceil(x - ORC_TIE) - 1.0;
+            un[t] = (plane[t] - x0[t]) / q[t];
+        } else {
+            plane[t] = 0.0;
+            un[t] = INFINITY;
+        }
+    }
+    int nseg = 0;
+    double u = u0;
+    while (u < u1 - ORC_TIE) {
+        double ue = u1;
+        if (pa < ue) ue = pa;
+        if (un[0] < ue) ue = un[0];
+        if (un[1] < ue) ue = un[1];
+        if (ue - u > ORC_TIE) {
+            double um = 0.5 * (u + ue);
+            double xa = f->sa > 0 ? um : (double)f->Na - um;
+            long ia = clampl((long)floor(xa), 0, f->Na - 1);
+            long ib = clampl((long)floor(x0[0] + q[0] * um), 0, f->Nb - 1);
+            long ic = clampl((long)floor(x0[1] + q[1] * um), 0, f->Nc - 1);
+            fn(ctx, cell_index(f, ia, ib, ic), (ue - u) / f->na);
+            nseg++;
+        }
+        if (pa <= ue + ORC_TIE) pa += 1.0;
+        for (int t = 0; t < 2; t++) {
+            if (un[t] <= ue + ORC_TIE) {
+                plane[t] += (q[t] > 0.0) ? 1.0 : -1.0;
+                un[t] = (plane[t] - x0[t]) / q[t];
+            }
+        }
+        u = ue;
+    }
+    return nseg;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One direction of the sweep.                                               */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int nx, ny, nz;
+    int nside;
+    double tie_tol;
+    int field_form;   /* 0: (kappa, S) inputs; 1: (kappa, emissivity) inputs */
+    int nthreads;
+} orc_sweep_cfg;
+
+typedef struct {
+    const double *kappa, *src;  /* per cell: kappa per cell width; S or eps*dx */
+    int form;
+    double I;                   /* running intensity along the ray */
+    double *A, *W;              /* per-cell accumulators of this direction */
+    /* optional per-segment record */
+    long *cells;
+    double *ds, *Iin;
+    int maxseg, nrec;
+    long only_cell;             /* >= 0: accumulate A, W for this cell only */
+} ray_ctx;
+
+/* Eq. (rt) for one segment, with the path-averaged incoming intensity
+ * Ibar_in = I_in (1 - e^-dtau)/dtau deposited with weight dtau; since kappa is
+ * constant inside a cell, the dtau weights of Eq. (averaged_intensity) equal
+ * ds weights, so A accumulates ds * Ibar_in and W accumulates ds. */
+static void seg_update(void *vctx, long cell, double ds)
+{
+    ray_ctx *r = (ray_ctx *)vctx;
+    const double kap = r->kappa[cell];
+    const double x = kap * ds;
+    const double e = exp(-x);
+    const double ph = phi_of(x);
+    const double Iin = r->I;
+    if (r->A && (r->only_cell < 0 || r->only_cell == cell)) {
+        r->A[r->only_cell < 0 ? cell : 0] += ds * Iin * ph;
+        r->W[r->only_cell < 0 ? cell : 0] += ds;
+    }
+    if (r->cells && r->nrec < r->maxseg) {
+        r->cells[r->nrec] = cell;
+        r->ds[r->nrec] = ds;
+        r->Iin[r->nrec] = Iin;
+    }
+    r->nrec++;
+    if (r->form == 0) {
+        const double S = r->src[cell];
+        r->I = S + (Iin - S) * e;                 /* Eq. (rt) */
+    } else {
+        r->I = Iin * e + r->src[cell] * ds * ph;  /* Eq. (rt) with S = eps/kappa */
+    }
+}
+
+static void make_frame(const orc_sweep_cfg *cfg, int d, frame_t *f)
+{
+    double n[3];
+    const int dims[3] = {cfg->nx, cfg->ny, cfg->nz};
+    orc_healpix_vec(cfg->nside, d, n);
+    frame_of(dims, n, cfg->tie_tol, f);
+}
+
+/* Accumulate A (sum of ds * Ibar_in) and W (sum of ds) of direction d over
+ * every ray of its family. */
+static void sweep_dir(const orc_sweep_cfg *cfg, const double *kappa, const double *src, int d,
+                      double *A, double *W)
+{
+    frame_t f;
+    make_frame(cfg, d, &f);
+    long jlo, jhi, klo, khi;
+    lattice_range(&f, &jlo, &jhi, &klo, &khi);
+    ray_ctx r;
+    memset(&r, 0, sizeof r);
+    r.kappa = kappa;
+    r.src = src;
+    r.form = cfg->field_form;
+    r.A = A;
+    r.W = W;
+    r.only_cell = -1;
+    for (long k = klo; k <= khi; k++)
+        for (long j = jlo; j <= jhi; j++) {
+            r.I = 0.0;   /* vacuum boundary: nothing enters the box */
+            march_ray(&f, j, k, seg_update, &r);
+        }
+}
+
+int orc_sweep_dir(const orc_sweep_cfg *cfg, const double *kappa, const double *src, int d,
+                  double *A, double *W)
+{
+    long ncell = (long)cfg->nx * cfg->ny * cfg->nz;
+    if (d < 0 || d >= orc_n_dirs(cfg->nside)) return -1;
+    memset(A, 0, sizeof(double) * ncell);
+    memset(W, 0, sizeof(double) * ncell);
+    sweep_dir(cfg, kappa, src, d, A, W);
+    return 0;
+}
+
+/* Sum over directions d0 <= d < d1, in RING order, of the per-cell average
+ * incoming intensity A/W of Eq. (averaged_intensity) (not yet divided by N_d).
+ * Returns the number of (cell, direction) pairs with W = 0 (expected: 0). */
+long orc_sweep_range(const orc_sweep_cfg *cfg, const double *kappa, const double *src,
+                     int d0, int d1, double *acc)
+{
+    const long ncell = (long)cfg->nx * cfg->ny * cfg->nz;
+    int nt = cfg->nthreads > 0 ? cfg->nthreads : 1;
+    double *buf = (double *)malloc(sizeof(double) * ncell * 2 * (size_t)nt);
+    if (!buf) return -1;
+    long nzero = 0;
+    memset(acc, 0, sizeof(double) * ncell);
+    for (int dc = d0; dc < d1; dc += nt) {
+        int cnt = (d1 - dc) < nt ? (d1 - dc) : nt;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static, 1) num_threads(nt)
+#endif
+        for (int t = 0; t < cnt; t++) {
+            double *A = buf + (size_t)2 * t * ncell, *W = A + ncell;
+            memset(A, 0, sizeof(double) * ncell * 2);
+            sweep_dir(cfg, kappa, src, dc + t, A, W);
+        }
+        for (int t = 0; t < cnt; t++) {
+            const double *A = buf + (size_t)2 * t * ncell, *W = A + ncell;
+            for (long i = 0; i < ncell; i++) {
+                if (W[i] > 0.0) acc[i] += A[i] / W[i];
+                else nzero++;
+            }
+        }
+    }
+    free(buf);
+    return nzero;
+}
+
+/* Full sweep, Eq. (mean_intensity): J^in = (1/N_d) sum_i Ibar^{ave,in}(n_i),
+ * J = J^in + S.  With emissivity inputs S = eps/kappa where kappa > 0; where
+ * kappa = 0 only J^in is defined and J = J^in is returned. */
+long orc_sweep(const orc_sweep_cfg *cfg, const double *kappa, const double *src,
+               double *Jin, double *J)
+{
+    const long ncell = (long)cfg->nx * cfg->ny * cfg->nz;
+    const int nd = orc_n_dirs(cfg->nside);
+    long nzero = orc_sweep_range(cfg, kappa, src, 0, nd, Jin);
+    if (nzero < 0) return nzero;
+    for (long i = 0; i < ncell; i++) Jin[i] /= (double)nd;
+    if (J) {
+        for (long i = 0; i < ncell; i++) {
+            double S = src[i];
+            if (cfg->field_form == 1) S = kappa[i] > 0.0 ? src[i] / kappa[i] : 0.0;
+            J[i] = Jin[i] + S;
+        }
+    }
+    return nzero;
+}
+
+/* Lattice description of direction d (for tests that enumerate rays). */
+int orc_lattice(const orc_sweep_cfg *cfg, int d, long *range4, int *axes4, double *q3)
+{
+    frame_t f;
+    if (d < 0 || d >= orc_n_dirs(cfg->nside)) return -1;
+    make_frame(cfg, d, &f);
+    lattice_range(&f, &range4[0], &range4[1], &range4[2], &range4[3]);
+    axes4[0] = f.a;
+    axes4[1] = f.b;
+    axes4[2] = f.c;
+    axes4[3] = f.sa;
+    q3[0] = f.qb;
+    q3[1] = f.qc;
+    q3[2] = f.na;
+    return 0;
+}
+
+/* Trace one lattice ray (j, k) of direction d.  Records up to maxseg segments
+ * (cell, ds, incoming intensity) and returns the number of segments, the exit
+ * intensity in *I_exit. */
+int orc_trace_ray(const orc_sweep_cfg *cfg, const double *kappa, const double *src, int d,
+                  long j, long k, long *cells, double *ds, double *Iin, int maxseg,
+                  double *I_exit)
+{
+    frame_t f;
+    if (d < 0 || d >= orc_n_dirs(cfg->nside)) return -1;
+    make_frame(cfg, d, &f);
+    ray_ctx r;
+    memset(&r, 0, sizeof r);
+    r.kappa = kappa;
+    r.src = src;
+    r.form = cfg->field_form;
+    r.cells = cells;
+    r.ds = ds;
+    r.Iin = Iin;
+    r.maxseg = maxseg;
+    r.only_cell = -1;
+    r.I = 0.0;
+    march_ray(&f, j, k, seg_update, &r);
+    if (I_exit) *I_exit = r.I;
+    return r.nrec;
+}
+
+/* J^in at selected cells, computed one by one: for every direction, every ray
+ * of the family that can pass through the cell is traced from its entry point
+ * and only its segment in that cell is kept. */
+int orc_jin_cells(const orc_sweep_cfg *cfg, const double *kappa, const double *src,
+                  const long *cells, int ncells, double *Jin)
+{
+    const int nd = orc_n_dirs(cfg->nside);
+    const int dims[3] = {cfg->nx, cfg->ny, cfg->nz};
+    int nt = cfg->nthreads > 0 ? cfg->nthreads : 1;
+    int bad = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt) reduction(+ : bad)
+#endif
+    for (int ci = 0; ci < ncells; ci++) {
+        long cell = cells[ci];
+        long x[3];
+        x[0] = cell % dims[0];
+        x[1] = (cell / dims[0]) % dims[1];
+        x[2] = cell / ((long)dims[0] * dims[1]);
+        double sum = 0.0;
+        for (int d = 0; d < nd; d++) {
+            frame_t f;
+            make_frame(cfg, d, &f);
+            /* u-interval of the cell along the ray family */
+            double ucell = f.sa > 0 ? (double)x[f.a] : (double)(f.Na - 1 - x[f.a]);
+            long jr[2], kr[2];
+            const double qq[2] = {f.qb, f.qc};
+            const long pc[2] = {x[f.b], x[f.c]};
+            long *rr[2] = {jr, kr};
+            for (int t = 0; t < 2; t++) {
+                double s0 = qq[t] * ucell, s1 = qq[t] * (ucell + 1.0);
+                double smin = s0 < s1 ? s0 : s1, smax = s0 < s1 ? s1 : s0;
+                rr[t][0] = (long)floor((double)pc[t] - 0.5 - smax) - 1;
+                rr[t][1] = (long)ceil((double)pc[t] + 0.5 - smin) + 1;
+            }
+            double A = 0.0, W = 0.0;
+            ray_ctx r;
+            memset(&r, 0, sizeof r);
+            r.kappa = kappa;
+            r.src = src;
+            r.form = cfg->field_form;
+            r.A = &A;
+            r.W = &W;
+            r.only_cell = cell;
+            for (long k = kr[0]; k <= kr[1]; k++)
+                for (long j = jr[0]; j <= jr[1]; j++) {
+                    r.I = 0.0;
+                    march_ray(&f, j, k, seg_update, &r);
+                }
+            if (W > 0.0) sum += A / W;
+            else bad++;
+        }
+        Jin[ci] = sum / (double)nd;
+    }
+    return bad;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Diffuse photo-ionization rate, Eq. (gamma_diff): the incoming part        */
+/* 4 pi Jcal^in * int_{nu0}^{nu0+dnu} sigma(nu)/(h nu) dnu.                  */
+/* sigma(nu) = sigma0 (nu/nu0)^-3 (hydrogenic threshold power law), so the  */
+/* band integral has the closed form sigma0 nu0^3/(3h) (nu0^-3 - nu1^-3).    */
+/* ------------------------------------------------------------------------ */
+double orc_band_integral(double sigma0, double h, double nu0, double nu1)
+{
+    return sigma0 * nu0 * nu0 * nu0 / (3.0 * h) * (1.0 / (nu0 * nu0 * nu0) - 1.0 / (nu1 * nu1 * nu1));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Point sources: long characteristics, photon-conserving rate (Sec. 2.1,   */
+/* App. A).  For each target cell and source, the ray from the source to    */
+/* the cell centre is marched; tau sums kappa*ds over the cells before the  */
+/* target cell, [r_in, r_out] is the ray's passage through the target cell  */
+/* (r_in = 0 in the source's own cell).  Per bin b:                          */
+/*   Ndot_abs = Q_b e^-tau (1 - e^-dtau),  dtau = kappa_b (r_out - r_in),    */
+/*   Gamma   += Ndot_abs / (n_HI * 4pi/3 (r_out^3 - r_in^3) dx^3)            */
+/* with n_HI = kappa_b/(sigma_b dx), written without the division by n_HI:   */
+/*   Gamma += Q_b e^-tau sigma_b (r_out - r_in) phi(dtau)                    */
+/*            / (4pi/3 (r_out^3 - r_in^3) dx^2).                             */
+/* Positions are in cell widths, box [0, n]^3.                               */
+/* ------------------------------------------------------------------------ */
+static double pt_one(const int dims[3], const double *kappa_bins, long ncell, int nbins,
+                     const double *sigma, const double *Qb, const double s[3], long target,
+                     double dx)
+{
+    long tx = target % dims[0], ty = (target / dims[0]) % dims[1], tz = target / ((long)dims[0] * dims[1]);
+    double c[3] = {tx + 0.5, ty + 0.5, tz + 0.5};
+    double dvec[3] = {c[0] - s[0], c[1] - s[1], c[2] - s[2]};
+    double L = sqrt(dvec[0] * dvec[0] + dvec[1] * dvec[1] + dvec[2] * dvec[2]);
+    double n[3];
+    if (L < 1e-12) { n[0] = 1.0; n[1] = 0.0; n[2] = 0.0; }
+    else { n[0] = dvec[0] / L; n[1] = dvec[1] / L; n[2] = dvec[2] / L; }
+    /* the first cell is the one containing s + 1e-9 n */
+    long cur[3];
+    for (int i = 0; i < 3; i++) {
+        double p = s[i] + 1e-9 * n[i];
+        long v = (long)floor(p);
+        cur[i] = v < 0 ? 0 : (v >= dims[i] ? dims[i] - 1 : v);
+    }
+    double tnext[3], step[3];
+    for (int i = 0; i < 3; i++) {
+        if (n[i] > 1e-300) { tnext[i] = ((double)(cur[i] + 1) - s[i]) / n[i]; step[i] = 1.0 / n[i]; }
+        else if (n[i] < -1e-300) { tnext[i] = ((double)cur[i] - s[i]) / n[i]; step[i] = -1.0 / n[i]; }
+        else { tnext[i] = INFINITY; step[i] = INFINITY; }
+    }
+    double tau_buf[16];
+    double *tau = nbins <= 16 ? tau_buf : (double *)calloc(nbins, sizeof(double));
+    for (int b = 0; b < nbins; b++) tau[b] = 0.0;
+    double t = 0.0, gamma = 0.0;
+    for (;;) {
+        double te = tnext[0];
+        if (tnext[1] < te) te = tnext[1];
+        if (tnext[2] < te) te = tnext[2];
+        long cidx = (cur[2] * dims[1] + cur[1]) * dims[0] + cur[0];
+        if (cidx == target) {
+            double rin = t, rout = te;
+            double vol = 4.0 * M_PI / 3.0 * (rout * rout * rout - rin * rin * rin);
+            for (int b = 0; b < nbins; b++) {
+                double dtau = kappa_bins[(size_t)b * ncell + cidx] * (rout - rin);
+                gamma += Qb[b] * exp(-tau[b]) * sigma[b] * (rout - rin) * phi_of(dtau) / (vol * dx * dx);
+            }
+            break;
+        }
+        for (int b = 0; b < nbins; b++) tau[b] += kappa_bins[(size_t)b * ncell + cidx] * (te - t);
+        /* advance every axis whose crossing coincides with te */
+        int moved = 0;
+        for (int i = 0; i < 3; i++) {
+            if (tnext[i] <= te + 1e-12) {
+                cur[i] += n[i] > 0 ? 1 : -1;
+                tnext[i] += step[i];
+                moved = 1;
+            }
+        }
+        t = te;
+        if (!moved || cur[0] < 0 || cur[1] < 0 || cur[2] < 0 || cur[0] >= dims[0] || cur[1] >= dims[1] ||
+            cur[2] >= dims[2])
+            break;   /* cannot happen for a target inside the box */
+    }
+    if (tau != tau_buf) free(tau);
+    return gamma;
+}
+
+int orc_point_sources(int nx, int ny, int nz, int nbins, const double *kappa_bins, const double *sigma,
+                      int nsrc, const double *pos, const double *Q, double dx, int nthreads,
+                      double *gamma)
+{
+    const int dims[3] = {nx, ny, nz};
+    const long ncell = (long)nx * ny * nz;
+    int nt = nthreads > 0 ? nthreads : 1;
+    (void)nt;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nt)
+#endif
+    for (long i = 0; i < ncell; i++) {
+        double g = 0.0;
+        for (int a = 0; a < nsrc; a++)
+            g += pt_one(dims, kappa_bins, ncell, nbins, sigma, Q + (size_t)a * nbins, pos + 3 * a, i, dx);
+        gamma[i] = g;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Ionization balance (App. B), hydrogen only, in the dt -> infinity limit:  */
+/*   alpha_A n_e n_HII = n_HI (Gamma_coll n_e + Gamma_gamma),                */
+/* Gamma_gamma = Gamma_point + Gamma^diff and Gamma^diff carries the local   */
+/* term Delta_alpha n_e n_HII / n_HI of Eq. (gamma_diff).  Taking that term  */
+/* at the same state as the rest, it moves to the left side and leaves       */
+/*   alpha_B n_e n_HII = n_HI (Gamma_coll n_e + g),  g = non-local rates.    */
+/* With n_HI = y n_H and n_e = n_HII = (1 - y) n_H, a = alpha_B n_H,         */
+/* c = Gamma_coll n_H:  (a + c) y^2 - (2a + c + g) y + a = 0, whose root in  */
+/* [0, 1] is y = 2a / (2a + c + g + sqrt(4 a g + (c + g)^2)) (no            */
+/* cancellation: the neutral fraction y is computed directly).              */
+/* ------------------------------------------------------------------------ */
+void orc_balance_eq(long ncell, const double *nH, double alphaB, double gcoll, const double *g,
+                    double *y)
+{
+    for (long i = 0; i < ncell; i++) {
+        double a = alphaB * nH[i], c = gcoll * nH[i], gg = g[i];
+        double disc = 4.0 * a * gg + (c + gg) * (c + gg);
+        y[i] = (a > 0.0) ? 2.0 * a / (2.0 * a + c + gg + sqrt(disc)) : 0.0;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* RT / ionization-balance fixed-point iteration (App. D): repeat            */
+/*   kappa = n_HI sigma0 dx,  eps = h nu0 dalpha n_e n_HII dx/(4 pi dnu)      */
+/*   (Eq. for eps_nu/(h nu) with the rectangular spectrum, at nu0),          */
+/*   J^in from the sweep (monochromatic at nu0, paper averaging),            */
+/*   g = 4 pi G J^in + Gamma_point,  y <- balance,                           */
+/* until max_cells |n_e^(i) - n_e^(i-1)| / n_e^(i) < tol.                    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double alphaA, alphaB, gcoll;   /* cm^3/s at the (fixed) temperature */
+    double sigma0;                  /* cm^2 at nu0 */
+    double h, nu0, dnu;             /* erg s, Hz, Hz (dnu = k_B T / h) */
+    double dx;                      /* cell width, cm */
+} orc_chem;
+
+int orc_iterate(const orc_sweep_cfg *cfg, const orc_chem *ch, const double *nH, int nsrc,
+                const double *pos, const double *Q, double tol, int max_iter, double *y,
+                double *resid_hist, int *iters)
+{
+    const long ncell = (long)cfg->nx * cfg->ny * cfg->nz;
+    double *kap = (double *)malloc(sizeof(double) * ncell);
+    double *eps = (double *)malloc(sizeof(double) * ncell);
+    double *jin = (double *)malloc(sizeof(double) * ncell);
+    double *gpt = (double *)malloc(sizeof(double) * ncell);
+    double *g = (double *)malloc(sizeof(double) * ncell);
+    double *yn = (double *)malloc(sizeof(double) * ncell);
+    if (!kap || !eps || !jin || !gpt || !g || !yn) return -1;
+    orc_sweep_cfg c = *cfg;
+    c.field_form = 1;
+    const double dalpha = ch->alphaA - ch->alphaB;
+    const double G = orc_band_integral(ch->sigma0, ch->h, ch->nu0, ch->nu0 + ch->dnu);
+    int it = 0, conv = 0;
+    for (it = 1; it <= max_iter; it++) {
+        for (long i = 0; i < ncell; i++) {
+            double nHI = y[i] * nH[i], ne = (1.0 - y[i]) * nH[i];
+            kap[i] = nHI * ch->sigma0 * ch->dx;
+            eps[i] = ch->h * ch->nu0 * dalpha * ne * ne * ch->dx / (4.0 * M_PI * ch->dnu);
+        }
+        orc_sweep(&c, kap, eps, jin, NULL);
+        const double s1 = ch->sigma0;
+        orc_point_sources(cfg->nx, cfg->ny, cfg->nz, 1, kap, &s1, nsrc, pos, Q, ch->dx, cfg->nthreads, gpt);
+        for (long i = 0; i < ncell; i++) g[i] = 4.0 * M_PI * G * jin[i] + gpt[i];
+        orc_balance_eq(ncell, nH, ch->alphaB, ch->gcoll, g, yn);
+        double r = 0.0;
+        for (long i = 0; i < ncell; i++) {
+            double ne_new = (1.0 - yn[i]) * nH[i], ne_old = (1.0 - y[i]) * nH[i];
+            double ri = fabs(ne_new - ne_old) / ne_new;
+            if (ri > r) r = ri;
+            y[i] = yn[i];
+        }
+        if (resid_hist) resid_hist[it - 1] = r;
+        if (r < tol) { conv = 1; break; }
+    }
+    if (iters) *iters = conv ? it : max_iter;
+    free(kap); free(eps); free(jin); free(gpt); free(g); free(yn);
+    return conv ? 0 : 1;
+}

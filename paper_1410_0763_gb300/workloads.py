@@ -1,0 +1,150 @@
+"""Seeded synthetic inputs for the diffuse-radiation sweep and the RT/ionization
+iteration.
+
+This module holds input recipes only -- random fields, grid shapes, physical
+constants and source lists -- and none of the method's arithmetic.  The tests
+feed the same arrays to the CUDA path and to the FP64 oracle; the benchmark
+uses the same recipes.
+
+Workloads (the paper's own test problems are parameter recipes in its text,
+Sec. 4, not datasets; these stand in for them):
+
+* ``lognormal_iid``   -- 16^3, N_side 1: kappa = 0.5 exp(Z), Z ~ N(0,1) i.i.d.
+  per cell, S ~ U[0,1) (seed 1).  FP64 path.
+* ``grf``             -- 64^3, N_side 4: periodic Gaussian random field with
+  power spectrum P(k) ~ k^-3, lognormal density rho = exp(s g - s^2/2), s = 1,
+  kappa = rho/<rho> * tau_box/N (tau_box = 10), S = rho/<rho> (seed 2).
+* ``hii_region``      -- 128^3, N_side 8: uniform n_H = 1e-3 cm^-3, T = 1e4 K,
+  box 6.6 kpc, one source of 5e48 ionizing photons/s at the box centre,
+  x0 = 1e-4 (the Test-1 medium of Sec. 4.1 with the source moved to the centre).
+* ``batch48``         -- 48 grids, N in {32,48,64,96}, N_side in {2,4,8}, the
+  ``grf`` recipe with s ~ U[0.5,1.5] (seed 4 + grid index).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# ---------------------------------------------------------------------------
+# Physical constants (cgs) and hydrogen rate coefficients at T = 1e4 K.
+# alpha_B is the value implied by the paper's printed recombination time
+# (t_rec = 122.4 Myr at n_H = 1e-3, Sec. 4.1) and Stromgren radius (5.4 kpc);
+# sigma0 is implied by the printed mean free path (51.4 pc at n_HI = 1e-3,
+# Sec. 4.2).  alpha_A and the collisional ionization rate come from the fits
+# the paper cites (Table tab:rate) and are not printed in it.
+# ---------------------------------------------------------------------------
+H_PLANCK = 6.62607015e-27      # erg s
+K_BOLTZ = 1.380649e-16         # erg / K
+NU0 = 3.2898419603e15          # Hz, hydrogen ionization threshold (13.6 eV)
+KPC = 3.0856775814913673e21    # cm
+PC = KPC * 1e-3
+MYR = 3.15576e13               # s
+SIGMA0 = 6.30e-18              # cm^2, HI cross section at nu0
+ALPHA_B_1E4 = 2.59e-13         # cm^3/s, case B at 1e4 K
+ALPHA_A_1E4 = 4.18e-13         # cm^3/s, case A at 1e4 K
+GAMMA_COLL_1E4 = 6.24e-16      # cm^3/s, HI collisional ionization at 1e4 K
+
+
+def chem_constants(T: float = 1e4, dx_cm: float = 6.6 * KPC / 128) -> dict:
+    """Rate coefficients and spectral constants for the fixed-temperature runs."""
+    if T != 1e4:
+        raise ValueError("only T = 1e4 K is tabulated")
+    return dict(alphaA=ALPHA_A_1E4, alphaB=ALPHA_B_1E4, gcoll=GAMMA_COLL_1E4, sigma0=SIGMA0,
+                h=H_PLANCK, nu0=NU0, dnu=K_BOLTZ * T / H_PLANCK, dx=dx_cm)
+
+
+# ---------------------------------------------------------------------------
+# Random fields
+# ---------------------------------------------------------------------------
+def gaussian_random_field(n: int, slope: float, rng: np.random.Generator) -> np.ndarray:
+    """Periodic Gaussian random field on n^3, P(k) ~ k^slope, zero mean, unit variance."""
+    w = rng.standard_normal((n, n, n))
+    wk = np.fft.rfftn(w)
+    kz = np.fft.fftfreq(n)[:, None, None]
+    ky = np.fft.fftfreq(n)[None, :, None]
+    kx = np.fft.rfftfreq(n)[None, None, :]
+    kk = np.sqrt(kx * kx + ky * ky + kz * kz)
+    amp = np.zeros_like(kk)
+    nz = kk > 0
+    amp[nz] = kk[nz] ** (0.5 * slope)
+    g = np.fft.irfftn(wk * amp, s=(n, n, n))
+    g -= g.mean()
+    g /= g.std()
+    return g
+
+
+def lognormal_density(n: int, sigma: float, slope: float, rng: np.random.Generator) -> np.ndarray:
+    """rho/<rho> for rho = exp(sigma g - sigma^2/2), g a unit-variance GRF."""
+    g = gaussian_random_field(n, slope, rng)
+    rho = np.exp(sigma * g - 0.5 * sigma * sigma)
+    return rho / rho.mean()
+
+
+# ---------------------------------------------------------------------------
+# Sweep workloads
+# ---------------------------------------------------------------------------
+@dataclass
+class SweepCase:
+    name: str
+    nside: int
+    kappa: np.ndarray          # [bins][z][y][x] or [z][y][x], per cell width
+    src: np.ndarray            # same shape: S (field_form 0) or eps*dx (field_form 1)
+    field_form: int = 0
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def shape(self):
+        return self.kappa.shape[-3:]
+
+
+def lognormal_iid(n: int = 16, nside: int = 1, seed: int = 1) -> SweepCase:
+    rng = np.random.default_rng(seed)
+    kappa = 0.5 * np.exp(rng.standard_normal((n, n, n)))
+    S = rng.random((n, n, n))
+    return SweepCase("lognormal_iid", nside, kappa, S, 0, dict(seed=seed, n=n))
+
+
+def grf(n: int = 64, nside: int = 4, seed: int = 2, sigma: float = 1.0, slope: float = -3.0,
+        tau_box: float = 10.0) -> SweepCase:
+    rng = np.random.default_rng(seed)
+    rho = lognormal_density(n, sigma, slope, rng)
+    kappa = rho * (tau_box / n)
+    S = rho.copy()
+    return SweepCase("grf", nside, kappa, S, 0,
+                     dict(seed=seed, n=n, sigma=sigma, slope=slope, tau_box=tau_box))
+
+
+def batch48(seed0: int = 4, count: int = 48):
+    """48 grids of uneven size and angular resolution (grf recipe per grid)."""
+    meta_rng = np.random.default_rng(seed0 * 1000 + 7)
+    sizes = meta_rng.choice([32, 48, 64, 96], size=count)
+    nsides = meta_rng.choice([2, 4, 8], size=count)
+    sigmas = meta_rng.uniform(0.5, 1.5, size=count)
+    return [grf(int(sizes[i]), int(nsides[i]), seed0 + i, float(sigmas[i])) for i in range(count)]
+
+
+# ---------------------------------------------------------------------------
+# Ionization workloads
+# ---------------------------------------------------------------------------
+@dataclass
+class HIICase:
+    name: str
+    nside: int
+    n: int
+    nH: np.ndarray             # [z][y][x] cm^-3
+    y0: np.ndarray             # initial neutral fraction
+    pos: np.ndarray            # [nsrc][3] (x, y, z) in cell widths
+    Q: np.ndarray              # [nsrc] photons/s
+    chem: dict
+    tol: float = 1e-6
+    box_cm: float = 6.6 * KPC
+
+
+def hii_region(n: int = 128, nside: int = 8, box_kpc: float = 6.6, nH: float = 1e-3,
+               Q: float = 5e48, x0: float = 1e-4, source_at: str = "center") -> HIICase:
+    dx = box_kpc * KPC / n
+    pos = np.array([[n / 2, n / 2, n / 2]]) if source_at == "center" else np.array([[0.0, 0.0, 0.0]])
+    return HIICase("hii_region", nside, n, np.full((n, n, n), nH), np.full((n, n, n), 1.0 - x0),
+                   pos, np.array([Q]), chem_constants(1e4, dx), 1e-6, box_kpc * KPC)
