@@ -1,0 +1,161 @@
+/*
+ * art.h -- C ABI of libart, a GB300 (sm_103a) implementation of the diffuse
+ * radiation ray-tracing scheme of Tanaka, Yoshikawa, Okamoto & Hasegawa (2014),
+ * "A new ray-tracing scheme for 3D diffuse radiation transfer on highly
+ * parallel architectures" (PASJ), and of the photo-ionization iteration it
+ * drives.
+ *
+ * Conventions shared by every entry point:
+ *   - Fields are 3D arrays of nz * ny * nx cells, x fastest ([z][y][x]); with
+ *     nu_bins > 1 the bin index is outermost ([bin][z][y][x]).  Lengths inside
+ *     the library are in cell widths, so kappa is the absorption coefficient
+ *     times the cell width (optical depth per cell width).
+ *   - The caller owns every input and output buffer.  The context owns its
+ *     device memory (field copies in sweep-axis layouts, ray-plane buffers,
+ *     per-class J partials, tables).  Nothing is retained from caller buffers
+ *     after a call returns, except that device-pointer inputs are read
+ *     stream-ordered on the given stream: keep them alive until that stream
+ *     has been synchronized.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that take host buffers synchronize that stream before
+ *     returning; calls on device buffers return without synchronizing.
+ *   - Every call returns an art_status and never aborts; the text of the last
+ *     error of a context is available from art_last_error().  A context is not
+ *     thread-safe; separate contexts are independent.
+ *   - Floating-point buffers are float (4 bytes) for ART_FP32 contexts and
+ *     double (8 bytes) for ART_FP64 contexts.
+ */
+#ifndef ART_H
+#define ART_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct art_ctx art_ctx;
+
+typedef enum {
+    ART_OK = 0,
+    ART_E_INVALID = 1,        /* bad argument or input value */
+    ART_E_CUDA = 2,           /* a CUDA call failed (message names it) */
+    ART_E_OOM = 3,            /* device or host allocation failed */
+    ART_E_NOT_CONVERGED = 4,  /* iteration hit max_iter before tol */
+    ART_E_TIMEOUT = 5,        /* a bounded device wait gave up */
+    ART_E_STATE = 6           /* call out of order (e.g. sweep before fields) */
+} art_status;
+
+enum { ART_FP32 = 0, ART_FP64 = 1 };
+/* ART_AVG_PAPER: Eq. (path_averaged_intensity): the cell average of the
+ * incoming intensity, J = J^in + S (Eq. mean_intensity). */
+enum { ART_AVG_PAPER = 0 };
+/* ART_FIELDS_S: inputs are (kappa, S), Eq. (rt).  ART_FIELDS_EPS: inputs are
+ * (kappa, eps) with eps the emissivity times the cell width (S = eps/kappa);
+ * kappa = 0 is then allowed and the transfer step adds eps * ds. */
+enum { ART_FIELDS_S = 0, ART_FIELDS_EPS = 1 };
+
+typedef struct {
+    int nx, ny, nz;   /* cells per axis, each >= 1 */
+    double dx_cm;     /* cell width in cm (used by the ionization side only) */
+} art_grid;
+
+typedef struct {
+    int precision;    /* ART_FP32 (default) or ART_FP64 */
+    int averaging;    /* ART_AVG_PAPER */
+    int field_form;   /* ART_FIELDS_S (default) or ART_FIELDS_EPS */
+    int tile_b;       /* ray-plane tile along the fastest transverse axis; 0 = auto */
+    int tile_c;       /* ray-plane tile along the other transverse axis;  0 = auto */
+    int slab;         /* slabs per launch along the sweep axis;           0 = auto */
+    int dir_split;    /* direction groups per octant class (J partials);  0 = auto */
+    double tie_tol;   /* dominant-axis tie tolerance (relative), default 1e-12 */
+} art_options;
+
+/* Statistics of one sweep, fixed at art_create. */
+typedef struct {
+    int64_t segments;        /* exact number of (ray, cell) pairs with ds > 0, all bins */
+    int32_t n_dirs;          /* 12 N_side^2 */
+    int32_t n_classes;       /* non-empty (dominant axis, octant) classes */
+    int32_t launches;        /* kernel launches per sweep and bin (sweep + reduce) */
+    int32_t ctas_per_launch; /* CTAs of one slab-block launch */
+    int32_t tile_b, tile_c, slab, dir_split;
+    int64_t device_bytes;    /* device memory owned by the context */
+} art_sweep_stats;
+
+/* Fill `opt` with defaults (FP32, paper averaging, (kappa, S) inputs, auto
+ * tiles, tie_tol 1e-12).  Never fails for a non-NULL pointer. */
+art_status art_options_default(art_options *opt);
+
+/*
+ * Create a context for one grid, angular resolution and number of frequency
+ * bins.  Directions are the 12 n_side^2 HEALPix pixel centres (Sec. 2.3,
+ * Gorski et al. 2005, RING order); each is swept by the family of parallel
+ * rays of Sec. 2.2 (Fig. parallel_ray): lines spaced one cell width apart on
+ * planes normal to the direction's dominant axis, through cell centres.
+ * Allocates all device memory of the sweep.  Errors: ART_E_INVALID (dims < 1,
+ * n_side < 1, nu_bins < 1, bad options), ART_E_OOM, ART_E_CUDA.
+ * On success *out owns the context; release it with art_destroy().
+ */
+art_status art_create(const art_grid *grid, int n_side, int nu_bins, const art_options *opt,
+                      art_ctx **out);
+
+/* Release a context and all its device memory.  NULL is accepted. */
+art_status art_destroy(art_ctx *ctx);
+
+/* Text of the last error on this context ("" if none).  The pointer stays
+ * valid until the next call on the context. */
+const char *art_last_error(const art_ctx *ctx);
+
+/*
+ * Host-only (no GPU needed): exact number of (ray, cell) pairs with path
+ * length > 0 in one sweep of one bin, from the per-slab segment tables the
+ * sweep uses.  Errors: ART_E_INVALID (dims < 1, n_side < 1, NULL out).
+ */
+art_status art_count_segments(const art_grid *grid, int n_side, double tie_tol, int64_t *out);
+
+/* Sweep statistics (segment count, launch shape, memory). */
+art_status art_get_stats(const art_ctx *ctx, art_sweep_stats *st);
+
+/*
+ * Set the absorption coefficient (per cell width) and the source function S
+ * (ART_FIELDS_S) or emissivity per cell width (ART_FIELDS_EPS) for every bin:
+ * two arrays of nu_bins * nz * ny * nx values ([bin][z][y][x]).  on_device = 0:
+ * host arrays, copied and validated synchronously; on_device = 1: device
+ * arrays, read stream-ordered on `stream`.  Validation (both cases): every
+ * value finite, kappa >= 0; failures return ART_E_INVALID and leave the
+ * previous fields in place.
+ */
+art_status art_set_fields(art_ctx *ctx, const void *kappa, const void *src, int on_device,
+                          void *stream);
+
+/*
+ * Band integrals G_b = int_bin sigma(nu)/(h nu) dnu, one per bin, used by the
+ * Gamma output of art_sweep: Gamma^diff_in = 4 pi sum_b G_b J^in_b (the
+ * non-local part of Eq. gamma_diff).  Host array of nu_bins doubles.  Without
+ * this call G_b = 0.
+ */
+art_status art_set_band(art_ctx *ctx, const double *G);
+
+/*
+ * One diffuse-radiation sweep (Sec. 2.2, Eqs. rt to mean_intensity, and
+ * Eq. gamma_diff):
+ *   J_in  = (1/N_d) sum_i Ibar^{ave,in}(n_i)          [bin][z][y][x]
+ *   J     = J_in + S  (S = eps/kappa for ART_FIELDS_EPS where kappa > 0,
+ *                      J = J_in where kappa = 0)       [bin][z][y][x]
+ *   gamma = 4 pi sum_b G_b J_in_b                      [z][y][x]
+ * Each output pointer may be NULL (not written).  on_device selects device or
+ * host output buffers.  The sweep marches every ray with vacuum entry
+ * intensity; Ibar^{ave,in} is the path-length-weighted average over the rays
+ * that cross a cell, which equals the Delta-tau weighting of
+ * Eq. (averaged_intensity) because kappa is constant inside a cell.
+ * Deterministic: repeated calls give bit-identical outputs.  Errors:
+ * ART_E_STATE (no fields set), ART_E_CUDA.
+ */
+art_status art_sweep(art_ctx *ctx, void *J, void *J_in, void *gamma, int on_device, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ART_H */

@@ -1,0 +1,252 @@
+"""Thin ctypes binding of libart (include/art.h).
+
+Argument marshalling only: every step of the sweep runs in the CUDA library.
+The module-level functions carry the C names; :class:`ArtSweep` wraps one
+context.  Buffers are torch CUDA tensors (device pointers, stream-ordered on
+the current torch stream) or numpy arrays (host pointers; the call copies and
+synchronizes).  Loading fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+ART_OK, ART_E_INVALID, ART_E_CUDA, ART_E_OOM, ART_E_NOT_CONVERGED, ART_E_TIMEOUT, ART_E_STATE = range(7)
+ART_FP32, ART_FP64 = 0, 1
+ART_AVG_PAPER = 0
+ART_FIELDS_S, ART_FIELDS_EPS = 0, 1
+_STATUS = {0: "ART_OK", 1: "ART_E_INVALID", 2: "ART_E_CUDA", 3: "ART_E_OOM",
+           4: "ART_E_NOT_CONVERGED", 5: "ART_E_TIMEOUT", 6: "ART_E_STATE"}
+
+
+class ArtGrid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx_cm", C.c_double)]
+
+
+class ArtOptions(C.Structure):
+    _fields_ = [("precision", C.c_int), ("averaging", C.c_int), ("field_form", C.c_int),
+                ("tile_b", C.c_int), ("tile_c", C.c_int), ("slab", C.c_int), ("dir_split", C.c_int),
+                ("tie_tol", C.c_double)]
+
+
+class ArtSweepStats(C.Structure):
+    _fields_ = [("segments", C.c_int64), ("n_dirs", C.c_int32), ("n_classes", C.c_int32),
+                ("launches", C.c_int32), ("ctas_per_launch", C.c_int32), ("tile_b", C.c_int32),
+                ("tile_c", C.c_int32), ("slab", C.c_int32), ("dir_split", C.c_int32),
+                ("device_bytes", C.c_int64)]
+
+
+class ArtError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load() -> C.CDLL:
+    """Load libart.so; raises if it is missing (no fallback path exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libart.so not built ({path}); run paper_1410_0763_gb300.build.build()")
+        lib = C.CDLL(path)
+        P = C.c_void_p
+        lib.art_options_default.argtypes = [C.POINTER(ArtOptions)]
+        lib.art_create.argtypes = [C.POINTER(ArtGrid), C.c_int, C.c_int, C.POINTER(ArtOptions), C.POINTER(P)]
+        lib.art_destroy.argtypes = [P]
+        lib.art_last_error.argtypes = [P]
+        lib.art_last_error.restype = C.c_char_p
+        lib.art_get_stats.argtypes = [P, C.POINTER(ArtSweepStats)]
+        lib.art_set_fields.argtypes = [P, P, P, C.c_int, P]
+        lib.art_set_band.argtypes = [P, C.POINTER(C.c_double)]
+        lib.art_sweep.argtypes = [P, P, P, P, C.c_int, P]
+        lib.art_count_segments.argtypes = [C.POINTER(ArtGrid), C.c_int, C.c_double, C.POINTER(C.c_int64)]
+        for f in ("art_options_default", "art_create", "art_count_segments", "art_destroy", "art_get_stats", "art_set_fields",
+                  "art_set_band", "art_sweep"):
+            getattr(lib, f).restype = C.c_int
+        _lib = lib
+        return lib
+
+
+# ---------------------------------------------------------------------------
+# C names
+# ---------------------------------------------------------------------------
+def art_options_default() -> ArtOptions:
+    o = ArtOptions()
+    load().art_options_default(C.byref(o))
+    return o
+
+
+def art_create(grid: ArtGrid, n_side: int, nu_bins: int, opt: ArtOptions | None):
+    h = C.c_void_p()
+    st = load().art_create(C.byref(grid), int(n_side), int(nu_bins), C.byref(opt) if opt else None, C.byref(h))
+    if st != ART_OK:
+        raise ArtError(st, "art_create failed")
+    return h
+
+
+def art_destroy(ctx) -> int:
+    return load().art_destroy(ctx)
+
+
+def art_last_error(ctx) -> str:
+    return load().art_last_error(ctx).decode()
+
+
+def art_get_stats(ctx) -> ArtSweepStats:
+    s = ArtSweepStats()
+    _check(ctx, load().art_get_stats(ctx, C.byref(s)))
+    return s
+
+
+def art_set_fields(ctx, kappa_ptr: int, src_ptr: int, on_device: int, stream: int) -> int:
+    return load().art_set_fields(ctx, C.c_void_p(kappa_ptr), C.c_void_p(src_ptr), int(on_device),
+                                 C.c_void_p(stream))
+
+
+def art_set_band(ctx, G) -> int:
+    arr = (C.c_double * len(G))(*[float(g) for g in G])
+    return load().art_set_band(ctx, arr)
+
+
+def art_sweep(ctx, J_ptr: int, Jin_ptr: int, gamma_ptr: int, on_device: int, stream: int) -> int:
+    return load().art_sweep(ctx, C.c_void_p(J_ptr or None), C.c_void_p(Jin_ptr or None),
+                            C.c_void_p(gamma_ptr or None), int(on_device), C.c_void_p(stream))
+
+
+def art_count_segments(shape, n_side: int, tie_tol: float = 1e-12) -> int:
+    nz, ny, nx = shape
+    out = C.c_int64(0)
+    st = load().art_count_segments(C.byref(ArtGrid(nx, ny, nz, 1.0)), int(n_side), float(tie_tol), C.byref(out))
+    if st != ART_OK:
+        raise ArtError(st, "art_count_segments failed")
+    return int(out.value)
+
+
+def _check(ctx, st: int):
+    if st != ART_OK:
+        raise ArtError(st, art_last_error(ctx) if ctx else "")
+
+
+# ---------------------------------------------------------------------------
+# Buffer marshalling
+# ---------------------------------------------------------------------------
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype, n):
+    """(pointer, on_device, keepalive) for a torch CUDA tensor or numpy array of n elements."""
+    if x is None:
+        return 0, None, None
+    if _is_torch(x):
+        import torch
+        want = torch.float64 if dtype == np.float64 else torch.float32
+        if x.dtype != want or not x.is_contiguous() or not x.is_cuda:
+            raise TypeError(f"expected a contiguous CUDA tensor of {want}")
+        if x.numel() != n:
+            raise ValueError(f"expected {n} elements, got {x.numel()}")
+        return x.data_ptr(), 1, x
+    a = np.asarray(x)
+    if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"expected a C-contiguous numpy array of {np.dtype(dtype).name}")
+    if a.size != n:
+        raise ValueError(f"expected {n} elements, got {a.size}")
+    return a.ctypes.data, 0, a
+
+
+def _stream(stream) -> int:
+    if stream is not None:
+        return int(stream)
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # pragma: no cover
+        pass
+    return 0
+
+
+class ArtSweep:
+    """One sweep context: grid (nz, ny, nx), N_side, frequency bins."""
+
+    def __init__(self, shape, nside: int, nbins: int = 1, precision: str = "fp32", field_form: int = 0,
+                 dx_cm: float = 1.0, tile_b: int = 0, tile_c: int = 0, slab: int = 0, dir_split: int = 0,
+                 tie_tol: float = 1e-12):
+        nz, ny, nx = shape
+        self.shape = (int(nz), int(ny), int(nx))
+        self.nside, self.nbins = int(nside), int(nbins)
+        self.dtype = np.float64 if precision == "fp64" else np.float32
+        opt = art_options_default()
+        opt.precision = ART_FP64 if precision == "fp64" else ART_FP32
+        opt.field_form = int(field_form)
+        opt.tile_b, opt.tile_c, opt.slab, opt.dir_split = tile_b, tile_c, slab, dir_split
+        opt.tie_tol = tie_tol
+        self._ctx = art_create(ArtGrid(nx, ny, nz, dx_cm), nside, nbins, opt)
+        self.ncell = nx * ny * nz
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            art_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def stats(self) -> ArtSweepStats:
+        return art_get_stats(self._ctx)
+
+    def set_fields(self, kappa, src, stream=None):
+        n = self.ncell * self.nbins
+        kp, kd, _k = _ptr(kappa, self.dtype, n)
+        sp, sd, _s = _ptr(src, self.dtype, n)
+        if kd != sd:
+            raise TypeError("kappa and src must both be host or both be device buffers")
+        _check(self._ctx, art_set_fields(self._ctx, kp, sp, kd, _stream(stream) if kd else 0))
+
+    def set_band(self, G):
+        if len(G) != self.nbins:
+            raise ValueError("one band integral per bin")
+        _check(self._ctx, art_set_band(self._ctx, G))
+
+    def sweep(self, J=None, J_in=None, gamma=None, stream=None):
+        n = self.ncell * self.nbins
+        bufs = [(J, n), (J_in, n), (gamma, self.ncell)]
+        ptrs, kinds, keep = [], set(), []
+        for b, m in bufs:
+            p, dev, k = _ptr(b, self.dtype, m)
+            ptrs.append(p)
+            keep.append(k)
+            if b is not None:
+                kinds.add(dev)
+        if len(kinds) > 1:
+            raise TypeError("outputs must all be host or all be device buffers")
+        on_dev = kinds.pop() if kinds else 1
+        _check(self._ctx, art_sweep(self._ctx, ptrs[0], ptrs[1], ptrs[2], on_dev,
+                                    _stream(stream) if on_dev else 0))
+        return J, J_in, gamma

@@ -1,0 +1,214 @@
+"""GPU parity of the diffuse-radiation sweep (C ABI) against the FP64 oracle.
+
+Bar: FP64 contexts within 1e-12 relative of the oracle; FP32 contexts within
+1e-5 relative per cell on J and J^in up to 128^3 and 1e-4 at 256^3 (the
+precision targets of the FP32 march).  The oracle runs on the FP32-rounded
+inputs, so only the arithmetic differs.  Full-size grids are checked on
+sampled cells that the oracle computes one by one.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1410_0763_gb300 import art, build
+from paper_1410_0763_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    art.load()
+
+
+def run(case_kappa, case_src, nside, precision="fp32", form=0, nbins=1, **kw):
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    shape = case_kappa.shape[-3:]
+    k = torch.as_tensor(np.ascontiguousarray(case_kappa), dtype=dt, device="cuda")
+    s = torch.as_tensor(np.ascontiguousarray(case_src), dtype=dt, device="cuda")
+    sw = art.ArtSweep(shape, nside, nbins, precision=precision, field_form=form, **kw)
+    J = torch.empty_like(k)
+    Jin = torch.empty_like(k)
+    sw.set_fields(k, s)
+    sw.sweep(J, Jin)
+    torch.cuda.synchronize()
+    out = J.cpu().numpy().astype(np.float64), Jin.cpu().numpy().astype(np.float64)
+    sw.close()
+    return out
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)))
+
+
+def f32(x):
+    return np.asarray(x, dtype=np.float32).astype(np.float64)
+
+
+def test_fp64_lognormal_16_nside1(orc):
+    c = wl.lognormal_iid(16, 1)
+    jin_o, j_o, nz = orc.sweep(c.kappa, c.src, 1)
+    assert nz == 0
+    J, Jin = run(c.kappa, c.src, 1, "fp64")
+    assert rel(Jin, jin_o) < 1e-12
+    assert rel(J, j_o) < 1e-12
+
+
+@pytest.mark.parametrize("tiles", [(32, 16, 4), (32, 32, 4), (32, 8, 4), (32, 16, 8)])
+def test_fp32_ragged_noncubic(orc, tiles):
+    rng = np.random.default_rng(7)
+    shape = (21, 26, 37)   # ragged against every tile size
+    kap = f32(0.5 * np.exp(rng.standard_normal(shape)))
+    S = f32(rng.random(shape))
+    jin_o, j_o, _ = orc.sweep(kap, S, 2)
+    tb, tc, blk = tiles
+    J, Jin = run(kap, S, 2, tile_b=tb, tile_c=tc, slab=blk)
+    assert rel(Jin, jin_o) < 1e-5
+    assert rel(J, j_o) < 1e-5
+
+
+@pytest.mark.parametrize("split", [1, 3])
+def test_fp64_ragged_direction_groups(orc, split):
+    rng = np.random.default_rng(8)
+    shape = (13, 22, 19)
+    kap = 0.7 * np.exp(rng.standard_normal(shape))
+    S = rng.random(shape)
+    jin_o, j_o, _ = orc.sweep(kap, S, 3)
+    J, Jin = run(kap, S, 3, "fp64", dir_split=split)
+    assert rel(Jin, jin_o) < 1e-12
+    assert rel(J, j_o) < 1e-12
+
+
+def test_fp32_grf_64_nside4(orc):
+    c = wl.grf(64, 4)
+    kap, S = f32(c.kappa), f32(c.src)
+    jin_o, j_o, _ = orc.sweep(kap, S, 4)
+    J, Jin = run(kap, S, 4)
+    assert rel(Jin, jin_o) < 1e-5
+    assert rel(J, j_o) < 1e-5
+
+
+def test_emissivity_form_with_transparent_cells(orc):
+    rng = np.random.default_rng(9)
+    shape = (18, 18, 18)
+    kap = 0.3 * np.exp(rng.standard_normal(shape))
+    kap[rng.random(shape) < 0.3] = 0.0
+    eps = rng.random(shape)
+    jin_o, j_o, _ = orc.sweep(kap, eps, 2, field_form=1)
+    J, Jin = run(kap, eps, 2, "fp64", form=1)
+    assert rel(Jin, jin_o) < 1e-12
+    assert rel(J, j_o) < 1e-12
+    J32, Jin32 = run(f32(kap), f32(eps), 2, form=1)
+    jin_o32, _, _ = orc.sweep(f32(kap), f32(eps), 2, field_form=1)
+    assert rel(Jin32, jin_o32) < 1e-5
+
+
+def test_uniform_optically_thin_and_thick(orc):
+    shape = (16, 16, 16)
+    for kap0 in (1e-6, 1e-3, 0.49, 0.51, 3.0, 60.0):
+        kap = np.full(shape, kap0)
+        S = np.full(shape, 0.8)
+        jin_o, _, _ = orc.sweep(f32(kap), f32(S), 2)
+        _, Jin = run(kap, S, 2)
+        assert rel(Jin, jin_o) < 1e-5, kap0
+
+
+def test_deterministic_bitwise():
+    c = wl.grf(32, 2, seed=5)
+    a = run(c.kappa, c.src, 2)
+    b = run(c.kappa, c.src, 2)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_host_buffers_match_device_buffers():
+    c = wl.grf(24, 2, seed=6)
+    kap = c.kappa.astype(np.float32)
+    S = c.src.astype(np.float32)
+    sw = art.ArtSweep(kap.shape, 2)
+    sw.set_fields(kap, S)
+    J = np.empty_like(kap)
+    Jin = np.empty_like(kap)
+    sw.sweep(J, Jin)
+    sw.close()
+    Jd, Jind = run(kap, S, 2)
+    assert np.array_equal(J.astype(np.float64), Jd)
+    assert np.array_equal(Jin.astype(np.float64), Jind)
+
+
+def test_gamma_output_and_band(orc):
+    c = wl.grf(20, 2, seed=3)
+    chem = wl.chem_constants()
+    G = orc.band_integral(chem["sigma0"], chem["h"], chem["nu0"], chem["nu0"] + chem["dnu"])
+    k = torch.as_tensor(c.kappa, dtype=torch.float64, device="cuda")
+    s = torch.as_tensor(c.src, dtype=torch.float64, device="cuda")
+    sw = art.ArtSweep(c.kappa.shape, 2, precision="fp64")
+    sw.set_fields(k, s)
+    sw.set_band([G])
+    Jin = torch.empty_like(k)
+    gam = torch.empty_like(k)
+    sw.sweep(None, Jin, gam)
+    torch.cuda.synchronize()
+    sw.close()
+    jin_o, _, _ = orc.sweep(c.kappa, c.src, 2)
+    assert rel(gam.cpu().numpy(), 4 * np.pi * G * jin_o) < 1e-12
+
+
+def test_multiple_bins(orc):
+    rng = np.random.default_rng(10)
+    shape = (12, 14, 16)
+    kap = f32(0.4 * np.exp(rng.standard_normal((3,) + shape)))
+    S = f32(rng.random((3,) + shape))
+    J, Jin = run(kap, S, 2, nbins=3)
+    for b in range(3):
+        jin_o, j_o, _ = orc.sweep(kap[b], S[b], 2)
+        assert rel(Jin[b], jin_o) < 1e-5
+        assert rel(J[b], j_o) < 1e-5
+
+
+def test_invalid_inputs_and_state():
+    shape = (8, 8, 8)
+    sw = art.ArtSweep(shape, 1)
+    with pytest.raises(art.ArtError) as e:
+        sw.sweep(torch.empty(512, device="cuda"))
+    assert e.value.status == art.ART_E_STATE
+    good = np.ones(shape, np.float32)
+    for bad in (np.nan, -1.0, np.inf):
+        k = good.copy()
+        k[3, 4, 5] = bad
+        with pytest.raises(art.ArtError) as e:
+            sw.set_fields(k, good)
+        assert e.value.status == art.ART_E_INVALID
+    s = good.copy()
+    s[0, 0, 0] = np.nan
+    with pytest.raises(art.ArtError):
+        sw.set_fields(good, s)
+    sw.set_fields(good, good)
+    J = np.empty_like(good)
+    sw.sweep(J)
+    assert np.all(np.isfinite(J))
+    sw.close()
+
+
+def test_stats_segment_count():
+    sw = art.ArtSweep((64, 64, 64), 4)
+    st = sw.stats
+    assert st.segments == art.art_count_segments((64, 64, 64), 4)
+    assert st.n_dirs == 192 and st.n_classes == 24
+    sw.close()
+
+
+@pytest.mark.parametrize("n,nside,bins,tol,ncells", [(128, 8, 1, 1e-5, 40), (256, 8, 1, 1e-4, 16)])
+def test_full_size_sampled_cells(orc, n, nside, bins, tol, ncells):
+    c = wl.grf(n, nside, seed=31, sigma=1.5)
+    kap, S = c.kappa.astype(np.float32), c.src.astype(np.float32)
+    J, Jin = run(kap, S, nside)
+    rng = np.random.default_rng(0)
+    cells = rng.choice(kap.size, ncells, replace=False)
+    # include the corners and a face centre
+    cells[:3] = [0, kap.size - 1, (n // 2) * n * n + (n // 2) * n]
+    ref = orc.jin_cells(f32(kap), f32(S), nside, cells)
+    assert rel(Jin.ravel()[cells], ref) < tol
