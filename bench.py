@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Benchmark of the diffuse-radiation parallel-ray sweep (Tanaka et al. 2014).
+
+Metric: ray-segment updates per second -- the exact number of (ray, cell)
+pairs with path length > 0 in one sweep (all directions, all bins), divided by
+device time.  A step is one sweep of the whole hot path: the per-slab
+transfer of Eq. (rt) along every ray of every HEALPix direction, the cell
+averages of Eq. (averaged_intensity), the angle average J^in / J of
+Eq. (mean_intensity) and the Gamma^diff epilogue of Eq. (gamma_diff).
+
+Default workload (``grf64``): 64^3 cells, N_side = 4 (192 directions), one
+frequency bin, FP32; kappa from a lognormal Gaussian random field (sigma = 1,
+P(k) ~ k^-3) scaled to box optical depth 10, S proportional to density.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank sweeps its own independent
+grid of the same size (weak scaling, no collective on the data path); the
+value is all ranks' segments divided by the max over ranks of the timed device
+time.  ``--impl reference`` times the FP64 CPU oracle on the host cores, on
+rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    "grf64": dict(n=64, nside=4, seed=2, sigma=1.0,
+                  desc="64^3 lognormal GRF (sigma 1, P(k)~k^-3, box tau 10), N_side 4 (192 dirs), 1 bin"),
+    "grf128": dict(n=128, nside=8, seed=3, sigma=1.0,
+                   desc="128^3 lognormal GRF (sigma 1, P(k)~k^-3, box tau 10), N_side 8 (768 dirs), 1 bin"),
+    "grf256": dict(n=256, nside=8, seed=5, sigma=1.5,
+                   desc="256^3 lognormal GRF (sigma 1.5, P(k)~k^-3, box tau 10), N_side 8 (768 dirs), 1 bin"),
+}
+METRIC = "ray-segment updates/sec"
+UNIT = "segments/s"
+L2_FLUSH_BYTES = 256 << 20      # > 129 MB L2
+# MUFU ex2 results per clock per SM on GB300 (measured) and SMs
+EX2_PER_CLK_SM = 32
+N_SM = 152
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default="grf64")
+    p.add_argument("--no-extra", action="store_true", help="skip the 128^3 / 256^3 side measurements")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing
+# ---------------------------------------------------------------------------
+class Dist:
+    def __init__(self, backend: str):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist:
+            self.dist.barrier()
+
+    def max(self, x: float, device) -> float:
+        if not self.dist:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist:
+            self.dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def make_case(wl_name: str, rank: int):
+    from paper_1410_0763_gb300 import workloads as wl
+    w = WORKLOADS[wl_name]
+    return wl.grf(w["n"], w["nside"], seed=w["seed"] + 1000 * rank, sigma=w["sigma"])
+
+
+def band_G():
+    from paper_1410_0763_gb300 import art
+    from paper_1410_0763_gb300 import workloads as wl
+    c = wl.chem_constants()
+    return art.art_band_integral(c["sigma0"], c["h"], c["nu0"], c["nu0"], c["nu0"] + c["dnu"])
+
+
+def time_device(sw, J, Jin, gam, steps, flush, torch):
+    """Per-step CUDA-event time (ms) of `steps` sweeps, L2 flushed between steps."""
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in evs:
+        flush.zero_()
+        a.record(stream)
+        sw.sweep(J, Jin, gam)
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def side_measure(wl_name, torch, dev, G, steps=5):
+    from paper_1410_0763_gb300 import art
+    c = make_case(wl_name, 0)
+    k = torch.as_tensor(c.kappa, dtype=torch.float32, device=dev)
+    s = torch.as_tensor(c.src, dtype=torch.float32, device=dev)
+    sw = art.ArtSweep(k.shape, c.nside)
+    sw.set_fields(k, s)
+    sw.set_band([G])
+    J, Jin, gam = torch.empty_like(k), torch.empty_like(k), torch.empty_like(k)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for _ in range(2):
+        sw.sweep(J, Jin, gam)
+    ms = time_device(sw, J, Jin, gam, steps, flush, torch)
+    seg = sw.stats.segments
+    sw.close()
+    t = statistics.median(ms)
+    return {"workload": WORKLOADS[wl_name]["desc"], "ms_per_step": round(t, 4),
+            "segments_per_step": int(seg), "value": seg / (t * 1e-3)}
+
+
+def cpu_baseline(case, seg_per_sweep: int, budget_s: float = 12.0) -> dict:
+    import oracle
+    oracle.build()
+    nt = oracle.default_threads()
+    k = case.kappa.astype(np.float32).astype(np.float64)
+    s = case.src.astype(np.float32).astype(np.float64)
+    nd = 12 * case.nside * case.nside
+    t0 = time.perf_counter()
+    segs = 0
+    sweeps = 0
+    while True:
+        _, n = oracle.sweep_range_count(k, s, case.nside, 0, nd, nthreads=nt)
+        segs += n
+        sweeps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": segs / dt, "unit": UNIT, "cores": nt, "kind": "oracle",
+            "sample": f"{sweeps} full FP64 oracle sweeps of the same workload ({segs} segments, {dt:.1f} s)"}
+
+
+def run_ours(args, d: Dist):
+    import torch
+    from paper_1410_0763_gb300 import art
+    from paper_1410_0763_gb300 import build as libbuild
+
+    dev = torch.device("cuda", d.local)
+    torch.cuda.set_device(dev)
+    if d.rank == 0:
+        libbuild.build()
+    d.barrier()
+    art.load()
+    case = make_case(args.workload, d.rank)
+    G = band_G()
+    k = torch.as_tensor(case.kappa, dtype=torch.float32, device=dev)
+    s = torch.as_tensor(case.src, dtype=torch.float32, device=dev)
+    sw = art.ArtSweep(k.shape, case.nside)
+    sw.set_fields(k, s)
+    sw.set_band([G])
+    st = sw.stats
+    seg = int(st.segments)
+    J, Jin, gam = torch.empty_like(k), torch.empty_like(k), torch.empty_like(k)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    clocks = ClockSampler(d.local)
+    clocks.start()
+    for _ in range(args.warmup):
+        sw.sweep(J, Jin, gam)
+    torch.cuda.synchronize()
+    d.barrier()
+    torch.cuda.synchronize()
+    ms = time_device(sw, J, Jin, gam, args.steps, flush, torch)
+    torch.cuda.synchronize()
+    d.barrier()
+    ck = clocks.stop()
+    total_ms = d.max(sum(ms), dev)
+    value = seg * d.world * args.steps / (total_ms * 1e-3)
+
+    # kernel-level roofline: same steps with per-kernel events inside the library
+    prof_steps = min(args.steps, 200)
+    sw.profile(True)
+    time_device(sw, J, Jin, gam, prof_steps, flush, torch)
+    sw.profile(False)
+    pr = sw.profile_read()
+    # algorithmic segments per sweep launch / average launch duration
+    achieved_gseg = seg * prof_steps / (pr.sweep_ms * 1e-3) / 1e9
+    sm_mhz = ck["sm_mhz"] or 2070.0
+    peak_gseg = EX2_PER_CLK_SM * N_SM * sm_mhz * 1e6 / 1e9
+    sweep_share = pr.sweep_ms / max(pr.sweep_ms + pr.reduce_ms, 1e-9)
+
+    # end to end through the C ABI with host buffers (pinned), copies included
+    e2e = None
+    if True:
+        kh = torch.as_tensor(case.kappa.astype(np.float32)).pin_memory()
+        sh = torch.as_tensor(case.src.astype(np.float32)).pin_memory()
+        Jh = torch.empty(k.shape, dtype=torch.float32).pin_memory()
+        e2e_steps = max(3, min(args.steps, 200))
+        for _ in range(3):
+            sw.set_fields(kh, sh)
+            sw.sweep(Jh)
+        torch.cuda.synchronize()
+        d.barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            sw.set_fields(kh, sh)
+            sw.sweep(Jh)
+        torch.cuda.synchronize()
+        dt = d.max(time.perf_counter() - t0, dev)
+        e2e = {"value": seg * d.world * e2e_steps / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(2 * kh.numel() * 4), "d2h_bytes_per_step": int(Jh.numel() * 4)}
+    sw.close()
+
+    extra = {}
+    if d.rank == 0 and d.world == 1 and not args.no_extra:
+        for name in ("grf128", "grf256"):
+            if name != args.workload:
+                try:
+                    extra[name] = side_measure(name, torch, dev, G)
+                except Exception as ex:  # pragma: no cover
+                    extra[name] = {"error": str(ex)}
+
+    cpu = None
+    if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(case, seg)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": d.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload]["desc"], "n": int(case.shape[0]),
+                   "nside": case.nside, "bins": 1, "segments_per_step": seg,
+                   "kernel": f"slab-block sweep, tile {st.tile_b}x{st.tile_c}, slab {st.slab}, "
+                             f"dir groups {st.dir_split}, {st.ctas_per_launch} CTAs x {st.launches - 1} launches",
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"weak x{d.world} (independent grid per GPU)"},
+        "roofline": {"bound": "alu", "achieved": achieved_gseg, "peak": peak_gseg, "unit": "Gseg/s",
+                     "frac": achieved_gseg / peak_gseg, "traffic": None,
+                     "kernel": "sweep_block_kernel", "kernel_share_of_step": sweep_share,
+                     "peak_basis": f"MUFU ex2 issue rate: 1 exp per segment, {EX2_PER_CLK_SM}/clk/SM x "
+                                   f"{N_SM} SMs x {sm_mhz:.0f} MHz (median SM clock under load)"},
+        "e2e": e2e,
+        "gpu_launches": int(args.steps * st.launches),
+        "clocks": ck,
+        "cpu_baseline": cpu,
+    }
+    if extra:
+        out["extra"] = extra
+    if d.rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args, d: Dist):
+    if d.rank != 0:
+        return
+    import oracle
+    oracle.build()
+    case = make_case(args.workload, 0)
+    nt = oracle.default_threads()
+    k = case.kappa.astype(np.float32).astype(np.float64)
+    s = case.src.astype(np.float32).astype(np.float64)
+    nd = 12 * case.nside * case.nside
+    # each step: a block of directions sized so that warmup + steps fit in ~3 minutes
+    _, n1 = oracle.sweep_range_count(k, s, case.nside, 0, 1, nthreads=1)
+    t0 = time.perf_counter()
+    oracle.sweep_range_count(k, s, case.nside, 0, min(nd, nt), nthreads=nt)
+    per_dir = (time.perf_counter() - t0) / min(nd, nt)
+    budget = 150.0 / max(args.steps + args.warmup, 1)
+    ndir = int(max(1, min(nd, budget / max(per_dir, 1e-9))))
+    pos = 0
+    segs, tsum = 0, 0.0
+    for i in range(args.warmup + args.steps):
+        d0 = pos % nd
+        d1 = min(nd, d0 + ndir)
+        pos = d1
+        t0 = time.perf_counter()
+        _, n = oracle.sweep_range_count(k, s, case.nside, d0, d1, nthreads=nt)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            segs += n
+            tsum += dt
+    value = segs / tsum
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": d.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tsum / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload]["desc"], "n": int(case.shape[0]),
+                   "nside": case.nside, "bins": 1},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle",
+                         "sample": f"each step: {ndir} of {nd} directions of the workload (FP64 oracle)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        d = Dist("gloo")
+        try:
+            run_reference(args, d)
+        finally:
+            d.close()
+        return
+    d = Dist("nccl")
+    try:
+        run_ours(args, d)
+    finally:
+        d.close()
+
+
+if __name__ == "__main__":
+    main()

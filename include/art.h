@@ -138,6 +138,16 @@ art_status art_set_fields(art_ctx *ctx, const void *kappa, const void *src, int 
 art_status art_set_band(art_ctx *ctx, const double *G);
 
 /*
+ * Host-only: G = int_{nu_lo}^{nu_hi} sigma(nu)/(h nu) dnu for the hydrogenic
+ * threshold power law sigma(nu) = sigma0 (nu/nu0)^-3, the band integral of
+ * Eq. (gamma_diff) (nu_lo = nu0, nu_hi = nu0 + k_B T/h for the rectangular
+ * recombination spectrum of Sec. 2.2).  Errors: ART_E_INVALID (non-positive
+ * or non-finite arguments, nu_hi < nu_lo, NULL out).
+ */
+art_status art_band_integral(double sigma0, double h, double nu0, double nu_lo, double nu_hi,
+                             double *G);
+
+/*
  * One diffuse-radiation sweep (Sec. 2.2, Eqs. rt to mean_intensity, and
  * Eq. gamma_diff):
  *   J_in  = (1/N_d) sum_i Ibar^{ave,in}(n_i)          [bin][z][y][x]
@@ -153,6 +163,27 @@ art_status art_set_band(art_ctx *ctx, const double *G);
  * ART_E_STATE (no fields set), ART_E_CUDA.
  */
 art_status art_sweep(art_ctx *ctx, void *J, void *J_in, void *gamma, int on_device, void *stream);
+
+/* Per-kernel device time accumulated while profiling is enabled. */
+typedef struct {
+    double sweep_ms;          /* slab-block sweep kernels */
+    int64_t sweep_launches;
+    double reduce_ms;         /* partial-reduction kernels */
+    int64_t reduce_launches;
+} art_profile;
+
+/*
+ * Enable (1) or disable (0) per-kernel timing: while enabled, art_sweep
+ * records CUDA events on its stream around the sweep launches of each bin and
+ * around the reduction.  The events add a few microseconds per sweep.
+ */
+art_status art_profile_enable(art_ctx *ctx, int enable);
+
+/*
+ * Wait for the recorded events, add their durations into *out and, if
+ * reset != 0, forget them.  Errors: ART_E_CUDA.
+ */
+art_status art_profile_read(art_ctx *ctx, art_profile *out, int reset);
 
 #ifdef __cplusplus
 }

@@ -69,6 +69,9 @@ def _lib_handle():
             lib.orc_sweep_dir.argtypes = [C.POINTER(SweepCfg), _D, _D, C.c_int, _D, _D]
             lib.orc_sweep_range.argtypes = [C.POINTER(SweepCfg), _D, _D, C.c_int, C.c_int, _D]
             lib.orc_sweep_range.restype = C.c_long
+            lib.orc_sweep_range_count.argtypes = [C.POINTER(SweepCfg), _D, _D, C.c_int, C.c_int, _D,
+                                                  C.POINTER(C.c_longlong)]
+            lib.orc_sweep_range_count.restype = C.c_long
             lib.orc_sweep.argtypes = [C.POINTER(SweepCfg), _D, _D, _D, _D]
             lib.orc_sweep.restype = C.c_long
             lib.orc_lattice.argtypes = [C.POINTER(SweepCfg), C.c_int, _L, C.POINTER(C.c_int), _D]
@@ -137,6 +140,19 @@ def sweep_range(kappa, src, nside, d0, d1, field_form=0, tie_tol=1e-12, nthreads
     if nz < 0:
         raise MemoryError("oracle sweep: allocation failed")
     return acc, int(nz)
+
+
+def sweep_range_count(kappa, src, nside, d0, d1, field_form=0, tie_tol=1e-12, nthreads=None):
+    """Like sweep_range, also returning the number of segments marched."""
+    k, s = _f64(kappa), _f64(src)
+    acc = np.empty_like(k)
+    n = C.c_longlong(0)
+    cfg = _cfg(k.shape, nside, field_form, tie_tol, nthreads)
+    nz = _lib_handle().orc_sweep_range_count(C.byref(cfg), _dp(k), _dp(s), int(d0), int(d1), _dp(acc),
+                                             C.byref(n))
+    if nz < 0:
+        raise MemoryError("oracle sweep: allocation failed")
+    return acc, int(n.value)
 
 
 def sweep_dir(kappa, src, nside, d, field_form=0, tie_tol=1e-12):

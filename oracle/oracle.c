@@ -263,6 +263,7 @@ typedef struct {
     double *ds, *Iin;
     int maxseg, nrec;
     long only_cell;             /* >= 0: accumulate A, W for this cell only */
+    long long nseg;             /* segments marched */
 } ray_ctx;
 
 /* Eq. (rt) for one segment, with the path-averaged incoming intensity
@@ -287,6 +288,7 @@ static void seg_update(void *vctx, long cell, double ds)
         r->Iin[r->nrec] = Iin;
     }
     r->nrec++;
+    r->nseg++;
     if (r->form == 0) {
         const double S = r->src[cell];
         r->I = S + (Iin - S) * e;                 /* Eq. (rt) */
@@ -305,8 +307,8 @@ static void make_frame(const orc_sweep_cfg *cfg, int d, frame_t *f)
 
 /* Accumulate A (sum of ds * Ibar_in) and W (sum of ds) of direction d over
  * every ray of its family. */
-static void sweep_dir(const orc_sweep_cfg *cfg, const double *kappa, const double *src, int d,
-                      double *A, double *W)
+static long long sweep_dir(const orc_sweep_cfg *cfg, const double *kappa, const double *src, int d,
+                           double *A, double *W)
 {
     frame_t f;
     make_frame(cfg, d, &f);
@@ -325,6 +327,7 @@ static void sweep_dir(const orc_sweep_cfg *cfg, const double *kappa, const doubl
             r.I = 0.0;   /* vacuum boundary: nothing enters the box */
             march_ray(&f, j, k, seg_update, &r);
         }
+    return r.nseg;
 }
 
 int orc_sweep_dir(const orc_sweep_cfg *cfg, const double *kappa, const double *src, int d,
@@ -341,24 +344,25 @@ int orc_sweep_dir(const orc_sweep_cfg *cfg, const double *kappa, const double *s
 /* Sum over directions d0 <= d < d1, in RING order, of the per-cell average
  * incoming intensity A/W of Eq. (averaged_intensity) (not yet divided by N_d).
  * Returns the number of (cell, direction) pairs with W = 0 (expected: 0). */
-long orc_sweep_range(const orc_sweep_cfg *cfg, const double *kappa, const double *src,
-                     int d0, int d1, double *acc)
+long orc_sweep_range_count(const orc_sweep_cfg *cfg, const double *kappa, const double *src,
+                           int d0, int d1, double *acc, long long *nseg)
 {
     const long ncell = (long)cfg->nx * cfg->ny * cfg->nz;
     int nt = cfg->nthreads > 0 ? cfg->nthreads : 1;
     double *buf = (double *)malloc(sizeof(double) * ncell * 2 * (size_t)nt);
     if (!buf) return -1;
     long nzero = 0;
+    long long segs = 0;
     memset(acc, 0, sizeof(double) * ncell);
     for (int dc = d0; dc < d1; dc += nt) {
         int cnt = (d1 - dc) < nt ? (d1 - dc) : nt;
 #ifdef _OPENMP
-#pragma omp parallel for schedule(static, 1) num_threads(nt)
+#pragma omp parallel for schedule(static, 1) num_threads(nt) reduction(+ : segs)
 #endif
         for (int t = 0; t < cnt; t++) {
             double *A = buf + (size_t)2 * t * ncell, *W = A + ncell;
             memset(A, 0, sizeof(double) * ncell * 2);
-            sweep_dir(cfg, kappa, src, dc + t, A, W);
+            segs += sweep_dir(cfg, kappa, src, dc + t, A, W);
         }
         for (int t = 0; t < cnt; t++) {
             const double *A = buf + (size_t)2 * t * ncell, *W = A + ncell;
@@ -369,7 +373,14 @@ long orc_sweep_range(const orc_sweep_cfg *cfg, const double *kappa, const double
         }
     }
     free(buf);
+    if (nseg) *nseg = segs;
     return nzero;
+}
+
+long orc_sweep_range(const orc_sweep_cfg *cfg, const double *kappa, const double *src,
+                     int d0, int d1, double *acc)
+{
+    return orc_sweep_range_count(cfg, kappa, src, d0, d1, acc, NULL);
 }
 
 /* Full sweep, Eq. (mean_intensity): J^in = (1/N_d) sum_i Ibar^{ave,in}(n_i),

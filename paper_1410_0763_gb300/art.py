@@ -41,6 +41,11 @@ class ArtSweepStats(C.Structure):
                 ("device_bytes", C.c_int64)]
 
 
+class ArtProfile(C.Structure):
+    _fields_ = [("sweep_ms", C.c_double), ("sweep_launches", C.c_int64), ("reduce_ms", C.c_double),
+                ("reduce_launches", C.c_int64)]
+
+
 class ArtError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{_STATUS.get(status, status)}: {msg}")
@@ -76,7 +81,10 @@ def load() -> C.CDLL:
         lib.art_set_band.argtypes = [P, C.POINTER(C.c_double)]
         lib.art_sweep.argtypes = [P, P, P, P, C.c_int, P]
         lib.art_count_segments.argtypes = [C.POINTER(ArtGrid), C.c_int, C.c_double, C.POINTER(C.c_int64)]
-        for f in ("art_options_default", "art_create", "art_count_segments", "art_destroy", "art_get_stats", "art_set_fields",
+        lib.art_band_integral.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_double)]
+        lib.art_profile_enable.argtypes = [P, C.c_int]
+        lib.art_profile_read.argtypes = [P, C.POINTER(ArtProfile), C.c_int]
+        for f in ("art_band_integral", "art_profile_enable", "art_profile_read", "art_options_default", "art_create", "art_count_segments", "art_destroy", "art_get_stats", "art_set_fields",
                   "art_set_band", "art_sweep"):
             getattr(lib, f).restype = C.c_int
         _lib = lib
@@ -129,6 +137,24 @@ def art_sweep(ctx, J_ptr: int, Jin_ptr: int, gamma_ptr: int, on_device: int, str
                             C.c_void_p(gamma_ptr or None), int(on_device), C.c_void_p(stream))
 
 
+def art_band_integral(sigma0, h, nu0, nu_lo, nu_hi) -> float:
+    out = C.c_double(0.0)
+    st = load().art_band_integral(float(sigma0), float(h), float(nu0), float(nu_lo), float(nu_hi), C.byref(out))
+    if st != ART_OK:
+        raise ArtError(st, "art_band_integral: bad arguments")
+    return out.value
+
+
+def art_profile_enable(ctx, enable: bool) -> int:
+    return load().art_profile_enable(ctx, int(bool(enable)))
+
+
+def art_profile_read(ctx, reset: bool = True) -> ArtProfile:
+    p = ArtProfile()
+    _check(ctx, load().art_profile_read(ctx, C.byref(p), int(bool(reset))))
+    return p
+
+
 def art_count_segments(shape, n_side: int, tie_tol: float = 1e-12) -> int:
     nz, ny, nx = shape
     out = C.c_int64(0)
@@ -154,6 +180,8 @@ def _ptr(x, dtype, n):
     """(pointer, on_device, keepalive) for a torch CUDA tensor or numpy array of n elements."""
     if x is None:
         return 0, None, None
+    if _is_torch(x) and not x.is_cuda:
+        x = x.numpy()          # CPU (e.g. pinned) tensor: a host buffer
     if _is_torch(x):
         import torch
         want = torch.float64 if dtype == np.float64 else torch.float32
@@ -220,6 +248,12 @@ class ArtSweep:
     @property
     def stats(self) -> ArtSweepStats:
         return art_get_stats(self._ctx)
+
+    def profile(self, enable: bool = True):
+        _check(self._ctx, art_profile_enable(self._ctx, enable))
+
+    def profile_read(self, reset: bool = True) -> ArtProfile:
+        return art_profile_read(self._ctx, reset)
 
     def set_fields(self, kappa, src, stream=None):
         n = self.ncell * self.nbins

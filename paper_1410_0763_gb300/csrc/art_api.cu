@@ -35,7 +35,7 @@ struct art_ctx {
     // device memory
     void *d_field = nullptr;   // [3][nbins][ncell] vec2
     void *d_plane[2] = {nullptr, nullptr};
-    void *d_jpart = nullptr;   // [n_part][ncell] vec2
+    void *d_jpart = nullptr;   // [n_part][ncell] real, natural layout
     void *d_segs = nullptr;
     DirDev *d_dirs = nullptr;
     ClassDev *d_classes = nullptr;
@@ -44,6 +44,9 @@ struct art_ctx {
     void *d_stage = nullptr;   // [2][nbins][ncell] real: host-input staging
     void *d_out = nullptr;     // [2 nbins + 1][ncell] real: host-output staging
     int *d_flag = nullptr;
+    // profiling: event triples (before sweep launches, after them, after reduce)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;
 };
 
 namespace {
@@ -83,18 +86,11 @@ struct KCfg {
 const KCfg kFP32Cfgs[] = {{32, 16, 4, 256}, {32, 32, 4, 256}, {32, 8, 4, 256}, {32, 16, 8, 256}};
 const KCfg kFP64Cfgs[] = {{16, 16, 4, 128}};
 
-template <typename real, int TB, int TC, int BLK, int NT>
-size_t smem_bytes()
-{
-    constexpr int NS = (TB + BLK) * (TC + BLK);
-    return size_t(BLK) * NS * sizeof(typename Vec2<real>::type) + 2 * size_t(NS) * sizeof(real);
-}
-
-template <typename real, int TB, int TC, int BLK, int NT>
+template <typename real, int TB, int TC, int BLK, int NT, int K, int MINB>
 cudaError_t launch_sweep(const SweepArgs<real> &a, int nwork, cudaStream_t st)
 {
-    const size_t sm = smem_bytes<real, TB, TC, BLK, NT>();
-    auto kern = sweep_block_kernel<real, TB, TC, BLK, NT>;
+    const size_t sm = SweepShape<TB, TC, BLK, NT, K>::template bytes<real>();
+    auto kern = sweep_block_kernel<real, TB, TC, BLK, NT, K, MINB>;
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
@@ -106,17 +102,17 @@ cudaError_t launch_sweep(const SweepArgs<real> &a, int nwork, cudaStream_t st)
 cudaError_t dispatch_sweep(const art_ctx *ctx, const SweepArgs<float> &a, cudaStream_t st)
 {
     const int tb = ctx->TB, tc = ctx->TC, blk = ctx->BLK;
-    if (tb == 32 && tc == 16 && blk == 4) return launch_sweep<float, 32, 16, 4, 256>(a, ctx->n_work, st);
-    if (tb == 32 && tc == 32 && blk == 4) return launch_sweep<float, 32, 32, 4, 256>(a, ctx->n_work, st);
-    if (tb == 32 && tc == 8 && blk == 4) return launch_sweep<float, 32, 8, 4, 256>(a, ctx->n_work, st);
-    if (tb == 32 && tc == 16 && blk == 8) return launch_sweep<float, 32, 16, 8, 256>(a, ctx->n_work, st);
+    if (tb == 32 && tc == 16 && blk == 4) return launch_sweep<float, 32, 16, 4, 256, 4, 3>(a, ctx->n_work, st);
+    if (tb == 32 && tc == 32 && blk == 4) return launch_sweep<float, 32, 32, 4, 256, 2, 2>(a, ctx->n_work, st);
+    if (tb == 32 && tc == 8 && blk == 4) return launch_sweep<float, 32, 8, 4, 256, 4, 3>(a, ctx->n_work, st);
+    if (tb == 32 && tc == 16 && blk == 8) return launch_sweep<float, 32, 16, 8, 256, 2, 2>(a, ctx->n_work, st);
     return cudaErrorInvalidConfiguration;
 }
 
 cudaError_t dispatch_sweep(const art_ctx *ctx, const SweepArgs<double> &a, cudaStream_t st)
 {
     if (ctx->TB == 16 && ctx->TC == 16 && ctx->BLK == 4)
-        return launch_sweep<double, 16, 16, 4, 128>(a, ctx->n_work, st);
+        return launch_sweep<double, 16, 16, 4, 128, 2, 1>(a, ctx->n_work, st);
     return cudaErrorInvalidConfiguration;
 }
 
@@ -201,8 +197,13 @@ template <typename real> art_status do_sweep(art_ctx *ctx, real *J, real *Jin, r
     real *planes[2] = {static_cast<real *>(ctx->d_plane[0]), static_cast<real *>(ctx->d_plane[1])};
     for (int b = 0; b < ctx->nbins; ++b) {
         SweepArgs<real> a;
-        for (int ax = 0; ax < 3; ++ax) a.field[ax] = fields + ((long long)ax * ctx->nbins + b) * n;
-        a.jpart = static_cast<v2 *>(ctx->d_jpart);
+        a.field0 = fields + (0LL * ctx->nbins + b) * n;
+        a.field1 = fields + (1LL * ctx->nbins + b) * n;
+        a.field2 = fields + (2LL * ctx->nbins + b) * n;
+        a.jpart = static_cast<real *>(ctx->d_jpart);
+        a.nx = ctx->grid.nx;
+        a.ny = ctx->grid.ny;
+        a.nz = ctx->grid.nz;
         a.segs = static_cast<const SegEntry<real> *>(ctx->d_segs);
         a.dirs = ctx->d_dirs;
         a.classes = ctx->d_classes;
@@ -210,20 +211,27 @@ template <typename real> art_status do_sweep(art_ctx *ctx, real *J, real *Jin, r
         a.ncell = n;
         a.split = ctx->split;
         a.field_form = ctx->opt.field_form;
+        cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+        if (ctx->profiling) {
+            CK(ctx, cudaEventCreate(&e0));
+            CK(ctx, cudaEventCreate(&e1));
+            CK(ctx, cudaEventCreate(&e2));
+            ctx->ev.push_back(e0);
+            ctx->ev.push_back(e1);
+            ctx->ev.push_back(e2);
+            CK(ctx, cudaEventRecord(e0, st));
+        }
         for (int k = 0; k < ctx->nblocks; ++k) {
             a.kblock = k;
             a.plane_in = planes[k & 1];
             a.plane_out = planes[(k + 1) & 1];
             CK(ctx, dispatch_sweep(ctx, a, st));
         }
+        if (ctx->profiling) CK(ctx, cudaEventRecord(e1, st));
         ReduceArgs<real> r;
-        r.jpart = static_cast<const v2 *>(ctx->d_jpart);
+        r.jpart = static_cast<const real *>(ctx->d_jpart);
         r.field_nat = fields + (2LL * ctx->nbins + b) * n;
-        r.part_axis = ctx->d_part_axis;
         r.n_part = ctx->n_part;
-        r.nx = ctx->grid.nx;
-        r.ny = ctx->grid.ny;
-        r.nz = ctx->grid.nz;
         r.ncell = n;
         r.inv_nd = real(1.0 / ctx->nd);
         r.gamma_coef = real(4.0 * M_PI * ctx->G[b]);
@@ -235,6 +243,7 @@ template <typename real> art_status do_sweep(art_ctx *ctx, real *J, real *Jin, r
         const int nt = 256;
         reduce_kernel<real><<<(unsigned)((n + nt - 1) / nt), nt, 0, st>>>(r);
         CK(ctx, cudaGetLastError());
+        if (ctx->profiling) CK(ctx, cudaEventRecord(e2, st));
     }
     return ART_OK;
 }
@@ -355,7 +364,7 @@ art_status art_create(const art_grid *grid, int n_side, int nu_bins, const art_o
     ALLOC(ctx->d_field, 3 * (size_t)nu_bins * n * 2 * rs);
     ALLOC(ctx->d_plane[0], (size_t)ctx->plane_elems * rs);
     ALLOC(ctx->d_plane[1], (size_t)ctx->plane_elems * rs);
-    ALLOC(ctx->d_jpart, (size_t)ctx->n_part * n * 2 * rs);
+    ALLOC(ctx->d_jpart, (size_t)ctx->n_part * n * rs);
     ALLOC(ctx->d_segs, t.geo.size() * (ctx->prec == ART_FP64 ? sizeof(SegEntry<double>) : sizeof(SegEntry<float>)));
     ALLOC(ctx->d_dirs, t.dirs.size() * sizeof(DirDev));
     ALLOC(ctx->d_classes, t.classes.size() * sizeof(ClassDev));
@@ -385,6 +394,17 @@ art_status art_create(const art_grid *grid, int n_side, int nu_bins, const art_o
     return ART_OK;
 }
 
+art_status art_band_integral(double sigma0, double h, double nu0, double nu_lo, double nu_hi, double *G)
+{
+    if (!G || !(sigma0 > 0.0) || !(h > 0.0) || !(nu0 > 0.0) || !(nu_lo > 0.0) || !(nu_hi >= nu_lo) ||
+        !std::isfinite(sigma0 * h * nu0 * nu_lo * nu_hi))
+        return ART_E_INVALID;
+    // sigma/(h nu) = sigma0 nu0^3 / (h nu^4); its antiderivative is -sigma0 nu0^3 / (3 h nu^3)
+    const double r_lo = nu0 / nu_lo, r_hi = nu0 / nu_hi;
+    *G = sigma0 / (3.0 * h) * (r_lo * r_lo * r_lo - r_hi * r_hi * r_hi);
+    return ART_OK;
+}
+
 art_status art_count_segments(const art_grid *grid, int n_side, double tie_tol, int64_t *out)
 {
     if (!grid || !out || grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || n_side < 1 || n_side > 1024)
@@ -403,9 +423,37 @@ art_status art_count_segments(const art_grid *grid, int n_side, double tie_tol, 
     return ART_OK;
 }
 
+art_status art_profile_enable(art_ctx *ctx, int enable)
+{
+    if (!ctx) return ART_E_INVALID;
+    ctx->profiling = enable != 0;
+    return ART_OK;
+}
+
+art_status art_profile_read(art_ctx *ctx, art_profile *out, int reset)
+{
+    if (!ctx || !out) return ART_E_INVALID;
+    for (size_t i = 0; i + 2 < ctx->ev.size(); i += 3) {
+        float a = 0.f, b = 0.f;
+        CK(ctx, cudaEventSynchronize(ctx->ev[i + 2]));
+        CK(ctx, cudaEventElapsedTime(&a, ctx->ev[i], ctx->ev[i + 1]));
+        CK(ctx, cudaEventElapsedTime(&b, ctx->ev[i + 1], ctx->ev[i + 2]));
+        out->sweep_ms += a;
+        out->sweep_launches += ctx->nblocks;
+        out->reduce_ms += b;
+        out->reduce_launches += 1;
+    }
+    if (reset) {
+        for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+        ctx->ev.clear();
+    }
+    return ART_OK;
+}
+
 art_status art_destroy(art_ctx *ctx)
 {
     if (!ctx) return ART_OK;
+    for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     void *ptrs[] = {ctx->d_field, ctx->d_plane[0], ctx->d_plane[1], ctx->d_jpart, ctx->d_segs,
                     ctx->d_dirs, ctx->d_classes, ctx->d_work, ctx->d_part_axis, ctx->d_stage,
                     ctx->d_out, ctx->d_flag};

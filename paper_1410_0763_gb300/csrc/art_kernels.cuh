@@ -64,16 +64,21 @@ struct WorkItem {
     int cls, pb, pc, group;   // class, tile origin (canonical b, c), direction group
 };
 
+template <typename real> struct alignas(4 * sizeof(real)) Quad {
+    real x, y, z, w;
+};
+
 template <typename real> struct SweepArgs {
-    const typename Vec2<real>::type *field[3];   // (kappa, src) in axis-a layout, one bin
+    const typename Vec2<real>::type *field0, *field1, *field2;   // (kappa, src), axis-a layouts, one bin
     const real *plane_in;
     real *plane_out;
-    typename Vec2<real>::type *jpart;            // [n_part][ncell] (sum, compensation)
+    real *jpart;                 // [n_part][ncell] J partials, natural [z][y][x] layout
     const SegEntry<real> *segs;
     const DirDev *dirs;
     const ClassDev *classes;
     const WorkItem *work;
     long long ncell;
+    int nx, ny, nz;
     int split;
     int kblock;
     int field_form;
@@ -89,39 +94,43 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
-// phi(x) = (1 - e^-x)/x, phi(0) = 1 (the path-averaged attenuation of a
-// segment, Sec. 2.2).  Below x = 0.5 the Maclaurin series
-// sum_n (-x)^n/(n+1)! to n = 7 (truncation < 1.5e-8 relative); above, the
-// hardware base-2 exponential (relative error ~2^-22) where 1 - e^-x loses
-// at most ~2 bits.
-__device__ __forceinline__ float phi_of(float x)
+// Coefficients of one segment of optical depth x = kappa ds:
+//   dsph = ds phi(x), xph = x phi(x) = 1 - e^-x,  phi(x) = (1 - e^-x)/x, phi(0) = 1
+// (phi: the path-averaged attenuation of the segment, Sec. 2.2).  FP32: below
+// x = 1/4 the Maclaurin series sum_n (-x)^n/(n+1)! to n = 5 (truncation
+// < 6e-8 relative); above, 1 - 2^(-x log2 e) from the hardware base-2
+// exponential (relative error ~2^-22, so < 1e-6 on 1 - e^-x there) and the
+// per-cell reciprocal 1/kappa (no per-segment division).  k2 = -kappa log2 e
+// and rk = 1/kappa are precomputed per cell.
+__device__ __forceinline__ void seg_coef(float kap, float k2, float rk, float ds, float &dsph, float &xph)
 {
-    float p = fmaf(x, -1.0f / 40320.0f, 1.0f / 5040.0f);
-    p = fmaf(x, p, -1.0f / 720.0f);
-    p = fmaf(x, p, 1.0f / 120.0f);
-    p = fmaf(x, p, -1.0f / 24.0f);
-    p = fmaf(x, p, 1.0f / 6.0f);
-    p = fmaf(x, p, -0.5f);
-    p = fmaf(x, p, 1.0f);
-    const float e = ex2_approx(-1.4426950408889634f * x);
-    const float q = __fdividef(1.0f - e, x);
-    return x < 0.5f ? p : q;
+    const float x = kap * ds;
+    float q = fmaf(x, -1.0f / 720.0f, 1.0f / 120.0f);
+    q = fmaf(x, q, -1.0f / 24.0f);
+    q = fmaf(x, q, 1.0f / 6.0f);
+    q = fmaf(x, q, -0.5f);
+    q = fmaf(x, q, 1.0f);
+    const float om = 1.0f - ex2_approx(k2 * ds);
+    const bool small = x < 0.25f;
+    dsph = small ? ds * q : om * rk;
+    xph = small ? x * q : om;
 }
 
-__device__ __forceinline__ double phi_of(double x) { return x > 0.0 ? -expm1(-x) / x : 1.0; }
-
-// One segment of Eq. (rt): deposit ds * I_in * phi(kappa ds) (the path-
-// averaged incoming intensity times the segment length) into A, then advance
-// I = S + (I - S) e^-dtau (field_form 0) or I = I e^-dtau + eps ds phi
-// (field_form 1, S = eps/kappa).
-template <typename real>
-__device__ __forceinline__ void seg_step(real &I, real &A, real kap, real src, real ds, int form)
+__device__ __forceinline__ void seg_coef(double kap, double, double, double ds, double &dsph, double &xph)
 {
-    const real x = kap * ds;
-    const real ph = phi_of(x);
-    const real dsph = ds * ph;
+    const double x = kap * ds;
+    const double ph = x > 0.0 ? -expm1(-x) / x : 1.0;
+    dsph = ds * ph;
+    xph = x * ph;
+}
+
+// One segment of Eq. (rt): deposit ds * I_in * phi into A (the path-averaged
+// incoming intensity times the segment length), then advance
+// I = S + (I - S) e^-x (form 0) or I = I e^-x + eps ds phi (form 1, S = eps/kappa).
+template <typename real>
+__device__ __forceinline__ void seg_apply(real &I, real &A, real src, real dsph, real xph, int form)
+{
     A = fma(I, dsph, A);
-    const real xph = x * ph;
     if (form == 0)
         I = fma(src - I, xph, I);
     else
@@ -146,47 +155,100 @@ __device__ __forceinline__ void kahan_add(double &s, double &c, double v)
 
 // ---------------------------------------------------------------------------
 // Slab-block sweep kernel.  Grid: one CTA per work item (class, tile, group).
+// The CTA takes the directions of its group K at a time: for each slab the K
+// directions share the cell loads and the exchange barriers, and each thread
+// carries K independent intensity chains per column.  Shared memory: (kappa,
+// src) of the region (tile + BLK + 1 upstream columns) for the BLK slabs, two
+// exchange buffers of K planes over the region, and the segment tables of a
+// chunk of directions.  Region columns upstream of the box are never written
+// and stay 0: rays there carry the vacuum boundary intensity.
 // ---------------------------------------------------------------------------
-template <typename real, int TB, int TC, int BLK, int NT>
-__global__ void __launch_bounds__(NT) sweep_block_kernel(const SweepArgs<real> p)
+template <typename real> struct DirSm {
+    long long plane_off;
+    real na;
+    int d0b, d0c;    // column shifts over the slab block
+};
+
+template <int TB, int TC, int BLK, int NT, int K> struct SweepShape {
+    static constexpr int HB = BLK + 1;
+    static constexpr int WB = TB + HB, WC = TC + HB, NS = WB * WC;
+    static constexpr int OPT = (TB * TC) / NT;
+    static constexpr int MAXH = BLK * (TB + BLK) + TC * BLK;
+    static constexpr int HPT = (MAXH + NT - 1) / NT;
+    static constexpr int DCH = 8 * K;   // directions staged per chunk
+    template <typename real> __host__ __device__ static constexpr size_t off_x()
+    {
+        return size_t(BLK) * NS * sizeof(typename Vec2<real>::type);
+    }
+    template <typename real> __host__ __device__ static constexpr size_t off_t()
+    {
+        return (off_x<real>() + 2 * size_t(K) * NS * sizeof(real) + 31) / 32 * 32;
+    }
+    template <typename real> __host__ __device__ static constexpr size_t off_d()
+    {
+        return off_t<real>() + size_t(DCH) * BLK * sizeof(SegEntry<real>);
+    }
+    template <typename real> __host__ __device__ static constexpr size_t bytes()
+    {
+        return off_d<real>() + size_t(DCH) * sizeof(DirSm<real>);
+    }
+};
+
+__device__ __forceinline__ float rcp_or_zero(float k)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(k));
+    return k > 0.0f ? r : 0.0f;
+}
+__device__ __forceinline__ double rcp_or_zero(double k) { return k > 0.0 ? 1.0 / k : 0.0; }
+
+template <typename real, int TB, int TC, int BLK, int NT, int K, int MINB>
+__global__ void __launch_bounds__(NT, MINB) sweep_block_kernel(const SweepArgs<real> p)
 {
     using v2 = typename Vec2<real>::type;
-    constexpr int WB = TB + BLK, WC = TC + BLK, NS = WB * WC;
+    using Sh = SweepShape<TB, TC, BLK, NT, K>;
+    constexpr int HB = Sh::HB, WB = Sh::WB, WC = Sh::WC, NS = Sh::NS, OPT = Sh::OPT, HPT = Sh::HPT,
+                  DCH = Sh::DCH;
     static_assert((TB * TC) % NT == 0, "owned columns must split evenly over threads");
-    constexpr int OPT = (TB * TC) / NT;
-    constexpr int MAXH = BLK * (TB + BLK) + TC * BLK;
-    constexpr int HPT = (MAXH + NT - 1) / NT;
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    v2 *ks = reinterpret_cast<v2 *>(smem_raw);                 // [BLK][NS] (kappa, src)
-    real *xbuf = reinterpret_cast<real *>(ks + BLK * NS);      // [2][NS] exchange
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    v2 *ks = reinterpret_cast<v2 *>(smem_raw);
+    real *xbuf = reinterpret_cast<real *>(smem_raw + Sh::template off_x<real>());   // [2][K][NS]
+    SegEntry<real> *tsm = reinterpret_cast<SegEntry<real> *>(smem_raw + Sh::template off_t<real>());
+    DirSm<real> *dsm = reinterpret_cast<DirSm<real> *>(smem_raw + Sh::template off_d<real>());
 
     const WorkItem w = p.work[blockIdx.x];
     const ClassDev C = p.classes[w.cls];
     const int m0 = p.kblock * BLK;
     if (m0 >= C.Na) return;
     const int Bp = min(BLK, C.Na - m0);
-    const int Rb = w.pb - BLK, Rc = w.pc - BLK;   // origin of the smem region
-    const v2 *__restrict__ F = p.field[C.a];
+    const int Rb = w.pb - HB, Rc = w.pc - HB;   // origin of the smem region
+    const v2 *__restrict__ F = C.a == 0 ? p.field0 : (C.a == 1 ? p.field1 : p.field2);
     const int tid = threadIdx.x;
+    const int form = p.field_form;
 
-    // Stage kappa and src of the region (tile + BLK upstream columns) for the
-    // BLK slabs; cells outside the box read as vacuum (0, 0).
-    for (int e = tid; e < BLK * NS; e += NT) {
-        const int i = e / NS, r = e - i * NS;
-        const int gb = Rb + r % WB, gc = Rc + r / WB;
-        v2 v;
-        v.x = real(0);
-        v.y = real(0);
-        if (i < Bp && gb >= 0 && gc >= 0 && gb < C.Nb && gc < C.Nc) {
-            const int am = m0 + i;
-            const int pa = C.sa > 0 ? am : C.Na - 1 - am;
-            const int pb = C.sb > 0 ? gb : C.Nb - 1 - gb;
-            const int pc = C.sc > 0 ? gc : C.Nc - 1 - gc;
-            v = F[((long long)pa * C.Nc + pc) * C.Nb + pb];
+    // Stage the region's (kappa, src) for the BLK slabs row by row (vacuum
+    // outside the box), and clear the exchange buffers.
+    {
+        const int nrows = BLK * WC;
+        for (int e = tid; e < nrows * WB; e += NT) {
+            const int rowi = e / WB, rb = e - rowi * WB;
+            const int i = rowi / WC, rc = rowi - i * WC;
+            const int gb = Rb + rb, gc = Rc + rc;
+            v2 v;
+            v.x = real(0);
+            v.y = real(0);
+            if (i < Bp && gb >= 0 && gc >= 0 && gb < C.Nb && gc < C.Nc) {
+                const int am = m0 + i;
+                const int pa = C.sa > 0 ? am : C.Na - 1 - am;
+                const int pb = C.sb > 0 ? gb : C.Nb - 1 - gb;
+                const int pc = C.sc > 0 ? gc : C.Nc - 1 - gc;
+                v = F[((long long)pa * C.Nc + pc) * C.Nb + pb];
+            }
+            ks[e] = v;
         }
-        ks[e] = v;
     }
+    for (int e = tid; e < 2 * K * NS; e += NT) xbuf[e] = real(0);
 
     int o_gb[OPT], o_gc[OPT], o_r[OPT];
     bool o_ok[OPT];
@@ -195,7 +257,7 @@ __global__ void __launch_bounds__(NT) sweep_block_kernel(const SweepArgs<real> p
         const int o = tid + s * NT;
         o_gb[s] = w.pb + o % TB;
         o_gc[s] = w.pc + o / TB;
-        o_r[s] = (o / TB + BLK) * WB + (o % TB + BLK);
+        o_r[s] = (o / TB + HB) * WB + (o % TB + HB);
         o_ok[s] = o_gb[s] < C.Nb && o_gc[s] < C.Nc;
     }
     real js[OPT][BLK], jc[OPT][BLK];
@@ -203,153 +265,215 @@ __global__ void __launch_bounds__(NT) sweep_block_kernel(const SweepArgs<real> p
     for (int s = 0; s < OPT; ++s)
 #pragma unroll
         for (int i = 0; i < BLK; ++i) js[s][i] = jc[s][i] = real(0);
-    __syncthreads();
 
     const int nd = C.dir_end - C.dir_begin;
     const int d0 = C.dir_begin + (int)((long long)nd * w.group / p.split);
     const int d1 = C.dir_begin + (int)((long long)nd * (w.group + 1) / p.split);
-    const int form = p.field_form;
+    const bool first = p.kblock == 0;
     int xs = 0;
 
-    // Intensity fetched across a column boundary: vacuum outside the box,
-    // harmless garbage outside the smem region (only cone cells that never
-    // feed the owned tile read there).
-    auto fetch = [&](const real *X, int gb, int gc) -> real {
-        if (gb < 0 || gc < 0) return real(0);
-        const int rb = gb - Rb, rc = gc - Rc;
-        if (rb < 0 || rc < 0) return real(0);
-        return X[rc * WB + rb];
-    };
-
-    for (int d = d0; d < d1; ++d) {
-        const DirDev D = p.dirs[d];
-        const SegEntry<real> *tab = p.segs + D.seg_off + m0;
-        int D0b = 0, D0c = 0;
-        for (int i = 0; i < Bp; ++i) {
-            const int code = tab[i].code;
-            D0b += (code >> 3) & 1;
-            D0c += (code >> 4) & 1;
+    for (int c0 = d0; c0 < d1; c0 += DCH) {
+        const int cnt = min(DCH, d1 - c0);
+        __syncthreads();   // previous chunk's tables are no longer read
+        for (int e = tid; e < cnt * BLK; e += NT) {
+            const int dl = e / BLK, i = e - dl * BLK;
+            if (i < Bp) tsm[e] = p.segs[p.dirs[c0 + dl].seg_off + m0 + i];
         }
-        // upstream cone of this direction: top strip D0c rows of TB + D0b
-        // columns, then TC rows of D0b columns
-        const int hw = TB + D0b;
-        const int n1 = D0c * hw, nh = n1 + TC * D0b;
-        int h_gb[HPT], h_gc[HPT], h_r[HPT];
-        bool h_ok[HPT];
-#pragma unroll
-        for (int s = 0; s < HPT; ++s) {
-            const int h = tid + s * NT;
-            int gb = -1, gc = -1;
-            if (h < n1) {
-                gc = w.pc - D0c + h / hw;
-                gb = w.pb - D0b + h % hw;
-            } else if (h < nh) {
-                const int h2 = h - n1;
-                gc = w.pc + h2 / D0b;
-                gb = w.pb - D0b + h2 % D0b;
+        for (int dl = tid; dl < cnt; dl += NT) {
+            const DirDev D = p.dirs[c0 + dl];
+            int sb = 0, sc = 0;
+            for (int i = 0; i < Bp; ++i) {
+                const int code = p.segs[D.seg_off + m0 + i].code;
+                sb += (code >> 3) & 1;
+                sc += (code >> 4) & 1;
             }
-            h_ok[s] = (h < nh) && gb >= 0 && gc >= 0 && gb < C.Nb && gc < C.Nc;
-            h_gb[s] = gb;
-            h_gc[s] = gc;
-            h_r[s] = (gc - Rc) * WB + (gb - Rb);
+            DirSm<real> q;
+            q.plane_off = D.plane_off;
+            q.na = real(D.na);
+            q.d0b = sb;
+            q.d0c = sc;
+            dsm[dl] = q;
         }
-        const real *pin = p.plane_in + D.plane_off;
-        real oI[OPT], hI[HPT];
+        __syncthreads();
+
+        for (int g0 = 0; g0 < cnt; g0 += K) {
+            const int kk = min(K, cnt - g0);
+            // union cone of the group
+            int D0b = 0, D0c = 0;
+            int Dbk[K], Dck[K];   // remaining cone of each direction
+            long long poff[K];
+            real na[K];
 #pragma unroll
-        for (int s = 0; s < OPT; ++s)
-            oI[s] = (p.kblock > 0 && o_ok[s]) ? pin[(long long)o_gc[s] * C.Nb + o_gb[s]] : real(0);
+            for (int k = 0; k < K; ++k) {
+                const DirSm<real> D = dsm[g0 + (k < kk ? k : 0)];
+                poff[k] = D.plane_off;
+                na[k] = k < kk ? D.na : real(0);
+                Dbk[k] = k < kk ? D.d0b : 0;
+                Dck[k] = k < kk ? D.d0c : 0;
+                D0b = max(D0b, Dbk[k]);
+                D0c = max(D0c, Dck[k]);
+            }
+            const int hw = TB + D0b;
+            const int n1 = D0c * hw, nh = n1 + TC * D0b;
+            int h_gb[HPT], h_gc[HPT], h_r[HPT];
+            bool h_ok[HPT];
 #pragma unroll
-        for (int s = 0; s < HPT; ++s)
-            hI[s] = (p.kblock > 0 && h_ok[s]) ? pin[(long long)h_gc[s] * C.Nb + h_gb[s]] : real(0);
-        const real na = real(D.na);
-        int Db = D0b, Dc = D0c;
+            for (int s = 0; s < HPT; ++s) {
+                const int h = tid + s * NT;
+                int gb = -1, gc = -1;
+                if (h < n1) {
+                    gc = w.pc - D0c + h / hw;
+                    gb = w.pb - D0b + h % hw;
+                } else if (h < nh) {
+                    const int h2 = h - n1;
+                    gc = w.pc + h2 / D0b;
+                    gb = w.pb - D0b + h2 % D0b;
+                }
+                h_ok[s] = h < nh && gb >= 0 && gc >= 0 && gb < C.Nb && gc < C.Nc;
+                h_gb[s] = gb;
+                h_gc[s] = gc;
+                h_r[s] = h_ok[s] ? (gc - Rc) * WB + (gb - Rb) : 0;
+            }
+            real oI[OPT][K], hI[HPT][K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const real *pin = p.plane_in + poff[k];
+#pragma unroll
+                for (int s = 0; s < OPT; ++s)
+                    oI[s][k] = (!first && o_ok[s] && k < kk) ? pin[(long long)o_gc[s] * C.Nb + o_gb[s]] : real(0);
+#pragma unroll
+                for (int s = 0; s < HPT; ++s)
+                    hI[s][k] = (!first && h_ok[s] && k < kk) ? pin[(long long)h_gc[s] * C.Nb + h_gb[s]] : real(0);
+            }
 
 #pragma unroll
-        for (int i = 0; i < BLK; ++i) {
-            if (i < Bp) {
-                const SegEntry<real> g = tab[i];
-                const int nseg = (g.code & 3) + 1;
-                const int cfirst = (g.code >> 2) & 1;
-                const int shb = (g.code >> 3) & 1, shc = (g.code >> 4) & 1;
-                const v2 *ksi = ks + i * NS;
-                bool h_act[HPT];
-                real hk[HPT], hs[HPT], ok[OPT], os[OPT], oA[OPT];
+            for (int i = 0; i < BLK; ++i) {
+                if (i < Bp) {
+                    SegEntry<real> g[K];
+                    int nsmax = 1, Db = 0, Dc = 0;   // union of the remaining cones
 #pragma unroll
-                for (int s = 0; s < HPT; ++s) {
-                    h_act[s] = h_ok[s] && h_gb[s] >= w.pb - Db && h_gc[s] >= w.pc - Dc;
-                    hk[s] = hs[s] = real(0);
-                    if (h_act[s]) {
-                        const v2 v = ksi[h_r[s]];
-                        hk[s] = v.x;
-                        hs[s] = v.y;
+                    for (int k = 0; k < K; ++k) {
+                        g[k] = tsm[(g0 + (k < kk ? k : 0)) * BLK + i];
+                        if (k >= kk) g[k].code = 0;   // inactive: one segment, ignored below
+                        nsmax = max(nsmax, (g[k].code & 3) + 1);
+                        Db = max(Db, Dbk[k]);
+                        Dc = max(Dc, Dck[k]);
+                        Dbk[k] -= (g[k].code >> 3) & 1;
+                        Dck[k] -= (g[k].code >> 4) & 1;
                     }
-                }
+                    const v2 *ksi = ks + i * NS;
+                    real ok[OPT], os[OPT], ok2[OPT], ork[OPT], oA[OPT][K];
+                    real hk[HPT], hs[HPT], hk2[HPT], hrk[HPT];
+                    bool h_act[HPT], hw_act[HPT];
 #pragma unroll
-                for (int s = 0; s < OPT; ++s) {
-                    const v2 v = ksi[o_r[s]];
-                    ok[s] = v.x;
-                    os[s] = v.y;
-                    oA[s] = real(0);
-                    seg_step(oI[s], oA[s], ok[s], os[s], g.ds1, form);
-                }
+                    for (int s = 0; s < OPT; ++s) {
+                        const v2 c = ksi[o_r[s]];
+                        ok[s] = c.x;
+                        os[s] = c.y;
+                        ok2[s] = real(-1.4426950408889634) * c.x;
+                        ork[s] = rcp_or_zero(c.x);
 #pragma unroll
-                for (int s = 0; s < HPT; ++s) {
-                    real dummy = real(0);
-                    if (h_act[s]) seg_step(hI[s], dummy, hk[s], hs[s], g.ds1, form);
-                }
-                if (nseg >= 2) {
-                    int ob, oc;
-                    if (nseg == 2) {
-                        ob = shb;
-                        oc = shc;
-                    } else {
-                        ob = cfirst ? 0 : 1;
-                        oc = cfirst;
+                        for (int k = 0; k < K; ++k) {
+                            real dsph, xph;
+                            seg_coef(ok[s], ok2[s], ork[s], g[k].ds1, dsph, xph);
+                            oA[s][k] = real(0);
+                            seg_apply(oI[s][k], oA[s][k], os[s], dsph, xph, form);
+                        }
                     }
-                    for (int step = 2; step <= nseg; ++step) {
-                        const real dsk = step == 2 ? g.ds2 : g.ds3;
-                        real *X = xbuf + xs * NS;
 #pragma unroll
-                        for (int s = 0; s < OPT; ++s) X[o_r[s]] = oI[s];
+                    for (int s = 0; s < HPT; ++s) {
+                        hw_act[s] = ((tid & ~31) + s * NT) < nh;
+                        h_act[s] = h_ok[s] && h_gb[s] >= w.pb - Db && h_gc[s] >= w.pc - Dc;
+                        hk[s] = hs[s] = hk2[s] = hrk[s] = real(0);
+                        if (hw_act[s] && h_act[s]) {
+                            const v2 c = ksi[h_r[s]];
+                            hk[s] = c.x;
+                            hs[s] = c.y;
+                            hk2[s] = real(-1.4426950408889634) * c.x;
+                            hrk[s] = rcp_or_zero(c.x);
 #pragma unroll
-                        for (int s = 0; s < HPT; ++s)
-                            if (h_act[s]) X[h_r[s]] = hI[s];
+                            for (int k = 0; k < K; ++k) {
+                                real dsph, xph, dummy = real(0);
+                                seg_coef(hk[s], hk2[s], hrk[s], g[k].ds1, dsph, xph);
+                                seg_apply(hI[s][k], dummy, hs[s], dsph, xph, form);
+                            }
+                        }
+                    }
+                    for (int step = 2; step <= nsmax; ++step) {
+                        real *X = xbuf + xs * K * NS;
+#pragma unroll
+                        for (int k = 0; k < K; ++k) {
+#pragma unroll
+                            for (int s = 0; s < OPT; ++s) X[k * NS + o_r[s]] = oI[s][k];
+#pragma unroll
+                            for (int s = 0; s < HPT; ++s)
+                                if (hw_act[s] && h_act[s]) X[k * NS + h_r[s]] = hI[s][k];
+                        }
                         __syncthreads();
 #pragma unroll
-                        for (int s = 0; s < OPT; ++s) {
-                            real Iin = fetch(X, o_gb[s] - ob, o_gc[s] - oc);
-                            seg_step(Iin, oA[s], ok[s], os[s], dsk, form);
-                            oI[s] = Iin;
-                        }
+                        for (int k = 0; k < K; ++k) {
+                            const int ns = (g[k].code & 3) + 1;
+                            if (ns < step) continue;   // uniform: this direction is done
+                            const int cf = (g[k].code >> 2) & 1;
+                            int ob, oc;
+                            if (ns == 2) {
+                                ob = (g[k].code >> 3) & 1;
+                                oc = (g[k].code >> 4) & 1;
+                            } else if (step == 2) {
+                                ob = 1 - cf;
+                                oc = cf;
+                            } else {
+                                ob = cf;
+                                oc = 1 - cf;
+                            }
+                            const int off = oc * WB + ob;
+                            const real dsk = step == 2 ? g[k].ds2 : g[k].ds3;
+                            const real *Xk = X + k * NS;
 #pragma unroll
-                        for (int s = 0; s < HPT; ++s) {
-                            if (h_act[s]) {
-                                real Iin = fetch(X, h_gb[s] - ob, h_gc[s] - oc);
-                                real dummy = real(0);
-                                seg_step(Iin, dummy, hk[s], hs[s], dsk, form);
-                                hI[s] = Iin;
+                            for (int s = 0; s < OPT; ++s) {
+                                real dsph, xph;
+                                seg_coef(ok[s], ok2[s], ork[s], dsk, dsph, xph);
+                                real Iin = Xk[o_r[s] - off];
+                                seg_apply(Iin, oA[s][k], os[s], dsph, xph, form);
+                                oI[s][k] = Iin;
+                            }
+#pragma unroll
+                            for (int s = 0; s < HPT; ++s) {
+                                if (hw_act[s] && h_act[s]) {
+                                    real dsph, xph, dummy = real(0);
+                                    seg_coef(hk[s], hk2[s], hrk[s], dsk, dsph, xph);
+                                    real Iin = Xk[h_r[s] - off];
+                                    seg_apply(Iin, dummy, hs[s], dsph, xph, form);
+                                    hI[s][k] = Iin;
+                                }
                             }
                         }
                         xs ^= 1;
-                        // the third segment comes from the other neighbour
-                        ob = 1 - ob;
-                        oc = 1 - oc;
+                    }
+#pragma unroll
+                    for (int s = 0; s < OPT; ++s) {
+                        if (o_ok[s]) {
+                            real a = real(0);
+#pragma unroll
+                            for (int k = 0; k < K; ++k) a = fma(oA[s][k], na[k], a);
+                            kahan_add(js[s][i], jc[s][i], a);
+                        }
                     }
                 }
+            }
 #pragma unroll
-                for (int s = 0; s < OPT; ++s)
-                    if (o_ok[s]) kahan_add(js[s][i], jc[s][i], oA[s] * na);
-                Db -= shb;
-                Dc -= shc;
+            for (int k = 0; k < K; ++k) {
+                if (k < kk) {
+                    real *pout = p.plane_out + poff[k];
+#pragma unroll
+                    for (int s = 0; s < OPT; ++s)
+                        if (o_ok[s]) pout[(long long)o_gc[s] * C.Nb + o_gb[s]] = oI[s][k];
+                }
             }
         }
-        real *pout = p.plane_out + D.plane_off;
-#pragma unroll
-        for (int s = 0; s < OPT; ++s)
-            if (o_ok[s]) pout[(long long)o_gc[s] * C.Nb + o_gb[s]] = oI[s];
     }
 
-    v2 *J = p.jpart + (long long)(C.part0 + w.group) * p.ncell;
+    real *J = p.jpart + (long long)(C.part0 + w.group) * p.ncell;
 #pragma unroll
     for (int s = 0; s < OPT; ++s) {
         if (!o_ok[s]) continue;
@@ -360,10 +484,10 @@ __global__ void __launch_bounds__(NT) sweep_block_kernel(const SweepArgs<real> p
             if (i < Bp) {
                 const int am = m0 + i;
                 const int pa = C.sa > 0 ? am : C.Na - 1 - am;
-                v2 v;
-                v.x = js[s][i];
-                v.y = jc[s][i];
-                J[((long long)pa * C.Nc + pc) * C.Nb + pb] = v;
+                const int x = C.a == 0 ? pa : pb;
+                const int y = C.a == 1 ? pa : (C.a == 0 ? pb : pc);
+                const int z = C.a == 2 ? pa : pc;
+                J[((long long)z * p.ny + y) * p.nx + x] = js[s][i] - jc[s][i];
             }
         }
     }
@@ -373,11 +497,9 @@ __global__ void __launch_bounds__(NT) sweep_block_kernel(const SweepArgs<real> p
 // Sum the class partials (fixed order, Kahan) into J^in, J and Gamma.
 // ---------------------------------------------------------------------------
 template <typename real> struct ReduceArgs {
-    const typename Vec2<real>::type *jpart;
-    const typename Vec2<real>::type *field_nat;   // (kappa, src) in [z][y][x]
-    const int *part_axis;
+    const real *jpart;                             // [n_part][ncell], natural layout
+    const typename Vec2<real>::type *field_nat;    // (kappa, src) in [z][y][x]
     int n_part;
-    int nx, ny, nz;
     long long ncell;
     real inv_nd;
     real gamma_coef;     // 4 pi G_b
@@ -391,16 +513,8 @@ template <typename real> __global__ void reduce_kernel(const ReduceArgs<real> p)
     using v2 = typename Vec2<real>::type;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= p.ncell) return;
-    const int x = (int)(i % p.nx);
-    const int y = (int)((i / p.nx) % p.ny);
-    const int z = (int)(i / ((long long)p.nx * p.ny));
-    const long long idx[3] = {((long long)x * p.nz + z) * p.ny + y, ((long long)y * p.nz + z) * p.nx + x, i};
     real s = real(0), c = real(0);
-    for (int k = 0; k < p.n_part; ++k) {
-        const v2 v = p.jpart[(long long)k * p.ncell + idx[p.part_axis[k]]];
-        kahan_add(s, c, v.x);
-        kahan_add(s, c, -v.y);
-    }
+    for (int k = 0; k < p.n_part; ++k) kahan_add(s, c, p.jpart[(long long)k * p.ncell + i]);
     const real jin = (s - c) * p.inv_nd;
     if (p.Jin) p.Jin[i] = jin;
     if (p.J) {
