@@ -47,9 +47,9 @@ WORKLOADS = {
 METRIC = "ray-segment updates/sec"
 UNIT = "segments/s"
 L2_FLUSH_BYTES = 256 << 20      # > 129 MB L2
-# MUFU ex2 results per clock per SM on GB300 (measured) and SMs
+# MUFU ex2 results per clock per SM measured on GB300 (profiles/peaks_gb300.md);
+# bench.py re-measures it on the box (art_measure_pipes) and uses the live value
 EX2_PER_CLK_SM = 32
-N_SM = 152
 
 
 def parse():
@@ -262,7 +262,13 @@ def run_ours(args, d: Dist):
     # algorithmic segments per sweep launch / average launch duration
     achieved_gseg = seg * prof_steps / (pr.sweep_ms * 1e-3) / 1e9
     sm_mhz = ck["sm_mhz"] or 2070.0
-    peak_gseg = EX2_PER_CLK_SM * N_SM * sm_mhz * 1e6 / 1e9
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    try:
+        pipes = art.art_measure_pipes()
+        ex2 = round(pipes["ex2"])
+    except Exception:  # pragma: no cover
+        pipes, ex2 = None, EX2_PER_CLK_SM
+    peak_gseg = ex2 * n_sm * sm_mhz * 1e6 / 1e9
     sweep_share = pr.sweep_ms / max(pr.sweep_ms + pr.reduce_ms, 1e-9)
 
     # end to end through the C ABI with host buffers (pinned), copies included
@@ -313,8 +319,9 @@ def run_ours(args, d: Dist):
         "roofline": {"bound": "alu", "achieved": achieved_gseg, "peak": peak_gseg, "unit": "Gseg/s",
                      "frac": achieved_gseg / peak_gseg, "traffic": None,
                      "kernel": "sweep_block_kernel", "kernel_share_of_step": sweep_share,
-                     "peak_basis": f"MUFU ex2 issue rate: 1 exp per segment, {EX2_PER_CLK_SM}/clk/SM x "
-                                   f"{N_SM} SMs x {sm_mhz:.0f} MHz (median SM clock under load)"},
+                     "peak_basis": f"MUFU ex2 issue rate: 1 exp per segment, {ex2}/clk/SM (measured) x "
+                                   f"{n_sm} SMs x {sm_mhz:.0f} MHz (median SM clock under load)",
+                     "pipes_per_clk_sm": pipes},
         "e2e": e2e,
         "gpu_launches": int(args.steps * st.launches),
         "clocks": ck,

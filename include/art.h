@@ -70,6 +70,7 @@ typedef struct {
     int slab;         /* slabs per launch along the sweep axis;           0 = auto */
     int dir_split;    /* direction groups per octant class (J partials);  0 = auto */
     double tie_tol;   /* dominant-axis tie tolerance (relative), default 1e-12 */
+    int variant;      /* sweep-kernel variant (1-based index of the compiled table); 0 = auto */
 } art_options;
 
 /* Statistics of one sweep, fixed at art_create. */
@@ -81,6 +82,8 @@ typedef struct {
     int32_t ctas_per_launch; /* CTAs of one slab-block launch */
     int32_t tile_b, tile_c, slab, dir_split;
     int64_t device_bytes;    /* device memory owned by the context */
+    int32_t variant;         /* sweep-kernel variant in use (1-based) */
+    int32_t group;           /* directions processed per exchange barrier */
 } art_sweep_stats;
 
 /* Fill `opt` with defaults (FP32, paper averaging, (kappa, S) inputs, auto
@@ -184,6 +187,16 @@ art_status art_profile_enable(art_ctx *ctx, int enable);
  * reset != 0, forget them.  Errors: ART_E_CUDA.
  */
 art_status art_profile_read(art_ctx *ctx, art_profile *out, int reset);
+
+/*
+ * Issue-rate microbenchmark of the current device (about 10 ms): results per
+ * clock per SM of MUFU ex2 (the one exponential of each segment), MUFU rcp and
+ * FP32 FFMA, from clock64() timings of independent chains with two 1024-thread
+ * CTAs per SM.  Used to state the sweep's arithmetic roofline.  Errors:
+ * ART_E_INVALID (NULL output), ART_E_OOM, ART_E_CUDA.
+ */
+art_status art_measure_pipes(double *ex2_per_clk_sm, double *rcp_per_clk_sm,
+                             double *ffma_per_clk_sm);
 
 #ifdef __cplusplus
 }

@@ -31,14 +31,14 @@ class ArtGrid(C.Structure):
 class ArtOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("averaging", C.c_int), ("field_form", C.c_int),
                 ("tile_b", C.c_int), ("tile_c", C.c_int), ("slab", C.c_int), ("dir_split", C.c_int),
-                ("tie_tol", C.c_double)]
+                ("tie_tol", C.c_double), ("variant", C.c_int)]
 
 
 class ArtSweepStats(C.Structure):
     _fields_ = [("segments", C.c_int64), ("n_dirs", C.c_int32), ("n_classes", C.c_int32),
                 ("launches", C.c_int32), ("ctas_per_launch", C.c_int32), ("tile_b", C.c_int32),
                 ("tile_c", C.c_int32), ("slab", C.c_int32), ("dir_split", C.c_int32),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("variant", C.c_int32), ("group", C.c_int32)]
 
 
 class ArtProfile(C.Structure):
@@ -82,9 +82,10 @@ def load() -> C.CDLL:
         lib.art_sweep.argtypes = [P, P, P, P, C.c_int, P]
         lib.art_count_segments.argtypes = [C.POINTER(ArtGrid), C.c_int, C.c_double, C.POINTER(C.c_int64)]
         lib.art_band_integral.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_double)]
+        lib.art_measure_pipes.argtypes = [C.POINTER(C.c_double)] * 3
         lib.art_profile_enable.argtypes = [P, C.c_int]
         lib.art_profile_read.argtypes = [P, C.POINTER(ArtProfile), C.c_int]
-        for f in ("art_band_integral", "art_profile_enable", "art_profile_read", "art_options_default", "art_create", "art_count_segments", "art_destroy", "art_get_stats", "art_set_fields",
+        for f in ("art_measure_pipes", "art_band_integral", "art_profile_enable", "art_profile_read", "art_options_default", "art_create", "art_count_segments", "art_destroy", "art_get_stats", "art_set_fields",
                   "art_set_band", "art_sweep"):
             getattr(lib, f).restype = C.c_int
         _lib = lib
@@ -143,6 +144,15 @@ def art_band_integral(sigma0, h, nu0, nu_lo, nu_hi) -> float:
     if st != ART_OK:
         raise ArtError(st, "art_band_integral: bad arguments")
     return out.value
+
+
+def art_measure_pipes() -> dict:
+    """Results per clock per SM of MUFU ex2, MUFU rcp and FP32 FFMA on the current GPU."""
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    st = load().art_measure_pipes(C.byref(a), C.byref(b), C.byref(c))
+    if st != ART_OK:
+        raise ArtError(st, "art_measure_pipes failed")
+    return {"ex2": a.value, "rcp": b.value, "ffma": c.value}
 
 
 def art_profile_enable(ctx, enable: bool) -> int:
@@ -215,7 +225,7 @@ class ArtSweep:
 
     def __init__(self, shape, nside: int, nbins: int = 1, precision: str = "fp32", field_form: int = 0,
                  dx_cm: float = 1.0, tile_b: int = 0, tile_c: int = 0, slab: int = 0, dir_split: int = 0,
-                 tie_tol: float = 1e-12):
+                 tie_tol: float = 1e-12, variant: int = 0):
         nz, ny, nx = shape
         self.shape = (int(nz), int(ny), int(nx))
         self.nside, self.nbins = int(nside), int(nbins)
@@ -225,6 +235,7 @@ class ArtSweep:
         opt.field_form = int(field_form)
         opt.tile_b, opt.tile_c, opt.slab, opt.dir_split = tile_b, tile_c, slab, dir_split
         opt.tie_tol = tie_tol
+        opt.variant = int(variant)
         self._ctx = art_create(ArtGrid(nx, ny, nz, dx_cm), nside, nbins, opt)
         self.ncell = nx * ny * nz
 

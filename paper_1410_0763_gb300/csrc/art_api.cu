@@ -25,7 +25,7 @@ struct art_ctx {
     size_t rsz = 4;           // bytes per real
     long long ncell = 0;
     int nd = 0;
-    int TB = 0, TC = 0, BLK = 0, NT = 0, split = 1, nblocks = 0;
+    int TB = 0, TC = 0, BLK = 0, NT = 0, KP = 1, variant = 0, split = 1, nblocks = 0;
     int n_classes = 0, n_part = 0, n_work = 0;
     long long seg_count = 0;  // segments per sweep, one bin
     long long plane_elems = 0;
@@ -79,18 +79,12 @@ template <typename T> art_status dev_alloc(art_ctx *ctx, T **p, size_t bytes)
     return ART_OK;
 }
 
-// Kernel configurations compiled into the library: (tile_b, tile_c, slab, threads).
-struct KCfg {
-    int tb, tc, blk, nt;
-};
-const KCfg kFP32Cfgs[] = {{32, 16, 4, 256}, {32, 32, 4, 256}, {32, 8, 4, 256}, {32, 16, 8, 256}};
-const KCfg kFP64Cfgs[] = {{16, 16, 4, 128}};
-
-template <typename real, int TB, int TC, int BLK, int NT, int K, int MINB>
-cudaError_t launch_sweep(const SweepArgs<real> &a, int nwork, cudaStream_t st)
+template <typename real, int TB, int TC, int BLK, int NT, int KP, int MINB>
+cudaError_t launch_sweep(const void *args, int nwork, cudaStream_t st)
 {
-    const size_t sm = SweepShape<TB, TC, BLK, NT, K>::template bytes<real>();
-    auto kern = sweep_block_kernel<real, TB, TC, BLK, NT, K, MINB>;
+    const SweepArgs<real> &a = *static_cast<const SweepArgs<real> *>(args);
+    const size_t sm = SweepShape<TB, TC, BLK, NT, KP>::template bytes<real>();
+    auto kern = sweep_block_kernel<real, TB, TC, BLK, NT, KP, MINB>;
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
@@ -99,22 +93,30 @@ cudaError_t launch_sweep(const SweepArgs<real> &a, int nwork, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t dispatch_sweep(const art_ctx *ctx, const SweepArgs<float> &a, cudaStream_t st)
-{
-    const int tb = ctx->TB, tc = ctx->TC, blk = ctx->BLK;
-    if (tb == 32 && tc == 16 && blk == 4) return launch_sweep<float, 32, 16, 4, 256, 4, 3>(a, ctx->n_work, st);
-    if (tb == 32 && tc == 32 && blk == 4) return launch_sweep<float, 32, 32, 4, 256, 2, 2>(a, ctx->n_work, st);
-    if (tb == 32 && tc == 8 && blk == 4) return launch_sweep<float, 32, 8, 4, 256, 4, 3>(a, ctx->n_work, st);
-    if (tb == 32 && tc == 16 && blk == 8) return launch_sweep<float, 32, 16, 8, 256, 2, 2>(a, ctx->n_work, st);
-    return cudaErrorInvalidConfiguration;
-}
-
-cudaError_t dispatch_sweep(const art_ctx *ctx, const SweepArgs<double> &a, cudaStream_t st)
-{
-    if (ctx->TB == 16 && ctx->TC == 16 && ctx->BLK == 4)
-        return launch_sweep<double, 16, 16, 4, 128, 2, 1>(a, ctx->n_work, st);
-    return cudaErrorInvalidConfiguration;
-}
+// Sweep-kernel variants compiled into the library: tile (b x c), slab block,
+// threads, direction pairs per exchange group, min CTAs per SM.  Index + 1 is
+// the value of art_options.variant that selects one (0 = default).
+struct KVariant {
+    int prec, tb, tc, blk, nt, kp, minb;
+    cudaError_t (*launch)(const void *, int, cudaStream_t);
+};
+#define ART_V(real, pr, tb, tc, blk, nt, kp, mb) \
+    {pr, tb, tc, blk, nt, kp, mb, &launch_sweep<real, tb, tc, blk, nt, kp, mb>}
+const KVariant kVariants[] = {
+    ART_V(float, ART_FP32, 32, 16, 4, 256, 2, 3),   //  1: default FP32
+    ART_V(float, ART_FP32, 32, 8, 4, 256, 2, 3),    //  2
+    ART_V(float, ART_FP32, 32, 16, 4, 256, 1, 4),   //  3
+    ART_V(float, ART_FP32, 32, 16, 4, 256, 3, 2),   //  4
+    ART_V(float, ART_FP32, 32, 16, 2, 256, 2, 3),   //  5
+    ART_V(float, ART_FP32, 32, 16, 4, 128, 2, 4),   //  6
+    ART_V(float, ART_FP32, 32, 32, 4, 512, 2, 1),   //  7
+    ART_V(float, ART_FP32, 64, 16, 4, 512, 2, 1),   //  8
+    ART_V(float, ART_FP32, 32, 16, 8, 256, 1, 2),   //  9
+    ART_V(float, ART_FP32, 32, 8, 4, 128, 2, 5),    // 10
+    ART_V(double, ART_FP64, 16, 16, 4, 128, 1, 1),  // 11: default FP64
+};
+#undef ART_V
+const int kNumVariants = int(sizeof(kVariants) / sizeof(kVariants[0]));
 
 struct HostTables {
     std::vector<ClassDev> classes;
@@ -135,8 +137,17 @@ void build_tables(const art_ctx *ctx, const std::vector<double> &xyz, HostTables
     for (int cls = 0; cls < 24; ++cls) {
         std::vector<int> members;
         for (int d = 0; d < ctx->nd; ++d)
-            if (fr[d].cls == cls) members.push_back(d);   // RING order within the class
+            if (fr[d].cls == cls) members.push_back(d);
         if (members.empty()) continue;
+        // Order within the class: by column drift per slab block along b, then
+        // c, then RING index.  Directions the kernel takes together then have
+        // similar upstream cones.  The order is fixed, so sums stay deterministic.
+        auto drift = [&](double q) { return (int)std::floor(q * ctx->BLK + 0.5); };
+        std::stable_sort(members.begin(), members.end(), [&](int x, int y) {
+            const int bx = drift(fr[x].qb), by = drift(fr[y].qb);
+            if (bx != by) return bx < by;
+            return drift(fr[x].qc) < drift(fr[y].qc);
+        });
         const Frame &f0 = fr[members[0]];
         ClassDev C;
         C.a = f0.a;
@@ -225,7 +236,7 @@ template <typename real> art_status do_sweep(art_ctx *ctx, real *J, real *Jin, r
             a.kblock = k;
             a.plane_in = planes[k & 1];
             a.plane_out = planes[(k + 1) & 1];
-            CK(ctx, dispatch_sweep(ctx, a, st));
+            CK(ctx, kVariants[ctx->variant].launch(&a, ctx->n_work, st));
         }
         if (ctx->profiling) CK(ctx, cudaEventRecord(e1, st));
         ReduceArgs<real> r;
@@ -294,30 +305,40 @@ art_status art_create(const art_grid *grid, int n_side, int nu_bins, const art_o
     ctx->nd = 12 * n_side * n_side;
     ctx->G.assign(nu_bins, 0.0);
 
-    // kernel configuration
-    bool found = false;
-    if (ctx->prec == ART_FP32) {
-        const KCfg def = kFP32Cfgs[0];
-        const int tb = ctx->opt.tile_b ? ctx->opt.tile_b : def.tb;
-        const int tc = ctx->opt.tile_c ? ctx->opt.tile_c : def.tc;
-        const int blk = ctx->opt.slab ? ctx->opt.slab : def.blk;
-        for (const KCfg &k : kFP32Cfgs)
-            if (k.tb == tb && k.tc == tc && k.blk == blk) {
-                ctx->TB = tb; ctx->TC = tc; ctx->BLK = blk; ctx->NT = k.nt; found = true;
+    // kernel variant
+    {
+        int pick = -1;
+        if (ctx->opt.variant > 0) {
+            pick = ctx->opt.variant - 1;
+            if (pick >= kNumVariants || kVariants[pick].prec != ctx->prec) pick = -2;
+        } else {
+            // measured on GB300: the 32 x 8 tile wins below ~100^3 cells
+            // (more CTAs per launch), the 32 x 16 tile above
+            const int prefer = (ctx->prec == ART_FP32 && ctx->ncell < 100LL * 100 * 100 && !ctx->opt.tile_b &&
+                                !ctx->opt.tile_c && !ctx->opt.slab)
+                                   ? 1
+                                   : -1;
+            if (prefer >= 0) pick = prefer;
+            for (int v = 0; v < kNumVariants && pick == -1; ++v) {
+                const KVariant &k = kVariants[v];
+                if (k.prec != ctx->prec) continue;
+                if ((ctx->opt.tile_b && k.tb != ctx->opt.tile_b) || (ctx->opt.tile_c && k.tc != ctx->opt.tile_c) ||
+                    (ctx->opt.slab && k.blk != ctx->opt.slab))
+                    continue;
+                pick = v;
             }
-    } else {
-        const KCfg def = kFP64Cfgs[0];
-        const int tb = ctx->opt.tile_b ? ctx->opt.tile_b : def.tb;
-        const int tc = ctx->opt.tile_c ? ctx->opt.tile_c : def.tc;
-        const int blk = ctx->opt.slab ? ctx->opt.slab : def.blk;
-        for (const KCfg &k : kFP64Cfgs)
-            if (k.tb == tb && k.tc == tc && k.blk == blk) {
-                ctx->TB = tb; ctx->TC = tc; ctx->BLK = blk; ctx->NT = k.nt; found = true;
-            }
-    }
-    if (!found) {
-        delete ctx;
-        return ART_E_INVALID;
+        }
+        if (pick < 0) {
+            delete ctx;
+            return ART_E_INVALID;
+        }
+        const KVariant &k = kVariants[pick];
+        ctx->variant = pick;
+        ctx->TB = k.tb;
+        ctx->TC = k.tc;
+        ctx->BLK = k.blk;
+        ctx->NT = k.nt;
+        ctx->KP = k.kp;
     }
 
     std::vector<double> xyz;
@@ -478,6 +499,8 @@ art_status art_get_stats(const art_ctx *ctx, art_sweep_stats *s)
     s->slab = ctx->BLK;
     s->dir_split = ctx->split;
     s->device_bytes = ctx->dev_bytes;
+    s->variant = ctx->variant + 1;
+    s->group = 2 * ctx->KP;
     return ART_OK;
 }
 

@@ -94,49 +94,6 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
-// Coefficients of one segment of optical depth x = kappa ds:
-//   dsph = ds phi(x), xph = x phi(x) = 1 - e^-x,  phi(x) = (1 - e^-x)/x, phi(0) = 1
-// (phi: the path-averaged attenuation of the segment, Sec. 2.2).  FP32: below
-// x = 1/4 the Maclaurin series sum_n (-x)^n/(n+1)! to n = 5 (truncation
-// < 6e-8 relative); above, 1 - 2^(-x log2 e) from the hardware base-2
-// exponential (relative error ~2^-22, so < 1e-6 on 1 - e^-x there) and the
-// per-cell reciprocal 1/kappa (no per-segment division).  k2 = -kappa log2 e
-// and rk = 1/kappa are precomputed per cell.
-__device__ __forceinline__ void seg_coef(float kap, float k2, float rk, float ds, float &dsph, float &xph)
-{
-    const float x = kap * ds;
-    float q = fmaf(x, -1.0f / 720.0f, 1.0f / 120.0f);
-    q = fmaf(x, q, -1.0f / 24.0f);
-    q = fmaf(x, q, 1.0f / 6.0f);
-    q = fmaf(x, q, -0.5f);
-    q = fmaf(x, q, 1.0f);
-    const float om = 1.0f - ex2_approx(k2 * ds);
-    const bool small = x < 0.25f;
-    dsph = small ? ds * q : om * rk;
-    xph = small ? x * q : om;
-}
-
-__device__ __forceinline__ void seg_coef(double kap, double, double, double ds, double &dsph, double &xph)
-{
-    const double x = kap * ds;
-    const double ph = x > 0.0 ? -expm1(-x) / x : 1.0;
-    dsph = ds * ph;
-    xph = x * ph;
-}
-
-// One segment of Eq. (rt): deposit ds * I_in * phi into A (the path-averaged
-// incoming intensity times the segment length), then advance
-// I = S + (I - S) e^-x (form 0) or I = I e^-x + eps ds phi (form 1, S = eps/kappa).
-template <typename real>
-__device__ __forceinline__ void seg_apply(real &I, real &A, real src, real dsph, real xph, int form)
-{
-    A = fma(I, dsph, A);
-    if (form == 0)
-        I = fma(src - I, xph, I);
-    else
-        I = fma(-I, xph, fma(src, dsph, I));
-}
-
 __device__ __forceinline__ void kahan_add(float &s, float &c, float v)
 {
     const float y = __fsub_rn(v, c);
@@ -154,14 +111,123 @@ __device__ __forceinline__ void kahan_add(double &s, double &c, double v)
 }
 
 // ---------------------------------------------------------------------------
+// Pair arithmetic: two directions per operation.  FP32 uses the packed
+// FP32x2 instructions of sm_100+ (one issue slot for two lanes); FP64 is
+// component-wise.
+// ---------------------------------------------------------------------------
+template <typename real> struct PairOps;
+template <> struct PairOps<float> {
+    using T = float2;
+    static __device__ __forceinline__ T mk(float a, float b) { return make_float2(a, b); }
+    static __device__ __forceinline__ T splat(float a) { return make_float2(a, a); }
+    static __device__ __forceinline__ T mul(T a, T b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ T fma(T a, T b, T c) { return __ffma2_rn(a, b, c); }
+};
+template <> struct PairOps<double> {
+    using T = double2;
+    static __device__ __forceinline__ T mk(double a, double b) { return make_double2(a, b); }
+    static __device__ __forceinline__ T splat(double a) { return make_double2(a, a); }
+    static __device__ __forceinline__ T mul(T a, T b) { return make_double2(a.x * b.x, a.y * b.y); }
+    static __device__ __forceinline__ T fma(T a, T b, T c)
+    {
+        return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y));
+    }
+};
+
+// Per-cell values used by every segment in the cell.
+template <typename real> struct CellVals {
+    real kap, src, k2, rk0, z;   // kappa, S or eps, -kappa log2 e, 1/kappa (0 if kappa = 0), [kappa == 0]
+};
+
+template <typename real> __device__ __forceinline__ CellVals<real> cell_vals(real kap, real src);
+template <> __device__ __forceinline__ CellVals<float> cell_vals<float>(float kap, float src)
+{
+    CellVals<float> c;
+    c.kap = kap;
+    c.src = src;
+    c.k2 = -1.4426950408889634f * kap;
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(kap));
+    c.rk0 = kap > 0.0f ? r : 0.0f;
+    c.z = kap > 0.0f ? 0.0f : 1.0f;
+    return c;
+}
+template <> __device__ __forceinline__ CellVals<double> cell_vals<double>(double kap, double src)
+{
+    CellVals<double> c;
+    c.kap = kap;
+    c.src = src;
+    c.k2 = 0.0;
+    c.rk0 = 0.0;
+    c.z = 0.0;
+    return c;
+}
+
+// Coefficients of one segment for two directions at once (path lengths ds),
+// x = kappa ds:  xph = x phi(x) = 1 - e^-x,  dsph = ds phi(x)
+// (phi = (1 - e^-x)/x, the path-averaged attenuation of the segment, Sec. 2.2).
+// FP32: below x = 1/4 the Maclaurin series sum_n (-x)^n/(n+1)! to n = 5
+// (truncation < 6e-8 relative); above, 1 - 2^(-x log2 e) from the hardware
+// base-2 exponential (relative error ~2^-22, < 1e-6 on 1 - e^-x there).
+// dsph = xph / kappa, except ds itself where kappa = 0 (phi(0) = 1), so no
+// division or select runs for it.
+__device__ __forceinline__ void seg_coef2(const CellVals<float> &c, float2 ds, float2 &dsph, float2 &xph)
+{
+    using P = PairOps<float>;
+    const float2 x = P::mul(P::splat(c.kap), ds);
+    float2 q = P::fma(x, P::splat(-1.0f / 720.0f), P::splat(1.0f / 120.0f));
+    q = P::fma(x, q, P::splat(-1.0f / 24.0f));
+    q = P::fma(x, q, P::splat(1.0f / 6.0f));
+    q = P::fma(x, q, P::splat(-0.5f));
+    q = P::fma(x, q, P::splat(1.0f));
+    const float2 arg = P::mul(P::splat(c.k2), ds);
+    const float2 e = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
+    const float2 om = P::fma(e, P::splat(-1.0f), P::splat(1.0f));
+    const float2 xq = P::mul(x, q);
+    xph.x = x.x < 0.25f ? xq.x : om.x;
+    xph.y = x.y < 0.25f ? xq.y : om.y;
+    dsph = P::fma(ds, P::splat(c.z), P::mul(xph, P::splat(c.rk0)));
+}
+
+__device__ __forceinline__ void seg_coef2(const CellVals<double> &c, double2 ds, double2 &dsph, double2 &xph)
+{
+    const double x0 = c.kap * ds.x, x1 = c.kap * ds.y;
+    const double p0 = x0 > 0.0 ? -expm1(-x0) / x0 : 1.0;
+    const double p1 = x1 > 0.0 ? -expm1(-x1) / x1 : 1.0;
+    dsph = make_double2(ds.x * p0, ds.y * p1);
+    xph = make_double2(x0 * p0, x1 * p1);
+}
+
+// Eq. (rt) for a pair: A += I_in dsph (path-averaged incoming intensity times
+// the segment length), then I = S + (I - S) e^-x (form 0) or
+// I = I e^-x + eps ds phi (form 1, S = eps/kappa).
+template <typename real>
+__device__ __forceinline__ void seg_apply2(typename PairOps<real>::T &I, typename PairOps<real>::T &A, real src,
+                                           typename PairOps<real>::T dsph, typename PairOps<real>::T xph, int form)
+{
+    using P = PairOps<real>;
+    A = P::fma(I, dsph, A);
+    if (form == 0) {
+        const auto d = P::fma(I, P::splat(real(-1)), P::splat(src));
+        I = P::fma(d, xph, I);
+    } else {
+        const auto t = P::fma(P::splat(src), dsph, I);
+        I = P::fma(I, P::mul(xph, P::splat(real(-1))), t);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Slab-block sweep kernel.  Grid: one CTA per work item (class, tile, group).
-// The CTA takes the directions of its group K at a time: for each slab the K
-// directions share the cell loads and the exchange barriers, and each thread
-// carries K independent intensity chains per column.  Shared memory: (kappa,
-// src) of the region (tile + BLK + 1 upstream columns) for the BLK slabs, two
-// exchange buffers of K planes over the region, and the segment tables of a
-// chunk of directions.  Region columns upstream of the box are never written
-// and stay 0: rays there carry the vacuum boundary intensity.
+// The CTA takes the directions of its group K = 2 KP at a time: for each slab
+// the K directions share the cell loads and the exchange barriers, and each
+// thread carries K independent intensity chains per column, two per packed
+// operation.  A step in which a direction has no segment is an exact no-op
+// (ds = 0, fetched from its own column), so all K run the same code.
+// Shared memory: (kappa, src) of the region (tile + BLK + 1 upstream
+// columns) for the BLK slabs, two exchange buffers of K planes (pairs
+// interleaved) over the region, and the decoded segment tables of a chunk of
+// directions.  Region columns upstream of the box are never written and stay
+// 0: rays there carry the vacuum boundary intensity.
 // ---------------------------------------------------------------------------
 template <typename real> struct DirSm {
     long long plane_off;
@@ -169,7 +235,16 @@ template <typename real> struct DirSm {
     int d0b, d0c;    // column shifts over the slab block
 };
 
-template <int TB, int TC, int BLK, int NT, int K> struct SweepShape {
+// Decoded segment entry: path lengths (0 where the direction has no such
+// segment) and the offsets, in elements of the pair-interleaved exchange
+// buffer, of the column that feeds segments 2 and 3 (0 = its own column).
+template <typename real> struct SegSm {
+    real ds1, ds2, ds3;
+    int bits;   // 2 off2 | 2 off3 << 12 | nseg << 24
+};
+
+template <int TB, int TC, int BLK, int NT, int KP> struct SweepShape {
+    static constexpr int K = 2 * KP;
     static constexpr int HB = BLK + 1;
     static constexpr int WB = TB + HB, WC = TC + HB, NS = WB * WC;
     static constexpr int OPT = (TB * TC) / NT;
@@ -178,7 +253,7 @@ template <int TB, int TC, int BLK, int NT, int K> struct SweepShape {
     static constexpr int DCH = 8 * K;   // directions staged per chunk
     template <typename real> __host__ __device__ static constexpr size_t off_x()
     {
-        return size_t(BLK) * NS * sizeof(typename Vec2<real>::type);
+        return (size_t(BLK) * NS * sizeof(typename Vec2<real>::type) + 31) / 32 * 32;
     }
     template <typename real> __host__ __device__ static constexpr size_t off_t()
     {
@@ -186,36 +261,36 @@ template <int TB, int TC, int BLK, int NT, int K> struct SweepShape {
     }
     template <typename real> __host__ __device__ static constexpr size_t off_d()
     {
-        return off_t<real>() + size_t(DCH) * BLK * sizeof(SegEntry<real>);
+        return off_t<real>() + size_t(DCH) * BLK * sizeof(SegSm<real>);
+    }
+    template <typename real> __host__ __device__ static constexpr size_t off_g()
+    {
+        return (off_d<real>() + size_t(DCH) * sizeof(DirSm<real>) + 15) / 16 * 16;
     }
     template <typename real> __host__ __device__ static constexpr size_t bytes()
     {
-        return off_d<real>() + size_t(DCH) * sizeof(DirSm<real>);
+        return off_g<real>() + size_t(DCH / K) * BLK * sizeof(int4);
     }
 };
 
-__device__ __forceinline__ float rcp_or_zero(float k)
-{
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(k));
-    return k > 0.0f ? r : 0.0f;
-}
-__device__ __forceinline__ double rcp_or_zero(double k) { return k > 0.0 ? 1.0 / k : 0.0; }
-
-template <typename real, int TB, int TC, int BLK, int NT, int K, int MINB>
+template <typename real, int TB, int TC, int BLK, int NT, int KP, int MINB>
 __global__ void __launch_bounds__(NT, MINB) sweep_block_kernel(const SweepArgs<real> p)
 {
     using v2 = typename Vec2<real>::type;
-    using Sh = SweepShape<TB, TC, BLK, NT, K>;
+    using P = PairOps<real>;
+    using pr = typename P::T;
+    using Sh = SweepShape<TB, TC, BLK, NT, KP>;
     constexpr int HB = Sh::HB, WB = Sh::WB, WC = Sh::WC, NS = Sh::NS, OPT = Sh::OPT, HPT = Sh::HPT,
-                  DCH = Sh::DCH;
+                  DCH = Sh::DCH, K = Sh::K;
     static_assert((TB * TC) % NT == 0, "owned columns must split evenly over threads");
+    static_assert(WB * WC < 4096, "exchange offsets are packed in 12 bits");
 
     extern __shared__ __align__(32) unsigned char smem_raw[];
     v2 *ks = reinterpret_cast<v2 *>(smem_raw);
-    real *xbuf = reinterpret_cast<real *>(smem_raw + Sh::template off_x<real>());   // [2][K][NS]
-    SegEntry<real> *tsm = reinterpret_cast<SegEntry<real> *>(smem_raw + Sh::template off_t<real>());
+    pr *xbuf = reinterpret_cast<pr *>(smem_raw + Sh::template off_x<real>());   // [2][KP][NS] pairs
+    SegSm<real> *tsm = reinterpret_cast<SegSm<real> *>(smem_raw + Sh::template off_t<real>());
     DirSm<real> *dsm = reinterpret_cast<DirSm<real> *>(smem_raw + Sh::template off_d<real>());
+    int4 *gsm = reinterpret_cast<int4 *>(smem_raw + Sh::template off_g<real>());
 
     const WorkItem w = p.work[blockIdx.x];
     const ClassDev C = p.classes[w.cls];
@@ -227,28 +302,25 @@ __global__ void __launch_bounds__(NT, MINB) sweep_block_kernel(const SweepArgs<r
     const int tid = threadIdx.x;
     const int form = p.field_form;
 
-    // Stage the region's (kappa, src) for the BLK slabs row by row (vacuum
-    // outside the box), and clear the exchange buffers.
-    {
-        const int nrows = BLK * WC;
-        for (int e = tid; e < nrows * WB; e += NT) {
-            const int rowi = e / WB, rb = e - rowi * WB;
-            const int i = rowi / WC, rc = rowi - i * WC;
-            const int gb = Rb + rb, gc = Rc + rc;
-            v2 v;
-            v.x = real(0);
-            v.y = real(0);
-            if (i < Bp && gb >= 0 && gc >= 0 && gb < C.Nb && gc < C.Nc) {
-                const int am = m0 + i;
-                const int pa = C.sa > 0 ? am : C.Na - 1 - am;
-                const int pb = C.sb > 0 ? gb : C.Nb - 1 - gb;
-                const int pc = C.sc > 0 ? gc : C.Nc - 1 - gc;
-                v = F[((long long)pa * C.Nc + pc) * C.Nb + pb];
-            }
-            ks[e] = v;
+    // Stage the region's (kappa, src) for the BLK slabs (vacuum outside the
+    // box) and clear the exchange buffers.
+    for (int e = tid; e < BLK * WC * WB; e += NT) {
+        const int rowi = e / WB, rb = e - rowi * WB;
+        const int i = rowi / WC, rc = rowi - i * WC;
+        const int gb = Rb + rb, gc = Rc + rc;
+        v2 v;
+        v.x = real(0);
+        v.y = real(0);
+        if (i < Bp && gb >= 0 && gc >= 0 && gb < C.Nb && gc < C.Nc) {
+            const int am = m0 + i;
+            const int pa = C.sa > 0 ? am : C.Na - 1 - am;
+            const int pb = C.sb > 0 ? gb : C.Nb - 1 - gb;
+            const int pc = C.sc > 0 ? gc : C.Nc - 1 - gc;
+            v = F[((long long)pa * C.Nc + pc) * C.Nb + pb];
         }
+        ks[e] = v;
     }
-    for (int e = tid; e < 2 * K * NS; e += NT) xbuf[e] = real(0);
+    for (int e = tid; e < 2 * KP * NS; e += NT) xbuf[e] = P::splat(real(0));
 
     int o_gb[OPT], o_gc[OPT], o_r[OPT];
     bool o_ok[OPT];
@@ -272,35 +344,73 @@ __global__ void __launch_bounds__(NT, MINB) sweep_block_kernel(const SweepArgs<r
     const bool first = p.kblock == 0;
     int xs = 0;
 
+    int o_r2[OPT];
+#pragma unroll
+    for (int s = 0; s < OPT; ++s) o_r2[s] = 2 * o_r[s];
+
     for (int c0 = d0; c0 < d1; c0 += DCH) {
         const int cnt = min(DCH, d1 - c0);
+        const int cntk = (cnt + K - 1) / K * K;   // padded with inactive directions
         __syncthreads();   // previous chunk's tables are no longer read
-        for (int e = tid; e < cnt * BLK; e += NT) {
+        for (int e = tid; e < cntk * BLK; e += NT) {
             const int dl = e / BLK, i = e - dl * BLK;
-            if (i < Bp) tsm[e] = p.segs[p.dirs[c0 + dl].seg_off + m0 + i];
+            SegSm<real> q;
+            q.ds1 = q.ds2 = q.ds3 = real(0);
+            q.bits = 1 << 24;   // inactive: one segment of length 0, own column
+            if (dl < cnt && i < Bp) {
+                const SegEntry<real> g = p.segs[p.dirs[c0 + dl].seg_off + m0 + i];
+                const int nseg = (g.code & 3) + 1, cf = (g.code >> 2) & 1;
+                const int shb = (g.code >> 3) & 1, shc = (g.code >> 4) & 1;
+                int off2 = 0, off3 = 0;
+                if (nseg == 2) off2 = shc * WB + shb;
+                if (nseg == 3) {
+                    off2 = cf * WB + (1 - cf);
+                    off3 = (1 - cf) * WB + cf;
+                }
+                q.ds1 = g.ds1;
+                q.ds2 = nseg >= 2 ? g.ds2 : real(0);
+                q.ds3 = nseg == 3 ? g.ds3 : real(0);
+                q.bits = (2 * off2) | ((2 * off3) << 12) | (nseg << 24);
+            }
+            tsm[e] = q;
         }
         for (int dl = tid; dl < cnt; dl += NT) {
             const DirDev D = p.dirs[c0 + dl];
-            int sb = 0, sc = 0;
-            for (int i = 0; i < Bp; ++i) {
-                const int code = p.segs[D.seg_off + m0 + i].code;
-                sb += (code >> 3) & 1;
-                sc += (code >> 4) & 1;
-            }
             DirSm<real> q;
             q.plane_off = D.plane_off;
             q.na = real(D.na);
-            q.d0b = sb;
-            q.d0c = sc;
+            q.d0b = q.d0c = 0;
             dsm[dl] = q;
+        }
+        // per (group, slab): max segment count and the union of the
+        // directions' remaining upstream cones at the start of the slab
+        for (int e = tid; e < (cntk / K) * BLK; e += NT) {
+            const int grp = e / BLK, i = e - grp * BLK;
+            int nsmax = 1, ub = 0, uc = 0;
+            if (i < Bp) {
+                for (int k = 0; k < K; ++k) {
+                    const int dl = grp * K + k;
+                    if (dl >= cnt) break;
+                    const long long so = p.dirs[c0 + dl].seg_off + m0;
+                    int rb = 0, rc = 0;
+                    for (int i2 = i; i2 < Bp; ++i2) {
+                        const int code = p.segs[so + i2].code;
+                        rb += (code >> 3) & 1;
+                        rc += (code >> 4) & 1;
+                    }
+                    ub = max(ub, rb);
+                    uc = max(uc, rc);
+                    nsmax = max(nsmax, (p.segs[so + i].code & 3) + 1);
+                }
+            }
+            gsm[e] = make_int4(nsmax, ub, uc, 0);
         }
         __syncthreads();
 
         for (int g0 = 0; g0 < cnt; g0 += K) {
             const int kk = min(K, cnt - g0);
-            // union cone of the group
-            int D0b = 0, D0c = 0;
-            int Dbk[K], Dck[K];   // remaining cone of each direction
+            const int4 *G = gsm + (g0 / K) * BLK;
+            const int D0b = G[0].y, D0c = G[0].z;   // union cone of the group
             long long poff[K];
             real na[K];
 #pragma unroll
@@ -308,15 +418,11 @@ __global__ void __launch_bounds__(NT, MINB) sweep_block_kernel(const SweepArgs<r
                 const DirSm<real> D = dsm[g0 + (k < kk ? k : 0)];
                 poff[k] = D.plane_off;
                 na[k] = k < kk ? D.na : real(0);
-                Dbk[k] = k < kk ? D.d0b : 0;
-                Dck[k] = k < kk ? D.d0c : 0;
-                D0b = max(D0b, Dbk[k]);
-                D0c = max(D0c, Dck[k]);
             }
             const int hw = TB + D0b;
             const int n1 = D0c * hw, nh = n1 + TC * D0b;
             int h_gb[HPT], h_gc[HPT], h_r[HPT];
-            bool h_ok[HPT];
+            bool h_ok[HPT], h_w[HPT];
 #pragma unroll
             for (int s = 0; s < HPT; ++s) {
                 const int h = tid + s * NT;
@@ -329,122 +435,109 @@ __global__ void __launch_bounds__(NT, MINB) sweep_block_kernel(const SweepArgs<r
                     gc = w.pc + h2 / D0b;
                     gb = w.pb - D0b + h2 % D0b;
                 }
+                h_w[s] = ((tid & ~31) + s * NT) < nh;   // warp-uniform: this warp has halo work
                 h_ok[s] = h < nh && gb >= 0 && gc >= 0 && gb < C.Nb && gc < C.Nc;
                 h_gb[s] = gb;
                 h_gc[s] = gc;
                 h_r[s] = h_ok[s] ? (gc - Rc) * WB + (gb - Rb) : 0;
             }
-            real oI[OPT][K], hI[HPT][K];
+            pr oI[OPT][KP], hI[HPT][KP];
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const real *pin = p.plane_in + poff[k];
+            for (int kp = 0; kp < KP; ++kp) {
+                const real *pa = p.plane_in + poff[2 * kp];
+                const real *pb = p.plane_in + poff[2 * kp + 1];
+                const bool va = !first && 2 * kp < kk, vb = !first && 2 * kp + 1 < kk;
 #pragma unroll
-                for (int s = 0; s < OPT; ++s)
-                    oI[s][k] = (!first && o_ok[s] && k < kk) ? pin[(long long)o_gc[s] * C.Nb + o_gb[s]] : real(0);
+                for (int s = 0; s < OPT; ++s) {
+                    const long long ci = (long long)o_gc[s] * C.Nb + o_gb[s];
+                    oI[s][kp] = P::mk(va && o_ok[s] ? pa[ci] : real(0), vb && o_ok[s] ? pb[ci] : real(0));
+                }
 #pragma unroll
-                for (int s = 0; s < HPT; ++s)
-                    hI[s][k] = (!first && h_ok[s] && k < kk) ? pin[(long long)h_gc[s] * C.Nb + h_gb[s]] : real(0);
+                for (int s = 0; s < HPT; ++s) {
+                    const long long ci = (long long)h_gc[s] * C.Nb + h_gb[s];
+                    hI[s][kp] = P::mk(va && h_ok[s] ? pa[ci] : real(0), vb && h_ok[s] ? pb[ci] : real(0));
+                }
             }
 
 #pragma unroll
             for (int i = 0; i < BLK; ++i) {
                 if (i < Bp) {
-                    SegEntry<real> g[K];
-                    int nsmax = 1, Db = 0, Dc = 0;   // union of the remaining cones
+                    const int4 Gi = G[i];
+                    SegSm<real> g[K];
 #pragma unroll
-                    for (int k = 0; k < K; ++k) {
-                        g[k] = tsm[(g0 + (k < kk ? k : 0)) * BLK + i];
-                        if (k >= kk) g[k].code = 0;   // inactive: one segment, ignored below
-                        nsmax = max(nsmax, (g[k].code & 3) + 1);
-                        Db = max(Db, Dbk[k]);
-                        Dc = max(Dc, Dck[k]);
-                        Dbk[k] -= (g[k].code >> 3) & 1;
-                        Dck[k] -= (g[k].code >> 4) & 1;
-                    }
+                    for (int k = 0; k < K; ++k) g[k] = tsm[(g0 + k) * BLK + i];
                     const v2 *ksi = ks + i * NS;
-                    real ok[OPT], os[OPT], ok2[OPT], ork[OPT], oA[OPT][K];
-                    real hk[HPT], hs[HPT], hk2[HPT], hrk[HPT];
-                    bool h_act[HPT], hw_act[HPT];
+                    CellVals<real> oc[OPT], hc[HPT];
+                    pr oA[OPT][KP];
+                    bool h_act[HPT];
 #pragma unroll
                     for (int s = 0; s < OPT; ++s) {
                         const v2 c = ksi[o_r[s]];
-                        ok[s] = c.x;
-                        os[s] = c.y;
-                        ok2[s] = real(-1.4426950408889634) * c.x;
-                        ork[s] = rcp_or_zero(c.x);
+                        oc[s] = cell_vals<real>(c.x, c.y);
 #pragma unroll
-                        for (int k = 0; k < K; ++k) {
-                            real dsph, xph;
-                            seg_coef(ok[s], ok2[s], ork[s], g[k].ds1, dsph, xph);
-                            oA[s][k] = real(0);
-                            seg_apply(oI[s][k], oA[s][k], os[s], dsph, xph, form);
+                        for (int kp = 0; kp < KP; ++kp) {
+                            pr dsph, xph;
+                            seg_coef2(oc[s], P::mk(g[2 * kp].ds1, g[2 * kp + 1].ds1), dsph, xph);
+                            oA[s][kp] = P::splat(real(0));
+                            seg_apply2<real>(oI[s][kp], oA[s][kp], oc[s].src, dsph, xph, form);
                         }
                     }
 #pragma unroll
                     for (int s = 0; s < HPT; ++s) {
-                        hw_act[s] = ((tid & ~31) + s * NT) < nh;
-                        h_act[s] = h_ok[s] && h_gb[s] >= w.pb - Db && h_gc[s] >= w.pc - Dc;
-                        hk[s] = hs[s] = hk2[s] = hrk[s] = real(0);
-                        if (hw_act[s] && h_act[s]) {
+                        h_act[s] = h_w[s] && h_ok[s] && h_gb[s] >= w.pb - Gi.y && h_gc[s] >= w.pc - Gi.z;
+                        hc[s] = cell_vals<real>(real(0), real(0));
+                        if (h_w[s] && h_act[s]) {
                             const v2 c = ksi[h_r[s]];
-                            hk[s] = c.x;
-                            hs[s] = c.y;
-                            hk2[s] = real(-1.4426950408889634) * c.x;
-                            hrk[s] = rcp_or_zero(c.x);
+                            hc[s] = cell_vals<real>(c.x, c.y);
 #pragma unroll
-                            for (int k = 0; k < K; ++k) {
-                                real dsph, xph, dummy = real(0);
-                                seg_coef(hk[s], hk2[s], hrk[s], g[k].ds1, dsph, xph);
-                                seg_apply(hI[s][k], dummy, hs[s], dsph, xph, form);
+                            for (int kp = 0; kp < KP; ++kp) {
+                                pr dsph, xph, dummy = P::splat(real(0));
+                                seg_coef2(hc[s], P::mk(g[2 * kp].ds1, g[2 * kp + 1].ds1), dsph, xph);
+                                seg_apply2<real>(hI[s][kp], dummy, hc[s].src, dsph, xph, form);
                             }
                         }
                     }
-                    for (int step = 2; step <= nsmax; ++step) {
-                        real *X = xbuf + xs * K * NS;
+                    // Segments 2 and 3: publish the intensities, then each column
+                    // takes the ray arriving from its upstream neighbour.
 #pragma unroll
-                        for (int k = 0; k < K; ++k) {
+                    for (int step = 2; step <= 3; ++step) {
+                        if (Gi.x < step) break;   // uniform
+                        pr *X = xbuf + xs * KP * NS;
 #pragma unroll
-                            for (int s = 0; s < OPT; ++s) X[k * NS + o_r[s]] = oI[s][k];
+                        for (int kp = 0; kp < KP; ++kp) {
+#pragma unroll
+                            for (int s = 0; s < OPT; ++s) X[kp * NS + o_r[s]] = oI[s][kp];
 #pragma unroll
                             for (int s = 0; s < HPT; ++s)
-                                if (hw_act[s] && h_act[s]) X[k * NS + h_r[s]] = hI[s][k];
+                                if (h_w[s] && h_act[s]) X[kp * NS + h_r[s]] = hI[s][kp];
                         }
                         __syncthreads();
 #pragma unroll
-                        for (int k = 0; k < K; ++k) {
-                            const int ns = (g[k].code & 3) + 1;
-                            if (ns < step) continue;   // uniform: this direction is done
-                            const int cf = (g[k].code >> 2) & 1;
-                            int ob, oc;
-                            if (ns == 2) {
-                                ob = (g[k].code >> 3) & 1;
-                                oc = (g[k].code >> 4) & 1;
-                            } else if (step == 2) {
-                                ob = 1 - cf;
-                                oc = cf;
-                            } else {
-                                ob = cf;
-                                oc = 1 - cf;
-                            }
-                            const int off = oc * WB + ob;
-                            const real dsk = step == 2 ? g[k].ds2 : g[k].ds3;
-                            const real *Xk = X + k * NS;
+                        for (int kp = 0; kp < KP; ++kp) {
+                            const SegSm<real> &ga = g[2 * kp], &gb = g[2 * kp + 1];
+                            // uniform: neither direction has this segment (a zero-length
+                            // segment through an edge still moves the ray to the next column)
+                            if (((ga.bits >> 24) & 7) < step && ((gb.bits >> 24) & 7) < step) continue;
+                            const int sh = step == 2 ? 0 : 12;
+                            const int offa = (ga.bits >> sh) & 4095, offb = ((gb.bits >> sh) & 4095) - 1;
+                            const pr dsv = step == 2 ? P::mk(ga.ds2, gb.ds2) : P::mk(ga.ds3, gb.ds3);
+                            const real *Xr = reinterpret_cast<const real *>(X + kp * NS);
 #pragma unroll
                             for (int s = 0; s < OPT; ++s) {
-                                real dsph, xph;
-                                seg_coef(ok[s], ok2[s], ork[s], dsk, dsph, xph);
-                                real Iin = Xk[o_r[s] - off];
-                                seg_apply(Iin, oA[s][k], os[s], dsph, xph, form);
-                                oI[s][k] = Iin;
+                                pr dsph, xph;
+                                seg_coef2(oc[s], dsv, dsph, xph);
+                                pr Iin = P::mk(Xr[o_r2[s] - offa], Xr[o_r2[s] - offb]);
+                                seg_apply2<real>(Iin, oA[s][kp], oc[s].src, dsph, xph, form);
+                                oI[s][kp] = Iin;
                             }
 #pragma unroll
                             for (int s = 0; s < HPT; ++s) {
-                                if (hw_act[s] && h_act[s]) {
-                                    real dsph, xph, dummy = real(0);
-                                    seg_coef(hk[s], hk2[s], hrk[s], dsk, dsph, xph);
-                                    real Iin = Xk[h_r[s] - off];
-                                    seg_apply(Iin, dummy, hs[s], dsph, xph, form);
-                                    hI[s][k] = Iin;
+                                if (h_w[s] && h_act[s]) {
+                                    pr dsph, xph, dummy = P::splat(real(0));
+                                    seg_coef2(hc[s], dsv, dsph, xph);
+                                    pr Iin = P::mk(Xr[2 * h_r[s] - offa], Xr[2 * h_r[s] - offb]);
+                                    seg_apply2<real>(Iin, dummy, hc[s].src, dsph, xph, form);
+                                    hI[s][kp] = Iin;
                                 }
                             }
                         }
@@ -453,21 +546,24 @@ __global__ void __launch_bounds__(NT, MINB) sweep_block_kernel(const SweepArgs<r
 #pragma unroll
                     for (int s = 0; s < OPT; ++s) {
                         if (o_ok[s]) {
-                            real a = real(0);
+                            pr a2 = P::splat(real(0));
 #pragma unroll
-                            for (int k = 0; k < K; ++k) a = fma(oA[s][k], na[k], a);
-                            kahan_add(js[s][i], jc[s][i], a);
+                            for (int kp = 0; kp < KP; ++kp) a2 = P::fma(oA[s][kp], P::mk(na[2 * kp], na[2 * kp + 1]), a2);
+                            kahan_add(js[s][i], jc[s][i], a2.x + a2.y);
                         }
                     }
                 }
             }
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                if (k < kk) {
-                    real *pout = p.plane_out + poff[k];
+            for (int kp = 0; kp < KP; ++kp) {
+                real *pa = p.plane_out + poff[2 * kp];
+                real *pb = p.plane_out + poff[2 * kp + 1];
 #pragma unroll
-                    for (int s = 0; s < OPT; ++s)
-                        if (o_ok[s]) pout[(long long)o_gc[s] * C.Nb + o_gb[s]] = oI[s][k];
+                for (int s = 0; s < OPT; ++s) {
+                    if (!o_ok[s]) continue;
+                    const long long ci = (long long)o_gc[s] * C.Nb + o_gb[s];
+                    if (2 * kp < kk) pa[ci] = oI[s][kp].x;
+                    if (2 * kp + 1 < kk) pb[ci] = oI[s][kp].y;
                 }
             }
         }

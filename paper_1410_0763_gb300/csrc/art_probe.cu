@@ -1,0 +1,84 @@
+// art_probe.cu -- issue-rate microbenchmark of the pipes the sweep relies on:
+// MUFU ex2 (one exponential per segment), MUFU rcp and FP32 FFMA.  Each CTA
+// runs 8 independent chains per thread and times itself with clock64(); the
+// result per pipe is operations per clock per SM (max cycle count over CTAs,
+// two CTAs of 1024 threads resident per SM).
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "art.h"
+
+namespace {
+
+template <int OP> __global__ void pipe_probe_kernel(float *out, long long *cyc, int iters)
+{
+    float a[8];
+    for (int i = 0; i < 8; i++) a[i] = (threadIdx.x + i) * 1e-3f;
+    __syncthreads();
+    const long long t0 = clock64();
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            float y;
+            if (OP == 0) {
+                asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a[i] * -0.5f));
+            } else if (OP == 1) {
+                asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a[i] + 1.0f));
+            } else {
+                y = fmaf(a[i], 1.0001f, 0.5f);
+            }
+            a[i] = y;
+        }
+    }
+    __syncthreads();
+    const long long t1 = clock64();
+    float s = 0.f;
+    for (int i = 0; i < 8; i++) s += a[i];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+    if (threadIdx.x == 0) cyc[blockIdx.x] = t1 - t0;
+}
+
+}  // namespace
+
+extern "C" art_status art_measure_pipes(double *ex2_per_clk_sm, double *rcp_per_clk_sm,
+                                        double *ffma_per_clk_sm)
+{
+    if (!ex2_per_clk_sm || !rcp_per_clk_sm || !ffma_per_clk_sm) return ART_E_INVALID;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        return ART_E_CUDA;
+    const int nt = 1024, per_sm = 2, nb = sms * per_sm, iters = 2048;
+    float *out = nullptr;
+    long long *cyc = nullptr;
+    if (cudaMalloc(&out, sizeof(float) * nb * nt) != cudaSuccess) return ART_E_OOM;
+    if (cudaMalloc(&cyc, sizeof(long long) * nb) != cudaSuccess) {
+        cudaFree(out);
+        return ART_E_OOM;
+    }
+    double *res[3] = {ex2_per_clk_sm, rcp_per_clk_sm, ffma_per_clk_sm};
+    std::vector<long long> h(nb);
+    art_status st = ART_OK;
+    for (int op = 0; op < 3 && st == ART_OK; op++) {
+        double best = 0.0;
+        for (int rep = 0; rep < 2; rep++) {
+            if (op == 0) pipe_probe_kernel<0><<<nb, nt>>>(out, cyc, iters);
+            else if (op == 1) pipe_probe_kernel<1><<<nb, nt>>>(out, cyc, iters);
+            else pipe_probe_kernel<2><<<nb, nt>>>(out, cyc, iters);
+            if (cudaDeviceSynchronize() != cudaSuccess ||
+                cudaMemcpy(h.data(), cyc, sizeof(long long) * nb, cudaMemcpyDeviceToHost) != cudaSuccess) {
+                st = ART_E_CUDA;
+                break;
+            }
+            long long mx = 1;
+            for (int i = 0; i < nb; i++) mx = h[i] > mx ? h[i] : mx;
+            const double v = double(per_sm) * nt * iters * 8 / double(mx);
+            best = v > best ? v : best;
+        }
+        *res[op] = best;
+    }
+    cudaFree(out);
+    cudaFree(cyc);
+    return st;
+}
