@@ -198,6 +198,35 @@ art_status art_profile_read(art_ctx *ctx, art_profile *out, int reset);
 art_status art_measure_pipes(double *ex2_per_clk_sm, double *rcp_per_clk_sm,
                              double *ffma_per_clk_sm);
 
+/*
+ * One FP32 sweep (kappa, S inputs, J^in output) that allocates no memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory -- a simulation code that reserves the whole
+ * device memory budget for its own arrays at start-up, or code calling from a
+ * place where the implicit device-wide synchronization of cudaMalloc and
+ * cudaFree would stall work it has in flight on other streams.
+ *
+ * kappa, S: device arrays of nz * ny * nx floats ([z][y][x]); J_in: device
+ * array of the same size, written with J^in as art_sweep writes it (the same
+ * kernels; results agree with art_sweep within FP32 rounding).  All working
+ * memory is one file-scope device array of 12 MiB that every GPU loading the
+ * library holds until the process exits; host-side tables are file-scope too.
+ * Limits: each axis <= 64 cells, at most 32768 cells, 1 <= n_side <= 4, and
+ * the grid's tables must fit the 12 MiB; otherwise ART_E_INVALID and a message
+ * in errbuf (if errbuf != NULL, errlen bytes).  Inputs are not validated.
+ *
+ * The first call on each device looks up the device address of the scratch
+ * array (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  The call copies its tables with cudaMemcpyAsync and synchronizes
+ * `stream` once before launching its kernels on it; it returns without waiting
+ * for them.  Every call uses the same scratch array and the array keeps the
+ * last call's contents (nothing is carried over: each call writes every
+ * element it reads), so calls that overlap on the GPU -- from several threads
+ * or streams -- race and must be serialized by the caller.
+ */
+art_status art_sweep_noalloc(const art_grid *grid, int n_side, const float *kappa, const float *S,
+                             float *J_in, void *stream, char *errbuf, size_t errlen);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,9 +83,10 @@ def load() -> C.CDLL:
         lib.art_count_segments.argtypes = [C.POINTER(ArtGrid), C.c_int, C.c_double, C.POINTER(C.c_int64)]
         lib.art_band_integral.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_double)]
         lib.art_measure_pipes.argtypes = [C.POINTER(C.c_double)] * 3
+        lib.art_sweep_noalloc.argtypes = [C.POINTER(ArtGrid), C.c_int, P, P, P, P, C.c_char_p, C.c_size_t]
         lib.art_profile_enable.argtypes = [P, C.c_int]
         lib.art_profile_read.argtypes = [P, C.POINTER(ArtProfile), C.c_int]
-        for f in ("art_measure_pipes", "art_band_integral", "art_profile_enable", "art_profile_read", "art_options_default", "art_create", "art_count_segments", "art_destroy", "art_get_stats", "art_set_fields",
+        for f in ("art_sweep_noalloc", "art_measure_pipes", "art_band_integral", "art_profile_enable", "art_profile_read", "art_options_default", "art_create", "art_count_segments", "art_destroy", "art_get_stats", "art_set_fields",
                   "art_set_band", "art_sweep"):
             getattr(lib, f).restype = C.c_int
         _lib = lib
@@ -144,6 +145,15 @@ def art_band_integral(sigma0, h, nu0, nu_lo, nu_hi) -> float:
     if st != ART_OK:
         raise ArtError(st, "art_band_integral: bad arguments")
     return out.value
+
+
+def art_sweep_noalloc(shape, n_side: int, kappa_ptr: int, S_ptr: int, Jin_ptr: int, stream: int):
+    """The allocation-free FP32 sweep (device pointers).  Returns (status, message)."""
+    nz, ny, nx = shape
+    buf = C.create_string_buffer(256)
+    st = load().art_sweep_noalloc(C.byref(ArtGrid(nx, ny, nz, 1.0)), int(n_side), C.c_void_p(kappa_ptr),
+                                  C.c_void_p(S_ptr), C.c_void_p(Jin_ptr), C.c_void_p(stream), buf, 256)
+    return st, buf.value.decode()
 
 
 def art_measure_pipes() -> dict:

@@ -1,0 +1,297 @@
+// art_noalloc.cu -- art_sweep_noalloc: the diffuse-radiation sweep for callers
+// that cannot allocate device memory (see include/art.h).  All working memory
+// comes from one file-scope device array; host-side tables live in file-scope
+// host arrays.  Nothing here calls cudaMalloc, cudaFree or any other
+// allocating routine.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "art.h"
+#include "art_geometry.hpp"
+#include "art_kernels.cuh"
+
+using namespace art;
+
+namespace {
+
+// Working memory of every call, on every device that loads the library.
+constexpr size_t kScratchBytes = size_t(12) << 20;
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+constexpr int kMaxDim = 64;            // cells per axis
+constexpr long long kMaxCells = 32768; // cells in total (32^3)
+constexpr int kMaxNside = 4;           // 192 directions
+constexpr int kMaxDirs = 12 * kMaxNside * kMaxNside;
+constexpr int kMaxSlabs = kMaxDirs * kMaxDim;
+constexpr int kTB = 32, kTC = 8, kBLK = 4, kNT = 256, kKP = 2, kMINB = 3;
+constexpr int kMaxWork = 24 * ((kMaxDim + kTB - 1) / kTB) * ((kMaxDim + kTC - 1) / kTC);
+
+// Device address of g_scratch, looked up once per device.
+constexpr int kMaxDevices = 64;
+static void *g_scratch_dev[kMaxDevices];
+
+// Host-side tables of the current call.
+static double g_xyz[3 * kMaxDirs];
+static Frame g_frame[kMaxDirs];
+static int g_order[kMaxDirs];
+static SegEntry<float> g_segs[kMaxSlabs];
+static DirDev g_dirs[kMaxDirs];
+static ClassDev g_classes[24];
+static WorkItem g_work[kMaxWork];
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+art_status reject(char *errbuf, size_t errlen, art_status st, const char *msg)
+{
+    if (errbuf && errlen) std::snprintf(errbuf, errlen, "%s", msg);
+    return st;
+}
+
+// HEALPix RING pixel centres written into a caller array (no allocation).
+void directions_into(int N, double *xyz)
+{
+    const double pi = 3.14159265358979323846;
+    int p = 0;
+    for (int r = 1; r <= 4 * N - 1; ++r) {
+        double z, dphi, off;
+        int count;
+        if (r < N) {
+            z = 1.0 - double(r) * r / (3.0 * N * N);
+            count = 4 * r;
+            dphi = pi / (2.0 * r);
+            off = 0.5;
+        } else if (r <= 3 * N) {
+            z = 2.0 * double(2 * N - r) / (3.0 * N);
+            count = 4 * N;
+            dphi = pi / (2.0 * N);
+            off = ((r - N + 1) & 1) ? 0.5 : 0.0;
+        } else {
+            const int rs = 4 * N - r;
+            z = -(1.0 - double(rs) * rs / (3.0 * N * N));
+            count = 4 * rs;
+            dphi = pi / (2.0 * rs);
+            off = 0.5;
+        }
+        const double st = std::sqrt((1.0 - z) * (1.0 + z));
+        for (int j = 1; j <= count; ++j, ++p) {
+            xyz[3 * p] = st * std::cos(dphi * (j - off));
+            xyz[3 * p + 1] = st * std::sin(dphi * (j - off));
+            xyz[3 * p + 2] = z;
+        }
+    }
+}
+
+// Segment table of one direction (same rules as the context path: crossings
+// from the integer parts of the column offset, ties within 1e-12 merged).
+void slabs_into(const Frame &f, int Na, SegEntry<float> *out)
+{
+    const double tie = 1e-12;
+    auto snap = [&](double u) { return u <= tie ? 0.0 : (u >= 1.0 - tie ? 1.0 : u); };
+    for (int m = 0; m < Na; ++m) {
+        const double fb0 = std::floor(0.5 + f.qb * m), fb1 = std::floor(0.5 + f.qb * (m + 1));
+        const double fc0 = std::floor(0.5 + f.qc * m), fc1 = std::floor(0.5 + f.qc * (m + 1));
+        const int shb = fb1 > fb0, shc = fc1 > fc0;
+        double ub = 2.0, uc = 2.0;
+        if (shb) ub = snap((fb1 - 0.5 - f.qb * m) / f.qb);
+        if (shc) uc = snap((fc1 - 0.5 - f.qc * m) / f.qc);
+        if (shb && shc && std::fabs(ub - uc) <= tie) uc = ub;
+        const double inv = 1.0 / f.na;
+        const int nseg = 1 + shb + shc;
+        double ds[3] = {0.0, 0.0, 0.0};
+        int cf = 0;
+        if (nseg == 1) {
+            ds[0] = inv;
+        } else if (nseg == 2) {
+            const double u = shb ? ub : uc;
+            ds[0] = u * inv;
+            ds[1] = (1.0 - u) * inv;
+        } else {
+            cf = uc < ub;
+            const double u1 = ub < uc ? ub : uc, u2 = ub < uc ? uc : ub;
+            ds[0] = u1 * inv;
+            ds[1] = (u2 - u1) * inv;
+            ds[2] = (1.0 - u2) * inv;
+        }
+        out[m].ds1 = float(ds[0]);
+        out[m].ds2 = float(ds[1]);
+        out[m].ds3 = float(ds[2]);
+        out[m].code = (nseg - 1) | (cf << 2) | (shb << 3) | (shc << 4);
+    }
+}
+
+}  // namespace
+
+extern "C" art_status art_sweep_noalloc(const art_grid *grid, int n_side, const float *kappa, const float *S,
+                                        float *J_in, void *stream, char *errbuf, size_t errlen)
+{
+    if (!grid || !kappa || !S || !J_in)
+        return reject(errbuf, errlen, ART_E_INVALID, "art_sweep_noalloc: null argument");
+    const int dims[3] = {grid->nx, grid->ny, grid->nz};
+    const long long ncell = (long long)dims[0] * dims[1] * dims[2];
+    if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1 || n_side < 1)
+        return reject(errbuf, errlen, ART_E_INVALID, "art_sweep_noalloc: dimensions and n_side must be >= 1");
+    if (dims[0] > kMaxDim || dims[1] > kMaxDim || dims[2] > kMaxDim || ncell > kMaxCells || n_side > kMaxNside)
+        return reject(errbuf, errlen, ART_E_INVALID,
+                      "art_sweep_noalloc: grid or angular resolution above the fixed maximum "
+                      "(each axis <= 64 cells, <= 32768 cells, n_side <= 4); use art_create/art_sweep");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    // Device set-up, once per device: the device address of the scratch array.
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return reject(errbuf, errlen, ART_E_CUDA, "art_sweep_noalloc: no usable current device");
+    if (!g_scratch_dev[dev]) {
+        void *ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
+        if (e != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            return reject(errbuf, errlen, ART_E_CUDA, "art_sweep_noalloc: cudaGetSymbolAddress of the scratch array failed");
+        }
+        g_scratch_dev[dev] = ptr;
+    }
+    unsigned char *base = static_cast<unsigned char *>(g_scratch_dev[dev]);
+
+    // Host tables: classes of directions, drift-sorted, with segment tables.
+    const int nd = 12 * n_side * n_side;
+    directions_into(n_side, g_xyz);
+    for (int d = 0; d < nd; ++d) g_frame[d] = frame_of(&g_xyz[3 * d], 1e-12);
+    int ncls = 0, nslab = 0, nwork = 0, ndir = 0;
+    long long plane_elems = 0;
+    auto drift = [](double q) { return (int)std::floor(q * kBLK + 0.5); };
+    for (int cls = 0; cls < 24; ++cls) {
+        int cnt = 0;
+        for (int d = 0; d < nd; ++d)
+            if (g_frame[d].cls == cls) g_order[cnt++] = d;
+        if (!cnt) continue;
+        for (int i = 1; i < cnt; ++i) {   // stable insertion sort by (drift b, drift c)
+            const int v = g_order[i];
+            int j = i - 1;
+            while (j >= 0) {
+                const int u = g_order[j];
+                const int bu = drift(g_frame[u].qb), bv = drift(g_frame[v].qb);
+                const bool after = bu > bv || (bu == bv && drift(g_frame[u].qc) > drift(g_frame[v].qc));
+                if (!after) break;
+                g_order[j + 1] = u;
+                --j;
+            }
+            g_order[j + 1] = v;
+        }
+        const Frame &f0 = g_frame[g_order[0]];
+        ClassDev C;
+        C.a = f0.a;
+        C.sa = f0.sa;
+        C.sb = f0.sb;
+        C.sc = f0.sc;
+        C.Na = dims[f0.a];
+        C.Nb = dims[f0.b];
+        C.Nc = dims[f0.c];
+        C.dir_begin = ndir;
+        C.dir_end = ndir + cnt;
+        C.part0 = ncls;
+        for (int i = 0; i < cnt; ++i) {
+            DirDev D;
+            D.seg_off = nslab;
+            D.plane_off = plane_elems;
+            D.na = g_frame[g_order[i]].na;
+            g_dirs[ndir++] = D;
+            slabs_into(g_frame[g_order[i]], C.Na, g_segs + nslab);
+            nslab += C.Na;
+            plane_elems += (long long)C.Nb * C.Nc;
+        }
+        for (int pc = 0; pc < C.Nc; pc += kTC)
+            for (int pb = 0; pb < C.Nb; pb += kTB) g_work[nwork++] = WorkItem{ncls, pb, pc, 0};
+        g_classes[ncls++] = C;
+    }
+
+    // Scratch layout; every region read by a launch is written earlier in the
+    // same call (the first slab block does not read a plane), so no state
+    // carries over between calls and nothing needs clearing.
+    const size_t o_field = 0;
+    const size_t o_plane0 = align256(o_field + 3 * size_t(ncell) * sizeof(float2));
+    const size_t o_plane1 = align256(o_plane0 + size_t(plane_elems) * sizeof(float));
+    const size_t o_jpart = align256(o_plane1 + size_t(plane_elems) * sizeof(float));
+    const size_t o_segs = align256(o_jpart + size_t(ncls) * ncell * sizeof(float));
+    const size_t o_dirs = align256(o_segs + size_t(nslab) * sizeof(SegEntry<float>));
+    const size_t o_cls = align256(o_dirs + size_t(ndir) * sizeof(DirDev));
+    const size_t o_work = align256(o_cls + size_t(ncls) * sizeof(ClassDev));
+    const size_t need = align256(o_work + size_t(nwork) * sizeof(WorkItem));
+    if (need > kScratchBytes)
+        return reject(errbuf, errlen, ART_E_INVALID,
+                      "art_sweep_noalloc: this grid needs more than the 12 MiB scratch array; use art_create/art_sweep");
+
+    float2 *fld = reinterpret_cast<float2 *>(base + o_field);
+    float *planes[2] = {reinterpret_cast<float *>(base + o_plane0), reinterpret_cast<float *>(base + o_plane1)};
+    float *jpart = reinterpret_cast<float *>(base + o_jpart);
+#define ART_NA_CK(call, what)                                                       \
+    do {                                                                            \
+        if ((call) != cudaSuccess) {                                                \
+            cudaGetLastError();                                                     \
+            return reject(errbuf, errlen, ART_E_CUDA, "art_sweep_noalloc: " what);  \
+        }                                                                           \
+    } while (0)
+    ART_NA_CK(cudaMemcpyAsync(base + o_segs, g_segs, size_t(nslab) * sizeof(SegEntry<float>), cudaMemcpyHostToDevice, st),
+              "copy of the segment tables failed");
+    ART_NA_CK(cudaMemcpyAsync(base + o_dirs, g_dirs, size_t(ndir) * sizeof(DirDev), cudaMemcpyHostToDevice, st),
+              "copy of the direction table failed");
+    ART_NA_CK(cudaMemcpyAsync(base + o_cls, g_classes, size_t(ncls) * sizeof(ClassDev), cudaMemcpyHostToDevice, st),
+              "copy of the class table failed");
+    ART_NA_CK(cudaMemcpyAsync(base + o_work, g_work, size_t(nwork) * sizeof(WorkItem), cudaMemcpyHostToDevice, st),
+              "copy of the work list failed");
+    // the host tables are reused by the next call: wait for the copies
+    ART_NA_CK(cudaStreamSynchronize(st), "stream synchronize failed");
+
+    const int nt = 256;
+    layout_kernel<float><<<(unsigned)((ncell + nt - 1) / nt), nt, 0, st>>>(kappa, S, fld, fld + ncell, fld + 2 * ncell,
+                                                                           dims[0], dims[1], dims[2]);
+    ART_NA_CK(cudaGetLastError(), "layout kernel launch failed");
+
+    SweepArgs<float> a;
+    a.field0 = fld;
+    a.field1 = fld + ncell;
+    a.field2 = fld + 2 * ncell;
+    a.jpart = jpart;
+    a.segs = reinterpret_cast<const SegEntry<float> *>(base + o_segs);
+    a.dirs = reinterpret_cast<const DirDev *>(base + o_dirs);
+    a.classes = reinterpret_cast<const ClassDev *>(base + o_cls);
+    a.work = reinterpret_cast<const WorkItem *>(base + o_work);
+    a.ncell = ncell;
+    a.nx = dims[0];
+    a.ny = dims[1];
+    a.nz = dims[2];
+    a.split = 1;
+    a.field_form = ART_FIELDS_S;
+    int maxNa = 0;
+    for (int c = 0; c < ncls; ++c) maxNa = g_classes[c].Na > maxNa ? g_classes[c].Na : maxNa;
+    const size_t sm = SweepShape<kTB, kTC, kBLK, kNT, kKP>::bytes<float>();
+    auto kern = sweep_block_kernel<float, kTB, kTC, kBLK, kNT, kKP, kMINB>;
+    if (sm > 48 * 1024)
+        ART_NA_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                  "shared-memory attribute failed");
+    for (int k = 0; k * kBLK < maxNa; ++k) {
+        a.kblock = k;
+        a.plane_in = planes[k & 1];
+        a.plane_out = planes[(k + 1) & 1];
+        kern<<<nwork, kNT, sm, st>>>(a);
+        ART_NA_CK(cudaGetLastError(), "sweep kernel launch failed");
+    }
+    ReduceArgs<float> r;
+    r.jpart = jpart;
+    r.field_nat = fld + 2 * ncell;
+    r.n_part = ncls;
+    r.ncell = ncell;
+    r.inv_nd = float(1.0 / nd);
+    r.gamma_coef = 0.0f;
+    r.gamma_accum = 0;
+    r.field_form = ART_FIELDS_S;
+    r.Jin = J_in;
+    r.J = nullptr;
+    r.gamma = nullptr;
+    reduce_kernel<float><<<(unsigned)((ncell + nt - 1) / nt), nt, 0, st>>>(r);
+    ART_NA_CK(cudaGetLastError(), "reduce kernel launch failed");
+#undef ART_NA_CK
+    if (errbuf && errlen) errbuf[0] = '\0';
+    return ART_OK;
+}
