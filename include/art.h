@@ -167,6 +167,73 @@ art_status art_band_integral(double sigma0, double h, double nu0, double nu_lo, 
  */
 art_status art_sweep(art_ctx *ctx, void *J, void *J_in, void *gamma, int on_device, void *stream);
 
+/* Hydrogen rate coefficients at the (fixed) gas temperature and the spectral
+ * constants of the recombination radiation (Sec. 2.2, App. B). */
+typedef struct {
+    double alphaA, alphaB;  /* case-A and case-B radiative recombination, cm^3/s */
+    double gcoll;           /* collisional ionization of HI, cm^3/s */
+    double sigma0;          /* HI photo-ionization cross section at nu0, cm^2 */
+    double h, nu0, dnu;     /* Planck constant (erg s), threshold (Hz), k_B T/h (Hz) */
+} art_chem;
+
+/* A point source: position in cell widths (box [0, nx] x [0, ny] x [0, nz]),
+ * ionizing photons per second (monochromatic at nu0 unless per-bin rates are
+ * given). */
+typedef struct {
+    double x, y, z;
+    double Q;
+} art_source;
+
+typedef struct {
+    int32_t iterations;     /* iterations run */
+    int32_t converged;      /* 1 if the residual fell below tol */
+    double residual;        /* last max_cells |n_e^(i) - n_e^(i-1)| / n_e^(i) */
+    double seconds;         /* wall time of the call */
+} art_iter_report;
+
+/*
+ * Photo-ionization rate per neutral atom from point sources (Sec. 2.1,
+ * App. A, Eq. pc_gamma), by long characteristics: for every cell and source
+ * (index order) the ray from the source to the cell centre is marched,
+ * tau_b = sum kappa_b ds over the cells before the target cell, [r_in, r_out]
+ * is the ray's passage through the target cell (r_in = 0 in the source's own
+ * cell; the first cell is the one containing source + 1e-9 * direction), and
+ *   Gamma += Q_b e^-tau_b (1 - e^-dtau_b) / (n_HI (4 pi/3)(r_out^3 - r_in^3) dx^3)
+ * with n_HI = kappa_b/(sigma_b dx) (absorbed photons = in - out; App. A prints
+ * out - in).  kappa: device [bin][z][y][x] floats per cell width; sigma: host
+ * array of nu_bins cross sections (cm^2); src: host array of n_src sources;
+ * Qb: host [n_src][nu_bins] photons/s per bin, or NULL to put each source's
+ * Q in bin 0; gamma: device [z][y][x] floats, s^-1.  Uses grid.dx_cm.
+ * Synchronizes `stream`.  Errors: ART_E_INVALID (null pointers, sources
+ * outside the box, more than 4 bins, dx_cm <= 0), ART_E_OOM, ART_E_CUDA.
+ */
+art_status art_point_sources(art_ctx *ctx, const float *kappa, const double *sigma, const art_source *src,
+                             const double *Qb, int n_src, float *gamma, void *stream);
+
+/*
+ * RT / ionization-balance fixed-point iteration (App. D) for hydrogen at a
+ * fixed temperature, in the equilibrium (dt -> infinity) limit of the BDF
+ * update of App. B.  Each iteration:
+ *   kappa = n_HI sigma0 dx,  eps = h nu0 (alpha_A - alpha_B) n_e n_HII dx / (4 pi dnu)
+ *   (the rectangular recombination spectrum of Sec. 2.2, swept at nu0);
+ *   Gamma_point from art_point_sources; J^in from the diffuse sweep;
+ *   g = Gamma_point + 4 pi G J^in, G = int sigma/(h nu) over [nu0, nu0 + dnu];
+ *   the local term of Eq. (gamma_diff), (alpha_A - alpha_B) n_e n_HII / n_HI,
+ *   taken at the new state, leaves alpha_B n_e n_HII = n_HI (Gamma_coll n_e + g),
+ *   solved for the neutral fraction y in FP64 without cancellation;
+ * until max_cells |n_e^(i) - n_e^(i-1)| / n_e^(i) < tol.
+ * The context must be FP32 with one bin and ART_FIELDS_EPS inputs.
+ * nH: device [z][y][x] doubles (cm^-3); y: device [z][y][x] doubles, the
+ * initial neutral fraction on input and the result on output; src: host
+ * array (monochromatic at nu0, src[i].Q); resid_hist: host array of max_iter
+ * doubles or NULL; rep: may be NULL.  One host synchronization per iteration
+ * (the residual).  Errors: ART_E_INVALID, ART_E_NOT_CONVERGED (y holds the
+ * last iterate), ART_E_OOM, ART_E_CUDA.
+ */
+art_status art_iterate_ionization(art_ctx *ctx, const art_chem *chem, const double *nH, const art_source *src,
+                                  int n_src, double tol, int max_iter, double *y, double *resid_hist,
+                                  art_iter_report *rep, void *stream);
+
 /* Per-kernel device time accumulated while profiling is enabled. */
 typedef struct {
     double sweep_ms;          /* slab-block sweep kernels */

@@ -41,6 +41,20 @@ class ArtSweepStats(C.Structure):
                 ("device_bytes", C.c_int64), ("variant", C.c_int32), ("group", C.c_int32)]
 
 
+class ArtChem(C.Structure):
+    _fields_ = [("alphaA", C.c_double), ("alphaB", C.c_double), ("gcoll", C.c_double), ("sigma0", C.c_double),
+                ("h", C.c_double), ("nu0", C.c_double), ("dnu", C.c_double)]
+
+
+class ArtSource(C.Structure):
+    _fields_ = [("x", C.c_double), ("y", C.c_double), ("z", C.c_double), ("Q", C.c_double)]
+
+
+class ArtIterReport(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("residual", C.c_double),
+                ("seconds", C.c_double)]
+
+
 class ArtProfile(C.Structure):
     _fields_ = [("sweep_ms", C.c_double), ("sweep_launches", C.c_int64), ("reduce_ms", C.c_double),
                 ("reduce_launches", C.c_int64)]
@@ -83,10 +97,14 @@ def load() -> C.CDLL:
         lib.art_count_segments.argtypes = [C.POINTER(ArtGrid), C.c_int, C.c_double, C.POINTER(C.c_int64)]
         lib.art_band_integral.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_double)]
         lib.art_measure_pipes.argtypes = [C.POINTER(C.c_double)] * 3
+        lib.art_point_sources.argtypes = [P, P, C.POINTER(C.c_double), C.POINTER(ArtSource), C.POINTER(C.c_double),
+                                          C.c_int, P, P]
+        lib.art_iterate_ionization.argtypes = [P, C.POINTER(ArtChem), P, C.POINTER(ArtSource), C.c_int, C.c_double,
+                                               C.c_int, P, C.POINTER(C.c_double), C.POINTER(ArtIterReport), P]
         lib.art_sweep_noalloc.argtypes = [C.POINTER(ArtGrid), C.c_int, P, P, P, P, C.c_char_p, C.c_size_t]
         lib.art_profile_enable.argtypes = [P, C.c_int]
         lib.art_profile_read.argtypes = [P, C.POINTER(ArtProfile), C.c_int]
-        for f in ("art_sweep_noalloc", "art_measure_pipes", "art_band_integral", "art_profile_enable", "art_profile_read", "art_options_default", "art_create", "art_count_segments", "art_destroy", "art_get_stats", "art_set_fields",
+        for f in ("art_point_sources", "art_iterate_ionization", "art_sweep_noalloc", "art_measure_pipes", "art_band_integral", "art_profile_enable", "art_profile_read", "art_options_default", "art_create", "art_count_segments", "art_destroy", "art_get_stats", "art_set_fields",
                   "art_set_band", "art_sweep"):
             getattr(lib, f).restype = C.c_int
         _lib = lib
@@ -230,6 +248,13 @@ def _stream(stream) -> int:
     return 0
 
 
+def _sources(sources):
+    arr = (ArtSource * max(1, len(sources)))()
+    for i, s in enumerate(sources):
+        arr[i] = ArtSource(float(s[0]), float(s[1]), float(s[2]), float(s[3]))
+    return arr
+
+
 class ArtSweep:
     """One sweep context: grid (nz, ny, nx), N_side, frequency bins."""
 
@@ -275,6 +300,42 @@ class ArtSweep:
 
     def profile_read(self, reset: bool = True) -> ArtProfile:
         return art_profile_read(self._ctx, reset)
+
+    def point_sources(self, kappa, sigma, sources, gamma, Qb=None, stream=None):
+        """Point-source rates (App. A) into `gamma` (device); kappa device [bins][z][y][x] FP32."""
+        kp, kd, _k = _ptr(kappa, np.float32, self.ncell * self.nbins)
+        gp, gd, _g = _ptr(gamma, np.float32, self.ncell)
+        if not (kd and gd):
+            raise TypeError("point_sources takes device buffers")
+        src = _sources(sources)
+        sig = (C.c_double * self.nbins)(*[float(x) for x in sigma])
+        q = None
+        if Qb is not None:
+            qa = np.ascontiguousarray(np.asarray(Qb, dtype=np.float64).reshape(len(sources), self.nbins))
+            q = qa.ctypes.data_as(C.POINTER(C.c_double))
+        _check(self._ctx, load().art_point_sources(self._ctx, C.c_void_p(kp), sig, src, q, len(sources),
+                                                    C.c_void_p(gp), C.c_void_p(_stream(stream))))
+        return gamma
+
+    def iterate(self, nH, chem: dict, sources, y, tol=1e-6, max_iter=200, stream=None):
+        """RT / balance iteration (App. D); nH, y: device FP64 [z][y][x]; y updated in place.
+        Returns (report, residual history); raises ArtError unless converged."""
+        npp, nd_, _n = _ptr(nH, np.float64, self.ncell)
+        yp, yd, _y = _ptr(y, np.float64, self.ncell)
+        if not (nd_ and yd):
+            raise TypeError("iterate takes device buffers")
+        ch = ArtChem(chem["alphaA"], chem["alphaB"], chem["gcoll"], chem["sigma0"], chem["h"], chem["nu0"],
+                     chem["dnu"])
+        src = _sources(sources)
+        hist = (C.c_double * max_iter)()
+        rep = ArtIterReport()
+        st = load().art_iterate_ionization(self._ctx, C.byref(ch), C.c_void_p(npp), src, len(sources), float(tol),
+                                           int(max_iter), C.c_void_p(yp), hist, C.byref(rep),
+                                           C.c_void_p(_stream(stream)))
+        n = max(0, min(rep.iterations, max_iter))
+        if st != ART_OK:
+            raise ArtError(st, art_last_error(self._ctx))
+        return rep, np.array(hist[:n])
 
     def set_fields(self, kappa, src, stream=None):
         n = self.ncell * self.nbins

@@ -16,46 +16,17 @@
 
 using namespace art;
 
-struct art_ctx {
-    art_grid grid{};
-    int nside = 0, nbins = 0;
-    art_options opt{};
-    std::string err;
-    int prec = ART_FP32;
-    size_t rsz = 4;           // bytes per real
-    long long ncell = 0;
-    int nd = 0;
-    int TB = 0, TC = 0, BLK = 0, NT = 0, KP = 1, variant = 0, split = 1, nblocks = 0;
-    int n_classes = 0, n_part = 0, n_work = 0;
-    long long seg_count = 0;  // segments per sweep, one bin
-    long long plane_elems = 0;
-    std::vector<double> G;
-    bool have_fields = false;
-    long long dev_bytes = 0;
-    // device memory
-    void *d_field = nullptr;   // [3][nbins][ncell] vec2
-    void *d_plane[2] = {nullptr, nullptr};
-    void *d_jpart = nullptr;   // [n_part][ncell] real, natural layout
-    void *d_segs = nullptr;
-    DirDev *d_dirs = nullptr;
-    ClassDev *d_classes = nullptr;
-    WorkItem *d_work = nullptr;
-    int *d_part_axis = nullptr;
-    void *d_stage = nullptr;   // [2][nbins][ncell] real: host-input staging
-    void *d_out = nullptr;     // [2 nbins + 1][ncell] real: host-output staging
-    int *d_flag = nullptr;
-    // profiling: event triples (before sweep launches, after them, after reduce)
-    bool profiling = false;
-    std::vector<cudaEvent_t> ev;
-};
+#include "art_ctx.hpp"
 
-namespace {
-
-art_status fail(art_ctx *ctx, art_status st, const std::string &msg)
+art_status art_fail(art_ctx *ctx, art_status st, const std::string &msg)
 {
     if (ctx) ctx->err = msg;
     return st;
 }
+
+namespace {
+
+art_status fail(art_ctx *ctx, art_status st, const std::string &msg) { return art_fail(ctx, st, msg); }
 
 #define CK(ctx, call)                                                                             \
     do {                                                                                          \
@@ -260,6 +231,39 @@ template <typename real> art_status do_sweep(art_ctx *ctx, real *J, real *Jin, r
 }
 
 }  // namespace
+
+art_status art_internal_sweep(art_ctx *ctx, void *J, void *J_in, void *gamma, cudaStream_t st)
+{
+    if (ctx->prec == ART_FP64)
+        return do_sweep<double>(ctx, static_cast<double *>(J), static_cast<double *>(J_in),
+                                static_cast<double *>(gamma), st);
+    return do_sweep<float>(ctx, static_cast<float *>(J), static_cast<float *>(J_in), static_cast<float *>(gamma), st);
+}
+
+art_status art_internal_layout(art_ctx *ctx, const void *kd, const void *sd, cudaStream_t st)
+{
+    const long long nc = ctx->ncell;
+    const int nt = 256;
+    const unsigned lb = (unsigned)((nc + nt - 1) / nt);
+    for (int b = 0; b < ctx->nbins; ++b) {
+        if (ctx->prec == ART_FP64) {
+            double2 *f = static_cast<double2 *>(ctx->d_field);
+            const double *k = static_cast<const double *>(kd) + (long long)b * nc;
+            const double *s = static_cast<const double *>(sd) + (long long)b * nc;
+            layout_kernel<double><<<lb, nt, 0, st>>>(k, s, f + (0LL * ctx->nbins + b) * nc, f + (1LL * ctx->nbins + b) * nc,
+                                                     f + (2LL * ctx->nbins + b) * nc, ctx->grid.nx, ctx->grid.ny, ctx->grid.nz);
+        } else {
+            float2 *f = static_cast<float2 *>(ctx->d_field);
+            const float *k = static_cast<const float *>(kd) + (long long)b * nc;
+            const float *s = static_cast<const float *>(sd) + (long long)b * nc;
+            layout_kernel<float><<<lb, nt, 0, st>>>(k, s, f + (0LL * ctx->nbins + b) * nc, f + (1LL * ctx->nbins + b) * nc,
+                                                    f + (2LL * ctx->nbins + b) * nc, ctx->grid.nx, ctx->grid.ny, ctx->grid.nz);
+        }
+        CK(ctx, cudaGetLastError());
+    }
+    ctx->have_fields = true;
+    return ART_OK;
+}
 
 extern "C" {
 
@@ -477,7 +481,8 @@ art_status art_destroy(art_ctx *ctx)
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     void *ptrs[] = {ctx->d_field, ctx->d_plane[0], ctx->d_plane[1], ctx->d_jpart, ctx->d_segs,
                     ctx->d_dirs, ctx->d_classes, ctx->d_work, ctx->d_part_axis, ctx->d_stage,
-                    ctx->d_out, ctx->d_flag};
+                    ctx->d_out, ctx->d_flag, ctx->it.nH, ctx->it.y, ctx->it.y0, ctx->it.gpt, ctx->it.kap,
+                    ctx->it.eps, ctx->it.jin, ctx->it.resid, ctx->it.src};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ctx;
@@ -532,28 +537,7 @@ art_status art_set_fields(art_ctx *ctx, const void *kappa, const void *src, int 
     CK(ctx, cudaStreamSynchronize(st));
     if (flag & 1) return fail(ctx, ART_E_INVALID, "art_set_fields: kappa negative or not finite");
     if (flag & 2) return fail(ctx, ART_E_INVALID, "art_set_fields: source term not finite");
-    const long long nc = ctx->ncell;
-    const unsigned lb = (unsigned)((nc + nt - 1) / nt);
-    for (int b = 0; b < ctx->nbins; ++b) {
-        if (ctx->prec == ART_FP64) {
-            using v2 = double2;
-            v2 *f = static_cast<v2 *>(ctx->d_field);
-            const double *k = static_cast<const double *>(kd) + (long long)b * nc;
-            const double *s = static_cast<const double *>(sd) + (long long)b * nc;
-            layout_kernel<double><<<lb, nt, 0, st>>>(k, s, f + (0LL * ctx->nbins + b) * nc, f + (1LL * ctx->nbins + b) * nc,
-                                                     f + (2LL * ctx->nbins + b) * nc, ctx->grid.nx, ctx->grid.ny, ctx->grid.nz);
-        } else {
-            using v2 = float2;
-            v2 *f = static_cast<v2 *>(ctx->d_field);
-            const float *k = static_cast<const float *>(kd) + (long long)b * nc;
-            const float *s = static_cast<const float *>(sd) + (long long)b * nc;
-            layout_kernel<float><<<lb, nt, 0, st>>>(k, s, f + (0LL * ctx->nbins + b) * nc, f + (1LL * ctx->nbins + b) * nc,
-                                                    f + (2LL * ctx->nbins + b) * nc, ctx->grid.nx, ctx->grid.ny, ctx->grid.nz);
-        }
-        CK(ctx, cudaGetLastError());
-    }
-    ctx->have_fields = true;
-    return ART_OK;
+    return art_internal_layout(ctx, kd, sd, st);
 }
 
 art_status art_set_band(art_ctx *ctx, const double *G)

@@ -1,0 +1,60 @@
+// art_ctx.hpp -- the context behind art_ctx* (private to libart).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "art.h"
+#include "art_kernels.cuh"
+
+// Device buffers of the RT / ionization-balance iteration (allocated on the
+// first art_iterate_ionization call).
+struct art_iter_bufs {
+    long long ncell = 0;
+    int nsrc_cap = 0;
+    double *nH = nullptr, *y = nullptr, *y0 = nullptr;   // FP64 state
+    float *gpt = nullptr, *kap = nullptr, *eps = nullptr, *jin = nullptr;
+    unsigned long long *resid = nullptr;
+    double *src = nullptr;                                // [nsrc][4]: x, y, z, Q
+};
+
+struct art_ctx {
+    art_grid grid{};
+    int nside = 0, nbins = 0;
+    art_options opt{};
+    std::string err;
+    int prec = ART_FP32;
+    size_t rsz = 4;           // bytes per real
+    long long ncell = 0;
+    int nd = 0;
+    int TB = 0, TC = 0, BLK = 0, NT = 0, KP = 1, variant = 0, split = 1, nblocks = 0;
+    int n_classes = 0, n_part = 0, n_work = 0;
+    long long seg_count = 0;  // segments per sweep, one bin
+    long long plane_elems = 0;
+    std::vector<double> G;
+    bool have_fields = false;
+    long long dev_bytes = 0;
+    // device memory
+    void *d_field = nullptr;   // [3][nbins][ncell] vec2
+    void *d_plane[2] = {nullptr, nullptr};
+    void *d_jpart = nullptr;   // [n_part][ncell] real, natural layout
+    void *d_segs = nullptr;
+    art::DirDev *d_dirs = nullptr;
+    art::ClassDev *d_classes = nullptr;
+    art::WorkItem *d_work = nullptr;
+    int *d_part_axis = nullptr;
+    void *d_stage = nullptr;   // [2][nbins][ncell] real: host-input staging
+    void *d_out = nullptr;     // [2 nbins + 1][ncell] real: host-output staging
+    int *d_flag = nullptr;
+    // profiling: event triples (before sweep launches, after them, after reduce)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;
+    art_iter_bufs it;
+};
+
+
+// internal entry points shared by the translation units of libart
+art_status art_fail(art_ctx *ctx, art_status st, const std::string &msg);
+art_status art_internal_sweep(art_ctx *ctx, void *J, void *J_in, void *gamma, cudaStream_t st);
+art_status art_internal_layout(art_ctx *ctx, const void *kappa, const void *src, cudaStream_t st);

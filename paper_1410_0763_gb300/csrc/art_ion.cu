@@ -1,0 +1,388 @@
+// art_ion.cu -- point sources (long characteristics with the photon-conserving
+// rate of App. A), the FP64 hydrogen ionization balance (App. B, equilibrium
+// limit) and the RT / balance fixed-point iteration (App. D) of Tanaka et al.
+// (2014), on top of the diffuse-radiation sweep.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "art.h"
+#include "art_ctx.hpp"
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+#define ICK(ctx, call)                                                                               \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return art_fail(ctx, e_ == cudaErrorMemoryAllocation ? ART_E_OOM : ART_E_CUDA,           \
+                            std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Point sources.  One thread per target cell; for each source (index order)
+// the straight ray from the source to the cell centre is marched cell by
+// cell, accumulating tau_b = sum kappa_b ds over the cells before the target
+// cell; [r_in, r_out] is the ray's passage through the target cell (r_in = 0
+// in the source's own cell).  Per bin (App. A, absorbed = in - out):
+//   Ndot_abs = Q_b e^-tau (1 - e^-dtau),  dtau = kappa_b (r_out - r_in),
+//   Gamma   += Ndot_abs / (n_HI 4pi/3 (r_out^3 - r_in^3) dx^3),  n_HI = kappa_b/(sigma_b dx)
+// which, with r_out^3 - r_in^3 = (r_out - r_in)(r_out^2 + r_out r_in + r_in^2), is
+//   Gamma   += 3 Q_b sigma_b e^-tau phi(dtau) / (4 pi dx^2 (r_out^2 + r_out r_in + r_in^2)),
+// free of the cancellation of r_out^3 - r_in^3 far from the source.  The
+// march is FP32 in relative form: it keeps, per axis, the parametric distance
+// to that axis' next plane (an O(1) number, so rounding stays ~1e-7 absolute
+// instead of growing with the distance from the source); crossings within
+// 1e-6 of each other are taken together.  r_in and r_out come from the target
+// cell's faces in FP64.
+// ---------------------------------------------------------------------------
+struct PtArgs {
+    const float *kappa;   // [bins][ncell]
+    const double *src;    // [nsrc][4]: x, y, z, (unused)
+    const double *Qb;     // [nsrc][bins]
+    const double *sigma;  // [bins]
+    int nsrc, nbins;
+    int nx, ny, nz;
+    long long ncell;
+    double dx;
+    float *gamma;
+};
+
+constexpr int kMaxBins = 4;   // point-source kernels are compiled for 1-4 bins
+
+template <int NB> __global__ void __launch_bounds__(128) point_source_kernel(const PtArgs p)
+{
+    const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= p.ncell) return;
+    const int tx = (int)(cell % p.nx), ty = (int)((cell / p.nx) % p.ny), tz = (int)(cell / ((long long)p.nx * p.ny));
+    const int dims[3] = {p.nx, p.ny, p.nz};
+    const int maxsteps = p.nx + p.ny + p.nz + 4;
+    double g = 0.0;
+    for (int a = 0; a < p.nsrc; ++a) {
+        const double s[3] = {p.src[4 * a], p.src[4 * a + 1], p.src[4 * a + 2]};
+        const double c[3] = {tx + 0.5, ty + 0.5, tz + 0.5};
+        double d[3] = {c[0] - s[0], c[1] - s[1], c[2] - s[2]};
+        const double L2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (L2 < 1e-24) {
+            d[0] = 1.0;
+            d[1] = d[2] = 0.0;
+        } else {
+            const double il = 1.0 / sqrt(L2);
+            d[0] *= il;
+            d[1] *= il;
+            d[2] *= il;
+        }
+        // first cell: the one containing s + 1e-9 d
+        int cur[3], stp[3];
+        double rn[3];
+        float r[3], dl[3];   // parametric distance to the next plane of each axis; plane spacing
+        for (int k = 0; k < 3; ++k) {
+            int v = (int)floor(s[k] + 1e-9 * d[k]);
+            cur[k] = v < 0 ? 0 : (v >= dims[k] ? dims[k] - 1 : v);
+            stp[k] = d[k] > 0.0 ? 1 : (d[k] < 0.0 ? -1 : 0);
+            rn[k] = stp[k] ? 1.0 / d[k] : 0.0;
+            r[k] = stp[k] > 0 ? (float)((cur[k] + 1 - s[k]) * rn[k])
+                              : (stp[k] < 0 ? (float)((cur[k] - s[k]) * rn[k]) : INFINITY);
+            dl[k] = stp[k] ? (float)fabs(rn[k]) : INFINITY;
+        }
+        float tau[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) tau[b] = 0.0f;
+        const long long target = cell;
+        for (int it = 0; it < maxsteps; ++it) {
+            const long long ci = ((long long)cur[2] * p.ny + cur[1]) * p.nx + cur[0];
+            if (ci == target) {
+                // passage through the target cell, exactly, from its faces
+                double rin = 0.0, rout = INFINITY;
+                for (int k = 0; k < 3; ++k) {
+                    if (!stp[k]) continue;
+                    const double t1 = (tx * (k == 0) + ty * (k == 1) + tz * (k == 2) - s[k]) * rn[k];
+                    const double t2 = t1 + rn[k];
+                    rin = fmax(rin, fmin(t1, t2));
+                    rout = fmin(rout, fmax(t1, t2));
+                }
+                const double den = 4.0 * kPi * p.dx * p.dx * (rout * rout + rout * rin + rin * rin);
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    const double x = (double)p.kappa[(long long)b * p.ncell + ci] * (rout - rin);
+                    const double ph = x > 0.0 ? -expm1(-x) / x : 1.0;
+                    g += 3.0 * p.Qb[(long long)a * p.nbins + b] * p.sigma[b] * exp(-(double)tau[b]) * ph / den;
+                }
+                break;
+            }
+            const float ds = fminf(r[0], fminf(r[1], r[2]));
+#pragma unroll
+            for (int b = 0; b < NB; ++b) tau[b] = fmaf(__ldg(p.kappa + (long long)b * p.ncell + ci), ds, tau[b]);
+            bool out = false;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                r[k] -= ds;
+                if (r[k] <= 1e-6f) {   // this axis' plane is crossed here (ties within 1e-6 together)
+                    cur[k] += stp[k];
+                    out |= cur[k] < 0 || cur[k] >= dims[k];
+                    r[k] += dl[k];
+                }
+            }
+            if (out) break;   // cannot happen for a target inside the box
+        }
+    }
+    p.gamma[cell] = (float)g;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 balance (App. B, dt -> infinity), hydrogen only.  With the local
+// recombination term of Eq. (gamma_diff) at the same state,
+//   alpha_B n_e n_HII = n_HI (Gamma_coll n_e + g),  g = Gamma_point + Gamma_diff,in,
+// n_HI = y n_H, n_e = n_HII = x n_H, x = 1 - y:  a = alpha_B n_H, c = Gamma_coll n_H,
+//   den = 2a + c + g + sqrt(4ag + (c + g)^2),  y = 2a/den,  x = (c + g + sqrt(.))/den
+// (both without cancellation).  Writes y, the next sweep inputs
+//   kappa = n_HI sigma0 dx,  eps' = 4 pi G eps dx = G h nu0 (alpha_A - alpha_B) n_e^2 dx / dnu
+// (eps' makes the sweep return Gamma_diff,in directly), and the block maxima
+// of |n_e^(i) - n_e^(i-1)| / n_e^(i) into an order-independent atomic max.
+// ---------------------------------------------------------------------------
+struct BalArgs {
+    const double *nH;
+    const float *gpt, *gdiff;   // may be null (prepare pass)
+    double alphaB, gcoll;
+    double kap_coef, eps_coef;  // sigma0 dx ; G h nu0 dalpha dx / dnu
+    double *y;
+    float *kap, *eps;
+    unsigned long long *resid;
+    long long ncell;
+    int solve;                  // 0: only derive kappa, eps from y
+};
+
+__global__ void balance_kernel(const BalArgs p)
+{
+    __shared__ double smax[32];
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double r = 0.0;
+    if (i < p.ncell) {
+        const double nH = p.nH[i];
+        const double yo = p.y[i];
+        double y = yo, x = 1.0 - yo;
+        if (p.solve) {
+            const double g = (double)p.gpt[i] + (double)p.gdiff[i];
+            const double a = p.alphaB * nH, c = p.gcoll * nH;
+            const double sq = sqrt(4.0 * a * g + (c + g) * (c + g));
+            const double den = 2.0 * a + c + g + sq;
+            y = den > 0.0 ? 2.0 * a / den : 0.0;
+            x = den > 0.0 ? (c + g + sq) / den : 1.0;
+            const double ne_new = x * nH, ne_old = (1.0 - yo) * nH;
+            r = ne_new > 0.0 ? fabs(ne_new - ne_old) / ne_new : (ne_old > 0.0 ? INFINITY : 0.0);
+            p.y[i] = y;
+        }
+        p.kap[i] = (float)(y * nH * p.kap_coef);
+        p.eps[i] = (float)(p.eps_coef * (x * nH) * (x * nH));
+    }
+    if (!p.solve) return;
+    // block max, then one atomic max on the bit pattern (r >= 0)
+    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = r;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        r = threadIdx.x < (blockDim.x >> 5) ? smax[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+        if (threadIdx.x == 0) atomicMax(p.resid, (unsigned long long)__double_as_longlong(r));
+    }
+}
+
+template <typename T> art_status ensure(art_ctx *ctx, T **p, size_t n)
+{
+    if (*p) return ART_OK;
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return art_fail(ctx, e == cudaErrorMemoryAllocation ? ART_E_OOM : ART_E_CUDA,
+                        std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    ctx->dev_bytes += (long long)(n * sizeof(T));
+    *p = static_cast<T *>(q);
+    return ART_OK;
+}
+
+art_status upload_sources(art_ctx *ctx, const art_source *src, int n_src, const double *Qb, int nbins,
+                          std::vector<double> &h_src, std::vector<double> &h_q)
+{
+    h_src.assign(4 * (size_t)n_src, 0.0);
+    h_q.assign((size_t)n_src * nbins, 0.0);
+    for (int a = 0; a < n_src; ++a) {
+        const art_source &s = src[a];
+        if (!std::isfinite(s.x) || !std::isfinite(s.y) || !std::isfinite(s.z) || !(s.Q >= 0.0) ||
+            s.x < 0 || s.y < 0 || s.z < 0 || s.x > ctx->grid.nx || s.y > ctx->grid.ny || s.z > ctx->grid.nz)
+            return art_fail(ctx, ART_E_INVALID, "point source outside the box or with a bad luminosity");
+        h_src[4 * a] = s.x;
+        h_src[4 * a + 1] = s.y;
+        h_src[4 * a + 2] = s.z;
+        for (int b = 0; b < nbins; ++b) h_q[(size_t)a * nbins + b] = Qb ? Qb[(size_t)a * nbins + b] : (b == 0 ? s.Q : 0.0);
+    }
+    return ART_OK;
+}
+
+// Point-source rates into gamma (device), kappa per bin on the device.
+art_status launch_points(art_ctx *ctx, const float *kappa, int nbins, const double *d_src, const double *d_q,
+                         const double *d_sigma, int n_src, float *gamma, cudaStream_t st)
+{
+    PtArgs a;
+    a.kappa = kappa;
+    a.src = d_src;
+    a.Qb = d_q;
+    a.sigma = d_sigma;
+    a.nsrc = n_src;
+    a.nbins = nbins;
+    a.nx = ctx->grid.nx;
+    a.ny = ctx->grid.ny;
+    a.nz = ctx->grid.nz;
+    a.ncell = ctx->ncell;
+    a.dx = ctx->grid.dx_cm;
+    a.gamma = gamma;
+    const int nt = 128;
+    const unsigned nb = (unsigned)((ctx->ncell + nt - 1) / nt);
+    switch (nbins) {
+    case 1: point_source_kernel<1><<<nb, nt, 0, st>>>(a); break;
+    case 2: point_source_kernel<2><<<nb, nt, 0, st>>>(a); break;
+    case 3: point_source_kernel<3><<<nb, nt, 0, st>>>(a); break;
+    case 4: point_source_kernel<4><<<nb, nt, 0, st>>>(a); break;
+    default: return art_fail(ctx, ART_E_INVALID, "point sources: 1 to 4 bins");
+    }
+    ICK(ctx, cudaGetLastError());
+    return ART_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+art_status art_point_sources(art_ctx *ctx, const float *kappa, const double *sigma, const art_source *src,
+                             const double *Qb, int n_src, float *gamma, void *stream)
+{
+    if (!ctx) return ART_E_INVALID;
+    if (!kappa || !sigma || !gamma || (n_src > 0 && !src) || n_src < 0)
+        return art_fail(ctx, ART_E_INVALID, "art_point_sources: null argument");
+    const int nbins = ctx->nbins;
+    if (nbins > kMaxBins) return art_fail(ctx, ART_E_INVALID, "art_point_sources: at most 4 bins");
+    if (!(ctx->grid.dx_cm > 0.0)) return art_fail(ctx, ART_E_INVALID, "art_point_sources: grid dx_cm must be > 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<double> h_src, h_q;
+    art_status s = upload_sources(ctx, src, n_src, Qb, nbins, h_src, h_q);
+    if (s != ART_OK) return s;
+    for (int b = 0; b < nbins; ++b)
+        if (!(sigma[b] >= 0.0)) return art_fail(ctx, ART_E_INVALID, "art_point_sources: bad cross section");
+    const int cap = n_src > 0 ? n_src : 1;
+    if (ctx->it.nsrc_cap < cap * (nbins + 4) + nbins) {
+        if (ctx->it.src) cudaFree(ctx->it.src);
+        ctx->it.src = nullptr;
+        ctx->it.nsrc_cap = cap * (nbins + 4) + nbins;
+        if ((s = ensure(ctx, &ctx->it.src, (size_t)ctx->it.nsrc_cap)) != ART_OK) return s;
+    }
+    double *d_src = ctx->it.src, *d_q = d_src + 4 * cap, *d_sig = d_q + (size_t)cap * nbins;
+    if (n_src > 0) {
+        ICK(ctx, cudaMemcpyAsync(d_src, h_src.data(), h_src.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        ICK(ctx, cudaMemcpyAsync(d_q, h_q.data(), h_q.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    }
+    ICK(ctx, cudaMemcpyAsync(d_sig, sigma, nbins * sizeof(double), cudaMemcpyHostToDevice, st));
+    s = launch_points(ctx, kappa, nbins, d_src, d_q, d_sig, n_src, gamma, st);
+    if (s != ART_OK) return s;
+    // host vectors are copied from: wait before they go out of scope
+    ICK(ctx, cudaStreamSynchronize(st));
+    return ART_OK;
+}
+
+art_status art_iterate_ionization(art_ctx *ctx, const art_chem *ch, const double *nH, const art_source *src,
+                                  int n_src, double tol, int max_iter, double *y, double *resid_hist,
+                                  art_iter_report *rep, void *stream)
+{
+    if (!ctx) return ART_E_INVALID;
+    if (!ch || !nH || !y || (n_src > 0 && !src) || n_src < 0 || max_iter < 1 || !(tol > 0.0))
+        return art_fail(ctx, ART_E_INVALID, "art_iterate_ionization: bad argument");
+    if (ctx->prec != ART_FP32 || ctx->nbins != 1 || ctx->opt.field_form != ART_FIELDS_EPS)
+        return art_fail(ctx, ART_E_INVALID,
+                        "art_iterate_ionization: needs an FP32 context with one bin and ART_FIELDS_EPS inputs");
+    if (!(ctx->grid.dx_cm > 0.0) || !(ch->sigma0 > 0.0) || !(ch->h > 0.0) || !(ch->nu0 > 0.0) || !(ch->dnu > 0.0) ||
+        !(ch->alphaB > 0.0) || !(ch->alphaA >= ch->alphaB) || !(ch->gcoll >= 0.0))
+        return art_fail(ctx, ART_E_INVALID, "art_iterate_ionization: bad chemistry constants");
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const long long n = ctx->ncell;
+    art_iter_bufs &B = ctx->it;
+    art_status s;
+    if ((s = ensure(ctx, &B.gpt, n)) != ART_OK || (s = ensure(ctx, &B.kap, n)) != ART_OK ||
+        (s = ensure(ctx, &B.eps, n)) != ART_OK || (s = ensure(ctx, &B.jin, n)) != ART_OK ||
+        (s = ensure(ctx, &B.resid, 1)) != ART_OK)
+        return s;
+    std::vector<double> h_src, h_q;
+    if ((s = upload_sources(ctx, src, n_src, nullptr, 1, h_src, h_q)) != ART_OK) return s;
+    const int cap = n_src > 0 ? n_src : 1;
+    if (B.nsrc_cap < cap * 5 + 1) {
+        if (B.src) cudaFree(B.src);
+        B.src = nullptr;
+        B.nsrc_cap = cap * 5 + 1;
+        if ((s = ensure(ctx, &B.src, (size_t)B.nsrc_cap)) != ART_OK) return s;
+    }
+    double *d_src = B.src, *d_q = d_src + 4 * cap, *d_sig = d_q + cap;
+    if (n_src > 0) {
+        ICK(ctx, cudaMemcpyAsync(d_src, h_src.data(), h_src.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        ICK(ctx, cudaMemcpyAsync(d_q, h_q.data(), h_q.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    }
+    ICK(ctx, cudaMemcpyAsync(d_sig, &ch->sigma0, sizeof(double), cudaMemcpyHostToDevice, st));
+
+    // G = int_{nu0}^{nu0 + dnu} sigma/(h nu) dnu for sigma = sigma0 (nu/nu0)^-3
+    double G = 0.0;
+    if (art_band_integral(ch->sigma0, ch->h, ch->nu0, ch->nu0, ch->nu0 + ch->dnu, &G) != ART_OK)
+        return art_fail(ctx, ART_E_INVALID, "art_iterate_ionization: bad band");
+    BalArgs ba;
+    ba.nH = nH;
+    ba.gpt = B.gpt;
+    ba.gdiff = B.jin;
+    ba.alphaB = ch->alphaB;
+    ba.gcoll = ch->gcoll;
+    ba.kap_coef = ch->sigma0 * ctx->grid.dx_cm;
+    ba.eps_coef = G * ch->h * ch->nu0 * (ch->alphaA - ch->alphaB) * ctx->grid.dx_cm / ch->dnu;
+    ba.y = y;
+    ba.kap = B.kap;
+    ba.eps = B.eps;
+    ba.resid = B.resid;
+    ba.ncell = n;
+    const int nt = 256;
+    const unsigned nb = (unsigned)((n + nt - 1) / nt);
+    ba.solve = 0;
+    balance_kernel<<<nb, nt, 0, st>>>(ba);
+    ICK(ctx, cudaGetLastError());
+    ba.solve = 1;
+
+    int it = 0, conv = 0;
+    double r = 0.0;
+    for (it = 1; it <= max_iter; ++it) {
+        if ((s = launch_points(ctx, B.kap, 1, d_src, d_q, d_sig, n_src, B.gpt, st)) != ART_OK) return s;
+        if ((s = art_internal_layout(ctx, B.kap, B.eps, st)) != ART_OK) return s;
+        if ((s = art_internal_sweep(ctx, nullptr, B.jin, nullptr, st)) != ART_OK) return s;
+        ICK(ctx, cudaMemsetAsync(B.resid, 0, sizeof(unsigned long long), st));
+        balance_kernel<<<nb, nt, 0, st>>>(ba);
+        ICK(ctx, cudaGetLastError());
+        unsigned long long bits = 0;
+        ICK(ctx, cudaMemcpyAsync(&bits, B.resid, sizeof(bits), cudaMemcpyDeviceToHost, st));
+        ICK(ctx, cudaStreamSynchronize(st));
+        std::memcpy(&r, &bits, sizeof(r));
+        if (resid_hist) resid_hist[it - 1] = r;
+        if (r < tol) {
+            conv = 1;
+            break;
+        }
+    }
+    if (rep) {
+        rep->iterations = conv ? it : max_iter;
+        rep->converged = conv;
+        rep->residual = r;
+        rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return conv ? ART_OK : art_fail(ctx, ART_E_NOT_CONVERGED, "art_iterate_ionization: max_iter reached");
+}
+
+}  // extern "C"

@@ -1,0 +1,123 @@
+"""GPU parity of the point sources (App. A), the FP64 balance (App. B) and the
+RT/balance iteration (App. D) against the FP64 oracle.
+
+Point sources: FP32 march, FP64 rate; within 1e-5 relative of the oracle on
+the FP32-rounded opacities.  Iteration: the converged neutral fraction within
+1e-4 relative of the oracle's (the FP32 sweep and march errors of ~1e-6 are
+amplified by the fixed point), same iteration count within one.  At the full
+128^3 / N_side 8 configuration the GPU's converged state is checked as a
+fixed point of the paper's equations evaluated by the oracle at sampled cells.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1410_0763_gb300 import art, build
+from paper_1410_0763_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    art.load()
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)))
+
+
+@pytest.mark.parametrize("nbins", [1, 3])
+def test_point_sources_match_oracle(orc, nbins):
+    rng = np.random.default_rng(21 + nbins)
+    shape = (20, 24, 28)
+    kap = (0.3 * np.exp(rng.standard_normal((nbins,) + shape))).astype(np.float32)
+    nz, ny, nx = shape
+    sources = [(nx / 2, ny / 2, nz / 2, 3e48),                 # on a vertex: tie-break
+               (3.37, 17.81, 5.12, 1e48),
+               (25.5, 0.25, 19.5, 2e48)]                       # on a cell-centre line
+    sigma = [6.3e-18, 3.1e-18, 1.2e-18][:nbins]
+    Qb = rng.uniform(0.5, 1.5, (3, nbins)) * np.array([s[3] for s in sources])[:, None]
+    dx = 1.6e20
+    sw = art.ArtSweep(shape, 2, nbins, dx_cm=dx)
+    k = torch.as_tensor(kap, device="cuda")
+    g = torch.empty(shape, dtype=torch.float32, device="cuda")
+    sw.point_sources(k, sigma, sources, g, Qb=Qb)
+    torch.cuda.synchronize()
+    sw.close()
+    ref = orc.point_sources(kap.astype(np.float64), sigma, np.array([s[:3] for s in sources]), Qb, dx)
+    assert rel(g.cpu().numpy().astype(np.float64), ref) < 1e-5
+
+
+def test_point_sources_thin_limit():
+    # kappa -> 0: Gamma -> Q sigma / (4 pi r^2) far from the source (inverse square)
+    shape = (32, 32, 32)
+    sw = art.ArtSweep(shape, 1, 1, dx_cm=1e20)
+    k = torch.zeros(shape, dtype=torch.float32, device="cuda")
+    g = torch.empty_like(k)
+    src = (1.3, 2.2, 0.7, 1e50)
+    sw.point_sources(k, [6.3e-18], [src], g)
+    torch.cuda.synchronize()
+    sw.close()
+    gh = g.cpu().numpy()
+    for (x, y, z) in [(30, 5, 2), (20, 28, 31), (31, 31, 31)]:
+        r = math.dist((x + 0.5, y + 0.5, z + 0.5), src[:3]) * 1e20
+        assert gh[z, y, x] == pytest.approx(1e50 * 6.3e-18 / (4 * math.pi * r * r), rel=2e-3)
+
+
+def _run_gpu_iteration(case, tol=1e-6, max_iter=300):
+    shape = case.nH.shape
+    sw = art.ArtSweep(shape, case.nside, 1, field_form=art.ART_FIELDS_EPS, dx_cm=case.chem["dx"])
+    nH = torch.as_tensor(case.nH, dtype=torch.float64, device="cuda")
+    y = torch.as_tensor(case.y0, dtype=torch.float64, device="cuda").clone()
+    srcs = [(p[0], p[1], p[2], q) for p, q in zip(case.pos, case.Q)]
+    rep, hist = sw.iterate(nH, case.chem, srcs, y, tol=tol, max_iter=max_iter)
+    torch.cuda.synchronize()
+    sw.close()
+    return y.cpu().numpy(), rep, hist
+
+
+@pytest.mark.parametrize("n,nside,box", [(16, 2, 1.6), (20, 2, 3.0)])
+def test_iteration_matches_oracle(orc, n, nside, box):
+    case = wl.hii_region(n=n, nside=nside, box_kpc=box)
+    y_gpu, rep, hist = _run_gpu_iteration(case)
+    y_orc, it_orc, hist_orc, conv = orc.iterate(case.nH, case.nside, case.chem, case.pos, case.Q, case.y0,
+                                                1e-6, 300)
+    assert conv and rep.converged
+    assert abs(rep.iterations - it_orc) <= 1
+    assert rel(y_gpu, y_orc) < 1e-4
+    assert rel(1 - y_gpu, 1 - y_orc) < 1e-4
+    # the residual history follows the oracle's until the last few iterations
+    k = min(len(hist), len(hist_orc)) - 3
+    assert np.allclose(hist[:k], hist_orc[:k], rtol=1e-3, atol=1e-9)
+
+
+def test_full_size_hii_region_is_a_fixed_point(orc):
+    case = wl.hii_region()          # 128^3, N_side 8, Q = 5e48 at the centre
+    y, rep, hist = _run_gpu_iteration(case, max_iter=200)
+    assert rep.converged and hist[-1] < 1e-6
+    assert np.all((y > 0) & (y < 1))
+    # R_S = 5.4 kpc exceeds the half box: the whole box is ionized
+    assert np.max(y) < 0.1
+    ch = case.chem
+    nH = case.nH
+    ne = (1 - y) * nH
+    kap = (y * nH * ch["sigma0"] * ch["dx"]).astype(np.float32).astype(np.float64)
+    dalpha = ch["alphaA"] - ch["alphaB"]
+    eps = (ch["h"] * ch["nu0"] * dalpha * ne * ne * ch["dx"] / (4 * math.pi * ch["dnu"]))
+    eps = eps.astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(3)
+    cells = rng.choice(y.size, 24, replace=False)
+    cells[:3] = [0, y.size - 1, (64 * 128 + 64) * 128 + 64]
+    jin = orc.jin_cells(kap, eps, case.nside, cells, field_form=1)
+    G = orc.band_integral(ch["sigma0"], ch["h"], ch["nu0"], ch["nu0"] + ch["dnu"])
+    gpt = orc.point_sources(kap, [ch["sigma0"]], case.pos, case.Q.reshape(-1, 1), ch["dx"]).ravel()[cells]
+    g = 4 * math.pi * G * jin + gpt
+    y_check = orc.balance_eq(nH.ravel()[cells], ch["alphaB"], ch["gcoll"], g)
+    assert rel(y.ravel()[cells], y_check) < 1e-4
