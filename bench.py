@@ -59,7 +59,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="grf64")
-    p.add_argument("--no-extra", action="store_true", help="skip the 128^3 / 256^3 side measurements")
+    p.add_argument("--no-extra", action="store_true", help="skip the side measurements (128^3, 256^3, 48-grid batch, 128^3 ionization solve)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -195,6 +195,69 @@ def side_measure(wl_name, torch, dev, G, steps=5):
             "segments_per_step": int(seg), "value": seg / (t * 1e-3)}
 
 
+def batch_measure(torch, dev, steps=5):
+    """48 grids of 32^3..96^3 cells and N_side 2..8 in one context: work-queue
+    launches replayed as a CUDA graph, kernel variant picked by the autotuner
+    (untimed), L2 flushed between timed steps."""
+    from paper_1410_0763_gb300 import art
+    from paper_1410_0763_gb300 import workloads as wl
+    cases = wl.batch48()
+    shapes = [c.kappa.shape for c in cases]
+    k = torch.cat([torch.as_tensor(c.kappa.ravel(), dtype=torch.float32) for c in cases]).to(dev)
+    s = torch.cat([torch.as_tensor(c.src.ravel(), dtype=torch.float32) for c in cases]).to(dev)
+    sw = art.ArtSweep(shapes, [c.nside for c in cases], graph=True)
+    sw.set_fields(k, s)
+    t0 = time.perf_counter()
+    best = sw.autotune(2)
+    tune_s = time.perf_counter() - t0
+    Jin = torch.empty_like(k)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        sw.sweep(J_in=Jin)
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in evs:
+        flush.zero_()
+        a.record(stream)
+        sw.sweep(J_in=Jin)
+        b.record(stream)
+    torch.cuda.synchronize()
+    t = statistics.median([a.elapsed_time(b) for a, b in evs])
+    st = sw.stats
+    sw.close()
+    return {"workload": "48 grids, sizes from {32,48,64,96}^3, N_side from {2,4,8}, lognormal GRF "
+                        "sigma in [0.5,1.5], one bin",
+            "cells": int(sum(np.prod(x) for x in shapes)), "ms_per_step": round(t, 4),
+            "segments_per_step": int(st.segments), "value": st.segments / (t * 1e-3),
+            "variant": best, "autotune_s": round(tune_s, 3), "work_items": int(st.work_items),
+            "ctas_per_launch": int(st.ctas_per_launch), "launches": int(st.launches), "graph": True}
+
+
+def ionization_measure(torch, dev, tol=1e-6):
+    """RT / ionization-balance iteration of a 128^3 HII region (N_side 8,
+    n_H 1e-3, Q 5e48 s^-1 at the centre, 6.6 kpc box) to residual tol, plain
+    start (uniform neutral fraction 1 - 1e-4)."""
+    from paper_1410_0763_gb300 import art
+    from paper_1410_0763_gb300 import workloads as wl
+    case = wl.hii_region()
+    sw = art.ArtSweep(case.nH.shape, case.nside, 1, field_form=art.ART_FIELDS_EPS, dx_cm=case.chem["dx"])
+    nH = torch.as_tensor(case.nH, dtype=torch.float64, device=dev)
+    srcs = [(p[0], p[1], p[2], q) for p, q in zip(case.pos, case.Q)]
+    y = torch.as_tensor(case.y0, dtype=torch.float64, device=dev).clone()
+    sw.iterate(nH, case.chem, srcs, y, tol=tol, max_iter=300)          # warm-up (first-call allocations)
+    y = torch.as_tensor(case.y0, dtype=torch.float64, device=dev).clone()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rep, hist = sw.iterate(nH, case.chem, srcs, y, tol=tol, max_iter=300)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    sw.close()
+    return {"workload": "128^3 HII region, N_side 8, uniform n_H 1e-3, T 1e4 K, Q 5e48 s^-1 central, 6.6 kpc, "
+                        "FP32 sweep + FP64 balance", "tol": tol, "iterations": int(rep.iterations),
+            "converged": bool(rep.converged), "residual": float(rep.residual), "seconds": round(dt, 4),
+            "start": "plain"}
+
+
 def cpu_baseline(case, seg_per_sweep: int, budget_s: float = 12.0) -> dict:
     import oracle
     oracle.build()
@@ -301,6 +364,11 @@ def run_ours(args, d: Dist):
                     extra[name] = side_measure(name, torch, dev, G)
                 except Exception as ex:  # pragma: no cover
                     extra[name] = {"error": str(ex)}
+        for name, fn in (("batch48", batch_measure), ("rt_ionization_128", ionization_measure)):
+            try:
+                extra[name] = fn(torch, dev)
+            except Exception as ex:  # pragma: no cover
+                extra[name] = {"error": str(ex)}
 
     cpu = None
     if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:

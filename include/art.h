@@ -71,6 +71,11 @@ typedef struct {
     int dir_split;    /* direction groups per octant class (J partials);  0 = auto */
     double tie_tol;   /* dominant-axis tie tolerance (relative), default 1e-12 */
     int variant;      /* sweep-kernel variant (1-based index of the compiled table); 0 = auto */
+    int persistent;   /* slab-block launches as a fixed grid of CTAs taking work items
+                         from a queue: 1 = on, -1 = off, 0 = auto (on for batches) */
+    int graph;        /* 1: art_sweep replays the launches of one sweep as a CUDA graph
+                         (captured on the first call and again whenever the output
+                         pointers, band integrals or variant change); 0 = plain launches */
 } art_options;
 
 /* Statistics of one sweep, fixed at art_create. */
@@ -84,6 +89,9 @@ typedef struct {
     int64_t device_bytes;    /* device memory owned by the context */
     int32_t variant;         /* sweep-kernel variant in use (1-based) */
     int32_t group;           /* directions processed per exchange barrier */
+    int32_t n_grids;         /* grids in the context (1 outside batches) */
+    int32_t work_items;      /* (class, tile, direction group) items per slab-block launch */
+    int32_t persistent;      /* 1 if launches take work items from a queue */
 } art_sweep_stats;
 
 /* Fill `opt` with defaults (FP32, paper averaging, (kappa, S) inputs, auto
@@ -102,6 +110,34 @@ art_status art_options_default(art_options *opt);
  */
 art_status art_create(const art_grid *grid, int n_side, int nu_bins, const art_options *opt,
                       art_ctx **out);
+
+/*
+ * Create a context for a batch of n_grids independent grids (the many-problem
+ * mode: e.g. several sub-volumes or snapshots solved together).  grids[g] and
+ * n_side[g] give each grid's cells and angular resolution; grids may differ in
+ * both.  One sweep covers every grid: each slab-block launch carries the work
+ * items (direction class x ray-plane tile x direction group) of all grids, so
+ * small grids fill the GPU together.  Field and output arrays are the grids'
+ * [bin][z][y][x] arrays concatenated grid after grid inside each bin:
+ * [bin][grid g cells ... ] with grid g starting at cell offset
+ * sum_{h<g} nx_h ny_h nz_h.  Results are identical to sweeping each grid in
+ * its own context.  Errors as art_create, plus ART_E_INVALID for n_grids < 1
+ * or > 4096 and for more than 2^31 cells in total.
+ */
+art_status art_batch_create(const art_grid *grids, const int *n_side, int n_grids, int nu_bins,
+                            const art_options *opt, art_ctx **out);
+
+/*
+ * Time every compiled sweep-kernel variant of the context's precision on the
+ * fields already set (reps sweeps each after one warm-up, on `stream`,
+ * synchronizing it), in both launch forms (one CTA per work item, or the
+ * persistent work queue) unless art_options.persistent fixed one, and keep
+ * the fastest; *best_variant (may be NULL) receives its 1-based index.  Outputs of the timing sweeps go to internal
+ * buffers.  Rebuilds the context's tables (direction groups chosen per
+ * variant as at creation unless options fixed them).  Errors: ART_E_STATE (no
+ * fields set), ART_E_OOM, ART_E_CUDA.
+ */
+art_status art_autotune(art_ctx *ctx, int reps, int *best_variant, void *stream);
 
 /* Release a context and all its device memory.  NULL is accepted. */
 art_status art_destroy(art_ctx *ctx);

@@ -31,14 +31,15 @@ class ArtGrid(C.Structure):
 class ArtOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("averaging", C.c_int), ("field_form", C.c_int),
                 ("tile_b", C.c_int), ("tile_c", C.c_int), ("slab", C.c_int), ("dir_split", C.c_int),
-                ("tie_tol", C.c_double), ("variant", C.c_int)]
+                ("tie_tol", C.c_double), ("variant", C.c_int), ("persistent", C.c_int), ("graph", C.c_int)]
 
 
 class ArtSweepStats(C.Structure):
     _fields_ = [("segments", C.c_int64), ("n_dirs", C.c_int32), ("n_classes", C.c_int32),
                 ("launches", C.c_int32), ("ctas_per_launch", C.c_int32), ("tile_b", C.c_int32),
                 ("tile_c", C.c_int32), ("slab", C.c_int32), ("dir_split", C.c_int32),
-                ("device_bytes", C.c_int64), ("variant", C.c_int32), ("group", C.c_int32)]
+                ("device_bytes", C.c_int64), ("variant", C.c_int32), ("group", C.c_int32),
+                ("n_grids", C.c_int32), ("work_items", C.c_int32), ("persistent", C.c_int32)]
 
 
 class ArtChem(C.Structure):
@@ -87,6 +88,9 @@ def load() -> C.CDLL:
         P = C.c_void_p
         lib.art_options_default.argtypes = [C.POINTER(ArtOptions)]
         lib.art_create.argtypes = [C.POINTER(ArtGrid), C.c_int, C.c_int, C.POINTER(ArtOptions), C.POINTER(P)]
+        lib.art_batch_create.argtypes = [C.POINTER(ArtGrid), C.POINTER(C.c_int), C.c_int, C.c_int,
+                                         C.POINTER(ArtOptions), C.POINTER(P)]
+        lib.art_autotune.argtypes = [P, C.c_int, C.POINTER(C.c_int), P]
         lib.art_destroy.argtypes = [P]
         lib.art_last_error.argtypes = [P]
         lib.art_last_error.restype = C.c_char_p
@@ -126,6 +130,23 @@ def art_create(grid: ArtGrid, n_side: int, nu_bins: int, opt: ArtOptions | None)
     if st != ART_OK:
         raise ArtError(st, "art_create failed")
     return h
+
+
+def art_batch_create(grids, n_side, nu_bins: int, opt: ArtOptions | None):
+    n = len(grids)
+    ga = (ArtGrid * n)(*grids)
+    na = (C.c_int * n)(*[int(x) for x in n_side])
+    h = C.c_void_p()
+    st = load().art_batch_create(ga, na, n, int(nu_bins), C.byref(opt) if opt else None, C.byref(h))
+    if st != ART_OK:
+        raise ArtError(st, "art_batch_create failed")
+    return h
+
+
+def art_autotune(ctx, reps: int, stream: int) -> tuple[int, int]:
+    best = C.c_int(0)
+    st = load().art_autotune(ctx, int(reps), C.byref(best), C.c_void_p(stream))
+    return st, best.value
 
 
 def art_destroy(ctx) -> int:
@@ -256,14 +277,24 @@ def _sources(sources):
 
 
 class ArtSweep:
-    """One sweep context: grid (nz, ny, nx), N_side, frequency bins."""
+    """One sweep context: a grid (nz, ny, nx) with its N_side, or a batch --
+    `shape` a list of (nz, ny, nx) and `nside` an int or one per grid -- and
+    the number of frequency bins.  Batch arrays are the grids' [z][y][x]
+    arrays concatenated inside each bin (see `offsets`)."""
 
-    def __init__(self, shape, nside: int, nbins: int = 1, precision: str = "fp32", field_form: int = 0,
+    def __init__(self, shape, nside, nbins: int = 1, precision: str = "fp32", field_form: int = 0,
                  dx_cm: float = 1.0, tile_b: int = 0, tile_c: int = 0, slab: int = 0, dir_split: int = 0,
-                 tie_tol: float = 1e-12, variant: int = 0):
-        nz, ny, nx = shape
-        self.shape = (int(nz), int(ny), int(nx))
-        self.nside, self.nbins = int(nside), int(nbins)
+                 tie_tol: float = 1e-12, variant: int = 0, persistent: int = 0, graph: bool = False):
+        batch = len(shape) > 0 and not np.isscalar(shape[0])
+        shapes = [tuple(int(v) for v in s) for s in (shape if batch else [shape])]
+        nsides = [int(v) for v in nside] if not np.isscalar(nside) else [int(nside)] * len(shapes)
+        if len(nsides) != len(shapes):
+            raise ValueError("one n_side per grid")
+        self.batch = batch
+        self.shapes = shapes
+        self.shape = shapes[0]
+        self.nsides = nsides
+        self.nside, self.nbins = nsides[0], int(nbins)
         self.dtype = np.float64 if precision == "fp64" else np.float32
         opt = art_options_default()
         opt.precision = ART_FP64 if precision == "fp64" else ART_FP32
@@ -271,8 +302,22 @@ class ArtSweep:
         opt.tile_b, opt.tile_c, opt.slab, opt.dir_split = tile_b, tile_c, slab, dir_split
         opt.tie_tol = tie_tol
         opt.variant = int(variant)
-        self._ctx = art_create(ArtGrid(nx, ny, nz, dx_cm), nside, nbins, opt)
-        self.ncell = nx * ny * nz
+        opt.persistent = int(persistent)
+        opt.graph = 1 if graph else 0
+        grids = [ArtGrid(nx, ny, nz, dx_cm) for (nz, ny, nx) in shapes]
+        if batch:
+            self._ctx = art_batch_create(grids, nsides, nbins, opt)
+        else:
+            self._ctx = art_create(grids[0], nsides[0], nbins, opt)
+        sizes = [nz * ny * nx for (nz, ny, nx) in shapes]
+        self.offsets = [int(v) for v in np.concatenate([[0], np.cumsum(sizes)[:-1]])]
+        self.ncell = int(sum(sizes))
+
+    def autotune(self, reps: int = 3, stream=None) -> int:
+        """Time every compiled kernel variant on the current fields; keep the fastest."""
+        st, best = art_autotune(self._ctx, reps, _stream(stream))
+        _check(self._ctx, st)
+        return best
 
     def close(self):
         if getattr(self, "_ctx", None):

@@ -1,5 +1,7 @@
-// art_api.cu -- C ABI of libart (see include/art.h): context set-up, device
-// memory, launches of the slab-block sweep and the partial reduction.
+// art_api.cu -- C ABI of libart (see include/art.h): context set-up for one
+// grid or a batch of grids, device memory, launches of the slab-block sweep
+// (one CTA per work item, or persistent CTAs on a work queue; optionally
+// replayed as a CUDA graph), the partial reduction and the variant autotuner.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -50,18 +52,48 @@ template <typename T> art_status dev_alloc(art_ctx *ctx, T **p, size_t bytes)
     return ART_OK;
 }
 
+template <typename T> void dev_free(art_ctx *ctx, T *&p, size_t &bytes)
+{
+    if (p) {
+        cudaFree(p);
+        ctx->dev_bytes -= (long long)bytes;
+    }
+    p = nullptr;
+    bytes = 0;
+}
+
+// Launch one slab-block sweep.  The shared-memory attribute is set by
+// prepare_sweep (outside any stream capture).
 template <typename real, int TB, int TC, int BLK, int NT, int KP, int MINB>
-cudaError_t launch_sweep(const void *args, int nwork, cudaStream_t st)
+cudaError_t launch_sweep(const void *args, int nctas, cudaStream_t st)
 {
     const SweepArgs<real> &a = *static_cast<const SweepArgs<real> *>(args);
     const size_t sm = SweepShape<TB, TC, BLK, NT, KP>::template bytes<real>();
-    auto kern = sweep_block_kernel<real, TB, TC, BLK, NT, KP, MINB>;
-    if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-    }
-    kern<<<nwork, NT, sm, st>>>(a);
+    if (a.counter)
+        sweep_queue_kernel<real, TB, TC, BLK, NT, KP, MINB><<<nctas, NT, sm, st>>>(a);
+    else
+        sweep_block_kernel<real, TB, TC, BLK, NT, KP, MINB><<<nctas, NT, sm, st>>>(a);
     return cudaGetLastError();
+}
+
+// Allow the variant's dynamic shared memory; returns its resident CTAs per SM
+// (0 on error).
+template <typename real, int TB, int TC, int BLK, int NT, int KP, int MINB> int prepare_sweep()
+{
+    const size_t sm = SweepShape<TB, TC, BLK, NT, KP>::template bytes<real>();
+    auto kern = sweep_block_kernel<real, TB, TC, BLK, NT, KP, MINB>;
+    auto qkern = sweep_queue_kernel<real, TB, TC, BLK, NT, KP, MINB>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
+        cudaFuncSetAttribute(qkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int per_sm = 0;   // of the queue form, which sizes the persistent grid
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qkern, NT, sm) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm;
 }
 
 // Sweep-kernel variants compiled into the library: tile (b x c), slab block,
@@ -70,12 +102,14 @@ cudaError_t launch_sweep(const void *args, int nwork, cudaStream_t st)
 struct KVariant {
     int prec, tb, tc, blk, nt, kp, minb;
     cudaError_t (*launch)(const void *, int, cudaStream_t);
+    int (*prepare)();
 };
-#define ART_V(real, pr, tb, tc, blk, nt, kp, mb) \
-    {pr, tb, tc, blk, nt, kp, mb, &launch_sweep<real, tb, tc, blk, nt, kp, mb>}
+#define ART_V(real, pr, tb, tc, blk, nt, kp, mb)                                                   \
+    {pr, tb, tc, blk, nt, kp, mb, &launch_sweep<real, tb, tc, blk, nt, kp, mb>,                      \
+     &prepare_sweep<real, tb, tc, blk, nt, kp, mb>}
 const KVariant kVariants[] = {
-    ART_V(float, ART_FP32, 32, 16, 4, 256, 2, 3),   //  1: default FP32
-    ART_V(float, ART_FP32, 32, 8, 4, 256, 2, 3),    //  2
+    ART_V(float, ART_FP32, 32, 16, 4, 256, 2, 3),   //  1: default FP32, grids of >= 100^3 cells
+    ART_V(float, ART_FP32, 32, 8, 4, 256, 2, 3),    //  2: default FP32, smaller grids
     ART_V(float, ART_FP32, 32, 16, 4, 256, 1, 4),   //  3
     ART_V(float, ART_FP32, 32, 16, 4, 256, 3, 2),   //  4
     ART_V(float, ART_FP32, 32, 16, 2, 256, 2, 3),   //  5
@@ -93,69 +127,112 @@ struct HostTables {
     std::vector<ClassDev> classes;
     std::vector<DirDev> dirs;
     std::vector<SlabGeom> geo;    // concatenated per class-sorted direction
-    std::vector<int> part_axis;
     std::vector<WorkItem> work;
+    std::vector<art_grid_host> grids;
     long long plane_elems = 0;
-    long long seg_count = 0;
+    long long jpart_elems = 0;
+    int max_blocks = 0;
+    int min_per_class = 1 << 30;  // fewest directions in a non-empty class
 };
 
-void build_tables(const art_ctx *ctx, const std::vector<double> &xyz, HostTables &t)
+// Tables of every grid for the context's tile, slab block and direction
+// groups.  Segment-table, plane and J-partial offsets run across the grids of
+// a batch; work items are ordered longest first, which the persistent queue
+// hands out first.  Each (class, group, cell) partial is written by exactly
+// one work item, so the order changes no result.
+void build_tables(const art_ctx *ctx, HostTables &t)
 {
-    const int dims[3] = {ctx->grid.nx, ctx->grid.ny, ctx->grid.nz};
-    std::vector<Frame> fr(ctx->nd);
-    for (int d = 0; d < ctx->nd; ++d) fr[d] = frame_of(&xyz[3 * d], ctx->opt.tie_tol);
-    long long seg_off = 0, plane_off = 0;
-    for (int cls = 0; cls < 24; ++cls) {
-        std::vector<int> members;
-        for (int d = 0; d < ctx->nd; ++d)
-            if (fr[d].cls == cls) members.push_back(d);
-        if (members.empty()) continue;
-        // Order within the class: by column drift per slab block along b, then
-        // c, then RING index.  Directions the kernel takes together then have
-        // similar upstream cones.  The order is fixed, so sums stay deterministic.
-        auto drift = [&](double q) { return (int)std::floor(q * ctx->BLK + 0.5); };
-        std::stable_sort(members.begin(), members.end(), [&](int x, int y) {
-            const int bx = drift(fr[x].qb), by = drift(fr[y].qb);
-            if (bx != by) return bx < by;
-            return drift(fr[x].qc) < drift(fr[y].qc);
-        });
-        const Frame &f0 = fr[members[0]];
-        ClassDev C;
-        C.a = f0.a;
-        C.sa = f0.sa;
-        C.sb = f0.sb;
-        C.sc = f0.sc;
-        C.Na = dims[f0.a];
-        C.Nb = dims[f0.b];
-        C.Nc = dims[f0.c];
-        C.dir_begin = (int)t.dirs.size();
-        C.dir_end = C.dir_begin + (int)members.size();
-        C.part0 = (int)t.part_axis.size();
-        const int split = std::min<int>(ctx->split, (int)members.size());
-        for (int g = 0; g < ctx->split; ++g) t.part_axis.push_back(f0.a);
-        (void)split;
-        const int ci = (int)t.classes.size();
-        t.classes.push_back(C);
-        for (int d : members) {
-            std::vector<SlabGeom> g;
-            slab_geometry(fr[d], C.Na, g);
-            DirDev D;
-            D.seg_off = seg_off;
-            D.plane_off = plane_off;
-            D.na = fr[d].na;
-            t.dirs.push_back(D);
-            for (const SlabGeom &s : g) {
-                t.geo.push_back(s);
-                t.seg_count += (long long)s.nonzero * C.Nb * C.Nc;
+    long long seg_off = 0, plane_off = 0, jpart_off = 0, cell_off = 0;
+    std::vector<long long> cost;
+    for (const art_grid_host &gin : ctx->grids) {
+        art_grid_host gh = gin;
+        const int dims[3] = {gh.g.nx, gh.g.ny, gh.g.nz};
+        std::vector<double> xyz;
+        healpix_directions(gh.nside, xyz);
+        std::vector<Frame> fr(gh.nd);
+        for (int d = 0; d < gh.nd; ++d) fr[d] = frame_of(&xyz[3 * d], ctx->opt.tie_tol);
+        gh.cell_off = cell_off;
+        gh.jpart_off = jpart_off;
+        gh.seg_count = 0;
+        int part = 0, maxNa = 0;
+        for (int cls = 0; cls < 24; ++cls) {
+            std::vector<int> members;
+            for (int d = 0; d < gh.nd; ++d)
+                if (fr[d].cls == cls) members.push_back(d);
+            if (members.empty()) continue;
+            t.min_per_class = std::min(t.min_per_class, (int)members.size());
+            // Order within the class: by column drift per slab block along b,
+            // then c, then RING index.  Directions the kernel takes together
+            // then have similar upstream cones.  The order is fixed, so sums
+            // stay deterministic.
+            auto drift = [&](double q) { return (int)std::floor(q * ctx->BLK + 0.5); };
+            std::stable_sort(members.begin(), members.end(), [&](int x, int y) {
+                const int bx = drift(fr[x].qb), by = drift(fr[y].qb);
+                if (bx != by) return bx < by;
+                return drift(fr[x].qc) < drift(fr[y].qc);
+            });
+            const Frame &f0 = fr[members[0]];
+            ClassDev C;
+            C.a = f0.a;
+            C.sa = f0.sa;
+            C.sb = f0.sb;
+            C.sc = f0.sc;
+            C.Na = dims[f0.a];
+            C.Nb = dims[f0.b];
+            C.Nc = dims[f0.c];
+            C.dir_begin = (int)t.dirs.size();
+            C.dir_end = C.dir_begin + (int)members.size();
+            C.part0 = part;
+            C.nx = dims[0];
+            C.ny = dims[1];
+            C.nz = dims[2];
+            C.cell_off = gh.cell_off;
+            C.jpart_off = gh.jpart_off + (long long)part * gh.ncell;
+            C.ncell = gh.ncell;
+            part += ctx->split;
+            maxNa = std::max(maxNa, C.Na);
+            const int ci = (int)t.classes.size();
+            t.classes.push_back(C);
+            for (int d : members) {
+                std::vector<SlabGeom> g;
+                slab_geometry(fr[d], C.Na, g);
+                DirDev D;
+                D.seg_off = seg_off;
+                D.plane_off = plane_off;
+                D.na = fr[d].na;
+                t.dirs.push_back(D);
+                for (const SlabGeom &s : g) {
+                    t.geo.push_back(s);
+                    gh.seg_count += (long long)s.nonzero * C.Nb * C.Nc;
+                }
+                seg_off += C.Na;
+                plane_off += (long long)C.Nb * C.Nc;
             }
-            seg_off += C.Na;
-            plane_off += (long long)C.Nb * C.Nc;
+            const long long ndir = (long long)members.size();
+            for (int pc = 0; pc < C.Nc; pc += ctx->TC)
+                for (int pb = 0; pb < C.Nb; pb += ctx->TB)
+                    for (int g = 0; g < ctx->split; ++g) {
+                        t.work.push_back(WorkItem{ci, pb, pc, g});
+                        const long long nd_g = (ndir * (g + 1)) / ctx->split - (ndir * g) / ctx->split;
+                        cost.push_back((nd_g + 1) * std::min(ctx->TB, C.Nb - pb) * std::min(ctx->TC, C.Nc - pc) *
+                                       (long long)C.Na);
+                    }
         }
-        for (int pc = 0; pc < C.Nc; pc += ctx->TC)
-            for (int pb = 0; pb < C.Nb; pb += ctx->TB)
-                for (int g = 0; g < ctx->split; ++g) t.work.push_back(WorkItem{ci, pb, pc, g});
+        gh.n_part = part;
+        gh.nblocks = (maxNa + ctx->BLK - 1) / ctx->BLK;
+        t.max_blocks = std::max(t.max_blocks, gh.nblocks);
+        jpart_off += (long long)part * gh.ncell;
+        cell_off += gh.ncell;
+        t.grids.push_back(gh);
     }
+    std::vector<int> idx(t.work.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    std::vector<WorkItem> w(t.work.size());
+    for (size_t i = 0; i < idx.size(); ++i) w[i] = t.work[idx[i]];
+    t.work.swap(w);
     t.plane_elems = plane_off;
+    t.jpart_elems = jpart_off;
 }
 
 template <typename real> std::vector<SegEntry<real>> pack_segs(const std::vector<SlabGeom> &geo)
@@ -171,6 +248,102 @@ template <typename real> std::vector<SegEntry<real>> pack_segs(const std::vector
     return out;
 }
 
+template <typename real> art_status upload_gridinfo(art_ctx *ctx)
+{
+    std::vector<GridDev<real>> gi;
+    for (const art_grid_host &g : ctx->grids)
+        gi.push_back(GridDev<real>{g.cell_off, g.ncell, g.jpart_off, g.n_part, real(1.0 / g.nd)});
+    CK(ctx, cudaMemcpy(ctx->d_gridinfo, gi.data(), gi.size() * sizeof(gi[0]), cudaMemcpyHostToDevice));
+    return ART_OK;
+}
+
+// Select a kernel variant: build its tables and (re)allocate the buffers that
+// depend on them.  Field, plane and staging buffers do not depend on it.
+art_status setup_variant(art_ctx *ctx, int variant)
+{
+    const KVariant &k = kVariants[variant];
+    const int per_sm = k.prepare();
+    if (per_sm < 1) return fail(ctx, ART_E_CUDA, "sweep kernel variant cannot be launched on this device");
+    if (ctx->gexec) {
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+    }
+    ctx->variant = variant;
+    ctx->TB = k.tb;
+    ctx->TC = k.tc;
+    ctx->BLK = k.blk;
+    ctx->NT = k.nt;
+    ctx->KP = k.kp;
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaGetLastError();
+    // direction groups per class: enough work items to cover the GPU twice
+    ctx->split = 1;
+    if (ctx->opt.dir_split > 0) {
+        ctx->split = ctx->opt.dir_split;
+    } else {
+        HostTables probe;
+        build_tables(ctx, probe);
+        const int base = (int)probe.work.size();
+        while (base * ctx->split < 2 * sms && ctx->split * 2 <= probe.min_per_class) ctx->split *= 2;
+    }
+    HostTables t;
+    build_tables(ctx, t);
+    ctx->grids = t.grids;
+    ctx->n_classes = (int)t.classes.size();
+    ctx->n_part = 0;
+    ctx->seg_count = 0;
+    for (const art_grid_host &g : ctx->grids) {
+        ctx->n_part += g.n_part;
+        ctx->seg_count += g.seg_count;
+    }
+    ctx->n_work = (int)t.work.size();
+    ctx->nblocks = t.max_blocks;
+    ctx->plane_elems = t.plane_elems;
+    ctx->n_ctas = std::min(ctx->n_work, sms * per_sm);
+
+    dev_free(ctx, ctx->d_jpart, ctx->jpart_bytes);
+    dev_free(ctx, ctx->d_segs, ctx->segs_bytes);
+    dev_free(ctx, ctx->d_dirs, ctx->dirs_bytes);
+    dev_free(ctx, ctx->d_classes, ctx->classes_bytes);
+    dev_free(ctx, ctx->d_work, ctx->work_bytes);
+    dev_free(ctx, ctx->d_counter, ctx->counter_bytes);
+    dev_free(ctx, ctx->d_gridinfo, ctx->gridinfo_bytes);
+    const size_t jb = (size_t)t.jpart_elems * ctx->rsz;
+    const size_t sb = t.geo.size() * (ctx->prec == ART_FP64 ? sizeof(SegEntry<double>) : sizeof(SegEntry<float>));
+    const size_t db = t.dirs.size() * sizeof(DirDev), cb = t.classes.size() * sizeof(ClassDev);
+    const size_t wb = t.work.size() * sizeof(WorkItem), qb = (size_t)std::max(1, ctx->nblocks) * sizeof(int);
+    const size_t gb = ctx->grids.size() * sizeof(GridDev<double>);
+    art_status s;
+    if ((s = dev_alloc(ctx, &ctx->d_jpart, jb)) != ART_OK) return s;
+    ctx->jpart_bytes = jb;
+    if ((s = dev_alloc(ctx, &ctx->d_segs, sb)) != ART_OK) return s;
+    ctx->segs_bytes = sb;
+    if ((s = dev_alloc(ctx, &ctx->d_dirs, db)) != ART_OK) return s;
+    ctx->dirs_bytes = db;
+    if ((s = dev_alloc(ctx, &ctx->d_classes, cb)) != ART_OK) return s;
+    ctx->classes_bytes = cb;
+    if ((s = dev_alloc(ctx, &ctx->d_work, wb)) != ART_OK) return s;
+    ctx->work_bytes = wb;
+    if ((s = dev_alloc(ctx, &ctx->d_counter, qb)) != ART_OK) return s;
+    ctx->counter_bytes = qb;
+    if ((s = dev_alloc(ctx, &ctx->d_gridinfo, gb)) != ART_OK) return s;
+    ctx->gridinfo_bytes = gb;
+    if (ctx->prec == ART_FP64) {
+        auto v = pack_segs<double>(t.geo);
+        CK(ctx, cudaMemcpy(ctx->d_segs, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice));
+        if ((s = upload_gridinfo<double>(ctx)) != ART_OK) return s;
+    } else {
+        auto v = pack_segs<float>(t.geo);
+        CK(ctx, cudaMemcpy(ctx->d_segs, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice));
+        if ((s = upload_gridinfo<float>(ctx)) != ART_OK) return s;
+    }
+    CK(ctx, cudaMemcpy(ctx->d_dirs, t.dirs.data(), db, cudaMemcpyHostToDevice));
+    CK(ctx, cudaMemcpy(ctx->d_classes, t.classes.data(), cb, cudaMemcpyHostToDevice));
+    CK(ctx, cudaMemcpy(ctx->d_work, t.work.data(), wb, cudaMemcpyHostToDevice));
+    return ART_OK;
+}
+
 template <typename real> art_status do_sweep(art_ctx *ctx, real *J, real *Jin, real *gam, cudaStream_t st)
 {
     using v2 = typename Vec2<real>::type;
@@ -183,14 +356,11 @@ template <typename real> art_status do_sweep(art_ctx *ctx, real *J, real *Jin, r
         a.field1 = fields + (1LL * ctx->nbins + b) * n;
         a.field2 = fields + (2LL * ctx->nbins + b) * n;
         a.jpart = static_cast<real *>(ctx->d_jpart);
-        a.nx = ctx->grid.nx;
-        a.ny = ctx->grid.ny;
-        a.nz = ctx->grid.nz;
         a.segs = static_cast<const SegEntry<real> *>(ctx->d_segs);
         a.dirs = ctx->d_dirs;
         a.classes = ctx->d_classes;
         a.work = ctx->d_work;
-        a.ncell = n;
+        a.n_work = ctx->n_work;
         a.split = ctx->split;
         a.field_form = ctx->opt.field_form;
         cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
@@ -201,21 +371,23 @@ template <typename real> art_status do_sweep(art_ctx *ctx, real *J, real *Jin, r
             ctx->ev.push_back(e0);
             ctx->ev.push_back(e1);
             ctx->ev.push_back(e2);
-            CK(ctx, cudaEventRecord(e0, st));
         }
+        if (ctx->persistent) CK(ctx, cudaMemsetAsync(ctx->d_counter, 0, ctx->counter_bytes, st));
+        if (ctx->profiling) CK(ctx, cudaEventRecord(e0, st));
         for (int k = 0; k < ctx->nblocks; ++k) {
             a.kblock = k;
             a.plane_in = planes[k & 1];
             a.plane_out = planes[(k + 1) & 1];
-            CK(ctx, kVariants[ctx->variant].launch(&a, ctx->n_work, st));
+            a.counter = ctx->persistent ? ctx->d_counter + k : nullptr;
+            CK(ctx, kVariants[ctx->variant].launch(&a, ctx->persistent ? ctx->n_ctas : ctx->n_work, st));
         }
         if (ctx->profiling) CK(ctx, cudaEventRecord(e1, st));
         ReduceArgs<real> r;
         r.jpart = static_cast<const real *>(ctx->d_jpart);
         r.field_nat = fields + (2LL * ctx->nbins + b) * n;
-        r.n_part = ctx->n_part;
-        r.ncell = n;
-        r.inv_nd = real(1.0 / ctx->nd);
+        r.grids = static_cast<const GridDev<real> *>(ctx->d_gridinfo);
+        r.n_grids = (int)ctx->grids.size();
+        r.total = n;
         r.gamma_coef = real(4.0 * M_PI * ctx->G[b]);
         r.gamma_accum = b > 0;
         r.field_form = ctx->opt.field_form;
@@ -230,9 +402,7 @@ template <typename real> art_status do_sweep(art_ctx *ctx, real *J, real *Jin, r
     return ART_OK;
 }
 
-}  // namespace
-
-art_status art_internal_sweep(art_ctx *ctx, void *J, void *J_in, void *gamma, cudaStream_t st)
+art_status sweep_launches(art_ctx *ctx, void *J, void *J_in, void *gamma, cudaStream_t st)
 {
     if (ctx->prec == ART_FP64)
         return do_sweep<double>(ctx, static_cast<double *>(J), static_cast<double *>(J_in),
@@ -240,26 +410,170 @@ art_status art_internal_sweep(art_ctx *ctx, void *J, void *J_in, void *gamma, cu
     return do_sweep<float>(ctx, static_cast<float *>(J), static_cast<float *>(J_in), static_cast<float *>(gamma), st);
 }
 
+// Replay the launches of one sweep as a CUDA graph, captured on an internal
+// stream and ordered after the work already queued on `st` and before
+// anything queued on `st` later.  Captured again whenever the outputs change.
+art_status sweep_graph(art_ctx *ctx, void *J, void *J_in, void *gamma, cudaStream_t st)
+{
+    if (!ctx->gstream) {
+        CK(ctx, cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
+        CK(ctx, cudaEventCreateWithFlags(&ctx->gev[0], cudaEventDisableTiming));
+        CK(ctx, cudaEventCreateWithFlags(&ctx->gev[1], cudaEventDisableTiming));
+    }
+    if (ctx->gexec && (ctx->g_key[0] != J || ctx->g_key[1] != J_in || ctx->g_key[2] != gamma)) {
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+    }
+    if (!ctx->gexec) {
+        cudaGraph_t graph = nullptr;
+        CK(ctx, cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal));
+        const art_status s = sweep_launches(ctx, J, J_in, gamma, ctx->gstream);
+        const cudaError_t e = cudaStreamEndCapture(ctx->gstream, &graph);
+        if (s != ART_OK || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return s != ART_OK ? s : fail(ctx, ART_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            ctx->gexec = nullptr;
+            return fail(ctx, ART_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+        }
+        ctx->g_key[0] = J;
+        ctx->g_key[1] = J_in;
+        ctx->g_key[2] = gamma;
+    }
+    CK(ctx, cudaEventRecord(ctx->gev[0], st));
+    CK(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->gev[0], 0));
+    CK(ctx, cudaGraphLaunch(ctx->gexec, ctx->gstream));
+    CK(ctx, cudaEventRecord(ctx->gev[1], ctx->gstream));
+    CK(ctx, cudaStreamWaitEvent(st, ctx->gev[1], 0));
+    return ART_OK;
+}
+
+art_status create_common(const art_grid *grids, const int *n_side, int n_grids, int nu_bins, const art_options *opt,
+                         art_ctx **out)
+{
+    if (!out) return ART_E_INVALID;
+    *out = nullptr;
+    if (!grids || !n_side || n_grids < 1 || n_grids > 4096 || nu_bins < 1) return ART_E_INVALID;
+    long long total = 0, largest = 0;
+    for (int g = 0; g < n_grids; ++g) {
+        const art_grid &gr = grids[g];
+        if (gr.nx < 1 || gr.ny < 1 || gr.nz < 1 || n_side[g] < 1 || n_side[g] > 1024) return ART_E_INVALID;
+        const long long c = (long long)gr.nx * gr.ny * gr.nz;
+        if (c > (1LL << 31)) return ART_E_INVALID;
+        total += c;
+        largest = std::max(largest, c);
+    }
+    if (total > (1LL << 31)) return ART_E_INVALID;
+    art_ctx *ctx = new (std::nothrow) art_ctx();
+    if (!ctx) return ART_E_OOM;
+    ctx->grid = grids[0];
+    ctx->nside = n_side[0];
+    ctx->nbins = nu_bins;
+    if (opt) ctx->opt = *opt;
+    else art_options_default(&ctx->opt);
+    if (!(ctx->opt.tie_tol >= 0.0) || ctx->opt.tie_tol > 1e-3) ctx->opt.tie_tol = 1e-12;
+    if ((ctx->opt.precision != ART_FP32 && ctx->opt.precision != ART_FP64) || ctx->opt.averaging != ART_AVG_PAPER ||
+        (ctx->opt.field_form != ART_FIELDS_S && ctx->opt.field_form != ART_FIELDS_EPS) || ctx->opt.dir_split < 0) {
+        delete ctx;
+        return ART_E_INVALID;
+    }
+    ctx->prec = ctx->opt.precision;
+    ctx->rsz = ctx->prec == ART_FP64 ? 8 : 4;
+    ctx->ncell = total;
+    ctx->nd = 0;
+    for (int g = 0; g < n_grids; ++g) {
+        art_grid_host gh;
+        gh.g = grids[g];
+        gh.nside = n_side[g];
+        gh.nd = 12 * n_side[g] * n_side[g];
+        gh.ncell = (long long)grids[g].nx * grids[g].ny * grids[g].nz;
+        ctx->grids.push_back(gh);
+        ctx->nd += gh.nd;
+    }
+    ctx->G.assign(nu_bins, 0.0);
+    ctx->persistent = ctx->opt.persistent > 0 ? 1 : (ctx->opt.persistent < 0 ? 0 : (n_grids > 1 ? 1 : 0));
+
+    int pick = -1;
+    if (ctx->opt.variant > 0) {
+        pick = ctx->opt.variant - 1;
+        if (pick >= kNumVariants || kVariants[pick].prec != ctx->prec) pick = -2;
+    } else {
+        // measured on GB300: the 32 x 8 tile wins for grids below ~100^3
+        // cells (more CTAs per launch), the 32 x 16 tile above
+        if (ctx->prec == ART_FP32 && largest < 100LL * 100 * 100 && !ctx->opt.tile_b && !ctx->opt.tile_c &&
+            !ctx->opt.slab)
+            pick = 1;
+        for (int v = 0; v < kNumVariants && pick == -1; ++v) {
+            const KVariant &k = kVariants[v];
+            if (k.prec != ctx->prec) continue;
+            if ((ctx->opt.tile_b && k.tb != ctx->opt.tile_b) || (ctx->opt.tile_c && k.tc != ctx->opt.tile_c) ||
+                (ctx->opt.slab && k.blk != ctx->opt.slab))
+                continue;
+            pick = v;
+        }
+    }
+    if (pick < 0) {
+        delete ctx;
+        return ART_E_INVALID;
+    }
+    art_status st = setup_variant(ctx, pick);
+    if (st != ART_OK) {
+        art_destroy(ctx);
+        return st;
+    }
+    const size_t rs = ctx->rsz, n = (size_t)ctx->ncell;
+#define ALLOC(ptr, bytes)                                       \
+    do {                                                        \
+        if ((st = dev_alloc(ctx, &(ptr), (bytes))) != ART_OK) { \
+            art_destroy(ctx);                                   \
+            return st;                                          \
+        }                                                       \
+    } while (0)
+    ALLOC(ctx->d_field, 3 * (size_t)nu_bins * n * 2 * rs);
+    ALLOC(ctx->d_plane[0], (size_t)ctx->plane_elems * rs);
+    ALLOC(ctx->d_plane[1], (size_t)ctx->plane_elems * rs);
+    ALLOC(ctx->d_stage, 2 * (size_t)nu_bins * n * rs);
+    ALLOC(ctx->d_out, (2 * (size_t)nu_bins + 1) * n * rs);
+    ALLOC(ctx->d_flag, sizeof(int));
+#undef ALLOC
+    *out = ctx;
+    return ART_OK;
+}
+
+}  // namespace
+
+art_status art_internal_sweep(art_ctx *ctx, void *J, void *J_in, void *gamma, cudaStream_t st)
+{
+    return sweep_launches(ctx, J, J_in, gamma, st);
+}
+
 art_status art_internal_layout(art_ctx *ctx, const void *kd, const void *sd, cudaStream_t st)
 {
     const long long nc = ctx->ncell;
     const int nt = 256;
-    const unsigned lb = (unsigned)((nc + nt - 1) / nt);
     for (int b = 0; b < ctx->nbins; ++b) {
-        if (ctx->prec == ART_FP64) {
-            double2 *f = static_cast<double2 *>(ctx->d_field);
-            const double *k = static_cast<const double *>(kd) + (long long)b * nc;
-            const double *s = static_cast<const double *>(sd) + (long long)b * nc;
-            layout_kernel<double><<<lb, nt, 0, st>>>(k, s, f + (0LL * ctx->nbins + b) * nc, f + (1LL * ctx->nbins + b) * nc,
-                                                     f + (2LL * ctx->nbins + b) * nc, ctx->grid.nx, ctx->grid.ny, ctx->grid.nz);
-        } else {
-            float2 *f = static_cast<float2 *>(ctx->d_field);
-            const float *k = static_cast<const float *>(kd) + (long long)b * nc;
-            const float *s = static_cast<const float *>(sd) + (long long)b * nc;
-            layout_kernel<float><<<lb, nt, 0, st>>>(k, s, f + (0LL * ctx->nbins + b) * nc, f + (1LL * ctx->nbins + b) * nc,
-                                                    f + (2LL * ctx->nbins + b) * nc, ctx->grid.nx, ctx->grid.ny, ctx->grid.nz);
+        for (const art_grid_host &g : ctx->grids) {
+            const unsigned lb = (unsigned)((g.ncell + nt - 1) / nt);
+            const long long off = (long long)b * nc + g.cell_off;
+            if (ctx->prec == ART_FP64) {
+                double2 *f = static_cast<double2 *>(ctx->d_field);
+                layout_kernel<double><<<lb, nt, 0, st>>>(
+                    static_cast<const double *>(kd) + off, static_cast<const double *>(sd) + off,
+                    f + (0LL * ctx->nbins + b) * nc + g.cell_off, f + (1LL * ctx->nbins + b) * nc + g.cell_off,
+                    f + (2LL * ctx->nbins + b) * nc + g.cell_off, g.g.nx, g.g.ny, g.g.nz);
+            } else {
+                float2 *f = static_cast<float2 *>(ctx->d_field);
+                layout_kernel<float><<<lb, nt, 0, st>>>(
+                    static_cast<const float *>(kd) + off, static_cast<const float *>(sd) + off,
+                    f + (0LL * ctx->nbins + b) * nc + g.cell_off, f + (1LL * ctx->nbins + b) * nc + g.cell_off,
+                    f + (2LL * ctx->nbins + b) * nc + g.cell_off, g.g.nx, g.g.ny, g.g.nz);
+            }
+            CK(ctx, cudaGetLastError());
         }
-        CK(ctx, cudaGetLastError());
     }
     ctx->have_fields = true;
     return ART_OK;
@@ -278,144 +592,74 @@ art_status art_options_default(art_options *opt)
     return ART_OK;
 }
 
-art_status art_create(const art_grid *grid, int n_side, int nu_bins, const art_options *opt,
-                      art_ctx **out)
+art_status art_create(const art_grid *grid, int n_side, int nu_bins, const art_options *opt, art_ctx **out)
 {
-    if (!out) return ART_E_INVALID;
-    *out = nullptr;
-    if (!grid || grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || n_side < 1 || nu_bins < 1)
-        return ART_E_INVALID;
-    if ((long long)grid->nx * grid->ny * grid->nz > (1LL << 31) || n_side > 1024) return ART_E_INVALID;
-    art_ctx *ctx = new (std::nothrow) art_ctx();
-    if (!ctx) return ART_E_OOM;
-    ctx->grid = *grid;
-    ctx->nside = n_side;
-    ctx->nbins = nu_bins;
-    if (opt) ctx->opt = *opt;
-    else art_options_default(&ctx->opt);
-    if (!(ctx->opt.tie_tol >= 0.0) || ctx->opt.tie_tol > 1e-3) ctx->opt.tie_tol = 1e-12;
-    if (ctx->opt.precision != ART_FP32 && ctx->opt.precision != ART_FP64) {
-        delete ctx;
+    if (!grid) {
+        if (out) *out = nullptr;
         return ART_E_INVALID;
     }
-    if (ctx->opt.averaging != ART_AVG_PAPER ||
-        (ctx->opt.field_form != ART_FIELDS_S && ctx->opt.field_form != ART_FIELDS_EPS)) {
-        delete ctx;
-        return ART_E_INVALID;
-    }
-    ctx->prec = ctx->opt.precision;
-    ctx->rsz = ctx->prec == ART_FP64 ? 8 : 4;
-    ctx->ncell = (long long)grid->nx * grid->ny * grid->nz;
-    ctx->nd = 12 * n_side * n_side;
-    ctx->G.assign(nu_bins, 0.0);
+    return create_common(grid, &n_side, 1, nu_bins, opt, out);
+}
 
-    // kernel variant
-    {
-        int pick = -1;
-        if (ctx->opt.variant > 0) {
-            pick = ctx->opt.variant - 1;
-            if (pick >= kNumVariants || kVariants[pick].prec != ctx->prec) pick = -2;
-        } else {
-            // measured on GB300: the 32 x 8 tile wins below ~100^3 cells
-            // (more CTAs per launch), the 32 x 16 tile above
-            const int prefer = (ctx->prec == ART_FP32 && ctx->ncell < 100LL * 100 * 100 && !ctx->opt.tile_b &&
-                                !ctx->opt.tile_c && !ctx->opt.slab)
-                                   ? 1
-                                   : -1;
-            if (prefer >= 0) pick = prefer;
-            for (int v = 0; v < kNumVariants && pick == -1; ++v) {
-                const KVariant &k = kVariants[v];
-                if (k.prec != ctx->prec) continue;
-                if ((ctx->opt.tile_b && k.tb != ctx->opt.tile_b) || (ctx->opt.tile_c && k.tc != ctx->opt.tile_c) ||
-                    (ctx->opt.slab && k.blk != ctx->opt.slab))
-                    continue;
-                pick = v;
+art_status art_batch_create(const art_grid *grids, const int *n_side, int n_grids, int nu_bins,
+                            const art_options *opt, art_ctx **out)
+{
+    return create_common(grids, n_side, n_grids, nu_bins, opt, out);
+}
+
+art_status art_autotune(art_ctx *ctx, int reps, int *best_variant, void *stream)
+{
+    if (!ctx) return ART_E_INVALID;
+    if (!ctx->have_fields) return fail(ctx, ART_E_STATE, "art_autotune: call art_set_fields first");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (reps < 1) reps = 3;
+    char *jin = static_cast<char *>(ctx->d_out) + (size_t)ctx->ncell * ctx->nbins * ctx->rsz;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(ctx, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(ctx, ART_E_CUDA, "art_autotune: cudaEventCreate failed");
+    }
+    const bool keep_prof = ctx->profiling;
+    ctx->profiling = false;
+    int best = ctx->variant, best_pers = ctx->persistent;
+    float best_ms = 3.0e38f;
+    art_status s = ART_OK;
+    // launch forms tried: both unless the options fixed one
+    const int forms[2] = {1, 0};
+    const int nforms = ctx->opt.persistent == 0 ? 2 : 1;
+    for (int v = 0; v < kNumVariants && s == ART_OK; ++v) {
+        if (kVariants[v].prec != ctx->prec || kVariants[v].prepare() < 1) continue;
+        if ((s = setup_variant(ctx, v)) != ART_OK) break;
+        for (int f = 0; f < nforms && s == ART_OK; ++f) {
+            if (nforms == 2) ctx->persistent = forms[f];
+            if ((s = sweep_launches(ctx, nullptr, jin, nullptr, st)) != ART_OK) break;   // warm-up
+            if (cudaEventRecord(e0, st) != cudaSuccess) {
+                s = fail(ctx, ART_E_CUDA, "art_autotune: cudaEventRecord failed");
+                break;
+            }
+            for (int r = 0; r < reps && s == ART_OK; ++r) s = sweep_launches(ctx, nullptr, jin, nullptr, st);
+            if (s != ART_OK) break;
+            float ms = 0.f;
+            if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                s = fail(ctx, ART_E_CUDA, "art_autotune: timing failed");
+                break;
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = v;
+                best_pers = ctx->persistent;
             }
         }
-        if (pick < 0) {
-            delete ctx;
-            return ART_E_INVALID;
-        }
-        const KVariant &k = kVariants[pick];
-        ctx->variant = pick;
-        ctx->TB = k.tb;
-        ctx->TC = k.tc;
-        ctx->BLK = k.blk;
-        ctx->NT = k.nt;
-        ctx->KP = k.kp;
     }
-
-    std::vector<double> xyz;
-    healpix_directions(n_side, xyz);
-    // direction groups per class: enough CTAs to cover the GPU at least twice
-    {
-        int dev = 0, sms = 152;
-        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaGetLastError();
-        if (ctx->opt.dir_split > 0) {
-            ctx->split = ctx->opt.dir_split;
-        } else {
-            ctx->split = 1;
-            HostTables probe;
-            build_tables(ctx, xyz, probe);
-            const int base = (int)probe.work.size();
-            const int per_class = std::max(1, ctx->nd / std::max<int>(1, (int)probe.classes.size()));
-            while (base * ctx->split < 2 * sms && ctx->split * 2 <= per_class) ctx->split *= 2;
-        }
-    }
-    HostTables t;
-    build_tables(ctx, xyz, t);
-    ctx->n_classes = (int)t.classes.size();
-    ctx->n_part = (int)t.part_axis.size();
-    ctx->n_work = (int)t.work.size();
-    ctx->seg_count = t.seg_count;
-    ctx->plane_elems = t.plane_elems;
-    int maxNa = 0;
-    for (const ClassDev &c : t.classes) maxNa = std::max(maxNa, c.Na);
-    ctx->nblocks = (maxNa + ctx->BLK - 1) / ctx->BLK;
-
-    const size_t rs = ctx->rsz, n = (size_t)ctx->ncell;
-    art_status st;
-#define ALLOC(ptr, bytes)                                      \
-    do {                                                       \
-        if ((st = dev_alloc(ctx, &(ptr), (bytes))) != ART_OK) { \
-            art_ctx *c_ = ctx;                                 \
-            std::string m_ = c_->err;                          \
-            art_destroy(c_);                                   \
-            (void)m_;                                          \
-            return st;                                         \
-        }                                                      \
-    } while (0)
-    ALLOC(ctx->d_field, 3 * (size_t)nu_bins * n * 2 * rs);
-    ALLOC(ctx->d_plane[0], (size_t)ctx->plane_elems * rs);
-    ALLOC(ctx->d_plane[1], (size_t)ctx->plane_elems * rs);
-    ALLOC(ctx->d_jpart, (size_t)ctx->n_part * n * rs);
-    ALLOC(ctx->d_segs, t.geo.size() * (ctx->prec == ART_FP64 ? sizeof(SegEntry<double>) : sizeof(SegEntry<float>)));
-    ALLOC(ctx->d_dirs, t.dirs.size() * sizeof(DirDev));
-    ALLOC(ctx->d_classes, t.classes.size() * sizeof(ClassDev));
-    ALLOC(ctx->d_work, t.work.size() * sizeof(WorkItem));
-    ALLOC(ctx->d_part_axis, t.part_axis.size() * sizeof(int));
-    ALLOC(ctx->d_stage, 2 * (size_t)nu_bins * n * rs);
-    ALLOC(ctx->d_out, (2 * (size_t)nu_bins + 1) * n * rs);
-    ALLOC(ctx->d_flag, sizeof(int));
-#undef ALLOC
-    cudaError_t e = cudaSuccess;
-    if (ctx->prec == ART_FP64) {
-        auto s = pack_segs<double>(t.geo);
-        e = cudaMemcpy(ctx->d_segs, s.data(), s.size() * sizeof(s[0]), cudaMemcpyHostToDevice);
-    } else {
-        auto s = pack_segs<float>(t.geo);
-        e = cudaMemcpy(ctx->d_segs, s.data(), s.size() * sizeof(s[0]), cudaMemcpyHostToDevice);
-    }
-    if (e == cudaSuccess) e = cudaMemcpy(ctx->d_dirs, t.dirs.data(), t.dirs.size() * sizeof(DirDev), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(ctx->d_classes, t.classes.data(), t.classes.size() * sizeof(ClassDev), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(ctx->d_work, t.work.data(), t.work.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(ctx->d_part_axis, t.part_axis.data(), t.part_axis.size() * sizeof(int), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-        art_destroy(ctx);
-        return ART_E_CUDA;
-    }
-    *out = ctx;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->profiling = keep_prof;
+    ctx->persistent = best_pers;
+    if (s != ART_OK) return s;
+    if ((s = setup_variant(ctx, best)) != ART_OK) return s;
+    if (best_variant) *best_variant = best + 1;
     return ART_OK;
 }
 
@@ -479,10 +723,14 @@ art_status art_destroy(art_ctx *ctx)
 {
     if (!ctx) return ART_OK;
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
-    void *ptrs[] = {ctx->d_field, ctx->d_plane[0], ctx->d_plane[1], ctx->d_jpart, ctx->d_segs,
-                    ctx->d_dirs, ctx->d_classes, ctx->d_work, ctx->d_part_axis, ctx->d_stage,
-                    ctx->d_out, ctx->d_flag, ctx->it.nH, ctx->it.y, ctx->it.y0, ctx->it.gpt, ctx->it.kap,
-                    ctx->it.eps, ctx->it.jin, ctx->it.resid, ctx->it.src};
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
+    for (cudaEvent_t e : ctx->gev)
+        if (e) cudaEventDestroy(e);
+    void *ptrs[] = {ctx->d_field, ctx->d_plane[0], ctx->d_plane[1], ctx->d_jpart, ctx->d_segs, ctx->d_dirs,
+                    ctx->d_classes, ctx->d_work, ctx->d_counter, ctx->d_gridinfo, ctx->d_stage, ctx->d_out,
+                    ctx->d_flag, ctx->it.nH, ctx->it.y, ctx->it.y0, ctx->it.gpt, ctx->it.kap, ctx->it.eps,
+                    ctx->it.jin, ctx->it.resid, ctx->it.src};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ctx;
@@ -498,7 +746,7 @@ art_status art_get_stats(const art_ctx *ctx, art_sweep_stats *s)
     s->n_dirs = ctx->nd;
     s->n_classes = ctx->n_classes;
     s->launches = ctx->nblocks + 1;
-    s->ctas_per_launch = ctx->n_work;
+    s->ctas_per_launch = ctx->persistent ? ctx->n_ctas : ctx->n_work;
     s->tile_b = ctx->TB;
     s->tile_c = ctx->TC;
     s->slab = ctx->BLK;
@@ -506,6 +754,9 @@ art_status art_get_stats(const art_ctx *ctx, art_sweep_stats *s)
     s->device_bytes = ctx->dev_bytes;
     s->variant = ctx->variant + 1;
     s->group = 2 * ctx->KP;
+    s->n_grids = (int32_t)ctx->grids.size();
+    s->work_items = ctx->n_work;
+    s->persistent = ctx->persistent;
     return ART_OK;
 }
 
@@ -528,9 +779,11 @@ art_status art_set_fields(art_ctx *ctx, const void *kappa, const void *src, int 
     const int nt = 256;
     const unsigned nb = (unsigned)std::min<long long>((n + nt - 1) / nt, 4096);
     if (ctx->prec == ART_FP64)
-        validate_kernel<double><<<nb, nt, 0, st>>>(static_cast<const double *>(kd), static_cast<const double *>(sd), n, ctx->d_flag);
+        validate_kernel<double><<<nb, nt, 0, st>>>(static_cast<const double *>(kd), static_cast<const double *>(sd), n,
+                                                   ctx->d_flag);
     else
-        validate_kernel<float><<<nb, nt, 0, st>>>(static_cast<const float *>(kd), static_cast<const float *>(sd), n, ctx->d_flag);
+        validate_kernel<float><<<nb, nt, 0, st>>>(static_cast<const float *>(kd), static_cast<const float *>(sd), n,
+                                                  ctx->d_flag);
     CK(ctx, cudaGetLastError());
     int flag = 0;
     CK(ctx, cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -544,9 +797,12 @@ art_status art_set_band(art_ctx *ctx, const double *G)
 {
     if (!ctx) return ART_E_INVALID;
     if (!G) return fail(ctx, ART_E_INVALID, "art_set_band: null pointer");
-    for (int b = 0; b < ctx->nbins; ++b) {
+    for (int b = 0; b < ctx->nbins; ++b)
         if (!std::isfinite(G[b])) return fail(ctx, ART_E_INVALID, "art_set_band: non-finite band integral");
-        ctx->G[b] = G[b];
+    for (int b = 0; b < ctx->nbins; ++b) ctx->G[b] = G[b];
+    if (ctx->gexec) {   // the captured reduction holds the old coefficients
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
     }
     return ART_OK;
 }
@@ -565,11 +821,8 @@ art_status art_sweep(art_ctx *ctx, void *J, void *J_in, void *gamma, int on_devi
         dJin = J_in ? o + nb * rs : nullptr;
         dG = gamma ? o + 2 * nb * rs : nullptr;
     }
-    art_status s;
-    if (ctx->prec == ART_FP64)
-        s = do_sweep<double>(ctx, static_cast<double *>(dJ), static_cast<double *>(dJin), static_cast<double *>(dG), st);
-    else
-        s = do_sweep<float>(ctx, static_cast<float *>(dJ), static_cast<float *>(dJin), static_cast<float *>(dG), st);
+    const art_status s = (ctx->opt.graph && !ctx->profiling) ? sweep_graph(ctx, dJ, dJin, dG, st)
+                                                              : sweep_launches(ctx, dJ, dJin, dG, st);
     if (s != ART_OK) return s;
     if (!on_device) {
         if (J) CK(ctx, cudaMemcpyAsync(J, dJ, nb * rs, cudaMemcpyDeviceToHost, st));

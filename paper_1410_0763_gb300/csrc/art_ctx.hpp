@@ -19,9 +19,31 @@ struct art_iter_bufs {
     double *src = nullptr;                                // [nsrc][4]: x, y, z, Q
 };
 
+// One grid of a context (a context holds one grid, or a batch of them).
+struct art_grid_host {
+    art_grid g{};
+    int nside = 0, nd = 0;
+    long long ncell = 0;
+    long long cell_off = 0;    // first cell in the concatenated [z][y][x] arrays
+    long long jpart_off = 0;   // first element of its J partials
+    int n_part = 0;            // J partials (classes x direction groups)
+    int nblocks = 0;           // slab blocks of its longest axis
+    long long seg_count = 0;   // segments per sweep and bin
+};
+
 struct art_ctx {
-    art_grid grid{};
+    art_grid grid{};           // first grid (the only one outside batches)
     int nside = 0, nbins = 0;
+    std::vector<art_grid_host> grids;
+    int persistent = 0;        // sweep launches take work items from a queue
+    int n_ctas = 0;            // CTAs of a persistent launch
+    int *d_counter = nullptr;  // queue heads, one per slab block
+    void *d_gridinfo = nullptr;
+    // CUDA graph of one sweep (device outputs), replayed while the outputs match
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t gev[2] = {nullptr, nullptr};
+    void *g_key[3] = {nullptr, nullptr, nullptr};
     art_options opt{};
     std::string err;
     int prec = ART_FP32;
@@ -43,7 +65,8 @@ struct art_ctx {
     art::DirDev *d_dirs = nullptr;
     art::ClassDev *d_classes = nullptr;
     art::WorkItem *d_work = nullptr;
-    int *d_part_axis = nullptr;
+    size_t jpart_bytes = 0, segs_bytes = 0, dirs_bytes = 0, classes_bytes = 0, work_bytes = 0,
+           counter_bytes = 0, gridinfo_bytes = 0;
     void *d_stage = nullptr;   // [2][nbins][ncell] real: host-input staging
     void *d_out = nullptr;     // [2 nbins + 1][ncell] real: host-output staging
     int *d_flag = nullptr;

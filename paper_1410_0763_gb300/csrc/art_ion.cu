@@ -264,6 +264,7 @@ art_status art_point_sources(art_ctx *ctx, const float *kappa, const double *sig
                              const double *Qb, int n_src, float *gamma, void *stream)
 {
     if (!ctx) return ART_E_INVALID;
+    if (ctx->grids.size() != 1) return art_fail(ctx, ART_E_INVALID, "art_point_sources: single-grid contexts only");
     if (!kappa || !sigma || !gamma || (n_src > 0 && !src) || n_src < 0)
         return art_fail(ctx, ART_E_INVALID, "art_point_sources: null argument");
     const int nbins = ctx->nbins;
@@ -300,6 +301,7 @@ art_status art_iterate_ionization(art_ctx *ctx, const art_chem *ch, const double
                                   art_iter_report *rep, void *stream)
 {
     if (!ctx) return ART_E_INVALID;
+    if (ctx->grids.size() != 1) return art_fail(ctx, ART_E_INVALID, "art_iterate_ionization: single-grid contexts only");
     if (!ch || !nH || !y || (n_src > 0 && !src) || n_src < 0 || max_iter < 1 || !(tol > 0.0))
         return art_fail(ctx, ART_E_INVALID, "art_iterate_ionization: bad argument");
     if (ctx->prec != ART_FP32 || ctx->nbins != 1 || ctx->opt.field_form != ART_FIELDS_EPS)

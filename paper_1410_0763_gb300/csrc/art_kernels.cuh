@@ -51,7 +51,18 @@ struct ClassDev {
     int a, sa, sb, sc;
     int Na, Nb, Nc;
     int dir_begin, dir_end;   // into the class-sorted direction table
-    int part0;                // first J partial of the class
+    int part0;                // first J partial of the class within its grid
+    int nx, ny, nz;           // the grid of this class (natural layout)
+    long long cell_off;       // first cell of the grid in the concatenated cell arrays
+    long long jpart_off;      // first element of the class's J partials
+    long long ncell;          // cells of the grid
+};
+
+// One grid of a batch, for the partial reduction.
+template <typename real> struct GridDev {
+    long long cell_off, ncell, jpart_off;
+    int n_part;
+    real inv_nd;
 };
 
 struct DirDev {
@@ -72,13 +83,13 @@ template <typename real> struct SweepArgs {
     const typename Vec2<real>::type *field0, *field1, *field2;   // (kappa, src), axis-a layouts, one bin
     const real *plane_in;
     real *plane_out;
-    real *jpart;                 // [n_part][ncell] J partials, natural [z][y][x] layout
+    real *jpart;                 // J partials, natural [z][y][x] layout per grid
     const SegEntry<real> *segs;
     const DirDev *dirs;
     const ClassDev *classes;
     const WorkItem *work;
-    long long ncell;
-    int nx, ny, nz;
+    int n_work;
+    int *counter;                // persistent mode: work-queue head (0 before the launch); else null
     int split;
     int kblock;
     int field_form;
@@ -273,8 +284,8 @@ template <int TB, int TC, int BLK, int NT, int KP> struct SweepShape {
     }
 };
 
-template <typename real, int TB, int TC, int BLK, int NT, int KP, int MINB>
-__global__ void __launch_bounds__(NT, MINB) sweep_block_kernel(const SweepArgs<real> p)
+template <typename real, int TB, int TC, int BLK, int NT, int KP>
+__device__ __forceinline__ void sweep_item(const SweepArgs<real> &p, int item, unsigned char *smem_raw)
 {
     using v2 = typename Vec2<real>::type;
     using P = PairOps<real>;
@@ -285,20 +296,19 @@ __global__ void __launch_bounds__(NT, MINB) sweep_block_kernel(const SweepArgs<r
     static_assert((TB * TC) % NT == 0, "owned columns must split evenly over threads");
     static_assert(WB * WC < 4096, "exchange offsets are packed in 12 bits");
 
-    extern __shared__ __align__(32) unsigned char smem_raw[];
     v2 *ks = reinterpret_cast<v2 *>(smem_raw);
     pr *xbuf = reinterpret_cast<pr *>(smem_raw + Sh::template off_x<real>());   // [2][KP][NS] pairs
     SegSm<real> *tsm = reinterpret_cast<SegSm<real> *>(smem_raw + Sh::template off_t<real>());
     DirSm<real> *dsm = reinterpret_cast<DirSm<real> *>(smem_raw + Sh::template off_d<real>());
     int4 *gsm = reinterpret_cast<int4 *>(smem_raw + Sh::template off_g<real>());
 
-    const WorkItem w = p.work[blockIdx.x];
+    const WorkItem w = p.work[item];
     const ClassDev C = p.classes[w.cls];
     const int m0 = p.kblock * BLK;
     if (m0 >= C.Na) return;
     const int Bp = min(BLK, C.Na - m0);
     const int Rb = w.pb - HB, Rc = w.pc - HB;   // origin of the smem region
-    const v2 *__restrict__ F = C.a == 0 ? p.field0 : (C.a == 1 ? p.field1 : p.field2);
+    const v2 *__restrict__ F = (C.a == 0 ? p.field0 : (C.a == 1 ? p.field1 : p.field2)) + C.cell_off;
     const int tid = threadIdx.x;
     const int form = p.field_form;
 
@@ -569,7 +579,10 @@ __global__ void __launch_bounds__(NT, MINB) sweep_block_kernel(const SweepArgs<r
         }
     }
 
-    real *J = p.jpart + (long long)(C.part0 + w.group) * p.ncell;
+    // grid fields of the class read here rather than kept live through the march
+    const ClassDev *Cg = p.classes + w.cls;
+    const int gnx = Cg->nx, gny = Cg->ny;
+    real *J = p.jpart + Cg->jpart_off + (long long)w.group * Cg->ncell;
 #pragma unroll
     for (int s = 0; s < OPT; ++s) {
         if (!o_ok[s]) continue;
@@ -583,9 +596,36 @@ __global__ void __launch_bounds__(NT, MINB) sweep_block_kernel(const SweepArgs<r
                 const int x = C.a == 0 ? pa : pb;
                 const int y = C.a == 1 ? pa : (C.a == 0 ? pb : pc);
                 const int z = C.a == 2 ? pa : pc;
-                J[((long long)z * p.ny + y) * p.nx + x] = js[s][i] - jc[s][i];
+                J[((long long)z * gny + y) * gnx + x] = js[s][i] - jc[s][i];
             }
         }
+    }
+    __syncthreads();   // shared memory is reused by the CTA's next work item
+}
+
+// One CTA per work item.
+template <typename real, int TB, int TC, int BLK, int NT, int KP, int MINB>
+__global__ void __launch_bounds__(NT, MINB) sweep_block_kernel(const SweepArgs<real> p)
+{
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    if ((int)blockIdx.x < p.n_work) sweep_item<real, TB, TC, BLK, NT, KP>(p, blockIdx.x, smem_raw);
+}
+
+// Persistent form: a fixed grid of CTAs taking work items from a queue
+// (p.counter, zero before the launch).  Items write disjoint outputs, so the
+// order in which CTAs take them changes no result.
+template <typename real, int TB, int TC, int BLK, int NT, int KP, int MINB>
+__global__ void __launch_bounds__(NT, MINB) sweep_queue_kernel(const SweepArgs<real> p)
+{
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(p.counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= p.n_work) break;
+        sweep_item<real, TB, TC, BLK, NT, KP>(p, item, smem_raw);
     }
 }
 
@@ -593,25 +633,33 @@ __global__ void __launch_bounds__(NT, MINB) sweep_block_kernel(const SweepArgs<r
 // Sum the class partials (fixed order, Kahan) into J^in, J and Gamma.
 // ---------------------------------------------------------------------------
 template <typename real> struct ReduceArgs {
-    const real *jpart;                             // [n_part][ncell], natural layout
-    const typename Vec2<real>::type *field_nat;    // (kappa, src) in [z][y][x]
-    int n_part;
-    long long ncell;
-    real inv_nd;
+    const real *jpart;
+    const typename Vec2<real>::type *field_nat;    // (kappa, src) in [z][y][x], concatenated grids, one bin
+    const GridDev<real> *grids;
+    int n_grids;
+    long long total;                               // cells of all grids
     real gamma_coef;     // 4 pi G_b
     int gamma_accum;     // add to gamma instead of overwriting
     int field_form;
-    real *Jin, *J, *gamma;
+    real *Jin, *J, *gamma;   // concatenated grids
 };
 
 template <typename real> __global__ void reduce_kernel(const ReduceArgs<real> p)
 {
     using v2 = typename Vec2<real>::type;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.ncell) return;
+    if (i >= p.total) return;
+    int lo = 0, hi = p.n_grids - 1;   // the grid holding cell i
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.grids[mid].cell_off <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    const GridDev<real> G = p.grids[lo];
+    const long long l = i - G.cell_off;
     real s = real(0), c = real(0);
-    for (int k = 0; k < p.n_part; ++k) kahan_add(s, c, p.jpart[(long long)k * p.ncell + i]);
-    const real jin = (s - c) * p.inv_nd;
+    for (int k = 0; k < G.n_part; ++k) kahan_add(s, c, p.jpart[G.jpart_off + (long long)k * G.ncell + l]);
+    const real jin = (s - c) * G.inv_nd;
     if (p.Jin) p.Jin[i] = jin;
     if (p.J) {
         const v2 f = p.field_nat[i];

@@ -41,6 +41,7 @@ static SegEntry<float> g_segs[kMaxSlabs];
 static DirDev g_dirs[kMaxDirs];
 static ClassDev g_classes[24];
 static WorkItem g_work[kMaxWork];
+static GridDev<float> g_grid;
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -191,6 +192,12 @@ extern "C" art_status art_sweep_noalloc(const art_grid *grid, int n_side, const 
         C.dir_begin = ndir;
         C.dir_end = ndir + cnt;
         C.part0 = ncls;
+        C.nx = dims[0];
+        C.ny = dims[1];
+        C.nz = dims[2];
+        C.cell_off = 0;
+        C.jpart_off = (long long)ncls * ncell;
+        C.ncell = ncell;
         for (int i = 0; i < cnt; ++i) {
             DirDev D;
             D.seg_off = nslab;
@@ -217,7 +224,8 @@ extern "C" art_status art_sweep_noalloc(const art_grid *grid, int n_side, const 
     const size_t o_dirs = align256(o_segs + size_t(nslab) * sizeof(SegEntry<float>));
     const size_t o_cls = align256(o_dirs + size_t(ndir) * sizeof(DirDev));
     const size_t o_work = align256(o_cls + size_t(ncls) * sizeof(ClassDev));
-    const size_t need = align256(o_work + size_t(nwork) * sizeof(WorkItem));
+    const size_t o_grid = align256(o_work + size_t(nwork) * sizeof(WorkItem));
+    const size_t need = align256(o_grid + sizeof(GridDev<float>));
     if (need > kScratchBytes)
         return reject(errbuf, errlen, ART_E_INVALID,
                       "art_sweep_noalloc: this grid needs more than the 12 MiB scratch array; use art_create/art_sweep");
@@ -240,6 +248,9 @@ extern "C" art_status art_sweep_noalloc(const art_grid *grid, int n_side, const 
               "copy of the class table failed");
     ART_NA_CK(cudaMemcpyAsync(base + o_work, g_work, size_t(nwork) * sizeof(WorkItem), cudaMemcpyHostToDevice, st),
               "copy of the work list failed");
+    g_grid = GridDev<float>{0, ncell, 0, ncls, float(1.0 / nd)};
+    ART_NA_CK(cudaMemcpyAsync(base + o_grid, &g_grid, sizeof(g_grid), cudaMemcpyHostToDevice, st),
+              "copy of the grid record failed");
     // the host tables are reused by the next call: wait for the copies
     ART_NA_CK(cudaStreamSynchronize(st), "stream synchronize failed");
 
@@ -257,10 +268,8 @@ extern "C" art_status art_sweep_noalloc(const art_grid *grid, int n_side, const 
     a.dirs = reinterpret_cast<const DirDev *>(base + o_dirs);
     a.classes = reinterpret_cast<const ClassDev *>(base + o_cls);
     a.work = reinterpret_cast<const WorkItem *>(base + o_work);
-    a.ncell = ncell;
-    a.nx = dims[0];
-    a.ny = dims[1];
-    a.nz = dims[2];
+    a.n_work = nwork;
+    a.counter = nullptr;
     a.split = 1;
     a.field_form = ART_FIELDS_S;
     int maxNa = 0;
@@ -280,9 +289,9 @@ extern "C" art_status art_sweep_noalloc(const art_grid *grid, int n_side, const 
     ReduceArgs<float> r;
     r.jpart = jpart;
     r.field_nat = fld + 2 * ncell;
-    r.n_part = ncls;
-    r.ncell = ncell;
-    r.inv_nd = float(1.0 / nd);
+    r.grids = reinterpret_cast<const GridDev<float> *>(base + o_grid);
+    r.n_grids = 1;
+    r.total = ncell;
     r.gamma_coef = 0.0f;
     r.gamma_accum = 0;
     r.field_form = ART_FIELDS_S;

@@ -69,7 +69,7 @@ def gaussian_random_field(n: int, slope: float, rng: np.random.Generator) -> np.
     amp = np.zeros_like(kk)
     nz = kk > 0
     amp[nz] = kk[nz] ** (0.5 * slope)
-    g = np.fft.irfftn(wk * amp, s=(n, n, n))
+    g = np.fft.irfftn(wk * amp, s=(n, n, n), axes=(0, 1, 2))
     g -= g.mean()
     g /= g.std()
     return g

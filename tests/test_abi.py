@@ -54,6 +54,19 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib, dims, nside,
     assert st == art.ART_E_INVALID and not h.value
 
 
+@pytest.mark.parametrize("dims,nsides,n", [([(4, 4, 4)], [1], 0), ([(4, 4, 4), (0, 4, 4)], [1, 1], 2),
+                                             ([(4, 4, 4), (5, 5, 5)], [1, 0], 2),
+                                             ([(4, 4, 4)], [1], 5000)])
+def test_batch_create_rejects_bad_arguments_without_touching_the_gpu(lib, dims, nsides, n):
+    grids = (art.ArtGrid * max(1, len(dims)))(*[art.ArtGrid(nx, ny, nz, 1.0) for (nz, ny, nx) in dims])
+    ns = (ctypes.c_int * len(nsides))(*nsides)
+    h = ctypes.c_void_p()
+    st = lib.art_batch_create(grids, ns, n, 1, None, ctypes.byref(h))
+    assert st == art.ART_E_INVALID and not h.value
+    assert lib.art_batch_create(None, ns, 1, 1, None, ctypes.byref(h)) == art.ART_E_INVALID
+    assert lib.art_autotune(None, 1, None, None) == art.ART_E_INVALID
+
+
 def test_null_context_calls_fail_cleanly(lib):
     assert lib.art_sweep(None, None, None, None, 1, None) == art.ART_E_INVALID
     assert lib.art_set_fields(None, None, None, 0, None) == art.ART_E_INVALID
