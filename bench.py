@@ -50,6 +50,23 @@ L2_FLUSH_BYTES = 256 << 20      # > 129 MB L2
 # MUFU ex2 results per clock per SM measured on GB300 (profiles/peaks_gb300.md);
 # bench.py re-measures it on the box (art_measure_pipes) and uses the live value
 EX2_PER_CLK_SM = 32
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def recorded_traffic(workload: str):
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+    taken on this workload with the kernel source as it is now; else None."""
+    import hashlib
+    path = os.path.join(HERE, "profiles", f"traffic_sweep_block_{workload}.txt")
+    src = os.path.join(HERE, "paper_1410_0763_gb300", "csrc", "art_kernels.cuh")
+    try:
+        rec = dict(line.split(": ", 1) for line in open(path).read().splitlines() if ": " in line)
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    if rec.get("kernel_source_sha256") != digest:
+        return None
+    return int(rec["dram_bytes_per_launch"])
 
 
 def parse():
@@ -385,7 +402,8 @@ def run_ours(args, d: Dist):
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"weak x{d.world} (independent grid per GPU)"},
         "roofline": {"bound": "alu", "achieved": achieved_gseg, "peak": peak_gseg, "unit": "Gseg/s",
-                     "frac": achieved_gseg / peak_gseg, "traffic": None,
+                     "frac": achieved_gseg / peak_gseg, "traffic": recorded_traffic(args.workload),
+                     "traffic_unit": "DRAM bytes per sweep launch (ncu, cold L2)",
                      "kernel": "sweep_block_kernel", "kernel_share_of_step": sweep_share,
                      "peak_basis": f"MUFU ex2 issue rate: 1 exp per segment, {ex2}/clk/SM (measured) x "
                                    f"{n_sm} SMs x {sm_mhz:.0f} MHz (median SM clock under load)",
