@@ -1,0 +1,150 @@
+/*
+ * art_net.h -- C ABI of the 3D-convolution surrogate of libart: a small
+ * network that predicts the diffuse mean intensity J^in of the sweep from
+ * the solver's state, trained on the GPU on plain-sweep results, and the
+ * RT / ionization-balance iteration it warm-starts.
+ *
+ * The paper iterates plain sweeps to convergence (App. D); the surrogate is
+ * an addition of this library and has no counterpart in the paper.  What it
+ * computes:
+ *   - inputs per cell (4 channels): 0.25 ln kappa, 0.1 ln(eps/eps_ref),
+ *     x = 1 - y, 0.1 ln(J_c/eps_ref); each logarithm clamped at ln(1e-30)
+ *     below its reference; eps_ref = max eps; kappa and eps the sweep's
+ *     absorption and emissivity per cell width (ART_FIELDS_EPS form) from the
+ *     neutral fraction y; J_c the J^in of a sweep on the mesh coarsened by a
+ *     factor f (block means times f), prolonged by injection;
+ *   - network: four 3x3x3 convolutions with zero padding and per-layer
+ *     dilations, channels 4 -> 32 -> 32 -> 32 -> 1, ReLU after the first
+ *     three; BF16 weights and activations, FP32 accumulation (tensor cores);
+ *   - prediction J^in = J_c exp(o); training target t = ln(J^in/J_c) on the
+ *     plain sweep's J^in (logarithms clamped at ln eps_ref - 69); loss
+ *     mean((o - t)^2); optimizer Adam with bias-corrected moments and FP32
+ *     master weights.
+ * Parameters (FP32, "params layout"): for each layer l = 0..3, W_l as
+ * [27][c_out][c_in] (tap t = 9 (dz+1) + 3 (dy+1) + (dx+1), offsets
+ * d_l * (dx, dy, dz) from the output cell; x fastest in cell indices),
+ * then b_l [c_out]; c_in/c_out = 4/32, 32/32, 32/32, 32/1; ART_NET_PARAMS
+ * floats in total.
+ * Grids passed to the network need nx * ny * nz a multiple of 128, with nx a
+ * divisor of 128 (and 128/nx dividing ny) or a multiple of 128.
+ * Conventions (ownership, streams, status codes) as in art.h.
+ */
+#ifndef ART_NET_H
+#define ART_NET_H
+
+#include "art.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ART_NET_PARAMS 59713
+
+typedef struct art_net art_net;
+
+typedef struct {
+    int dilation[4];      /* per layer; default {1, 2, 4, 8} */
+    uint64_t seed;        /* He-normal initialisation (last layer x 0.1), default 1 */
+    double lr, beta1, beta2, adam_eps;   /* Adam; default 1e-3, 0.9, 0.999, 1e-8 */
+} art_net_options;
+
+/* Defaults as stated above.  Never fails for a non-NULL pointer. */
+art_status art_net_options_default(art_net_options *opt);
+
+/* Create a network with freshly initialised weights (device memory for the
+ * weights and optimizer state; activation workspace grows with the grids it
+ * sees).  Errors: ART_E_INVALID (dilations outside 1..16), ART_E_OOM,
+ * ART_E_CUDA. */
+art_status art_net_create(const art_net_options *opt, art_net **out);
+
+/* Release the network.  NULL is accepted. */
+art_status art_net_destroy(art_net *net);
+
+/* Text of the last error ("" if none). */
+const char *art_net_last_error(const art_net *net);
+
+/* Copy the FP32 master parameters to / from a host array of ART_NET_PARAMS
+ * floats (params layout).  Setting resets the Adam moments and step count.
+ * Synchronous.  Errors: ART_E_INVALID, ART_E_CUDA. */
+art_status art_net_get_params(art_net *net, float *host);
+art_status art_net_set_params(art_net *net, const float *host);
+
+/*
+ * Forward pass: X device [4][nz][ny][nx] floats (the input channels), o
+ * device [nz][ny][nx] floats.  Stream-ordered on `stream`.  Errors:
+ * ART_E_INVALID (grid shape, NULL), ART_E_OOM, ART_E_CUDA.
+ */
+art_status art_net_forward(art_net *net, int nx, int ny, int nz, const float *X, float *o, void *stream);
+
+/*
+ * Forward and backward pass on one sample (X as above, t device [nz][ny][nx]
+ * targets): *loss (host) receives mean((o - t)^2) and grads (host, may be
+ * NULL) the gradient of the loss in every parameter (params layout).
+ * Synchronizes `stream`.  Errors as art_net_forward.
+ */
+art_status art_net_gradients(art_net *net, int nx, int ny, int nz, const float *X, const float *t, double *loss,
+                             float *grads, void *stream);
+
+/*
+ * One Adam step on one sample: forward, backward, update of the master
+ * weights and of their BF16 copies.  *loss (host, may be NULL) receives the
+ * loss before the step; reading it synchronizes `stream`.  Errors as
+ * art_net_forward.
+ */
+art_status art_net_train_step(art_net *net, int nx, int ny, int nz, const float *X, const float *t, double *loss,
+                              void *stream);
+
+/*
+ * Training sample of the solver state y (device [z][y][x] doubles) on the
+ * context's grid: kappa = y nH sigma0 dx and eps as in art_iterate_ionization,
+ * a plain sweep for J^in and a coarse sweep (factor coarse_factor, N_side
+ * coarse_nside) for J_c.  Outputs (device, any may be NULL): X [4][V] inputs,
+ * t [V] target, jin [V] the sweep's J^in, jc [V] the prolonged coarse J^in.
+ * The context must satisfy art_iterate_ionization's requirements, with grid
+ * dimensions divisible by coarse_factor.  Stream-ordered.  Errors:
+ * ART_E_INVALID, ART_E_OOM, ART_E_CUDA.
+ */
+art_status art_surrogate_sample(art_ctx *ctx, const art_chem *chem, const double *nH, const double *y,
+                                int coarse_factor, int coarse_nside, float *X, float *t, float *jin, float *jc,
+                                void *stream);
+
+typedef struct {
+    int coarse_factor;     /* mesh coarsening of the coarse sweep, default 4 */
+    int coarse_nside;      /* N_side of the coarse sweep, default 4 */
+    int use_net;           /* 1 (default): J^in = J_c exp(net); 0: J^in = J_c (coarse sweep alone) */
+    int phase1_max_iter;   /* surrogate iterations at most, default 40 */
+    double phase1_tol;     /* surrogate phase ends below this residual, default 1e-4 */
+    double judge_tol;      /* fall back when sum|J_s - J|/sum J exceeds this, default 0.3 */
+} art_warm_options;
+
+typedef struct {
+    art_iter_report total;        /* all iterations, as art_iterate_ionization */
+    int32_t surrogate_iterations; /* iterations that took J^in from the surrogate */
+    int32_t plain_sweeps;         /* full sweeps run (judge included) */
+    int32_t fell_back;            /* 1 if the judge restarted from the initial state */
+    double judge_error;           /* sum|J_s - J| / sum J at the end of the surrogate phase */
+} art_warm_report;
+
+/* Fill `opt` with the defaults above. */
+art_status art_warm_options_default(art_warm_options *opt);
+
+/*
+ * The iteration of art_iterate_ionization (same arguments, same fixed point
+ * and stopping rule), warm-started: while the residual is above phase1_tol
+ * (and for at most phase1_max_iter iterations) J^in comes from the surrogate
+ * (coarse sweep plus network) instead of the full sweep; then one full sweep
+ * judges the surrogate on the current state; if its error exceeds judge_tol
+ * the state is reset to the initial y (fell_back = 1); plain iterations then
+ * run to tol.  net may be NULL only with use_net = 0.  Errors as
+ * art_iterate_ionization.
+ */
+art_status art_iterate_ionization_warm(art_ctx *ctx, art_net *net, const art_chem *chem, const double *nH,
+                                       const art_source *src, int n_src, double tol, int max_iter,
+                                       const art_warm_options *wopt, double *y, double *resid_hist,
+                                       art_warm_report *rep, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ART_NET_H */

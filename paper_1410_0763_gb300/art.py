@@ -61,6 +61,25 @@ class ArtProfile(C.Structure):
                 ("reduce_launches", C.c_int64)]
 
 
+class ArtNetOptions(C.Structure):
+    _fields_ = [("dilation", C.c_int * 4), ("seed", C.c_uint64), ("lr", C.c_double), ("beta1", C.c_double),
+                ("beta2", C.c_double), ("adam_eps", C.c_double)]
+
+
+class ArtWarmOptions(C.Structure):
+    _fields_ = [("coarse_factor", C.c_int), ("coarse_nside", C.c_int), ("use_net", C.c_int),
+                ("phase1_max_iter", C.c_int), ("phase1_tol", C.c_double), ("judge_tol", C.c_double)]
+
+
+class ArtWarmReport(C.Structure):
+    _fields_ = [("total", ArtIterReport), ("surrogate_iterations", C.c_int32), ("plain_sweeps", C.c_int32),
+                ("fell_back", C.c_int32), ("judge_error", C.c_double)]
+
+
+ART_NET_PARAMS = 59713
+NET_LAYERS = [(4, 32), (32, 32), (32, 32), (32, 1)]   # (c_in, c_out)
+
+
 class ArtError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{_STATUS.get(status, status)}: {msg}")
@@ -108,6 +127,26 @@ def load() -> C.CDLL:
         lib.art_sweep_noalloc.argtypes = [C.POINTER(ArtGrid), C.c_int, P, P, P, P, C.c_char_p, C.c_size_t]
         lib.art_profile_enable.argtypes = [P, C.c_int]
         lib.art_profile_read.argtypes = [P, C.POINTER(ArtProfile), C.c_int]
+        lib.art_net_options_default.argtypes = [C.POINTER(ArtNetOptions)]
+        lib.art_net_create.argtypes = [C.POINTER(ArtNetOptions), C.POINTER(P)]
+        lib.art_net_destroy.argtypes = [P]
+        lib.art_net_last_error.argtypes = [P]
+        lib.art_net_last_error.restype = C.c_char_p
+        lib.art_net_get_params.argtypes = [P, P]
+        lib.art_net_set_params.argtypes = [P, P]
+        lib.art_net_forward.argtypes = [P, C.c_int, C.c_int, C.c_int, P, P, P]
+        lib.art_net_gradients.argtypes = [P, C.c_int, C.c_int, C.c_int, P, P, C.POINTER(C.c_double), P, P]
+        lib.art_net_train_step.argtypes = [P, C.c_int, C.c_int, C.c_int, P, P, C.POINTER(C.c_double), P]
+        lib.art_surrogate_sample.argtypes = [P, C.POINTER(ArtChem), P, P, C.c_int, C.c_int, P, P, P, P, P]
+        lib.art_warm_options_default.argtypes = [C.POINTER(ArtWarmOptions)]
+        lib.art_iterate_ionization_warm.argtypes = [P, P, C.POINTER(ArtChem), P, C.POINTER(ArtSource), C.c_int,
+                                                    C.c_double, C.c_int, C.POINTER(ArtWarmOptions), P,
+                                                    C.POINTER(C.c_double), C.POINTER(ArtWarmReport), P]
+        for f in ("art_net_options_default", "art_net_create", "art_net_destroy", "art_net_get_params",
+                  "art_net_set_params", "art_net_forward", "art_net_gradients", "art_net_train_step",
+                  "art_surrogate_sample", "art_warm_options_default", "art_iterate_ionization_warm",
+                  "art_batch_create", "art_autotune"):
+            getattr(lib, f).restype = C.c_int
         for f in ("art_point_sources", "art_iterate_ionization", "art_sweep_noalloc", "art_measure_pipes", "art_band_integral", "art_profile_enable", "art_profile_read", "art_options_default", "art_create", "art_count_segments", "art_destroy", "art_get_stats", "art_set_fields",
                   "art_set_band", "art_sweep"):
             getattr(lib, f).restype = C.c_int
@@ -382,6 +421,54 @@ class ArtSweep:
             raise ArtError(st, art_last_error(self._ctx))
         return rep, np.array(hist[:n])
 
+    def _chem(self, chem: dict) -> ArtChem:
+        return ArtChem(chem["alphaA"], chem["alphaB"], chem["gcoll"], chem["sigma0"], chem["h"], chem["nu0"],
+                       chem["dnu"])
+
+    def iterate_warm(self, net, nH, chem: dict, sources, y, tol=1e-6, max_iter=200, coarse_factor=4,
+                     coarse_nside=4, use_net=True, phase1_max_iter=40, phase1_tol=1e-4, judge_tol=0.3,
+                     stream=None):
+        """The iteration of `iterate`, warm-started by the surrogate (coarse sweep + network).
+        Returns (warm report, residual history); raises ArtError unless converged."""
+        npp, nd_, _n = _ptr(nH, np.float64, self.ncell)
+        yp, yd, _y = _ptr(y, np.float64, self.ncell)
+        if not (nd_ and yd):
+            raise TypeError("iterate_warm takes device buffers")
+        w = ArtWarmOptions()
+        load().art_warm_options_default(C.byref(w))
+        w.coarse_factor, w.coarse_nside, w.use_net = int(coarse_factor), int(coarse_nside), 1 if use_net else 0
+        w.phase1_max_iter, w.phase1_tol, w.judge_tol = int(phase1_max_iter), float(phase1_tol), float(judge_tol)
+        src = _sources(sources)
+        hist = (C.c_double * max_iter)()
+        rep = ArtWarmReport()
+        st = load().art_iterate_ionization_warm(self._ctx, net._net if net is not None else None,
+                                                C.byref(self._chem(chem)), C.c_void_p(npp), src, len(sources),
+                                                float(tol), int(max_iter), C.byref(w), C.c_void_p(yp), hist,
+                                                C.byref(rep), C.c_void_p(_stream(stream)))
+        n = max(0, min(rep.total.iterations, max_iter))
+        if st != ART_OK:
+            raise ArtError(st, art_last_error(self._ctx))
+        return rep, np.array(hist[:n])
+
+    def surrogate_sample(self, nH, chem: dict, y, X=None, t=None, jin=None, jc=None, coarse_factor=4,
+                         coarse_nside=4, stream=None):
+        """Training sample of state y (device FP64): inputs X [4][V], target t, J^in, prolonged J_c
+        (device float32 buffers, each optional)."""
+        npp, _, _n = _ptr(nH, np.float64, self.ncell)
+        yp, _, _y = _ptr(y, np.float64, self.ncell)
+        ptrs = []
+        keep = []
+        for b, m in ((X, 4 * self.ncell), (t, self.ncell), (jin, self.ncell), (jc, self.ncell)):
+            p_, d_, k_ = _ptr(b, np.float32, m)
+            if b is not None and not d_:
+                raise TypeError("surrogate_sample writes device buffers")
+            ptrs.append(p_)
+            keep.append(k_)
+        _check(self._ctx, load().art_surrogate_sample(self._ctx, C.byref(self._chem(chem)), C.c_void_p(npp),
+                                                       C.c_void_p(yp), int(coarse_factor), int(coarse_nside),
+                                                       *[C.c_void_p(p_) for p_ in ptrs],
+                                                       C.c_void_p(_stream(stream))))
+
     def set_fields(self, kappa, src, stream=None):
         n = self.ncell * self.nbins
         kp, kd, _k = _ptr(kappa, self.dtype, n)
@@ -411,3 +498,96 @@ class ArtSweep:
         _check(self._ctx, art_sweep(self._ctx, ptrs[0], ptrs[1], ptrs[2], on_dev,
                                     _stream(stream) if on_dev else 0))
         return J, J_in, gamma
+
+
+class ArtNet:
+    """The 3D-convolution surrogate (include/art_net.h): 4 -> 32 -> 32 -> 32 -> 1 channels,
+    3x3x3 kernels with per-layer dilations, BF16 tensor-core kernels, FP32 master weights."""
+
+    def __init__(self, dilation=(1, 2, 4, 8), seed: int = 1, lr: float = 1e-3, beta1: float = 0.9,
+                 beta2: float = 0.999, adam_eps: float = 1e-8):
+        o = ArtNetOptions()
+        load().art_net_options_default(C.byref(o))
+        for i, d in enumerate(dilation):
+            o.dilation[i] = int(d)
+        o.seed, o.lr, o.beta1, o.beta2, o.adam_eps = int(seed), float(lr), float(beta1), float(beta2), float(adam_eps)
+        h = C.c_void_p()
+        st = load().art_net_create(C.byref(o), C.byref(h))
+        if st != ART_OK:
+            raise ArtError(st, "art_net_create failed")
+        self._net = h
+        self.dilation = tuple(int(d) for d in dilation)
+
+    def close(self):
+        if getattr(self, "_net", None):
+            load().art_net_destroy(self._net)
+            self._net = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != ART_OK:
+            raise ArtError(st, load().art_net_last_error(self._net).decode())
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(ART_NET_PARAMS, dtype=np.float32)
+        self._check(load().art_net_get_params(self._net, out.ctypes.data))
+        return out
+
+    def set_params(self, p):
+        a = np.ascontiguousarray(np.asarray(p, dtype=np.float32))
+        if a.size != ART_NET_PARAMS:
+            raise ValueError(f"expected {ART_NET_PARAMS} parameters")
+        self._check(load().art_net_set_params(self._net, a.ctypes.data))
+
+    @staticmethod
+    def split_params(flat):
+        """params layout -> [(W [27][c_out][c_in], b [c_out])] per layer."""
+        out, off = [], 0
+        for ci, co in NET_LAYERS:
+            W = np.asarray(flat[off:off + 27 * co * ci]).reshape(27, co, ci)
+            off += 27 * co * ci
+            b = np.asarray(flat[off:off + co])
+            off += co
+            out.append((W, b))
+        return out
+
+    @staticmethod
+    def join_params(layers):
+        return np.concatenate([np.concatenate([np.ravel(W), np.ravel(b)]) for W, b in layers])
+
+    def _dev(self, x, n, name):
+        p_, d_, k_ = _ptr(x, np.float32, n)
+        if not d_:
+            raise TypeError(f"{name} must be a CUDA float32 tensor")
+        return p_
+
+    def forward(self, X, o, shape, stream=None):
+        nz, ny, nx = shape
+        V = nx * ny * nz
+        self._check(load().art_net_forward(self._net, nx, ny, nz, C.c_void_p(self._dev(X, 4 * V, "X")),
+                                           C.c_void_p(self._dev(o, V, "o")), C.c_void_p(_stream(stream))))
+        return o
+
+    def gradients(self, X, t, shape, stream=None):
+        nz, ny, nx = shape
+        V = nx * ny * nz
+        loss = C.c_double(0.0)
+        g = np.empty(ART_NET_PARAMS, dtype=np.float32)
+        self._check(load().art_net_gradients(self._net, nx, ny, nz, C.c_void_p(self._dev(X, 4 * V, "X")),
+                                             C.c_void_p(self._dev(t, V, "t")), C.byref(loss), g.ctypes.data,
+                                             C.c_void_p(_stream(stream))))
+        return loss.value, g
+
+    def train_step(self, X, t, shape, want_loss=True, stream=None):
+        nz, ny, nx = shape
+        V = nx * ny * nz
+        loss = C.c_double(float("nan"))
+        self._check(load().art_net_train_step(self._net, nx, ny, nz, C.c_void_p(self._dev(X, 4 * V, "X")),
+                                              C.c_void_p(self._dev(t, V, "t")),
+                                              C.byref(loss) if want_loss else None, C.c_void_p(_stream(stream))))
+        return loss.value

@@ -19,8 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "lib")
 LIB = os.path.join(OUT_DIR, "libart.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["art_api.cu", "art_geometry.cpp", "art_probe.cu", "art_noalloc.cu", "art_ion.cu"]
-HEADERS = ["art_kernels.cuh", "art_geometry.hpp", "art_ctx.hpp"]
+SOURCES = ["art_api.cu", "art_geometry.cpp", "art_probe.cu", "art_noalloc.cu", "art_ion.cu", "art_net.cu"]
+HEADERS = ["art_kernels.cuh", "art_geometry.hpp", "art_ctx.hpp", "art_net_kernels.cuh", "art_net_internal.hpp"]
 
 
 def nvcc_path() -> str:
@@ -34,7 +34,7 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(INCLUDE, "art.h"), __file__]
+    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(INCLUDE, h) for h in ("art.h", "art_net.h")] + [__file__]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

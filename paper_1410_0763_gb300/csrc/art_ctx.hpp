@@ -15,6 +15,7 @@ struct art_iter_bufs {
     int nsrc_cap = 0;
     double *nH = nullptr, *y = nullptr, *y0 = nullptr;   // FP64 state
     float *gpt = nullptr, *kap = nullptr, *eps = nullptr, *jin = nullptr;
+    float *jsur = nullptr;                                // surrogate J^in / prolonged J_c
     unsigned long long *resid = nullptr;
     double *src = nullptr;                                // [nsrc][4]: x, y, z, Q
 };
@@ -29,6 +30,14 @@ struct art_grid_host {
     int n_part = 0;            // J partials (classes x direction groups)
     int nblocks = 0;           // slab blocks of its longest axis
     long long seg_count = 0;   // segments per sweep and bin
+};
+
+// Scratch of the surrogate on this context's grid (coarse fields, coarse
+// J^in, network output, eps_ref).
+struct art_sur_bufs {
+    long long n = 0;
+    int f = 0, nside = 0;
+    void *kc = nullptr, *ec = nullptr, *jc = nullptr, *o = nullptr, *eref = nullptr;
 };
 
 struct art_ctx {
@@ -74,6 +83,8 @@ struct art_ctx {
     bool profiling = false;
     std::vector<cudaEvent_t> ev;
     art_iter_bufs it;
+    art_ctx *coarse = nullptr;  // coarse-mesh sweep of the surrogate
+    art_sur_bufs sur;
 };
 
 

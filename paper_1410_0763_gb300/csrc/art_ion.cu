@@ -12,6 +12,8 @@
 
 #include "art.h"
 #include "art_ctx.hpp"
+#include "art_net.h"
+#include "art_net_internal.hpp"
 
 namespace {
 
@@ -296,29 +298,67 @@ art_status art_point_sources(art_ctx *ctx, const float *kappa, const double *sig
     return ART_OK;
 }
 
-art_status art_iterate_ionization(art_ctx *ctx, const art_chem *ch, const double *nH, const art_source *src,
-                                  int n_src, double tol, int max_iter, double *y, double *resid_hist,
-                                  art_iter_report *rep, void *stream)
+}  // extern "C"
+
+namespace {
+
+art_status check_iteration_context(art_ctx *ctx, const art_chem *ch, const char *who)
 {
-    if (!ctx) return ART_E_INVALID;
-    if (ctx->grids.size() != 1) return art_fail(ctx, ART_E_INVALID, "art_iterate_ionization: single-grid contexts only");
-    if (!ch || !nH || !y || (n_src > 0 && !src) || n_src < 0 || max_iter < 1 || !(tol > 0.0))
-        return art_fail(ctx, ART_E_INVALID, "art_iterate_ionization: bad argument");
+    if (ctx->grids.size() != 1) return art_fail(ctx, ART_E_INVALID, std::string(who) + ": single-grid contexts only");
+    if (!ch) return art_fail(ctx, ART_E_INVALID, std::string(who) + ": null chemistry");
     if (ctx->prec != ART_FP32 || ctx->nbins != 1 || ctx->opt.field_form != ART_FIELDS_EPS)
         return art_fail(ctx, ART_E_INVALID,
-                        "art_iterate_ionization: needs an FP32 context with one bin and ART_FIELDS_EPS inputs");
+                        std::string(who) + ": needs an FP32 context with one bin and ART_FIELDS_EPS inputs");
     if (!(ctx->grid.dx_cm > 0.0) || !(ch->sigma0 > 0.0) || !(ch->h > 0.0) || !(ch->nu0 > 0.0) || !(ch->dnu > 0.0) ||
         !(ch->alphaB > 0.0) || !(ch->alphaA >= ch->alphaB) || !(ch->gcoll >= 0.0))
-        return art_fail(ctx, ART_E_INVALID, "art_iterate_ionization: bad chemistry constants");
+        return art_fail(ctx, ART_E_INVALID, std::string(who) + ": bad chemistry constants");
+    return ART_OK;
+}
+
+// Balance-kernel arguments: kappa = y nH sigma0 dx and the recombination
+// emissivity eps = G h nu0 (alpha_A - alpha_B) (x nH)^2 dx / dnu, scaled by
+// the band integral G so that the sweep's J^in is Gamma_diff / (4 pi).
+BalArgs balance_args(art_ctx *ctx, const art_chem *ch, const double *nH, double *y)
+{
+    double G = 0.0;
+    art_band_integral(ch->sigma0, ch->h, ch->nu0, ch->nu0, ch->nu0 + ch->dnu, &G);
+    art_iter_bufs &B = ctx->it;
+    BalArgs ba;
+    ba.nH = nH;
+    ba.gpt = B.gpt;
+    ba.gdiff = B.jin;
+    ba.alphaB = ch->alphaB;
+    ba.gcoll = ch->gcoll;
+    ba.kap_coef = ch->sigma0 * ctx->grid.dx_cm;
+    ba.eps_coef = G * ch->h * ch->nu0 * (ch->alphaA - ch->alphaB) * ctx->grid.dx_cm / ch->dnu;
+    ba.y = y;
+    ba.kap = B.kap;
+    ba.eps = B.eps;
+    ba.resid = B.resid;
+    ba.ncell = ctx->ncell;
+    ba.solve = 0;
+    return ba;
+}
+
+// The RT / balance fixed-point iteration; with `warm`, J^in comes from the
+// surrogate until its phase ends, then from plain sweeps.
+art_status iterate_impl(art_ctx *ctx, art_net *net, const art_chem *ch, const double *nH, const art_source *src,
+                        int n_src, double tol, int max_iter, const art_warm_options *warm, double *y,
+                        double *resid_hist, art_iter_report *rep, art_warm_report *wrep, cudaStream_t st)
+{
+    if (!ctx) return ART_E_INVALID;
+    art_status s = check_iteration_context(ctx, ch, "art_iterate_ionization");
+    if (s != ART_OK) return s;
+    if (!nH || !y || (n_src > 0 && !src) || n_src < 0 || max_iter < 1 || !(tol > 0.0))
+        return art_fail(ctx, ART_E_INVALID, "art_iterate_ionization: bad argument");
     const auto t0 = std::chrono::steady_clock::now();
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     const long long n = ctx->ncell;
     art_iter_bufs &B = ctx->it;
-    art_status s;
     if ((s = ensure(ctx, &B.gpt, n)) != ART_OK || (s = ensure(ctx, &B.kap, n)) != ART_OK ||
         (s = ensure(ctx, &B.eps, n)) != ART_OK || (s = ensure(ctx, &B.jin, n)) != ART_OK ||
         (s = ensure(ctx, &B.resid, 1)) != ART_OK)
         return s;
+    if (warm && ((s = ensure(ctx, &B.y0, n)) != ART_OK || (s = ensure(ctx, &B.jsur, n)) != ART_OK)) return s;
     std::vector<double> h_src, h_q;
     if ((s = upload_sources(ctx, src, n_src, nullptr, 1, h_src, h_q)) != ART_OK) return s;
     const int cap = n_src > 0 ? n_src : 1;
@@ -335,36 +375,32 @@ art_status art_iterate_ionization(art_ctx *ctx, const art_chem *ch, const double
     }
     ICK(ctx, cudaMemcpyAsync(d_sig, &ch->sigma0, sizeof(double), cudaMemcpyHostToDevice, st));
 
-    // G = int_{nu0}^{nu0 + dnu} sigma/(h nu) dnu for sigma = sigma0 (nu/nu0)^-3
-    double G = 0.0;
-    if (art_band_integral(ch->sigma0, ch->h, ch->nu0, ch->nu0, ch->nu0 + ch->dnu, &G) != ART_OK)
-        return art_fail(ctx, ART_E_INVALID, "art_iterate_ionization: bad band");
-    BalArgs ba;
-    ba.nH = nH;
-    ba.gpt = B.gpt;
-    ba.gdiff = B.jin;
-    ba.alphaB = ch->alphaB;
-    ba.gcoll = ch->gcoll;
-    ba.kap_coef = ch->sigma0 * ctx->grid.dx_cm;
-    ba.eps_coef = G * ch->h * ch->nu0 * (ch->alphaA - ch->alphaB) * ctx->grid.dx_cm / ch->dnu;
-    ba.y = y;
-    ba.kap = B.kap;
-    ba.eps = B.eps;
-    ba.resid = B.resid;
-    ba.ncell = n;
+    BalArgs ba = balance_args(ctx, ch, nH, y);
     const int nt = 256;
     const unsigned nb = (unsigned)((n + nt - 1) / nt);
-    ba.solve = 0;
-    balance_kernel<<<nb, nt, 0, st>>>(ba);
+    balance_kernel<<<nb, nt, 0, st>>>(ba);   // kappa, eps of the initial state
     ICK(ctx, cudaGetLastError());
     ba.solve = 1;
+    if (warm) ICK(ctx, cudaMemcpyAsync(B.y0, y, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
 
-    int it = 0, conv = 0;
-    double r = 0.0;
+    bool phase1 = warm != nullptr && warm->phase1_max_iter > 0;
+    bool have_jin = false;
+    int it = 0, conv = 0, it1 = 0, sweeps = 0, fell_back = 0;
+    double r = 0.0, judge = 0.0;
     for (it = 1; it <= max_iter; ++it) {
         if ((s = launch_points(ctx, B.kap, 1, d_src, d_q, d_sig, n_src, B.gpt, st)) != ART_OK) return s;
-        if ((s = art_internal_layout(ctx, B.kap, B.eps, st)) != ART_OK) return s;
-        if ((s = art_internal_sweep(ctx, nullptr, B.jin, nullptr, st)) != ART_OK) return s;
+        if (have_jin) {
+            have_jin = false;   // J^in of this state came with the judge's sweep
+        } else if (phase1) {
+            s = artnet_surrogate(ctx, net, warm->use_net, warm->coarse_factor, warm->coarse_nside, B.kap, B.eps, y,
+                                 B.jin, nullptr, nullptr, st);
+            if (s != ART_OK) return s;
+            ++it1;
+        } else {
+            if ((s = art_internal_layout(ctx, B.kap, B.eps, st)) != ART_OK) return s;
+            if ((s = art_internal_sweep(ctx, nullptr, B.jin, nullptr, st)) != ART_OK) return s;
+            ++sweeps;
+        }
         ICK(ctx, cudaMemsetAsync(B.resid, 0, sizeof(unsigned long long), st));
         balance_kernel<<<nb, nt, 0, st>>>(ba);
         ICK(ctx, cudaGetLastError());
@@ -373,9 +409,32 @@ art_status art_iterate_ionization(art_ctx *ctx, const art_chem *ch, const double
         ICK(ctx, cudaStreamSynchronize(st));
         std::memcpy(&r, &bits, sizeof(r));
         if (resid_hist) resid_hist[it - 1] = r;
-        if (r < tol) {
+        if (!phase1 && r < tol) {
             conv = 1;
             break;
+        }
+        if (phase1 && (r < warm->phase1_tol || it1 >= warm->phase1_max_iter)) {
+            // judge the surrogate against a full sweep on the current state
+            if (warm->use_net && (s = artnet_check(net, st)) != ART_OK)
+                return art_fail(ctx, s, std::string("surrogate network: ") + artnet_error(net));
+            s = artnet_surrogate(ctx, net, warm->use_net, warm->coarse_factor, warm->coarse_nside, B.kap, B.eps, y,
+                                 B.jsur, nullptr, nullptr, st);
+            if (s != ART_OK) return s;
+            if ((s = art_internal_layout(ctx, B.kap, B.eps, st)) != ART_OK) return s;
+            if ((s = art_internal_sweep(ctx, nullptr, B.jin, nullptr, st)) != ART_OK) return s;
+            ++sweeps;
+            if ((s = artnet_l1(ctx, B.jsur, B.jin, &judge, st)) != ART_OK) return s;
+            phase1 = false;
+            if (!(judge <= warm->judge_tol)) {
+                fell_back = 1;
+                ICK(ctx, cudaMemcpyAsync(y, B.y0, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+                ba.solve = 0;
+                balance_kernel<<<nb, nt, 0, st>>>(ba);
+                ICK(ctx, cudaGetLastError());
+                ba.solve = 1;
+            } else {
+                have_jin = true;
+            }
         }
     }
     if (rep) {
@@ -384,7 +443,84 @@ art_status art_iterate_ionization(art_ctx *ctx, const art_chem *ch, const double
         rep->residual = r;
         rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
+    if (wrep) {
+        wrep->surrogate_iterations = it1;
+        wrep->plain_sweeps = sweeps;
+        wrep->fell_back = fell_back;
+        wrep->judge_error = judge;
+    }
     return conv ? ART_OK : art_fail(ctx, ART_E_NOT_CONVERGED, "art_iterate_ionization: max_iter reached");
+}
+
+}  // namespace
+
+extern "C" {
+
+art_status art_iterate_ionization(art_ctx *ctx, const art_chem *ch, const double *nH, const art_source *src,
+                                  int n_src, double tol, int max_iter, double *y, double *resid_hist,
+                                  art_iter_report *rep, void *stream)
+{
+    return iterate_impl(ctx, nullptr, ch, nH, src, n_src, tol, max_iter, nullptr, y, resid_hist, rep, nullptr,
+                        static_cast<cudaStream_t>(stream));
+}
+
+art_status art_warm_options_default(art_warm_options *o)
+{
+    if (!o) return ART_E_INVALID;
+    o->coarse_factor = 4;
+    o->coarse_nside = 4;
+    o->use_net = 1;
+    o->phase1_max_iter = 40;
+    o->phase1_tol = 1e-4;
+    o->judge_tol = 0.3;
+    return ART_OK;
+}
+
+art_status art_iterate_ionization_warm(art_ctx *ctx, art_net *net, const art_chem *ch, const double *nH,
+                                       const art_source *src, int n_src, double tol, int max_iter,
+                                       const art_warm_options *wopt, double *y, double *resid_hist,
+                                       art_warm_report *rep, void *stream)
+{
+    if (!ctx) return ART_E_INVALID;
+    art_warm_options w;
+    if (wopt) w = *wopt;
+    else art_warm_options_default(&w);
+    if (w.coarse_factor < 1 || w.coarse_nside < 1 || w.phase1_max_iter < 0 || !(w.phase1_tol > 0.0) ||
+        !(w.judge_tol >= 0.0) || (w.use_net && !net))
+        return art_fail(ctx, ART_E_INVALID, "art_iterate_ionization_warm: bad warm-start options");
+    art_iter_report r{};
+    art_status s = iterate_impl(ctx, net, ch, nH, src, n_src, tol, max_iter, &w, y, resid_hist, &r, rep,
+                                static_cast<cudaStream_t>(stream));
+    if (rep) rep->total = r;
+    return s;
+}
+
+art_status art_surrogate_sample(art_ctx *ctx, const art_chem *ch, const double *nH, const double *y,
+                                int coarse_factor, int coarse_nside, float *X, float *t, float *jin, float *jc,
+                                void *stream)
+{
+    if (!ctx) return ART_E_INVALID;
+    art_status s = check_iteration_context(ctx, ch, "art_surrogate_sample");
+    if (s != ART_OK) return s;
+    if (!nH || !y) return art_fail(ctx, ART_E_INVALID, "art_surrogate_sample: null state");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const long long n = ctx->ncell;
+    art_iter_bufs &B = ctx->it;
+    if ((s = ensure(ctx, &B.kap, n)) != ART_OK || (s = ensure(ctx, &B.eps, n)) != ART_OK ||
+        (s = ensure(ctx, &B.jin, n)) != ART_OK || (s = ensure(ctx, &B.jsur, n)) != ART_OK)
+        return s;
+    BalArgs ba = balance_args(ctx, ch, nH, const_cast<double *>(y));
+    balance_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ba);
+    ICK(ctx, cudaGetLastError());
+    float *jcf = jc ? jc : B.jsur;
+    float *jf = jin ? jin : B.jin;
+    if ((s = artnet_surrogate(ctx, nullptr, 0, coarse_factor, coarse_nside, B.kap, B.eps, y, nullptr, X, jcf, st)) !=
+        ART_OK)
+        return s;
+    if ((s = art_internal_layout(ctx, B.kap, B.eps, st)) != ART_OK) return s;
+    if ((s = art_internal_sweep(ctx, nullptr, jf, nullptr, st)) != ART_OK) return s;
+    if (t && (s = artnet_target(ctx, jf, jcf, t, st)) != ART_OK) return s;
+    return ART_OK;
 }
 
 }  // extern "C"

@@ -1,0 +1,730 @@
+// art_net_kernels.cuh -- device code of the 3D-convolution surrogate (private
+// to libart): the tensor-core implicit-GEMM convolution (TMA-fed shared
+// memory, tcgen05 MMA with the accumulator in tensor memory), the weight
+// gradient, and the small elementwise kernels around them.
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace artnet {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int TILE_M = 128;          // voxels per MMA tile (accumulator lanes)
+constexpr int CONV_THREADS = 192;    // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int CONV_STAGES = 6;       // A-operand ring (one tap per stage)
+constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz: bounded waits
+
+enum { MODE_RELU = 0, MODE_OUT = 1, MODE_DGRAD = 2 };
+enum { ERR_TIMEOUT_PRODUCER = 1, ERR_TIMEOUT_MMA = 2, ERR_TIMEOUT_EPILOGUE = 4 };
+
+struct ConvArgs {
+    const float *bias;     // [COUT] (MODE_RELU, MODE_OUT)
+    const bf16 *mask;      // [V][COUT] activation whose sign gates the gradient (MODE_DGRAD)
+    bf16 *out;             // [V][COUT] (MODE_RELU, MODE_DGRAD)
+    float *out_f32;        // [V] channel 0 (MODE_OUT)
+    int nx, ny, nz, dil;
+    int ntiles;
+    int *err;              // device error word (timeouts)
+};
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for the phase of the given parity to complete; gives up after about
+// two seconds or when another role of the CTA gave up (abort flag).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_test(bar, parity)) return true;
+        if (*abort) return false;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1, int c2,
+                                            int c3)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor of a K-major operand tile whose rows
+// (one per M or N index) are `row_bytes` long and stored with the matching
+// TMA swizzle (64-byte rows: 64B swizzle; 32-byte rows: 32B swizzle); groups
+// of 8 rows are row_bytes * 8 apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, int row_bytes)
+{
+    const uint64_t sbo = (uint64_t)(row_bytes * 8) >> 4;
+    const uint64_t layout = row_bytes == 64 ? 4ull : 6ull;   // SWIZZLE_64B : SWIZZLE_32B
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | (1ull << 16) | (sbo << 32) | (1ull << 46) | (layout << 61);
+}
+
+// Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major.
+__host__ __device__ constexpr uint32_t mma_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 16 consecutive FP32 columns of this warp's 32 accumulator lanes.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Implicit-GEMM 3x3x3 convolution on tensor cores.
+//   out[v][co] = epilogue( sum_t sum_ci W[t][co][ci] * in[v + dil * off_t][ci] )
+// Activations are channels-last BF16 [V][C]; a tile is 128 consecutive
+// voxels (whole x rows), so each tap's operand tile is one TMA box of the
+// input shifted by dil * (dx, dy, dz), zero-filled outside the grid.  The
+// 27 tap tiles stream through a ring of shared-memory stages; all 27 tap
+// weight blocks stay in shared memory.  One thread issues the MMAs
+// (M = 128, N = COUT, K = 16 per instruction) into a double-buffered TMEM
+// accumulator that four epilogue warps drain.
+// ---------------------------------------------------------------------------
+template <int CIN, int COUT> struct ConvSmem {
+    static constexpr int A_BYTES = TILE_M * CIN * 2;
+    static constexpr int W_TAP = COUT * CIN * 2;
+    static constexpr int W_BYTES = 27 * W_TAP;
+    static constexpr int NCOLS = 2 * COUT < 32 ? 32 : 2 * COUT;   // power of two
+    static constexpr int BAR_OFF = W_BYTES + CONV_STAGES * A_BYTES;
+    static constexpr int NBARS = 2 * CONV_STAGES + 1 + 2 + 2 + 1;
+    static constexpr int BYTES = BAR_OFF + NBARS * 8 + 1024;        // + alignment slack
+};
+
+template <int CIN, int COUT, int MODE>
+__global__ void __launch_bounds__(CONV_THREADS, 1)
+    conv_tc_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap wmap, const ConvArgs p)
+{
+    using L = ConvSmem<CIN, COUT>;
+    static_assert(CIN == 16 || CIN == 32, "16 or 32 input channels");
+    static_assert(COUT == 16 || COUT == 32, "16 or 32 output channels");
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const uint32_t sW = smem_u32(smem);
+    const uint32_t sA = sW + L::W_BYTES;
+    const uint32_t bar0 = sW + L::BAR_OFF;
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (CONV_STAGES + s); };
+    const uint32_t w_bar = bar0 + 8u * (2 * CONV_STAGES);
+    auto tfull_bar = [&](int a) { return bar0 + 8u * (2 * CONV_STAGES + 1 + a); };
+    auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * CONV_STAGES + 3 + a); };
+    const uint32_t done_bar = bar0 + 8u * (2 * CONV_STAGES + 5);
+    volatile int *abort = &s_abort;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < CONV_STAGES; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        mbar_init(w_bar, 1);
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(tfull_bar(a), 1);
+            mbar_init(tempty_bar(a), 4);
+        }
+        mbar_init(done_bar, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(L::NCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    const int nx = p.nx, ny = p.ny, dil = p.dil;
+    const int bx = nx < TILE_M ? nx : TILE_M;
+    const int by = TILE_M / bx;
+    (void)by;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            mbar_expect_tx(w_bar, L::W_BYTES);
+            for (int t = 0; t < 27; ++t) tma_load_2d(sW + t * L::W_TAP, &wmap, w_bar, 0, t * COUT);
+            int s = 0;
+            uint32_t ph = 0;
+            for (int tile = blockIdx.x; tile < p.ntiles && !*abort; tile += gridDim.x) {
+                const long long vb = (long long)tile * TILE_M;
+                const long long plane = (long long)nx * ny;
+                const int z = (int)(vb / plane);
+                const long long rem = vb - (long long)z * plane;
+                const int y0 = (int)(rem / nx), x0 = (int)(rem - (long long)y0 * nx);
+                for (int t = 0; t < 27; ++t) {
+                    if (!mbar_wait(empty_bar(s), ph ^ 1u, abort)) {
+                        *abort = 1;
+                        atomicOr(p.err, ERR_TIMEOUT_PRODUCER);
+                        break;
+                    }
+                    const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+                    mbar_expect_tx(full_bar(s), L::A_BYTES);
+                    tma_load_4d(sA + s * L::A_BYTES, &amap, full_bar(s), 0, x0 + dx * dil, y0 + dy * dil, z + dz * dil);
+                    if (++s == CONV_STAGES) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+            }
+            // drain: every load issued has landed before the CTA may exit
+            for (int k = 0; k < CONV_STAGES; ++k) {
+                if (--s < 0) {
+                    s = CONV_STAGES - 1;
+                    ph ^= 1u;
+                }
+                mbar_wait(full_bar(s), ph, abort);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            constexpr uint32_t idesc = mma_idesc(TILE_M, COUT);
+            bool ok = mbar_wait(w_bar, 0, abort);
+            int s = 0, it = 0;
+            uint32_t ph = 0;
+            for (int tile = blockIdx.x; ok && tile < p.ntiles; tile += gridDim.x, ++it) {
+                const int acc = it & 1;
+                const uint32_t aph = (uint32_t)(it >> 1) & 1u;
+                if (!mbar_wait(tempty_bar(acc), aph ^ 1u, abort)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(acc * COUT);
+                for (int t = 0; t < 27; ++t) {
+                    if (!mbar_wait(full_bar(s), ph, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a_base = sA + s * L::A_BYTES, b_base = sW + t * L::W_TAP;
+#pragma unroll
+                    for (int k = 0; k < CIN / 16; ++k)
+                        mma_bf16(d, smem_desc(a_base + 32 * k, CIN * 2), smem_desc(b_base + 32 * k, CIN * 2), idesc,
+                                 (t | k) != 0);
+                    mma_commit(empty_bar(s));
+                    if (++s == CONV_STAGES) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(tfull_bar(acc));
+            }
+            if (!ok) {
+                *abort = 1;
+                atomicOr(p.err, ERR_TIMEOUT_MMA);
+            }
+            // every MMA issued has completed before TMEM is released
+            mma_commit(done_bar);
+            mbar_wait(done_bar, 0, abort);
+        }
+    } else {
+        // ---------------- epilogue (warps 2-5) ----------------
+        const int q = warp & 3;                 // TMEM lane quarter this warp may access
+        const int row = q * 32 + lane;
+        int it = 0;
+        for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x, ++it) {
+            const int acc = it & 1;
+            const uint32_t aph = (uint32_t)(it >> 1) & 1u;
+            if (!mbar_wait(tfull_bar(acc), aph, abort)) {
+                *abort = 1;
+                atomicOr(p.err, ERR_TIMEOUT_EPILOGUE);
+                break;
+            }
+            tc_fence_after();
+            float v[COUT];
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * COUT);
+#pragma unroll
+            for (int c = 0; c < COUT; c += 16) tmem_ld16(taddr + c, v + c);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty_bar(acc));
+            const long long vox = (long long)tile * TILE_M + row;
+            if (MODE == MODE_OUT) {
+                p.out_f32[vox] = v[0] + p.bias[0];
+            } else {
+                uint32_t packed[COUT / 2];
+                if (MODE == MODE_RELU) {
+#pragma unroll
+                    for (int c = 0; c < COUT; c += 2) {
+                        const float a0 = fmaxf(v[c] + p.bias[c], 0.f), a1 = fmaxf(v[c + 1] + p.bias[c + 1], 0.f);
+                        const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
+                        packed[c / 2] = *reinterpret_cast<const uint32_t *>(&h);
+                    }
+                } else {
+                    uint4 m[COUT / 8];
+                    const uint4 *mp = reinterpret_cast<const uint4 *>(p.mask + vox * COUT);
+#pragma unroll
+                    for (int i = 0; i < COUT / 8; ++i) m[i] = mp[i];
+                    const bf16 *mh = reinterpret_cast<const bf16 *>(m);
+#pragma unroll
+                    for (int c = 0; c < COUT; c += 2) {
+                        const float a0 = __bfloat162float(mh[c]) > 0.f ? v[c] : 0.f;
+                        const float a1 = __bfloat162float(mh[c + 1]) > 0.f ? v[c + 1] : 0.f;
+                        const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
+                        packed[c / 2] = *reinterpret_cast<const uint32_t *>(&h);
+                    }
+                }
+                uint4 *op = reinterpret_cast<uint4 *>(p.out + vox * COUT);
+#pragma unroll
+                for (int i = 0; i < COUT / 8; ++i)
+                    op[i] = make_uint4(packed[4 * i], packed[4 * i + 1], packed[4 * i + 2], packed[4 * i + 3]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::NCOLS) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient: gW[t][co][ci] = sum_v g[v][co] * a[v + dil * off_t][ci]
+// (BF16 operands, FP32 accumulation with mma.sync m16n8k16).  Grid (chunks,
+// 27 taps); each CTA writes its chunk's partial sums, which gw_reduce_kernel
+// adds in chunk order.
+// ---------------------------------------------------------------------------
+constexpr int WG_CHUNK = 4096;
+constexpr int WG_STEP = 64;
+
+__device__ __forceinline__ void mma_m16n8k16(float *c, const uint32_t *a, const uint32_t *b)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128) wgrad_kernel(const bf16 *__restrict__ g, const bf16 *__restrict__ a, int nx, int ny,
+                                                    int nz, int dil, float *__restrict__ part)
+{
+    constexpr int LD = WG_STEP + 8;   // padded row (bank-conflict free fragment loads)
+    __shared__ __align__(16) bf16 Gt[COUT][LD];
+    __shared__ __align__(16) bf16 At[CIN][LD];
+    __shared__ float red[4][COUT * CIN];
+    const int t = blockIdx.y;
+    const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+    const long long V = (long long)nx * ny * nz;
+    const long long v_begin = (long long)blockIdx.x * WG_CHUNK;
+    const long long v_end = v_begin + WG_CHUNK < V ? v_begin + WG_CHUNK : V;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int gq = lane >> 2, tq = lane & 3;
+    float acc[COUT / 16][CIN / 8][4];
+#pragma unroll
+    for (int i = 0; i < COUT / 16; ++i)
+#pragma unroll
+        for (int j = 0; j < CIN / 8; ++j)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
+
+    for (long long vb = v_begin; vb < v_end; vb += WG_STEP) {
+        // stage g and the shifted a, transposed to [channel][voxel]
+        for (int e = tid; e < WG_STEP * (COUT / 8); e += 128) {
+            const int j = e / (COUT / 8), c8 = e % (COUT / 8);
+            const long long v = vb + j;
+            uint4 w = make_uint4(0, 0, 0, 0);
+            if (v < v_end) w = *reinterpret_cast<const uint4 *>(g + v * COUT + c8 * 8);
+            const bf16 *h = reinterpret_cast<const bf16 *>(&w);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) Gt[c8 * 8 + i][j] = h[i];
+        }
+        for (int e = tid; e < WG_STEP * (CIN / 8); e += 128) {
+            const int j = e / (CIN / 8), c8 = e % (CIN / 8);
+            const long long v = vb + j;
+            uint4 w = make_uint4(0, 0, 0, 0);
+            if (v < v_end) {
+                const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
+                const int xs = x + dx * dil, ys = y + dy * dil, zs = z + dz * dil;
+                if (xs >= 0 && xs < nx && ys >= 0 && ys < ny && zs >= 0 && zs < nz)
+                    w = *reinterpret_cast<const uint4 *>(a + (((long long)zs * ny + ys) * nx + xs) * CIN + c8 * 8);
+            }
+            const bf16 *h = reinterpret_cast<const bf16 *>(&w);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) At[c8 * 8 + i][j] = h[i];
+        }
+        __syncthreads();
+        const int k0 = 16 * warp;   // this warp's 16 voxels of the step
+#pragma unroll
+        for (int mi = 0; mi < COUT / 16; ++mi) {
+            uint32_t af[4];
+            af[0] = *reinterpret_cast<const uint32_t *>(&Gt[16 * mi + gq][k0 + 2 * tq]);
+            af[1] = *reinterpret_cast<const uint32_t *>(&Gt[16 * mi + gq + 8][k0 + 2 * tq]);
+            af[2] = *reinterpret_cast<const uint32_t *>(&Gt[16 * mi + gq][k0 + 2 * tq + 8]);
+            af[3] = *reinterpret_cast<const uint32_t *>(&Gt[16 * mi + gq + 8][k0 + 2 * tq + 8]);
+#pragma unroll
+            for (int ni = 0; ni < CIN / 8; ++ni) {
+                uint32_t bfr[2];
+                bfr[0] = *reinterpret_cast<const uint32_t *>(&At[8 * ni + gq][k0 + 2 * tq]);
+                bfr[1] = *reinterpret_cast<const uint32_t *>(&At[8 * ni + gq][k0 + 2 * tq + 8]);
+                mma_m16n8k16(acc[mi][ni], af, bfr);
+            }
+        }
+        __syncthreads();
+    }
+    // fixed-order sum of the four warps' partials
+#pragma unroll
+    for (int mi = 0; mi < COUT / 16; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < CIN / 8; ++ni) {
+            const int r0 = 16 * mi + gq, c0 = 8 * ni + 2 * tq;
+            red[warp][r0 * CIN + c0] = acc[mi][ni][0];
+            red[warp][r0 * CIN + c0 + 1] = acc[mi][ni][1];
+            red[warp][(r0 + 8) * CIN + c0] = acc[mi][ni][2];
+            red[warp][(r0 + 8) * CIN + c0 + 1] = acc[mi][ni][3];
+        }
+    __syncthreads();
+    float *dst = part + ((long long)blockIdx.x * 27 + t) * (COUT * CIN);
+    for (int e = tid; e < COUT * CIN; e += 128) dst[e] = ((red[0][e] + red[1][e]) + red[2][e]) + red[3][e];
+}
+
+// Bias gradient partials: pb[chunk][co] = sum over the chunk of g[v][co].
+template <int COUT>
+__global__ void __launch_bounds__(COUT * 8) bgrad_kernel(const bf16 *__restrict__ g, long long V, float *__restrict__ pb)
+{
+    __shared__ float red[8][COUT];
+    const int co = threadIdx.x % COUT, lane8 = threadIdx.x / COUT;
+    const long long v_begin = (long long)blockIdx.x * WG_CHUNK;
+    const long long v_end = v_begin + WG_CHUNK < V ? v_begin + WG_CHUNK : V;
+    float s = 0.f;
+    for (long long v = v_begin + lane8; v < v_end; v += 8) s += __bfloat162float(g[v * COUT + co]);
+    red[lane8][co] = s;
+    __syncthreads();
+    if (threadIdx.x < COUT) {
+        float r = 0.f;
+        for (int i = 0; i < 8; ++i) r += red[i][co];
+        pb[(long long)blockIdx.x * COUT + co] = r;
+    }
+}
+
+// Sum chunk partials in chunk order into the params-layout gradient:
+// grad[t][co][ci] for co < cout, ci < cin (padded channels dropped), then
+// grad_b[co].
+__global__ void gw_reduce_kernel(const float *__restrict__ part, const float *__restrict__ pb, int nchunks, int coutp,
+                                 int cinp, int cout, int cin, float *__restrict__ grad_w, float *__restrict__ grad_b)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nw = 27 * cout * cin;
+    if (e < nw) {
+        const int t = e / (cout * cin), r = e % (cout * cin), co = r / cin, ci = r % cin;
+        const long long off = (long long)t * coutp * cinp + co * cinp + ci;
+        float s = 0.f;
+        for (int k = 0; k < nchunks; ++k) s += part[(long long)k * 27 * coutp * cinp + off];
+        grad_w[e] = s;
+    } else if (e < nw + cout) {
+        const int co = e - nw;
+        float s = 0.f;
+        for (int k = 0; k < nchunks; ++k) s += pb[(long long)k * coutp + co];
+        grad_b[co] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Parameters: Adam on the FP32 master copy, BF16 copies for the kernels.
+// ---------------------------------------------------------------------------
+__global__ void adam_kernel(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
+                            const float *__restrict__ g, int n, float lr, float b1, float b2, float eps, float c1,
+                            float c2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+struct LayerDev {
+    long long w_off, b_off;   // into the params array
+    int cin, cout, cinp, coutp;
+};
+
+// Forward weights [27][coutp][cinp] (zero padding), padded biases, and the
+// input-gradient weights [27][cinp][coutp] with the taps mirrored
+// (wd[t][ci][co] = W[26 - t][co][ci]).
+__global__ void pack_kernel(const float *__restrict__ params, LayerDev L, bf16 *__restrict__ wf, float *__restrict__ bias,
+                            bf16 *__restrict__ wd)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = 27 * L.coutp * L.cinp;
+    if (e < n) {
+        const int t = e / (L.coutp * L.cinp), r = e % (L.coutp * L.cinp), co = r / L.cinp, ci = r % L.cinp;
+        float w = 0.f;
+        if (co < L.cout && ci < L.cin) w = params[L.w_off + ((long long)t * L.cout + co) * L.cin + ci];
+        wf[e] = __float2bfloat16_rn(w);
+        if (wd) {
+            const int tm = 26 - t;
+            wd[((long long)tm * L.cinp + ci) * L.coutp + co] = __float2bfloat16_rn(w);
+        }
+    }
+    if (e < L.coutp) bias[e] = e < L.cout ? params[L.b_off + e] : 0.f;
+}
+
+// FP32 channel-major [4][V] inputs -> BF16 channels-last [V][16].
+__global__ void pack_input_kernel(const float *__restrict__ X, long long V, bf16 *__restrict__ out)
+{
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    __align__(16) bf16 h[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) h[c] = __float2bfloat16_rn(c < 4 ? X[c * V + v] : 0.f);
+    uint4 *o = reinterpret_cast<uint4 *>(out + v * 16);
+    o[0] = reinterpret_cast<const uint4 *>(h)[0];
+    o[1] = reinterpret_cast<const uint4 *>(h)[1];
+}
+
+// Loss partial sums and the output gradient g[v][0] = 2 (o - t) / V (BF16,
+// channels 1..15 zero).
+__global__ void loss_grad_kernel(const float *__restrict__ o, const float *__restrict__ t, long long V,
+                                 bf16 *__restrict__ g, double *__restrict__ partial)
+{
+    __shared__ double red[256];
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double sq = 0.0;
+    if (v < V) {
+        const float d = o[v] - t[v];
+        sq = (double)d * d;
+        __align__(16) bf16 h[16];
+        h[0] = __float2bfloat16_rn(2.f * d / (float)V);
+#pragma unroll
+        for (int c = 1; c < 16; ++c) h[c] = __float2bfloat16_rn(0.f);
+        uint4 *op = reinterpret_cast<uint4 *>(g + v * 16);
+        op[0] = reinterpret_cast<const uint4 *>(h)[0];
+        op[1] = reinterpret_cast<const uint4 *>(h)[1];
+    }
+    red[threadIdx.x] = sq;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void sum_partials_kernel(const double *__restrict__ partial, int n, double scale, double *__restrict__ out)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += partial[i];
+        *out = s * scale;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Surrogate inputs and outputs on the solver's fields
+// ---------------------------------------------------------------------------
+constexpr float kLogFloor = -69.0f;
+
+// Coarse fields: f * block mean over f^3 fine cells.
+__global__ void restrict_kernel(const float *__restrict__ a, const float *__restrict__ b, int nx, int ny, int nz, int f,
+                                float *__restrict__ ac, float *__restrict__ bc)
+{
+    const int cx = nx / f, cy = ny / f, cz = nz / f;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)cx * cy * cz) return;
+    const int X = (int)(i % cx), Y = (int)((i / cx) % cy), Z = (int)(i / ((long long)cx * cy));
+    double sa = 0.0, sb = 0.0;
+    for (int k = 0; k < f; ++k)
+        for (int j = 0; j < f; ++j) {
+            const long long row = ((long long)(Z * f + k) * ny + (Y * f + j)) * nx + (long long)X * f;
+            for (int l = 0; l < f; ++l) {
+                sa += a[row + l];
+                sb += b[row + l];
+            }
+        }
+    const double s = 1.0 / ((double)f * f);   // f * mean = sum / f^2
+    ac[i] = (float)(sa * s);
+    bc[i] = (float)(sb * s);
+}
+
+// max of a non-negative field (float bits compare as integers)
+__global__ void max_kernel(const float *__restrict__ a, long long n, unsigned int *__restrict__ out)
+{
+    unsigned int m = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = max(m, __float_as_uint(fmaxf(a[i], 0.f)));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+struct FeatArgs {
+    const float *kap, *eps, *jc;   // jc: coarse grid
+    const double *y;
+    const unsigned int *eref_bits;
+    int nx, ny, nz, f;
+    bf16 *X16;                     // [V][16] (may be null)
+    float *X32;                    // [4][V] (may be null)
+    float *jc_fine;                // [V] prolonged J_c (may be null)
+};
+
+__device__ __forceinline__ float clamp_log(float v, float lref)
+{
+    return v > 0.f ? fmaxf(__logf(v) - lref, kLogFloor) : kLogFloor;
+}
+
+__global__ void features_kernel(const FeatArgs p)
+{
+    const long long V = (long long)p.nx * p.ny * p.nz;
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    const int x = (int)(v % p.nx), y = (int)((v / p.nx) % p.ny), z = (int)(v / ((long long)p.nx * p.ny));
+    const int cx = p.nx / p.f, cy = p.ny / p.f;
+    const float jc = p.jc[((long long)(z / p.f) * cy + y / p.f) * cx + x / p.f];
+    const float eref = __uint_as_float(*p.eref_bits);
+    const float lref = eref > 0.f ? __logf(eref) : 0.f;
+    const float f0 = 0.25f * clamp_log(p.kap[v], 0.f);
+    const float f1 = 0.1f * clamp_log(p.eps[v], lref);
+    const float f2 = (float)(1.0 - p.y[v]);
+    const float f3 = 0.1f * clamp_log(jc, lref);
+    if (p.X32) {
+        p.X32[v] = f0;
+        p.X32[V + v] = f1;
+        p.X32[2 * V + v] = f2;
+        p.X32[3 * V + v] = f3;
+    }
+    if (p.X16) {
+        __align__(16) bf16 h[16];
+        h[0] = __float2bfloat16_rn(f0);
+        h[1] = __float2bfloat16_rn(f1);
+        h[2] = __float2bfloat16_rn(f2);
+        h[3] = __float2bfloat16_rn(f3);
+#pragma unroll
+        for (int c = 4; c < 16; ++c) h[c] = __float2bfloat16_rn(0.f);
+        uint4 *o = reinterpret_cast<uint4 *>(p.X16 + v * 16);
+        o[0] = reinterpret_cast<const uint4 *>(h)[0];
+        o[1] = reinterpret_cast<const uint4 *>(h)[1];
+    }
+    if (p.jc_fine) p.jc_fine[v] = jc;
+}
+
+// t = max(ln J, floor) - max(ln J_c, floor), floor = ln eps_ref - 69.
+__global__ void target_kernel(const float *__restrict__ jin, const float *__restrict__ jcf, long long V,
+                              const unsigned int *__restrict__ eref_bits, float *__restrict__ t)
+{
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    const float eref = __uint_as_float(*eref_bits);
+    const float lref = eref > 0.f ? __logf(eref) : 0.f;
+    t[v] = clamp_log(jin[v], lref) - clamp_log(jcf[v], lref);
+}
+
+// J^in = J_c exp(o) (or J_c alone when o is null), J_c read on the coarse grid.
+__global__ void predict_kernel(const float *__restrict__ jc, const float *__restrict__ o, int nx, int ny, int nz, int f,
+                               float *__restrict__ jin)
+{
+    const long long V = (long long)nx * ny * nz;
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
+    const int cx = nx / f, cy = ny / f;
+    const float j = jc[((long long)(z / f) * cy + y / f) * cx + x / f];
+    jin[v] = o ? j * __expf(o[v]) : j;
+}
+
+// sum |a - b| and sum |b| in double, per block (fixed-order final sum on the host side kernel).
+__global__ void l1_kernel(const float *__restrict__ a, const float *__restrict__ b, long long n, double *__restrict__ part)
+{
+    __shared__ double r0[256], r1[256];
+    double s0 = 0.0, s1 = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        s0 += fabs((double)a[i] - (double)b[i]);
+        s1 += fabs((double)b[i]);
+    }
+    r0[threadIdx.x] = s0;
+    r1[threadIdx.x] = s1;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            r0[threadIdx.x] += r0[threadIdx.x + s];
+            r1[threadIdx.x] += r1[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = r0[0];
+        part[2 * blockIdx.x + 1] = r1[0];
+    }
+}
+
+}  // namespace artnet
