@@ -250,29 +250,97 @@ def batch_measure(torch, dev, steps=5):
             "ctas_per_launch": int(st.ctas_per_launch), "launches": int(st.launches), "graph": True}
 
 
-def ionization_measure(torch, dev, tol=1e-6):
-    """RT / ionization-balance iteration of a 128^3 HII region (N_side 8,
-    n_H 1e-3, Q 5e48 s^-1 at the centre, 6.6 kpc box) to residual tol, plain
-    start (uniform neutral fraction 1 - 1e-4)."""
+def ionization_measure(torch, dev, tol=1e-6, n_setups=8, n_iter=24, train_steps=1500):
+    """RT / ionization-balance solve of a 128^3 HII region (N_side 8, n_H 1e-3,
+    Q 5e48 s^-1 at the centre, 6.6 kpc box) to residual tol: plain iteration
+    from x = 1e-4, and warm-started (coarse-mesh solve, factor 4, N_side 4;
+    then the surrogate phase with the network, or without it).  The network is
+    first trained (untimed) on the iterates of n_setups random HII setups
+    (lognormal density, 1-8 sources) that do not include this one."""
     from paper_1410_0763_gb300 import art
     from paper_1410_0763_gb300 import workloads as wl
     case = wl.hii_region()
+    n = case.n
+    V = n ** 3
+    srcs = [(p[0], p[1], p[2], q) for p, q in zip(case.pos, case.Q)]
     sw = art.ArtSweep(case.nH.shape, case.nside, 1, field_form=art.ART_FIELDS_EPS, dx_cm=case.chem["dx"])
     nH = torch.as_tensor(case.nH, dtype=torch.float64, device=dev)
-    srcs = [(p[0], p[1], p[2], q) for p, q in zip(case.pos, case.Q)]
-    y = torch.as_tensor(case.y0, dtype=torch.float64, device=dev).clone()
-    sw.iterate(nH, case.chem, srcs, y, tol=tol, max_iter=300)          # warm-up (first-call allocations)
-    y = torch.as_tensor(case.y0, dtype=torch.float64, device=dev).clone()
-    torch.cuda.synchronize()
+
+    def fresh():
+        return torch.as_tensor(case.y0, dtype=torch.float64, device=dev).clone()
+
+    def timed(fn, reps=3):
+        best, out = None, None
+        for _ in range(reps):
+            y = fresh()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = fn(y)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        return best, out, y
+
+    sw.iterate(nH, case.chem, srcs, fresh(), tol=tol, max_iter=300)        # warm-up (first-call allocations)
+    t_plain, (rep, _), y_plain = timed(lambda y: sw.iterate(nH, case.chem, srcs, y, tol=tol, max_iter=300))
+    y_plain = y_plain.cpu().numpy()
+    out = {"workload": "128^3 HII region, N_side 8, uniform n_H 1e-3, T 1e4 K, Q 5e48 s^-1 central, 6.6 kpc, "
+                       "FP32 sweep + FP64 balance", "tol": tol, "seconds_best_of": 3,
+           "plain": {"iterations": int(rep.iterations), "seconds": round(t_plain, 4), "converged": bool(rep.converged)}}
+
+    def warm(label, net, **kw):
+        t, (wr, _), y = timed(lambda y: sw.iterate_warm(net, nH, case.chem, srcs, y, tol=tol, max_iter=300, **kw))
+        dy = float(np.max(np.abs(y.cpu().numpy() - y_plain) / y_plain))
+        out[label] = {"iterations": int(wr.total.iterations), "coarse_iterations": int(wr.coarse_iterations),
+                      "surrogate_iterations": int(wr.surrogate_iterations), "full_sweeps": int(wr.plain_sweeps),
+                      "judge_error": round(float(wr.judge_error), 5), "fell_back": bool(wr.fell_back),
+                      "seconds": round(t, 4), "speedup_vs_plain": round(t_plain / t, 3),
+                      "max_rel_dy_vs_plain": dy, "converged": bool(wr.total.converged)}
+
+    warm("warm_coarse_solve", None, use_net=False, phase1_max_iter=0)
+    warm("warm_coarse_solve_coarse_sweep_phase", None, use_net=False)
+    # train the network on other setups (untimed)
+    X = torch.empty((n_setups * n_iter, 4, V), device=dev)
+    T = torch.empty((n_setups * n_iter, V), device=dev)
+    W = torch.empty((n_setups * n_iter, V), device=dev)
     t0 = time.perf_counter()
-    rep, hist = sw.iterate(nH, case.chem, srcs, y, tol=tol, max_iter=300)
+    for k in range(n_setups):
+        c = wl.hii_random(n, case.nside, seed=100 + k)
+        sk = art.ArtSweep(c.nH.shape, c.nside, 1, field_form=art.ART_FIELDS_EPS, dx_cm=c.chem["dx"])
+        yk = torch.as_tensor(c.y0, dtype=torch.float64, device=dev).clone()
+        sk.surrogate_collect(torch.as_tensor(c.nH, dtype=torch.float64, device=dev), c.chem,
+                             [(p[0], p[1], p[2], q) for p, q in zip(c.pos, c.Q)], yk,
+                             X[k * n_iter:(k + 1) * n_iter], T[k * n_iter:(k + 1) * n_iter], n_iter,
+                             w=W[k * n_iter:(k + 1) * n_iter])
+        sk.close()
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+    t_collect = time.perf_counter() - t0
+    net = art.ArtNet(dilation=(1, 2, 4, 8), lr=3e-4, seed=1)
+    t0 = time.perf_counter()
+    hist = net.train(X, T, (n, n, n), n_setups * n_iter, train_steps, w=W, seed=1)
+    t_train = time.perf_counter() - t0
+    del X, T, W
+    warm("warm_coarse_solve_net_phase", net)
+    out["training"] = {"samples": n_setups * n_iter, "steps": train_steps, "collect_seconds": round(t_collect, 2),
+                       "train_seconds": round(t_train, 2), "loss_first100": float(np.mean(hist[:100])),
+                       "loss_last100": float(np.mean(hist[-100:]))}
+    o = torch.empty(V, device=dev)
+    xin = torch.zeros(4 * V, device=dev)
+    for _ in range(3):
+        net.forward(xin, o, (n, n, n))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        net.forward(xin, o, (n, n, n))
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 20
+    flops = 2.0 * 27 * V * (4 * 32 + 32 * 32 * 2 + 32 * 1)
+    out["network_forward"] = {"ms": round(ms, 4), "tflops_algorithmic": round(flops / (ms * 1e-3) / 1e12, 1),
+                              "note": "4 layers, 128^3 cells, BF16 tcgen05 MMA, FP32 accumulation"}
+    net.close()
     sw.close()
-    return {"workload": "128^3 HII region, N_side 8, uniform n_H 1e-3, T 1e4 K, Q 5e48 s^-1 central, 6.6 kpc, "
-                        "FP32 sweep + FP64 balance", "tol": tol, "iterations": int(rep.iterations),
-            "converged": bool(rep.converged), "residual": float(rep.residual), "seconds": round(dt, 4),
-            "start": "plain"}
+    return out
 
 
 def cpu_baseline(case, seg_per_sweep: int, budget_s: float = 12.0) -> dict:

@@ -18,7 +18,8 @@
  *     three; BF16 weights and activations, FP32 accumulation (tensor cores);
  *   - prediction J^in = J_c exp(o); training target t = ln(J^in/J_c) on the
  *     plain sweep's J^in (logarithms clamped at ln eps_ref - 69); loss
- *     mean((o - t)^2); optimizer Adam with bias-corrected moments and FP32
+ *     mean(w (o - t)^2) with cell weights w = J^in / mean J^in (or 1);
+ *     optimizer Adam with bias-corrected moments and FP32
  *     master weights.
  * Parameters (FP32, "params layout"): for each layer l = 0..3, W_l as
  * [27][c_out][c_in] (tap t = 9 (dz+1) + 3 (dy+1) + (dx+1), offsets
@@ -78,21 +79,22 @@ art_status art_net_forward(art_net *net, int nx, int ny, int nz, const float *X,
 
 /*
  * Forward and backward pass on one sample (X as above, t device [nz][ny][nx]
- * targets): *loss (host) receives mean((o - t)^2) and grads (host, may be
- * NULL) the gradient of the loss in every parameter (params layout).
- * Synchronizes `stream`.  Errors as art_net_forward.
+ * targets, w device [nz][ny][nx] loss weights or NULL for 1): *loss (host)
+ * receives mean(w (o - t)^2) and grads (host, may be NULL) the gradient of
+ * the loss in every parameter (params layout).  Synchronizes `stream`.
+ * Errors as art_net_forward.
  */
-art_status art_net_gradients(art_net *net, int nx, int ny, int nz, const float *X, const float *t, double *loss,
-                             float *grads, void *stream);
+art_status art_net_gradients(art_net *net, int nx, int ny, int nz, const float *X, const float *t, const float *w,
+                             double *loss, float *grads, void *stream);
 
 /*
- * One Adam step on one sample: forward, backward, update of the master
- * weights and of their BF16 copies.  *loss (host, may be NULL) receives the
+ * One Adam step on one sample (X, t, w as in art_net_gradients): forward,
+ * backward, update of the master weights and of their BF16 copies.  *loss (host, may be NULL) receives the
  * loss before the step; reading it synchronizes `stream`.  Errors as
  * art_net_forward.
  */
-art_status art_net_train_step(art_net *net, int nx, int ny, int nz, const float *X, const float *t, double *loss,
-                              void *stream);
+art_status art_net_train_step(art_net *net, int nx, int ny, int nz, const float *X, const float *t, const float *w,
+                              double *loss, void *stream);
 
 /*
  * Training sample of the solver state y (device [z][y][x] doubles) on the
@@ -108,13 +110,40 @@ art_status art_surrogate_sample(art_ctx *ctx, const art_chem *chem, const double
                                 int coarse_factor, int coarse_nside, float *X, float *t, float *jin, float *jc,
                                 void *stream);
 
+/*
+ * Training data from the plain iteration: runs n_iter iterations of
+ * art_iterate_ionization from the state y (device, updated in place) and
+ * records, for every iteration k, the sample of the state the iteration
+ * starts from: inputs X + k * 4V (layout [4][V]), target t + k * V and loss
+ * weights w + k * V (J^in / mean J^in; w may be NULL), target and weights
+ * taken on the J^in of that iteration's own sweep.  X, t, w are device arrays
+ * of n_iter samples.  Stream-ordered except for one host
+ * synchronization per iteration.  Errors as art_surrogate_sample.
+ */
+art_status art_surrogate_collect(art_ctx *ctx, const art_chem *chem, const double *nH, const art_source *src,
+                                 int n_src, double *y, int n_iter, int coarse_factor, int coarse_nside, float *X,
+                                 float *t, float *w, void *stream);
+
+/*
+ * Adam steps over a set of n_samples samples of one grid shape (X device
+ * [n_samples][4][V], t and w device [n_samples][V], w may be NULL): `steps` steps, one sample per
+ * step, in epochs of a permutation drawn from `seed` (splitmix64 keys,
+ * deterministic).  loss_hist (host, may be NULL) receives the loss of every
+ * step (reading it synchronizes once at the end).  Errors as
+ * art_net_train_step.
+ */
+art_status art_net_train(art_net *net, int nx, int ny, int nz, int n_samples, const float *X, const float *t,
+                         const float *w, int steps, uint64_t seed, double *loss_hist, void *stream);
+
 typedef struct {
     int coarse_factor;     /* mesh coarsening of the coarse sweep, default 4 */
     int coarse_nside;      /* N_side of the coarse sweep, default 4 */
     int use_net;           /* 1 (default): J^in = J_c exp(net); 0: J^in = J_c (coarse sweep alone) */
     int phase1_max_iter;   /* surrogate iterations at most, default 40 */
-    double phase1_tol;     /* surrogate phase ends below this residual, default 1e-4 */
+    double phase1_tol;     /* surrogate phase ends below this residual, default 1e-3 */
     double judge_tol;      /* fall back when sum|J_s - J|/sum J exceeds this, default 0.3 */
+    int coarse_solve;      /* 1 (default): start from the coarse-mesh solution (see below) */
+    double coarse_tol;     /* residual of the coarse-mesh solve, default 1e-4 */
 } art_warm_options;
 
 typedef struct {
@@ -123,6 +152,7 @@ typedef struct {
     int32_t plain_sweeps;         /* full sweeps run (judge included) */
     int32_t fell_back;            /* 1 if the judge restarted from the initial state */
     double judge_error;           /* sum|J_s - J| / sum J at the end of the surrogate phase */
+    int32_t coarse_iterations;    /* iterations of the coarse-mesh solve */
 } art_warm_report;
 
 /* Fill `opt` with the defaults above. */
@@ -130,13 +160,17 @@ art_status art_warm_options_default(art_warm_options *opt);
 
 /*
  * The iteration of art_iterate_ionization (same arguments, same fixed point
- * and stopping rule), warm-started: while the residual is above phase1_tol
- * (and for at most phase1_max_iter iterations) J^in comes from the surrogate
- * (coarse sweep plus network) instead of the full sweep; then one full sweep
- * judges the surrogate on the current state; if its error exceeds judge_tol
- * the state is reset to the initial y (fell_back = 1); plain iterations then
- * run to tol.  net may be NULL only with use_net = 0.  Errors as
- * art_iterate_ionization.
+ * and stopping rule), warm-started.  With coarse_solve, the whole RT /
+ * balance problem is first solved on the mesh coarsened by coarse_factor
+ * (N_side coarse_nside; n_H and y block means, sources at the same place) to
+ * coarse_tol, and the fine iteration starts from that neutral fraction
+ * (injection).  Then, while the residual is above phase1_tol (and for at
+ * most phase1_max_iter iterations), J^in comes from the surrogate (coarse
+ * sweep of the current state, corrected by the network when use_net) instead
+ * of the full sweep; one full sweep then judges the surrogate on the current
+ * state; if its error exceeds judge_tol the state is reset to the initial y
+ * (fell_back = 1); plain iterations run to tol.  net may be NULL only with
+ * use_net = 0.  Errors as art_iterate_ionization.
  */
 art_status art_iterate_ionization_warm(art_ctx *ctx, art_net *net, const art_chem *chem, const double *nH,
                                        const art_source *src, int n_src, double tol, int max_iter,

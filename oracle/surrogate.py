@@ -21,7 +21,7 @@ convergence, App. D); it is specified here:
   channels, ReLU after the first three, one output channel o.
 * Prediction J^in = J_c exp(o); training target t = ln(J^in / J_c) on the
   plain sweep's J^in (logarithms clamped at ln eps_ref - 69); loss
-  mean((o - t)^2).
+  mean(w (o - t)^2) with cell weights w = J^in / mean(J^in) (or 1).
 * Optimizer: Adam (Kingma & Ba 2015), bias-corrected moments.
 
 ``bf16_mode=True`` rounds weights, activations and back-propagated gradients
@@ -132,15 +132,24 @@ def forward(X, params, dil, bf16_mode=False):
     return o, acts
 
 
-def loss(o, t):
-    return float(np.mean((o - t) ** 2))
+def loss(o, t, w=None):
+    """mean(w (o - t)^2), w = 1 when not given."""
+    d2 = (o - t) ** 2
+    return float(np.mean(d2 if w is None else w * d2))
 
 
-def backward(o, t, acts, params, dil, bf16_mode=False):
-    """Gradients of loss(o, t) in every weight and bias (list of (gW, gb))."""
+def weights(jin):
+    """Per-cell loss weights J^in / mean(J^in): the loss then measures the
+    intensity-weighted error that the surrogate's judge measures."""
+    m = float(np.mean(jin))
+    return jin / m if m > 0 else np.ones_like(jin)
+
+
+def backward(o, t, acts, params, dil, bf16_mode=False, w=None):
+    """Gradients of loss(o, t, w) in every weight and bias (list of (gW, gb))."""
     r = bf16 if bf16_mode else (lambda v: v)
     V = o.size
-    g = (2.0 / V) * (o - t)[None]
+    g = (2.0 / V) * ((o - t) if w is None else w * (o - t))[None]
     grads = [None] * 4
     for i in range(3, -1, -1):
         W, _ = params[i]

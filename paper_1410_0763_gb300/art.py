@@ -68,12 +68,13 @@ class ArtNetOptions(C.Structure):
 
 class ArtWarmOptions(C.Structure):
     _fields_ = [("coarse_factor", C.c_int), ("coarse_nside", C.c_int), ("use_net", C.c_int),
-                ("phase1_max_iter", C.c_int), ("phase1_tol", C.c_double), ("judge_tol", C.c_double)]
+                ("phase1_max_iter", C.c_int), ("phase1_tol", C.c_double), ("judge_tol", C.c_double),
+                ("coarse_solve", C.c_int), ("coarse_tol", C.c_double)]
 
 
 class ArtWarmReport(C.Structure):
     _fields_ = [("total", ArtIterReport), ("surrogate_iterations", C.c_int32), ("plain_sweeps", C.c_int32),
-                ("fell_back", C.c_int32), ("judge_error", C.c_double)]
+                ("fell_back", C.c_int32), ("judge_error", C.c_double), ("coarse_iterations", C.c_int32)]
 
 
 ART_NET_PARAMS = 59713
@@ -135,9 +136,13 @@ def load() -> C.CDLL:
         lib.art_net_get_params.argtypes = [P, P]
         lib.art_net_set_params.argtypes = [P, P]
         lib.art_net_forward.argtypes = [P, C.c_int, C.c_int, C.c_int, P, P, P]
-        lib.art_net_gradients.argtypes = [P, C.c_int, C.c_int, C.c_int, P, P, C.POINTER(C.c_double), P, P]
-        lib.art_net_train_step.argtypes = [P, C.c_int, C.c_int, C.c_int, P, P, C.POINTER(C.c_double), P]
+        lib.art_net_gradients.argtypes = [P, C.c_int, C.c_int, C.c_int, P, P, P, C.POINTER(C.c_double), P, P]
+        lib.art_net_train_step.argtypes = [P, C.c_int, C.c_int, C.c_int, P, P, P, C.POINTER(C.c_double), P]
         lib.art_surrogate_sample.argtypes = [P, C.POINTER(ArtChem), P, P, C.c_int, C.c_int, P, P, P, P, P]
+        lib.art_surrogate_collect.argtypes = [P, C.POINTER(ArtChem), P, C.POINTER(ArtSource), C.c_int, P, C.c_int,
+                                              C.c_int, C.c_int, P, P, P, P]
+        lib.art_net_train.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P, C.c_int, C.c_uint64,
+                                      C.POINTER(C.c_double), P]
         lib.art_warm_options_default.argtypes = [C.POINTER(ArtWarmOptions)]
         lib.art_iterate_ionization_warm.argtypes = [P, P, C.POINTER(ArtChem), P, C.POINTER(ArtSource), C.c_int,
                                                     C.c_double, C.c_int, C.POINTER(ArtWarmOptions), P,
@@ -145,6 +150,7 @@ def load() -> C.CDLL:
         for f in ("art_net_options_default", "art_net_create", "art_net_destroy", "art_net_get_params",
                   "art_net_set_params", "art_net_forward", "art_net_gradients", "art_net_train_step",
                   "art_surrogate_sample", "art_warm_options_default", "art_iterate_ionization_warm",
+                  "art_surrogate_collect", "art_net_train",
                   "art_batch_create", "art_autotune"):
             getattr(lib, f).restype = C.c_int
         for f in ("art_point_sources", "art_iterate_ionization", "art_sweep_noalloc", "art_measure_pipes", "art_band_integral", "art_profile_enable", "art_profile_read", "art_options_default", "art_create", "art_count_segments", "art_destroy", "art_get_stats", "art_set_fields",
@@ -426,8 +432,8 @@ class ArtSweep:
                        chem["dnu"])
 
     def iterate_warm(self, net, nH, chem: dict, sources, y, tol=1e-6, max_iter=200, coarse_factor=4,
-                     coarse_nside=4, use_net=True, phase1_max_iter=40, phase1_tol=1e-4, judge_tol=0.3,
-                     stream=None):
+                     coarse_nside=4, use_net=True, phase1_max_iter=40, phase1_tol=1e-3, judge_tol=0.3,
+                     coarse_solve=True, coarse_tol=1e-4, stream=None):
         """The iteration of `iterate`, warm-started by the surrogate (coarse sweep + network).
         Returns (warm report, residual history); raises ArtError unless converged."""
         npp, nd_, _n = _ptr(nH, np.float64, self.ncell)
@@ -438,6 +444,7 @@ class ArtSweep:
         load().art_warm_options_default(C.byref(w))
         w.coarse_factor, w.coarse_nside, w.use_net = int(coarse_factor), int(coarse_nside), 1 if use_net else 0
         w.phase1_max_iter, w.phase1_tol, w.judge_tol = int(phase1_max_iter), float(phase1_tol), float(judge_tol)
+        w.coarse_solve, w.coarse_tol = 1 if coarse_solve else 0, float(coarse_tol)
         src = _sources(sources)
         hist = (C.c_double * max_iter)()
         rep = ArtWarmReport()
@@ -468,6 +475,24 @@ class ArtSweep:
                                                        C.c_void_p(yp), int(coarse_factor), int(coarse_nside),
                                                        *[C.c_void_p(p_) for p_ in ptrs],
                                                        C.c_void_p(_stream(stream))))
+
+    def surrogate_collect(self, nH, chem: dict, sources, y, X, t, n_iter, w=None, coarse_factor=4,
+                          coarse_nside=4, stream=None):
+        """Run n_iter plain iterations from y (device FP64, updated) recording one training sample per
+        iteration into X (device float32 [n_iter][4][V]), t and w ([n_iter][V], w optional)."""
+        npp, _, _n = _ptr(nH, np.float64, self.ncell)
+        yp, yd, _y = _ptr(y, np.float64, self.ncell)
+        xp, xd, _x = _ptr(X, np.float32, n_iter * 4 * self.ncell)
+        tp, td, _t = _ptr(t, np.float32, n_iter * self.ncell)
+        wp, wd, _w = _ptr(w, np.float32, n_iter * self.ncell)
+        if not (yd and xd and td) or (w is not None and not wd):
+            raise TypeError("surrogate_collect takes device buffers")
+        src = _sources(sources)
+        _check(self._ctx, load().art_surrogate_collect(self._ctx, C.byref(self._chem(chem)), C.c_void_p(npp), src,
+                                                        len(sources), C.c_void_p(yp), int(n_iter),
+                                                        int(coarse_factor), int(coarse_nside), C.c_void_p(xp),
+                                                        C.c_void_p(tp), C.c_void_p(wp),
+                                                        C.c_void_p(_stream(stream))))
 
     def set_fields(self, kappa, src, stream=None):
         n = self.ncell * self.nbins
@@ -573,21 +598,37 @@ class ArtNet:
                                            C.c_void_p(self._dev(o, V, "o")), C.c_void_p(_stream(stream))))
         return o
 
-    def gradients(self, X, t, shape, stream=None):
+    def gradients(self, X, t, shape, w=None, stream=None):
         nz, ny, nx = shape
         V = nx * ny * nz
         loss = C.c_double(0.0)
         g = np.empty(ART_NET_PARAMS, dtype=np.float32)
+        wp = self._dev(w, V, "w") if w is not None else 0
         self._check(load().art_net_gradients(self._net, nx, ny, nz, C.c_void_p(self._dev(X, 4 * V, "X")),
-                                             C.c_void_p(self._dev(t, V, "t")), C.byref(loss), g.ctypes.data,
-                                             C.c_void_p(_stream(stream))))
+                                             C.c_void_p(self._dev(t, V, "t")), C.c_void_p(wp), C.byref(loss),
+                                             g.ctypes.data, C.c_void_p(_stream(stream))))
         return loss.value, g
 
-    def train_step(self, X, t, shape, want_loss=True, stream=None):
+    def train(self, X, t, shape, n_samples, steps, w=None, seed=0, stream=None):
+        """`steps` Adam steps over n_samples samples (device X [n][4][V], t and w [n][V]); returns the
+        loss per step."""
+        nz, ny, nx = shape
+        V = nx * ny * nz
+        hist = np.zeros(max(steps, 1), dtype=np.float64)
+        wp = self._dev(w, n_samples * V, "w") if w is not None else 0
+        self._check(load().art_net_train(self._net, nx, ny, nz, int(n_samples),
+                                         C.c_void_p(self._dev(X, n_samples * 4 * V, "X")),
+                                         C.c_void_p(self._dev(t, n_samples * V, "t")), C.c_void_p(wp), int(steps),
+                                         int(seed),
+                                         hist.ctypes.data_as(C.POINTER(C.c_double)), C.c_void_p(_stream(stream))))
+        return hist[:steps]
+
+    def train_step(self, X, t, shape, w=None, want_loss=True, stream=None):
         nz, ny, nx = shape
         V = nx * ny * nz
         loss = C.c_double(float("nan"))
+        wp = self._dev(w, V, "w") if w is not None else 0
         self._check(load().art_net_train_step(self._net, nx, ny, nz, C.c_void_p(self._dev(X, 4 * V, "X")),
-                                              C.c_void_p(self._dev(t, V, "t")),
+                                              C.c_void_p(self._dev(t, V, "t")), C.c_void_p(wp),
                                               C.byref(loss) if want_loss else None, C.c_void_p(_stream(stream))))
         return loss.value

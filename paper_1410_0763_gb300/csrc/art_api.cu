@@ -733,7 +733,7 @@ art_status art_destroy(art_ctx *ctx)
                     ctx->it.jin, ctx->it.jsur, ctx->it.resid, ctx->it.src};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    void *sur[] = {ctx->sur.kc, ctx->sur.ec, ctx->sur.jc, ctx->sur.o, ctx->sur.eref};
+    void *sur[] = {ctx->sur.kc, ctx->sur.ec, ctx->sur.jc, ctx->sur.o, ctx->sur.eref, ctx->sur.nHc, ctx->sur.yc};
     for (void *p : sur)
         if (p) cudaFree(p);
     if (ctx->coarse) art_destroy(ctx->coarse);

@@ -38,6 +38,7 @@ struct art_sur_bufs {
     long long n = 0;
     int f = 0, nside = 0;
     void *kc = nullptr, *ec = nullptr, *jc = nullptr, *o = nullptr, *eref = nullptr;
+    double *nHc = nullptr, *yc = nullptr;   // coarse-mesh solve of the warm start
 };
 
 struct art_ctx {

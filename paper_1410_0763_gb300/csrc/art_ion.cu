@@ -340,11 +340,50 @@ BalArgs balance_args(art_ctx *ctx, const art_chem *ch, const double *nH, double 
     return ba;
 }
 
+// Block means over f^3 cells of two FP64 fields (coarse-mesh n_H and y).
+__global__ void mean_d_kernel(const double *__restrict__ a, const double *__restrict__ b, int nx, int ny, int nz, int f,
+                              double *__restrict__ ac, double *__restrict__ bc)
+{
+    const int cx = nx / f, cy = ny / f, cz = nz / f;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)cx * cy * cz) return;
+    const int X = (int)(i % cx), Y = (int)((i / cx) % cy), Z = (int)(i / ((long long)cx * cy));
+    double sa = 0.0, sb = 0.0;
+    for (int k = 0; k < f; ++k)
+        for (int j = 0; j < f; ++j)
+            for (int l = 0; l < f; ++l) {
+                const long long v = ((long long)(Z * f + k) * ny + (Y * f + j)) * nx + (long long)X * f + l;
+                sa += a[v];
+                sb += b[v];
+            }
+    const double inv = 1.0 / ((double)f * f * f);
+    ac[i] = sa * inv;
+    bc[i] = sb * inv;
+}
+
+// Every fine cell takes its coarse cell's value.
+__global__ void inject_d_kernel(const double *__restrict__ c, int nx, int ny, int nz, int f, double *__restrict__ out)
+{
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= (long long)nx * ny * nz) return;
+    const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
+    out[v] = c[((long long)(z / f) * (ny / f) + y / f) * (nx / f) + x / f];
+}
+
+// Where the iteration records training samples (art_surrogate_collect).
+struct SampleSink {
+    float *X, *t, *w;
+    int n;
+};
+
 // The RT / balance fixed-point iteration; with `warm`, J^in comes from the
-// surrogate until its phase ends, then from plain sweeps.
+// surrogate until its phase ends, then from plain sweeps.  With `sink`, every
+// plain iteration records the surrogate inputs of its starting state and the
+// target from its sweep.
 art_status iterate_impl(art_ctx *ctx, art_net *net, const art_chem *ch, const double *nH, const art_source *src,
                         int n_src, double tol, int max_iter, const art_warm_options *warm, double *y,
-                        double *resid_hist, art_iter_report *rep, art_warm_report *wrep, cudaStream_t st)
+                        double *resid_hist, art_iter_report *rep, art_warm_report *wrep, cudaStream_t st,
+                        SampleSink *sink = nullptr)
 {
     if (!ctx) return ART_E_INVALID;
     art_status s = check_iteration_context(ctx, ch, "art_iterate_ionization");
@@ -375,13 +414,38 @@ art_status iterate_impl(art_ctx *ctx, art_net *net, const art_chem *ch, const do
     }
     ICK(ctx, cudaMemcpyAsync(d_sig, &ch->sigma0, sizeof(double), cudaMemcpyHostToDevice, st));
 
-    BalArgs ba = balance_args(ctx, ch, nH, y);
     const int nt = 256;
     const unsigned nb = (unsigned)((n + nt - 1) / nt);
-    balance_kernel<<<nb, nt, 0, st>>>(ba);   // kappa, eps of the initial state
+    if (warm) ICK(ctx, cudaMemcpyAsync(B.y0, y, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    int coarse_it = 0;
+    if (warm && warm->coarse_solve) {
+        // the whole problem on the coarse mesh; its neutral fraction starts the fine iteration
+        const int f = warm->coarse_factor;
+        if ((s = artnet_coarse(ctx, f, warm->coarse_nside)) != ART_OK) return s;
+        art_sur_bufs &S = ctx->sur;
+        const long long nc = n / ((long long)f * f * f);
+        mean_d_kernel<<<(unsigned)((nc + nt - 1) / nt), nt, 0, st>>>(nH, y, ctx->grid.nx, ctx->grid.ny, ctx->grid.nz, f,
+                                                                     S.nHc, S.yc);
+        ICK(ctx, cudaGetLastError());
+        std::vector<art_source> csrc(src, src + n_src);
+        for (art_source &c : csrc) {
+            c.x /= f;
+            c.y /= f;
+            c.z /= f;
+        }
+        art_iter_report cr{};
+        const art_status cs = iterate_impl(ctx->coarse, nullptr, ch, S.nHc, csrc.data(), n_src, warm->coarse_tol,
+                                           max_iter, nullptr, S.yc, nullptr, &cr, nullptr, st);
+        if (cs != ART_OK && cs != ART_E_NOT_CONVERGED)
+            return art_fail(ctx, cs, std::string("warm start: coarse solve: ") + art_last_error(ctx->coarse));
+        coarse_it = cr.iterations;
+        inject_d_kernel<<<nb, nt, 0, st>>>(S.yc, ctx->grid.nx, ctx->grid.ny, ctx->grid.nz, f, y);
+        ICK(ctx, cudaGetLastError());
+    }
+    BalArgs ba = balance_args(ctx, ch, nH, y);
+    balance_kernel<<<nb, nt, 0, st>>>(ba);   // kappa, eps of the starting state
     ICK(ctx, cudaGetLastError());
     ba.solve = 1;
-    if (warm) ICK(ctx, cudaMemcpyAsync(B.y0, y, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
 
     bool phase1 = warm != nullptr && warm->phase1_max_iter > 0;
     bool have_jin = false;
@@ -397,9 +461,20 @@ art_status iterate_impl(art_ctx *ctx, art_net *net, const art_chem *ch, const do
             if (s != ART_OK) return s;
             ++it1;
         } else {
+            if (sink && it <= sink->n) {
+                const long long V = n;
+                float *Xk = sink->X + (long long)(it - 1) * 4 * V;
+                s = artnet_surrogate(ctx, nullptr, 0, warm->coarse_factor, warm->coarse_nside, B.kap, B.eps, y,
+                                     nullptr, Xk, B.jsur, st);
+                if (s != ART_OK) return s;
+            }
             if ((s = art_internal_layout(ctx, B.kap, B.eps, st)) != ART_OK) return s;
             if ((s = art_internal_sweep(ctx, nullptr, B.jin, nullptr, st)) != ART_OK) return s;
             ++sweeps;
+            if (sink && it <= sink->n) {
+                if ((s = artnet_target(ctx, B.jin, B.jsur, sink->t + (long long)(it - 1) * n, st))) return s;
+                if (sink->w && (s = artnet_weights(ctx, B.jin, sink->w + (long long)(it - 1) * n, st))) return s;
+            }
         }
         ICK(ctx, cudaMemsetAsync(B.resid, 0, sizeof(unsigned long long), st));
         balance_kernel<<<nb, nt, 0, st>>>(ba);
@@ -448,6 +523,7 @@ art_status iterate_impl(art_ctx *ctx, art_net *net, const art_chem *ch, const do
         wrep->plain_sweeps = sweeps;
         wrep->fell_back = fell_back;
         wrep->judge_error = judge;
+        wrep->coarse_iterations = coarse_it;
     }
     return conv ? ART_OK : art_fail(ctx, ART_E_NOT_CONVERGED, "art_iterate_ionization: max_iter reached");
 }
@@ -471,8 +547,10 @@ art_status art_warm_options_default(art_warm_options *o)
     o->coarse_nside = 4;
     o->use_net = 1;
     o->phase1_max_iter = 40;
-    o->phase1_tol = 1e-4;
+    o->phase1_tol = 1e-3;
     o->judge_tol = 0.3;
+    o->coarse_solve = 1;
+    o->coarse_tol = 1e-4;
     return ART_OK;
 }
 
@@ -486,7 +564,7 @@ art_status art_iterate_ionization_warm(art_ctx *ctx, art_net *net, const art_che
     if (wopt) w = *wopt;
     else art_warm_options_default(&w);
     if (w.coarse_factor < 1 || w.coarse_nside < 1 || w.phase1_max_iter < 0 || !(w.phase1_tol > 0.0) ||
-        !(w.judge_tol >= 0.0) || (w.use_net && !net))
+        !(w.judge_tol >= 0.0) || (w.use_net && !net) || (w.coarse_solve && !(w.coarse_tol > 0.0)))
         return art_fail(ctx, ART_E_INVALID, "art_iterate_ionization_warm: bad warm-start options");
     art_iter_report r{};
     art_status s = iterate_impl(ctx, net, ch, nH, src, n_src, tol, max_iter, &w, y, resid_hist, &r, rep,
@@ -521,6 +599,26 @@ art_status art_surrogate_sample(art_ctx *ctx, const art_chem *ch, const double *
     if ((s = art_internal_sweep(ctx, nullptr, jf, nullptr, st)) != ART_OK) return s;
     if (t && (s = artnet_target(ctx, jf, jcf, t, st)) != ART_OK) return s;
     return ART_OK;
+}
+
+art_status art_surrogate_collect(art_ctx *ctx, const art_chem *ch, const double *nH, const art_source *src, int n_src,
+                                 double *y, int n_iter, int coarse_factor, int coarse_nside, float *X, float *t,
+                                 float *w, void *stream)
+{
+    if (!ctx) return ART_E_INVALID;
+    if (!X || !t || n_iter < 1) return art_fail(ctx, ART_E_INVALID, "art_surrogate_collect: bad argument");
+    art_warm_options wo;
+    art_warm_options_default(&wo);
+    wo.coarse_factor = coarse_factor;
+    wo.coarse_nside = coarse_nside;
+    wo.use_net = 0;
+    wo.phase1_max_iter = 0;
+    wo.coarse_solve = 0;
+    SampleSink sink{X, t, w, n_iter};
+    art_iter_report r{};
+    const art_status s = iterate_impl(ctx, nullptr, ch, nH, src, n_src, 1e-300, n_iter, &wo, y, nullptr, &r, nullptr,
+                                      static_cast<cudaStream_t>(stream), &sink);
+    return s == ART_E_NOT_CONVERGED ? ART_OK : s;
 }
 
 }  // extern "C"

@@ -263,12 +263,12 @@ art_status wgrad(art_net *n, const bf16 *g, const bf16 *a, int l, cudaStream_t s
 }
 
 // forward + loss + backward: gradients into n->grad, loss into n->loss (device)
-art_status forward_backward(art_net *n, const float *t, cudaStream_t st)
+art_status forward_backward(art_net *n, const float *t, const float *w, cudaStream_t st)
 {
     art_status s;
     if ((s = forward16(n, n->o, st))) return s;
     const int nb = (int)((n->V + 255) / 256);
-    loss_grad_kernel<<<nb, 256, 0, st>>>(n->o, t, n->V, n->g16, n->lpart);
+    loss_grad_kernel<<<nb, 256, 0, st>>>(n->o, t, w, n->V, n->g16, n->lpart);
     NCK(n, cudaGetLastError());
     sum_partials_kernel<<<1, 32, 0, st>>>(n->lpart, nb, 1.0 / (double)n->V, n->loss);
     NCK(n, cudaGetLastError());
@@ -315,8 +315,7 @@ art_status artnet_forward(art_net *n, float *o, cudaStream_t st) { return forwar
 art_status artnet_check(art_net *n, cudaStream_t st) { return check_err(n, st); }
 const char *artnet_error(const art_net *n) { return n ? n->err.c_str() : "null network"; }
 
-art_status artnet_surrogate(art_ctx *ctx, art_net *net, int use_net, int f, int nside_c, const float *kap,
-                            const float *eps, const double *y, float *jin, float *X32, float *jc_fine, cudaStream_t st)
+art_status artnet_coarse(art_ctx *ctx, int f, int nside_c)
 {
     const int nx = ctx->grid.nx, ny = ctx->grid.ny, nz = ctx->grid.nz;
     if (f < 1 || nx % f || ny % f || nz % f || nside_c < 1)
@@ -335,9 +334,10 @@ art_status artnet_surrogate(art_ctx *ctx, art_net *net, int use_net, int f, int 
         if (s != ART_OK) return art_fail(ctx, s, "surrogate: coarse sweep context could not be created");
         S.f = f;
         S.nside = nside_c;
+        S.n = 0;   // coarse buffers follow the coarse mesh
     }
     if (S.n != V) {
-        void *ptrs[] = {S.kc, S.ec, S.jc, S.o, S.eref};
+        void *ptrs[] = {S.kc, S.ec, S.jc, S.o, S.eref, S.nHc, S.yc};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         const int keep_f = S.f, keep_nside = S.nside;
@@ -346,17 +346,30 @@ art_status artnet_surrogate(art_ctx *ctx, art_net *net, int use_net, int f, int 
         S.nside = keep_nside;
         if (cudaMalloc(&S.kc, Vc * 4) != cudaSuccess || cudaMalloc(&S.ec, Vc * 4) != cudaSuccess ||
             cudaMalloc(&S.jc, Vc * 4) != cudaSuccess || cudaMalloc(&S.o, V * 4) != cudaSuccess ||
-            cudaMalloc(&S.eref, 16) != cudaSuccess) {
+            cudaMalloc(&S.eref, 16) != cudaSuccess || cudaMalloc(&S.nHc, Vc * 8) != cudaSuccess ||
+            cudaMalloc(&S.yc, Vc * 8) != cudaSuccess) {
             cudaGetLastError();
             return art_fail(ctx, ART_E_OOM, "surrogate: scratch allocation failed");
         }
         S.n = V;
     }
+    return ART_OK;
+}
+
+art_status artnet_surrogate(art_ctx *ctx, art_net *net, int use_net, int f, int nside_c, const float *kap,
+                            const float *eps, const double *y, float *jin, float *X32, float *jc_fine, cudaStream_t st)
+{
+    const int nx = ctx->grid.nx, ny = ctx->grid.ny, nz = ctx->grid.nz;
+    art_status s = artnet_coarse(ctx, f, nside_c);
+    if (s != ART_OK) return s;
+    const long long V = ctx->ncell;
+    const long long Vc = V / ((long long)f * f * f);
+    art_sur_bufs &S = ctx->sur;
     const int nt = 256;
     restrict_kernel<<<(unsigned)((Vc + nt - 1) / nt), nt, 0, st>>>(kap, eps, nx, ny, nz, f, static_cast<float *>(S.kc),
                                                                    static_cast<float *>(S.ec));
     if (cudaGetLastError() != cudaSuccess) return art_fail(ctx, ART_E_CUDA, "surrogate: restrict launch failed");
-    art_status s = art_internal_layout(ctx->coarse, S.kc, S.ec, st);
+    s = art_internal_layout(ctx->coarse, S.kc, S.ec, st);
     if (s == ART_OK) s = art_internal_sweep(ctx->coarse, nullptr, S.jc, nullptr, st);
     if (s != ART_OK) return art_fail(ctx, s, std::string("surrogate: coarse sweep: ") + art_last_error(ctx->coarse));
     unsigned int *eref = static_cast<unsigned int *>(S.eref);
@@ -403,6 +416,24 @@ art_status artnet_target(art_ctx *ctx, const float *jin, const float *jc_fine, f
     target_kernel<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(jin, jc_fine, V,
                                                                static_cast<const unsigned int *>(ctx->sur.eref), t);
     if (cudaGetLastError() != cudaSuccess) return art_fail(ctx, ART_E_CUDA, "surrogate: target launch failed");
+    return ART_OK;
+}
+
+art_status artnet_weights(art_ctx *ctx, const float *jin, float *w, cudaStream_t st)
+{
+    const long long V = ctx->ncell;
+    const int nb = 256;
+    double *part = nullptr;
+    if (cudaMalloc(&part, nb * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return art_fail(ctx, ART_E_OOM, "surrogate: weight buffer");
+    }
+    sum_kernel<<<nb, 256, 0, st>>>(jin, V, part);
+    weight_scale_kernel<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(jin, V, part, nb, w);
+    const cudaError_t e = cudaGetLastError();
+    cudaStreamSynchronize(st);   // the partial buffer is freed below
+    cudaFree(part);
+    if (e != cudaSuccess) return art_fail(ctx, ART_E_CUDA, "surrogate: weight launch failed");
     return ART_OK;
 }
 
@@ -558,8 +589,8 @@ art_status art_net_forward(art_net *n, int nx, int ny, int nz, const float *X, f
     return forward16(n, o, st);
 }
 
-art_status art_net_gradients(art_net *n, int nx, int ny, int nz, const float *X, const float *t, double *loss,
-                             float *grads, void *stream)
+art_status art_net_gradients(art_net *n, int nx, int ny, int nz, const float *X, const float *t, const float *w,
+                             double *loss, float *grads, void *stream)
 {
     if (!n) return ART_E_INVALID;
     if (!X || !t || !loss) return nfail(n, ART_E_INVALID, "art_net_gradients: null pointer");
@@ -568,14 +599,71 @@ art_status art_net_gradients(art_net *n, int nx, int ny, int nz, const float *X,
     if (s) return s;
     pack_input_kernel<<<(unsigned)((n->V + 255) / 256), 256, 0, st>>>(X, n->V, n->X16);
     NCK(n, cudaGetLastError());
-    if ((s = forward_backward(n, t, st))) return s;
+    if ((s = forward_backward(n, t, w, st))) return s;
     NCK(n, cudaMemcpyAsync(loss, n->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
     if (grads) NCK(n, cudaMemcpyAsync(grads, n->grad, ART_NET_PARAMS * sizeof(float), cudaMemcpyDeviceToHost, st));
     return check_err(n, st);
 }
 
-art_status art_net_train_step(art_net *n, int nx, int ny, int nz, const float *X, const float *t, double *loss,
-                              void *stream)
+art_status art_net_train(art_net *n, int nx, int ny, int nz, int n_samples, const float *X, const float *t,
+                         const float *w, int steps, uint64_t seed, double *loss_hist, void *stream)
+{
+    if (!n) return ART_E_INVALID;
+    if (!X || !t || n_samples < 1 || steps < 0) return nfail(n, ART_E_INVALID, "art_net_train: bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    art_status s = ensure_workspace(n, nx, ny, nz);
+    if (s) return s;
+    const long long V = n->V;
+    double *d_hist = nullptr;
+    if (loss_hist && steps > 0) NCK(n, cudaMalloc(&d_hist, (size_t)steps * sizeof(double)));
+    std::vector<int> order(n_samples);
+    for (int step = 0; step < steps; ++step) {
+        const int k = step % n_samples;
+        if (k == 0) {   // new epoch: order by splitmix64 keys of (seed, epoch, sample)
+            const uint64_t epoch = (uint64_t)(step / n_samples);
+            std::vector<std::pair<uint64_t, int>> key(n_samples);
+            for (int i = 0; i < n_samples; ++i) {
+                uint64_t z = seed * 0x9E3779B97F4A7C15ull + epoch * 0xD1B54A32D192ED03ull + (uint64_t)i;
+                z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+                z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+                key[i] = {z ^ (z >> 31), i};
+            }
+            std::sort(key.begin(), key.end());
+            for (int i = 0; i < n_samples; ++i) order[i] = key[i].second;
+        }
+        const int smp = order[k];
+        pack_input_kernel<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(X + (long long)smp * 4 * V, V, n->X16);
+        if (cudaGetLastError() != cudaSuccess) {
+            if (d_hist) cudaFree(d_hist);
+            return nfail(n, ART_E_CUDA, "art_net_train: launch failed");
+        }
+        if ((s = forward_backward(n, t + (long long)smp * V, w ? w + (long long)smp * V : nullptr, st))) {
+            if (d_hist) cudaFree(d_hist);
+            return s;
+        }
+        if (d_hist) cudaMemcpyAsync(d_hist + step, n->loss, sizeof(double), cudaMemcpyDeviceToDevice, st);
+        n->step += 1;
+        const double c1 = 1.0 - std::pow(n->opt.beta1, n->step), c2 = 1.0 - std::pow(n->opt.beta2, n->step);
+        adam_kernel<<<(ART_NET_PARAMS + 255) / 256, 256, 0, st>>>(n->params, n->m, n->v, n->grad, ART_NET_PARAMS,
+                                                                  (float)n->opt.lr, (float)n->opt.beta1,
+                                                                  (float)n->opt.beta2, (float)n->opt.adam_eps,
+                                                                  (float)c1, (float)c2);
+        if ((s = pack_weights(n, st))) {
+            if (d_hist) cudaFree(d_hist);
+            return s;
+        }
+    }
+    if (d_hist) {
+        cudaError_t e = cudaMemcpyAsync(loss_hist, d_hist, (size_t)steps * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFree(d_hist);
+        if (e != cudaSuccess) return nfail(n, ART_E_CUDA, std::string("art_net_train: ") + cudaGetErrorString(e));
+    }
+    return check_err(n, st);
+}
+
+art_status art_net_train_step(art_net *n, int nx, int ny, int nz, const float *X, const float *t, const float *w,
+                              double *loss, void *stream)
 {
     if (!n) return ART_E_INVALID;
     if (!X || !t) return nfail(n, ART_E_INVALID, "art_net_train_step: null pointer");
@@ -584,7 +672,7 @@ art_status art_net_train_step(art_net *n, int nx, int ny, int nz, const float *X
     if (s) return s;
     pack_input_kernel<<<(unsigned)((n->V + 255) / 256), 256, 0, st>>>(X, n->V, n->X16);
     NCK(n, cudaGetLastError());
-    if ((s = forward_backward(n, t, st))) return s;
+    if ((s = forward_backward(n, t, w, st))) return s;
     n->step += 1;
     const double c1 = 1.0 - std::pow(n->opt.beta1, n->step), c2 = 1.0 - std::pow(n->opt.beta2, n->step);
     adam_kernel<<<(ART_NET_PARAMS + 255) / 256, 256, 0, st>>>(n->params, n->m, n->v, n->grad, ART_NET_PARAMS,

@@ -8,6 +8,9 @@
 
 struct art_ctx;
 
+// The coarse-mesh context (factor f, N_side nside_c) and the surrogate
+// scratch of this context, created on first use.
+art_status artnet_coarse(art_ctx *ctx, int f, int nside_c);
 // Surrogate J^in on the context's grid from the solver fields kappa, eps (FP32
 // per cell width) and the neutral fraction y: coarse sweep (factor f, N_side
 // nside_c), inputs, and (use_net) the network.  Outputs, each optional:
@@ -18,6 +21,8 @@ art_status artnet_surrogate(art_ctx *ctx, art_net *net, int use_net, int f, int 
 // Training target from the sweep's J^in and the prolonged J_c of the last
 // artnet_surrogate call on this context (its eps_ref).
 art_status artnet_target(art_ctx *ctx, const float *jin, const float *jc_fine, float *t, cudaStream_t st);
+// Loss weights w = J / mean(J) over the context's cells (synchronizes st).
+art_status artnet_weights(art_ctx *ctx, const float *jin, float *w, cudaStream_t st);
 // sum |a - b| / sum |b| over the context's cells (synchronizes st).
 art_status artnet_l1(art_ctx *ctx, const float *a, const float *b, double *err, cudaStream_t st);
 // Bounded-wait status of the network's last kernels (synchronizes st).

@@ -554,19 +554,20 @@ __global__ void pack_input_kernel(const float *__restrict__ X, long long V, bf16
     o[1] = reinterpret_cast<const uint4 *>(h)[1];
 }
 
-// Loss partial sums and the output gradient g[v][0] = 2 (o - t) / V (BF16,
-// channels 1..15 zero).
-__global__ void loss_grad_kernel(const float *__restrict__ o, const float *__restrict__ t, long long V,
-                                 bf16 *__restrict__ g, double *__restrict__ partial)
+// Loss partial sums and the output gradient g[v][0] = 2 w (o - t) / V (BF16,
+// channels 1..15 zero); w = 1 when null.
+__global__ void loss_grad_kernel(const float *__restrict__ o, const float *__restrict__ t, const float *__restrict__ w,
+                                 long long V, bf16 *__restrict__ g, double *__restrict__ partial)
 {
     __shared__ double red[256];
     const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double sq = 0.0;
     if (v < V) {
         const float d = o[v] - t[v];
-        sq = (double)d * d;
+        const float wv = w ? w[v] : 1.f;
+        sq = (double)wv * d * d;
         __align__(16) bf16 h[16];
-        h[0] = __float2bfloat16_rn(2.f * d / (float)V);
+        h[0] = __float2bfloat16_rn(2.f * wv * d / (float)V);
 #pragma unroll
         for (int c = 1; c < 16; ++c) h[c] = __float2bfloat16_rn(0.f);
         uint4 *op = reinterpret_cast<uint4 *>(g + v * 16);
@@ -700,6 +701,37 @@ __global__ void predict_kernel(const float *__restrict__ jc, const float *__rest
     const int cx = nx / f, cy = ny / f;
     const float j = jc[((long long)(z / f) * cy + y / f) * cx + x / f];
     jin[v] = o ? j * __expf(o[v]) : j;
+}
+
+// Loss weights w = J / mean(J): per-block sums, then a fixed-order total and
+// the scaling (weight_scale_kernel reads the total on the device).
+__global__ void sum_kernel(const float *__restrict__ a, long long n, double *__restrict__ part)
+{
+    __shared__ double r[256];
+    double s = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        s += (double)a[i];
+    r[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) r[threadIdx.x] += r[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = r[0];
+}
+
+__global__ void weight_scale_kernel(const float *__restrict__ j, long long n, const double *__restrict__ part, int nparts,
+                                    float *__restrict__ w)
+{
+    __shared__ double mean;
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < nparts; ++i) s += part[i];
+        mean = s / (double)n;
+    }
+    __syncthreads();
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) w[i] = mean > 0.0 ? (float)((double)j[i] / mean) : 1.f;
 }
 
 // sum |a - b| and sum |b| in double, per block (fixed-order final sum on the host side kernel).

@@ -148,3 +148,19 @@ def hii_region(n: int = 128, nside: int = 8, box_kpc: float = 6.6, nH: float = 1
     pos = np.array([[n / 2, n / 2, n / 2]]) if source_at == "center" else np.array([[0.0, 0.0, 0.0]])
     return HIICase("hii_region", nside, n, np.full((n, n, n), nH), np.full((n, n, n), 1.0 - x0),
                    pos, np.array([Q]), chem_constants(1e4, dx), 1e-6, box_kpc * KPC)
+
+
+def hii_random(n: int = 128, nside: int = 8, seed: int = 100, box_kpc: float = 6.6, nH_mean: float = 1e-3,
+               x0: float = 1e-4) -> HIICase:
+    """Surrogate training setup: lognormal density (sigma uniform in [0, 1.5],
+    P(k) ~ k^-3, mean nH_mean), 1-8 sources uniform in the box with Q uniform in
+    [1e48, 1e49] s^-1."""
+    rng = np.random.default_rng(seed)
+    sigma = float(rng.uniform(0.0, 1.5))
+    rho = lognormal_density(n, sigma, -3.0, rng) if sigma > 0 else np.ones((n, n, n))
+    nsrc = int(rng.integers(1, 9))
+    pos = rng.uniform(0.5, n - 0.5, size=(nsrc, 3))
+    Q = rng.uniform(1e48, 1e49, size=nsrc)
+    dx = box_kpc * KPC / n
+    return HIICase("hii_random", nside, n, nH_mean * rho, np.full((n, n, n), 1.0 - x0), pos, Q,
+                   chem_constants(1e4, dx), 1e-6, box_kpc * KPC)

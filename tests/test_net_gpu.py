@@ -69,17 +69,22 @@ def test_forward_matches_oracle(shape, dil):
     net.close()
 
 
-@pytest.mark.parametrize("shape,dil", [((16, 16, 16), (1, 2, 4, 8)), ((4, 4, 128), (2, 1, 1, 3))])
-def test_gradients_match_oracle(shape, dil):
+@pytest.mark.parametrize("shape,dil,weighted", [((16, 16, 16), (1, 2, 4, 8), False), ((4, 4, 128), (2, 1, 1, 3), False),
+                                                 ((16, 16, 16), (1, 2, 4, 8), True)])
+def test_gradients_match_oracle(shape, dil, weighted):
     net = art.ArtNet(dilation=dil)
     flat = art.ArtNet.join_params(params_with_bias(4)).astype(np.float32)
     net.set_params(flat)
     X, t = random_case(shape, 2)
-    loss, g = net.gradients(torch.as_tensor(X).cuda().reshape(-1), torch.as_tensor(t).cuda().reshape(-1), shape)
+    w = sg.weights(np.random.default_rng(9).random(shape) ** 4).astype(np.float32) if weighted else None
+    wd = torch.as_tensor(w).cuda().reshape(-1) if weighted else None
+    loss, g = net.gradients(torch.as_tensor(X).cuda().reshape(-1), torch.as_tensor(t).cuda().reshape(-1), shape,
+                            w=wd)
     P = oracle_params(flat)
     o, acts = sg.forward(X.astype(np.float64), P, dil, bf16_mode=True)
-    want = sg.backward(o, t.astype(np.float64), acts, P, dil, bf16_mode=True)
-    assert loss == pytest.approx(sg.loss(o, t), rel=1e-3)
+    w64 = None if w is None else w.astype(np.float64)
+    want = sg.backward(o, t.astype(np.float64), acts, P, dil, bf16_mode=True, w=w64)
+    assert loss == pytest.approx(sg.loss(o, t, w64), rel=1e-3)
     got = art.ArtNet.split_params(g)
     for li in range(4):
         assert relnorm(got[li][0], want[li][0]) < 1e-2, (li, relnorm(got[li][0], want[li][0]))

@@ -69,15 +69,17 @@ def test_adjoints_by_dot_products():
         assert np.allclose(gb, g.sum(axis=(1, 2, 3)))
 
 
-def test_backward_matches_central_differences():
+@pytest.mark.parametrize("weighted", [False, True])
+def test_backward_matches_central_differences(weighted):
     rng = np.random.default_rng(5)
     X = rng.standard_normal((2, 8, 8, 8))
     t = rng.standard_normal((8, 8, 8))
+    w = sg.weights(rng.random((8, 8, 8)) ** 3) if weighted else None
     dil = (1, 2, 1, 2)
     params = sg.init_params(seed=3, n_in=2, hidden=4)
     params = [(W, rng.standard_normal(b.shape) * 0.1) for W, b in params]
     o, acts = sg.forward(X, params, dil)
-    grads = sg.backward(o, t, acts, params, dil)
+    grads = sg.backward(o, t, acts, params, dil, w=w)
     h = 1e-6
     for li in range(4):
         W, b = params[li]
@@ -88,9 +90,9 @@ def test_backward_matches_central_differences():
             Wm[idx] -= h
             pp = list(params)
             pp[li] = (Wp, b)
-            lp = sg.loss(sg.forward(X, pp, dil)[0], t)
+            lp = sg.loss(sg.forward(X, pp, dil)[0], t, w)
             pp[li] = (Wm, b)
-            lm = sg.loss(sg.forward(X, pp, dil)[0], t)
+            lm = sg.loss(sg.forward(X, pp, dil)[0], t, w)
             fd = (lp - lm) / (2 * h)
             assert grads[li][0][idx] == pytest.approx(fd, rel=1e-5, abs=1e-9)
         j = int(rng.integers(0, b.shape[0]))
@@ -99,9 +101,9 @@ def test_backward_matches_central_differences():
         bm[j] -= h
         pp = list(params)
         pp[li] = (W, bp)
-        lp = sg.loss(sg.forward(X, pp, dil)[0], t)
+        lp = sg.loss(sg.forward(X, pp, dil)[0], t, w)
         pp[li] = (W, bm)
-        lm = sg.loss(sg.forward(X, pp, dil)[0], t)
+        lm = sg.loss(sg.forward(X, pp, dil)[0], t, w)
         assert grads[li][1][j] == pytest.approx((lp - lm) / (2 * h), rel=1e-5, abs=1e-9)
 
 
@@ -140,3 +142,10 @@ def test_features_are_scale_free_in_the_emissivity():
     f1 = sg.features(kap, eps, y, jc)
     f2 = sg.features(kap, 1e5 * eps, y, 1e5 * jc)   # J^in is linear in eps
     assert np.allclose(f1, f2, atol=1e-12)
+
+
+def test_weights_have_unit_mean_and_follow_the_intensity():
+    j = np.array([[[0.0, 1.0], [2.0, 5.0]]])
+    w = sg.weights(j)
+    assert w.mean() == pytest.approx(1.0) and w[0, 1, 1] == pytest.approx(2.5)
+    assert np.all(sg.weights(np.zeros((2, 2, 2))) == 1.0)

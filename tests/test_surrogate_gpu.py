@@ -1,0 +1,143 @@
+"""GPU tests of the surrogate pipeline on a sweep context: its inputs and
+target against the FP64 oracle (the sweeps, the coarse mesh, the features);
+the warm-started iteration reaching the plain iteration's fixed point (with
+and without the network, through the judge's fall-back); and what the
+trained network gains over the coarse sweep alone on held-out states."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import surrogate as sg
+from paper_1410_0763_gb300 import art, build
+from paper_1410_0763_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    art.load()
+
+
+def srcs(case):
+    return [(p[0], p[1], p[2], q) for p, q in zip(case.pos, case.Q)]
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def test_sample_matches_oracle(orc):
+    """Inputs X and target t of a state: kappa and eps from y, a fine and a
+    coarse (factor 4) sweep, clamped logarithms -- each recomputed by the oracle."""
+    n, nside, f, nside_c = 32, 2, 4, 1
+    case = wl.hii_region(n=n, nside=nside, box_kpc=1.6)
+    ch = case.chem
+    rng = np.random.default_rng(11)
+    y = 1.0 / (1.0 + np.exp(-4.0 * rng.standard_normal((n, n, n))))   # neutral fraction in (0, 1)
+    y[0, 0, :4] = 1.0                                                   # fully neutral: eps = 0 (floors)
+    nH = case.nH * np.exp(0.5 * rng.standard_normal((n, n, n)))
+    sw = art.ArtSweep((n, n, n), nside, 1, field_form=art.ART_FIELDS_EPS, dx_cm=ch["dx"])
+    V = n ** 3
+    X = torch.empty(4 * V, device="cuda")
+    t = torch.empty(V, device="cuda")
+    jin = torch.empty(V, device="cuda")
+    jc = torch.empty(V, device="cuda")
+    sw.surrogate_sample(torch.as_tensor(nH, device="cuda"), ch, torch.as_tensor(y, device="cuda"), X, t, jin, jc,
+                        coarse_factor=f, coarse_nside=nside_c)
+    torch.cuda.synchronize()
+    sw.close()
+    # oracle: kappa = y nH sigma0 dx, eps proportional to (x nH)^2 (the features and target are scale-free in eps)
+    kap = f32(y * nH * ch["sigma0"] * ch["dx"])
+    eps = f32(((1.0 - y) * nH) ** 2 * 1e-20)
+    jin_o, _, _ = orc.sweep(kap, eps, nside, field_form=1)
+    kc, ec = sg.restrict(kap, f), sg.restrict(eps, f)
+    jc_o = sg.prolong(orc.sweep(f32(kc), f32(ec), nside_c, field_form=1)[0], f)
+    X_o = sg.features(kap, eps, y, jc_o)
+    t_o = sg.target(jin_o, jc_o, eps)
+    Xg = X.cpu().numpy().astype(np.float64).reshape(4, n, n, n)
+    assert np.max(np.abs(Xg - X_o)) < 2e-4
+    assert np.max(np.abs(t.cpu().numpy().reshape(n, n, n) - t_o)) < 2e-3
+
+
+def _plain(case, sw, nH):
+    y = torch.as_tensor(case.y0, dtype=torch.float64, device="cuda").clone()
+    rep, _ = sw.iterate(nH, case.chem, srcs(case), y, tol=1e-6, max_iter=300)
+    return y.cpu().numpy(), rep
+
+
+@pytest.mark.parametrize("mode", ["coarse", "net", "fallback", "coarse_solve_only"])
+def test_warm_start_reaches_the_plain_fixed_point(mode):
+    n, nside = 32, 2
+    case = wl.hii_region(n=n, nside=nside, box_kpc=1.6)
+    sw = art.ArtSweep((n, n, n), nside, 1, field_form=art.ART_FIELDS_EPS, dx_cm=case.chem["dx"])
+    nH = torch.as_tensor(case.nH, dtype=torch.float64, device="cuda")
+    y_plain, rep_plain = _plain(case, sw, nH)
+    net = art.ArtNet(dilation=(1, 2, 2, 1)) if mode == "net" else None
+    kw = dict(coarse_factor=4, coarse_nside=1, use_net=(mode == "net"))
+    if mode == "fallback":
+        kw["judge_tol"] = 0.0          # any judge error restarts from the initial state
+    if mode == "net":
+        kw["judge_tol"] = 10.0         # an untrained network: keep its state whatever its error
+    if mode == "coarse_solve_only":
+        kw["phase1_max_iter"] = 0
+    y = torch.as_tensor(case.y0, dtype=torch.float64, device="cuda").clone()
+    rep, hist = sw.iterate_warm(net, nH, case.chem, srcs(case), y, tol=1e-6, max_iter=300, **kw)
+    yw = y.cpu().numpy()
+    assert rep.total.converged and hist[-1] < 1e-6
+    assert rep.coarse_iterations >= 1
+    if mode == "coarse_solve_only":
+        assert rep.surrogate_iterations == 0
+    else:
+        assert rep.surrogate_iterations >= 1 and rep.judge_error > 0
+    assert rep.fell_back == (1 if mode == "fallback" else 0)
+    assert rep.plain_sweeps <= rep.total.iterations
+    # both stop at a residual below 1e-6 of the same fixed point
+    assert np.max(np.abs(yw - y_plain) / y_plain) < 1e-4
+    assert np.max(np.abs((1 - yw) - (1 - y_plain)) / (1 - y_plain)) < 1e-4
+    if net is not None:
+        net.close()
+    sw.close()
+
+
+def test_trained_network_beats_the_coarse_sweep_on_held_out_states():
+    """Training on iterates of random HII setups (lognormal density, 1-8
+    sources) lowers the intensity-weighted log error of J^in below the coarse
+    sweep's own on the iterates of a held-out setup (the uniform medium with a
+    central source)."""
+    n, nside, NIT = 64, 4, 16
+    V = n ** 3
+    train_setups = [wl.hii_random(n, nside, seed=200 + k, box_kpc=3.3) for k in range(4)]
+    X = torch.empty((len(train_setups) * NIT, 4, V), device="cuda")
+    T = torch.empty((len(train_setups) * NIT, V), device="cuda")
+    W = torch.empty((len(train_setups) * NIT, V), device="cuda")
+    for k, c in enumerate(train_setups):
+        sk = art.ArtSweep(c.nH.shape, c.nside, 1, field_form=art.ART_FIELDS_EPS, dx_cm=c.chem["dx"])
+        yk = torch.as_tensor(c.y0, dtype=torch.float64, device="cuda").clone()
+        sk.surrogate_collect(torch.as_tensor(c.nH, device="cuda"), c.chem, srcs(c), yk, X[k * NIT:(k + 1) * NIT],
+                             T[k * NIT:(k + 1) * NIT], NIT, w=W[k * NIT:(k + 1) * NIT], coarse_nside=2)
+        sk.close()
+    held = wl.hii_region(n=n, nside=nside, box_kpc=3.3)
+    sh = art.ArtSweep((n, n, n), nside, 1, field_form=art.ART_FIELDS_EPS, dx_cm=held.chem["dx"])
+    Xe = torch.empty((NIT, 4, V), device="cuda")
+    Te = torch.empty((NIT, V), device="cuda")
+    We = torch.empty((NIT, V), device="cuda")
+    ye = torch.as_tensor(held.y0, dtype=torch.float64, device="cuda").clone()
+    sh.surrogate_collect(torch.as_tensor(held.nH, device="cuda"), held.chem, srcs(held), ye, Xe, Te, NIT, w=We,
+                         coarse_nside=2)
+    sh.close()
+    coarse_err = float((We * Te * Te).mean())      # the coarse sweep alone predicts o = 0
+    net = art.ArtNet(dilation=(1, 2, 4, 8), lr=3e-4, seed=3)
+    before = np.mean([net.gradients(Xe[k].reshape(-1), Te[k], (n, n, n), w=We[k])[0] for k in range(NIT)])
+    hist = net.train(X, T, (n, n, n), X.shape[0], 600, w=W, seed=1)
+    after = np.mean([net.gradients(Xe[k].reshape(-1), Te[k], (n, n, n), w=We[k])[0] for k in range(NIT)])
+    assert np.all(np.isfinite(hist)) and hist[-50:].mean() < hist[:50].mean()
+    assert after < before
+    assert after < 0.8 * coarse_err, (after, coarse_err)
+    net.close()
