@@ -76,6 +76,10 @@ typedef struct {
     int graph;        /* 1: art_sweep replays the launches of one sweep as a CUDA graph
                          (captured on the first call and again whenever the output
                          pointers, band integrals or variant change); 0 = plain launches */
+    int dir_begin, dir_end;  /* direction shard: sweep only RING indices [dir_begin, dir_end)
+                                (single-grid contexts); 0, 0 = all directions.  J_in and
+                                gamma are then this shard's additive share (still divided by
+                                the full N_d), and the J output is not available */
 } art_options;
 
 /* Statistics of one sweep, fixed at art_create. */
@@ -138,6 +142,15 @@ art_status art_batch_create(const art_grid *grids, const int *n_side, int n_grid
  * fields set), ART_E_OOM, ART_E_CUDA.
  */
 art_status art_autotune(art_ctx *ctx, int reps, int *best_variant, void *stream);
+
+/*
+ * Fixed-order sum of n_parts FP32 partial fields (device [n_parts][n], part
+ * order = the order of the sum, with Kahan compensation) into out (device
+ * [n]); used to combine the J_in shares of direction shards (one per rank) so
+ * that the result does not depend on how a collective would order the sum.
+ * Stream-ordered.  Errors: ART_E_INVALID, ART_E_CUDA.
+ */
+art_status art_sum_partials(const float *parts, int n_parts, int64_t n, float *out, void *stream);
 
 /* Release a context and all its device memory.  NULL is accepted. */
 art_status art_destroy(art_ctx *ctx);

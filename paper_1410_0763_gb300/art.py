@@ -31,7 +31,8 @@ class ArtGrid(C.Structure):
 class ArtOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("averaging", C.c_int), ("field_form", C.c_int),
                 ("tile_b", C.c_int), ("tile_c", C.c_int), ("slab", C.c_int), ("dir_split", C.c_int),
-                ("tie_tol", C.c_double), ("variant", C.c_int), ("persistent", C.c_int), ("graph", C.c_int)]
+                ("tie_tol", C.c_double), ("variant", C.c_int), ("persistent", C.c_int), ("graph", C.c_int),
+                ("dir_begin", C.c_int), ("dir_end", C.c_int)]
 
 
 class ArtSweepStats(C.Structure):
@@ -111,6 +112,8 @@ def load() -> C.CDLL:
         lib.art_batch_create.argtypes = [C.POINTER(ArtGrid), C.POINTER(C.c_int), C.c_int, C.c_int,
                                          C.POINTER(ArtOptions), C.POINTER(P)]
         lib.art_autotune.argtypes = [P, C.c_int, C.POINTER(C.c_int), P]
+        lib.art_sum_partials.argtypes = [P, C.c_int, C.c_int64, P, P]
+        lib.art_sum_partials.restype = C.c_int
         lib.art_destroy.argtypes = [P]
         lib.art_last_error.argtypes = [P]
         lib.art_last_error.restype = C.c_char_p
@@ -192,6 +195,20 @@ def art_autotune(ctx, reps: int, stream: int) -> tuple[int, int]:
     best = C.c_int(0)
     st = load().art_autotune(ctx, int(reps), C.byref(best), C.c_void_p(stream))
     return st, best.value
+
+
+def art_sum_partials(parts, out, stream=None):
+    """Fixed-order (part-order, Kahan) sum of device float32 parts [n_parts][n] into out [n]."""
+    n_parts = int(parts.shape[0])
+    n = int(out.numel())
+    pp, pd, _p = _ptr(parts.reshape(-1), np.float32, n_parts * n)
+    op, od, _o = _ptr(out, np.float32, n)
+    if not (pd and od):
+        raise TypeError("art_sum_partials takes device buffers")
+    st = load().art_sum_partials(C.c_void_p(pp), n_parts, n, C.c_void_p(op), C.c_void_p(_stream(stream)))
+    if st != ART_OK:
+        raise ArtError(st, "art_sum_partials failed")
+    return out
 
 
 def art_destroy(ctx) -> int:
@@ -329,7 +346,8 @@ class ArtSweep:
 
     def __init__(self, shape, nside, nbins: int = 1, precision: str = "fp32", field_form: int = 0,
                  dx_cm: float = 1.0, tile_b: int = 0, tile_c: int = 0, slab: int = 0, dir_split: int = 0,
-                 tie_tol: float = 1e-12, variant: int = 0, persistent: int = 0, graph: bool = False):
+                 tie_tol: float = 1e-12, variant: int = 0, persistent: int = 0, graph: bool = False,
+                 dir_range=None):
         batch = len(shape) > 0 and not np.isscalar(shape[0])
         shapes = [tuple(int(v) for v in s) for s in (shape if batch else [shape])]
         nsides = [int(v) for v in nside] if not np.isscalar(nside) else [int(nside)] * len(shapes)
@@ -349,6 +367,8 @@ class ArtSweep:
         opt.variant = int(variant)
         opt.persistent = int(persistent)
         opt.graph = 1 if graph else 0
+        if dir_range is not None:
+            opt.dir_begin, opt.dir_end = int(dir_range[0]), int(dir_range[1])
         grids = [ArtGrid(nx, ny, nz, dx_cm) for (nz, ny, nx) in shapes]
         if batch:
             self._ctx = art_batch_create(grids, nsides, nbins, opt)

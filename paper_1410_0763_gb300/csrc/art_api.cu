@@ -38,6 +38,16 @@ art_status fail(art_ctx *ctx, art_status st, const std::string &msg) { return ar
                         std::string(#call) + ": " + cudaGetErrorString(e_));                      \
     } while (0)
 
+// Fixed-order Kahan sum of n_parts partial fields (direction shards).
+__global__ void shard_sum_kernel(const float *__restrict__ parts, int n_parts, long long n, float *__restrict__ out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s = 0.f, c = 0.f;
+    for (int k = 0; k < n_parts; ++k) kahan_add(s, c, parts[(long long)k * n + i]);
+    out[i] = s - c;
+}
+
 template <typename T> art_status dev_alloc(art_ctx *ctx, T **p, size_t bytes)
 {
     void *q = nullptr;
@@ -151,6 +161,8 @@ void build_tables(const art_ctx *ctx, HostTables &t)
         healpix_directions(gh.nside, xyz);
         std::vector<Frame> fr(gh.nd);
         for (int d = 0; d < gh.nd; ++d) fr[d] = frame_of(&xyz[3 * d], ctx->opt.tie_tol);
+        const bool ranged = ctx->opt.dir_end > ctx->opt.dir_begin;
+        auto in_shard = [&](int d) { return !ranged || (d >= ctx->opt.dir_begin && d < ctx->opt.dir_end); };
         gh.cell_off = cell_off;
         gh.jpart_off = jpart_off;
         gh.seg_count = 0;
@@ -158,7 +170,7 @@ void build_tables(const art_ctx *ctx, HostTables &t)
         for (int cls = 0; cls < 24; ++cls) {
             std::vector<int> members;
             for (int d = 0; d < gh.nd; ++d)
-                if (fr[d].cls == cls) members.push_back(d);
+                if (fr[d].cls == cls && in_shard(d)) members.push_back(d);
             if (members.empty()) continue;
             t.min_per_class = std::min(t.min_per_class, (int)members.size());
             // Order within the class: by column drift per slab block along b,
@@ -477,14 +489,17 @@ art_status create_common(const art_grid *grids, const int *n_side, int n_grids, 
     else art_options_default(&ctx->opt);
     if (!(ctx->opt.tie_tol >= 0.0) || ctx->opt.tie_tol > 1e-3) ctx->opt.tie_tol = 1e-12;
     if ((ctx->opt.precision != ART_FP32 && ctx->opt.precision != ART_FP64) || ctx->opt.averaging != ART_AVG_PAPER ||
-        (ctx->opt.field_form != ART_FIELDS_S && ctx->opt.field_form != ART_FIELDS_EPS) || ctx->opt.dir_split < 0) {
+        (ctx->opt.field_form != ART_FIELDS_S && ctx->opt.field_form != ART_FIELDS_EPS) || ctx->opt.dir_split < 0 ||
+        ctx->opt.dir_begin < 0 || ctx->opt.dir_end < 0 ||
+        (ctx->opt.dir_end != 0 || ctx->opt.dir_begin != 0) &&
+            (n_grids != 1 || ctx->opt.dir_begin >= ctx->opt.dir_end || ctx->opt.dir_end > 12 * n_side[0] * n_side[0])) {
         delete ctx;
         return ART_E_INVALID;
     }
     ctx->prec = ctx->opt.precision;
     ctx->rsz = ctx->prec == ART_FP64 ? 8 : 4;
     ctx->ncell = total;
-    ctx->nd = 0;
+    ctx->nd = 0;   // directions swept (all, or the shard)
     for (int g = 0; g < n_grids; ++g) {
         art_grid_host gh;
         gh.g = grids[g];
@@ -494,6 +509,7 @@ art_status create_common(const art_grid *grids, const int *n_side, int n_grids, 
         ctx->grids.push_back(gh);
         ctx->nd += gh.nd;
     }
+    if (ctx->opt.dir_end > ctx->opt.dir_begin) ctx->nd = ctx->opt.dir_end - ctx->opt.dir_begin;
     ctx->G.assign(nu_bins, 0.0);
     ctx->persistent = ctx->opt.persistent > 0 ? 1 : (ctx->opt.persistent < 0 ? 0 : (n_grids > 1 ? 1 : 0));
 
@@ -663,6 +679,16 @@ art_status art_autotune(art_ctx *ctx, int reps, int *best_variant, void *stream)
     return ART_OK;
 }
 
+art_status art_sum_partials(const float *parts, int n_parts, int64_t n, float *out, void *stream)
+{
+    if (!parts || !out || n_parts < 1 || n < 0) return ART_E_INVALID;
+    if (n == 0) return ART_OK;
+    const int nt = 256;
+    shard_sum_kernel<<<(unsigned)((n + nt - 1) / nt), nt, 0, static_cast<cudaStream_t>(stream)>>>(parts, n_parts, n,
+                                                                                                      out);
+    return cudaGetLastError() == cudaSuccess ? ART_OK : ART_E_CUDA;
+}
+
 art_status art_band_integral(double sigma0, double h, double nu0, double nu_lo, double nu_hi, double *G)
 {
     if (!G || !(sigma0 > 0.0) || !(h > 0.0) || !(nu0 > 0.0) || !(nu_lo > 0.0) || !(nu_hi >= nu_lo) ||
@@ -815,6 +841,8 @@ art_status art_sweep(art_ctx *ctx, void *J, void *J_in, void *gamma, int on_devi
 {
     if (!ctx) return ART_E_INVALID;
     if (!ctx->have_fields) return fail(ctx, ART_E_STATE, "art_sweep: call art_set_fields first");
+    if (J && ctx->opt.dir_end > ctx->opt.dir_begin)
+        return fail(ctx, ART_E_INVALID, "art_sweep: a direction shard has no J output (sum the J_in shares)");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const long long nb = ctx->ncell * ctx->nbins;
     const size_t rs = ctx->rsz;

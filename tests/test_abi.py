@@ -67,6 +67,15 @@ def test_batch_create_rejects_bad_arguments_without_touching_the_gpu(lib, dims, 
     assert lib.art_autotune(None, 1, None, None) == art.ART_E_INVALID
 
 
+@pytest.mark.parametrize("rng", [(3, 3), (5, 2), (-1, 4), (0, 13)])
+def test_bad_direction_shards_are_rejected_without_touching_the_gpu(lib, rng):
+    o = art.art_options_default()
+    o.dir_begin, o.dir_end = rng
+    h = ctypes.c_void_p()
+    st = lib.art_create(ctypes.byref(art.ArtGrid(4, 4, 4, 1.0)), 1, 1, ctypes.byref(o), ctypes.byref(h))
+    assert st == art.ART_E_INVALID and not h.value
+
+
 def test_null_context_calls_fail_cleanly(lib):
     assert lib.art_sweep(None, None, None, None, 1, None) == art.ART_E_INVALID
     assert lib.art_set_fields(None, None, None, 0, None) == art.ART_E_INVALID
