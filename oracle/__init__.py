@@ -85,6 +85,8 @@ def _lib_handle():
             lib.orc_balance_eq.argtypes = [C.c_long, _D, C.c_double, C.c_double, _D, _D]
             lib.orc_iterate.argtypes = [C.POINTER(SweepCfg), C.POINTER(Chem), _D, C.c_int, _D, _D,
                                         C.c_double, C.c_int, _D, _D, C.POINTER(C.c_int)]
+            lib.orc_iterate_bins.argtypes = [C.POINTER(SweepCfg), C.POINTER(Chem), _D, C.c_int, _D, _D,
+                                             C.c_int, _D, _D, C.c_double, C.c_int, _D, _D, C.POINTER(C.c_int)]
             _lib = lib
     return _lib
 
@@ -240,19 +242,24 @@ def balance_eq(nH, alphaB, gcoll, g):
     return y
 
 
-def iterate(nH, nside, chem: dict, pos, Q, y0, tol=1e-6, max_iter=200, nthreads=None):
-    """RT / balance fixed-point iteration (App. D).  Returns (y, iters, residuals, converged)."""
+def iterate(nH, nside, chem: dict, pos, Q, y0, tol=1e-6, max_iter=200, nthreads=None, sigma_bins=None,
+            frac_bins=None):
+    """RT / balance fixed-point iteration (App. D).  Point sources emit Q * frac_b in bin b with cross
+    section sigma_b (default: one bin at sigma0).  Returns (y, iters, residuals, converged)."""
     n = _f64(nH)
     y = _f64(y0).copy()
     p = _f64(pos).reshape(-1, 3)
     q = _f64(Q).reshape(p.shape[0])
+    sig = _f64([chem["sigma0"]] if sigma_bins is None else sigma_bins)
+    frac = _f64([1.0] if frac_bins is None else frac_bins)
     hist = np.zeros(max_iter)
     it = C.c_int(0)
     ch = Chem(chem["alphaA"], chem["alphaB"], chem["gcoll"], chem["sigma0"], chem["h"],
               chem["nu0"], chem["dnu"], chem["dx"])
     cfg = _cfg(n.shape, nside, 1, 1e-12, nthreads)
-    rc = _lib_handle().orc_iterate(C.byref(cfg), C.byref(ch), _dp(n), p.shape[0], _dp(p), _dp(q),
-                                   float(tol), int(max_iter), _dp(y), _dp(hist), C.byref(it))
+    rc = _lib_handle().orc_iterate_bins(C.byref(cfg), C.byref(ch), _dp(n), p.shape[0], _dp(p), _dp(q),
+                                        int(sig.size), _dp(sig), _dp(frac), float(tol), int(max_iter),
+                                        _dp(y), _dp(hist), C.byref(it))
     if rc < 0:
         raise MemoryError("oracle iterate: allocation failed")
     return y, it.value, hist[: it.value].copy(), rc == 0

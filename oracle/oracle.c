@@ -646,18 +646,41 @@ typedef struct {
     double dx;                      /* cell width, cm */
 } orc_chem;
 
+int orc_iterate_bins(const orc_sweep_cfg *cfg, const orc_chem *ch, const double *nH, int nsrc,
+                     const double *pos, const double *Q, int nb, const double *sigma_b,
+                     const double *frac_b, double tol, int max_iter, double *y,
+                     double *resid_hist, int *iters);
+
 int orc_iterate(const orc_sweep_cfg *cfg, const orc_chem *ch, const double *nH, int nsrc,
                 const double *pos, const double *Q, double tol, int max_iter, double *y,
                 double *resid_hist, int *iters)
 {
+    const double one = 1.0;
+    return orc_iterate_bins(cfg, ch, nH, nsrc, pos, Q, 1, &ch->sigma0, &one, tol, max_iter, y,
+                            resid_hist, iters);
+}
+
+/* The iteration with point sources over nb frequency bins (App. A, Eq.
+ * pc_gamma summed over bins): source a emits Q_a frac_b photons/s in bin b,
+ * absorbed with cross section sigma_b (kappa_b = n_HI sigma_b dx); the
+ * diffuse recombination field stays the band [nu0, nu0 + dnu] at sigma0. */
+int orc_iterate_bins(const orc_sweep_cfg *cfg, const orc_chem *ch, const double *nH, int nsrc,
+                     const double *pos, const double *Q, int nb, const double *sigma_b,
+                     const double *frac_b, double tol, int max_iter, double *y,
+                     double *resid_hist, int *iters)
+{
     const long ncell = (long)cfg->nx * cfg->ny * cfg->nz;
     double *kap = (double *)malloc(sizeof(double) * ncell);
+    double *kapb = (double *)malloc(sizeof(double) * ncell * nb);
+    double *qb = (double *)malloc(sizeof(double) * (nsrc > 0 ? nsrc : 1) * nb);
     double *eps = (double *)malloc(sizeof(double) * ncell);
     double *jin = (double *)malloc(sizeof(double) * ncell);
     double *gpt = (double *)malloc(sizeof(double) * ncell);
     double *g = (double *)malloc(sizeof(double) * ncell);
     double *yn = (double *)malloc(sizeof(double) * ncell);
-    if (!kap || !eps || !jin || !gpt || !g || !yn) return -1;
+    if (!kap || !kapb || !qb || !eps || !jin || !gpt || !g || !yn) return -1;
+    for (int a = 0; a < nsrc; a++)
+        for (int b = 0; b < nb; b++) qb[a * nb + b] = Q[a] * frac_b[b];
     orc_sweep_cfg c = *cfg;
     c.field_form = 1;
     const double dalpha = ch->alphaA - ch->alphaB;
@@ -670,8 +693,9 @@ int orc_iterate(const orc_sweep_cfg *cfg, const orc_chem *ch, const double *nH, 
             eps[i] = ch->h * ch->nu0 * dalpha * ne * ne * ch->dx / (4.0 * M_PI * ch->dnu);
         }
         orc_sweep(&c, kap, eps, jin, NULL);
-        const double s1 = ch->sigma0;
-        orc_point_sources(cfg->nx, cfg->ny, cfg->nz, 1, kap, &s1, nsrc, pos, Q, ch->dx, cfg->nthreads, gpt);
+        for (int b = 0; b < nb; b++)
+            for (long i = 0; i < ncell; i++) kapb[b * ncell + i] = y[i] * nH[i] * sigma_b[b] * ch->dx;
+        orc_point_sources(cfg->nx, cfg->ny, cfg->nz, nb, kapb, sigma_b, nsrc, pos, qb, ch->dx, cfg->nthreads, gpt);
         for (long i = 0; i < ncell; i++) g[i] = 4.0 * M_PI * G * jin[i] + gpt[i];
         orc_balance_eq(ncell, nH, ch->alphaB, ch->gcoll, g, yn);
         double r = 0.0;
@@ -685,6 +709,6 @@ int orc_iterate(const orc_sweep_cfg *cfg, const orc_chem *ch, const double *nH, 
         if (r < tol) { conv = 1; break; }
     }
     if (iters) *iters = conv ? it : max_iter;
-    free(kap); free(eps); free(jin); free(gpt); free(g); free(yn);
+    free(kap); free(kapb); free(qb); free(eps); free(jin); free(gpt); free(g); free(yn);
     return conv ? 0 : 1;
 }

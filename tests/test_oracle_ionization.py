@@ -203,3 +203,17 @@ def test_diffuse_field_enlarges_ionized_region(orc):
     y_diff, *_ = orc.iterate(case.nH, 2, case.chem, case.pos, case.Q, case.y0, 1e-6, 300)
     assert np.all(y_diff <= y_otsa * (1 + 1e-9))
     assert np.sum(1 - y_diff) > np.sum(1 - y_otsa)
+
+
+def test_iteration_source_bins_split_and_scale(orc):
+    """Splitting each source's photons over bins of equal cross section leaves
+    the iteration unchanged (Gamma is linear in Q per bin, Eq. pc_gamma); a
+    bin with a larger cross section and no photons changes nothing either."""
+    n, nside = 12, 1
+    case = wl.hii_region(n=n, nside=nside, box_kpc=1.2)
+    s0 = case.chem["sigma0"]
+    y1, it1, h1, c1 = orc.iterate(case.nH, nside, case.chem, case.pos, case.Q, case.y0, 1e-6, 200)
+    y2, it2, h2, c2 = orc.iterate(case.nH, nside, case.chem, case.pos, case.Q, case.y0, 1e-6, 200,
+                                  sigma_bins=[s0, s0, 3 * s0], frac_bins=[0.25, 0.75, 0.0])
+    assert c1 and c2 and it1 == it2
+    assert np.allclose(y1, y2, rtol=1e-12, atol=0)
