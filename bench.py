@@ -338,7 +338,60 @@ def ionization_measure(torch, dev, tol=1e-6, n_setups=8, n_iter=24, train_steps=
     flops = 2.0 * 27 * V * (4 * 32 + 32 * 32 * 2 + 32 * 1)
     out["network_forward"] = {"ms": round(ms, 4), "tflops_algorithmic": round(flops / (ms * 1e-3) / 1e12, 1),
                               "note": "4 layers, 128^3 cells, BF16 tcgen05 MMA, FP32 accumulation"}
+    sw.close()
+    clumpy = clumpy_measure(torch, dev, net, tol)
     net.close()
+    return out, clumpy
+
+
+def clumpy_measure(torch, dev, net, tol=1e-6):
+    """The clumpy 256^3 medium (lognormal sigma 1.5 plus 200 clumps of
+    overdensity 100, mean n_H 1e-3, 6.6 kpc, N_side 8) with 8 sources of
+    5e48 s^-1 over 4 blackbody (1e5 K) bins above 13.6 eV: plain iteration and
+    warm starts, one run each (the network is the one trained at 128^3)."""
+    from paper_1410_0763_gb300 import art
+    from paper_1410_0763_gb300 import workloads as wl
+    case = wl.clumpy()
+    frac, sig, _ = wl.blackbody_bins()
+    srcs = [(p[0], p[1], p[2], q) for p, q in zip(case.pos, case.Q)]
+    sw = art.ArtSweep(case.nH.shape, case.nside, 1, field_form=art.ART_FIELDS_EPS, dx_cm=case.chem["dx"])
+    sw.set_source_spectrum(sig, frac)
+    nH = torch.as_tensor(case.nH, dtype=torch.float64, device=dev)
+    out = {"workload": "256^3 clumpy (lognormal sigma 1.5 + 200 clumps x100, mean n_H 1e-3), N_side 8, 8 sources "
+                       "x 5e48 s^-1, 4 blackbody bins (1e5 K) above 13.6 eV, 6.6 kpc", "tol": tol,
+           "bins": {"frac": [round(float(v), 5) for v in frac], "sigma_over_sigma0": [round(float(v / wl.SIGMA0), 5)
+                                                                                      for v in sig]}}
+
+    def run(label, fn):
+        y = torch.as_tensor(case.y0, dtype=torch.float64, device=dev).clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        try:
+            res = fn(y)
+        except Exception as ex:  # pragma: no cover
+            out[label] = {"error": str(ex)}
+            return None
+        torch.cuda.synchronize()
+        out[label] = {"seconds": round(time.perf_counter() - t0, 3)}
+        return res, y
+
+    r = run("plain", lambda y: sw.iterate(nH, case.chem, srcs, y, tol=tol, max_iter=400))
+    if r:
+        (rep, _), y_plain = r
+        y_plain = y_plain.cpu().numpy()
+        out["plain"].update(iterations=int(rep.iterations), converged=bool(rep.converged))
+        for label, kw in (("warm_coarse_solve", dict(use_net=False, phase1_max_iter=0)),
+                          ("warm_coarse_solve_net_phase", dict(use_net=True))):
+            r2 = run(label, lambda y: sw.iterate_warm(net if kw["use_net"] else None, nH, case.chem, srcs, y,
+                                                      tol=tol, max_iter=400, **kw))
+            if r2:
+                (wr, _), y = r2
+                out[label].update(iterations=int(wr.total.iterations), coarse_iterations=int(wr.coarse_iterations),
+                                  surrogate_iterations=int(wr.surrogate_iterations),
+                                  full_sweeps=int(wr.plain_sweeps), judge_error=round(float(wr.judge_error), 5),
+                                  converged=bool(wr.total.converged),
+                                  speedup_vs_plain=round(out["plain"]["seconds"] / out[label]["seconds"], 3),
+                                  max_rel_dy_vs_plain=float(np.max(np.abs(y.cpu().numpy() - y_plain) / y_plain)))
     sw.close()
     return out
 
@@ -449,11 +502,14 @@ def run_ours(args, d: Dist):
                     extra[name] = side_measure(name, torch, dev, G)
                 except Exception as ex:  # pragma: no cover
                     extra[name] = {"error": str(ex)}
-        for name, fn in (("batch48", batch_measure), ("rt_ionization_128", ionization_measure)):
-            try:
-                extra[name] = fn(torch, dev)
-            except Exception as ex:  # pragma: no cover
-                extra[name] = {"error": str(ex)}
+        try:
+            extra["batch48"] = batch_measure(torch, dev)
+        except Exception as ex:  # pragma: no cover
+            extra["batch48"] = {"error": str(ex)}
+        try:
+            extra["rt_ionization_128"], extra["rt_ionization_256_clumpy"] = ionization_measure(torch, dev)
+        except Exception as ex:  # pragma: no cover
+            extra["rt_ionization_128"] = {"error": str(ex)}
 
     cpu = None
     if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:

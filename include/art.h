@@ -274,7 +274,8 @@ art_status art_point_sources(art_ctx *ctx, const float *kappa, const double *sig
  * The context must be FP32 with one bin and ART_FIELDS_EPS inputs.
  * nH: device [z][y][x] doubles (cm^-3); y: device [z][y][x] doubles, the
  * initial neutral fraction on input and the result on output; src: host
- * array (monochromatic at nu0, src[i].Q); resid_hist: host array of max_iter
+ * array (src[i].Q photons/s, monochromatic at nu0 unless
+ * art_set_source_spectrum gave bins); resid_hist: host array of max_iter
  * doubles or NULL; rep: may be NULL.  One host synchronization per iteration
  * (the residual).  Errors: ART_E_INVALID, ART_E_NOT_CONVERGED (y holds the
  * last iterate), ART_E_OOM, ART_E_CUDA.
@@ -282,6 +283,17 @@ art_status art_point_sources(art_ctx *ctx, const float *kappa, const double *sig
 art_status art_iterate_ionization(art_ctx *ctx, const art_chem *chem, const double *nH, const art_source *src,
                                   int n_src, double tol, int max_iter, double *y, double *resid_hist,
                                   art_iter_report *rep, void *stream);
+
+/*
+ * Source spectrum of art_iterate_ionization on this context (App. A with
+ * frequency bins): every point source emits Q * frac[b] photons/s in bin b,
+ * absorbed with cross section sigma[b] (cm^2; kappa_b = n_HI sigma[b] dx);
+ * Gamma sums over the bins (Eq. pc_gamma per bin).  The diffuse
+ * recombination field keeps its band at nu0.  nbins = 0 restores the
+ * default (one bin at chem->sigma0, frac 1).  1 <= nbins <= 4.  Errors:
+ * ART_E_INVALID.
+ */
+art_status art_set_source_spectrum(art_ctx *ctx, int nbins, const double *sigma, const double *frac);
 
 /* Per-kernel device time accumulated while profiling is enabled. */
 typedef struct {

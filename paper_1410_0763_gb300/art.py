@@ -113,6 +113,8 @@ def load() -> C.CDLL:
                                          C.POINTER(ArtOptions), C.POINTER(P)]
         lib.art_autotune.argtypes = [P, C.c_int, C.POINTER(C.c_int), P]
         lib.art_sum_partials.argtypes = [P, C.c_int, C.c_int64, P, P]
+        lib.art_set_source_spectrum.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        lib.art_set_source_spectrum.restype = C.c_int
         lib.art_sum_partials.restype = C.c_int
         lib.art_destroy.argtypes = [P]
         lib.art_last_error.argtypes = [P]
@@ -446,6 +448,17 @@ class ArtSweep:
         if st != ART_OK:
             raise ArtError(st, art_last_error(self._ctx))
         return rep, np.array(hist[:n])
+
+    def set_source_spectrum(self, sigma=None, frac=None):
+        """Point-source bins of the iteration: cross sections sigma[b] (cm^2), photon fractions frac[b];
+        None restores one bin at sigma0."""
+        if sigma is None:
+            _check(self._ctx, load().art_set_source_spectrum(self._ctx, 0, None, None))
+            return
+        n = len(sigma)
+        sg = (C.c_double * n)(*[float(v) for v in sigma])
+        fr = (C.c_double * n)(*[float(v) for v in frac])
+        _check(self._ctx, load().art_set_source_spectrum(self._ctx, n, sg, fr))
 
     def _chem(self, chem: dict) -> ArtChem:
         return ArtChem(chem["alphaA"], chem["alphaB"], chem["gcoll"], chem["sigma0"], chem["h"], chem["nu0"],

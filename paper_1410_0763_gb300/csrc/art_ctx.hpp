@@ -84,6 +84,8 @@ struct art_ctx {
     bool profiling = false;
     std::vector<cudaEvent_t> ev;
     art_iter_bufs it;
+    int spec_bins = 0;          // point-source spectrum of the iteration (0: one bin at sigma0)
+    double spec_sigma[4] = {0, 0, 0, 0}, spec_frac[4] = {0, 0, 0, 0};
     art_ctx *coarse = nullptr;  // coarse-mesh sweep of the surrogate
     art_sur_bufs sur;
 };

@@ -45,7 +45,7 @@ constexpr double kPi = 3.14159265358979323846;
 // cell's faces in FP64.
 // ---------------------------------------------------------------------------
 struct PtArgs {
-    const float *kappa;   // [bins][ncell]
+    const float *kappa;   // [bins][ncell], or one field scaled per bin (scaled != 0)
     const double *src;    // [nsrc][4]: x, y, z, (unused)
     const double *Qb;     // [nsrc][bins]
     const double *sigma;  // [bins]
@@ -54,11 +54,13 @@ struct PtArgs {
     long long ncell;
     double dx;
     float *gamma;
+    int scaled;           // kappa_b = kappa * kscale[b] (one field for all bins, one tau to march)
+    float kscale[4];
 };
 
 constexpr int kMaxBins = 4;   // point-source kernels are compiled for 1-4 bins
 
-template <int NB> __global__ void __launch_bounds__(128) point_source_kernel(const PtArgs p)
+template <int NB, bool SCALED> __global__ void __launch_bounds__(128) point_source_kernel(const PtArgs p)
 {
     const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= p.ncell) return;
@@ -112,15 +114,19 @@ template <int NB> __global__ void __launch_bounds__(128) point_source_kernel(con
                 const double den = 4.0 * kPi * p.dx * p.dx * (rout * rout + rout * rin + rin * rin);
 #pragma unroll
                 for (int b = 0; b < NB; ++b) {
-                    const double x = (double)p.kappa[(long long)b * p.ncell + ci] * (rout - rin);
+                    const double kb = SCALED ? (double)p.kappa[ci] * p.kscale[b]
+                                             : (double)p.kappa[(long long)b * p.ncell + ci];
+                    const double tb = SCALED ? (double)tau[0] * p.kscale[b] : (double)tau[b];
+                    const double x = kb * (rout - rin);
                     const double ph = x > 0.0 ? -expm1(-x) / x : 1.0;
-                    g += 3.0 * p.Qb[(long long)a * p.nbins + b] * p.sigma[b] * exp(-(double)tau[b]) * ph / den;
+                    g += 3.0 * p.Qb[(long long)a * p.nbins + b] * p.sigma[b] * exp(-tb) * ph / den;
                 }
                 break;
             }
             const float ds = fminf(r[0], fminf(r[1], r[2]));
 #pragma unroll
-            for (int b = 0; b < NB; ++b) tau[b] = fmaf(__ldg(p.kappa + (long long)b * p.ncell + ci), ds, tau[b]);
+            for (int b = 0; b < (SCALED ? 1 : NB); ++b)
+                tau[b] = fmaf(__ldg(p.kappa + (long long)b * p.ncell + ci), ds, tau[b]);
             bool out = false;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
@@ -228,9 +234,11 @@ art_status upload_sources(art_ctx *ctx, const art_source *src, int n_src, const 
     return ART_OK;
 }
 
-// Point-source rates into gamma (device), kappa per bin on the device.
+// Point-source rates into gamma (device), kappa per bin on the device, or
+// (kscale != null) one kappa field scaled per bin.
 art_status launch_points(art_ctx *ctx, const float *kappa, int nbins, const double *d_src, const double *d_q,
-                         const double *d_sigma, int n_src, float *gamma, cudaStream_t st)
+                         const double *d_sigma, int n_src, float *gamma, cudaStream_t st,
+                         const float *kscale = nullptr)
 {
     PtArgs a;
     a.kappa = kappa;
@@ -245,14 +253,26 @@ art_status launch_points(art_ctx *ctx, const float *kappa, int nbins, const doub
     a.ncell = ctx->ncell;
     a.dx = ctx->grid.dx_cm;
     a.gamma = gamma;
+    a.scaled = kscale != nullptr;
+    for (int b = 0; b < 4; ++b) a.kscale[b] = kscale && b < nbins ? kscale[b] : 1.0f;
     const int nt = 128;
     const unsigned nb = (unsigned)((ctx->ncell + nt - 1) / nt);
-    switch (nbins) {
-    case 1: point_source_kernel<1><<<nb, nt, 0, st>>>(a); break;
-    case 2: point_source_kernel<2><<<nb, nt, 0, st>>>(a); break;
-    case 3: point_source_kernel<3><<<nb, nt, 0, st>>>(a); break;
-    case 4: point_source_kernel<4><<<nb, nt, 0, st>>>(a); break;
-    default: return art_fail(ctx, ART_E_INVALID, "point sources: 1 to 4 bins");
+    if (a.scaled) {
+        switch (nbins) {
+        case 1: point_source_kernel<1, true><<<nb, nt, 0, st>>>(a); break;
+        case 2: point_source_kernel<2, true><<<nb, nt, 0, st>>>(a); break;
+        case 3: point_source_kernel<3, true><<<nb, nt, 0, st>>>(a); break;
+        case 4: point_source_kernel<4, true><<<nb, nt, 0, st>>>(a); break;
+        default: return art_fail(ctx, ART_E_INVALID, "point sources: 1 to 4 bins");
+        }
+    } else {
+        switch (nbins) {
+        case 1: point_source_kernel<1, false><<<nb, nt, 0, st>>>(a); break;
+        case 2: point_source_kernel<2, false><<<nb, nt, 0, st>>>(a); break;
+        case 3: point_source_kernel<3, false><<<nb, nt, 0, st>>>(a); break;
+        case 4: point_source_kernel<4, false><<<nb, nt, 0, st>>>(a); break;
+        default: return art_fail(ctx, ART_E_INVALID, "point sources: 1 to 4 bins");
+        }
     }
     ICK(ctx, cudaGetLastError());
     return ART_OK;
@@ -398,21 +418,34 @@ art_status iterate_impl(art_ctx *ctx, art_net *net, const art_chem *ch, const do
         (s = ensure(ctx, &B.resid, 1)) != ART_OK)
         return s;
     if (warm && ((s = ensure(ctx, &B.y0, n)) != ART_OK || (s = ensure(ctx, &B.jsur, n)) != ART_OK)) return s;
+    // source spectrum: Q_a frac_b photons/s in bin b, cross section sigma_b (default: one bin at sigma0)
+    const int nbp = ctx->spec_bins > 0 ? ctx->spec_bins : 1;
+    std::vector<double> sig(nbp), frac(nbp);
+    std::vector<float> kscale(nbp);
+    for (int b = 0; b < nbp; ++b) {
+        sig[b] = ctx->spec_bins > 0 ? ctx->spec_sigma[b] : ch->sigma0;
+        frac[b] = ctx->spec_bins > 0 ? ctx->spec_frac[b] : 1.0;
+        kscale[b] = (float)(sig[b] / ch->sigma0);
+    }
     std::vector<double> h_src, h_q;
     if ((s = upload_sources(ctx, src, n_src, nullptr, 1, h_src, h_q)) != ART_OK) return s;
+    std::vector<double> h_qb((size_t)(n_src > 0 ? n_src : 1) * nbp, 0.0);
+    for (int a = 0; a < n_src; ++a)
+        for (int b = 0; b < nbp; ++b) h_qb[(size_t)a * nbp + b] = h_q[a] * frac[b];
     const int cap = n_src > 0 ? n_src : 1;
-    if (B.nsrc_cap < cap * 5 + 1) {
+    const int need = cap * (4 + nbp) + nbp;
+    if (B.nsrc_cap < need) {
         if (B.src) cudaFree(B.src);
         B.src = nullptr;
-        B.nsrc_cap = cap * 5 + 1;
+        B.nsrc_cap = need;
         if ((s = ensure(ctx, &B.src, (size_t)B.nsrc_cap)) != ART_OK) return s;
     }
-    double *d_src = B.src, *d_q = d_src + 4 * cap, *d_sig = d_q + cap;
+    double *d_src = B.src, *d_q = d_src + 4 * cap, *d_sig = d_q + (size_t)cap * nbp;
     if (n_src > 0) {
         ICK(ctx, cudaMemcpyAsync(d_src, h_src.data(), h_src.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-        ICK(ctx, cudaMemcpyAsync(d_q, h_q.data(), h_q.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        ICK(ctx, cudaMemcpyAsync(d_q, h_qb.data(), (size_t)n_src * nbp * sizeof(double), cudaMemcpyHostToDevice, st));
     }
-    ICK(ctx, cudaMemcpyAsync(d_sig, &ch->sigma0, sizeof(double), cudaMemcpyHostToDevice, st));
+    ICK(ctx, cudaMemcpyAsync(d_sig, sig.data(), nbp * sizeof(double), cudaMemcpyHostToDevice, st));
 
     const int nt = 256;
     const unsigned nb = (unsigned)((n + nt - 1) / nt);
@@ -433,6 +466,11 @@ art_status iterate_impl(art_ctx *ctx, art_net *net, const art_chem *ch, const do
             c.y /= f;
             c.z /= f;
         }
+        ctx->coarse->spec_bins = ctx->spec_bins;
+        for (int b = 0; b < 4; ++b) {
+            ctx->coarse->spec_sigma[b] = ctx->spec_sigma[b];
+            ctx->coarse->spec_frac[b] = ctx->spec_frac[b];
+        }
         art_iter_report cr{};
         const art_status cs = iterate_impl(ctx->coarse, nullptr, ch, S.nHc, csrc.data(), n_src, warm->coarse_tol,
                                            max_iter, nullptr, S.yc, nullptr, &cr, nullptr, st);
@@ -452,7 +490,8 @@ art_status iterate_impl(art_ctx *ctx, art_net *net, const art_chem *ch, const do
     int it = 0, conv = 0, it1 = 0, sweeps = 0, fell_back = 0;
     double r = 0.0, judge = 0.0;
     for (it = 1; it <= max_iter; ++it) {
-        if ((s = launch_points(ctx, B.kap, 1, d_src, d_q, d_sig, n_src, B.gpt, st)) != ART_OK) return s;
+        if ((s = launch_points(ctx, B.kap, nbp, d_src, d_q, d_sig, n_src, B.gpt, st, kscale.data())) != ART_OK)
+            return s;
         if (have_jin) {
             have_jin = false;   // J^in of this state came with the judge's sweep
         } else if (phase1) {
@@ -538,6 +577,26 @@ art_status art_iterate_ionization(art_ctx *ctx, const art_chem *ch, const double
 {
     return iterate_impl(ctx, nullptr, ch, nH, src, n_src, tol, max_iter, nullptr, y, resid_hist, rep, nullptr,
                         static_cast<cudaStream_t>(stream));
+}
+
+art_status art_set_source_spectrum(art_ctx *ctx, int nbins, const double *sigma, const double *frac)
+{
+    if (!ctx) return ART_E_INVALID;
+    if (nbins == 0) {
+        ctx->spec_bins = 0;
+        return ART_OK;
+    }
+    if (nbins < 1 || nbins > kMaxBins || !sigma || !frac)
+        return art_fail(ctx, ART_E_INVALID, "art_set_source_spectrum: 1 to 4 bins with cross sections and fractions");
+    for (int b = 0; b < nbins; ++b)
+        if (!(sigma[b] > 0.0) || !std::isfinite(sigma[b]) || !(frac[b] >= 0.0) || !std::isfinite(frac[b]))
+            return art_fail(ctx, ART_E_INVALID, "art_set_source_spectrum: bad cross section or fraction");
+    ctx->spec_bins = nbins;
+    for (int b = 0; b < nbins; ++b) {
+        ctx->spec_sigma[b] = sigma[b];
+        ctx->spec_frac[b] = frac[b];
+    }
+    return ART_OK;
 }
 
 art_status art_warm_options_default(art_warm_options *o)

@@ -164,3 +164,49 @@ def hii_random(n: int = 128, nside: int = 8, seed: int = 100, box_kpc: float = 6
     dx = box_kpc * KPC / n
     return HIICase("hii_random", nside, n, nH_mean * rho, np.full((n, n, n), 1.0 - x0), pos, Q,
                    chem_constants(1e4, dx), 1e-6, box_kpc * KPC)
+
+
+def blackbody_bins(T: float = 1e5, edges_ev=(13.6, 24.6, 54.4, 100.0, 500.0), n_quad: int = 4000):
+    """Photon fractions and photon-weighted cross sections of a blackbody of
+    temperature T over bins above the HI threshold (hydrogenic sigma0 (nu/nu0)^-3):
+    frac_b = int_b B_nu/(h nu) / int_all, sigma_b = int_b sigma n_nu / int_b n_nu.
+    Returns (frac [nb], sigma [nb], edges in Hz)."""
+    ev = 1.602176634e-12
+    nu_edges = np.array(edges_ev) * ev / H_PLANCK
+    x = lambda nu: H_PLANCK * nu / (K_BOLTZ * T)
+    frac, sig = [], []
+    for lo, hi in zip(nu_edges[:-1], nu_edges[1:]):
+        nu = np.linspace(lo, hi, n_quad)
+        n_nu = nu ** 2 / np.expm1(x(nu))              # photon number per frequency (B_nu / h nu)
+        s = SIGMA0 * (nu / NU0) ** -3
+        w = np.trapezoid(n_nu, nu)
+        frac.append(w)
+        sig.append(np.trapezoid(s * n_nu, nu) / w)
+    frac = np.array(frac) / np.sum(frac)
+    return frac, np.array(sig), nu_edges
+
+
+def clumpy(n: int = 256, nside: int = 8, seed: int = 5, sigma: float = 1.5, n_clumps: int = 200,
+           overdensity: float = 100.0, n_src: int = 8, Q: float = 5e48, box_kpc: float = 6.6,
+           nH_mean: float = 1e-3, x0: float = 1e-4) -> HIICase:
+    """Clumpy medium: lognormal density (sigma, P(k) ~ k^-3) plus n_clumps spheres
+    (centres uniform, radius uniform in [2, 8] cells) at overdensity x the mean,
+    then scaled to mean n_H nH_mean; n_src sources of Q photons/s at uniform
+    positions."""
+    rng = np.random.default_rng(seed)
+    rho = lognormal_density(n, sigma, -3.0, rng)
+    centres = rng.uniform(0, n, size=(n_clumps, 3))
+    radii = rng.uniform(2.0, 8.0, size=n_clumps)
+    g = np.arange(n) + 0.5
+    for c, r in zip(centres, radii):
+        lo = np.maximum(np.floor(c - r).astype(int), 0)
+        hi = np.minimum(np.ceil(c + r).astype(int) + 1, n)
+        zz, yy, xx = np.meshgrid(g[lo[2]:hi[2]], g[lo[1]:hi[1]], g[lo[0]:hi[0]], indexing="ij")
+        inside = (xx - c[0]) ** 2 + (yy - c[1]) ** 2 + (zz - c[2]) ** 2 <= r * r
+        blk = rho[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]]
+        blk[inside] = overdensity
+    rho /= rho.mean()
+    pos = rng.uniform(0.5, n - 0.5, size=(n_src, 3))
+    dx = box_kpc * KPC / n
+    return HIICase("clumpy", nside, n, nH_mean * rho, np.full((n, n, n), 1.0 - x0), pos, np.full(n_src, Q),
+                   chem_constants(1e4, dx), 1e-6, box_kpc * KPC)

@@ -121,3 +121,23 @@ def test_full_size_hii_region_is_a_fixed_point(orc):
     g = 4 * math.pi * G * jin + gpt
     y_check = orc.balance_eq(nH.ravel()[cells], ch["alphaB"], ch["gcoll"], g)
     assert rel(y.ravel()[cells], y_check) < 1e-4
+
+
+def test_iteration_with_source_bins_matches_oracle(orc):
+    """Point sources over three frequency bins (blackbody fractions, photon-weighted
+    cross sections) inside the RT / balance iteration."""
+    case = wl.hii_region(n=16, nside=2, box_kpc=1.6)
+    frac, sig, _ = wl.blackbody_bins(edges_ev=(13.6, 24.6, 54.4, 200.0))
+    sw = art.ArtSweep(case.nH.shape, case.nside, 1, field_form=art.ART_FIELDS_EPS, dx_cm=case.chem["dx"])
+    sw.set_source_spectrum(sig, frac)
+    nH = torch.as_tensor(case.nH, dtype=torch.float64, device="cuda")
+    y = torch.as_tensor(case.y0, dtype=torch.float64, device="cuda").clone()
+    srcs = [(p[0], p[1], p[2], q) for p, q in zip(case.pos, case.Q)]
+    rep, hist = sw.iterate(nH, case.chem, srcs, y, tol=1e-6, max_iter=300)
+    sw.close()
+    y_o, it_o, _, conv = orc.iterate(case.nH, case.nside, case.chem, case.pos, case.Q, case.y0, 1e-6, 300,
+                                     sigma_bins=sig, frac_bins=frac)
+    assert conv and rep.converged and abs(rep.iterations - it_o) <= 1
+    yg = y.cpu().numpy()
+    assert rel(yg, y_o) < 1e-4
+    assert rel(1 - yg, 1 - y_o) < 1e-4

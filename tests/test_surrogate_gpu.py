@@ -53,9 +53,12 @@ def test_sample_matches_oracle(orc):
                         coarse_factor=f, coarse_nside=nside_c)
     torch.cuda.synchronize()
     sw.close()
-    # oracle: kappa = y nH sigma0 dx, eps proportional to (x nH)^2 (the features and target are scale-free in eps)
+    # oracle: kappa = y nH sigma0 dx and the iteration's emissivity G h nu0 (alpha_A - alpha_B) (x nH)^2 dx / dnu
+    # (same scale as the library, so that FP32 rounds the same values)
+    G = orc.band_integral(ch["sigma0"], ch["h"], ch["nu0"], ch["nu0"] + ch["dnu"])
     kap = f32(y * nH * ch["sigma0"] * ch["dx"])
-    eps = f32(((1.0 - y) * nH) ** 2 * 1e-20)
+    coef = G * ch["h"] * ch["nu0"] * (ch["alphaA"] - ch["alphaB"]) * ch["dx"] / ch["dnu"]
+    eps = f32(coef * ((1.0 - y) * nH) ** 2)
     jin_o, _, _ = orc.sweep(kap, eps, nside, field_form=1)
     kc, ec = sg.restrict(kap, f), sg.restrict(eps, f)
     jc_o = sg.prolong(orc.sweep(f32(kc), f32(ec), nside_c, field_form=1)[0], f)
