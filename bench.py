@@ -53,9 +53,10 @@ EX2_PER_CLK_SM = 32
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
-def recorded_traffic(workload: str):
+def recorded_traffic(workload: str, variant: int, persistent: int):
     """DRAM bytes per sweep launch from the committed ncu summary, if it was
-    taken on this workload with the kernel source as it is now; else None."""
+    taken on this workload, kernel variant and launch form with the kernel
+    source as it is now; else None."""
     import hashlib
     path = os.path.join(HERE, "profiles", f"traffic_sweep_block_{workload}.txt")
     src = os.path.join(HERE, "paper_1410_0763_gb300", "csrc", "art_kernels.cuh")
@@ -64,7 +65,8 @@ def recorded_traffic(workload: str):
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
     except OSError:
         return None
-    if rec.get("kernel_source_sha256") != digest:
+    if rec.get("kernel_source_sha256") != digest or int(rec.get("variant", -1)) != variant or \
+            int(rec.get("persistent", -1)) != persistent:
         return None
     return int(rec["dram_bytes_per_launch"])
 
@@ -76,6 +78,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="grf64")
+    p.add_argument("--no-autotune", action="store_true", help="keep the default kernel variant")
+    p.add_argument("--no-graph", action="store_true", help="plain launches instead of CUDA-graph replay")
     p.add_argument("--no-extra", action="store_true", help="skip the side measurements (128^3, 256^3, 48-grid batch, 128^3 ionization solve)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -432,9 +436,11 @@ def run_ours(args, d: Dist):
     G = band_G()
     k = torch.as_tensor(case.kappa, dtype=torch.float32, device=dev)
     s = torch.as_tensor(case.src, dtype=torch.float32, device=dev)
-    sw = art.ArtSweep(k.shape, case.nside)
+    sw = art.ArtSweep(k.shape, case.nside, graph=not args.no_graph)
     sw.set_fields(k, s)
     sw.set_band([G])
+    if not args.no_autotune:
+        sw.autotune(3)          # untimed: the library's own variant / launch-form choice
     st = sw.stats
     seg = int(st.segments)
     J, Jin, gam = torch.empty_like(k), torch.empty_like(k), torch.empty_like(k)
@@ -526,9 +532,12 @@ def run_ours(args, d: Dist):
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"weak x{d.world} (independent grid per GPU)"},
         "roofline": {"bound": "alu", "achieved": achieved_gseg, "peak": peak_gseg, "unit": "Gseg/s",
-                     "frac": achieved_gseg / peak_gseg, "traffic": recorded_traffic(args.workload),
+                     "frac": achieved_gseg / peak_gseg,
+                     "traffic": recorded_traffic(args.workload, int(st.variant), int(st.persistent)),
                      "traffic_unit": "DRAM bytes per sweep launch (ncu, cold L2)",
-                     "kernel": "sweep_block_kernel", "kernel_share_of_step": sweep_share,
+                     "kernel": ("sweep_queue_kernel" if st.persistent else "sweep_block_kernel") +
+                               f" variant {st.variant} (tile {st.tile_b}x{st.tile_c}, slab {st.slab})",
+                     "kernel_share_of_step": sweep_share,
                      "peak_basis": f"MUFU ex2 issue rate: 1 exp per segment, {ex2}/clk/SM (measured) x "
                                    f"{n_sm} SMs x {sm_mhz:.0f} MHz (median SM clock under load)",
                      "pipes_per_clk_sm": pipes},

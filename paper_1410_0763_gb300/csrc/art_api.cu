@@ -129,6 +129,9 @@ const KVariant kVariants[] = {
     ART_V(float, ART_FP32, 32, 16, 8, 256, 1, 2),   //  9
     ART_V(float, ART_FP32, 32, 8, 4, 128, 2, 5),    // 10
     ART_V(double, ART_FP64, 16, 16, 4, 128, 1, 1),  // 11: default FP64
+    ART_V(float, ART_FP32, 64, 8, 4, 256, 2, 2),    // 12: wide tiles (less halo along b)
+    ART_V(float, ART_FP32, 128, 8, 4, 512, 2, 1),   // 13
+    ART_V(float, ART_FP32, 64, 8, 2, 256, 2, 3),    // 14
 };
 #undef ART_V
 const int kNumVariants = int(sizeof(kVariants) / sizeof(kVariants[0]));

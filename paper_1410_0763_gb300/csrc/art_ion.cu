@@ -95,13 +95,55 @@ template <int NB, bool SCALED> __global__ void __launch_bounds__(128) point_sour
                               : (stp[k] < 0 ? (float)((cur[k] - s[k]) * rn[k]) : INFINITY);
             dl[k] = stp[k] ? (float)fabs(rn[k]) : INFINITY;
         }
-        float tau[NB];
+        // March in rounds of U steps: first the U cells and path lengths (the
+        // cell walk does not depend on kappa), with their kappa loads issued
+        // together, then the U optical-depth updates in order.
+        constexpr int U = 4;
+        constexpr int NK = SCALED ? 1 : NB;   // kappa fields marched
+        float tau[NK];
 #pragma unroll
-        for (int b = 0; b < NB; ++b) tau[b] = 0.0f;
+        for (int b = 0; b < NK; ++b) tau[b] = 0.0f;
         const long long target = cell;
-        for (int it = 0; it < maxsteps; ++it) {
-            const long long ci = ((long long)cur[2] * p.ny + cur[1]) * p.nx + cur[0];
-            if (ci == target) {
+        int state = 0;   // 0 marching, 1 at the target cell, 2 left the box (cannot happen)
+        int it = 0;
+        while (state == 0 && it < maxsteps) {
+            float kv[U][NK], dv[U];
+            int nu = 0;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (state == 0 && it < maxsteps) {
+                    const long long ci = ((long long)cur[2] * p.ny + cur[1]) * p.nx + cur[0];
+                    if (ci == target) {
+                        state = 1;
+                    } else {
+                        const float ds = fminf(r[0], fminf(r[1], r[2]));
+#pragma unroll
+                        for (int b = 0; b < NK; ++b) kv[u][b] = __ldg(p.kappa + (long long)b * p.ncell + ci);
+                        dv[u] = ds;
+                        nu = u + 1;
+                        ++it;
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            r[k] -= ds;
+                            if (r[k] <= 1e-6f) {   // this axis' plane is crossed here (ties within 1e-6 together)
+                                cur[k] += stp[k];
+                                if (cur[k] < 0 || cur[k] >= dims[k]) state = 2;
+                                r[k] += dl[k];
+                            }
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (u < nu) {
+#pragma unroll
+                    for (int b = 0; b < NK; ++b) tau[b] = fmaf(kv[u][b], dv[u], tau[b]);
+                }
+        }
+        if (state == 1) {
+            const long long ci = target;
+            {
                 // passage through the target cell, exactly, from its faces
                 double rin = 0.0, rout = INFINITY;
                 for (int k = 0; k < 3; ++k) {
@@ -121,23 +163,7 @@ template <int NB, bool SCALED> __global__ void __launch_bounds__(128) point_sour
                     const double ph = x > 0.0 ? -expm1(-x) / x : 1.0;
                     g += 3.0 * p.Qb[(long long)a * p.nbins + b] * p.sigma[b] * exp(-tb) * ph / den;
                 }
-                break;
             }
-            const float ds = fminf(r[0], fminf(r[1], r[2]));
-#pragma unroll
-            for (int b = 0; b < (SCALED ? 1 : NB); ++b)
-                tau[b] = fmaf(__ldg(p.kappa + (long long)b * p.ncell + ci), ds, tau[b]);
-            bool out = false;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                r[k] -= ds;
-                if (r[k] <= 1e-6f) {   // this axis' plane is crossed here (ties within 1e-6 together)
-                    cur[k] += stp[k];
-                    out |= cur[k] < 0 || cur[k] >= dims[k];
-                    r[k] += dl[k];
-                }
-            }
-            if (out) break;   // cannot happen for a target inside the box
         }
     }
     p.gamma[cell] = (float)g;

@@ -138,7 +138,7 @@ def test_autotune_keeps_parity(orc):
     s = torch.cat([torch.as_tensor(f[1].ravel(), dtype=torch.float32) for f in fields]).cuda()
     sw.set_fields(k, s)
     best = sw.autotune(2)
-    assert 1 <= best <= 10
+    assert 1 <= best <= 14 and best != 11     # FP32 variants (11 is the FP64 one)
     assert sw.stats.variant == best
     Jin = torch.empty_like(k)
     sw.sweep(J_in=Jin)

@@ -58,7 +58,7 @@ def test_fp64_lognormal_16_nside1(orc):
     assert rel(J, j_o) < 1e-12
 
 
-@pytest.mark.parametrize("tiles", [(32, 16, 4), (32, 32, 4), (32, 8, 4), (32, 16, 8)])
+@pytest.mark.parametrize("tiles", [(32, 16, 4), (32, 32, 4), (32, 8, 4), (32, 16, 8), (64, 8, 4), (128, 8, 4), (64, 8, 2)])
 def test_fp32_ragged_noncubic(orc, tiles):
     rng = np.random.default_rng(7)
     shape = (21, 26, 37)   # ragged against every tile size
