@@ -97,6 +97,23 @@ art_status art_net_train_step(art_net *net, int nx, int ny, int nz, const float 
                               double *loss, void *stream);
 
 /*
+ * Synchronize `stream` and report whether any convolution kernel of the
+ * network gave up a bounded wait since the last check: ART_E_TIMEOUT (the
+ * error word is then cleared; outputs of those launches are undefined, the
+ * network and the CUDA context stay usable) or ART_OK.  The convolution
+ * kernels bound every wait on a shared-memory barrier to about one second,
+ * then drain their copies, free tensor memory and return.
+ */
+art_status art_net_check(art_net *net, void *stream);
+
+/*
+ * Test hook for the bounded waits: while on != 0, the convolution kernels
+ * issue no loads, so their waits run out (about one second per launch) and
+ * the next art_net_check reports ART_E_TIMEOUT.  Off by default.
+ */
+art_status art_net_set_test_stall(art_net *net, int on);
+
+/*
  * Training sample of the solver state y (device [z][y][x] doubles) on the
  * context's grid: kappa = y nH sigma0 dx and eps as in art_iterate_ionization,
  * a plain sweep for J^in and a coarse sweep (factor coarse_factor, N_side

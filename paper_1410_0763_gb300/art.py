@@ -149,6 +149,10 @@ def load() -> C.CDLL:
         lib.art_net_train.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P, C.c_int, C.c_uint64,
                                       C.POINTER(C.c_double), P]
         lib.art_warm_options_default.argtypes = [C.POINTER(ArtWarmOptions)]
+        lib.art_net_check.argtypes = [P, P]
+        lib.art_net_check.restype = C.c_int
+        lib.art_net_set_test_stall.argtypes = [P, C.c_int]
+        lib.art_net_set_test_stall.restype = C.c_int
         lib.art_iterate_ionization_warm.argtypes = [P, P, C.POINTER(ArtChem), P, C.POINTER(ArtSource), C.c_int,
                                                     C.c_double, C.c_int, C.POINTER(ArtWarmOptions), P,
                                                     C.POINTER(C.c_double), C.POINTER(ArtWarmReport), P]
@@ -590,6 +594,13 @@ class ArtNet:
     def _check(self, st):
         if st != ART_OK:
             raise ArtError(st, load().art_net_last_error(self._net).decode())
+
+    def check(self, stream=None) -> int:
+        """Synchronize and return the bounded-wait status of the network's kernels (ART_OK or ART_E_TIMEOUT)."""
+        return load().art_net_check(self._net, C.c_void_p(_stream(stream)))
+
+    def set_test_stall(self, on: bool):
+        self._check(load().art_net_set_test_stall(self._net, 1 if on else 0))
 
     def get_params(self) -> np.ndarray:
         out = np.empty(ART_NET_PARAMS, dtype=np.float32)

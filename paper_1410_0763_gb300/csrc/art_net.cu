@@ -113,6 +113,7 @@ struct art_net {
     double *lpart = nullptr, *loss = nullptr;
     CUtensorMap amap_X, amap_h[3], amap_g16, amap_gA, amap_gB;
     int sms = 152;
+    int test_stall = 0;
 };
 
 namespace {
@@ -216,6 +217,7 @@ art_status conv(art_net *n, const CUtensorMap &amap, const CUtensorMap &wmap, co
     a.dil = dil;
     a.ntiles = (int)(n->V / TILE_M);
     a.err = n->d_err;
+    a.test_stall = n->test_stall;
     const int grid = std::min(a.ntiles, 2 * n->sms);
     kern<<<grid, CONV_THREADS, L::BYTES, st>>>(amap, wmap, a);
     NCK(n, cudaGetLastError());
@@ -603,6 +605,19 @@ art_status art_net_gradients(art_net *n, int nx, int ny, int nz, const float *X,
     NCK(n, cudaMemcpyAsync(loss, n->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
     if (grads) NCK(n, cudaMemcpyAsync(grads, n->grad, ART_NET_PARAMS * sizeof(float), cudaMemcpyDeviceToHost, st));
     return check_err(n, st);
+}
+
+art_status art_net_check(art_net *n, void *stream)
+{
+    if (!n) return ART_E_INVALID;
+    return check_err(n, static_cast<cudaStream_t>(stream));
+}
+
+art_status art_net_set_test_stall(art_net *n, int on)
+{
+    if (!n) return ART_E_INVALID;
+    n->test_stall = on != 0;
+    return ART_OK;
 }
 
 art_status art_net_train(art_net *n, int nx, int ny, int nz, int n_samples, const float *X, const float *t,

@@ -15,7 +15,7 @@ using bf16 = __nv_bfloat16;
 constexpr int TILE_M = 128;          // voxels per MMA tile (accumulator lanes)
 constexpr int CONV_THREADS = 192;    // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr int CONV_STAGES = 6;       // A-operand ring (one tap per stage)
-constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz: bounded waits
+constexpr long long kWaitCycles = 2000000000LL;   // ~1 s at 2 GHz: bounded waits
 
 enum { MODE_RELU = 0, MODE_OUT = 1, MODE_DGRAD = 2 };
 enum { ERR_TIMEOUT_PRODUCER = 1, ERR_TIMEOUT_MMA = 2, ERR_TIMEOUT_EPILOGUE = 4 };
@@ -28,6 +28,7 @@ struct ConvArgs {
     int nx, ny, nz, dil;
     int ntiles;
     int *err;              // device error word (timeouts)
+    int test_stall;        // test hook: the producer issues no loads, so the waits run out
 };
 
 // ---------------------------------------------------------------------------
@@ -66,7 +67,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     const long long t0 = clock64();
     for (;;) {
         if (mbar_test(bar, parity)) return true;
-        if (*abort) return false;
+        if (abort && *abort) return false;
         if (clock64() - t0 > kWaitCycles) return false;
     }
 }
@@ -216,11 +217,13 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
     if (warp == 0) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
-            mbar_expect_tx(w_bar, L::W_BYTES);
-            for (int t = 0; t < 27; ++t) tma_load_2d(sW + t * L::W_TAP, &wmap, w_bar, 0, t * COUT);
+            if (!p.test_stall) {
+                mbar_expect_tx(w_bar, L::W_BYTES);
+                for (int t = 0; t < 27; ++t) tma_load_2d(sW + t * L::W_TAP, &wmap, w_bar, 0, t * COUT);
+            }
             int s = 0;
             uint32_t ph = 0;
-            for (int tile = blockIdx.x; tile < p.ntiles && !*abort; tile += gridDim.x) {
+            for (int tile = blockIdx.x; tile < p.ntiles && !*abort && !p.test_stall; tile += gridDim.x) {
                 const long long vb = (long long)tile * TILE_M;
                 const long long plane = (long long)nx * ny;
                 const int z = (int)(vb / plane);
@@ -242,12 +245,14 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                 }
             }
             // drain: every load issued has landed before the CTA may exit
+            // (time-bounded waits that an abort does not cut short)
+            if (!p.test_stall) mbar_wait(w_bar, 0, nullptr);
             for (int k = 0; k < CONV_STAGES; ++k) {
                 if (--s < 0) {
                     s = CONV_STAGES - 1;
                     ph ^= 1u;
                 }
-                mbar_wait(full_bar(s), ph, abort);
+                mbar_wait(full_bar(s), ph, nullptr);
             }
         }
     } else if (warp == 1) {
@@ -292,7 +297,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
             }
             // every MMA issued has completed before TMEM is released
             mma_commit(done_bar);
-            mbar_wait(done_bar, 0, abort);
+            mbar_wait(done_bar, 0, nullptr);
         }
     } else {
         // ---------------- epilogue (warps 2-5) ----------------
@@ -302,9 +307,11 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
         for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x, ++it) {
             const int acc = it & 1;
             const uint32_t aph = (uint32_t)(it >> 1) & 1u;
-            if (!mbar_wait(tfull_bar(acc), aph, abort)) {
+            // the warp agrees before the warp-collective TMEM loads
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull_bar(acc), aph, abort));
+            if (!ok) {
                 *abort = 1;
-                atomicOr(p.err, ERR_TIMEOUT_EPILOGUE);
+                if (lane == 0) atomicOr(p.err, ERR_TIMEOUT_EPILOGUE);
                 break;
             }
             tc_fence_after();

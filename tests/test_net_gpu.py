@@ -123,3 +123,27 @@ def test_bad_shapes_are_rejected():
         net.forward(X, o, (10, 10, 10))
     assert e.value.status == art.ART_E_INVALID
     net.close()
+
+
+def test_bounded_waits_report_a_timeout_and_the_network_recovers():
+    """The test hook stops the TMA loads, so every convolution kernel's bounded
+    waits run out (about a second each); the host sees ART_E_TIMEOUT, and
+    the next passes are correct again (no GPU fault, context usable)."""
+    shape, dil = (16, 16, 16), (1, 2, 4, 8)
+    net = art.ArtNet(dilation=dil)
+    flat = art.ArtNet.join_params(params_with_bias(3)).astype(np.float32)
+    net.set_params(flat)
+    X, _ = random_case(shape, 1)
+    Xd = torch.as_tensor(X).cuda().reshape(-1)
+    o = torch.empty(int(np.prod(shape)), dtype=torch.float32, device="cuda")
+    net.set_test_stall(True)
+    net.forward(Xd, o, shape)
+    assert net.check() == art.ART_E_TIMEOUT
+    assert net.check() == art.ART_OK            # the error word was cleared
+    net.set_test_stall(False)
+    net.forward(Xd, o, shape)
+    assert net.check() == art.ART_OK
+    got = o.cpu().numpy().astype(np.float64).reshape(shape)
+    want, _ = sg.forward(X.astype(np.float64), oracle_params(flat), dil, bf16_mode=True)
+    assert relnorm(got, want) < 2e-3
+    net.close()
