@@ -50,6 +50,11 @@ L2_FLUSH_BYTES = 256 << 20      # > 129 MB L2
 # MUFU ex2 results per clock per SM measured on GB300 (profiles/peaks_gb300.md);
 # bench.py re-measures it on the box (art_measure_pipes) and uses the live value
 EX2_PER_CLK_SM = 32
+FFMA_PER_CLK_SM = 128
+# FP32 operations of one segment, counted from Eq. (rt) and the deposit of
+# Eq. (averaged_intensity): dtau = kappa ds; 1 - e^-dtau; I_in (1 - e) / kappa
+# (two products) added to the cell sum; I_out = S + (I_in - S) e (two).
+FP32_OPS_PER_SEG = 7
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
@@ -473,9 +478,15 @@ def run_ours(args, d: Dist):
     try:
         pipes = art.art_measure_pipes()
         ex2 = round(pipes["ex2"])
+        ffma = round(pipes["ffma"])
     except Exception:  # pragma: no cover
-        pipes, ex2 = None, EX2_PER_CLK_SM
-    peak_gseg = ex2 * n_sm * sm_mhz * 1e6 / 1e9
+        pipes, ex2, ffma = None, EX2_PER_CLK_SM, FFMA_PER_CLK_SM
+    # two roofs for the algorithmic work of one segment (Eq. rt and the
+    # path-averaged deposit): one exponential on the MUFU pipe, and
+    # FP32_OPS_PER_SEG FP32 operations on the FMA pipe; the lower one binds
+    peak_mufu = ex2 * n_sm * sm_mhz * 1e6 / 1e9
+    peak_fp32 = ffma / FP32_OPS_PER_SEG * n_sm * sm_mhz * 1e6 / 1e9
+    peak_gseg = min(peak_mufu, peak_fp32)
     sweep_share = pr.sweep_ms / max(pr.sweep_ms + pr.reduce_ms, 1e-9)
 
     # end to end through the C ABI with host buffers (pinned), copies included
@@ -538,8 +549,11 @@ def run_ours(args, d: Dist):
                      "kernel": ("sweep_queue_kernel" if st.persistent else "sweep_block_kernel") +
                                f" variant {st.variant} (tile {st.tile_b}x{st.tile_c}, slab {st.slab})",
                      "kernel_share_of_step": sweep_share,
-                     "peak_basis": f"MUFU ex2 issue rate: 1 exp per segment, {ex2}/clk/SM (measured) x "
-                                   f"{n_sm} SMs x {sm_mhz:.0f} MHz (median SM clock under load)",
+                     "peak_basis": f"binding roof = min(FP32: {ffma}/clk/SM (measured FFMA) / "
+                                   f"{FP32_OPS_PER_SEG} ops per segment = {peak_fp32:.0f} Gseg/s, "
+                                   f"MUFU: 1 ex2 per segment x {ex2}/clk/SM (measured) = {peak_mufu:.0f} Gseg/s), "
+                                   f"x {n_sm} SMs x {sm_mhz:.0f} MHz (median SM clock under load)",
+                     "peak_fp32_gseg": peak_fp32, "peak_mufu_gseg": peak_mufu,
                      "pipes_per_clk_sm": pipes},
         "e2e": e2e,
         "gpu_launches": int(args.steps * st.launches),
