@@ -140,6 +140,7 @@ struct HostTables {
     std::vector<ClassDev> classes;
     std::vector<DirDev> dirs;
     std::vector<SlabGeom> geo;    // concatenated per class-sorted direction
+    std::vector<int> na;          // slabs of each direction, in table order
     std::vector<WorkItem> work;
     std::vector<art_grid_host> grids;
     long long plane_elems = 0;
@@ -211,6 +212,7 @@ void build_tables(const art_ctx *ctx, HostTables &t)
             for (int d : members) {
                 std::vector<SlabGeom> g;
                 slab_geometry(fr[d], C.Na, g);
+                t.na.push_back(C.Na);
                 DirDev D;
                 D.seg_off = seg_off;
                 D.plane_off = plane_off;
@@ -250,15 +252,29 @@ void build_tables(const art_ctx *ctx, HostTables &t)
     t.jpart_elems = jpart_off;
 }
 
-template <typename real> std::vector<SegEntry<real>> pack_segs(const std::vector<SlabGeom> &geo)
+// Segment entries of the tables; the code also carries, per slab, the column
+// shifts that the direction still makes from this slab to the end of its slab
+// block (the upstream cone the kernel must recompute), so the kernel reads
+// them instead of summing them.  `na` holds each direction's slab count, in
+// table order.
+template <typename real>
+std::vector<SegEntry<real>> pack_segs(const std::vector<SlabGeom> &geo, const std::vector<int> &na, int blk)
 {
     std::vector<SegEntry<real>> out(geo.size());
-    for (size_t i = 0; i < geo.size(); ++i) {
-        const SlabGeom &g = geo[i];
-        out[i].ds1 = real(g.ds[0]);
-        out[i].ds2 = real(g.ds[1]);
-        out[i].ds3 = real(g.ds[2]);
-        out[i].code = (g.nseg - 1) | (g.cfirst << 2) | (g.shb << 3) | (g.shc << 4);
+    size_t base = 0;
+    for (int n : na) {
+        for (int m = n - 1; m >= 0; --m) {
+            const SlabGeom &g = geo[base + m];
+            const bool last_in_block = (m + 1) % blk == 0 || m + 1 == n;
+            const int rb = g.shb + (last_in_block ? 0 : ((out[base + m + 1].code >> 5) & 15));
+            const int rc = g.shc + (last_in_block ? 0 : ((out[base + m + 1].code >> 9) & 15));
+            SegEntry<real> &e = out[base + m];
+            e.ds1 = real(g.ds[0]);
+            e.ds2 = real(g.ds[1]);
+            e.ds3 = real(g.ds[2]);
+            e.code = (g.nseg - 1) | (g.cfirst << 2) | (g.shb << 3) | (g.shc << 4) | (rb << 5) | (rc << 9);
+        }
+        base += n;
     }
     return out;
 }
@@ -345,11 +361,11 @@ art_status setup_variant(art_ctx *ctx, int variant)
     if ((s = dev_alloc(ctx, &ctx->d_gridinfo, gb)) != ART_OK) return s;
     ctx->gridinfo_bytes = gb;
     if (ctx->prec == ART_FP64) {
-        auto v = pack_segs<double>(t.geo);
+        auto v = pack_segs<double>(t.geo, t.na, ctx->BLK);
         CK(ctx, cudaMemcpy(ctx->d_segs, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice));
         if ((s = upload_gridinfo<double>(ctx)) != ART_OK) return s;
     } else {
-        auto v = pack_segs<float>(t.geo);
+        auto v = pack_segs<float>(t.geo, t.na, ctx->BLK);
         CK(ctx, cudaMemcpy(ctx->d_segs, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice));
         if ((s = upload_gridinfo<float>(ctx)) != ART_OK) return s;
     }

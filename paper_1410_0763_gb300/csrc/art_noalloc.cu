@@ -205,6 +205,15 @@ extern "C" art_status art_sweep_noalloc(const art_grid *grid, int n_side, const 
             D.na = g_frame[g_order[i]].na;
             g_dirs[ndir++] = D;
             slabs_into(g_frame[g_order[i]], C.Na, g_segs + nslab);
+            // remaining column shifts to the end of each slab block (read by the kernel)
+            for (int m = C.Na - 1; m >= 0; --m) {
+                SegEntry<float> &e = g_segs[nslab + m];
+                const bool last = (m + 1) % kBLK == 0 || m + 1 == C.Na;
+                const int nxt = last ? 0 : g_segs[nslab + m + 1].code;
+                const int rb = ((e.code >> 3) & 1) + ((nxt >> 5) & 15);
+                const int rc = ((e.code >> 4) & 1) + ((nxt >> 9) & 15);
+                e.code = (e.code & 31) | (rb << 5) | (rc << 9);
+            }
             nslab += C.Na;
             plane_elems += (long long)C.Nb * C.Nc;
         }
