@@ -41,7 +41,9 @@ template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };
 
 // Segment table entry of one (direction, slab).
-// code bits: 0-1 nseg-1, 2 c-plane crossed first, 3 b-shift, 4 c-shift.
+// code bits: 0-1 nseg-1, 2 c-plane crossed first, 3 b-shift, 4 c-shift,
+// 5-8 and 9-12 the b- and c-shifts from this slab to the end of its slab
+// block (this slab included).
 template <typename real> struct SegEntry {
     real ds1, ds2, ds3;
     int code;
@@ -393,24 +395,23 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<real> &p, int item, u
             dsm[dl] = q;
         }
         // per (group, slab): max segment count and the union of the
-        // directions' remaining upstream cones at the start of the slab
+        // directions' remaining upstream cones at the start of the slab (the
+        // table carries each direction's remaining shifts to the block end)
         for (int e = tid; e < (cntk / K) * BLK; e += NT) {
             const int grp = e / BLK, i = e - grp * BLK;
             int nsmax = 1, ub = 0, uc = 0;
             if (i < Bp) {
+                int code[K];
+#pragma unroll
                 for (int k = 0; k < K; ++k) {
                     const int dl = grp * K + k;
-                    if (dl >= cnt) break;
-                    const long long so = p.dirs[c0 + dl].seg_off + m0;
-                    int rb = 0, rc = 0;
-                    for (int i2 = i; i2 < Bp; ++i2) {
-                        const int code = p.segs[so + i2].code;
-                        rb += (code >> 3) & 1;
-                        rc += (code >> 4) & 1;
-                    }
-                    ub = max(ub, rb);
-                    uc = max(uc, rc);
-                    nsmax = max(nsmax, (p.segs[so + i].code & 3) + 1);
+                    code[k] = dl < cnt ? p.segs[p.dirs[c0 + dl].seg_off + m0 + i].code : 0;
+                }
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    ub = max(ub, (code[k] >> 5) & 15);
+                    uc = max(uc, (code[k] >> 9) & 15);
+                    nsmax = max(nsmax, (code[k] & 3) + 1);
                 }
             }
             gsm[e] = make_int4(nsmax, ub, uc, 0);
