@@ -59,6 +59,9 @@ struct PtArgs {
 };
 
 constexpr int kMaxBins = 4;   // point-source kernels are compiled for 1-4 bins
+#ifndef PT_UNROLL
+#define PT_UNROLL 4                // march steps whose kappa loads are issued together
+#endif
 
 template <int NB, bool SCALED> __global__ void __launch_bounds__(128) point_source_kernel(const PtArgs p)
 {
@@ -98,7 +101,7 @@ template <int NB, bool SCALED> __global__ void __launch_bounds__(128) point_sour
         // March in rounds of U steps: first the U cells and path lengths (the
         // cell walk does not depend on kappa), with their kappa loads issued
         // together, then the U optical-depth updates in order.
-        constexpr int U = 4;
+        constexpr int U = PT_UNROLL;
         constexpr int NK = SCALED ? 1 : NB;   // kappa fields marched
         float tau[NK];
 #pragma unroll
