@@ -114,6 +114,14 @@ art_status art_net_check(art_net *net, void *stream);
 art_status art_net_set_test_stall(art_net *net, int on);
 
 /*
+ * Output planes per work item of the convolution kernels: 1, 2 or 4 (planes
+ * z, z + d, ... of one tile position share the loaded tap tiles), or 0 to
+ * choose by grid and dilation (the default).  Results do not depend on it.
+ * Errors: ART_E_INVALID.
+ */
+art_status art_net_set_plane_group(art_net *net, int planes);
+
+/*
  * Training sample of the solver state y (device [z][y][x] doubles) on the
  * context's grid: kappa = y nH sigma0 dx and eps as in art_iterate_ionization,
  * a plain sweep for J^in and a coarse sweep (factor coarse_factor, N_side

@@ -153,6 +153,8 @@ def load() -> C.CDLL:
         lib.art_net_check.restype = C.c_int
         lib.art_net_set_test_stall.argtypes = [P, C.c_int]
         lib.art_net_set_test_stall.restype = C.c_int
+        lib.art_net_set_plane_group.argtypes = [P, C.c_int]
+        lib.art_net_set_plane_group.restype = C.c_int
         lib.art_iterate_ionization_warm.argtypes = [P, P, C.POINTER(ArtChem), P, C.POINTER(ArtSource), C.c_int,
                                                     C.c_double, C.c_int, C.POINTER(ArtWarmOptions), P,
                                                     C.POINTER(C.c_double), C.POINTER(ArtWarmReport), P]
@@ -598,6 +600,10 @@ class ArtNet:
     def check(self, stream=None) -> int:
         """Synchronize and return the bounded-wait status of the network's kernels (ART_OK or ART_E_TIMEOUT)."""
         return load().art_net_check(self._net, C.c_void_p(_stream(stream)))
+
+    def set_plane_group(self, planes: int):
+        """Output planes per convolution work item: 1, 2, 4, or 0 for the automatic choice."""
+        self._check(load().art_net_set_plane_group(self._net, int(planes)))
 
     def set_test_stall(self, on: bool):
         self._check(load().art_net_set_test_stall(self._net, 1 if on else 0))

@@ -114,6 +114,7 @@ struct art_net {
     CUtensorMap amap_X, amap_h[3], amap_g16, amap_gA, amap_gB;
     int sms = 152;
     int test_stall = 0;
+    int plane_group = 0;   // output planes per convolution work item (0: by grid and dilation)
 };
 
 namespace {
@@ -195,17 +196,35 @@ art_status ensure_workspace(art_net *n, int nx, int ny, int nz)
     return ART_OK;
 }
 
+template <int CIN, int COUT, int MODE, int G>
+art_status conv_g(art_net *n, const CUtensorMap &amap, const CUtensorMap &wmap, const ConvArgs &a, cudaStream_t st)
+{
+    using L = ConvSmem<CIN, COUT, G>;
+    auto kern = conv_tc_kernel<CIN, COUT, MODE, G>;
+    // at most two CTAs per SM whenever their TMEM allocations (2 G COUT
+    // columns each) would not fit three times into the SM's 512 columns:
+    // the shared-memory request is raised so a third cannot be resident
+    constexpr int SMEM = (3 * L::NCOLS > 512 && L::BYTES < 80 * 1024) ? 80 * 1024 : L::BYTES;
+    static bool attr = false;
+    if (!attr) {
+        NCK(n, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
+        attr = true;
+    }
+    const long long plane = (long long)a.nx * a.ny;
+    const int nzg = (a.nz + G * a.dil - 1) / (G * a.dil) * a.dil;
+    const long long items = plane / TILE_M * nzg;
+    const int grid = (int)std::min<long long>(items, 2LL * n->sms);
+    kern<<<grid, CONV_THREADS, SMEM, st>>>(amap, wmap, a);
+    NCK(n, cudaGetLastError());
+    return ART_OK;
+}
+
+// Planes per work item: 4 when the grid holds four planes at this dilation,
+// else 2 or 1 (fewer planes beyond the grid to skip).
 template <int CIN, int COUT, int MODE>
 art_status conv(art_net *n, const CUtensorMap &amap, const CUtensorMap &wmap, const float *bias, const bf16 *mask,
                 bf16 *out, float *out_f32, int dil, cudaStream_t st)
 {
-    using L = ConvSmem<CIN, COUT>;
-    auto kern = conv_tc_kernel<CIN, COUT, MODE>;
-    static bool attr = false;
-    if (!attr) {
-        NCK(n, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES));
-        attr = true;
-    }
     ConvArgs a;
     a.bias = bias;
     a.mask = mask;
@@ -218,10 +237,10 @@ art_status conv(art_net *n, const CUtensorMap &amap, const CUtensorMap &wmap, co
     a.ntiles = (int)(n->V / TILE_M);
     a.err = n->d_err;
     a.test_stall = n->test_stall;
-    const int grid = std::min(a.ntiles, 2 * n->sms);
-    kern<<<grid, CONV_THREADS, L::BYTES, st>>>(amap, wmap, a);
-    NCK(n, cudaGetLastError());
-    return ART_OK;
+    const int g = n->plane_group > 0 ? n->plane_group : (n->nz >= 4 * dil ? 4 : (n->nz >= 2 * dil ? 2 : 1));
+    if (g >= 4) return conv_g<CIN, COUT, MODE, 4>(n, amap, wmap, a, st);
+    if (g == 2) return conv_g<CIN, COUT, MODE, 2>(n, amap, wmap, a, st);
+    return conv_g<CIN, COUT, MODE, 1>(n, amap, wmap, a, st);
 }
 
 art_status pack_weights(art_net *n, cudaStream_t st)
@@ -617,6 +636,15 @@ art_status art_net_set_test_stall(art_net *n, int on)
 {
     if (!n) return ART_E_INVALID;
     n->test_stall = on != 0;
+    return ART_OK;
+}
+
+art_status art_net_set_plane_group(art_net *n, int planes)
+{
+    if (!n) return ART_E_INVALID;
+    if (planes != 0 && planes != 1 && planes != 2 && planes != 4)
+        return nfail(n, ART_E_INVALID, "art_net_set_plane_group: 0 (auto), 1, 2 or 4");
+    n->plane_group = planes;
     return ART_OK;
 }
 

@@ -26,7 +26,7 @@ struct ConvArgs {
     bf16 *out;             // [V][COUT] (MODE_RELU, MODE_DGRAD)
     float *out_f32;        // [V] channel 0 (MODE_OUT)
     int nx, ny, nz, dil;
-    int ntiles;
+    int ntiles;            // 128-voxel tiles of the grid (grid sizing)
     int *err;              // device error word (timeouts)
     int test_stall;        // test hook: the producer issues no loads, so the waits run out
 };
@@ -143,31 +143,38 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
 // ---------------------------------------------------------------------------
 // Implicit-GEMM 3x3x3 convolution on tensor cores.
 //   out[v][co] = epilogue( sum_t sum_ci W[t][co][ci] * in[v + dil * off_t][ci] )
-// Activations are channels-last BF16 [V][C]; a tile is 128 consecutive
+// Activations are channels-last BF16 [V][C].  A tile is 128 consecutive
 // voxels (whole x rows), so each tap's operand tile is one TMA box of the
-// input shifted by dil * (dx, dy, dz), zero-filled outside the grid.  The
-// 27 tap tiles stream through a ring of shared-memory stages; all 27 tap
-// weight blocks stay in shared memory.  One thread issues the MMAs
-// (M = 128, N = COUT, K = 16 per instruction) into a double-buffered TMEM
-// accumulator that four epilogue warps drain.
+// input shifted by dil * (dx, dy, dz), zero-filled outside the grid.  A work
+// item is a group of G tiles at the same (x, y) in planes z0, z0 + d, ...,
+// z0 + (G-1) d: the input plane z0 + k d (k = -1..G) feeds output plane j
+// through tap dz = k - j, so each loaded tap tile serves up to three
+// accumulators and the group loads (G + 2) 9 tiles instead of 27 G.  Every
+// accumulator still receives its 27 taps in tap order.  The loaded tiles
+// stream through a ring of shared-memory stages; the 27 tap weight blocks
+// stay in shared memory.  One thread issues the MMAs (M = 128, N = COUT,
+// K = 16 per instruction) into double-buffered TMEM accumulators (G per
+// buffer) that four epilogue warps drain.
 // ---------------------------------------------------------------------------
-template <int CIN, int COUT> struct ConvSmem {
+template <int CIN, int COUT, int G> struct ConvSmem {
     static constexpr int A_BYTES = TILE_M * CIN * 2;
     static constexpr int W_TAP = COUT * CIN * 2;
     static constexpr int W_BYTES = 27 * W_TAP;
-    static constexpr int NCOLS = 2 * COUT < 32 ? 32 : 2 * COUT;   // power of two
+    static constexpr int NCOLS_RAW = 2 * G * COUT;
+    static constexpr int NCOLS = NCOLS_RAW <= 32 ? 32 : (NCOLS_RAW <= 64 ? 64 : (NCOLS_RAW <= 128 ? 128 : 256));
     static constexpr int BAR_OFF = W_BYTES + CONV_STAGES * A_BYTES;
     static constexpr int NBARS = 2 * CONV_STAGES + 1 + 2 + 2 + 1;
     static constexpr int BYTES = BAR_OFF + NBARS * 8 + 1024;        // + alignment slack
 };
 
-template <int CIN, int COUT, int MODE>
+template <int CIN, int COUT, int MODE, int G>
 __global__ void __launch_bounds__(CONV_THREADS, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap wmap, const ConvArgs p)
 {
-    using L = ConvSmem<CIN, COUT>;
+    using L = ConvSmem<CIN, COUT, G>;
     static_assert(CIN == 16 || CIN == 32, "16 or 32 input channels");
     static_assert(COUT == 16 || COUT == 32, "16 or 32 output channels");
+    static_assert(2 * G * COUT <= 256, "accumulators fit the TMEM allocation");
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
@@ -209,10 +216,18 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = s_tmem;
 
-    const int nx = p.nx, ny = p.ny, dil = p.dil;
-    const int bx = nx < TILE_M ? nx : TILE_M;
-    const int by = TILE_M / bx;
-    (void)by;
+    const int nx = p.nx, ny = p.ny, nz = p.nz, dil = p.dil;
+    const long long plane = (long long)nx * ny;
+    const int tpp = (int)(plane / TILE_M);                  // tiles per plane
+    const int nzg = (nz + G * dil - 1) / (G * dil) * dil;   // plane groups
+    const int nitems = tpp * nzg;
+    // work item -> (first plane z0, voxel offset of the tile inside a plane)
+    auto item_of = [&](int w, int &z0, long long &vb) {
+        const int zg = w / tpp, tp = w - zg * tpp;
+        z0 = (zg / dil) * (G * dil) + zg % dil;
+        vb = (long long)tp * TILE_M;
+    };
+    constexpr int NLOAD = (G + 2) * 9;
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
@@ -223,21 +238,21 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
             }
             int s = 0;
             uint32_t ph = 0;
-            for (int tile = blockIdx.x; tile < p.ntiles && !*abort && !p.test_stall; tile += gridDim.x) {
-                const long long vb = (long long)tile * TILE_M;
-                const long long plane = (long long)nx * ny;
-                const int z = (int)(vb / plane);
-                const long long rem = vb - (long long)z * plane;
-                const int y0 = (int)(rem / nx), x0 = (int)(rem - (long long)y0 * nx);
-                for (int t = 0; t < 27; ++t) {
+            for (int w = blockIdx.x; w < nitems && !*abort && !p.test_stall; w += gridDim.x) {
+                int z0;
+                long long vb;
+                item_of(w, z0, vb);
+                const int y0 = (int)(vb / nx), x0 = (int)(vb - (long long)y0 * nx);
+                for (int l = 0; l < NLOAD; ++l) {
                     if (!mbar_wait(empty_bar(s), ph ^ 1u, abort)) {
                         *abort = 1;
                         atomicOr(p.err, ERR_TIMEOUT_PRODUCER);
                         break;
                     }
-                    const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+                    const int k = l / 9 - 1, dy = (l / 3) % 3 - 1, dx = l % 3 - 1;
                     mbar_expect_tx(full_bar(s), L::A_BYTES);
-                    tma_load_4d(sA + s * L::A_BYTES, &amap, full_bar(s), 0, x0 + dx * dil, y0 + dy * dil, z + dz * dil);
+                    tma_load_4d(sA + s * L::A_BYTES, &amap, full_bar(s), 0, x0 + dx * dil, y0 + dy * dil,
+                                z0 + k * dil);
                     if (++s == CONV_STAGES) {
                         s = 0;
                         ph ^= 1u;
@@ -262,26 +277,34 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
             bool ok = mbar_wait(w_bar, 0, abort);
             int s = 0, it = 0;
             uint32_t ph = 0;
-            for (int tile = blockIdx.x; ok && tile < p.ntiles; tile += gridDim.x, ++it) {
-                const int acc = it & 1;
+            for (int w = blockIdx.x; ok && w < nitems; w += gridDim.x, ++it) {
+                const int buf = it & 1;
                 const uint32_t aph = (uint32_t)(it >> 1) & 1u;
-                if (!mbar_wait(tempty_bar(acc), aph ^ 1u, abort)) {
+                if (!mbar_wait(tempty_bar(buf), aph ^ 1u, abort)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(acc * COUT);
-                for (int t = 0; t < 27; ++t) {
+                for (int l = 0; l < NLOAD; ++l) {
                     if (!mbar_wait(full_bar(s), ph, abort)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a_base = sA + s * L::A_BYTES, b_base = sW + t * L::W_TAP;
+                    const int k = l / 9 - 1, dyx = l % 9;
+                    const uint32_t a_base = sA + s * L::A_BYTES;
 #pragma unroll
-                    for (int k = 0; k < CIN / 16; ++k)
-                        mma_bf16(d, smem_desc(a_base + 32 * k, CIN * 2), smem_desc(b_base + 32 * k, CIN * 2), idesc,
-                                 (t | k) != 0);
+                    for (int j = 0; j < G; ++j) {
+                        const int dz = k - j;
+                        if (dz < -1 || dz > 1) continue;
+                        const int t = (dz + 1) * 9 + dyx;
+                        const uint32_t d = tmem + (uint32_t)((buf * G + j) * COUT);
+                        const uint32_t b_base = sW + t * L::W_TAP;
+#pragma unroll
+                        for (int kk = 0; kk < CIN / 16; ++kk)
+                            mma_bf16(d, smem_desc(a_base + 32 * kk, CIN * 2), smem_desc(b_base + 32 * kk, CIN * 2),
+                                     idesc, (t | kk) != 0);
+                    }
                     mma_commit(empty_bar(s));
                     if (++s == CONV_STAGES) {
                         s = 0;
@@ -289,7 +312,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                     }
                 }
                 if (!ok) break;
-                mma_commit(tfull_bar(acc));
+                mma_commit(tfull_bar(buf));
             }
             if (!ok) {
                 *abort = 1;
@@ -304,54 +327,66 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
         const int row = q * 32 + lane;
         int it = 0;
-        for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x, ++it) {
-            const int acc = it & 1;
+        for (int w = blockIdx.x; w < nitems; w += gridDim.x, ++it) {
+            const int buf = it & 1;
             const uint32_t aph = (uint32_t)(it >> 1) & 1u;
             // the warp agrees before the warp-collective TMEM loads
-            const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull_bar(acc), aph, abort));
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull_bar(buf), aph, abort));
             if (!ok) {
                 *abort = 1;
                 if (lane == 0) atomicOr(p.err, ERR_TIMEOUT_EPILOGUE);
                 break;
             }
             tc_fence_after();
-            float v[COUT];
-            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * COUT);
+            int z0;
+            long long vb;
+            item_of(w, z0, vb);
+            // one plane's accumulator at a time (registers), the buffer is
+            // released after the last
+#pragma unroll 1
+            for (int j = 0; j < G; ++j) {
+                float v[1][COUT];
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((buf * G + j) * COUT);
 #pragma unroll
-            for (int c = 0; c < COUT; c += 16) tmem_ld16(taddr + c, v + c);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(tempty_bar(acc));
-            const long long vox = (long long)tile * TILE_M + row;
-            if (MODE == MODE_OUT) {
-                p.out_f32[vox] = v[0] + p.bias[0];
-            } else {
-                uint32_t packed[COUT / 2];
-                if (MODE == MODE_RELU) {
-#pragma unroll
-                    for (int c = 0; c < COUT; c += 2) {
-                        const float a0 = fmaxf(v[c] + p.bias[c], 0.f), a1 = fmaxf(v[c + 1] + p.bias[c + 1], 0.f);
-                        const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
-                        packed[c / 2] = *reinterpret_cast<const uint32_t *>(&h);
-                    }
-                } else {
-                    uint4 m[COUT / 8];
-                    const uint4 *mp = reinterpret_cast<const uint4 *>(p.mask + vox * COUT);
-#pragma unroll
-                    for (int i = 0; i < COUT / 8; ++i) m[i] = mp[i];
-                    const bf16 *mh = reinterpret_cast<const bf16 *>(m);
-#pragma unroll
-                    for (int c = 0; c < COUT; c += 2) {
-                        const float a0 = __bfloat162float(mh[c]) > 0.f ? v[c] : 0.f;
-                        const float a1 = __bfloat162float(mh[c + 1]) > 0.f ? v[c + 1] : 0.f;
-                        const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
-                        packed[c / 2] = *reinterpret_cast<const uint32_t *>(&h);
-                    }
+                for (int c = 0; c < COUT; c += 16) tmem_ld16(taddr + c, v[0] + c);
+                if (j == G - 1) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(tempty_bar(buf));
                 }
-                uint4 *op = reinterpret_cast<uint4 *>(p.out + vox * COUT);
+                const int z = z0 + j * dil;
+                if (z >= nz) continue;
+                const long long vox = (long long)z * plane + vb + row;
+                if (MODE == MODE_OUT) {
+                    p.out_f32[vox] = v[0][0] + p.bias[0];
+                } else {
+                    uint32_t packed[COUT / 2];
+                    if (MODE == MODE_RELU) {
 #pragma unroll
-                for (int i = 0; i < COUT / 8; ++i)
-                    op[i] = make_uint4(packed[4 * i], packed[4 * i + 1], packed[4 * i + 2], packed[4 * i + 3]);
+                        for (int c = 0; c < COUT; c += 2) {
+                            const float a0 = fmaxf(v[0][c] + p.bias[c], 0.f), a1 = fmaxf(v[0][c + 1] + p.bias[c + 1], 0.f);
+                            const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
+                            packed[c / 2] = *reinterpret_cast<const uint32_t *>(&h);
+                        }
+                    } else {
+                        uint4 m[COUT / 8];
+                        const uint4 *mp = reinterpret_cast<const uint4 *>(p.mask + vox * COUT);
+#pragma unroll
+                        for (int i = 0; i < COUT / 8; ++i) m[i] = mp[i];
+                        const bf16 *mh = reinterpret_cast<const bf16 *>(m);
+#pragma unroll
+                        for (int c = 0; c < COUT; c += 2) {
+                            const float a0 = __bfloat162float(mh[c]) > 0.f ? v[0][c] : 0.f;
+                            const float a1 = __bfloat162float(mh[c + 1]) > 0.f ? v[0][c + 1] : 0.f;
+                            const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
+                            packed[c / 2] = *reinterpret_cast<const uint32_t *>(&h);
+                        }
+                    }
+                    uint4 *op = reinterpret_cast<uint4 *>(p.out + vox * COUT);
+#pragma unroll
+                    for (int i = 0; i < COUT / 8; ++i)
+                        op[i] = make_uint4(packed[4 * i], packed[4 * i + 1], packed[4 * i + 2], packed[4 * i + 3]);
+                }
             }
         }
     }

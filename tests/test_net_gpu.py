@@ -52,10 +52,14 @@ def oracle_params(flat32):
     return [(W.astype(np.float64), b.astype(np.float64)) for W, b in art.ArtNet.split_params(flat32)]
 
 
-@pytest.mark.parametrize("shape,dil", [((16, 16, 16), (1, 2, 4, 8)), ((4, 4, 128), (1, 2, 1, 2)),
-                                        ((2, 3, 256), (1, 1, 2, 1))])
-def test_forward_matches_oracle(shape, dil):
+@pytest.mark.parametrize("shape,dil,planes", [((16, 16, 16), (1, 2, 4, 8), 0), ((4, 4, 128), (1, 2, 1, 2), 0),
+                                               ((2, 3, 256), (1, 1, 2, 1), 0), ((16, 16, 16), (1, 2, 4, 8), 1),
+                                               ((16, 16, 16), (1, 2, 4, 8), 2), ((13, 8, 16), (1, 2, 4, 1), 4)])
+def test_forward_matches_oracle(shape, dil, planes):
+    """planes: output planes per convolution work item (0 = automatic); 13 planes leave
+    groups that run past the grid."""
     net = art.ArtNet(dilation=dil)
+    net.set_plane_group(planes)
     flat = art.ArtNet.join_params(params_with_bias(3)).astype(np.float32)
     net.set_params(flat)
     X, _ = random_case(shape, 1)
@@ -69,10 +73,13 @@ def test_forward_matches_oracle(shape, dil):
     net.close()
 
 
-@pytest.mark.parametrize("shape,dil,weighted", [((16, 16, 16), (1, 2, 4, 8), False), ((4, 4, 128), (2, 1, 1, 3), False),
-                                                 ((16, 16, 16), (1, 2, 4, 8), True)])
-def test_gradients_match_oracle(shape, dil, weighted):
+@pytest.mark.parametrize("shape,dil,weighted,planes", [((16, 16, 16), (1, 2, 4, 8), False, 0),
+                                                        ((4, 4, 128), (2, 1, 1, 3), False, 0),
+                                                        ((16, 16, 16), (1, 2, 4, 8), True, 0),
+                                                        ((13, 8, 16), (1, 2, 1, 3), True, 4)])
+def test_gradients_match_oracle(shape, dil, weighted, planes):
     net = art.ArtNet(dilation=dil)
+    net.set_plane_group(planes)
     flat = art.ArtNet.join_params(params_with_bias(4)).astype(np.float32)
     net.set_params(flat)
     X, t = random_case(shape, 2)
