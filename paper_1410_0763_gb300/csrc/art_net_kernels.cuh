@@ -416,13 +416,24 @@ __device__ __forceinline__ void mma_m16n8k16(float *c, const uint32_t *a, const 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(128) wgrad_kernel(const bf16 *__restrict__ g, const bf16 *__restrict__ a, int nx, int ny,
                                                     int nz, int dil, float *__restrict__ part)
 {
-    constexpr int LD = WG_STEP + 8;   // padded row (bank-conflict free fragment loads)
-    __shared__ __align__(16) bf16 Gt[COUT][LD];
-    __shared__ __align__(16) bf16 At[CIN][LD];
+    // Tiles as stored, [voxel][channel], rows padded to a 16-byte multiple
+    // that keeps the eight rows of each ldmatrix on distinct banks; the MMA
+    // fragments (channel-major in the voxel dimension) come from the
+    // transposing ldmatrix.
+    constexpr int GS = COUT * 2 + 16, AS = CIN * 2 + 16;   // row strides in bytes
+    __shared__ __align__(16) unsigned char Gs[WG_STEP * GS];
+    __shared__ __align__(16) unsigned char As[WG_STEP * AS];
     __shared__ float red[4][COUT * CIN];
     const int t = blockIdx.y;
     const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
@@ -438,47 +449,57 @@ __global__ void __launch_bounds__(128) wgrad_kernel(const bf16 *__restrict__ g, 
         for (int j = 0; j < CIN / 8; ++j)
 #pragma unroll
             for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
+    const uint32_t gs0 = smem_u32(Gs), as0 = smem_u32(As);
 
     for (long long vb = v_begin; vb < v_end; vb += WG_STEP) {
-        // stage g and the shifted a, transposed to [channel][voxel]
+        // coordinates of the step's first voxel (one set of divisions per step)
+        const long long plane = (long long)nx * ny;
+        const int bz = (int)(vb / plane);
+        const long long brem = vb - (long long)bz * plane;
+        const int by = (int)(brem / nx), bx = (int)(brem - (long long)by * nx);
         for (int e = tid; e < WG_STEP * (COUT / 8); e += 128) {
             const int j = e / (COUT / 8), c8 = e % (COUT / 8);
             const long long v = vb + j;
             uint4 w = make_uint4(0, 0, 0, 0);
             if (v < v_end) w = *reinterpret_cast<const uint4 *>(g + v * COUT + c8 * 8);
-            const bf16 *h = reinterpret_cast<const bf16 *>(&w);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) Gt[c8 * 8 + i][j] = h[i];
+            *reinterpret_cast<uint4 *>(Gs + j * GS + c8 * 16) = w;
         }
         for (int e = tid; e < WG_STEP * (CIN / 8); e += 128) {
             const int j = e / (CIN / 8), c8 = e % (CIN / 8);
             const long long v = vb + j;
             uint4 w = make_uint4(0, 0, 0, 0);
             if (v < v_end) {
-                const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
+                int x = bx + j, y = by, z = bz;   // j < 64: a few row carries at most
+                while (x >= nx) {
+                    x -= nx;
+                    if (++y == ny) {
+                        y = 0;
+                        ++z;
+                    }
+                }
                 const int xs = x + dx * dil, ys = y + dy * dil, zs = z + dz * dil;
                 if (xs >= 0 && xs < nx && ys >= 0 && ys < ny && zs >= 0 && zs < nz)
                     w = *reinterpret_cast<const uint4 *>(a + (((long long)zs * ny + ys) * nx + xs) * CIN + c8 * 8);
             }
-            const bf16 *h = reinterpret_cast<const bf16 *>(&w);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) At[c8 * 8 + i][j] = h[i];
+            *reinterpret_cast<uint4 *>(As + j * AS + c8 * 16) = w;
         }
         __syncthreads();
         const int k0 = 16 * warp;   // this warp's 16 voxels of the step
+        // lane l addresses row (l & 7) + 8 * ((l >> 3) & 1) of its 8x8 block,
+        // blocks ordered (rows 0-7, ch 0-7), (rows 0-7, ch 8-15), (rows 8-15, ch 0-7), (rows 8-15, ch 8-15)
+        const int lr = (lane & 7) + ((lane >> 4) & 1) * 8;   // voxel row within the 16
+        const int lc = ((lane >> 3) & 1) * 8;               // channel offset 0 or 8
 #pragma unroll
         for (int mi = 0; mi < COUT / 16; ++mi) {
             uint32_t af[4];
-            af[0] = *reinterpret_cast<const uint32_t *>(&Gt[16 * mi + gq][k0 + 2 * tq]);
-            af[1] = *reinterpret_cast<const uint32_t *>(&Gt[16 * mi + gq + 8][k0 + 2 * tq]);
-            af[2] = *reinterpret_cast<const uint32_t *>(&Gt[16 * mi + gq][k0 + 2 * tq + 8]);
-            af[3] = *reinterpret_cast<const uint32_t *>(&Gt[16 * mi + gq + 8][k0 + 2 * tq + 8]);
+            ldsm_x4_trans(gs0 + (k0 + lr) * GS + (16 * mi + lc) * 2, af[0], af[1], af[2], af[3]);
 #pragma unroll
-            for (int ni = 0; ni < CIN / 8; ++ni) {
-                uint32_t bfr[2];
-                bfr[0] = *reinterpret_cast<const uint32_t *>(&At[8 * ni + gq][k0 + 2 * tq]);
-                bfr[1] = *reinterpret_cast<const uint32_t *>(&At[8 * ni + gq][k0 + 2 * tq + 8]);
-                mma_m16n8k16(acc[mi][ni], af, bfr);
+            for (int nj = 0; nj < CIN / 16; ++nj) {
+                uint32_t b0, b1, b2, b3;   // n-blocks 2 nj (b0, b2) and 2 nj + 1 (b1, b3)
+                ldsm_x4_trans(as0 + (k0 + lr) * AS + (16 * nj + lc) * 2, b0, b1, b2, b3);
+                const uint32_t bA[2] = {b0, b2}, bB[2] = {b1, b3};
+                mma_m16n8k16(acc[mi][2 * nj], af, bA);
+                mma_m16n8k16(acc[mi][2 * nj + 1], af, bB);
             }
         }
         __syncthreads();
