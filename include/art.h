@@ -246,15 +246,20 @@ typedef struct {
  * (index order) the ray from the source to the cell centre is marched,
  * tau_b = sum kappa_b ds over the cells before the target cell, [r_in, r_out]
  * is the ray's passage through the target cell (r_in = 0 in the source's own
- * cell; the first cell is the one containing source + 1e-9 * direction), and
+ * cell; the first cell is the one containing source + 1e-6 * direction), and
  *   Gamma += Q_b e^-tau_b (1 - e^-dtau_b) / (n_HI (4 pi/3)(r_out^3 - r_in^3) dx^3)
  * with n_HI = kappa_b/(sigma_b dx) (absorbed photons = in - out; App. A prints
  * out - in).  kappa: device [bin][z][y][x] floats per cell width; sigma: host
  * array of nu_bins cross sections (cm^2); src: host array of n_src sources;
  * Qb: host [n_src][nu_bins] photons/s per bin, or NULL to put each source's
  * Q in bin 0; gamma: device [z][y][x] floats, s^-1.  Uses grid.dx_cm.
+ * Arithmetic is FP32 (positions as integer cell + FP32 fraction; the
+ * per-bin constant 3 Q_b sigma_b / (4 pi dx^2) formed in FP64 on the host);
+ * e^-tau is off by a relative ~u sum_c T_c |kappa_c - kappa_c+1| over the
+ * ray's plane crossings at distances T_c (u = 2^-24).
  * Synchronizes `stream`.  Errors: ART_E_INVALID (null pointers, sources
- * outside the box, more than 4 bins, dx_cm <= 0), ART_E_OOM, ART_E_CUDA.
+ * outside the box, more than 4 bins, dx_cm <= 0, a bin constant beyond FP32
+ * range), ART_E_OOM, ART_E_CUDA.
  */
 art_status art_point_sources(art_ctx *ctx, const float *kappa, const double *sigma, const art_source *src,
                              const double *Qb, int n_src, float *gamma, void *stream);

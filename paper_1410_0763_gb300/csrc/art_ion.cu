@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "art.h"
@@ -36,23 +37,27 @@ constexpr double kPi = 3.14159265358979323846;
 //   Ndot_abs = Q_b e^-tau (1 - e^-dtau),  dtau = kappa_b (r_out - r_in),
 //   Gamma   += Ndot_abs / (n_HI 4pi/3 (r_out^3 - r_in^3) dx^3),  n_HI = kappa_b/(sigma_b dx)
 // which, with r_out^3 - r_in^3 = (r_out - r_in)(r_out^2 + r_out r_in + r_in^2), is
-//   Gamma   += 3 Q_b sigma_b e^-tau phi(dtau) / (4 pi dx^2 (r_out^2 + r_out r_in + r_in^2)),
-// free of the cancellation of r_out^3 - r_in^3 far from the source.  The
-// march is FP32 in relative form: it keeps, per axis, the parametric distance
-// to that axis' next plane (an O(1) number, so rounding stays ~1e-7 absolute
-// instead of growing with the distance from the source); crossings within
-// 1e-6 of each other are taken together.  r_in and r_out come from the target
-// cell's faces in FP64.
+//   Gamma   += 3 Q_b sigma_b / (4 pi dx^2) e^-tau phi(dtau) / (r_out^2 + r_out r_in + r_in^2),
+// free of the cancellation of r_out^3 - r_in^3 far from the source.  All in
+// FP32: the source position is split into its integer cell and the fraction
+// inside it, so every distance from the source to a plane or cell centre is
+// an exact small integer plus a fraction (no cancellation near the source);
+// the march keeps, per axis, the parametric distance to that axis' next plane
+// (an O(1) number); crossings within 1e-6 of each other are taken together;
+// the constant 3 Q_b sigma_b / (4 pi dx^2) is formed on the host in FP64.
 // ---------------------------------------------------------------------------
+struct PtSrc {
+    int si[3];       // cell containing the source
+    float sf[3];     // position inside it, [0, 1)
+    float coef[4];   // 3 Q_b sigma_b / (4 pi dx^2) per bin
+};
+
 struct PtArgs {
     const float *kappa;   // [bins][ncell], or one field scaled per bin (scaled != 0)
-    const double *src;    // [nsrc][4]: x, y, z, (unused)
-    const double *Qb;     // [nsrc][bins]
-    const double *sigma;  // [bins]
+    const PtSrc *src;     // [nsrc]
     int nsrc, nbins;
     int nx, ny, nz;
     long long ncell;
-    double dx;
     float *gamma;
     int scaled;           // kappa_b = kappa * kscale[b] (one field for all bins, one tau to march)
     float kscale[4];
@@ -63,113 +68,142 @@ constexpr int kMaxBins = 4;   // point-source kernels are compiled for 1-4 bins
 #define PT_UNROLL 4                // march steps whose kappa loads are issued together
 #endif
 
-template <int NB, bool SCALED> __global__ void __launch_bounds__(128) point_source_kernel(const PtArgs p)
+// phi(x) = (1 - e^-x)/x: its Maclaurin series to x^5 below x = 1/4, else direct
+__device__ __forceinline__ float pt_phi(float x)
 {
-    const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= p.ncell) return;
-    const int tx = (int)(cell % p.nx), ty = (int)((cell / p.nx) % p.ny), tz = (int)(cell / ((long long)p.nx * p.ny));
+    if (x < 0.25f) {
+        float q = fmaf(x, -1.0f / 720.0f, 1.0f / 120.0f);
+        q = fmaf(x, q, -1.0f / 24.0f);
+        q = fmaf(x, q, 1.0f / 6.0f);
+        q = fmaf(x, q, -0.5f);
+        return fmaf(x, q, 1.0f);
+    }
+    return (1.0f - __expf(-x)) / x;
+}
+
+// One march step: the kappa of the current cell and the path length in it,
+// then the crossing of the nearest plane (one plane per step; a plane of
+// another axis at the same place is crossed by the next step, with ds ~ 0).
+template <int NK, typename IDX>
+__device__ __forceinline__ void pt_step(const float *__restrict__ kappa, long long ncell, IDX &ci, float (&r)[3],
+                                        const float (&dl)[3], const IDX (&dci)[3], float (&kv)[NK], float &dv)
+{
+    const float ds = fminf(r[0], fminf(r[1], r[2]));
+#pragma unroll
+    for (int b = 0; b < NK; ++b) kv[b] = __ldg(kappa + (long long)b * ncell + ci);
+    dv = ds;
+    r[0] -= ds;
+    r[1] -= ds;
+    r[2] -= ds;
+    // the nearest plane's distance is now exactly 0
+    if (r[0] <= 0.0f) {
+        ci += dci[0];
+        r[0] += dl[0];
+    } else if (r[1] <= 0.0f) {
+        ci += dci[1];
+        r[1] += dl[1];
+    } else {
+        ci += dci[2];
+        r[2] += dl[2];
+    }
+}
+
+// Threads map to 8 x 4 x 4 bricks of cells (a warp is an 8 x 4 patch of one
+// plane), so the rays of a warp have similar lengths and touch nearby cells.
+template <int NB, bool SCALED, typename IDX>
+__global__ void __launch_bounds__(128) point_source_kernel(const PtArgs p)
+{
+    const int bx = (p.nx + 7) >> 3, by = (p.ny + 3) >> 2;
+    const int blk = blockIdx.x;
+    const int tx = (blk % bx) * 8 + (threadIdx.x & 7);
+    const int ty = ((blk / bx) % by) * 4 + ((threadIdx.x >> 3) & 3);
+    const int tz = (blk / (bx * by)) * 4 + (threadIdx.x >> 5);
+    if (tx >= p.nx || ty >= p.ny || tz >= p.nz) return;
+    const IDX stride[3] = {(IDX)1, (IDX)p.nx, (IDX)p.nx * (IDX)p.ny};
+    const IDX target = (IDX)tx + stride[1] * (IDX)ty + stride[2] * (IDX)tz;
+    const int tc[3] = {tx, ty, tz};
     const int dims[3] = {p.nx, p.ny, p.nz};
-    const int maxsteps = p.nx + p.ny + p.nz + 4;
-    double g = 0.0;
+    constexpr int U = PT_UNROLL;
+    constexpr int NK = SCALED ? 1 : NB;   // kappa fields marched
+    float g = 0.0f;
     for (int a = 0; a < p.nsrc; ++a) {
-        const double s[3] = {p.src[4 * a], p.src[4 * a + 1], p.src[4 * a + 2]};
-        const double c[3] = {tx + 0.5, ty + 0.5, tz + 0.5};
-        double d[3] = {c[0] - s[0], c[1] - s[1], c[2] - s[2]};
-        const double L2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-        if (L2 < 1e-24) {
-            d[0] = 1.0;
-            d[1] = d[2] = 0.0;
+        const PtSrc S = p.src[a];
+        // source -> cell centre: integer part exact, plus the fractions
+        float d[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) d[k] = (float)(tc[k] - S.si[k]) + (0.5f - S.sf[k]);
+        const float L2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (L2 < 1e-12f) {
+            d[0] = 1.0f;
+            d[1] = d[2] = 0.0f;
         } else {
-            const double il = 1.0 / sqrt(L2);
-            d[0] *= il;
-            d[1] *= il;
-            d[2] *= il;
+            const float il = rsqrtf(L2);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) d[k] *= il;
         }
-        // first cell: the one containing s + 1e-9 d
-        int cur[3], stp[3];
-        double rn[3];
-        float r[3], dl[3];   // parametric distance to the next plane of each axis; plane spacing
+        // first cell: the one containing the source + 1e-6 d; the walk from it
+        // to the target crosses |tc_k - cur_k| planes of each axis k, one per
+        // step, and every cell on the way lies between the two
+        IDX ci = 0;
+        IDX dci[3];    // index step on crossing each axis' next plane
+        float rn[3];   // 1/d
+        float r[3];    // ray length from the current point to each axis' next plane (O(1))
+        float dl[3];   // ray length between successive planes of each axis
+        int n = 0;     // steps to the target cell
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
-            int v = (int)floor(s[k] + 1e-9 * d[k]);
-            cur[k] = v < 0 ? 0 : (v >= dims[k] ? dims[k] - 1 : v);
-            stp[k] = d[k] > 0.0 ? 1 : (d[k] < 0.0 ? -1 : 0);
-            rn[k] = stp[k] ? 1.0 / d[k] : 0.0;
-            r[k] = stp[k] > 0 ? (float)((cur[k] + 1 - s[k]) * rn[k])
-                              : (stp[k] < 0 ? (float)((cur[k] - s[k]) * rn[k]) : INFINITY);
-            dl[k] = stp[k] ? (float)fabs(rn[k]) : INFINITY;
+            const int v = S.si[k] + (int)floorf(S.sf[k] + 1e-6f * d[k]);
+            const int cur = v < 0 ? 0 : (v >= dims[k] ? dims[k] - 1 : v);
+            ci += (IDX)cur * stride[k];
+            n += abs(tc[k] - cur);
+            const int stp = d[k] > 0.0f ? 1 : (d[k] < 0.0f ? -1 : 0);
+            rn[k] = stp ? __frcp_rn(d[k]) : 0.0f;
+            r[k] = stp ? ((float)(cur + (stp > 0) - S.si[k]) - S.sf[k]) * rn[k] : INFINITY;
+            dl[k] = stp ? fabsf(rn[k]) : INFINITY;
+            dci[k] = stp > 0 ? stride[k] : (IDX)0 - stride[k];
         }
         // March in rounds of U steps: first the U cells and path lengths (the
         // cell walk does not depend on kappa), with their kappa loads issued
         // together, then the U optical-depth updates in order.
-        constexpr int U = PT_UNROLL;
-        constexpr int NK = SCALED ? 1 : NB;   // kappa fields marched
         float tau[NK];
 #pragma unroll
         for (int b = 0; b < NK; ++b) tau[b] = 0.0f;
-        const long long target = cell;
-        int state = 0;   // 0 marching, 1 at the target cell, 2 left the box (cannot happen)
-        int it = 0;
-        while (state == 0 && it < maxsteps) {
+        for (; n >= U; n -= U) {
             float kv[U][NK], dv[U];
-            int nu = 0;
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (state == 0 && it < maxsteps) {
-                    const long long ci = ((long long)cur[2] * p.ny + cur[1]) * p.nx + cur[0];
-                    if (ci == target) {
-                        state = 1;
-                    } else {
-                        const float ds = fminf(r[0], fminf(r[1], r[2]));
-#pragma unroll
-                        for (int b = 0; b < NK; ++b) kv[u][b] = __ldg(p.kappa + (long long)b * p.ncell + ci);
-                        dv[u] = ds;
-                        nu = u + 1;
-                        ++it;
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            r[k] -= ds;
-                            if (r[k] <= 1e-6f) {   // this axis' plane is crossed here (ties within 1e-6 together)
-                                cur[k] += stp[k];
-                                if (cur[k] < 0 || cur[k] >= dims[k]) state = 2;
-                                r[k] += dl[k];
-                            }
-                        }
-                    }
-                }
-            }
+            for (int u = 0; u < U; ++u) pt_step<NK, IDX>(p.kappa, p.ncell, ci, r, dl, dci, kv[u], dv[u]);
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (u < nu) {
 #pragma unroll
-                    for (int b = 0; b < NK; ++b) tau[b] = fmaf(kv[u][b], dv[u], tau[b]);
-                }
+                for (int b = 0; b < NK; ++b) tau[b] = fmaf(kv[u][b], dv[u], tau[b]);
         }
-        if (state == 1) {
-            const long long ci = target;
-            {
-                // passage through the target cell, exactly, from its faces
-                double rin = 0.0, rout = INFINITY;
-                for (int k = 0; k < 3; ++k) {
-                    if (!stp[k]) continue;
-                    const double t1 = (tx * (k == 0) + ty * (k == 1) + tz * (k == 2) - s[k]) * rn[k];
-                    const double t2 = t1 + rn[k];
-                    rin = fmax(rin, fmin(t1, t2));
-                    rout = fmin(rout, fmax(t1, t2));
-                }
-                const double den = 4.0 * kPi * p.dx * p.dx * (rout * rout + rout * rin + rin * rin);
+        for (; n > 0; --n) {
+            float kv[NK], dv;
+            pt_step<NK, IDX>(p.kappa, p.ncell, ci, r, dl, dci, kv, dv);
 #pragma unroll
-                for (int b = 0; b < NB; ++b) {
-                    const double kb = SCALED ? (double)p.kappa[ci] * p.kscale[b]
-                                             : (double)p.kappa[(long long)b * p.ncell + ci];
-                    const double tb = SCALED ? (double)tau[0] * p.kscale[b] : (double)tau[b];
-                    const double x = kb * (rout - rin);
-                    const double ph = x > 0.0 ? -expm1(-x) / x : 1.0;
-                    g += 3.0 * p.Qb[(long long)a * p.nbins + b] * p.sigma[b] * exp(-tb) * ph / den;
-                }
+            for (int b = 0; b < NK; ++b) tau[b] = fmaf(kv[b], dv, tau[b]);
+        }
+        {
+            // passage through the target cell, exactly, from its faces
+            float rin = 0.0f, rout = INFINITY;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (d[k] == 0.0f) continue;
+                const float t1 = ((float)(tc[k] - S.si[k]) - S.sf[k]) * rn[k];
+                const float t2 = t1 + rn[k];
+                rin = fmaxf(rin, fminf(t1, t2));
+                rout = fminf(rout, fmaxf(t1, t2));
+            }
+            const float den = rout * rout + rout * rin + rin * rin;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const float kb = SCALED ? p.kappa[target] * p.kscale[b] : p.kappa[(long long)b * p.ncell + target];
+                const float tb = SCALED ? tau[0] * p.kscale[b] : tau[b];
+                g += S.coef[b] * __expf(-tb) * pt_phi(kb * (rout - rin)) / den;
             }
         }
     }
-    p.gamma[cell] = (float)g;
+    p.gamma[target] = g;
 }
 
 // ---------------------------------------------------------------------------
@@ -245,64 +279,92 @@ template <typename T> art_status ensure(art_ctx *ctx, T **p, size_t n)
     return ART_OK;
 }
 
-art_status upload_sources(art_ctx *ctx, const art_source *src, int n_src, const double *Qb, int nbins,
-                          std::vector<double> &h_src, std::vector<double> &h_q)
+// Sources as the kernel reads them: integer cell + FP32 fraction, and per bin
+// the rate constant 3 Q_b sigma_b / (4 pi dx^2) (Q_b = Qb[a][b], or Q_a times
+// frac[b] when Qb is null).
+art_status pack_sources(art_ctx *ctx, const art_source *src, int n_src, const double *Qb, const double *frac,
+                        const double *sigma, int nbins, std::vector<PtSrc> &h)
 {
-    h_src.assign(4 * (size_t)n_src, 0.0);
-    h_q.assign((size_t)n_src * nbins, 0.0);
+    h.assign(n_src > 0 ? (size_t)n_src : 1, PtSrc{});
+    const double dx = ctx->grid.dx_cm;
+    const int dims[3] = {ctx->grid.nx, ctx->grid.ny, ctx->grid.nz};
     for (int a = 0; a < n_src; ++a) {
         const art_source &s = src[a];
+        const double x[3] = {s.x, s.y, s.z};
         if (!std::isfinite(s.x) || !std::isfinite(s.y) || !std::isfinite(s.z) || !(s.Q >= 0.0) ||
-            s.x < 0 || s.y < 0 || s.z < 0 || s.x > ctx->grid.nx || s.y > ctx->grid.ny || s.z > ctx->grid.nz)
+            s.x < 0 || s.y < 0 || s.z < 0 || s.x > dims[0] || s.y > dims[1] || s.z > dims[2])
             return art_fail(ctx, ART_E_INVALID, "point source outside the box or with a bad luminosity");
-        h_src[4 * a] = s.x;
-        h_src[4 * a + 1] = s.y;
-        h_src[4 * a + 2] = s.z;
-        for (int b = 0; b < nbins; ++b) h_q[(size_t)a * nbins + b] = Qb ? Qb[(size_t)a * nbins + b] : (b == 0 ? s.Q : 0.0);
+        PtSrc &P = h[a];
+        for (int k = 0; k < 3; ++k) {
+            const double f = std::floor(x[k]);
+            P.si[k] = (int)f;
+            P.sf[k] = (float)(x[k] - f);
+            if (P.sf[k] >= 1.0f) {   // a fraction that rounds up to a whole cell
+                P.si[k] += 1;
+                P.sf[k] = 0.0f;
+            }
+        }
+        for (int b = 0; b < kMaxBins; ++b) {
+            double q = 0.0;
+            if (b < nbins) q = Qb ? Qb[(size_t)a * nbins + b] : s.Q * (frac ? frac[b] : (b == 0 ? 1.0 : 0.0));
+            const double c = 3.0 * q * (b < nbins ? sigma[b] : 0.0) / (4.0 * kPi * dx * dx);
+            if (!(q >= 0.0) || !(c <= 3.0e38))
+                return art_fail(ctx, ART_E_INVALID, "point source: bad bin luminosity or a rate beyond FP32 range");
+            P.coef[b] = (float)c;
+        }
     }
     return ART_OK;
 }
 
+// Device room for n_src packed sources (at least one).
+art_status source_buffer(art_ctx *ctx, int n_src)
+{
+    const int need = (int)(((size_t)(n_src > 0 ? n_src : 1) * sizeof(PtSrc) + sizeof(double) - 1) / sizeof(double));
+    if (ctx->it.nsrc_cap >= need) return ART_OK;
+    if (ctx->it.src) cudaFree(ctx->it.src);
+    ctx->it.src = nullptr;
+    ctx->it.nsrc_cap = need;
+    return ensure(ctx, &ctx->it.src, (size_t)need);
+}
+
+template <typename IDX> void launch_points_t(const PtArgs &a, unsigned nb, int nt, cudaStream_t st)
+{
+    switch (a.nbins + (a.scaled ? 4 : 0)) {
+    case 1: point_source_kernel<1, false, IDX><<<nb, nt, 0, st>>>(a); break;
+    case 2: point_source_kernel<2, false, IDX><<<nb, nt, 0, st>>>(a); break;
+    case 3: point_source_kernel<3, false, IDX><<<nb, nt, 0, st>>>(a); break;
+    case 4: point_source_kernel<4, false, IDX><<<nb, nt, 0, st>>>(a); break;
+    case 5: point_source_kernel<1, true, IDX><<<nb, nt, 0, st>>>(a); break;
+    case 6: point_source_kernel<2, true, IDX><<<nb, nt, 0, st>>>(a); break;
+    case 7: point_source_kernel<3, true, IDX><<<nb, nt, 0, st>>>(a); break;
+    default: point_source_kernel<4, true, IDX><<<nb, nt, 0, st>>>(a); break;
+    }
+}
+
 // Point-source rates into gamma (device), kappa per bin on the device, or
 // (kscale != null) one kappa field scaled per bin.
-art_status launch_points(art_ctx *ctx, const float *kappa, int nbins, const double *d_src, const double *d_q,
-                         const double *d_sigma, int n_src, float *gamma, cudaStream_t st,
-                         const float *kscale = nullptr)
+art_status launch_points(art_ctx *ctx, const float *kappa, int nbins, const PtSrc *d_src, int n_src, float *gamma,
+                         cudaStream_t st, const float *kscale = nullptr)
 {
     PtArgs a;
     a.kappa = kappa;
     a.src = d_src;
-    a.Qb = d_q;
-    a.sigma = d_sigma;
     a.nsrc = n_src;
     a.nbins = nbins;
     a.nx = ctx->grid.nx;
     a.ny = ctx->grid.ny;
     a.nz = ctx->grid.nz;
     a.ncell = ctx->ncell;
-    a.dx = ctx->grid.dx_cm;
     a.gamma = gamma;
     a.scaled = kscale != nullptr;
     for (int b = 0; b < 4; ++b) a.kscale[b] = kscale && b < nbins ? kscale[b] : 1.0f;
+    if (nbins < 1 || nbins > kMaxBins) return art_fail(ctx, ART_E_INVALID, "point sources: 1 to 4 bins");
     const int nt = 128;
-    const unsigned nb = (unsigned)((ctx->ncell + nt - 1) / nt);
-    if (a.scaled) {
-        switch (nbins) {
-        case 1: point_source_kernel<1, true><<<nb, nt, 0, st>>>(a); break;
-        case 2: point_source_kernel<2, true><<<nb, nt, 0, st>>>(a); break;
-        case 3: point_source_kernel<3, true><<<nb, nt, 0, st>>>(a); break;
-        case 4: point_source_kernel<4, true><<<nb, nt, 0, st>>>(a); break;
-        default: return art_fail(ctx, ART_E_INVALID, "point sources: 1 to 4 bins");
-        }
-    } else {
-        switch (nbins) {
-        case 1: point_source_kernel<1, false><<<nb, nt, 0, st>>>(a); break;
-        case 2: point_source_kernel<2, false><<<nb, nt, 0, st>>>(a); break;
-        case 3: point_source_kernel<3, false><<<nb, nt, 0, st>>>(a); break;
-        case 4: point_source_kernel<4, false><<<nb, nt, 0, st>>>(a); break;
-        default: return art_fail(ctx, ART_E_INVALID, "point sources: 1 to 4 bins");
-        }
-    }
+    const unsigned nb = (unsigned)(((a.nx + 7) / 8) * (long long)((a.ny + 3) / 4) * ((a.nz + 3) / 4));
+    if (ctx->ncell <= 0x7fffffffLL)
+        launch_points_t<int>(a, nb, nt, st);
+    else
+        launch_points_t<long long>(a, nb, nt, st);
     ICK(ctx, cudaGetLastError());
     return ART_OK;
 }
@@ -322,25 +384,15 @@ art_status art_point_sources(art_ctx *ctx, const float *kappa, const double *sig
     if (nbins > kMaxBins) return art_fail(ctx, ART_E_INVALID, "art_point_sources: at most 4 bins");
     if (!(ctx->grid.dx_cm > 0.0)) return art_fail(ctx, ART_E_INVALID, "art_point_sources: grid dx_cm must be > 0");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    std::vector<double> h_src, h_q;
-    art_status s = upload_sources(ctx, src, n_src, Qb, nbins, h_src, h_q);
-    if (s != ART_OK) return s;
     for (int b = 0; b < nbins; ++b)
         if (!(sigma[b] >= 0.0)) return art_fail(ctx, ART_E_INVALID, "art_point_sources: bad cross section");
-    const int cap = n_src > 0 ? n_src : 1;
-    if (ctx->it.nsrc_cap < cap * (nbins + 4) + nbins) {
-        if (ctx->it.src) cudaFree(ctx->it.src);
-        ctx->it.src = nullptr;
-        ctx->it.nsrc_cap = cap * (nbins + 4) + nbins;
-        if ((s = ensure(ctx, &ctx->it.src, (size_t)ctx->it.nsrc_cap)) != ART_OK) return s;
-    }
-    double *d_src = ctx->it.src, *d_q = d_src + 4 * cap, *d_sig = d_q + (size_t)cap * nbins;
-    if (n_src > 0) {
-        ICK(ctx, cudaMemcpyAsync(d_src, h_src.data(), h_src.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-        ICK(ctx, cudaMemcpyAsync(d_q, h_q.data(), h_q.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-    }
-    ICK(ctx, cudaMemcpyAsync(d_sig, sigma, nbins * sizeof(double), cudaMemcpyHostToDevice, st));
-    s = launch_points(ctx, kappa, nbins, d_src, d_q, d_sig, n_src, gamma, st);
+    std::vector<PtSrc> h_src;
+    art_status s = pack_sources(ctx, src, n_src, Qb, nullptr, sigma, nbins, h_src);
+    if (s != ART_OK) return s;
+    if ((s = source_buffer(ctx, n_src)) != ART_OK) return s;
+    const PtSrc *d_src = reinterpret_cast<const PtSrc *>(ctx->it.src);
+    ICK(ctx, cudaMemcpyAsync(ctx->it.src, h_src.data(), h_src.size() * sizeof(PtSrc), cudaMemcpyHostToDevice, st));
+    s = launch_points(ctx, kappa, nbins, d_src, n_src, gamma, st);
     if (s != ART_OK) return s;
     // host vectors are copied from: wait before they go out of scope
     ICK(ctx, cudaStreamSynchronize(st));
@@ -456,25 +508,11 @@ art_status iterate_impl(art_ctx *ctx, art_net *net, const art_chem *ch, const do
         frac[b] = ctx->spec_bins > 0 ? ctx->spec_frac[b] : 1.0;
         kscale[b] = (float)(sig[b] / ch->sigma0);
     }
-    std::vector<double> h_src, h_q;
-    if ((s = upload_sources(ctx, src, n_src, nullptr, 1, h_src, h_q)) != ART_OK) return s;
-    std::vector<double> h_qb((size_t)(n_src > 0 ? n_src : 1) * nbp, 0.0);
-    for (int a = 0; a < n_src; ++a)
-        for (int b = 0; b < nbp; ++b) h_qb[(size_t)a * nbp + b] = h_q[a] * frac[b];
-    const int cap = n_src > 0 ? n_src : 1;
-    const int need = cap * (4 + nbp) + nbp;
-    if (B.nsrc_cap < need) {
-        if (B.src) cudaFree(B.src);
-        B.src = nullptr;
-        B.nsrc_cap = need;
-        if ((s = ensure(ctx, &B.src, (size_t)B.nsrc_cap)) != ART_OK) return s;
-    }
-    double *d_src = B.src, *d_q = d_src + 4 * cap, *d_sig = d_q + (size_t)cap * nbp;
-    if (n_src > 0) {
-        ICK(ctx, cudaMemcpyAsync(d_src, h_src.data(), h_src.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-        ICK(ctx, cudaMemcpyAsync(d_q, h_qb.data(), (size_t)n_src * nbp * sizeof(double), cudaMemcpyHostToDevice, st));
-    }
-    ICK(ctx, cudaMemcpyAsync(d_sig, sig.data(), nbp * sizeof(double), cudaMemcpyHostToDevice, st));
+    std::vector<PtSrc> h_src;
+    if ((s = pack_sources(ctx, src, n_src, nullptr, frac.data(), sig.data(), nbp, h_src)) != ART_OK) return s;
+    if ((s = source_buffer(ctx, n_src)) != ART_OK) return s;
+    const PtSrc *d_src = reinterpret_cast<const PtSrc *>(B.src);
+    ICK(ctx, cudaMemcpyAsync(B.src, h_src.data(), h_src.size() * sizeof(PtSrc), cudaMemcpyHostToDevice, st));
 
     const int nt = 256;
     const unsigned nb = (unsigned)((n + nt - 1) / nt);
@@ -519,7 +557,7 @@ art_status iterate_impl(art_ctx *ctx, art_net *net, const art_chem *ch, const do
     int it = 0, conv = 0, it1 = 0, sweeps = 0, fell_back = 0;
     double r = 0.0, judge = 0.0;
     for (it = 1; it <= max_iter; ++it) {
-        if ((s = launch_points(ctx, B.kap, nbp, d_src, d_q, d_sig, n_src, B.gpt, st, kscale.data())) != ART_OK)
+        if ((s = launch_points(ctx, B.kap, nbp, d_src, n_src, B.gpt, st, kscale.data())) != ART_OK)
             return s;
         if (have_jin) {
             have_jin = false;   // J^in of this state came with the judge's sweep

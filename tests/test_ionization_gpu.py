@@ -1,8 +1,9 @@
 """GPU parity of the point sources (App. A), the FP64 balance (App. B) and the
 RT/balance iteration (App. D) against the FP64 oracle.
 
-Point sources: FP32 march, FP64 rate; within 1e-5 relative of the oracle on
-the FP32-rounded opacities.  Iteration: the converged neutral fraction within
+Point sources: all FP32 (source position split into its integer cell and
+an FP32 fraction, rate constant folded on the host in FP64); within 4e-5
+relative of the oracle on the FP32-rounded opacities.  Iteration: the converged neutral fraction within
 1e-4 relative of the oracle's (the FP32 sweep and march errors of ~1e-6 are
 amplified by the fixed point), same iteration count within one.  At the full
 128^3 / N_side 8 configuration the GPU's converged state is checked as a
@@ -52,7 +53,14 @@ def test_point_sources_match_oracle(orc, nbins):
     torch.cuda.synchronize()
     sw.close()
     ref = orc.point_sources(kap.astype(np.float64), sigma, np.array([s[:3] for s in sources]), Qb, dx)
-    assert rel(g.cpu().numpy().astype(np.float64), ref) < 1e-5
+    # FP32 geometry: each plane-crossing parameter T along a ray is rounded to
+    # a few ulp of T, so a cell's optical depth is off by about
+    # u * sum_c T_c |kappa_c - kappa_c+1| over the ray's crossings, and
+    # e^-tau by the same amount relative.  On this medium (tau <= 33 along
+    # rays of at most 43 cells) the worst of the 40k rays is ~1.5e-5.
+    err = rel(g.cpu().numpy().astype(np.float64), ref)
+    print(f"\nPRECISION point sources, {nbins} bin(s): max relative error {err:.2e}")
+    assert err < 4e-5
 
 
 def test_point_sources_thin_limit():
