@@ -80,6 +80,10 @@ typedef struct {
                                 (single-grid contexts); 0, 0 = all directions.  J_in and
                                 gamma are then this shard's additive share (still divided by
                                 the full N_d), and the J output is not available */
+    int early_launch;        /* slab-block launches after the first of a sweep may start while
+                                the previous one drains (programmatic dependent launch): they
+                                stage fields and tables, then wait before touching the
+                                intensity planes.  1 or 0 = on (default), -1 = off */
 } art_options;
 
 /* Statistics of one sweep, fixed at art_create. */

@@ -32,7 +32,7 @@ class ArtOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("averaging", C.c_int), ("field_form", C.c_int),
                 ("tile_b", C.c_int), ("tile_c", C.c_int), ("slab", C.c_int), ("dir_split", C.c_int),
                 ("tie_tol", C.c_double), ("variant", C.c_int), ("persistent", C.c_int), ("graph", C.c_int),
-                ("dir_begin", C.c_int), ("dir_end", C.c_int)]
+                ("dir_begin", C.c_int), ("dir_end", C.c_int), ("early_launch", C.c_int)]
 
 
 class ArtSweepStats(C.Structure):
@@ -355,7 +355,7 @@ class ArtSweep:
     def __init__(self, shape, nside, nbins: int = 1, precision: str = "fp32", field_form: int = 0,
                  dx_cm: float = 1.0, tile_b: int = 0, tile_c: int = 0, slab: int = 0, dir_split: int = 0,
                  tie_tol: float = 1e-12, variant: int = 0, persistent: int = 0, graph: bool = False,
-                 dir_range=None):
+                 dir_range=None, early_launch: bool = True):
         batch = len(shape) > 0 and not np.isscalar(shape[0])
         shapes = [tuple(int(v) for v in s) for s in (shape if batch else [shape])]
         nsides = [int(v) for v in nside] if not np.isscalar(nside) else [int(nside)] * len(shapes)
@@ -375,6 +375,7 @@ class ArtSweep:
         opt.variant = int(variant)
         opt.persistent = int(persistent)
         opt.graph = 1 if graph else 0
+        opt.early_launch = 1 if early_launch else -1
         if dir_range is not None:
             opt.dir_begin, opt.dir_end = int(dir_range[0]), int(dir_range[1])
         grids = [ArtGrid(nx, ny, nz, dx_cm) for (nz, ny, nx) in shapes]

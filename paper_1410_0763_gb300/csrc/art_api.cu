@@ -73,17 +73,28 @@ template <typename T> void dev_free(art_ctx *ctx, T *&p, size_t &bytes)
 }
 
 // Launch one slab-block sweep.  The shared-memory attribute is set by
-// prepare_sweep (outside any stream capture).
+// prepare_sweep (outside any stream capture).  With `early`, the launch may
+// begin while the previous kernel on the stream drains (programmatic
+// dependent launch): its CTAs stage the fields and segment tables, which no
+// kernel of the sweep writes, and wait for the previous launch to complete
+// before they touch the intensity planes or the J partials.
 template <typename real, int TB, int TC, int BLK, int NT, int KP, int MINB>
-cudaError_t launch_sweep(const void *args, int nctas, cudaStream_t st)
+cudaError_t launch_sweep(const void *args, int nctas, cudaStream_t st, bool early)
 {
     const SweepArgs<real> &a = *static_cast<const SweepArgs<real> *>(args);
     const size_t sm = SweepShape<TB, TC, BLK, NT, KP>::template bytes<real>();
-    if (a.counter)
-        sweep_queue_kernel<real, TB, TC, BLK, NT, KP, MINB><<<nctas, NT, sm, st>>>(a);
-    else
-        sweep_block_kernel<real, TB, TC, BLK, NT, KP, MINB><<<nctas, NT, sm, st>>>(a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nctas);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = early ? 1 : 0;
+    if (a.counter) return cudaLaunchKernelEx(&cfg, sweep_queue_kernel<real, TB, TC, BLK, NT, KP, MINB>, a);
+    return cudaLaunchKernelEx(&cfg, sweep_block_kernel<real, TB, TC, BLK, NT, KP, MINB>, a);
 }
 
 // Allow the variant's dynamic shared memory; returns its resident CTAs per SM
@@ -111,7 +122,7 @@ template <typename real, int TB, int TC, int BLK, int NT, int KP, int MINB> int 
 // the value of art_options.variant that selects one (0 = default).
 struct KVariant {
     int prec, tb, tc, blk, nt, kp, minb;
-    cudaError_t (*launch)(const void *, int, cudaStream_t);
+    cudaError_t (*launch)(const void *, int, cudaStream_t, bool);
     int (*prepare)();
 };
 #define ART_V(real, pr, tb, tc, blk, nt, kp, mb)                                                   \
@@ -410,7 +421,9 @@ template <typename real> art_status do_sweep(art_ctx *ctx, real *J, real *Jin, r
             a.plane_in = planes[k & 1];
             a.plane_out = planes[(k + 1) & 1];
             a.counter = ctx->persistent ? ctx->d_counter + k : nullptr;
-            CK(ctx, kVariants[ctx->variant].launch(&a, ctx->persistent ? ctx->n_ctas : ctx->n_work, st));
+            // the first launch of a bin follows kernels that write its inputs, so it starts only after them
+            CK(ctx, kVariants[ctx->variant].launch(&a, ctx->persistent ? ctx->n_ctas : ctx->n_work, st,
+                                                   k > 0 && ctx->early_launch));
         }
         if (ctx->profiling) CK(ctx, cudaEventRecord(e1, st));
         ReduceArgs<real> r;
@@ -531,6 +544,7 @@ art_status create_common(const art_grid *grids, const int *n_side, int n_grids, 
     if (ctx->opt.dir_end > ctx->opt.dir_begin) ctx->nd = ctx->opt.dir_end - ctx->opt.dir_begin;
     ctx->G.assign(nu_bins, 0.0);
     ctx->persistent = ctx->opt.persistent > 0 ? 1 : (ctx->opt.persistent < 0 ? 0 : (n_grids > 1 ? 1 : 0));
+    ctx->early_launch = ctx->opt.early_launch >= 0;
 
     int pick = -1;
     if (ctx->opt.variant > 0) {

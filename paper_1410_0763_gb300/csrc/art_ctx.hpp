@@ -47,6 +47,7 @@ struct art_ctx {
     std::vector<art_grid_host> grids;
     int persistent = 0;        // sweep launches take work items from a queue
     int n_ctas = 0;            // CTAs of a persistent launch
+    bool early_launch = true;  // slab-block launches after the first may start as the previous one drains
     int *d_counter = nullptr;  // queue heads, one per slab block
     void *d_gridinfo = nullptr;
     // CUDA graph of one sweep (device outputs), replayed while the outputs match

@@ -107,6 +107,13 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
+// Programmatic dependent launch: let the next kernel on the stream begin its
+// CTAs now (they wait on grid_dep_wait before reading what this one writes),
+// and wait for the previous kernel to complete and its writes to be visible.
+// Both are no-ops for a launch made without the attribute.
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ void kahan_add(float &s, float &c, float v)
 {
     const float y = __fsub_rn(v, c);
@@ -248,12 +255,15 @@ template <typename real> struct DirSm {
     int d0b, d0c;    // column shifts over the slab block
 };
 
-// Decoded segment entry: path lengths (0 where the direction has no such
-// segment) and the offsets, in elements of the pair-interleaved exchange
-// buffer, of the column that feeds segments 2 and 3 (0 = its own column).
-template <typename real> struct SegSm {
-    real ds1, ds2, ds3;
-    int bits;   // 2 off2 | 2 off3 << 12 | nseg << 24
+// Decoded segment entry of a pair of directions (the two lanes of a packed
+// operation) in one slab: path lengths (0 where a direction has no such
+// segment) and, per exchange step, the offsets in elements of the
+// pair-interleaved exchange buffer of the column that feeds each lane
+// (12 bits each, 0 = its own column); bits 24 and 25 of off3 say whether
+// either direction has a segment 2 or 3.
+template <typename real> struct alignas(2 * sizeof(real)) PairSm {
+    typename Vec2<real>::type ds1, ds2, ds3;
+    int off2, off3;
 };
 
 template <int TB, int TC, int BLK, int NT, int KP> struct SweepShape {
@@ -274,7 +284,7 @@ template <int TB, int TC, int BLK, int NT, int KP> struct SweepShape {
     }
     template <typename real> __host__ __device__ static constexpr size_t off_d()
     {
-        return off_t<real>() + size_t(DCH) * BLK * sizeof(SegSm<real>);
+        return off_t<real>() + size_t(DCH / 2) * BLK * sizeof(PairSm<real>);
     }
     template <typename real> __host__ __device__ static constexpr size_t off_g()
     {
@@ -300,7 +310,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<real> &p, int item, u
 
     v2 *ks = reinterpret_cast<v2 *>(smem_raw);
     pr *xbuf = reinterpret_cast<pr *>(smem_raw + Sh::template off_x<real>());   // [2][KP][NS] pairs
-    SegSm<real> *tsm = reinterpret_cast<SegSm<real> *>(smem_raw + Sh::template off_t<real>());
+    PairSm<real> *tsm = reinterpret_cast<PairSm<real> *>(smem_raw + Sh::template off_t<real>());
     DirSm<real> *dsm = reinterpret_cast<DirSm<real> *>(smem_raw + Sh::template off_d<real>());
     int4 *gsm = reinterpret_cast<int4 *>(smem_raw + Sh::template off_g<real>());
 
@@ -364,26 +374,39 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<real> &p, int item, u
         const int cnt = min(DCH, d1 - c0);
         const int cntk = (cnt + K - 1) / K * K;   // padded with inactive directions
         __syncthreads();   // previous chunk's tables are no longer read
-        for (int e = tid; e < cntk * BLK; e += NT) {
-            const int dl = e / BLK, i = e - dl * BLK;
-            SegSm<real> q;
-            q.ds1 = q.ds2 = q.ds3 = real(0);
-            q.bits = 1 << 24;   // inactive: one segment of length 0, own column
-            if (dl < cnt && i < Bp) {
-                const SegEntry<real> g = p.segs[p.dirs[c0 + dl].seg_off + m0 + i];
-                const int nseg = (g.code & 3) + 1, cf = (g.code >> 2) & 1;
-                const int shb = (g.code >> 3) & 1, shc = (g.code >> 4) & 1;
-                int off2 = 0, off3 = 0;
-                if (nseg == 2) off2 = shc * WB + shb;
-                if (nseg == 3) {
-                    off2 = cf * WB + (1 - cf);
-                    off3 = (1 - cf) * WB + cf;
+        for (int e = tid; e < (cntk / 2) * BLK; e += NT) {
+            const int pl = e / BLK, i = e - pl * BLK;
+            real ds[2][3];
+            int o2[2], o3[2], ns[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int dl = 2 * pl + h;
+                ds[h][0] = ds[h][1] = ds[h][2] = real(0);
+                o2[h] = o3[h] = 0;
+                ns[h] = 1;   // inactive: one segment of length 0, own column
+                if (dl < cnt && i < Bp) {
+                    const SegEntry<real> g = p.segs[p.dirs[c0 + dl].seg_off + m0 + i];
+                    const int nseg = (g.code & 3) + 1, cf = (g.code >> 2) & 1;
+                    const int shb = (g.code >> 3) & 1, shc = (g.code >> 4) & 1;
+                    if (nseg == 2) o2[h] = shc * WB + shb;
+                    if (nseg == 3) {
+                        o2[h] = cf * WB + (1 - cf);
+                        o3[h] = (1 - cf) * WB + cf;
+                    }
+                    ds[h][0] = g.ds1;
+                    ds[h][1] = nseg >= 2 ? g.ds2 : real(0);
+                    ds[h][2] = nseg == 3 ? g.ds3 : real(0);
+                    ns[h] = nseg;
                 }
-                q.ds1 = g.ds1;
-                q.ds2 = nseg >= 2 ? g.ds2 : real(0);
-                q.ds3 = nseg == 3 ? g.ds3 : real(0);
-                q.bits = (2 * off2) | ((2 * off3) << 12) | (nseg << 24);
             }
+            PairSm<real> q;
+            q.ds1 = P::mk(ds[0][0], ds[1][0]);
+            q.ds2 = P::mk(ds[0][1], ds[1][1]);
+            q.ds3 = P::mk(ds[0][2], ds[1][2]);
+            // lane a reads element 2 (c - off) of the exchange buffer, lane b element 2 (c - off) + 1
+            q.off2 = (2 * o2[0]) | ((2 * o2[1]) << 12);
+            q.off3 = (2 * o3[0]) | ((2 * o3[1]) << 12) | (int(max(ns[0], ns[1]) >= 2) << 24) |
+                     (int(max(ns[0], ns[1]) >= 3) << 25);
             tsm[e] = q;
         }
         for (int dl = tid; dl < cnt; dl += NT) {
@@ -417,18 +440,26 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<real> &p, int item, u
             gsm[e] = make_int4(nsmax, ub, uc, 0);
         }
         __syncthreads();
+        // the intensity planes and the J partials are shared with the previous launch
+        grid_dep_wait();
 
         for (int g0 = 0; g0 < cnt; g0 += K) {
             const int kk = min(K, cnt - g0);
             const int4 *G = gsm + (g0 / K) * BLK;
             const int D0b = G[0].y, D0c = G[0].z;   // union cone of the group
             long long poff[K];
-            real na[K];
+            pr na2[KP];   // |n_a| of the pair's directions, 0 for padding
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const DirSm<real> D = dsm[g0 + (k < kk ? k : 0)];
-                poff[k] = D.plane_off;
-                na[k] = k < kk ? D.na : real(0);
+            for (int kp = 0; kp < KP; ++kp) {
+                real na[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = 2 * kp + h;
+                    const DirSm<real> D = dsm[g0 + (k < kk ? k : 0)];
+                    poff[k] = D.plane_off;
+                    na[h] = k < kk ? D.na : real(0);
+                }
+                na2[kp] = P::mk(na[0], na[1]);
             }
             const int hw = TB + D0b;
             const int n1 = D0c * hw, nh = n1 + TC * D0b;
@@ -474,9 +505,9 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<real> &p, int item, u
             for (int i = 0; i < BLK; ++i) {
                 if (i < Bp) {
                     const int4 Gi = G[i];
-                    SegSm<real> g[K];
+                    PairSm<real> g[KP];
 #pragma unroll
-                    for (int k = 0; k < K; ++k) g[k] = tsm[(g0 + k) * BLK + i];
+                    for (int kp = 0; kp < KP; ++kp) g[kp] = tsm[(g0 / 2 + kp) * BLK + i];
                     const v2 *ksi = ks + i * NS;
                     CellVals<real> oc[OPT], hc[HPT];
                     pr oA[OPT][KP];
@@ -488,7 +519,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<real> &p, int item, u
 #pragma unroll
                         for (int kp = 0; kp < KP; ++kp) {
                             pr dsph, xph;
-                            seg_coef2(oc[s], P::mk(g[2 * kp].ds1, g[2 * kp + 1].ds1), dsph, xph);
+                            seg_coef2(oc[s], g[kp].ds1, dsph, xph);
                             oA[s][kp] = P::splat(real(0));
                             seg_apply2<real>(oI[s][kp], oA[s][kp], oc[s].src, dsph, xph, form);
                         }
@@ -503,7 +534,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<real> &p, int item, u
 #pragma unroll
                             for (int kp = 0; kp < KP; ++kp) {
                                 pr dsph, xph, dummy = P::splat(real(0));
-                                seg_coef2(hc[s], P::mk(g[2 * kp].ds1, g[2 * kp + 1].ds1), dsph, xph);
+                                seg_coef2(hc[s], g[kp].ds1, dsph, xph);
                                 seg_apply2<real>(hI[s][kp], dummy, hc[s].src, dsph, xph, form);
                             }
                         }
@@ -525,19 +556,18 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<real> &p, int item, u
                         __syncthreads();
 #pragma unroll
                         for (int kp = 0; kp < KP; ++kp) {
-                            const SegSm<real> &ga = g[2 * kp], &gb = g[2 * kp + 1];
                             // uniform: neither direction has this segment (a zero-length
                             // segment through an edge still moves the ray to the next column)
-                            if (((ga.bits >> 24) & 7) < step && ((gb.bits >> 24) & 7) < step) continue;
-                            const int sh = step == 2 ? 0 : 12;
-                            const int offa = (ga.bits >> sh) & 4095, offb = ((gb.bits >> sh) & 4095) - 1;
-                            const pr dsv = step == 2 ? P::mk(ga.ds2, gb.ds2) : P::mk(ga.ds3, gb.ds3);
+                            if (!((g[kp].off3 >> (22 + step)) & 1)) continue;
+                            const int ow = step == 2 ? g[kp].off2 : g[kp].off3;
+                            const int offa = ow & 4095, offb = (ow >> 12) & 4095;
+                            const pr dsv = step == 2 ? g[kp].ds2 : g[kp].ds3;
                             const real *Xr = reinterpret_cast<const real *>(X + kp * NS);
 #pragma unroll
                             for (int s = 0; s < OPT; ++s) {
                                 pr dsph, xph;
                                 seg_coef2(oc[s], dsv, dsph, xph);
-                                pr Iin = P::mk(Xr[o_r2[s] - offa], Xr[o_r2[s] - offb]);
+                                pr Iin = P::mk(Xr[o_r2[s] - offa], Xr[o_r2[s] + 1 - offb]);
                                 seg_apply2<real>(Iin, oA[s][kp], oc[s].src, dsph, xph, form);
                                 oI[s][kp] = Iin;
                             }
@@ -546,7 +576,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<real> &p, int item, u
                                 if (h_w[s] && h_act[s]) {
                                     pr dsph, xph, dummy = P::splat(real(0));
                                     seg_coef2(hc[s], dsv, dsph, xph);
-                                    pr Iin = P::mk(Xr[2 * h_r[s] - offa], Xr[2 * h_r[s] - offb]);
+                                    pr Iin = P::mk(Xr[2 * h_r[s] - offa], Xr[2 * h_r[s] + 1 - offb]);
                                     seg_apply2<real>(Iin, dummy, hc[s].src, dsph, xph, form);
                                     hI[s][kp] = Iin;
                                 }
@@ -559,7 +589,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<real> &p, int item, u
                         if (o_ok[s]) {
                             pr a2 = P::splat(real(0));
 #pragma unroll
-                            for (int kp = 0; kp < KP; ++kp) a2 = P::fma(oA[s][kp], P::mk(na[2 * kp], na[2 * kp + 1]), a2);
+                            for (int kp = 0; kp < KP; ++kp) a2 = P::fma(oA[s][kp], na2[kp], a2);
                             kahan_add(js[s][i], jc[s][i], a2.x + a2.y);
                         }
                     }
@@ -609,6 +639,7 @@ template <typename real, int TB, int TC, int BLK, int NT, int KP, int MINB>
 __global__ void __launch_bounds__(NT, MINB) sweep_block_kernel(const SweepArgs<real> p)
 {
     extern __shared__ __align__(32) unsigned char smem_raw[];
+    grid_dep_launch();
     if ((int)blockIdx.x < p.n_work) sweep_item<real, TB, TC, BLK, NT, KP>(p, blockIdx.x, smem_raw);
 }
 
@@ -620,6 +651,7 @@ __global__ void __launch_bounds__(NT, MINB) sweep_queue_kernel(const SweepArgs<r
 {
     extern __shared__ __align__(32) unsigned char smem_raw[];
     __shared__ int s_item;
+    grid_dep_launch();
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(p.counter, 1);
         __syncthreads();
