@@ -71,6 +71,20 @@ def test_fp32_ragged_noncubic(orc, tiles):
     assert rel(J, j_o) < 1e-5
 
 
+@pytest.mark.parametrize("variant", [3, 4, 6, 9, 10])
+def test_fp32_ragged_by_variant(orc, variant):
+    """Variants that share a tile shape with another (thread count, pairs per
+    exchange, CTAs per SM differ), selected by index."""
+    rng = np.random.default_rng(8)
+    shape = (21, 26, 37)
+    kap = f32(0.5 * np.exp(rng.standard_normal(shape)))
+    S = f32(rng.random(shape))
+    jin_o, j_o, _ = orc.sweep(kap, S, 2)
+    J, Jin = run(kap, S, 2, variant=variant)
+    assert rel(Jin, jin_o) < 1e-5
+    assert rel(J, j_o) < 1e-5
+
+
 @pytest.mark.parametrize("split", [1, 3])
 def test_fp64_ragged_direction_groups(orc, split):
     rng = np.random.default_rng(8)
