@@ -317,6 +317,16 @@ def ionization_measure(torch, dev, tol=1e-6, n_setups=8, n_iter=24, train_steps=
 
     warm("warm_coarse_solve", None, use_net=False, phase1_max_iter=0)
     warm("warm_coarse_solve_coarse_sweep_phase", None, use_net=False)
+    # the on-the-spot approximation (alpha_A = alpha_B: no diffuse field, no sweep)
+    otsa = dict(case.chem, alphaA=case.chem["alphaB"])
+    sw.iterate(nH, otsa, srcs, fresh(), tol=tol, max_iter=300)
+    t_otsa, (rep_o, _), y_otsa = timed(lambda y: sw.iterate(nH, otsa, srcs, y, tol=tol, max_iter=300))
+    y_otsa = y_otsa.cpu().numpy()
+    out["on_the_spot"] = {"iterations": int(rep_o.iterations), "seconds": round(t_otsa, 4),
+                          "converged": bool(rep_o.converged),
+                          "mean_neutral_fraction": float(np.mean(y_otsa)),
+                          "mean_neutral_fraction_with_diffuse": float(np.mean(y_plain)),
+                          "ionized_volume_ratio_diffuse_over_otsa": float(np.sum(1 - y_plain) / np.sum(1 - y_otsa))}
     # train the network on other setups (untimed)
     X = torch.empty((n_setups * n_iter, 4, V), device=dev)
     T = torch.empty((n_setups * n_iter, V), device=dev)
@@ -417,6 +427,46 @@ def clumpy_measure(torch, dev, net, tol=1e-6):
                                   converged=bool(wr.total.converged),
                                   speedup_vs_plain=round(out["plain"]["seconds"] / out[label]["seconds"], 3),
                                   max_rel_dy_vs_plain=float(np.max(np.abs(y.cpu().numpy() - y_plain) / y_plain)))
+    sw.close()
+    return out
+
+
+def shadow_measure(torch, dev, tol=1e-6):
+    """The geometry of the paper's Test 3 at 128^3, N_side 8: uniform n_H 2e-4
+    with a clump of 200x density (radius 0.8 kpc, 1.7 kpc from the centre along
+    x), lit by a plane-parallel flux of 1e6 photons/s/cm^2 through the x = 0
+    face over 4 blackbody (1e5 K) bins; equilibrium solve at 1e4 K with the
+    diffuse field and on the spot.  Reports the neutral fraction on the clump's
+    axis just behind it and at the same depth off the shadow."""
+    from paper_1410_0763_gb300 import art
+    from paper_1410_0763_gb300 import workloads as wl
+    case = wl.shadow_clump()
+    frac, sig, _ = wl.blackbody_bins()
+    n = case.n
+    sw = art.ArtSweep(case.nH.shape, case.nside, 1, field_form=art.ART_FIELDS_EPS, dx_cm=case.chem["dx"])
+    sw.set_source_spectrum(sig, frac)
+    sw.set_plane_source(*case.plane)
+    nH = torch.as_tensor(case.nH, dtype=torch.float64, device=dev)
+    out = {"workload": "128^3 Test-3 geometry: n_H 2e-4, clump x200 (r 0.8 kpc, 1.7 kpc off centre along x), "
+                       "plane-parallel flux 1e6 s^-1 cm^-2 through x = 0, 4 blackbody bins, N_side 8, 1e4 K",
+           "tol": tol}
+    mid = n // 2
+    behind = (mid, mid, n - 2)          # (z, y, x): on the clump's axis, behind it
+    beside = (mid, n // 8, n - 2)       # same depth, outside the shadow
+    for label, chem in (("with_diffuse", case.chem), ("on_the_spot", dict(case.chem, alphaA=case.chem["alphaB"]))):
+        y = torch.as_tensor(case.y0, dtype=torch.float64, device=dev).clone()
+        sw.iterate(nH, chem, [], y, tol=tol, max_iter=400)       # first-call allocations
+        y = torch.as_tensor(case.y0, dtype=torch.float64, device=dev).clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep, _ = sw.iterate(nH, chem, [], y, tol=tol, max_iter=400)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        yh = y.cpu().numpy()
+        out[label] = {"iterations": int(rep.iterations), "seconds": round(dt, 4), "converged": bool(rep.converged),
+                      "neutral_fraction_behind_clump": float(yh[behind]),
+                      "neutral_fraction_beside_shadow": float(yh[beside]),
+                      "mean_neutral_fraction": float(np.mean(yh))}
     sw.close()
     return out
 
@@ -543,6 +593,10 @@ def run_ours(args, d: Dist):
             extra["rt_ionization_128"], extra["rt_ionization_256_clumpy"] = ionization_measure(torch, dev)
         except Exception as ex:  # pragma: no cover
             extra["rt_ionization_128"] = {"error": str(ex)}
+        try:
+            extra["rt_ionization_128_plane_flux"] = shadow_measure(torch, dev)
+        except Exception as ex:  # pragma: no cover
+            extra["rt_ionization_128_plane_flux"] = {"error": str(ex)}
 
     cpu = None
     if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:

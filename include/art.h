@@ -194,6 +194,17 @@ art_status art_set_fields(art_ctx *ctx, const void *kappa, const void *src, int 
 art_status art_set_band(art_ctx *ctx, const double *G);
 
 /*
+ * Boundary intensity of the diffuse sweep: every ray of every direction
+ * enters the box with intensity I_bc[b] in bin b (isotropic, uniform over the
+ * faces), instead of the vacuum boundary I = 0 of Eq. (rad_tr2) with
+ * I(0) = 0.  The formal solution then carries I_bc e^-tau into the box (the
+ * incident-radiation boundary of Sec. 4.3).  Host array of nu_bins doubles,
+ * each finite and >= 0; NULL restores vacuum.  Applies to the following
+ * art_sweep calls (a captured graph is re-captured).  Errors: ART_E_INVALID.
+ */
+art_status art_set_boundary_intensity(art_ctx *ctx, const double *I_bc);
+
+/*
  * Host-only: G = int_{nu_lo}^{nu_hi} sigma(nu)/(h nu) dnu for the hydrogenic
  * threshold power law sigma(nu) = sigma0 (nu/nu0)^-3, the band integral of
  * Eq. (gamma_diff) (nu_lo = nu0, nu_hi = nu0 + k_B T/h for the rectangular
@@ -280,6 +291,10 @@ art_status art_point_sources(art_ctx *ctx, const float *kappa, const double *sig
  *   taken at the new state, leaves alpha_B n_e n_HII = n_HI (Gamma_coll n_e + g),
  *   solved for the neutral fraction y in FP64 without cancellation;
  * until max_cells |n_e^(i) - n_e^(i-1)| / n_e^(i) < tol.
+ * alpha_A == alpha_B selects the on-the-spot approximation (Sec. 2.1, Eq.
+ * on_the_spot): the recombination emissivity vanishes, the source function is
+ * neglected, J^in = 0 and no sweep runs, leaving case-B recombination
+ * against the point sources (and collisions).
  * The context must be FP32 with one bin and ART_FIELDS_EPS inputs.
  * nH: device [z][y][x] doubles (cm^-3); y: device [z][y][x] doubles, the
  * initial neutral fraction on input and the result on output; src: host
@@ -303,6 +318,33 @@ art_status art_iterate_ionization(art_ctx *ctx, const art_chem *chem, const doub
  * ART_E_INVALID.
  */
 art_status art_set_source_spectrum(art_ctx *ctx, int nbins, const double *sigma, const double *frac);
+
+/*
+ * Photo-ionization rate of a plane-parallel incident flux, the Test-3 setup
+ * of Sec. 4.3 (a constant photon flux through one face of the box: a point
+ * source at infinity).  The beam travels along +axis (dir = 1, entering at
+ * coordinate 0) or -axis (dir = -1); axis 0, 1, 2 = x, y, z.  In bin b a cell
+ * absorbs flux[b] dx^2 e^-tau (1 - e^-dtau) photons/s, tau summing kappa_b
+ * over the cells before it along the beam and dtau = kappa_b, so per
+ * neutral atom
+ *   Gamma = sum_b flux[b] sigma[b] e^-tau (1 - e^-dtau) / dtau
+ * (photon-conserving as App. A's point-source rate; no dependence on dx).
+ * kappa: device [bin][z][y][x] floats per cell width; sigma, flux: host
+ * arrays of nu_bins values (cm^2, photons/s/cm^2); gamma: device [z][y][x]
+ * floats (s^-1), overwritten.  FP32, stream-ordered.  Errors: ART_E_INVALID
+ * (null pointers, bad axis or dir, negative or non-finite values, more than
+ * 4 bins, a rate beyond FP32 range), ART_E_CUDA.
+ */
+art_status art_plane_source(art_ctx *ctx, const float *kappa, const double *sigma, int axis, int dir,
+                            const double *flux, float *gamma, void *stream);
+
+/*
+ * Adds a plane-parallel incident flux (as art_plane_source) to the point
+ * sources of art_iterate_ionization on this context: flux photons/s/cm^2
+ * along axis in direction dir, split over the source spectrum's bins like
+ * the point sources' photons.  flux = 0 removes it.  Errors: ART_E_INVALID.
+ */
+art_status art_set_plane_source(art_ctx *ctx, int axis, int dir, double flux);
 
 /* Per-kernel device time accumulated while profiling is enabled. */
 typedef struct {

@@ -143,7 +143,8 @@ art_status art_surrogate_sample(art_ctx *ctx, const art_chem *chem, const double
  * weights w + k * V (J^in / mean J^in; w may be NULL), target and weights
  * taken on the J^in of that iteration's own sweep.  X, t, w are device arrays
  * of n_iter samples.  Stream-ordered except for one host
- * synchronization per iteration.  Errors as art_surrogate_sample.
+ * synchronization per iteration.  Errors as art_surrogate_sample, and
+ * ART_E_INVALID under the on-the-spot approximation (no diffuse field).
  */
 art_status art_surrogate_collect(art_ctx *ctx, const art_chem *chem, const double *nH, const art_source *src,
                                  int n_src, double *y, int n_iter, int coarse_factor, int coarse_nside, float *X,
@@ -195,7 +196,9 @@ art_status art_warm_options_default(art_warm_options *opt);
  * of the full sweep; one full sweep then judges the surrogate on the current
  * state; if its error exceeds judge_tol the state is reset to the initial y
  * (fell_back = 1); plain iterations run to tol.  net may be NULL only with
- * use_net = 0.  Errors as art_iterate_ionization.
+ * use_net = 0.  Under the on-the-spot approximation (alpha_A == alpha_B)
+ * there is no diffuse field: only the coarse-mesh solve runs before the
+ * plain iterations.  Errors as art_iterate_ionization.
  */
 art_status art_iterate_ionization_warm(art_ctx *ctx, art_net *net, const art_chem *chem, const double *nH,
                                        const art_source *src, int n_src, double tol, int max_iter,

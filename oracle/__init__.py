@@ -45,7 +45,8 @@ def build(force: bool = False) -> str:
 
 class SweepCfg(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("nside", C.c_int),
-                ("tie_tol", C.c_double), ("field_form", C.c_int), ("nthreads", C.c_int)]
+                ("tie_tol", C.c_double), ("field_form", C.c_int), ("nthreads", C.c_int),
+                ("i_bc", C.c_double)]
 
 
 class Chem(C.Structure):
@@ -87,6 +88,10 @@ def _lib_handle():
                                         C.c_double, C.c_int, _D, _D, C.POINTER(C.c_int)]
             lib.orc_iterate_bins.argtypes = [C.POINTER(SweepCfg), C.POINTER(Chem), _D, C.c_int, _D, _D,
                                              C.c_int, _D, _D, C.c_double, C.c_int, _D, _D, C.POINTER(C.c_int)]
+            lib.orc_iterate_ext.argtypes = [C.POINTER(SweepCfg), C.POINTER(Chem), _D, C.c_int, _D, _D,
+                                            C.c_int, _D, _D, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
+                                            _D, _D, C.POINTER(C.c_int)]
+            lib.orc_plane_source.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _D, _D, C.c_int, C.c_int, _D, _D]
             _lib = lib
     return _lib
 
@@ -103,10 +108,10 @@ def default_threads() -> int:
     return max(1, min(os.cpu_count() or 1, 64))
 
 
-def _cfg(shape, nside, field_form=0, tie_tol=1e-12, nthreads=None) -> SweepCfg:
+def _cfg(shape, nside, field_form=0, tie_tol=1e-12, nthreads=None, i_bc=0.0) -> SweepCfg:
     nz, ny, nx = shape
     return SweepCfg(nx, ny, nz, nside, tie_tol, int(field_form),
-                    default_threads() if nthreads is None else int(nthreads))
+                    default_threads() if nthreads is None else int(nthreads), float(i_bc))
 
 
 def n_dirs(nside: int) -> int:
@@ -121,12 +126,13 @@ def healpix_dirs(nside: int) -> np.ndarray:
     return out
 
 
-def sweep(kappa, src, nside, field_form=0, tie_tol=1e-12, nthreads=None):
-    """Full sweep (Sec. 2.2).  kappa, src: [z][y][x].  Returns (J_in, J, n_w_zero)."""
+def sweep(kappa, src, nside, field_form=0, tie_tol=1e-12, nthreads=None, i_bc=0.0):
+    """Full sweep (Sec. 2.2).  kappa, src: [z][y][x]; i_bc: intensity of every ray
+    entering the box (0: vacuum).  Returns (J_in, J, n_w_zero)."""
     k, s = _f64(kappa), _f64(src)
     jin = np.empty_like(k)
     j = np.empty_like(k)
-    cfg = _cfg(k.shape, nside, field_form, tie_tol, nthreads)
+    cfg = _cfg(k.shape, nside, field_form, tie_tol, nthreads, i_bc)
     nz = _lib_handle().orc_sweep(C.byref(cfg), _dp(k), _dp(s), _dp(jin), _dp(j))
     if nz < 0:
         raise MemoryError("oracle sweep: allocation failed")
@@ -157,12 +163,12 @@ def sweep_range_count(kappa, src, nside, d0, d1, field_form=0, tie_tol=1e-12, nt
     return acc, int(n.value)
 
 
-def sweep_dir(kappa, src, nside, d, field_form=0, tie_tol=1e-12):
+def sweep_dir(kappa, src, nside, d, field_form=0, tie_tol=1e-12, i_bc=0.0):
     """Per-cell A (sum ds*Ibar_in) and W (sum ds) of one direction."""
     k, s = _f64(kappa), _f64(src)
     A = np.empty_like(k)
     W = np.empty_like(k)
-    cfg = _cfg(k.shape, nside, field_form, tie_tol, 1)
+    cfg = _cfg(k.shape, nside, field_form, tie_tol, 1, i_bc)
     if _lib_handle().orc_sweep_dir(C.byref(cfg), _dp(k), _dp(s), int(d), _dp(A), _dp(W)) != 0:
         raise ValueError("bad direction index")
     return A, W
@@ -179,14 +185,14 @@ def lattice(shape, nside, d, tie_tol=1e-12):
     return tuple(int(v) for v in r), tuple(ax), tuple(q)
 
 
-def trace_ray(kappa, src, nside, d, j, k, field_form=0, tie_tol=1e-12, maxseg=100000):
+def trace_ray(kappa, src, nside, d, j, k, field_form=0, tie_tol=1e-12, maxseg=100000, i_bc=0.0):
     """Segments (cell, ds, I_in) of lattice ray (j, k) of direction d, and the exit intensity."""
     kk, s = _f64(kappa), _f64(src)
     cells = np.zeros(maxseg, dtype=np.int64)
     ds = np.zeros(maxseg)
     iin = np.zeros(maxseg)
     iex = C.c_double(0.0)
-    cfg = _cfg(kk.shape, nside, field_form, tie_tol, 1)
+    cfg = _cfg(kk.shape, nside, field_form, tie_tol, 1, i_bc)
     n = _lib_handle().orc_trace_ray(C.byref(cfg), _dp(kk), _dp(s), int(d), int(j), int(k),
                                     cells.ctypes.data_as(_L), _dp(ds), _dp(iin), maxseg,
                                     C.byref(iex))
@@ -195,12 +201,12 @@ def trace_ray(kappa, src, nside, d, j, k, field_form=0, tie_tol=1e-12, maxseg=10
     return cells[:n].copy(), ds[:n].copy(), iin[:n].copy(), iex.value
 
 
-def jin_cells(kappa, src, nside, cells, field_form=0, tie_tol=1e-12, nthreads=None):
+def jin_cells(kappa, src, nside, cells, field_form=0, tie_tol=1e-12, nthreads=None, i_bc=0.0):
     """J^in at the given flat cell indices, computed one cell at a time."""
     k, s = _f64(kappa), _f64(src)
     c = np.ascontiguousarray(np.asarray(cells, dtype=np.int64))
     out = np.empty(c.shape[0])
-    cfg = _cfg(k.shape, nside, field_form, tie_tol, nthreads)
+    cfg = _cfg(k.shape, nside, field_form, tie_tol, nthreads, i_bc)
     bad = _lib_handle().orc_jin_cells(C.byref(cfg), _dp(k), _dp(s), c.ctypes.data_as(_L),
                                       int(c.shape[0]), _dp(out))
     if bad:
@@ -242,10 +248,29 @@ def balance_eq(nH, alphaB, gcoll, g):
     return y
 
 
+def plane_source(kappa_bins, sigma, axis, direction, flux):
+    """Photo-ionization rate of a plane-parallel incident flux (the Test-3 setup, Sec. 4.3): flux[b]
+    photons/s/cm^2 in bin b travelling along +axis (direction 1) or -axis (-1); axis 0, 1, 2 = x, y, z.
+    kappa_bins: [bin][z][y][x] per cell width.  Returns Gamma [z][y][x] in s^-1."""
+    k = _f64(kappa_bins)
+    if k.ndim == 3:
+        k = k[None]
+    nb = k.shape[0]
+    sig = _f64(sigma).reshape(nb)
+    F = _f64(flux).reshape(nb)
+    nz, ny, nx = k.shape[1:]
+    out = np.empty((nz, ny, nx))
+    if _lib_handle().orc_plane_source(nx, ny, nz, nb, _dp(k), _dp(sig), int(axis), int(direction), _dp(F),
+                                      _dp(out)) != 0:
+        raise ValueError("axis must be 0-2 and direction +-1")
+    return out
+
+
 def iterate(nH, nside, chem: dict, pos, Q, y0, tol=1e-6, max_iter=200, nthreads=None, sigma_bins=None,
-            frac_bins=None):
+            frac_bins=None, plane=None):
     """RT / balance fixed-point iteration (App. D).  Point sources emit Q * frac_b in bin b with cross
-    section sigma_b (default: one bin at sigma0).  Returns (y, iters, residuals, converged)."""
+    section sigma_b (default: one bin at sigma0); plane = (axis, direction, flux) adds a plane-parallel
+    incident flux split over the bins the same way.  Returns (y, iters, residuals, converged)."""
     n = _f64(nH)
     y = _f64(y0).copy()
     p = _f64(pos).reshape(-1, 3)
@@ -257,9 +282,10 @@ def iterate(nH, nside, chem: dict, pos, Q, y0, tol=1e-6, max_iter=200, nthreads=
     ch = Chem(chem["alphaA"], chem["alphaB"], chem["gcoll"], chem["sigma0"], chem["h"],
               chem["nu0"], chem["dnu"], chem["dx"])
     cfg = _cfg(n.shape, nside, 1, 1e-12, nthreads)
-    rc = _lib_handle().orc_iterate_bins(C.byref(cfg), C.byref(ch), _dp(n), p.shape[0], _dp(p), _dp(q),
-                                        int(sig.size), _dp(sig), _dp(frac), float(tol), int(max_iter),
-                                        _dp(y), _dp(hist), C.byref(it))
+    pa, pd, pf = plane if plane is not None else (0, 1, 0.0)
+    rc = _lib_handle().orc_iterate_ext(C.byref(cfg), C.byref(ch), _dp(n), p.shape[0], _dp(p), _dp(q),
+                                       int(sig.size), _dp(sig), _dp(frac), int(pa), int(pd), float(pf),
+                                       float(tol), int(max_iter), _dp(y), _dp(hist), C.byref(it))
     if rc < 0:
         raise MemoryError("oracle iterate: allocation failed")
     return y, it.value, hist[: it.value].copy(), rc == 0

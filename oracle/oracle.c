@@ -15,7 +15,8 @@
  *   - the parallel-ray family of each direction (Sec. 2.2, Fig. parallel_ray;
  *     reading: a unit lattice of lines on planes normal to the dominant axis,
  *     offset to cell centres), each line marched cell by cell from where it
- *     enters the box with vacuum intensity;
+ *     enters the box with vacuum intensity, or with a given boundary
+ *     intensity (the incident-radiation boundary of Sec. 4.3);
  *   - the per-segment transfer step, Eq. (rt); the path-averaged incoming
  *     intensity of a segment (the equation after Eq. (rt)); the Delta-tau
  *     weighted cell average, Eqs. (path_averaged_intensity) and
@@ -25,6 +26,10 @@
  *   - point sources by long characteristics with the photon-conserving rate
  *     of App. A, Eq. (pc_gamma), with the absorbed count taken as in minus
  *     out (App. A prints out minus in; the sign is a typo);
+ *   - a plane-parallel incident photon flux through one face (Test-3 setup,
+ *     Sec. 4.3), absorbed cell by cell with the same photon-conserving rate;
+ *   - the on-the-spot approximation (Sec. 2.1, Eq. on_the_spot) as the case
+ *     alpha_A = alpha_B, where the recombination emissivity vanishes;
  *   - the hydrogen ionization balance of App. B in its dt -> infinity
  *     (equilibrium) limit, and the RT/balance fixed-point iteration of App. D
  *     with the electron-density convergence test.
@@ -251,6 +256,7 @@ typedef struct {
     double tie_tol;
     int field_form;   /* 0: (kappa, S) inputs; 1: (kappa, emissivity) inputs */
     int nthreads;
+    double i_bc;      /* intensity of every ray where it enters the box (0: vacuum) */
 } orc_sweep_cfg;
 
 typedef struct {
@@ -324,7 +330,7 @@ static long long sweep_dir(const orc_sweep_cfg *cfg, const double *kappa, const 
     r.only_cell = -1;
     for (long k = klo; k <= khi; k++)
         for (long j = jlo; j <= jhi; j++) {
-            r.I = 0.0;   /* vacuum boundary: nothing enters the box */
+            r.I = cfg->i_bc;   /* boundary intensity entering the box (0: vacuum) */
             march_ray(&f, j, k, seg_update, &r);
         }
     return r.nseg;
@@ -441,7 +447,7 @@ int orc_trace_ray(const orc_sweep_cfg *cfg, const double *kappa, const double *s
     r.Iin = Iin;
     r.maxseg = maxseg;
     r.only_cell = -1;
-    r.I = 0.0;
+    r.I = cfg->i_bc;
     march_ray(&f, j, k, seg_update, &r);
     if (I_exit) *I_exit = r.I;
     return r.nrec;
@@ -493,7 +499,7 @@ int orc_jin_cells(const orc_sweep_cfg *cfg, const double *kappa, const double *s
             r.only_cell = cell;
             for (long k = kr[0]; k <= kr[1]; k++)
                 for (long j = jr[0]; j <= jr[1]; j++) {
-                    r.I = 0.0;
+                    r.I = cfg->i_bc;
                     march_ray(&f, j, k, seg_update, &r);
                 }
             if (W > 0.0) sum += A / W;
@@ -610,6 +616,42 @@ int orc_point_sources(int nx, int ny, int nz, int nbins, const double *kappa_bin
 }
 
 /* ------------------------------------------------------------------------ */
+/* Plane-parallel incident flux (the Test-3 setup of Sec. 4.3: a constant    */
+/* photon flux F through one face of the box, i.e. a point source at         */
+/* infinity).  The beam travels along +axis (dir = +1, entering at the face  */
+/* coordinate 0) or -axis (dir = -1).  In bin b, the photons absorbed in a   */
+/* cell per unit time are F_b dx^2 e^-tau (1 - e^-dtau), tau summing kappa_b */
+/* over the cells before it along the beam and dtau = kappa_b of the cell;   */
+/* per neutral atom (n_HI dx^3 = kappa_b dx^2 / sigma_b):                    */
+/*   Gamma += F_b sigma_b e^-tau (1 - e^-dtau) / dtau.                       */
+/* ------------------------------------------------------------------------ */
+int orc_plane_source(int nx, int ny, int nz, int nbins, const double *kappa_bins, const double *sigma,
+                     int axis, int dir, const double *F, double *gamma)
+{
+    const int dims[3] = {nx, ny, nz};
+    const long stride[3] = {1, nx, (long)nx * ny};
+    const long ncell = (long)nx * ny * nz;
+    if (axis < 0 || axis > 2 || (dir != 1 && dir != -1)) return -1;
+    const int u = axis == 0 ? 1 : 0, v = axis == 2 ? 1 : 2;   /* the two transverse axes */
+    for (long i = 0; i < ncell; i++) gamma[i] = 0.0;
+    for (int b = 0; b < nbins; b++) {
+        const double *kap = kappa_bins + (size_t)b * ncell;
+        for (int q = 0; q < dims[v]; q++)
+            for (int p = 0; p < dims[u]; p++) {
+                double tau = 0.0;
+                for (int m = 0; m < dims[axis]; m++) {
+                    const int a = dir > 0 ? m : dims[axis] - 1 - m;
+                    const long cell = a * stride[axis] + p * stride[u] + q * stride[v];
+                    const double dtau = kap[cell];
+                    gamma[cell] += F[b] * sigma[b] * exp(-tau) * phi_of(dtau);
+                    tau += dtau;
+                }
+            }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Ionization balance (App. B), hydrogen only, in the dt -> infinity limit:  */
 /*   alpha_A n_e n_HII = n_HI (Gamma_coll n_e + Gamma_gamma),                */
 /* Gamma_gamma = Gamma_point + Gamma^diff and Gamma^diff carries the local   */
@@ -650,6 +692,10 @@ int orc_iterate_bins(const orc_sweep_cfg *cfg, const orc_chem *ch, const double 
                      const double *pos, const double *Q, int nb, const double *sigma_b,
                      const double *frac_b, double tol, int max_iter, double *y,
                      double *resid_hist, int *iters);
+int orc_iterate_ext(const orc_sweep_cfg *cfg, const orc_chem *ch, const double *nH, int nsrc,
+                    const double *pos, const double *Q, int nb, const double *sigma_b,
+                    const double *frac_b, int pl_axis, int pl_dir, double pl_flux, double tol,
+                    int max_iter, double *y, double *resid_hist, int *iters);
 
 int orc_iterate(const orc_sweep_cfg *cfg, const orc_chem *ch, const double *nH, int nsrc,
                 const double *pos, const double *Q, double tol, int max_iter, double *y,
@@ -669,6 +715,18 @@ int orc_iterate_bins(const orc_sweep_cfg *cfg, const orc_chem *ch, const double 
                      const double *frac_b, double tol, int max_iter, double *y,
                      double *resid_hist, int *iters)
 {
+    return orc_iterate_ext(cfg, ch, nH, nsrc, pos, Q, nb, sigma_b, frac_b, 0, 1, 0.0, tol, max_iter, y,
+                           resid_hist, iters);
+}
+
+/* ... and, with pl_flux > 0, a plane-parallel incident flux of pl_flux
+ * photons/s/cm^2 along axis pl_axis in direction pl_dir, split over the bins
+ * like the point sources' photons (frac_b). */
+int orc_iterate_ext(const orc_sweep_cfg *cfg, const orc_chem *ch, const double *nH, int nsrc,
+                    const double *pos, const double *Q, int nb, const double *sigma_b,
+                    const double *frac_b, int pl_axis, int pl_dir, double pl_flux, double tol,
+                    int max_iter, double *y, double *resid_hist, int *iters)
+{
     const long ncell = (long)cfg->nx * cfg->ny * cfg->nz;
     double *kap = (double *)malloc(sizeof(double) * ncell);
     double *kapb = (double *)malloc(sizeof(double) * ncell * nb);
@@ -678,7 +736,10 @@ int orc_iterate_bins(const orc_sweep_cfg *cfg, const orc_chem *ch, const double 
     double *gpt = (double *)malloc(sizeof(double) * ncell);
     double *g = (double *)malloc(sizeof(double) * ncell);
     double *yn = (double *)malloc(sizeof(double) * ncell);
-    if (!kap || !kapb || !qb || !eps || !jin || !gpt || !g || !yn) return -1;
+    double *gpl = (double *)malloc(sizeof(double) * ncell);
+    double *fb = (double *)malloc(sizeof(double) * nb);
+    if (!kap || !kapb || !qb || !eps || !jin || !gpt || !g || !yn || !gpl || !fb) return -1;
+    for (int b = 0; b < nb; b++) fb[b] = pl_flux * frac_b[b];
     for (int a = 0; a < nsrc; a++)
         for (int b = 0; b < nb; b++) qb[a * nb + b] = Q[a] * frac_b[b];
     orc_sweep_cfg c = *cfg;
@@ -696,6 +757,11 @@ int orc_iterate_bins(const orc_sweep_cfg *cfg, const orc_chem *ch, const double 
         for (int b = 0; b < nb; b++)
             for (long i = 0; i < ncell; i++) kapb[b * ncell + i] = y[i] * nH[i] * sigma_b[b] * ch->dx;
         orc_point_sources(cfg->nx, cfg->ny, cfg->nz, nb, kapb, sigma_b, nsrc, pos, qb, ch->dx, cfg->nthreads, gpt);
+        if (pl_flux > 0.0) {
+            if (orc_plane_source(cfg->nx, cfg->ny, cfg->nz, nb, kapb, sigma_b, pl_axis, pl_dir, fb, gpl) != 0)
+                return -1;
+            for (long i = 0; i < ncell; i++) gpt[i] += gpl[i];
+        }
         for (long i = 0; i < ncell; i++) g[i] = 4.0 * M_PI * G * jin[i] + gpt[i];
         orc_balance_eq(ncell, nH, ch->alphaB, ch->gcoll, g, yn);
         double r = 0.0;
@@ -709,6 +775,6 @@ int orc_iterate_bins(const orc_sweep_cfg *cfg, const orc_chem *ch, const double 
         if (r < tol) { conv = 1; break; }
     }
     if (iters) *iters = conv ? it : max_iter;
-    free(kap); free(kapb); free(qb); free(eps); free(jin); free(gpt); free(g); free(yn);
+    free(kap); free(kapb); free(qb); free(eps); free(jin); free(gpt); free(g); free(yn); free(gpl); free(fb);
     return conv ? 0 : 1;
 }

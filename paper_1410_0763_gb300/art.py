@@ -122,6 +122,11 @@ def load() -> C.CDLL:
         lib.art_get_stats.argtypes = [P, C.POINTER(ArtSweepStats)]
         lib.art_set_fields.argtypes = [P, P, P, C.c_int, P]
         lib.art_set_band.argtypes = [P, C.POINTER(C.c_double)]
+        lib.art_set_boundary_intensity.argtypes = [P, C.POINTER(C.c_double)]
+        lib.art_plane_source.argtypes = [P, P, C.POINTER(C.c_double), C.c_int, C.c_int, C.POINTER(C.c_double), P, P]
+        lib.art_plane_source.restype = C.c_int
+        lib.art_set_plane_source.argtypes = [P, C.c_int, C.c_int, C.c_double]
+        lib.art_set_plane_source.restype = C.c_int
         lib.art_sweep.argtypes = [P, P, P, P, C.c_int, P]
         lib.art_count_segments.argtypes = [C.POINTER(ArtGrid), C.c_int, C.c_double, C.POINTER(C.c_int64)]
         lib.art_band_integral.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_double)]
@@ -165,7 +170,7 @@ def load() -> C.CDLL:
                   "art_batch_create", "art_autotune"):
             getattr(lib, f).restype = C.c_int
         for f in ("art_point_sources", "art_iterate_ionization", "art_sweep_noalloc", "art_measure_pipes", "art_band_integral", "art_profile_enable", "art_profile_read", "art_options_default", "art_create", "art_count_segments", "art_destroy", "art_get_stats", "art_set_fields",
-                  "art_set_band", "art_sweep"):
+                  "art_set_band", "art_set_boundary_intensity", "art_sweep"):
             getattr(lib, f).restype = C.c_int
         _lib = lib
         return lib
@@ -241,6 +246,11 @@ def art_set_fields(ctx, kappa_ptr: int, src_ptr: int, on_device: int, stream: in
 def art_set_band(ctx, G) -> int:
     arr = (C.c_double * len(G))(*[float(g) for g in G])
     return load().art_set_band(ctx, arr)
+
+
+def art_set_boundary_intensity(ctx, I_bc) -> int:
+    arr = None if I_bc is None else (C.c_double * len(I_bc))(*[float(v) for v in I_bc])
+    return load().art_set_boundary_intensity(ctx, arr)
 
 
 def art_sweep(ctx, J_ptr: int, Jin_ptr: int, gamma_ptr: int, on_device: int, stream: int) -> int:
@@ -436,6 +446,23 @@ class ArtSweep:
                                                     C.c_void_p(gp), C.c_void_p(_stream(stream))))
         return gamma
 
+    def plane_source(self, kappa, sigma, axis, direction, flux, gamma, stream=None):
+        """Plane-parallel incident flux (Test-3 setup, Sec. 4.3) into `gamma` (device): flux[b]
+        photons/s/cm^2 along +axis (direction 1) or -axis (-1); kappa device [bins][z][y][x] FP32."""
+        kp, kd, _k = _ptr(kappa, np.float32, self.ncell * self.nbins)
+        gp, gd, _g = _ptr(gamma, np.float32, self.ncell)
+        if not (kd and gd):
+            raise TypeError("plane_source takes device buffers")
+        sig = (C.c_double * self.nbins)(*[float(x) for x in sigma])
+        fl = (C.c_double * self.nbins)(*[float(x) for x in flux])
+        _check(self._ctx, load().art_plane_source(self._ctx, C.c_void_p(kp), sig, int(axis), int(direction), fl,
+                                                   C.c_void_p(gp), C.c_void_p(_stream(stream))))
+        return gamma
+
+    def set_plane_source(self, axis=0, direction=1, flux=0.0):
+        """Plane-parallel incident flux of the iteration (photons/s/cm^2; 0 removes it)."""
+        _check(self._ctx, load().art_set_plane_source(self._ctx, int(axis), int(direction), float(flux)))
+
     def iterate(self, nH, chem: dict, sources, y, tol=1e-6, max_iter=200, stream=None):
         """RT / balance iteration (App. D); nH, y: device FP64 [z][y][x]; y updated in place.
         Returns (report, residual history); raises ArtError unless converged."""
@@ -546,6 +573,12 @@ class ArtSweep:
         if len(G) != self.nbins:
             raise ValueError("one band integral per bin")
         _check(self._ctx, art_set_band(self._ctx, G))
+
+    def set_boundary_intensity(self, I_bc):
+        """Intensity of every ray entering the box, one value per bin (None: vacuum)."""
+        if I_bc is not None and len(I_bc) != self.nbins:
+            raise ValueError("one boundary intensity per bin")
+        _check(self._ctx, art_set_boundary_intensity(self._ctx, I_bc))
 
     def sweep(self, J=None, J_in=None, gamma=None, stream=None):
         n = self.ncell * self.nbins

@@ -405,6 +405,7 @@ template <typename real> art_status do_sweep(art_ctx *ctx, real *J, real *Jin, r
         a.n_work = ctx->n_work;
         a.split = ctx->split;
         a.field_form = ctx->opt.field_form;
+        a.i_bc = real(ctx->i_bc[b]);
         cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
         if (ctx->profiling) {
             CK(ctx, cudaEventCreate(&e0));
@@ -543,6 +544,7 @@ art_status create_common(const art_grid *grids, const int *n_side, int n_grids, 
     }
     if (ctx->opt.dir_end > ctx->opt.dir_begin) ctx->nd = ctx->opt.dir_end - ctx->opt.dir_begin;
     ctx->G.assign(nu_bins, 0.0);
+    ctx->i_bc.assign(nu_bins, 0.0);
     ctx->persistent = ctx->opt.persistent > 0 ? 1 : (ctx->opt.persistent < 0 ? 0 : (n_grids > 1 ? 1 : 0));
     ctx->early_launch = ctx->opt.early_launch >= 0;
 
@@ -864,6 +866,20 @@ art_status art_set_band(art_ctx *ctx, const double *G)
         if (!std::isfinite(G[b])) return fail(ctx, ART_E_INVALID, "art_set_band: non-finite band integral");
     for (int b = 0; b < ctx->nbins; ++b) ctx->G[b] = G[b];
     if (ctx->gexec) {   // the captured reduction holds the old coefficients
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+    }
+    return ART_OK;
+}
+
+art_status art_set_boundary_intensity(art_ctx *ctx, const double *I_bc)
+{
+    if (!ctx) return ART_E_INVALID;
+    for (int b = 0; I_bc && b < ctx->nbins; ++b)
+        if (!std::isfinite(I_bc[b]) || I_bc[b] < 0.0)
+            return fail(ctx, ART_E_INVALID, "art_set_boundary_intensity: intensities must be finite and >= 0");
+    for (int b = 0; b < ctx->nbins; ++b) ctx->i_bc[b] = I_bc ? I_bc[b] : 0.0;
+    if (ctx->gexec) {   // the captured launches hold the old value
         cudaGraphExecDestroy(ctx->gexec);
         ctx->gexec = nullptr;
     }

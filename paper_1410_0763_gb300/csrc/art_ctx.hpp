@@ -66,6 +66,7 @@ struct art_ctx {
     long long seg_count = 0;  // segments per sweep, one bin
     long long plane_elems = 0;
     std::vector<double> G;
+    std::vector<double> i_bc;  // boundary intensity per bin (0: vacuum)
     bool have_fields = false;
     long long dev_bytes = 0;
     // device memory
@@ -87,6 +88,8 @@ struct art_ctx {
     art_iter_bufs it;
     int spec_bins = 0;          // point-source spectrum of the iteration (0: one bin at sigma0)
     double spec_sigma[4] = {0, 0, 0, 0}, spec_frac[4] = {0, 0, 0, 0};
+    int plane_axis = 0, plane_dir = 1;   // plane-parallel incident flux of the iteration
+    double plane_flux = 0.0;             // photons/s/cm^2 (0: none)
     art_ctx *coarse = nullptr;  // coarse-mesh sweep of the surrogate
     art_sur_bufs sur;
 };

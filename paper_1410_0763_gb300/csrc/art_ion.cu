@@ -207,6 +207,100 @@ __global__ void __launch_bounds__(128) point_source_kernel(const PtArgs p)
 }
 
 // ---------------------------------------------------------------------------
+// Plane-parallel incident flux (the Test-3 setup of Sec. 4.3: a constant
+// photon flux F through one face, a point source at infinity).  One thread
+// per transverse column marches along the beam; in bin b a cell absorbs
+// F_b dx^2 e^-tau (1 - e^-dtau) photons per second, tau summing kappa_b over
+// the cells before it and dtau = kappa_b, so per neutral atom
+// (n_HI dx^3 = kappa_b dx^2 / sigma_b)
+//   Gamma += F_b sigma_b e^-tau phi(dtau),  phi(x) = (1 - e^-x)/x.
+// FP32; threads run along x where x is transverse, so loads coalesce.
+// ---------------------------------------------------------------------------
+struct PlaneArgs {
+    const float *kappa;   // [bins][ncell], or one field scaled per bin (scaled != 0)
+    long long ncell;
+    int nx, ny, nz;
+    int axis, dir;        // beam along +axis (dir 1, entering at coordinate 0) or -axis (dir -1)
+    float coef[4];        // F_b sigma_b
+    int scaled;
+    float kscale[4];
+    int accumulate;       // add to gamma instead of overwriting it
+    float *gamma;
+};
+
+template <int NB, bool SCALED> __global__ void __launch_bounds__(128) plane_source_kernel(const PlaneArgs p)
+{
+    const int dims[3] = {p.nx, p.ny, p.nz};
+    const long long stride[3] = {1, p.nx, (long long)p.nx * p.ny};
+    const int u = p.axis == 0 ? 1 : 0, v = p.axis == 2 ? 1 : 2;   // transverse axes, u fastest
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)dims[u] * dims[v]) return;
+    const int pu = (int)(t % dims[u]), pv = (int)(t / dims[u]);
+    const int na = dims[p.axis];
+    const long long step = p.dir > 0 ? stride[p.axis] : -stride[p.axis];
+    long long ci = pu * stride[u] + pv * stride[v] + (p.dir > 0 ? 0 : (long long)(na - 1) * stride[p.axis]);
+    constexpr int NK = SCALED ? 1 : NB;
+    float tau[NK];
+#pragma unroll
+    for (int b = 0; b < NK; ++b) tau[b] = 0.0f;
+    for (int m = 0; m < na; ++m, ci += step) {
+        float kc[NK];
+#pragma unroll
+        for (int b = 0; b < NK; ++b) kc[b] = __ldg(p.kappa + (long long)b * p.ncell + ci);
+        float g = 0.0f;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const float kb = SCALED ? kc[0] * p.kscale[b] : kc[b];
+            const float tb = SCALED ? tau[0] * p.kscale[b] : tau[b];
+            g += p.coef[b] * __expf(-tb) * pt_phi(kb);
+        }
+#pragma unroll
+        for (int b = 0; b < NK; ++b) tau[b] += kc[b];
+        p.gamma[ci] = p.accumulate ? p.gamma[ci] + g : g;
+    }
+}
+
+art_status launch_plane(art_ctx *ctx, const float *kappa, int nbins, int axis, int dir, const double *coef,
+                        float *gamma, int accumulate, cudaStream_t st, const float *kscale = nullptr)
+{
+    PlaneArgs a;
+    a.kappa = kappa;
+    a.ncell = ctx->ncell;
+    a.nx = ctx->grid.nx;
+    a.ny = ctx->grid.ny;
+    a.nz = ctx->grid.nz;
+    a.axis = axis;
+    a.dir = dir;
+    for (int b = 0; b < 4; ++b) {
+        const double c = b < nbins ? coef[b] : 0.0;
+        if (!(c >= 0.0) || !(c <= 3.0e38))
+            return art_fail(ctx, ART_E_INVALID, "plane source: bad flux or a rate beyond FP32 range");
+        a.coef[b] = (float)c;
+        a.kscale[b] = kscale && b < nbins ? kscale[b] : 1.0f;
+    }
+    a.scaled = kscale != nullptr;
+    a.accumulate = accumulate;
+    a.gamma = gamma;
+    const int dims[3] = {a.nx, a.ny, a.nz};
+    const long long ncol = (long long)dims[axis == 0 ? 1 : 0] * dims[axis == 2 ? 1 : 2];
+    const int nt = 128;
+    const unsigned nb = (unsigned)((ncol + nt - 1) / nt);
+    switch (nbins + (a.scaled ? 4 : 0)) {
+    case 1: plane_source_kernel<1, false><<<nb, nt, 0, st>>>(a); break;
+    case 2: plane_source_kernel<2, false><<<nb, nt, 0, st>>>(a); break;
+    case 3: plane_source_kernel<3, false><<<nb, nt, 0, st>>>(a); break;
+    case 4: plane_source_kernel<4, false><<<nb, nt, 0, st>>>(a); break;
+    case 5: plane_source_kernel<1, true><<<nb, nt, 0, st>>>(a); break;
+    case 6: plane_source_kernel<2, true><<<nb, nt, 0, st>>>(a); break;
+    case 7: plane_source_kernel<3, true><<<nb, nt, 0, st>>>(a); break;
+    case 8: plane_source_kernel<4, true><<<nb, nt, 0, st>>>(a); break;
+    default: return art_fail(ctx, ART_E_INVALID, "plane source: 1 to 4 bins");
+    }
+    ICK(ctx, cudaGetLastError());
+    return ART_OK;
+}
+
+// ---------------------------------------------------------------------------
 // FP64 balance (App. B, dt -> infinity), hydrogen only.  With the local
 // recombination term of Eq. (gamma_diff) at the same state,
 //   alpha_B n_e n_HII = n_HI (Gamma_coll n_e + g),  g = Gamma_point + Gamma_diff,in,
@@ -508,6 +602,8 @@ art_status iterate_impl(art_ctx *ctx, art_net *net, const art_chem *ch, const do
         frac[b] = ctx->spec_bins > 0 ? ctx->spec_frac[b] : 1.0;
         kscale[b] = (float)(sig[b] / ch->sigma0);
     }
+    double plane_coef[4] = {0, 0, 0, 0};   // F frac_b sigma_b of the plane-parallel flux
+    for (int b = 0; b < nbp; ++b) plane_coef[b] = ctx->plane_flux * frac[b] * sig[b];
     std::vector<PtSrc> h_src;
     if ((s = pack_sources(ctx, src, n_src, nullptr, frac.data(), sig.data(), nbp, h_src)) != ART_OK) return s;
     if ((s = source_buffer(ctx, n_src)) != ART_OK) return s;
@@ -534,6 +630,9 @@ art_status iterate_impl(art_ctx *ctx, art_net *net, const art_chem *ch, const do
             c.z /= f;
         }
         ctx->coarse->spec_bins = ctx->spec_bins;
+        ctx->coarse->plane_axis = ctx->plane_axis;   // a flux per area: the same on the coarse mesh
+        ctx->coarse->plane_dir = ctx->plane_dir;
+        ctx->coarse->plane_flux = ctx->plane_flux;
         for (int b = 0; b < 4; ++b) {
             ctx->coarse->spec_sigma[b] = ctx->spec_sigma[b];
             ctx->coarse->spec_frac[b] = ctx->spec_frac[b];
@@ -552,14 +651,25 @@ art_status iterate_impl(art_ctx *ctx, art_net *net, const art_chem *ch, const do
     ICK(ctx, cudaGetLastError());
     ba.solve = 1;
 
-    bool phase1 = warm != nullptr && warm->phase1_max_iter > 0;
+    // On-the-spot approximation (Sec. 2.1, Eq. on_the_spot): alpha_A = alpha_B
+    // makes the recombination emissivity vanish, so the source function is
+    // neglected and J^in = 0 exactly; no sweep (and no surrogate phase) runs.
+    const bool otsa = ch->alphaA == ch->alphaB;
+    if (otsa) ICK(ctx, cudaMemsetAsync(B.jin, 0, n * sizeof(float), st));
+    bool phase1 = !otsa && warm != nullptr && warm->phase1_max_iter > 0;
     bool have_jin = false;
     int it = 0, conv = 0, it1 = 0, sweeps = 0, fell_back = 0;
     double r = 0.0, judge = 0.0;
     for (it = 1; it <= max_iter; ++it) {
         if ((s = launch_points(ctx, B.kap, nbp, d_src, n_src, B.gpt, st, kscale.data())) != ART_OK)
             return s;
-        if (have_jin) {
+        if (ctx->plane_flux > 0.0 &&
+            (s = launch_plane(ctx, B.kap, nbp, ctx->plane_axis, ctx->plane_dir, plane_coef, B.gpt, 1, st,
+                              kscale.data())) != ART_OK)
+            return s;
+        if (otsa) {
+            // J^in stays 0
+        } else if (have_jin) {
             have_jin = false;   // J^in of this state came with the judge's sweep
         } else if (phase1) {
             s = artnet_surrogate(ctx, net, warm->use_net, warm->coarse_factor, warm->coarse_nside, B.kap, B.eps, y,
@@ -644,6 +754,37 @@ art_status art_iterate_ionization(art_ctx *ctx, const art_chem *ch, const double
 {
     return iterate_impl(ctx, nullptr, ch, nH, src, n_src, tol, max_iter, nullptr, y, resid_hist, rep, nullptr,
                         static_cast<cudaStream_t>(stream));
+}
+
+art_status art_set_plane_source(art_ctx *ctx, int axis, int dir, double flux)
+{
+    if (!ctx) return ART_E_INVALID;
+    if (axis < 0 || axis > 2 || (dir != 1 && dir != -1) || !(flux >= 0.0) || !std::isfinite(flux))
+        return art_fail(ctx, ART_E_INVALID, "art_set_plane_source: axis 0-2, dir +-1, finite flux >= 0");
+    ctx->plane_axis = axis;
+    ctx->plane_dir = dir;
+    ctx->plane_flux = flux;
+    return ART_OK;
+}
+
+art_status art_plane_source(art_ctx *ctx, const float *kappa, const double *sigma, int axis, int dir,
+                            const double *flux, float *gamma, void *stream)
+{
+    if (!ctx) return ART_E_INVALID;
+    if (ctx->grids.size() != 1) return art_fail(ctx, ART_E_INVALID, "art_plane_source: single-grid contexts only");
+    if (!kappa || !sigma || !flux || !gamma) return art_fail(ctx, ART_E_INVALID, "art_plane_source: null argument");
+    if (axis < 0 || axis > 2 || (dir != 1 && dir != -1))
+        return art_fail(ctx, ART_E_INVALID, "art_plane_source: axis 0-2 and dir +-1");
+    const int nbins = ctx->nbins;
+    if (nbins > kMaxBins) return art_fail(ctx, ART_E_INVALID, "art_plane_source: at most 4 bins");
+    double coef[4] = {0, 0, 0, 0};
+    for (int b = 0; b < nbins; ++b) {
+        if (!(sigma[b] >= 0.0) || !(flux[b] >= 0.0) || !std::isfinite(sigma[b]) || !std::isfinite(flux[b]))
+            return art_fail(ctx, ART_E_INVALID, "art_plane_source: bad cross section or flux");
+        coef[b] = flux[b] * sigma[b];
+    }
+    const art_status s = launch_plane(ctx, kappa, nbins, axis, dir, coef, gamma, 0, static_cast<cudaStream_t>(stream));
+    return s;
 }
 
 art_status art_set_source_spectrum(art_ctx *ctx, int nbins, const double *sigma, const double *frac)
@@ -733,6 +874,8 @@ art_status art_surrogate_collect(art_ctx *ctx, const art_chem *ch, const double 
 {
     if (!ctx) return ART_E_INVALID;
     if (!X || !t || n_iter < 1) return art_fail(ctx, ART_E_INVALID, "art_surrogate_collect: bad argument");
+    if (ch && ch->alphaA == ch->alphaB)
+        return art_fail(ctx, ART_E_INVALID, "art_surrogate_collect: no diffuse field to learn under the on-the-spot approximation");
     art_warm_options wo;
     art_warm_options_default(&wo);
     wo.coarse_factor = coarse_factor;

@@ -26,7 +26,9 @@
 //    columns, at most BLK wide, starting from the plane values that the
 //    previous launch stored.  Values in the cone that depend on columns
 //    outside it are wrong but never reach the owned tile (a ray moves at most
-//    one column per slab).
+//    one column per slab).  Rays enter the box with the boundary intensity
+//    (0 for vacuum): the first slab block starts every column with it, and
+//    columns outside the box keep it (their cells have kappa = S = 0).
 //  * One launch per slab block; plane buffers ping-pong between launches.
 //    Each class writes its J partial once per cell; a reduce kernel sums the
 //    partials in fixed class order.
@@ -95,6 +97,7 @@ template <typename real> struct SweepArgs {
     int split;
     int kblock;
     int field_form;
+    real i_bc;                   // intensity of every ray where it enters the box (0: vacuum)
 };
 
 // ---------------------------------------------------------------------------
@@ -246,8 +249,8 @@ __device__ __forceinline__ void seg_apply2(typename PairOps<real>::T &I, typenam
 // Shared memory: (kappa, src) of the region (tile + BLK + 1 upstream
 // columns) for the BLK slabs, two exchange buffers of K planes (pairs
 // interleaved) over the region, and the decoded segment tables of a chunk of
-// directions.  Region columns upstream of the box are never written and stay
-// 0: rays there carry the vacuum boundary intensity.
+// directions.  Region columns outside the box hold kappa = S = 0 and their
+// exchange slots are never written: rays there carry the boundary intensity.
 // ---------------------------------------------------------------------------
 template <typename real> struct DirSm {
     long long plane_off;
@@ -342,7 +345,8 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<real> &p, int item, u
         }
         ks[e] = v;
     }
-    for (int e = tid; e < 2 * KP * NS; e += NT) xbuf[e] = P::splat(real(0));
+    // columns outside the box are never written: they carry the boundary intensity
+    for (int e = tid; e < 2 * KP * NS; e += NT) xbuf[e] = P::splat(p.i_bc);
 
     int o_gb[OPT], o_gc[OPT], o_r[OPT];
     bool o_ok[OPT];
@@ -492,12 +496,12 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<real> &p, int item, u
 #pragma unroll
                 for (int s = 0; s < OPT; ++s) {
                     const long long ci = (long long)o_gc[s] * C.Nb + o_gb[s];
-                    oI[s][kp] = P::mk(va && o_ok[s] ? pa[ci] : real(0), vb && o_ok[s] ? pb[ci] : real(0));
+                    oI[s][kp] = P::mk(va && o_ok[s] ? pa[ci] : p.i_bc, vb && o_ok[s] ? pb[ci] : p.i_bc);
                 }
 #pragma unroll
                 for (int s = 0; s < HPT; ++s) {
                     const long long ci = (long long)h_gc[s] * C.Nb + h_gb[s];
-                    hI[s][kp] = P::mk(va && h_ok[s] ? pa[ci] : real(0), vb && h_ok[s] ? pb[ci] : real(0));
+                    hI[s][kp] = P::mk(va && h_ok[s] ? pa[ci] : p.i_bc, vb && h_ok[s] ? pb[ci] : p.i_bc);
                 }
             }
 

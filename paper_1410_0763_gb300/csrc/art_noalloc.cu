@@ -281,6 +281,7 @@ extern "C" art_status art_sweep_noalloc(const art_grid *grid, int n_side, const 
     a.counter = nullptr;
     a.split = 1;
     a.field_form = ART_FIELDS_S;
+    a.i_bc = 0.0f;   // vacuum boundary
     int maxNa = 0;
     for (int c = 0; c < ncls; ++c) maxNa = g_classes[c].Na > maxNa ? g_classes[c].Na : maxNa;
     const size_t sm = SweepShape<kTB, kTC, kBLK, kNT, kKP>::bytes<float>();

@@ -140,6 +140,7 @@ class HIICase:
     chem: dict
     tol: float = 1e-6
     box_cm: float = 6.6 * KPC
+    plane: tuple | None = None  # (axis, direction, photons/s/cm^2) of a plane-parallel incident flux
 
 
 def hii_region(n: int = 128, nside: int = 8, box_kpc: float = 6.6, nH: float = 1e-3,
@@ -164,6 +165,24 @@ def hii_random(n: int = 128, nside: int = 8, seed: int = 100, box_kpc: float = 6
     dx = box_kpc * KPC / n
     return HIICase("hii_random", nside, n, nH_mean * rho, np.full((n, n, n), 1.0 - x0), pos, Q,
                    chem_constants(1e4, dx), 1e-6, box_kpc * KPC)
+
+
+def shadow_clump(n: int = 128, nside: int = 8, box_kpc: float = 6.6, nH: float = 2e-4,
+                 overdensity: float = 200.0, r_kpc: float = 0.8, offset_kpc: float = 1.7,
+                 flux: float = 1e6, x0: float = 1e-4) -> HIICase:
+    """The geometry of the paper's Test 3 (Sec. 4.3): uniform n_H with a sphere
+    of radius r_kpc at overdensity x n_H, centred offset_kpc from the box
+    centre along +x, lit by a plane-parallel photon flux (photons/s/cm^2)
+    entering the x = 0 face along +x.  No point sources.  The gas is held at
+    1e4 K (the rates of chem_constants), not at the paper's 8000 K / 40 K."""
+    dx = box_kpc * KPC / n
+    c = (np.arange(n) + 0.5) * dx
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    mid = 0.5 * box_kpc * KPC
+    r2 = (x - mid - offset_kpc * KPC) ** 2 + (y - mid) ** 2 + (z - mid) ** 2
+    dens = np.where(r2 <= (r_kpc * KPC) ** 2, overdensity * nH, nH)
+    return HIICase("shadow_clump", nside, n, dens, np.full((n, n, n), 1.0 - x0), np.zeros((0, 3)),
+                   np.zeros(0), chem_constants(1e4, dx), 1e-6, box_kpc * KPC, (0, 1, flux))
 
 
 def blackbody_bins(T: float = 1e5, edges_ev=(13.6, 24.6, 54.4, 100.0, 500.0), n_quad: int = 4000):

@@ -149,3 +149,59 @@ def test_iteration_with_source_bins_matches_oracle(orc):
     yg = y.cpu().numpy()
     assert rel(yg, y_o) < 1e-4
     assert rel(1 - yg, 1 - y_o) < 1e-4
+
+
+# --- on-the-spot approximation (Sec. 2.1, Eq. on_the_spot): alpha_A = alpha_B ---
+
+def _stromgren_case(n, nside=2, nH=1e-1, Q=5e48, size_rs=2.5):
+    rs = (3 * Q / (4 * math.pi * nH * nH * wl.ALPHA_B_1E4)) ** (1 / 3)
+    dx = size_rs * rs / n
+    case = wl.hii_region(n=n, nside=nside, box_kpc=n * dx / wl.KPC, nH=nH, Q=Q)
+    return case, rs, dx
+
+
+def _otsa(chem):
+    return dict(chem, alphaA=chem["alphaB"])
+
+
+def test_otsa_iteration_matches_oracle(orc):
+    case, _, _ = _stromgren_case(20)
+    case.chem = _otsa(case.chem)
+    y_gpu, rep, hist = _run_gpu_iteration(case)
+    y_o, it_o, hist_o, conv = orc.iterate(case.nH, case.nside, case.chem, case.pos, case.Q, case.y0, 1e-6, 300)
+    assert conv and rep.converged and abs(rep.iterations - it_o) <= 1
+    assert rel(y_gpu, y_o) < 1e-4
+    assert rel(1 - y_gpu, 1 - y_o) < 1e-4
+
+
+def test_otsa_stromgren_sphere_and_case_b_photon_balance(orc):
+    """64^3, uniform n_H = 0.1 cm^-3, Q = 5e48 s^-1 at the centre, box 2.5 R_S.
+    The converged on-the-spot state holds a case-B Stromgren sphere, and summed
+    over the box, case-B recombinations equal photo- plus collisional
+    ionizations with the oracle's point-source rates at that state."""
+    case, rs, dx = _stromgren_case(64)
+    case.chem = _otsa(case.chem)
+    y, rep, hist = _run_gpu_iteration(case, max_iter=300)
+    assert rep.converged
+    ch = case.chem
+    vol = np.sum(1 - y) * dx ** 3
+    assert vol == pytest.approx(4 * math.pi / 3 * rs ** 3, rel=0.05)
+    nH = case.nH
+    ne, nHI = (1 - y) * nH, y * nH
+    kap = (nHI * ch["sigma0"] * dx).astype(np.float32).astype(np.float64)
+    gpt = orc.point_sources(kap, [ch["sigma0"]], case.pos, case.Q.reshape(-1, 1), dx)
+    recomb = np.sum(ch["alphaB"] * ne * ne)
+    ioniz = np.sum(nHI * (ch["gcoll"] * ne + gpt))
+    assert recomb == pytest.approx(ioniz, rel=1e-4)
+
+
+def test_diffuse_field_enlarges_ionized_region_gpu():
+    """Sec. 4.1: with the recombination radiation transferred (alpha_A > alpha_B)
+    the ionized region is larger than on the spot."""
+    case, _, _ = _stromgren_case(32)
+    y_diff, rep_d, _ = _run_gpu_iteration(case)
+    case.chem = _otsa(case.chem)
+    y_otsa, rep_o, _ = _run_gpu_iteration(case)
+    assert rep_d.converged and rep_o.converged
+    assert np.all(y_diff <= y_otsa * (1 + 1e-4))
+    assert np.sum(1 - y_diff) > 1.02 * np.sum(1 - y_otsa)
