@@ -471,6 +471,45 @@ def shadow_measure(torch, dev, tol=1e-6):
     return out
 
 
+def evolve_measure(torch, dev, F=1.0):
+    """Time-dependent mode on the paper's Test-1 setup at 64^3, N_side 4: n_H
+    1e-3, Q 5e48 s^-1 at a corner of a 6.6 kpc box, from x = 1e-4 to the
+    paper's 30, 100 and 500 Myr, with the diffuse field and on the spot, at
+    1e4 K (no energy equation).  Reports steps, iterations, sweeps, wall time
+    and the ionized-volume radius against the on-the-spot Stromgren growth
+    R_S (1 - e^{-t/t_rec})^{1/3}."""
+    import math
+    from paper_1410_0763_gb300 import art
+    from paper_1410_0763_gb300 import workloads as wl
+    nH0, Q = 1e-3, 5e48
+    case = wl.hii_region(n=64, nside=4, box_kpc=6.6, nH=nH0, Q=Q, source_at="corner")
+    aB, dx = case.chem["alphaB"], case.chem["dx"]
+    t_rec = 1.0 / (aB * nH0)
+    rs = (3 * Q / (4 * math.pi * nH0 * nH0 * aB)) ** (1 / 3)
+    srcs = [(p[0], p[1], p[2], q) for p, q in zip(case.pos, case.Q)]
+    sw = art.ArtSweep(case.nH.shape, case.nside, 1, field_form=art.ART_FIELDS_EPS, dx_cm=dx)
+    nH = torch.as_tensor(case.nH, dtype=torch.float64, device=dev)
+    out = {"workload": "Test-1 setup, 64^3, N_side 4: n_H 1e-3, Q 5e48 s^-1 at a corner, 6.6 kpc, 1e4 K, "
+                       f"F = {F}, eps_iter 1e-3", "t_rec_myr": round(t_rec / wl.MYR, 2),
+           "r_s_kpc": round(rs / wl.KPC, 3)}
+    for label, chem in (("with_diffuse", case.chem), ("on_the_spot", dict(case.chem, alphaA=aB))):
+        y = torch.as_tensor(case.y0, dtype=torch.float64, device=dev).clone()
+        t, rows, tot = 0.0, [], {"steps": 0, "iterations": 0, "sweeps": 0, "seconds": 0.0}
+        for t_myr in (30.0, 100.0, 500.0):
+            rep = sw.evolve(nH, chem, srcs, y, t_myr * wl.MYR - t, F=F)
+            t = t_myr * wl.MYR
+            for k in ("steps", "iterations", "sweeps"):
+                tot[k] += int(getattr(rep, k))
+            tot["seconds"] += float(rep.seconds)
+            vol = 8 * float(torch.sum(1 - y)) * dx ** 3
+            r = (3 * vol / (4 * math.pi)) ** (1 / 3)
+            rows.append({"t_myr": t_myr, "r_ion_over_r_s": round(r / rs, 4),
+                         "stromgren_growth": round((1 - math.exp(-t / t_rec)) ** (1 / 3), 4)})
+        out[label] = dict(tot, seconds=round(tot["seconds"], 3), radius=rows)
+    sw.close()
+    return out
+
+
 def cpu_baseline(case, seg_per_sweep: int, budget_s: float = 12.0) -> dict:
     import oracle
     oracle.build()
@@ -597,6 +636,10 @@ def run_ours(args, d: Dist):
             extra["rt_ionization_128_plane_flux"] = shadow_measure(torch, dev)
         except Exception as ex:  # pragma: no cover
             extra["rt_ionization_128_plane_flux"] = {"error": str(ex)}
+        try:
+            extra["time_dependent_64"] = evolve_measure(torch, dev)
+        except Exception as ex:  # pragma: no cover
+            extra["time_dependent_64"] = {"error": str(ex)}
 
     cpu = None
     if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:

@@ -309,6 +309,56 @@ art_status art_iterate_ionization(art_ctx *ctx, const art_chem *chem, const doub
                                   art_iter_report *rep, void *stream);
 
 /*
+ * Time-dependent mode (App. B-D) for hydrogen at the fixed temperature of
+ * `chem`.  From t = 0 to t_end, in RT steps of
+ *   dt = F min_cells dt_chem  (App. D; or dt_fixed when > 0),
+ *   dt_chem = eps_e |n_e / n_e'| + eps_hi |n_HI / n_HI'|
+ * evaluated at the state and rates at the start of the step.  Each step
+ * iterates: the chemistry of every cell over dt from the state at t, at the
+ * rates of the current iterate (the BDF update of App. B,
+ * n_HI <- (C dtc + n_HI) / (1 + D dtc), C = alpha_B n_e n_HII,
+ * D = Gamma_coll n_e + g, sub-cycled with dt_chem, the last sub-step cut to
+ * end at dt), then the rates of the new iterate (point sources with the
+ * source spectrum, the plane-parallel flux, the diffuse sweep), until
+ * max_cells |n_e^(i) - n_e^(i-1)| / n_e^(i) < eps_iter.  g holds the
+ * non-local rates; the local recombination term of Eq. gamma_diff cancels
+ * the ground-state recombinations (alpha_B), and alpha_A == alpha_B is the
+ * on-the-spot approximation (no sweep).  The energy equation of App. C is not
+ * solved: the temperature stays that of the rate constants.  FP64 chemistry,
+ * one host synchronization per iteration.  nH, y: device [z][y][x] doubles;
+ * y is the state at t = 0 on input and at t_end on output.  Errors:
+ * ART_E_INVALID, ART_E_NOT_CONVERGED (max_steps before t_end, or a step that
+ * reached max_iter: y holds the last state), ART_E_OOM, ART_E_CUDA.
+ */
+typedef struct {
+    double t_end;      /* s */
+    double F;          /* default 10 */
+    double eps_iter;   /* default 1e-3 (App. D) */
+    double eps_e;      /* default 0.2 */
+    double eps_hi;     /* default 0.002 */
+    double dt_fixed;   /* > 0: every step is dt_fixed (s); default 0 */
+    int max_steps;     /* default 100000 */
+    int max_iter;      /* per step, default 100 */
+    int max_sub;       /* chemistry sub-steps per cell and step, default 1e6 */
+} art_evolve_options;
+
+typedef struct {
+    int32_t steps;          /* RT steps taken */
+    int32_t iterations;     /* chemistry / RT iterations over all steps */
+    int32_t sweeps;         /* diffuse sweeps run */
+    int32_t converged;      /* 1 if every step met eps_iter */
+    int64_t sub_overflow;   /* (cell, iteration) pairs that ran out of sub-steps */
+    double t;               /* time reached, s */
+    double dt_min, dt_max;  /* smallest and largest step, s */
+    double seconds;         /* wall time of the call */
+} art_evolve_report;
+
+art_status art_evolve_options_default(art_evolve_options *opt);
+art_status art_evolve_ionization(art_ctx *ctx, const art_chem *chem, const double *nH, const art_source *src,
+                                 int n_src, const art_evolve_options *opt, double *y, art_evolve_report *rep,
+                                 void *stream);
+
+/*
  * Source spectrum of art_iterate_ionization on this context (App. A with
  * frequency bins): every point source emits Q * frac[b] photons/s in bin b,
  * absorbed with cross section sigma[b] (cm^2; kappa_b = n_HI sigma[b] dx);

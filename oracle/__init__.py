@@ -55,6 +55,11 @@ class Chem(C.Structure):
                 ("dnu", C.c_double), ("dx", C.c_double)]
 
 
+class EvolveOpt(C.Structure):
+    _fields_ = [("F", C.c_double), ("eps_iter", C.c_double), ("eps_e", C.c_double), ("eps_hi", C.c_double),
+                ("dt_fixed", C.c_double), ("max_steps", C.c_int), ("max_iter", C.c_int), ("max_sub", C.c_int)]
+
+
 _D = C.POINTER(C.c_double)
 _L = C.POINTER(C.c_long)
 
@@ -92,6 +97,9 @@ def _lib_handle():
                                             C.c_int, _D, _D, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
                                             _D, _D, C.POINTER(C.c_int)]
             lib.orc_plane_source.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _D, _D, C.c_int, C.c_int, _D, _D]
+            lib.orc_evolve.argtypes = [C.POINTER(SweepCfg), C.POINTER(Chem), _D, C.c_int, _D, _D, C.c_int, _D, _D,
+                                       C.c_int, C.c_int, C.c_double, C.POINTER(EvolveOpt), C.c_double, _D,
+                                       C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double), _D]
             _lib = lib
     return _lib
 
@@ -289,6 +297,35 @@ def iterate(nH, nside, chem: dict, pos, Q, y0, tol=1e-6, max_iter=200, nthreads=
     if rc < 0:
         raise MemoryError("oracle iterate: allocation failed")
     return y, it.value, hist[: it.value].copy(), rc == 0
+
+
+
+def evolve(nH, nside, chem: dict, pos, Q, y0, t_end, F=10.0, eps_iter=1e-3, eps_e=0.2, eps_hi=0.002,
+           dt_fixed=0.0, max_steps=100000, max_iter=100, max_sub=1000000, sigma_bins=None, frac_bins=None,
+           plane=None, nthreads=None):
+    """Time-dependent mode (App. B-D) at fixed temperature from t = 0 to t_end (s).  Returns
+    (y, steps, iterations, t_reached, dts, rc): rc 0 when t_end is reached with every step converged,
+    1 if some step's iteration hit max_iter, 2 if max_steps ran out."""
+    n = _f64(nH)
+    y = _f64(y0).copy()
+    p = _f64(pos).reshape(-1, 3)
+    q = _f64(Q).reshape(p.shape[0])
+    sig = _f64([chem["sigma0"]] if sigma_bins is None else sigma_bins)
+    frac = _f64([1.0] if frac_bins is None else frac_bins)
+    ch = Chem(chem["alphaA"], chem["alphaB"], chem["gcoll"], chem["sigma0"], chem["h"],
+              chem["nu0"], chem["dnu"], chem["dx"])
+    cfg = _cfg(n.shape, nside, 1, 1e-12, nthreads)
+    pa, pd, pf = plane if plane is not None else (0, 1, 0.0)
+    opt = EvolveOpt(float(F), float(eps_iter), float(eps_e), float(eps_hi), float(dt_fixed), int(max_steps),
+                    int(max_iter), int(max_sub))
+    dts = np.zeros(max_steps)
+    steps, iters, t = C.c_int(0), C.c_int(0), C.c_double(0.0)
+    rc = _lib_handle().orc_evolve(C.byref(cfg), C.byref(ch), _dp(n), p.shape[0], _dp(p), _dp(q), int(sig.size),
+                                  _dp(sig), _dp(frac), int(pa), int(pd), float(pf), C.byref(opt), float(t_end),
+                                  _dp(y), C.byref(steps), C.byref(iters), C.byref(t), _dp(dts))
+    if rc < 0:
+        raise MemoryError("oracle evolve: allocation failed")
+    return y, steps.value, iters.value, t.value, dts[: steps.value].copy(), rc
 
 
 if __name__ == "__main__":  # pragma: no cover

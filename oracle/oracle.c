@@ -32,7 +32,10 @@
  *     alpha_A = alpha_B, where the recombination emissivity vanishes;
  *   - the hydrogen ionization balance of App. B in its dt -> infinity
  *     (equilibrium) limit, and the RT/balance fixed-point iteration of App. D
- *     with the electron-density convergence test.
+ *     with the electron-density convergence test;
+ *   - the time-dependent mode: the BDF update of App. B sub-cycled with the
+ *     chemical timestep of App. D, RT steps of F times the smallest of them,
+ *     each iterated to convergence of n_e (fixed temperature).
  *
  * Everything is FP64.  Summations run in a fixed order (directions in RING
  * order, rays in lattice order, sources in index order), so the oracle is
@@ -777,4 +780,159 @@ int orc_iterate_ext(const orc_sweep_cfg *cfg, const orc_chem *ch, const double *
     if (iters) *iters = conv ? it : max_iter;
     free(kap); free(kapb); free(qb); free(eps); free(jin); free(gpt); free(g); free(yn); free(gpl); free(fb);
     return conv ? 0 : 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Time-dependent mode (App. B-D), hydrogen only, at the fixed temperature   */
+/* of the chemistry constants.                                              */
+/*                                                                          */
+/* One cell over dt at fixed photo-ionization rate g (App. B): the BDF step */
+/*   n_HI <- (C dtc + n_HI) / (1 + D dtc),  C = alpha_B n_e n_HII,          */
+/*   D = Gamma_coll n_e + g,  n_e = n_HII = n_H - n_HI,                     */
+/* with C and D taken at the start of the sub-step (hydrogen is the lowest  */
+/* ionization level, updated first), sub-cycled with the chemical timestep  */
+/* of App. D, dtc = eps_e |n_e / n_e'| + eps_HI |n_HI / n_HI'|, the last    */
+/* sub-step cut to end at dt.  alpha_B because the local recombination term */
+/* of Eq. (gamma_diff) cancels the ground-state recombinations, as in the   */
+/* equilibrium balance; g holds the non-local rates.                        */
+/* ------------------------------------------------------------------------ */
+static double dtchem_cell(double nH, double y, double alphaB, double gcoll, double g, double eps_e,
+                          double eps_hi)
+{
+    const double nHI = y * nH, ne = (1.0 - y) * nH;
+    const double dHI = alphaB * ne * ne - (gcoll * ne + g) * nHI;   /* dn_HI/dt = -dn_e/dt */
+    if (dHI == 0.0) return INFINITY;
+    return eps_e * fabs(ne / dHI) + eps_hi * fabs(nHI / dHI);
+}
+
+static int chem_cell(double nH, double y0, double alphaB, double gcoll, double g, double dt, double eps_e,
+                     double eps_hi, int max_sub, double *y_out)
+{
+    double y = y0, tau = 0.0;
+    int n = 0;
+    while (tau < dt && n < max_sub) {
+        const double nHI = y * nH, ne = (1.0 - y) * nH;
+        const double C = alphaB * ne * ne, D = gcoll * ne + g;
+        double dtc = dtchem_cell(nH, y, alphaB, gcoll, g, eps_e, eps_hi);
+        const int last = !(dtc < dt - tau);
+        if (last) dtc = dt - tau;
+        y = (C * dtc + nHI) / (1.0 + D * dtc) / nH;
+        if (y > 1.0) y = 1.0;
+        tau = last ? dt : tau + dtc;
+        n++;
+    }
+    *y_out = y;
+    return n;
+}
+
+typedef struct {
+    double F;          /* Delta t = F min_i Delta t_chem,i (App. D) */
+    double eps_iter;   /* n_e convergence of the RT / chemistry iteration per step */
+    double eps_e, eps_hi;
+    double dt_fixed;   /* > 0: every step is dt_fixed instead */
+    int max_steps, max_iter, max_sub;
+} orc_evolve_opt;
+
+/* Photo-ionization rates g of state y: point sources (+ plane flux) over the
+ * bins and 4 pi G J^in from the sweep of the state's emissivity. */
+static void rates_of(const orc_sweep_cfg *cfg, const orc_chem *ch, const double *nH, const double *y,
+                     int nsrc, const double *pos, const double *qb, int nb, const double *sigma_b,
+                     int pl_axis, int pl_dir, double pl_flux, const double *fb, double G,
+                     double *kap, double *kapb, double *eps, double *jin, double *gpt, double *gpl, double *g)
+{
+    const long ncell = (long)cfg->nx * cfg->ny * cfg->nz;
+    orc_sweep_cfg c = *cfg;
+    c.field_form = 1;
+    const double dalpha = ch->alphaA - ch->alphaB;
+    for (long i = 0; i < ncell; i++) {
+        double nHI = y[i] * nH[i], ne = (1.0 - y[i]) * nH[i];
+        kap[i] = nHI * ch->sigma0 * ch->dx;
+        eps[i] = ch->h * ch->nu0 * dalpha * ne * ne * ch->dx / (4.0 * M_PI * ch->dnu);
+    }
+    orc_sweep(&c, kap, eps, jin, NULL);
+    for (int b = 0; b < nb; b++)
+        for (long i = 0; i < ncell; i++) kapb[b * ncell + i] = y[i] * nH[i] * sigma_b[b] * ch->dx;
+    orc_point_sources(cfg->nx, cfg->ny, cfg->nz, nb, kapb, sigma_b, nsrc, pos, qb, ch->dx, cfg->nthreads, gpt);
+    if (pl_flux > 0.0) {
+        orc_plane_source(cfg->nx, cfg->ny, cfg->nz, nb, kapb, sigma_b, pl_axis, pl_dir, fb, gpl);
+        for (long i = 0; i < ncell; i++) gpt[i] += gpl[i];
+    }
+    for (long i = 0; i < ncell; i++) g[i] = 4.0 * M_PI * G * jin[i] + gpt[i];
+}
+
+/* Evolve y from t = 0 to t_end in RT steps: the rates of the state at t
+ * give Delta t; then iterate {chemistry of every cell over Delta t from the
+ * state at t, at the rates of the current iterate; the rates of the new
+ * iterate} until max |n_e^(i) - n_e^(i-1)| / n_e^(i) < eps_iter (App. D).
+ * Returns 0 when t_end is reached with every step converged, 1 if an
+ * iteration hit max_iter (the last iterate is kept), 2 if max_steps ran out
+ * first, -1 on allocation failure. */
+int orc_evolve(const orc_sweep_cfg *cfg, const orc_chem *ch, const double *nH, int nsrc, const double *pos,
+               const double *Q, int nb, const double *sigma_b, const double *frac_b, int pl_axis, int pl_dir,
+               double pl_flux, const orc_evolve_opt *opt, double t_end, double *y, int *steps_out,
+               int *iters_out, double *t_out, double *dt_hist)
+{
+    const long ncell = (long)cfg->nx * cfg->ny * cfg->nz;
+    double *kap = malloc(sizeof(double) * ncell), *kapb = malloc(sizeof(double) * ncell * nb);
+    double *eps = malloc(sizeof(double) * ncell), *jin = malloc(sizeof(double) * ncell);
+    double *gpt = malloc(sizeof(double) * ncell), *gpl = malloc(sizeof(double) * ncell);
+    double *g = malloc(sizeof(double) * ncell), *yp = malloc(sizeof(double) * ncell);
+    double *yn = malloc(sizeof(double) * ncell);
+    double *qb = malloc(sizeof(double) * (nsrc > 0 ? nsrc : 1) * nb), *fb = malloc(sizeof(double) * nb);
+    if (!kap || !kapb || !eps || !jin || !gpt || !gpl || !g || !yp || !yn || !qb || !fb) return -1;
+    for (int a = 0; a < nsrc; a++)
+        for (int b = 0; b < nb; b++) qb[a * nb + b] = Q[a] * frac_b[b];
+    for (int b = 0; b < nb; b++) fb[b] = pl_flux * frac_b[b];
+    const double G = orc_band_integral(ch->sigma0, ch->h, ch->nu0, ch->nu0 + ch->dnu);
+    double t = 0.0;
+    int steps = 0, iters = 0, unconverged = 0;
+    while (t < t_end && steps < opt->max_steps) {
+        rates_of(cfg, ch, nH, y, nsrc, pos, qb, nb, sigma_b, pl_axis, pl_dir, pl_flux, fb, G, kap, kapb, eps,
+                 jin, gpt, gpl, g);
+        double dt;
+        if (opt->dt_fixed > 0.0) {
+            dt = opt->dt_fixed;
+        } else {
+            double m = INFINITY;
+            for (long i = 0; i < ncell; i++) {
+                const double d = dtchem_cell(nH[i], y[i], ch->alphaB, ch->gcoll, g[i], opt->eps_e, opt->eps_hi);
+                if (d < m) m = d;
+            }
+            dt = opt->F * m;
+        }
+        const int last = !(dt < t_end - t);
+        if (last) dt = t_end - t;
+        for (long i = 0; i < ncell; i++) yp[i] = y[i];
+        int conv = 0;
+        for (int k = 1; k <= opt->max_iter; k++) {
+            iters++;
+            double r = 0.0;
+            for (long i = 0; i < ncell; i++) {
+                chem_cell(nH[i], y[i], ch->alphaB, ch->gcoll, g[i], dt, opt->eps_e, opt->eps_hi, opt->max_sub,
+                          &yn[i]);
+                const double ne_new = (1.0 - yn[i]) * nH[i], ne_old = (1.0 - yp[i]) * nH[i];
+                const double ri = ne_new > 0.0 ? fabs(ne_new - ne_old) / ne_new : (ne_old > 0.0 ? INFINITY : 0.0);
+                if (ri > r) r = ri;
+            }
+            for (long i = 0; i < ncell; i++) yp[i] = yn[i];
+            if (r < opt->eps_iter) {
+                conv = 1;
+                break;
+            }
+            rates_of(cfg, ch, nH, yp, nsrc, pos, qb, nb, sigma_b, pl_axis, pl_dir, pl_flux, fb, G, kap, kapb,
+                     eps, jin, gpt, gpl, g);
+        }
+        if (!conv) unconverged = 1;
+        for (long i = 0; i < ncell; i++) y[i] = yp[i];
+        if (dt_hist) dt_hist[steps] = dt;
+        t = last ? t_end : t + dt;
+        steps++;
+    }
+    if (steps_out) *steps_out = steps;
+    if (iters_out) *iters_out = iters;
+    if (t_out) *t_out = t;
+    free(kap); free(kapb); free(eps); free(jin); free(gpt); free(gpl); free(g); free(yp); free(yn);
+    free(qb); free(fb);
+    if (t < t_end) return 2;
+    return unconverged ? 1 : 0;
 }

@@ -48,6 +48,18 @@ class ArtChem(C.Structure):
                 ("h", C.c_double), ("nu0", C.c_double), ("dnu", C.c_double)]
 
 
+class ArtEvolveOptions(C.Structure):
+    _fields_ = [("t_end", C.c_double), ("F", C.c_double), ("eps_iter", C.c_double), ("eps_e", C.c_double),
+                ("eps_hi", C.c_double), ("dt_fixed", C.c_double), ("max_steps", C.c_int), ("max_iter", C.c_int),
+                ("max_sub", C.c_int)]
+
+
+class ArtEvolveReport(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("iterations", C.c_int32), ("sweeps", C.c_int32), ("converged", C.c_int32),
+                ("sub_overflow", C.c_int64), ("t", C.c_double), ("dt_min", C.c_double), ("dt_max", C.c_double),
+                ("seconds", C.c_double)]
+
+
 class ArtSource(C.Structure):
     _fields_ = [("x", C.c_double), ("y", C.c_double), ("z", C.c_double), ("Q", C.c_double)]
 
@@ -127,6 +139,11 @@ def load() -> C.CDLL:
         lib.art_plane_source.restype = C.c_int
         lib.art_set_plane_source.argtypes = [P, C.c_int, C.c_int, C.c_double]
         lib.art_set_plane_source.restype = C.c_int
+        lib.art_evolve_options_default.argtypes = [C.POINTER(ArtEvolveOptions)]
+        lib.art_evolve_options_default.restype = C.c_int
+        lib.art_evolve_ionization.argtypes = [P, C.POINTER(ArtChem), P, C.POINTER(ArtSource), C.c_int,
+                                              C.POINTER(ArtEvolveOptions), P, C.POINTER(ArtEvolveReport), P]
+        lib.art_evolve_ionization.restype = C.c_int
         lib.art_sweep.argtypes = [P, P, P, P, C.c_int, P]
         lib.art_count_segments.argtypes = [C.POINTER(ArtGrid), C.c_int, C.c_double, C.POINTER(C.c_int64)]
         lib.art_band_integral.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_double)]
@@ -462,6 +479,29 @@ class ArtSweep:
     def set_plane_source(self, axis=0, direction=1, flux=0.0):
         """Plane-parallel incident flux of the iteration (photons/s/cm^2; 0 removes it)."""
         _check(self._ctx, load().art_set_plane_source(self._ctx, int(axis), int(direction), float(flux)))
+
+    def evolve(self, nH, chem: dict, sources, y, t_end, stream=None, **opts):
+        """Time-dependent mode (App. B-D) from t = 0 to t_end (s); nH, y: device FP64 [z][y][x], y updated
+        in place.  opts: F, eps_iter, eps_e, eps_hi, dt_fixed, max_steps, max_iter, max_sub.  Returns the
+        report; raises ArtError unless t_end was reached with every step converged."""
+        npp, nd_, _n = _ptr(nH, np.float64, self.ncell)
+        yp, yd, _y = _ptr(y, np.float64, self.ncell)
+        if not (nd_ and yd):
+            raise TypeError("evolve takes device buffers")
+        o = ArtEvolveOptions()
+        load().art_evolve_options_default(C.byref(o))
+        o.t_end = float(t_end)
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, type(getattr(o, k))(v))
+        src = _sources(sources)
+        rep = ArtEvolveReport()
+        ch = self._chem(chem)
+        st = load().art_evolve_ionization(self._ctx, C.byref(ch), C.c_void_p(npp), src, len(sources), C.byref(o),
+                                          C.c_void_p(yp), C.byref(rep), C.c_void_p(_stream(stream)))
+        _check(self._ctx, st)
+        return rep
 
     def iterate(self, nH, chem: dict, sources, y, tol=1e-6, max_iter=200, stream=None):
         """RT / balance iteration (App. D); nH, y: device FP64 [z][y][x]; y updated in place.

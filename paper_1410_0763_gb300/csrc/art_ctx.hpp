@@ -17,7 +17,9 @@ struct art_iter_bufs {
     float *gpt = nullptr, *kap = nullptr, *eps = nullptr, *jin = nullptr;
     float *jsur = nullptr;                                // surrogate J^in / prolonged J_c
     unsigned long long *resid = nullptr;
-    double *src = nullptr;                                // [nsrc][4]: x, y, z, Q
+    double *src = nullptr;                                // packed point sources
+    double *yit = nullptr;                                // time-dependent mode: the iterate at t + dt
+    unsigned long long *evo = nullptr;                    // [3]: residual, min dt_chem (double bits), overflows
 };
 
 // One grid of a context (a context holds one grid, or a batch of them).

@@ -744,6 +744,235 @@ art_status iterate_impl(art_ctx *ctx, art_net *net, const art_chem *ch, const do
     return conv ? ART_OK : art_fail(ctx, ART_E_NOT_CONVERGED, "art_iterate_ionization: max_iter reached");
 }
 
+// ---------------------------------------------------------------------------
+// Time-dependent mode (App. B-D), hydrogen at the fixed temperature of the
+// chemistry constants, FP64 per cell.  In one cell over dt at fixed rate g
+// the BDF step of App. B,
+//   n_HI <- (C dtc + n_HI) / (1 + D dtc),  C = alpha_B n_e n_HII,  D = Gamma_coll n_e + g,
+// takes C and D at the start of the sub-step (hydrogen is the lowest
+// ionization level, updated first) and is sub-cycled with the chemical
+// timestep of App. D, dtc = eps_e |n_e/n_e'| + eps_HI |n_HI/n_HI'|, the last
+// sub-step cut to end at dt.  alpha_B: the local recombination term of
+// Eq. (gamma_diff) cancels the ground-state recombinations, as in the
+// equilibrium balance; g = Gamma_point + Gamma^diff_in.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double dtchem_of(double nH, double y, double alphaB, double gcoll, double g,
+                                            double eps_e, double eps_hi)
+{
+    const double nHI = y * nH, ne = (1.0 - y) * nH;
+    const double dHI = alphaB * ne * ne - (gcoll * ne + g) * nHI;   // dn_HI/dt = -dn_e/dt
+    if (dHI == 0.0) return INFINITY;
+    return eps_e * fabs(ne / dHI) + eps_hi * fabs(nHI / dHI);
+}
+
+struct ChemArgs {
+    const double *nH;
+    const float *gpt, *gdiff;
+    const double *y_t;          // state at t
+    double *y;                  // in: previous iterate at t + dt; out: the new one
+    double alphaB, gcoll, dt, eps_e, eps_hi;
+    int max_sub;
+    long long ncell;
+    unsigned long long *evo;    // [0] max residual, [1] min dt_chem, [2] cells out of sub-steps (double bits / count)
+    int mode;                   // 0: min dt_chem of y_t; 1: chemistry over dt
+};
+
+__device__ __forceinline__ void block_reduce_bits(unsigned long long v, bool is_max, unsigned long long *dst)
+{
+    __shared__ unsigned long long sred[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = is_max ? (w > v ? w : v) : (w < v ? w : v);
+    }
+    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const unsigned long long id = is_max ? 0ull : ~0ull;
+        v = threadIdx.x < (blockDim.x >> 5) ? sred[threadIdx.x] : id;
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+            v = is_max ? (w > v ? w : v) : (w < v ? w : v);
+        }
+        if (threadIdx.x == 0) {
+            if (is_max) atomicMax(dst, v);
+            else atomicMin(dst, v);
+        }
+    }
+}
+
+// Non-negative doubles order like their bit patterns, so max / min reduce on the bits.
+__global__ void __launch_bounds__(256) chem_kernel(const ChemArgs p)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in = i < p.ncell;
+    if (p.mode == 0) {
+        double d = INFINITY;
+        if (in) d = dtchem_of(p.nH[i], p.y_t[i], p.alphaB, p.gcoll, (double)p.gpt[i] + (double)p.gdiff[i], p.eps_e,
+                              p.eps_hi);
+        block_reduce_bits((unsigned long long)__double_as_longlong(d), false, p.evo + 1);
+        return;
+    }
+    double r = 0.0;
+    if (in) {
+        const double nH = p.nH[i], g = (double)p.gpt[i] + (double)p.gdiff[i];
+        double y = p.y_t[i], tau = 0.0;
+        int n = 0;
+        while (tau < p.dt && n < p.max_sub) {
+            const double nHI = y * nH, ne = (1.0 - y) * nH;
+            const double C = p.alphaB * ne * ne, D = p.gcoll * ne + g;
+            double dtc = dtchem_of(nH, y, p.alphaB, p.gcoll, g, p.eps_e, p.eps_hi);
+            const bool last = !(dtc < p.dt - tau);
+            if (last) dtc = p.dt - tau;
+            y = fmin((C * dtc + nHI) / (1.0 + D * dtc) / nH, 1.0);
+            tau = last ? p.dt : tau + dtc;
+            ++n;
+        }
+        if (tau < p.dt) atomicAdd(p.evo + 2, 1ull);
+        const double ne_new = (1.0 - y) * nH, ne_old = (1.0 - p.y[i]) * nH;
+        r = ne_new > 0.0 ? fabs(ne_new - ne_old) / ne_new : (ne_old > 0.0 ? INFINITY : 0.0);
+        p.y[i] = y;
+    }
+    block_reduce_bits((unsigned long long)__double_as_longlong(r), true, p.evo);
+}
+
+art_status evolve_impl(art_ctx *ctx, const art_chem *ch, const double *nH, const art_source *src, int n_src,
+                       const art_evolve_options *o, double *y, art_evolve_report *rep, cudaStream_t st)
+{
+    if (!ctx) return ART_E_INVALID;
+    art_status s = check_iteration_context(ctx, ch, "art_evolve_ionization");
+    if (s != ART_OK) return s;
+    if (!nH || !y || !o || (n_src > 0 && !src) || n_src < 0 || !(o->t_end >= 0.0) || !std::isfinite(o->t_end) ||
+        !(o->F > 0.0) || !(o->eps_iter > 0.0) || !(o->eps_e >= 0.0) || !(o->eps_hi >= 0.0) ||
+        !(o->eps_e + o->eps_hi > 0.0) || !(o->dt_fixed >= 0.0) || o->max_steps < 1 || o->max_iter < 1 ||
+        o->max_sub < 1)
+        return art_fail(ctx, ART_E_INVALID, "art_evolve_ionization: bad argument");
+    const auto t0 = std::chrono::steady_clock::now();
+    const long long n = ctx->ncell;
+    art_iter_bufs &B = ctx->it;
+    if ((s = ensure(ctx, &B.gpt, n)) != ART_OK || (s = ensure(ctx, &B.kap, n)) != ART_OK ||
+        (s = ensure(ctx, &B.eps, n)) != ART_OK || (s = ensure(ctx, &B.jin, n)) != ART_OK ||
+        (s = ensure(ctx, &B.yit, n)) != ART_OK || (s = ensure(ctx, &B.evo, 3)) != ART_OK)
+        return s;
+    const int nbp = ctx->spec_bins > 0 ? ctx->spec_bins : 1;
+    std::vector<double> sig(nbp), frac(nbp);
+    std::vector<float> kscale(nbp);
+    for (int b = 0; b < nbp; ++b) {
+        sig[b] = ctx->spec_bins > 0 ? ctx->spec_sigma[b] : ch->sigma0;
+        frac[b] = ctx->spec_bins > 0 ? ctx->spec_frac[b] : 1.0;
+        kscale[b] = (float)(sig[b] / ch->sigma0);
+    }
+    double plane_coef[4] = {0, 0, 0, 0};
+    for (int b = 0; b < nbp; ++b) plane_coef[b] = ctx->plane_flux * frac[b] * sig[b];
+    std::vector<PtSrc> h_src;
+    if ((s = pack_sources(ctx, src, n_src, nullptr, frac.data(), sig.data(), nbp, h_src)) != ART_OK) return s;
+    if ((s = source_buffer(ctx, n_src)) != ART_OK) return s;
+    const PtSrc *d_src = reinterpret_cast<const PtSrc *>(B.src);
+    ICK(ctx, cudaMemcpyAsync(B.src, h_src.data(), h_src.size() * sizeof(PtSrc), cudaMemcpyHostToDevice, st));
+    const bool otsa = ch->alphaA == ch->alphaB;
+    if (otsa) ICK(ctx, cudaMemsetAsync(B.jin, 0, n * sizeof(float), st));
+    ICK(ctx, cudaMemsetAsync(B.evo, 0, 3 * sizeof(unsigned long long), st));
+
+    // photo-ionization rates of state ys into B.gpt (+ plane) and B.jin
+    int sweeps = 0;
+    auto rates = [&](double *ys) -> art_status {
+        BalArgs ba = balance_args(ctx, ch, nH, ys);
+        const int nt = 256;
+        balance_kernel<<<(unsigned)((n + nt - 1) / nt), nt, 0, st>>>(ba);   // kappa, eps of the state
+        ICK(ctx, cudaGetLastError());
+        art_status r = launch_points(ctx, B.kap, nbp, d_src, n_src, B.gpt, st, kscale.data());
+        if (r != ART_OK) return r;
+        if (ctx->plane_flux > 0.0 &&
+            (r = launch_plane(ctx, B.kap, nbp, ctx->plane_axis, ctx->plane_dir, plane_coef, B.gpt, 1, st,
+                              kscale.data())) != ART_OK)
+            return r;
+        if (!otsa) {
+            if ((r = art_internal_layout(ctx, B.kap, B.eps, st)) != ART_OK) return r;
+            if ((r = art_internal_sweep(ctx, nullptr, B.jin, nullptr, st)) != ART_OK) return r;
+            ++sweeps;
+        }
+        return ART_OK;
+    };
+    ChemArgs ca;
+    ca.nH = nH;
+    ca.gpt = B.gpt;
+    ca.gdiff = B.jin;
+    ca.y_t = y;
+    ca.y = B.yit;
+    ca.alphaB = ch->alphaB;
+    ca.gcoll = ch->gcoll;
+    ca.eps_e = o->eps_e;
+    ca.eps_hi = o->eps_hi;
+    ca.max_sub = o->max_sub;
+    ca.ncell = n;
+    ca.evo = B.evo;
+    const int nt = 256;
+    const unsigned nb = (unsigned)((n + nt - 1) / nt);
+    double t = 0.0, dt_min = INFINITY, dt_max = 0.0;
+    int steps = 0, iters = 0, unconverged = 0;
+    unsigned long long overflow = 0;
+    while (t < o->t_end && steps < o->max_steps) {
+        if ((s = rates(y)) != ART_OK) return s;
+        double dt = o->dt_fixed;
+        if (!(dt > 0.0)) {
+            const unsigned long long inf_bits = 0x7ff0000000000000ull;
+            ICK(ctx, cudaMemcpyAsync(B.evo + 1, &inf_bits, sizeof(inf_bits), cudaMemcpyHostToDevice, st));
+            ca.mode = 0;
+            chem_kernel<<<nb, nt, 0, st>>>(ca);
+            ICK(ctx, cudaGetLastError());
+            unsigned long long bits = 0;
+            ICK(ctx, cudaMemcpyAsync(&bits, B.evo + 1, sizeof(bits), cudaMemcpyDeviceToHost, st));
+            ICK(ctx, cudaStreamSynchronize(st));
+            double m;
+            std::memcpy(&m, &bits, sizeof(m));
+            dt = o->F * m;
+        }
+        const bool last = !(dt < o->t_end - t);
+        if (last) dt = o->t_end - t;
+        ca.dt = dt;
+        ca.mode = 1;
+        ICK(ctx, cudaMemcpyAsync(B.yit, y, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        int conv = 0;
+        for (int k = 1; k <= o->max_iter; ++k) {
+            ++iters;
+            ICK(ctx, cudaMemsetAsync(B.evo, 0, sizeof(unsigned long long), st));
+            chem_kernel<<<nb, nt, 0, st>>>(ca);
+            ICK(ctx, cudaGetLastError());
+            unsigned long long bits = 0;
+            ICK(ctx, cudaMemcpyAsync(&bits, B.evo, sizeof(bits), cudaMemcpyDeviceToHost, st));
+            ICK(ctx, cudaStreamSynchronize(st));
+            double r;
+            std::memcpy(&r, &bits, sizeof(r));
+            if (r < o->eps_iter) {
+                conv = 1;
+                break;
+            }
+            if ((s = rates(B.yit)) != ART_OK) return s;
+        }
+        if (!conv) unconverged = 1;
+        ICK(ctx, cudaMemcpyAsync(y, B.yit, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        dt_min = std::min(dt_min, dt);
+        dt_max = std::max(dt_max, dt);
+        t = last ? o->t_end : t + dt;
+        ++steps;
+    }
+    ICK(ctx, cudaMemcpyAsync(&overflow, B.evo + 2, sizeof(overflow), cudaMemcpyDeviceToHost, st));
+    ICK(ctx, cudaStreamSynchronize(st));
+    if (rep) {
+        rep->steps = steps;
+        rep->iterations = iters;
+        rep->sweeps = sweeps;
+        rep->converged = !unconverged;
+        rep->sub_overflow = (long long)overflow;
+        rep->t = t;
+        rep->dt_min = steps ? dt_min : 0.0;
+        rep->dt_max = dt_max;
+        rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (t < o->t_end) return art_fail(ctx, ART_E_NOT_CONVERGED, "art_evolve_ionization: max_steps before t_end");
+    if (unconverged) return art_fail(ctx, ART_E_NOT_CONVERGED, "art_evolve_ionization: a step reached max_iter");
+    return ART_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -754,6 +983,28 @@ art_status art_iterate_ionization(art_ctx *ctx, const art_chem *ch, const double
 {
     return iterate_impl(ctx, nullptr, ch, nH, src, n_src, tol, max_iter, nullptr, y, resid_hist, rep, nullptr,
                         static_cast<cudaStream_t>(stream));
+}
+
+art_status art_evolve_options_default(art_evolve_options *o)
+{
+    if (!o) return ART_E_INVALID;
+    o->t_end = 0.0;
+    o->F = 10.0;
+    o->eps_iter = 1e-3;
+    o->eps_e = 0.2;
+    o->eps_hi = 0.002;
+    o->dt_fixed = 0.0;
+    o->max_steps = 100000;
+    o->max_iter = 100;
+    o->max_sub = 1000000;
+    return ART_OK;
+}
+
+art_status art_evolve_ionization(art_ctx *ctx, const art_chem *ch, const double *nH, const art_source *src,
+                                 int n_src, const art_evolve_options *opt, double *y, art_evolve_report *rep,
+                                 void *stream)
+{
+    return evolve_impl(ctx, ch, nH, src, n_src, opt, y, rep, static_cast<cudaStream_t>(stream));
 }
 
 art_status art_set_plane_source(art_ctx *ctx, int axis, int dir, double flux)
