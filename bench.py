@@ -510,6 +510,49 @@ def evolve_measure(torch, dev, F=1.0):
     return out
 
 
+def ablation_measure(torch, dev, reps=3):
+    """The paper's ray-grouping comparison (Sec. 5) restated on GB300: the
+    thread-per-ray layout of Sec. 3.1 with float atomics against the same
+    layout with the four ray groups, both CUDA-graph replays of one launch
+    (atomics) or four (groups) per direction, and the production tiled sweep,
+    on the GRF workloads.  Milliseconds per sweep, best of reps after a
+    warm-up."""
+    from paper_1410_0763_gb300 import art
+    from paper_1410_0763_gb300 import workloads as wl
+    out = {"note": "benchmark only; the paper reports grouping > 2x faster than atomics on its GPUs"}
+    for name, n, nside in (("grf64", 64, 4), ("grf128", 128, 8)):
+        c = wl.grf(n, nside)
+        k = torch.as_tensor(c.kappa, dtype=torch.float32, device=dev)
+        s = torch.as_tensor(c.src, dtype=torch.float32, device=dev)
+        sw = art.ArtSweep(k.shape, nside, 1, graph=True)
+        sw.set_fields(k, s)
+        j = torch.empty_like(k)
+
+        def best(fn):
+            fn()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return min(ts)
+        t_atomic = best(lambda: sw.ablation_sweep(0, j))
+        t_group = best(lambda: sw.ablation_sweep(1, j))
+        t_tiled = best(lambda: sw.sweep(J_in=j))
+        segs = sw.stats.segments
+        out[name] = {"ms_atomic": round(t_atomic, 3), "ms_ray_groups": round(t_group, 3),
+                     "ms_tiled_sweep": round(t_tiled, 3), "groups_over_atomic_speedup": round(t_atomic / t_group, 3),
+                     "tiled_over_groups_speedup": round(t_group / t_tiled, 3),
+                     "gseg_per_s": {"atomic": round(segs / t_atomic / 1e6, 1), "ray_groups": round(segs / t_group / 1e6, 1),
+                                    "tiled": round(segs / t_tiled / 1e6, 1)}}
+        sw.close()
+    return out
+
+
 def cpu_baseline(case, seg_per_sweep: int, budget_s: float = 12.0) -> dict:
     import oracle
     oracle.build()
@@ -640,6 +683,10 @@ def run_ours(args, d: Dist):
             extra["time_dependent_64"] = evolve_measure(torch, dev)
         except Exception as ex:  # pragma: no cover
             extra["time_dependent_64"] = {"error": str(ex)}
+        try:
+            extra["ablation_ray_grouping"] = ablation_measure(torch, dev)
+        except Exception as ex:  # pragma: no cover
+            extra["ablation_ray_grouping"] = {"error": str(ex)}
 
     cpu = None
     if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:

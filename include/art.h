@@ -194,6 +194,24 @@ art_status art_set_fields(art_ctx *ctx, const void *kappa, const void *src, int 
 art_status art_set_band(art_ctx *ctx, const double *G);
 
 /*
+ * The straightforward layout of Sec. 3.1, kept to measure the ray grouping
+ * (benchmark only): one thread per light-ray of a direction marches the whole
+ * box and deposits (|n_a| / N_d) ds Ibar_in into J_in of every cell it
+ * crosses (the same per-segment arithmetic and geometry as art_sweep).
+ * Rays of one direction share cells, so mode 0 makes one launch per
+ * direction with float atomicAdd deposits (results vary in the last bits
+ * with the order of the atomics), and mode 1 four launches per direction,
+ * one per ray group of starting columns (j mod 2, k mod 2), which visit no
+ * cell twice, with plain read-modify-write deposits.  Directions run one
+ * after another; the launches are captured once as a CUDA graph (per mode
+ * and output pointer) and replayed on an internal stream ordered with
+ * `stream`.  J_in: device [z][y][x] floats, overwritten with J^in.  Single
+ * grid, FP32, one bin, ART_FIELDS_S, all directions, vacuum boundary, after
+ * art_set_fields.  Errors: ART_E_INVALID, ART_E_STATE, ART_E_CUDA.
+ */
+art_status art_ablation_sweep(art_ctx *ctx, int mode, float *J_in, void *stream);
+
+/*
  * Boundary intensity of the diffuse sweep: every ray of every direction
  * enters the box with intensity I_bc[b] in bin b (isotropic, uniform over the
  * faces), instead of the vacuum boundary I = 0 of Eq. (rad_tr2) with

@@ -139,6 +139,8 @@ def load() -> C.CDLL:
         lib.art_plane_source.restype = C.c_int
         lib.art_set_plane_source.argtypes = [P, C.c_int, C.c_int, C.c_double]
         lib.art_set_plane_source.restype = C.c_int
+        lib.art_ablation_sweep.argtypes = [P, C.c_int, P, P]
+        lib.art_ablation_sweep.restype = C.c_int
         lib.art_evolve_options_default.argtypes = [C.POINTER(ArtEvolveOptions)]
         lib.art_evolve_options_default.restype = C.c_int
         lib.art_evolve_ionization.argtypes = [P, C.POINTER(ArtChem), P, C.POINTER(ArtSource), C.c_int,
@@ -613,6 +615,15 @@ class ArtSweep:
         if len(G) != self.nbins:
             raise ValueError("one band integral per bin")
         _check(self._ctx, art_set_band(self._ctx, G))
+
+    def ablation_sweep(self, mode, J_in, stream=None):
+        """Thread-per-ray sweep of Sec. 3.1 into J_in (device FP32): mode 0 float atomics, mode 1 the
+        paper's four ray groups (benchmark only)."""
+        jp, jd, _j = _ptr(J_in, np.float32, self.ncell)
+        if not jd:
+            raise TypeError("ablation_sweep takes a device buffer")
+        _check(self._ctx, load().art_ablation_sweep(self._ctx, int(mode), C.c_void_p(jp), C.c_void_p(_stream(stream))))
+        return J_in
 
     def set_boundary_intensity(self, I_bc):
         """Intensity of every ray entering the box, one value per bin (None: vacuum)."""

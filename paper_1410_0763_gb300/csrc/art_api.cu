@@ -797,6 +797,7 @@ art_status art_destroy(art_ctx *ctx)
     void *sur[] = {ctx->sur.kc, ctx->sur.ec, ctx->sur.jc, ctx->sur.o, ctx->sur.eref, ctx->sur.nHc, ctx->sur.yc};
     for (void *p : sur)
         if (p) cudaFree(p);
+    art_internal_ablation_free(ctx);
     if (ctx->coarse) art_destroy(ctx->coarse);
     delete ctx;
     return ART_OK;

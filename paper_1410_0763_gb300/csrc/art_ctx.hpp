@@ -93,11 +93,13 @@ struct art_ctx {
     int plane_axis = 0, plane_dir = 1;   // plane-parallel incident flux of the iteration
     double plane_flux = 0.0;             // photons/s/cm^2 (0: none)
     art_ctx *coarse = nullptr;  // coarse-mesh sweep of the surrogate
+    void *ablation = nullptr;   // thread-per-ray comparison sweep (tables, graphs)
     art_sur_bufs sur;
 };
 
 
 // internal entry points shared by the translation units of libart
 art_status art_fail(art_ctx *ctx, art_status st, const std::string &msg);
+void art_internal_ablation_free(art_ctx *ctx);
 art_status art_internal_sweep(art_ctx *ctx, void *J, void *J_in, void *gamma, cudaStream_t st);
 art_status art_internal_layout(art_ctx *ctx, const void *kappa, const void *src, cudaStream_t st);

@@ -1,0 +1,53 @@
+"""The thread-per-ray layout of Sec. 3.1 (benchmark only) computes the same
+J^in as the oracle and the production sweep, with float atomics (mode 0) and
+with the paper's four ray groups (mode 1, deterministic: no cell is visited
+twice within a group, so plain read-modify-write deposits are race-free)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1410_0763_gb300 import art, build
+from paper_1410_0763_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    art.load()
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)))
+
+
+@pytest.mark.parametrize("shape,nside", [((21, 26, 37), 2), ((32, 32, 32), 4)])
+def test_thread_per_ray_sweeps_match_oracle(orc, shape, nside):
+    rng = np.random.default_rng(51)
+    kap = (0.5 * np.exp(rng.standard_normal(shape))).astype(np.float32)
+    S = rng.random(shape).astype(np.float32)
+    want, _, _ = orc.sweep(kap.astype(np.float64), S.astype(np.float64), nside)
+    k = torch.as_tensor(kap, device="cuda")
+    s = torch.as_tensor(S, device="cuda")
+    sw = art.ArtSweep(shape, nside, 1)
+    sw.set_fields(k, s)
+    prod = torch.empty_like(k)
+    sw.sweep(J_in=prod)
+    out = {}
+    for mode in (0, 1):
+        runs = []
+        for _ in range(2):
+            j = torch.empty_like(k)
+            sw.ablation_sweep(mode, j)
+            torch.cuda.synchronize()
+            runs.append(j.cpu().numpy().astype(np.float64))
+        out[mode] = runs
+        assert rel(runs[0], want) < 1e-5
+    sw.close()
+    assert np.array_equal(out[1][0], out[1][1])          # grouped: deterministic
+    assert rel(out[0][0], out[1][0]) < 1e-5
+    assert rel(prod.cpu().numpy().astype(np.float64), out[1][0]) < 1e-5
