@@ -170,14 +170,15 @@ typedef struct {
     double judge_tol;      /* fall back when sum|J_s - J|/sum J exceeds this, default 0.3 */
     int coarse_solve;      /* 1 (default): start from the coarse-mesh solution (see below) */
     double coarse_tol;     /* residual of the coarse-mesh solve, default 1e-4 */
+    int judge_after;       /* also judge after this many surrogate iterations, default 2; 0: only at the end */
 } art_warm_options;
 
 typedef struct {
     art_iter_report total;        /* all iterations, as art_iterate_ionization */
     int32_t surrogate_iterations; /* iterations that took J^in from the surrogate */
     int32_t plain_sweeps;         /* full sweeps run (judge included) */
-    int32_t fell_back;            /* 1 if the judge restarted from the initial state */
-    double judge_error;           /* sum|J_s - J| / sum J at the end of the surrogate phase */
+    int32_t fell_back;            /* 1 if a judge restarted from the fallback state */
+    double judge_error;           /* sum|J_s - J| / sum J at the last judge */
     int32_t coarse_iterations;    /* iterations of the coarse-mesh solve */
 } art_warm_report;
 
@@ -193,9 +194,12 @@ art_status art_warm_options_default(art_warm_options *opt);
  * (injection).  Then, while the residual is above phase1_tol (and for at
  * most phase1_max_iter iterations), J^in comes from the surrogate (coarse
  * sweep of the current state, corrected by the network when use_net) instead
- * of the full sweep; one full sweep then judges the surrogate on the current
- * state; if its error exceeds judge_tol the state is reset to the initial y
- * (fell_back = 1); plain iterations run to tol.  net may be NULL only with
+ * of the full sweep.  One full sweep judges the surrogate on the current
+ * state after judge_after surrogate iterations and again when the phase
+ * ends; its exact J^in serves the next iteration.  If a judge's error
+ * exceeds judge_tol the state is reset to the fallback state -- the
+ * coarse-mesh start, or the caller's y without coarse_solve -- and
+ * (fell_back = 1) plain iterations run to tol from there.  net may be NULL only with
  * use_net = 0.  Under the on-the-spot approximation (alpha_A == alpha_B)
  * there is no diffuse field: only the coarse-mesh solve runs before the
  * plain iterations.  Errors as art_iterate_ionization.

@@ -82,7 +82,7 @@ class ArtNetOptions(C.Structure):
 class ArtWarmOptions(C.Structure):
     _fields_ = [("coarse_factor", C.c_int), ("coarse_nside", C.c_int), ("use_net", C.c_int),
                 ("phase1_max_iter", C.c_int), ("phase1_tol", C.c_double), ("judge_tol", C.c_double),
-                ("coarse_solve", C.c_int), ("coarse_tol", C.c_double)]
+                ("coarse_solve", C.c_int), ("coarse_tol", C.c_double), ("judge_after", C.c_int)]
 
 
 class ArtWarmReport(C.Structure):
@@ -542,7 +542,7 @@ class ArtSweep:
 
     def iterate_warm(self, net, nH, chem: dict, sources, y, tol=1e-6, max_iter=200, coarse_factor=4,
                      coarse_nside=4, use_net=True, phase1_max_iter=40, phase1_tol=1e-3, judge_tol=0.3,
-                     coarse_solve=True, coarse_tol=1e-4, stream=None):
+                     coarse_solve=True, coarse_tol=1e-4, judge_after=2, stream=None):
         """The iteration of `iterate`, warm-started by the surrogate (coarse sweep + network).
         Returns (warm report, residual history); raises ArtError unless converged."""
         npp, nd_, _n = _ptr(nH, np.float64, self.ncell)
@@ -554,6 +554,7 @@ class ArtSweep:
         w.coarse_factor, w.coarse_nside, w.use_net = int(coarse_factor), int(coarse_nside), 1 if use_net else 0
         w.phase1_max_iter, w.phase1_tol, w.judge_tol = int(phase1_max_iter), float(phase1_tol), float(judge_tol)
         w.coarse_solve, w.coarse_tol = 1 if coarse_solve else 0, float(coarse_tol)
+        w.judge_after = int(judge_after)
         src = _sources(sources)
         hist = (C.c_double * max_iter)()
         rep = ArtWarmReport()

@@ -612,7 +612,6 @@ art_status iterate_impl(art_ctx *ctx, art_net *net, const art_chem *ch, const do
 
     const int nt = 256;
     const unsigned nb = (unsigned)((n + nt - 1) / nt);
-    if (warm) ICK(ctx, cudaMemcpyAsync(B.y0, y, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     int coarse_it = 0;
     if (warm && warm->coarse_solve) {
         // the whole problem on the coarse mesh; its neutral fraction starts the fine iteration
@@ -646,6 +645,8 @@ art_status iterate_impl(art_ctx *ctx, art_net *net, const art_chem *ch, const do
         inject_d_kernel<<<nb, nt, 0, st>>>(S.yc, ctx->grid.nx, ctx->grid.ny, ctx->grid.nz, f, y);
         ICK(ctx, cudaGetLastError());
     }
+    // the state a failed judge falls back to: the coarse-mesh start (or the caller's y)
+    if (warm) ICK(ctx, cudaMemcpyAsync(B.y0, y, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     BalArgs ba = balance_args(ctx, ch, nH, y);
     balance_kernel<<<nb, nt, 0, st>>>(ba);   // kappa, eps of the starting state
     ICK(ctx, cudaGetLastError());
@@ -657,7 +658,7 @@ art_status iterate_impl(art_ctx *ctx, art_net *net, const art_chem *ch, const do
     const bool otsa = ch->alphaA == ch->alphaB;
     if (otsa) ICK(ctx, cudaMemsetAsync(B.jin, 0, n * sizeof(float), st));
     bool phase1 = !otsa && warm != nullptr && warm->phase1_max_iter > 0;
-    bool have_jin = false;
+    bool have_jin = false, judged_early = false;
     int it = 0, conv = 0, it1 = 0, sweeps = 0, fell_back = 0;
     double r = 0.0, judge = 0.0;
     for (it = 1; it <= max_iter; ++it) {
@@ -704,7 +705,10 @@ art_status iterate_impl(art_ctx *ctx, art_net *net, const art_chem *ch, const do
             conv = 1;
             break;
         }
-        if (phase1 && (r < warm->phase1_tol || it1 >= warm->phase1_max_iter)) {
+        const bool end_phase = phase1 && (r < warm->phase1_tol || it1 >= warm->phase1_max_iter);
+        const bool early = phase1 && !end_phase && !judged_early && warm->judge_after > 0 &&
+                           it1 == warm->judge_after;
+        if (end_phase || early) {
             // judge the surrogate against a full sweep on the current state
             if (warm->use_net && (s = artnet_check(net, st)) != ART_OK)
                 return art_fail(ctx, s, std::string("surrogate network: ") + artnet_error(net));
@@ -715,8 +719,8 @@ art_status iterate_impl(art_ctx *ctx, art_net *net, const art_chem *ch, const do
             if ((s = art_internal_sweep(ctx, nullptr, B.jin, nullptr, st)) != ART_OK) return s;
             ++sweeps;
             if ((s = artnet_l1(ctx, B.jsur, B.jin, &judge, st)) != ART_OK) return s;
-            phase1 = false;
             if (!(judge <= warm->judge_tol)) {
+                phase1 = false;
                 fell_back = 1;
                 ICK(ctx, cudaMemcpyAsync(y, B.y0, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
                 ba.solve = 0;
@@ -724,7 +728,9 @@ art_status iterate_impl(art_ctx *ctx, art_net *net, const art_chem *ch, const do
                 ICK(ctx, cudaGetLastError());
                 ba.solve = 1;
             } else {
-                have_jin = true;
+                have_jin = true;   // the next iteration takes the judge's exact J^in
+                if (end_phase) phase1 = false;
+                if (early) judged_early = true;
             }
         }
     }
@@ -1069,6 +1075,7 @@ art_status art_warm_options_default(art_warm_options *o)
     o->judge_tol = 0.3;
     o->coarse_solve = 1;
     o->coarse_tol = 1e-4;
+    o->judge_after = 2;
     return ART_OK;
 }
 
@@ -1082,7 +1089,8 @@ art_status art_iterate_ionization_warm(art_ctx *ctx, art_net *net, const art_che
     if (wopt) w = *wopt;
     else art_warm_options_default(&w);
     if (w.coarse_factor < 1 || w.coarse_nside < 1 || w.phase1_max_iter < 0 || !(w.phase1_tol > 0.0) ||
-        !(w.judge_tol >= 0.0) || (w.use_net && !net) || (w.coarse_solve && !(w.coarse_tol > 0.0)))
+        !(w.judge_tol >= 0.0) || (w.use_net && !net) || (w.coarse_solve && !(w.coarse_tol > 0.0)) ||
+        w.judge_after < 0)
         return art_fail(ctx, ART_E_INVALID, "art_iterate_ionization_warm: bad warm-start options");
     art_iter_report r{};
     art_status s = iterate_impl(ctx, net, ch, nH, src, n_src, tol, max_iter, &w, y, resid_hist, &r, rep,

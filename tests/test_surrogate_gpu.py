@@ -91,7 +91,7 @@ def test_warm_start_reaches_the_plain_fixed_point(mode):
     net = art.ArtNet(dilation=(1, 2, 2, 1)) if mode == "net" else None
     kw = dict(coarse_factor=4, coarse_nside=1, use_net=(mode == "net"))
     if mode == "fallback":
-        kw["judge_tol"] = 0.0          # any judge error restarts from the initial state
+        kw["judge_tol"] = 0.0          # the early judge fails: restart from the coarse-mesh start
     if mode == "net":
         kw["judge_tol"] = 10.0         # an untrained network: keep its state whatever its error
     if mode == "coarse_solve_only":
@@ -106,6 +106,8 @@ def test_warm_start_reaches_the_plain_fixed_point(mode):
     else:
         assert rep.surrogate_iterations >= 1 and rep.judge_error > 0
     assert rep.fell_back == (1 if mode == "fallback" else 0)
+    if mode == "fallback":
+        assert rep.surrogate_iterations <= 2          # judged by judge_after = 2 surrogate iterations at the latest
     assert rep.plain_sweeps <= rep.total.iterations
     # both stop at a residual below 1e-6 of the same fixed point
     assert np.max(np.abs(yw - y_plain) / y_plain) < 1e-4
