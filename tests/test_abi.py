@@ -79,6 +79,17 @@ def test_bad_direction_shards_are_rejected_without_touching_the_gpu(lib, rng):
 def test_null_context_calls_fail_cleanly(lib):
     assert lib.art_sweep(None, None, None, None, 1, None) == art.ART_E_INVALID
     assert lib.art_set_fields(None, None, None, 0, None) == art.ART_E_INVALID
+    assert lib.art_set_boundary_intensity(None, None) == art.ART_E_INVALID
+    assert lib.art_plane_source(None, None, None, 0, 1, None, None, None) == art.ART_E_INVALID
+    assert lib.art_set_plane_source(None, 0, 1, 1.0) == art.ART_E_INVALID
+    assert lib.art_evolve_ionization(None, None, None, None, 0, None, None, None, None) == art.ART_E_INVALID
+    assert lib.art_evolve_options_default(None) == art.ART_E_INVALID
+    assert lib.art_ablation_sweep(None, 0, None, None) == art.ART_E_INVALID
+    o = art.ArtEvolveOptions()
+    assert lib.art_evolve_options_default(ctypes.byref(o)) == art.ART_OK
+    assert (o.F, o.eps_iter, o.eps_e, o.eps_hi, o.dt_fixed) == (10.0, 1e-3, 0.2, 0.002, 0.0)
+    w = art.ArtWarmOptions()
+    assert lib.art_warm_options_default(ctypes.byref(w)) == art.ART_OK and w.judge_after == 2
     assert lib.art_destroy(None) == art.ART_OK
     assert lib.art_last_error(None) == b"null context"
 

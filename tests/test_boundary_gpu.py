@@ -173,3 +173,29 @@ def test_iteration_lit_by_a_plane_flux_with_bins_matches_oracle(orc):
     assert conv and rep.converged and abs(rep.iterations - it_o) <= _iteration_slack(hist_o)
     assert rel(y, y_o) < 1e-4
     assert rel(1 - y, 1 - y_o) < 1e-4
+
+
+def test_invalid_arguments_are_rejected():
+    shape = (8, 9, 10)
+    sw = art.ArtSweep(shape, 1, 1, dx_cm=1e20)
+    k = torch.zeros(shape, dtype=torch.float32, device="cuda")
+    g = torch.empty_like(k)
+    for axis, direction, flux in ((3, 1, [1e6]), (0, 0, [1e6]), (0, 1, [-1.0]), (1, -1, [float("nan")])):
+        with pytest.raises(art.ArtError) as ex:
+            sw.plane_source(k, [6.3e-18], axis, direction, flux, g)
+        assert ex.value.status == art.ART_E_INVALID
+    for bad in ([-1.0], [float("inf")]):
+        with pytest.raises(art.ArtError):
+            sw.set_boundary_intensity(bad)
+    with pytest.raises(art.ArtError):
+        sw.set_plane_source(0, 2, 1e6)
+    with pytest.raises(art.ArtError):
+        sw.ablation_sweep(0, g)            # no fields yet
+    sw.close()
+    sw = art.ArtSweep(shape, 1, 1, precision="fp64")
+    sw.set_fields(torch.zeros(shape, dtype=torch.float64, device="cuda"),
+                  torch.zeros(shape, dtype=torch.float64, device="cuda"))
+    with pytest.raises(art.ArtError) as ex:
+        sw.ablation_sweep(1, g)            # FP32 contexts only
+    assert ex.value.status == art.ART_E_INVALID
+    sw.close()

@@ -141,3 +141,22 @@ def test_long_evolution_reaches_the_equilibrium():
     assert rel(a, b) < 1e-3
     assert rel(1 - a, 1 - b) < 1e-3
     sw.close()
+
+
+def test_invalid_options_are_rejected():
+    case = wl.hii_region(n=8, nside=1, box_kpc=1.6)
+    sw = _ctx(case)
+    nH, y = _dev(case.nH), _dev(case.y0)
+    for kw in (dict(F=0.0), dict(eps_iter=0.0), dict(eps_e=0.0, eps_hi=0.0), dict(max_steps=0),
+               dict(dt_fixed=-1.0)):
+        with pytest.raises(art.ArtError) as ex:
+            sw.evolve(nH, case.chem, _srcs(case), y, 1e12, **kw)
+        assert ex.value.status == art.ART_E_INVALID
+    with pytest.raises(art.ArtError) as ex:
+        sw.evolve(nH, case.chem, _srcs(case), y, float("inf"))
+    assert ex.value.status == art.ART_E_INVALID
+    # too few steps for t_end: not converged, y holds the state reached
+    with pytest.raises(art.ArtError) as ex:
+        sw.evolve(nH, case.chem, _srcs(case), y, 1e20, max_steps=2)
+    assert ex.value.status == art.ART_E_NOT_CONVERGED
+    sw.close()
