@@ -49,8 +49,13 @@ typedef enum {
 
 enum { ART_FP32 = 0, ART_FP64 = 1 };
 /* ART_AVG_PAPER: Eq. (path_averaged_intensity): the cell average of the
- * incoming intensity, J = J^in + S (Eq. mean_intensity). */
-enum { ART_AVG_PAPER = 0 };
+ * incoming intensity, J = J^in + S (Eq. mean_intensity).
+ * ART_AVG_EXACT: the exact path average of I over each segment,
+ * S + (I_in - S) phi(dtau), in place of the paper's I_in phi + S, which
+ * counts the local emission as absorbed locally and also propagates it.
+ * J = S + (1/N_d) sum_n <(I_in - S) phi> and J^in = J - S (with emissivity
+ * inputs, J^in = J where kappa = 0).  Gamma stays 4 pi sum_b G_b J^in_b. */
+enum { ART_AVG_PAPER = 0, ART_AVG_EXACT = 1 };
 /* ART_FIELDS_S: inputs are (kappa, S), Eq. (rt).  ART_FIELDS_EPS: inputs are
  * (kappa, eps) with eps the emissivity times the cell width (S = eps/kappa);
  * kappa = 0 is then allowed and the transfer step adds eps * ds. */
@@ -63,7 +68,7 @@ typedef struct {
 
 typedef struct {
     int precision;    /* ART_FP32 (default) or ART_FP64 */
-    int averaging;    /* ART_AVG_PAPER */
+    int averaging;    /* ART_AVG_PAPER (default) or ART_AVG_EXACT */
     int field_form;   /* ART_FIELDS_S (default) or ART_FIELDS_EPS */
     int tile_b;       /* ray-plane tile along the fastest transverse axis; 0 = auto */
     int tile_c;       /* ray-plane tile along the other transverse axis;  0 = auto */

@@ -46,7 +46,7 @@ def build(force: bool = False) -> str:
 class SweepCfg(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("nside", C.c_int),
                 ("tie_tol", C.c_double), ("field_form", C.c_int), ("nthreads", C.c_int),
-                ("i_bc", C.c_double)]
+                ("i_bc", C.c_double), ("averaging", C.c_int)]
 
 
 class Chem(C.Structure):
@@ -116,10 +116,10 @@ def default_threads() -> int:
     return max(1, min(os.cpu_count() or 1, 64))
 
 
-def _cfg(shape, nside, field_form=0, tie_tol=1e-12, nthreads=None, i_bc=0.0) -> SweepCfg:
+def _cfg(shape, nside, field_form=0, tie_tol=1e-12, nthreads=None, i_bc=0.0, averaging=0) -> SweepCfg:
     nz, ny, nx = shape
     return SweepCfg(nx, ny, nz, nside, tie_tol, int(field_form),
-                    default_threads() if nthreads is None else int(nthreads), float(i_bc))
+                    default_threads() if nthreads is None else int(nthreads), float(i_bc), int(averaging))
 
 
 def n_dirs(nside: int) -> int:
@@ -134,13 +134,14 @@ def healpix_dirs(nside: int) -> np.ndarray:
     return out
 
 
-def sweep(kappa, src, nside, field_form=0, tie_tol=1e-12, nthreads=None, i_bc=0.0):
+def sweep(kappa, src, nside, field_form=0, tie_tol=1e-12, nthreads=None, i_bc=0.0, averaging=0):
     """Full sweep (Sec. 2.2).  kappa, src: [z][y][x]; i_bc: intensity of every ray
-    entering the box (0: vacuum).  Returns (J_in, J, n_w_zero)."""
+    entering the box (0: vacuum); averaging 0: the paper's cell average, 1: the
+    exact path average.  Returns (J_in, J, n_w_zero)."""
     k, s = _f64(kappa), _f64(src)
     jin = np.empty_like(k)
     j = np.empty_like(k)
-    cfg = _cfg(k.shape, nside, field_form, tie_tol, nthreads, i_bc)
+    cfg = _cfg(k.shape, nside, field_form, tie_tol, nthreads, i_bc, averaging)
     nz = _lib_handle().orc_sweep(C.byref(cfg), _dp(k), _dp(s), _dp(jin), _dp(j))
     if nz < 0:
         raise MemoryError("oracle sweep: allocation failed")
@@ -171,12 +172,12 @@ def sweep_range_count(kappa, src, nside, d0, d1, field_form=0, tie_tol=1e-12, nt
     return acc, int(n.value)
 
 
-def sweep_dir(kappa, src, nside, d, field_form=0, tie_tol=1e-12, i_bc=0.0):
-    """Per-cell A (sum ds*Ibar_in) and W (sum ds) of one direction."""
+def sweep_dir(kappa, src, nside, d, field_form=0, tie_tol=1e-12, i_bc=0.0, averaging=0):
+    """Per-cell A (sum ds*Ibar_in, or the exact average's deposit) and W (sum ds) of one direction."""
     k, s = _f64(kappa), _f64(src)
     A = np.empty_like(k)
     W = np.empty_like(k)
-    cfg = _cfg(k.shape, nside, field_form, tie_tol, 1, i_bc)
+    cfg = _cfg(k.shape, nside, field_form, tie_tol, 1, i_bc, averaging)
     if _lib_handle().orc_sweep_dir(C.byref(cfg), _dp(k), _dp(s), int(d), _dp(A), _dp(W)) != 0:
         raise ValueError("bad direction index")
     return A, W
@@ -209,12 +210,12 @@ def trace_ray(kappa, src, nside, d, j, k, field_form=0, tie_tol=1e-12, maxseg=10
     return cells[:n].copy(), ds[:n].copy(), iin[:n].copy(), iex.value
 
 
-def jin_cells(kappa, src, nside, cells, field_form=0, tie_tol=1e-12, nthreads=None, i_bc=0.0):
+def jin_cells(kappa, src, nside, cells, field_form=0, tie_tol=1e-12, nthreads=None, i_bc=0.0, averaging=0):
     """J^in at the given flat cell indices, computed one cell at a time."""
     k, s = _f64(kappa), _f64(src)
     c = np.ascontiguousarray(np.asarray(cells, dtype=np.int64))
     out = np.empty(c.shape[0])
-    cfg = _cfg(k.shape, nside, field_form, tie_tol, nthreads, i_bc)
+    cfg = _cfg(k.shape, nside, field_form, tie_tol, nthreads, i_bc, averaging)
     bad = _lib_handle().orc_jin_cells(C.byref(cfg), _dp(k), _dp(s), c.ctypes.data_as(_L),
                                       int(c.shape[0]), _dp(out))
     if bad:

@@ -260,11 +260,13 @@ typedef struct {
     int field_form;   /* 0: (kappa, S) inputs; 1: (kappa, emissivity) inputs */
     int nthreads;
     double i_bc;      /* intensity of every ray where it enters the box (0: vacuum) */
+    int averaging;    /* 0: the paper's cell average (J = J^in + S); 1: the exact path average */
 } orc_sweep_cfg;
 
 typedef struct {
     const double *kappa, *src;  /* per cell: kappa per cell width; S or eps*dx */
     int form;
+    int exact;                  /* exact path average instead of the paper's */
     double I;                   /* running intensity along the ray */
     double *A, *W;              /* per-cell accumulators of this direction */
     /* optional per-segment record */
@@ -288,7 +290,21 @@ static void seg_update(void *vctx, long cell, double ds)
     const double ph = phi_of(x);
     const double Iin = r->I;
     if (r->A && (r->only_cell < 0 || r->only_cell == cell)) {
-        r->A[r->only_cell < 0 ? cell : 0] += ds * Iin * ph;
+        /* paper: ds Ibar_in = ds I_in phi.  Exact: the path average of I over
+         * the segment, S + (I_in - S) phi, less S (source-function inputs),
+         * or in full, ds I_in phi + eps ds^2 psi with psi = (1 - phi)/x
+         * (emissivity inputs, where kappa may vanish). */
+        double dep = ds * Iin * ph;
+        if (r->exact) {
+            if (r->form == 0) {
+                dep = ds * (Iin - r->src[cell]) * ph;
+            } else {
+                const double psi = x < 1e-3 ? 0.5 - x / 6.0 + x * x / 24.0 - x * x * x / 120.0
+                                            : (x + expm1(-x)) / (x * x);
+                dep += r->src[cell] * ds * ds * psi;
+            }
+        }
+        r->A[r->only_cell < 0 ? cell : 0] += dep;
         r->W[r->only_cell < 0 ? cell : 0] += ds;
     }
     if (r->cells && r->nrec < r->maxseg) {
@@ -328,6 +344,7 @@ static long long sweep_dir(const orc_sweep_cfg *cfg, const double *kappa, const 
     r.kappa = kappa;
     r.src = src;
     r.form = cfg->field_form;
+    r.exact = cfg->averaging;
     r.A = A;
     r.W = W;
     r.only_cell = -1;
@@ -394,7 +411,10 @@ long orc_sweep_range(const orc_sweep_cfg *cfg, const double *kappa, const double
 
 /* Full sweep, Eq. (mean_intensity): J^in = (1/N_d) sum_i Ibar^{ave,in}(n_i),
  * J = J^in + S.  With emissivity inputs S = eps/kappa where kappa > 0; where
- * kappa = 0 only J^in is defined and J = J^in is returned. */
+ * kappa = 0 only J^in is defined and J = J^in is returned.  Exact averaging:
+ * with source-function inputs the sum is of (I_in - S) phi, so again
+ * J = J^in + S; with emissivity inputs it is of the whole path average, so
+ * J is the sum and J^in = J - S (J where kappa = 0). */
 long orc_sweep(const orc_sweep_cfg *cfg, const double *kappa, const double *src,
                double *Jin, double *J)
 {
@@ -403,10 +423,14 @@ long orc_sweep(const orc_sweep_cfg *cfg, const double *kappa, const double *src,
     long nzero = orc_sweep_range(cfg, kappa, src, 0, nd, Jin);
     if (nzero < 0) return nzero;
     for (long i = 0; i < ncell; i++) Jin[i] /= (double)nd;
-    if (J) {
-        for (long i = 0; i < ncell; i++) {
-            double S = src[i];
-            if (cfg->field_form == 1) S = kappa[i] > 0.0 ? src[i] / kappa[i] : 0.0;
+    const int whole = cfg->averaging == 1 && cfg->field_form == 1;   /* Jin holds J */
+    for (long i = 0; i < ncell; i++) {
+        double S = src[i];
+        if (cfg->field_form == 1) S = kappa[i] > 0.0 ? src[i] / kappa[i] : 0.0;
+        if (whole) {
+            if (J) J[i] = Jin[i];
+            Jin[i] -= S;
+        } else if (J) {
             J[i] = Jin[i] + S;
         }
     }
@@ -445,6 +469,7 @@ int orc_trace_ray(const orc_sweep_cfg *cfg, const double *kappa, const double *s
     r.kappa = kappa;
     r.src = src;
     r.form = cfg->field_form;
+    r.exact = cfg->averaging;
     r.cells = cells;
     r.ds = ds;
     r.Iin = Iin;
@@ -497,6 +522,7 @@ int orc_jin_cells(const orc_sweep_cfg *cfg, const double *kappa, const double *s
             r.kappa = kappa;
             r.src = src;
             r.form = cfg->field_form;
+            r.exact = cfg->averaging;
             r.A = &A;
             r.W = &W;
             r.only_cell = cell;
@@ -509,6 +535,8 @@ int orc_jin_cells(const orc_sweep_cfg *cfg, const double *kappa, const double *s
             else bad++;
         }
         Jin[ci] = sum / (double)nd;
+        if (cfg->averaging == 1 && cfg->field_form == 1 && kappa[cell] > 0.0)
+            Jin[ci] -= src[cell] / kappa[cell];   /* the sum was the whole path average */
     }
     return bad;
 }

@@ -18,7 +18,7 @@ from . import build as _build
 
 ART_OK, ART_E_INVALID, ART_E_CUDA, ART_E_OOM, ART_E_NOT_CONVERGED, ART_E_TIMEOUT, ART_E_STATE = range(7)
 ART_FP32, ART_FP64 = 0, 1
-ART_AVG_PAPER = 0
+ART_AVG_PAPER, ART_AVG_EXACT = 0, 1
 ART_FIELDS_S, ART_FIELDS_EPS = 0, 1
 _STATUS = {0: "ART_OK", 1: "ART_E_INVALID", 2: "ART_E_CUDA", 3: "ART_E_OOM",
            4: "ART_E_NOT_CONVERGED", 5: "ART_E_TIMEOUT", 6: "ART_E_STATE"}
@@ -384,7 +384,7 @@ class ArtSweep:
     def __init__(self, shape, nside, nbins: int = 1, precision: str = "fp32", field_form: int = 0,
                  dx_cm: float = 1.0, tile_b: int = 0, tile_c: int = 0, slab: int = 0, dir_split: int = 0,
                  tie_tol: float = 1e-12, variant: int = 0, persistent: int = 0, graph: bool = False,
-                 dir_range=None, early_launch: bool = True):
+                 dir_range=None, early_launch: bool = True, averaging: int = 0):
         batch = len(shape) > 0 and not np.isscalar(shape[0])
         shapes = [tuple(int(v) for v in s) for s in (shape if batch else [shape])]
         nsides = [int(v) for v in nside] if not np.isscalar(nside) else [int(nside)] * len(shapes)
@@ -405,6 +405,7 @@ class ArtSweep:
         opt.persistent = int(persistent)
         opt.graph = 1 if graph else 0
         opt.early_launch = 1 if early_launch else -1
+        opt.averaging = int(averaging)
         if dir_range is not None:
             opt.dir_begin, opt.dir_end = int(dir_range[0]), int(dir_range[1])
         grids = [ArtGrid(nx, ny, nz, dx_cm) for (nz, ny, nx) in shapes]

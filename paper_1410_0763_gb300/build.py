@@ -19,9 +19,10 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "lib")
 LIB = os.path.join(OUT_DIR, "libart.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["art_api.cu", "art_geometry.cpp", "art_probe.cu", "art_noalloc.cu", "art_ion.cu", "art_net.cu",
-           "art_ablation.cu"]
-HEADERS = ["art_kernels.cuh", "art_geometry.hpp", "art_ctx.hpp", "art_net_kernels.cuh", "art_net_internal.hpp"]
+SOURCES = ["art_api.cu", "art_sweep_exact.cu", "art_geometry.cpp", "art_probe.cu", "art_noalloc.cu", "art_ion.cu",
+           "art_net.cu", "art_ablation.cu"]
+HEADERS = ["art_kernels.cuh", "art_geometry.hpp", "art_ctx.hpp", "art_net_kernels.cuh", "art_net_internal.hpp",
+           "art_variants.inc"]
 
 
 def nvcc_path() -> str:

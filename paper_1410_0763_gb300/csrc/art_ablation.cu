@@ -222,9 +222,10 @@ extern "C" art_status art_ablation_sweep(art_ctx *ctx, int mode, float *J_in, vo
     if (mode != 0 && mode != 1) return art_fail(ctx, ART_E_INVALID, "art_ablation_sweep: mode 0 (atomics) or 1 (groups)");
     if (!J_in) return art_fail(ctx, ART_E_INVALID, "art_ablation_sweep: null output");
     if (ctx->grids.size() != 1 || ctx->prec != ART_FP32 || ctx->nbins != 1 || ctx->opt.field_form != ART_FIELDS_S ||
-        ctx->opt.dir_end > ctx->opt.dir_begin)
+        ctx->opt.averaging != ART_AVG_PAPER || ctx->opt.dir_end > ctx->opt.dir_begin)
         return art_fail(ctx, ART_E_INVALID,
-                        "art_ablation_sweep: single-grid FP32 contexts, one bin, ART_FIELDS_S, all directions");
+                        "art_ablation_sweep: single-grid FP32 contexts, one bin, ART_FIELDS_S, the paper's averaging, "
+                        "all directions");
     if (!ctx->have_fields) return art_fail(ctx, ART_E_STATE, "art_ablation_sweep: call art_set_fields first");
     for (double v : ctx->i_bc)
         if (v != 0.0) return art_fail(ctx, ART_E_INVALID, "art_ablation_sweep: vacuum boundary only");

@@ -18,6 +18,12 @@
 
 using namespace art;
 
+// The exact-average kernels live in art_sweep_exact.cu (one instantiation per
+// variant of art_variants.inc).
+template <typename real, int TB, int TC, int BLK, int NT, int KP, int MINB>
+cudaError_t art_launch_exact(const cudaLaunchConfig_t &cfg, const SweepArgs<real> &a);
+template <typename real, int TB, int TC, int BLK, int NT, int KP, int MINB> cudaError_t art_prepare_exact(int smem);
+
 #include "art_ctx.hpp"
 
 art_status art_fail(art_ctx *ctx, art_status st, const std::string &msg)
@@ -93,6 +99,7 @@ cudaError_t launch_sweep(const void *args, int nctas, cudaStream_t st, bool earl
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = early ? 1 : 0;
+    if (a.averaging) return art_launch_exact<real, TB, TC, BLK, NT, KP, MINB>(cfg, a);
     if (a.counter) return cudaLaunchKernelEx(&cfg, sweep_queue_kernel<real, TB, TC, BLK, NT, KP, MINB>, a);
     return cudaLaunchKernelEx(&cfg, sweep_block_kernel<real, TB, TC, BLK, NT, KP, MINB>, a);
 }
@@ -105,7 +112,8 @@ template <typename real, int TB, int TC, int BLK, int NT, int KP, int MINB> int 
     auto kern = sweep_block_kernel<real, TB, TC, BLK, NT, KP, MINB>;
     auto qkern = sweep_queue_kernel<real, TB, TC, BLK, NT, KP, MINB>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
-        cudaFuncSetAttribute(qkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+        cudaFuncSetAttribute(qkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
+        art_prepare_exact<real, TB, TC, BLK, NT, KP, MINB>((int)sm) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -129,20 +137,9 @@ struct KVariant {
     {pr, tb, tc, blk, nt, kp, mb, &launch_sweep<real, tb, tc, blk, nt, kp, mb>,                      \
      &prepare_sweep<real, tb, tc, blk, nt, kp, mb>}
 const KVariant kVariants[] = {
-    ART_V(float, ART_FP32, 32, 16, 4, 256, 2, 3),   //  1: default FP32, grids of >= 100^3 cells
-    ART_V(float, ART_FP32, 32, 8, 4, 256, 2, 3),    //  2: default FP32, smaller grids
-    ART_V(float, ART_FP32, 32, 16, 4, 256, 1, 4),   //  3
-    ART_V(float, ART_FP32, 32, 16, 4, 256, 3, 2),   //  4
-    ART_V(float, ART_FP32, 32, 16, 2, 256, 2, 3),   //  5
-    ART_V(float, ART_FP32, 32, 16, 4, 128, 2, 4),   //  6
-    ART_V(float, ART_FP32, 32, 32, 4, 512, 2, 1),   //  7
-    ART_V(float, ART_FP32, 64, 16, 4, 512, 2, 1),   //  8
-    ART_V(float, ART_FP32, 32, 16, 8, 256, 1, 2),   //  9
-    ART_V(float, ART_FP32, 32, 8, 4, 128, 2, 5),    // 10
-    ART_V(double, ART_FP64, 16, 16, 4, 128, 1, 1),  // 11: default FP64
-    ART_V(float, ART_FP32, 64, 8, 4, 256, 2, 2),    // 12: wide tiles (less halo along b)
-    ART_V(float, ART_FP32, 128, 8, 4, 512, 2, 1),   // 13
-    ART_V(float, ART_FP32, 64, 8, 2, 256, 2, 3),    // 14
+#define ART_VARIANT(real, pr, tb, tc, blk, nt, kp, mb) ART_V(real, pr, tb, tc, blk, nt, kp, mb),
+#include "art_variants.inc"
+#undef ART_VARIANT
 };
 #undef ART_V
 const int kNumVariants = int(sizeof(kVariants) / sizeof(kVariants[0]));
@@ -393,7 +390,7 @@ template <typename real> art_status do_sweep(art_ctx *ctx, real *J, real *Jin, r
     v2 *fields = static_cast<v2 *>(ctx->d_field);
     real *planes[2] = {static_cast<real *>(ctx->d_plane[0]), static_cast<real *>(ctx->d_plane[1])};
     for (int b = 0; b < ctx->nbins; ++b) {
-        SweepArgs<real> a;
+        SweepArgs<real> a{};
         a.field0 = fields + (0LL * ctx->nbins + b) * n;
         a.field1 = fields + (1LL * ctx->nbins + b) * n;
         a.field2 = fields + (2LL * ctx->nbins + b) * n;
@@ -406,6 +403,7 @@ template <typename real> art_status do_sweep(art_ctx *ctx, real *J, real *Jin, r
         a.split = ctx->split;
         a.field_form = ctx->opt.field_form;
         a.i_bc = real(ctx->i_bc[b]);
+        a.averaging = ctx->opt.averaging;
         cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
         if (ctx->profiling) {
             CK(ctx, cudaEventCreate(&e0));
@@ -427,7 +425,7 @@ template <typename real> art_status do_sweep(art_ctx *ctx, real *J, real *Jin, r
                                                    k > 0 && ctx->early_launch));
         }
         if (ctx->profiling) CK(ctx, cudaEventRecord(e1, st));
-        ReduceArgs<real> r;
+        ReduceArgs<real> r{};
         r.jpart = static_cast<const real *>(ctx->d_jpart);
         r.field_nat = fields + (2LL * ctx->nbins + b) * n;
         r.grids = static_cast<const GridDev<real> *>(ctx->d_gridinfo);
@@ -436,6 +434,7 @@ template <typename real> art_status do_sweep(art_ctx *ctx, real *J, real *Jin, r
         r.gamma_coef = real(4.0 * M_PI * ctx->G[b]);
         r.gamma_accum = b > 0;
         r.field_form = ctx->opt.field_form;
+        r.whole = ctx->opt.averaging == ART_AVG_EXACT && ctx->opt.field_form == ART_FIELDS_EPS;
         r.Jin = Jin ? Jin + (long long)b * n : nullptr;
         r.J = J ? J + (long long)b * n : nullptr;
         r.gamma = gam;
@@ -521,7 +520,8 @@ art_status create_common(const art_grid *grids, const int *n_side, int n_grids, 
     if (opt) ctx->opt = *opt;
     else art_options_default(&ctx->opt);
     if (!(ctx->opt.tie_tol >= 0.0) || ctx->opt.tie_tol > 1e-3) ctx->opt.tie_tol = 1e-12;
-    if ((ctx->opt.precision != ART_FP32 && ctx->opt.precision != ART_FP64) || ctx->opt.averaging != ART_AVG_PAPER ||
+    if ((ctx->opt.precision != ART_FP32 && ctx->opt.precision != ART_FP64) ||
+        (ctx->opt.averaging != ART_AVG_PAPER && ctx->opt.averaging != ART_AVG_EXACT) ||
         (ctx->opt.field_form != ART_FIELDS_S && ctx->opt.field_form != ART_FIELDS_EPS) || ctx->opt.dir_split < 0 ||
         ctx->opt.dir_begin < 0 || ctx->opt.dir_end < 0 ||
         (ctx->opt.dir_end != 0 || ctx->opt.dir_begin != 0) &&

@@ -98,6 +98,7 @@ template <typename real> struct SweepArgs {
     int kblock;
     int field_form;
     real i_bc;                   // intensity of every ray where it enters the box (0: vacuum)
+    int averaging;               // 0: the paper's cell average; 1: the exact path average
 };
 
 // ---------------------------------------------------------------------------
@@ -221,15 +222,50 @@ __device__ __forceinline__ void seg_coef2(const CellVals<double> &c, double2 ds,
     xph = make_double2(x0 * p0, x1 * p1);
 }
 
-// Eq. (rt) for a pair: A += I_in dsph (path-averaged incoming intensity times
-// the segment length), then I = S + (I - S) e^-x (form 0) or
-// I = I e^-x + eps ds phi (form 1, S = eps/kappa).
+// ds^2 psi(x), psi = (1 - phi)/x (-> 1/2 at x = 0): the emission part of the
+// exact path average with emissivity inputs, ds <I> = I_in dsph + eps ds^2 psi.
+// FP32: the Maclaurin series of psi below x = 1/4, else (x - xph)/kappa^2.
+__device__ __forceinline__ float2 seg_psids(const CellVals<float> &c, float2 ds, float2 xph)
+{
+    using P = PairOps<float>;
+    const float2 x = P::mul(P::splat(c.kap), ds);
+    float2 q = P::fma(x, P::splat(-1.0f / 5040.0f), P::splat(1.0f / 720.0f));
+    q = P::fma(x, q, P::splat(-1.0f / 120.0f));
+    q = P::fma(x, q, P::splat(1.0f / 24.0f));
+    q = P::fma(x, q, P::splat(-1.0f / 6.0f));
+    q = P::fma(x, q, P::splat(0.5f));
+    const float2 small = P::mul(P::mul(ds, ds), q);
+    const float r2 = c.rk0 * c.rk0;
+    return make_float2(x.x < 0.25f ? small.x : (x.x - xph.x) * r2, x.y < 0.25f ? small.y : (x.y - xph.y) * r2);
+}
+
+__device__ __forceinline__ double2 seg_psids(const CellVals<double> &c, double2 ds, double2)
+{
+    const double x0 = c.kap * ds.x, x1 = c.kap * ds.y;
+    auto psi = [](double x) {
+        return x < 1e-3 ? 0.5 - x / 6.0 + x * x / 24.0 - x * x * x / 120.0 : (x + expm1(-x)) / (x * x);
+    };
+    return make_double2(ds.x * ds.x * psi(x0), ds.y * ds.y * psi(x1));
+}
+
+// Eq. (rt) for a pair: the deposit, then I = S + (I - S) e^-x (form 0) or
+// I = I e^-x + eps ds phi (form 1, S = eps/kappa).  Deposit of the paper's
+// average (avg 0): A += I_in dsph, the path-averaged incoming intensity times
+// the segment length.  Exact path average (avg 1): A += (I_in - S) dsph with
+// source-function inputs (J = S + the cell average), or the whole
+// ds <I> = I_in dsph + eps ds^2 psi with emissivity inputs.
 template <typename real>
 __device__ __forceinline__ void seg_apply2(typename PairOps<real>::T &I, typename PairOps<real>::T &A, real src,
-                                           typename PairOps<real>::T dsph, typename PairOps<real>::T xph, int form)
+                                           typename PairOps<real>::T dsph, typename PairOps<real>::T xph, int form,
+                                           int avg, const CellVals<real> &c, typename PairOps<real>::T ds)
 {
     using P = PairOps<real>;
-    A = P::fma(I, dsph, A);
+    if (avg == 0)
+        A = P::fma(I, dsph, A);
+    else if (form == 0)
+        A = P::fma(P::fma(I, P::splat(real(1)), P::splat(-src)), dsph, A);
+    else
+        A = P::fma(P::splat(src), seg_psids(c, ds, xph), P::fma(I, dsph, A));
     if (form == 0) {
         const auto d = P::fma(I, P::splat(real(-1)), P::splat(src));
         I = P::fma(d, xph, I);
@@ -299,7 +335,7 @@ template <int TB, int TC, int BLK, int NT, int KP> struct SweepShape {
     }
 };
 
-template <typename real, int TB, int TC, int BLK, int NT, int KP>
+template <typename real, int TB, int TC, int BLK, int NT, int KP, int AVG>
 __device__ __forceinline__ void sweep_item(const SweepArgs<real> &p, int item, unsigned char *smem_raw)
 {
     using v2 = typename Vec2<real>::type;
@@ -326,6 +362,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<real> &p, int item, u
     const v2 *__restrict__ F = (C.a == 0 ? p.field0 : (C.a == 1 ? p.field1 : p.field2)) + C.cell_off;
     const int tid = threadIdx.x;
     const int form = p.field_form;
+    constexpr int avg = AVG;   // averaging mode, fixed per kernel instantiation
 
     // Stage the region's (kappa, src) for the BLK slabs (vacuum outside the
     // box) and clear the exchange buffers.
@@ -525,7 +562,8 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<real> &p, int item, u
                             pr dsph, xph;
                             seg_coef2(oc[s], g[kp].ds1, dsph, xph);
                             oA[s][kp] = P::splat(real(0));
-                            seg_apply2<real>(oI[s][kp], oA[s][kp], oc[s].src, dsph, xph, form);
+                            seg_apply2<real>(oI[s][kp], oA[s][kp], oc[s].src, dsph, xph, form, avg, oc[s],
+                                             g[kp].ds1);
                         }
                     }
 #pragma unroll
@@ -539,7 +577,8 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<real> &p, int item, u
                             for (int kp = 0; kp < KP; ++kp) {
                                 pr dsph, xph, dummy = P::splat(real(0));
                                 seg_coef2(hc[s], g[kp].ds1, dsph, xph);
-                                seg_apply2<real>(hI[s][kp], dummy, hc[s].src, dsph, xph, form);
+                                seg_apply2<real>(hI[s][kp], dummy, hc[s].src, dsph, xph, form, 0, hc[s],
+                                                 g[kp].ds1);
                             }
                         }
                     }
@@ -572,7 +611,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<real> &p, int item, u
                                 pr dsph, xph;
                                 seg_coef2(oc[s], dsv, dsph, xph);
                                 pr Iin = P::mk(Xr[o_r2[s] - offa], Xr[o_r2[s] + 1 - offb]);
-                                seg_apply2<real>(Iin, oA[s][kp], oc[s].src, dsph, xph, form);
+                                seg_apply2<real>(Iin, oA[s][kp], oc[s].src, dsph, xph, form, avg, oc[s], dsv);
                                 oI[s][kp] = Iin;
                             }
 #pragma unroll
@@ -581,7 +620,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<real> &p, int item, u
                                     pr dsph, xph, dummy = P::splat(real(0));
                                     seg_coef2(hc[s], dsv, dsph, xph);
                                     pr Iin = P::mk(Xr[2 * h_r[s] - offa], Xr[2 * h_r[s] + 1 - offb]);
-                                    seg_apply2<real>(Iin, dummy, hc[s].src, dsph, xph, form);
+                                    seg_apply2<real>(Iin, dummy, hc[s].src, dsph, xph, form, 0, hc[s], dsv);
                                     hI[s][kp] = Iin;
                                 }
                             }
@@ -638,19 +677,20 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<real> &p, int item, u
     __syncthreads();   // shared memory is reused by the CTA's next work item
 }
 
-// One CTA per work item.
-template <typename real, int TB, int TC, int BLK, int NT, int KP, int MINB>
+// One CTA per work item.  AVG: the averaging mode (0 the paper's, 1 exact),
+// a separate instantiation so the paper's path keeps its own registers.
+template <typename real, int TB, int TC, int BLK, int NT, int KP, int MINB, int AVG = 0>
 __global__ void __launch_bounds__(NT, MINB) sweep_block_kernel(const SweepArgs<real> p)
 {
     extern __shared__ __align__(32) unsigned char smem_raw[];
     grid_dep_launch();
-    if ((int)blockIdx.x < p.n_work) sweep_item<real, TB, TC, BLK, NT, KP>(p, blockIdx.x, smem_raw);
+    if ((int)blockIdx.x < p.n_work) sweep_item<real, TB, TC, BLK, NT, KP, AVG>(p, blockIdx.x, smem_raw);
 }
 
 // Persistent form: a fixed grid of CTAs taking work items from a queue
 // (p.counter, zero before the launch).  Items write disjoint outputs, so the
 // order in which CTAs take them changes no result.
-template <typename real, int TB, int TC, int BLK, int NT, int KP, int MINB>
+template <typename real, int TB, int TC, int BLK, int NT, int KP, int MINB, int AVG = 0>
 __global__ void __launch_bounds__(NT, MINB) sweep_queue_kernel(const SweepArgs<real> p)
 {
     extern __shared__ __align__(32) unsigned char smem_raw[];
@@ -662,13 +702,10 @@ __global__ void __launch_bounds__(NT, MINB) sweep_queue_kernel(const SweepArgs<r
         const int item = s_item;
         __syncthreads();
         if (item >= p.n_work) break;
-        sweep_item<real, TB, TC, BLK, NT, KP>(p, item, smem_raw);
+        sweep_item<real, TB, TC, BLK, NT, KP, AVG>(p, item, smem_raw);
     }
 }
 
-// ---------------------------------------------------------------------------
-// Sum the class partials (fixed order, Kahan) into J^in, J and Gamma.
-// ---------------------------------------------------------------------------
 template <typename real> struct ReduceArgs {
     const real *jpart;
     const typename Vec2<real>::type *field_nat;    // (kappa, src) in [z][y][x], concatenated grids, one bin
@@ -678,6 +715,7 @@ template <typename real> struct ReduceArgs {
     real gamma_coef;     // 4 pi G_b
     int gamma_accum;     // add to gamma instead of overwriting
     int field_form;
+    int whole;           // the partials sum to J (exact average, emissivity inputs): J^in = J - S
     real *Jin, *J, *gamma;   // concatenated grids
 };
 
@@ -696,14 +734,16 @@ template <typename real> __global__ void reduce_kernel(const ReduceArgs<real> p)
     const long long l = i - G.cell_off;
     real s = real(0), c = real(0);
     for (int k = 0; k < G.n_part; ++k) kahan_add(s, c, p.jpart[G.jpart_off + (long long)k * G.ncell + l]);
-    const real jin = (s - c) * G.inv_nd;
-    if (p.Jin) p.Jin[i] = jin;
-    if (p.J) {
+    const real acc = (s - c) * G.inv_nd;
+    real jin = acc;
+    if (p.J || p.whole) {
         const v2 f = p.field_nat[i];
         real S = f.y;
         if (p.field_form == 1) S = f.x > real(0) ? f.y / f.x : real(0);
-        p.J[i] = jin + S;
+        if (p.whole) jin = acc - S;
+        if (p.J) p.J[i] = p.whole ? acc : acc + S;
     }
+    if (p.Jin) p.Jin[i] = jin;
     if (p.gamma) {
         const real g = p.gamma_coef * jin;
         p.gamma[i] = p.gamma_accum ? p.gamma[i] + g : g;

@@ -351,6 +351,7 @@ art_status artnet_coarse(art_ctx *ctx, int f, int nside_c)
         art_options o;
         art_options_default(&o);
         o.field_form = ART_FIELDS_EPS;
+        o.averaging = ctx->opt.averaging;   // the coarse sweep averages as the fine one
         art_status s = art_create(&gc, nside_c, 1, &o, &ctx->coarse);
         if (s != ART_OK) return art_fail(ctx, s, "surrogate: coarse sweep context could not be created");
         S.f = f;

@@ -268,7 +268,7 @@ extern "C" art_status art_sweep_noalloc(const art_grid *grid, int n_side, const 
                                                                            dims[0], dims[1], dims[2]);
     ART_NA_CK(cudaGetLastError(), "layout kernel launch failed");
 
-    SweepArgs<float> a;
+    SweepArgs<float> a{};
     a.field0 = fld;
     a.field1 = fld + ncell;
     a.field2 = fld + 2 * ncell;
@@ -282,6 +282,7 @@ extern "C" art_status art_sweep_noalloc(const art_grid *grid, int n_side, const 
     a.split = 1;
     a.field_form = ART_FIELDS_S;
     a.i_bc = 0.0f;   // vacuum boundary
+    a.averaging = ART_AVG_PAPER;
     int maxNa = 0;
     for (int c = 0; c < ncls; ++c) maxNa = g_classes[c].Na > maxNa ? g_classes[c].Na : maxNa;
     const size_t sm = SweepShape<kTB, kTC, kBLK, kNT, kKP>::bytes<float>();
@@ -296,7 +297,7 @@ extern "C" art_status art_sweep_noalloc(const art_grid *grid, int n_side, const 
         kern<<<nwork, kNT, sm, st>>>(a);
         ART_NA_CK(cudaGetLastError(), "sweep kernel launch failed");
     }
-    ReduceArgs<float> r;
+    ReduceArgs<float> r{};
     r.jpart = jpart;
     r.field_nat = fld + 2 * ncell;
     r.grids = reinterpret_cast<const GridDev<float> *>(base + o_grid);
@@ -305,6 +306,7 @@ extern "C" art_status art_sweep_noalloc(const art_grid *grid, int n_side, const 
     r.gamma_coef = 0.0f;
     r.gamma_accum = 0;
     r.field_form = ART_FIELDS_S;
+    r.whole = 0;
     r.Jin = J_in;
     r.J = nullptr;
     r.gamma = nullptr;

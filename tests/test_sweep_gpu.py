@@ -226,3 +226,21 @@ def test_full_size_sampled_cells(orc, n, nside, bins, tol, ncells):
     cells[:3] = [0, kap.size - 1, (n // 2) * n * n + (n // 2) * n]
     ref = orc.jin_cells(f32(kap), f32(S), nside, cells)
     assert rel(Jin.ravel()[cells], ref) < tol
+
+
+@pytest.mark.parametrize("precision,form", [("fp64", 0), ("fp64", 1), ("fp32", 0), ("fp32", 1)])
+def test_exact_averaging_matches_oracle(orc, precision, form):
+    """ART_AVG_EXACT: J against the oracle (1e-12 FP64, 1e-5 FP32 relative);
+    J^in = J - S, which can cross zero, to the same tolerance times max |J|."""
+    rng = np.random.default_rng(71 + form)
+    shape = (21, 26, 37)
+    kap = f32(0.5 * np.exp(rng.standard_normal(shape)))
+    if form == 1:
+        kap[rng.random(shape) < 0.1] = 0.0           # emissivity inputs allow kappa = 0
+    S = f32(rng.random(shape))
+    src = f32(S * kap) if form == 1 else S
+    jin_o, j_o, _ = orc.sweep(kap, src, 2, field_form=form, averaging=1)
+    J, Jin = run(kap, src, 2, precision, form=form, averaging=art.ART_AVG_EXACT)
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    assert rel(J, j_o) < tol
+    assert np.max(np.abs(Jin - jin_o)) < tol * np.max(np.abs(j_o))
