@@ -570,8 +570,21 @@ def cpu_baseline(case, seg_per_sweep: int, budget_s: float = 12.0) -> dict:
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
+    # one core: a bounded sample of directions (the oracle's cost is per segment)
+    d1 = max(1, nd // 16)
+    t1 = time.perf_counter()
+    segs1 = 0
+    while True:
+        _, n1 = oracle.sweep_range_count(k, s, case.nside, 0, d1, nthreads=1)
+        segs1 += n1
+        if time.perf_counter() - t1 > budget_s / 4:
+            break
+    dt1 = time.perf_counter() - t1
     return {"value": segs / dt, "unit": UNIT, "cores": nt, "kind": "oracle",
-            "sample": f"{sweeps} full FP64 oracle sweeps of the same workload ({segs} segments, {dt:.1f} s)"}
+            "sample": f"{sweeps} full FP64 oracle sweeps of the same workload ({segs} segments, {dt:.1f} s)",
+            "single_core": {"value": segs1 / dt1, "unit": UNIT, "cores": 1,
+                            "sample": f"directions 0-{d1 - 1} of the same workload repeated ({segs1} segments, "
+                                      f"{dt1:.1f} s)"}}
 
 
 def run_ours(args, d: Dist):
