@@ -38,13 +38,13 @@ constexpr double kPi = 3.14159265358979323846;
 //   Gamma   += Ndot_abs / (n_HI 4pi/3 (r_out^3 - r_in^3) dx^3),  n_HI = kappa_b/(sigma_b dx)
 // which, with r_out^3 - r_in^3 = (r_out - r_in)(r_out^2 + r_out r_in + r_in^2), is
 //   Gamma   += 3 Q_b sigma_b / (4 pi dx^2) e^-tau phi(dtau) / (r_out^2 + r_out r_in + r_in^2),
-// free of the cancellation of r_out^3 - r_in^3 far from the source.  All in
-// FP32: the source position is split into its integer cell and the fraction
+// free of the cancellation of r_out^3 - r_in^3 far from the source.  The march
+// and each source's rate are FP32: the source position is split into its integer cell and the fraction
 // inside it, so every distance from the source to a plane or cell centre is
 // an exact small integer plus a fraction (no cancellation near the source);
 // the march keeps, per axis, the parametric distance to that axis' next plane
-// (an O(1) number); crossings within 1e-6 of each other are taken together;
-// the constant 3 Q_b sigma_b / (4 pi dx^2) is formed on the host in FP64.
+// (an O(1) number); the constant 3 Q_b sigma_b / (4 pi dx^2) is formed on
+// the host in FP64, and the sources' rates are summed in FP64.
 // ---------------------------------------------------------------------------
 struct PtSrc {
     int si[3];       // cell containing the source
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(128) point_source_kernel(const PtArgs p)
     const int dims[3] = {p.nx, p.ny, p.nz};
     constexpr int U = PT_UNROLL;
     constexpr int NK = SCALED ? 1 : NB;   // kappa fields marched
-    float g = 0.0f;
+    double g = 0.0;                       // the sum over sources, in index order, in FP64
     for (int a = 0; a < p.nsrc; ++a) {
         const PtSrc S = p.src[a];
         // source -> cell centre: integer part exact, plus the fractions
@@ -195,15 +195,17 @@ __global__ void __launch_bounds__(128) point_source_kernel(const PtArgs p)
                 rout = fminf(rout, fmaxf(t1, t2));
             }
             const float den = rout * rout + rout * rin + rin * rin;
+            float ga = 0.0f;
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
                 const float kb = SCALED ? p.kappa[target] * p.kscale[b] : p.kappa[(long long)b * p.ncell + target];
                 const float tb = SCALED ? tau[0] * p.kscale[b] : tau[b];
-                g += S.coef[b] * __expf(-tb) * pt_phi(kb * (rout - rin)) / den;
+                ga += S.coef[b] * __expf(-tb) * pt_phi(kb * (rout - rin)) / den;
             }
+            g += (double)ga;
         }
     }
-    p.gamma[target] = g;
+    p.gamma[target] = (float)g;
 }
 
 // ---------------------------------------------------------------------------
