@@ -96,6 +96,8 @@ def _lib_handle():
             lib.orc_iterate_ext.argtypes = [C.POINTER(SweepCfg), C.POINTER(Chem), _D, C.c_int, _D, _D,
                                             C.c_int, _D, _D, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
                                             _D, _D, C.POINTER(C.c_int)]
+            lib.orc_point_sources_cells.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _D, _D, C.c_int, _D, _D,
+                                                     C.c_double, _L, C.c_int, _D]
             lib.orc_plane_source.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _D, _D, C.c_int, C.c_int, _D, _D]
             lib.orc_evolve.argtypes = [C.POINTER(SweepCfg), C.POINTER(Chem), _D, C.c_int, _D, _D, C.c_int, _D, _D,
                                        C.c_int, C.c_int, C.c_double, C.POINTER(EvolveOpt), C.c_double, _D,
@@ -255,6 +257,24 @@ def balance_eq(nH, alphaB, gcoll, g):
     y = np.empty_like(n)
     _lib_handle().orc_balance_eq(n.size, _dp(n), float(alphaB), float(gcoll), _dp(gg), _dp(y))
     return y
+
+
+def point_sources_cells(kappa_bins, sigma, pos, Qb, dx, cells):
+    """Point-source rates (App. A) at the given flat cell indices only; arguments as point_sources."""
+    k = _f64(kappa_bins)
+    if k.ndim == 3:
+        k = k[None]
+    nb = k.shape[0]
+    nz, ny, nx = k.shape[1:]
+    sig = _f64(sigma).reshape(nb)
+    p = _f64(pos).reshape(-1, 3)
+    q = _f64(Qb).reshape(p.shape[0], nb)
+    c = np.ascontiguousarray(np.asarray(cells, dtype=np.int64))
+    out = np.empty(c.shape[0])
+    if _lib_handle().orc_point_sources_cells(nx, ny, nz, nb, _dp(k), _dp(sig), p.shape[0], _dp(p), _dp(q), float(dx),
+                                             c.ctypes.data_as(_L), int(c.shape[0]), _dp(out)) != 0:
+        raise ValueError("cell index out of range")
+    return out
 
 
 def plane_source(kappa_bins, sigma, axis, direction, flux):

@@ -646,6 +646,23 @@ int orc_point_sources(int nx, int ny, int nz, int nbins, const double *kappa_bin
     return 0;
 }
 
+/* The same rates at selected target cells only (flat indices). */
+int orc_point_sources_cells(int nx, int ny, int nz, int nbins, const double *kappa_bins, const double *sigma,
+                            int nsrc, const double *pos, const double *Q, double dx, const long *cells,
+                            int ncells, double *gamma)
+{
+    const int dims[3] = {nx, ny, nz};
+    const long ncell = (long)nx * ny * nz;
+    for (int c = 0; c < ncells; c++) {
+        if (cells[c] < 0 || cells[c] >= ncell) return -1;
+        double g = 0.0;
+        for (int a = 0; a < nsrc; a++)
+            g += pt_one(dims, kappa_bins, ncell, nbins, sigma, Q + (size_t)a * nbins, pos + 3 * a, cells[c], dx);
+        gamma[c] = g;
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Plane-parallel incident flux (the Test-3 setup of Sec. 4.3: a constant    */
 /* photon flux F through one face of the box, i.e. a point source at         */

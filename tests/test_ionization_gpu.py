@@ -131,6 +131,43 @@ def test_full_size_hii_region_is_a_fixed_point(orc):
     assert rel(y.ravel()[cells], y_check) < 1e-4
 
 
+def test_full_size_clumpy_medium_with_bins_is_a_fixed_point(orc):
+    """The clumpy 256^3 medium, N_side 8, 8 sources over 4 blackbody bins, as
+    the benchmark solves it: the GPU's converged state satisfies the balance
+    at sampled cells with the oracle's J^in and point-source rates there."""
+    case = wl.clumpy()
+    frac, sig, _ = wl.blackbody_bins()
+    ch = case.chem
+    sw = art.ArtSweep(case.nH.shape, case.nside, 1, field_form=art.ART_FIELDS_EPS, dx_cm=ch["dx"])
+    sw.set_source_spectrum(sig, frac)
+    nH = torch.as_tensor(case.nH, dtype=torch.float64, device="cuda")
+    y = torch.as_tensor(case.y0, dtype=torch.float64, device="cuda").clone()
+    srcs = [(p[0], p[1], p[2], q) for p, q in zip(case.pos, case.Q)]
+    rep, hist = sw.iterate(nH, ch, srcs, y, tol=1e-6, max_iter=400)
+    sw.close()
+    assert rep.converged
+    y = y.cpu().numpy()
+    ne = (1 - y) * case.nH
+    kap = (y * case.nH * ch["sigma0"] * ch["dx"]).astype(np.float32).astype(np.float64)
+    eps = (ch["h"] * ch["nu0"] * (ch["alphaA"] - ch["alphaB"]) * ne * ne * ch["dx"] / (4 * math.pi * ch["dnu"]))
+    eps = eps.astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(5)
+    # cells across the range of ionization: half drawn from the neutral gas, half from the ionized
+    flat = y.ravel()
+    order = np.argsort(flat)
+    cells = np.concatenate([rng.choice(order[: flat.size // 2], 8, replace=False),
+                            rng.choice(order[flat.size // 2:], 8, replace=False)])
+    jin = orc.jin_cells(kap, eps, case.nside, cells, field_form=1)
+    G = orc.band_integral(ch["sigma0"], ch["h"], ch["nu0"], ch["nu0"] + ch["dnu"])
+    kapb = np.stack([kap * (s / ch["sigma0"]) for s in sig])
+    Qb = np.outer(case.Q, frac)
+    gpt = orc.point_sources_cells(kapb, sig, case.pos, Qb, ch["dx"], cells)
+    g = 4 * math.pi * G * jin + gpt
+    y_check = orc.balance_eq(case.nH.ravel()[cells], ch["alphaB"], ch["gcoll"], g)
+    assert rel(flat[cells], y_check) < 1e-4
+    assert rel(1 - flat[cells], 1 - y_check) < 1e-4
+
+
 def test_iteration_with_source_bins_matches_oracle(orc):
     """Point sources over three frequency bins (blackbody fractions, photon-weighted
     cross sections) inside the RT / balance iteration."""

@@ -217,3 +217,15 @@ def test_iteration_source_bins_split_and_scale(orc):
                                   sigma_bins=[s0, s0, 3 * s0], frac_bins=[0.25, 0.75, 0.0])
     assert c1 and c2 and it1 == it2
     assert np.allclose(y1, y2, rtol=1e-12, atol=0)
+
+
+def test_point_sources_at_selected_cells_equal_the_full_evaluation(orc):
+    rng = np.random.default_rng(81)
+    shape = (9, 10, 11)
+    kap = 0.4 * np.exp(rng.standard_normal((2,) + shape))
+    sig = [6.3e-18, 2.0e-18]
+    pos = np.array([[2.3, 4.1, 7.7], [10.0, 0.0, 4.5]])
+    Qb = np.array([[1e48, 2e47], [5e47, 5e47]])
+    full = orc.point_sources(kap, sig, pos, Qb, 1e20).ravel()
+    cells = rng.choice(full.size, 40, replace=False)
+    assert np.array_equal(orc.point_sources_cells(kap, sig, pos, Qb, 1e20, cells), full[cells])
