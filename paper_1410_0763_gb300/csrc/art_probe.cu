@@ -1,16 +1,20 @@
 // art_probe.cu -- issue-rate microbenchmark of the pipes the sweep relies on:
 // MUFU ex2 (one exponential per segment), MUFU rcp and FP32 FFMA.  Each CTA
-// runs 8 independent chains per thread and times itself with clock64(); the
-// result per pipe is operations per clock per SM (max cycle count over CTAs,
-// two CTAs of 1024 threads resident per SM).
+// runs 8 independent chains per thread and records its SM and its first and
+// last clock64() (a per-SM counter).  Per SM the window runs from the earliest
+// start to the latest end of the CTAs it ran, so that CTAs which did not start
+// together do not shorten it; the result per pipe is the median over SMs of
+// operations per clock (two CTAs of 1024 threads resident per SM).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "art.h"
 
 namespace {
 
+// cyc[3 b] = first clock, cyc[3 b + 1] = last clock, cyc[3 b + 2] = SM of CTA b
 template <int OP> __global__ void pipe_probe_kernel(float *out, long long *cyc, int iters)
 {
     float a[8];
@@ -36,7 +40,13 @@ template <int OP> __global__ void pipe_probe_kernel(float *out, long long *cyc, 
     float s = 0.f;
     for (int i = 0; i < 8; i++) s += a[i];
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
-    if (threadIdx.x == 0) cyc[blockIdx.x] = t1 - t0;
+    if (threadIdx.x == 0) {
+        unsigned smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        cyc[3 * blockIdx.x] = t0;
+        cyc[3 * blockIdx.x + 1] = t1;
+        cyc[3 * blockIdx.x + 2] = smid;
+    }
 }
 
 }  // namespace
@@ -53,12 +63,12 @@ extern "C" art_status art_measure_pipes(double *ex2_per_clk_sm, double *rcp_per_
     float *out = nullptr;
     long long *cyc = nullptr;
     if (cudaMalloc(&out, sizeof(float) * nb * nt) != cudaSuccess) return ART_E_OOM;
-    if (cudaMalloc(&cyc, sizeof(long long) * nb) != cudaSuccess) {
+    if (cudaMalloc(&cyc, sizeof(long long) * 3 * nb) != cudaSuccess) {
         cudaFree(out);
         return ART_E_OOM;
     }
     double *res[3] = {ex2_per_clk_sm, rcp_per_clk_sm, ffma_per_clk_sm};
-    std::vector<long long> h(nb);
+    std::vector<long long> h(3 * nb);
     art_status st = ART_OK;
     for (int op = 0; op < 3 && st == ART_OK; op++) {
         double best = 0.0;
@@ -67,13 +77,27 @@ extern "C" art_status art_measure_pipes(double *ex2_per_clk_sm, double *rcp_per_
             else if (op == 1) pipe_probe_kernel<1><<<nb, nt>>>(out, cyc, iters);
             else pipe_probe_kernel<2><<<nb, nt>>>(out, cyc, iters);
             if (cudaDeviceSynchronize() != cudaSuccess ||
-                cudaMemcpy(h.data(), cyc, sizeof(long long) * nb, cudaMemcpyDeviceToHost) != cudaSuccess) {
+                cudaMemcpy(h.data(), cyc, sizeof(long long) * 3 * nb, cudaMemcpyDeviceToHost) != cudaSuccess) {
                 st = ART_E_CUDA;
                 break;
             }
-            long long mx = 1;
-            for (int i = 0; i < nb; i++) mx = h[i] > mx ? h[i] : mx;
-            const double v = double(per_sm) * nt * iters * 8 / double(mx);
+            // per SM: CTAs run, earliest start, latest end
+            int nsm_ids = 0;
+            for (int b = 0; b < nb; b++) nsm_ids = std::max(nsm_ids, int(h[3 * b + 2]) + 1);
+            std::vector<long long> lo(nsm_ids, 0), hi(nsm_ids, 0);
+            std::vector<int> cnt(nsm_ids, 0);
+            for (int b = 0; b < nb; b++) {
+                const int s = int(h[3 * b + 2]);
+                lo[s] = cnt[s] ? std::min(lo[s], h[3 * b]) : h[3 * b];
+                hi[s] = cnt[s] ? std::max(hi[s], h[3 * b + 1]) : h[3 * b + 1];
+                cnt[s]++;
+            }
+            std::vector<double> rate;
+            for (int s = 0; s < nsm_ids; s++)
+                if (cnt[s] && hi[s] > lo[s]) rate.push_back(double(cnt[s]) * nt * iters * 8 / double(hi[s] - lo[s]));
+            if (rate.empty()) continue;
+            std::nth_element(rate.begin(), rate.begin() + rate.size() / 2, rate.end());
+            const double v = rate[rate.size() / 2];
             best = v > best ? v : best;
         }
         *res[op] = best;
