@@ -60,6 +60,12 @@ class EvolveOpt(C.Structure):
                 ("dt_fixed", C.c_double), ("max_steps", C.c_int), ("max_iter", C.c_int), ("max_sub", C.c_int)]
 
 
+class Thermal(C.Structure):
+    _fields_ = [("on_the_spot", C.c_int), ("cool_mask", C.c_int), ("e_bin", C.c_double * 4),
+                ("e_diff", C.c_double), ("z", C.c_double), ("kB", C.c_double), ("T_min", C.c_double),
+                ("T_max", C.c_double)]
+
+
 _D = C.POINTER(C.c_double)
 _L = C.POINTER(C.c_long)
 
@@ -102,6 +108,22 @@ def _lib_handle():
             lib.orc_evolve.argtypes = [C.POINTER(SweepCfg), C.POINTER(Chem), _D, C.c_int, _D, _D, C.c_int, _D, _D,
                                        C.c_int, C.c_int, C.c_double, C.POINTER(EvolveOpt), C.c_double, _D,
                                        C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double), _D]
+            for f in ("alpha_A", "alpha_B", "gamma_coll", "cool_rec_A", "cool_rec_B", "cool_ci", "cool_ce",
+                      "cool_ff"):
+                getattr(lib, "orc_" + f).argtypes = [C.c_double]
+                getattr(lib, "orc_" + f).restype = C.c_double
+            lib.orc_compton_coef.argtypes = [C.c_double, C.c_double]
+            lib.orc_compton_coef.restype = C.c_double
+            TP = C.POINTER(Thermal)
+            lib.orc_cooling.argtypes = [TP, C.c_double, C.c_double, C.c_double]
+            lib.orc_cooling.restype = C.c_double
+            lib.orc_energy_step.argtypes = [TP] + [C.c_double] * 6
+            lib.orc_energy_step.restype = C.c_double
+            lib.orc_thermal_cell.argtypes = [TP] + [C.c_double] * 9 + [C.c_int, _D, _D]
+            lib.orc_evolve_thermal.argtypes = [C.POINTER(SweepCfg), C.POINTER(Chem), TP, _D, C.c_int, _D, _D,
+                                               C.c_int, _D, _D, C.c_int, C.c_int, C.c_double,
+                                               C.POINTER(EvolveOpt), C.c_double, _D, _D, C.POINTER(C.c_int),
+                                               C.POINTER(C.c_int), C.POINTER(C.c_double), _D]
             _lib = lib
     return _lib
 
@@ -347,6 +369,78 @@ def evolve(nH, nside, chem: dict, pos, Q, y0, t_end, F=10.0, eps_iter=1e-3, eps_
     if rc < 0:
         raise MemoryError("oracle evolve: allocation failed")
     return y, steps.value, iters.value, t.value, dts[: steps.value].copy(), rc
+
+
+def _thermal(th: dict) -> Thermal:
+    e = list(th.get("e_bin", [0.0])) + [0.0] * 4
+    return Thermal(int(th.get("on_the_spot", 0)), int(th.get("cool_mask", 31)), (C.c_double * 4)(*e[:4]),
+                   float(th.get("e_diff", 0.0)), float(th.get("z", -1.0)), float(th["kB"]),
+                   float(th.get("T_min", 10.0)), float(th.get("T_max", 1e9)))
+
+
+def rate_fit(name: str, T, z: float = 0.0, kB: float = 1.380649e-16):
+    """Temperature fits of the energy equation (App. C; see oracle.c for the sources):
+    alpha_A, alpha_B, gamma_coll (cm^3/s); cool_rec_A, cool_rec_B, cool_ci, cool_ce, cool_ff
+    (erg cm^3/s); compton (erg/s/K per electron, independent of T)."""
+    lib = _lib_handle()
+    if name == "compton":
+        return float(lib.orc_compton_coef(float(z), float(kB)))
+    f = getattr(lib, "orc_" + name)
+    return np.array([f(float(t)) for t in np.atleast_1d(np.asarray(T, dtype=np.float64))])
+
+
+def cooling(th: dict, nH: float, y: float, T: float) -> float:
+    """Cooling rate C(n, T) in erg/s/cm^3 (App. C) of hydrogen with neutral fraction y."""
+    t = _thermal(th)
+    return float(_lib_handle().orc_cooling(C.byref(t), float(nH), float(y), float(T)))
+
+
+def energy_step(th: dict, nH, y0, T0, y1, H1, dt) -> float:
+    """The implicit energy update of App. C for one cell: T at t + dt."""
+    t = _thermal(th)
+    return float(_lib_handle().orc_energy_step(C.byref(t), float(nH), float(y0), float(T0), float(y1),
+                                               float(H1), float(dt)))
+
+
+def thermal_cell(th: dict, nH, y0, T0, gpt, hpt, gdiff, dt, eps_e=0.2, eps_hi=0.002, max_sub=1000000):
+    """One cell over dt at fixed rates: chemistry sub-steps (App. B, D) each followed by the
+    implicit energy update (App. C).  Returns (y, T, sub-steps)."""
+    t = _thermal(th)
+    y, T = C.c_double(0.0), C.c_double(0.0)
+    n = _lib_handle().orc_thermal_cell(C.byref(t), float(nH), float(y0), float(T0), float(gpt), float(hpt),
+                                       float(gdiff), float(dt), float(eps_e), float(eps_hi), int(max_sub),
+                                       C.byref(y), C.byref(T))
+    return y.value, T.value, n
+
+
+def evolve_thermal(nH, nside, chem: dict, thermal: dict, pos, Q, y0, T0, t_end, F=10.0, eps_iter=1e-3,
+                   eps_e=0.2, eps_hi=0.002, dt_fixed=0.0, max_steps=100000, max_iter=100, max_sub=1000000,
+                   sigma_bins=None, frac_bins=None, plane=None, nthreads=None):
+    """Time-dependent mode with the energy equation (App. B-D) from t = 0 to t_end (s).  Returns
+    (y, T, steps, iterations, t_reached, dts, rc), rc as in `evolve`."""
+    n = _f64(nH)
+    y = _f64(y0).copy()
+    T = np.broadcast_to(_f64(T0), n.shape).copy()
+    p = _f64(pos).reshape(-1, 3)
+    q = _f64(Q).reshape(p.shape[0])
+    sig = _f64([chem["sigma0"]] if sigma_bins is None else sigma_bins)
+    frac = _f64([1.0] if frac_bins is None else frac_bins)
+    ch = Chem(chem["alphaA"], chem["alphaB"], chem["gcoll"], chem["sigma0"], chem["h"],
+              chem["nu0"], chem["dnu"], chem["dx"])
+    th = _thermal(thermal)
+    cfg = _cfg(n.shape, nside, 1, 1e-12, nthreads)
+    pa, pd, pf = plane if plane is not None else (0, 1, 0.0)
+    opt = EvolveOpt(float(F), float(eps_iter), float(eps_e), float(eps_hi), float(dt_fixed), int(max_steps),
+                    int(max_iter), int(max_sub))
+    dts = np.zeros(max_steps)
+    steps, iters, t = C.c_int(0), C.c_int(0), C.c_double(0.0)
+    rc = _lib_handle().orc_evolve_thermal(C.byref(cfg), C.byref(ch), C.byref(th), _dp(n), p.shape[0], _dp(p),
+                                          _dp(q), int(sig.size), _dp(sig), _dp(frac), int(pa), int(pd), float(pf),
+                                          C.byref(opt), float(t_end), _dp(y), _dp(T), C.byref(steps),
+                                          C.byref(iters), C.byref(t), _dp(dts))
+    if rc < 0:
+        raise MemoryError("oracle evolve_thermal: allocation failed")
+    return y, T, steps.value, iters.value, t.value, dts[: steps.value].copy(), rc
 
 
 if __name__ == "__main__":  # pragma: no cover

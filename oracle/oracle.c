@@ -35,7 +35,10 @@
  *     with the electron-density convergence test;
  *   - the time-dependent mode: the BDF update of App. B sub-cycled with the
  *     chemical timestep of App. D, RT steps of F times the smallest of them,
- *     each iterated to convergence of n_e (fixed temperature).
+ *     each iterated to convergence of n_e (fixed temperature); and with the
+ *     energy equation of App. C: temperature-dependent rates, photo-heating
+ *     and radiative cooling, the implicit update of the specific energy,
+ *     each RT step iterated to convergence of n_e and u.
  *
  * Everything is FP64.  Summations run in a fixed order (directions in RING
  * order, rays in lattice order, sources in index order), so the oracle is
@@ -978,6 +981,335 @@ int orc_evolve(const orc_sweep_cfg *cfg, const orc_chem *ch, const double *nH, i
     if (t_out) *t_out = t;
     free(kap); free(kapb); free(eps); free(jin); free(gpt); free(gpl); free(g); free(yp); free(yn);
     free(qb); free(fb);
+    if (t < t_end) return 2;
+    return unconverged ? 1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Energy equation (App. C) and temperature-dependent rates, hydrogen only. */
+/*                                                                          */
+/* The paper takes its rate and cooling coefficients from the works listed  */
+/* in its rate table without printing them.  The fits used here, T in K,    */
+/* lambda = 2 T_HI / T with T_HI = 157807 K (Hui & Gnedin 1997):            */
+/*   alpha_A  case-A recombination   Hui & Gnedin (1997)                    */
+/*   alpha_B  case-B recombination   Hui & Gnedin (1997)                    */
+/*   Gamma_coll  collisional ionization of HI   Cen (1992)                  */
+/*   recombination cooling, case A   Cen (1992); case B   Hui & Gnedin      */
+/*   collisional ionization / excitation cooling of HI   Cen (1992)         */
+/*   free-free cooling   1.42e-27 g_ff sqrt(T), g_ff of Spitzer's form      */
+/*   Compton cooling off the CMB   4 sigma_T a T_g^4 k_B (T - T_g) / (m_e c) */
+/*     per electron, T_g = 2.7255 (1 + z) K                                 */
+/* ------------------------------------------------------------------------ */
+#define ORC_T_HI 157807.0
+
+double orc_alpha_A(double T)
+{
+    const double l = 2.0 * ORC_T_HI / T;
+    return 1.269e-13 * pow(l, 1.503) / pow(1.0 + pow(l / 0.522, 0.470), 1.923);
+}
+
+double orc_alpha_B(double T)
+{
+    const double l = 2.0 * ORC_T_HI / T;
+    return 2.753e-14 * pow(l, 1.500) / pow(1.0 + pow(l / 2.740, 0.407), 2.242);
+}
+
+double orc_gamma_coll(double T)
+{
+    return 5.85e-11 * sqrt(T) * exp(-157809.1 / T) / (1.0 + sqrt(T / 1e5));
+}
+
+/* cooling coefficients: erg cm^3 / s, times n_e n_HII (recombination,
+ * free-free) or n_e n_HI (collisional ionization, excitation) */
+double orc_cool_rec_A(double T) { return 8.70e-27 * sqrt(T) * pow(T / 1e3, -0.2) / (1.0 + pow(T / 1e6, 0.7)); }
+
+double orc_cool_rec_B(double T)
+{
+    const double l = 2.0 * ORC_T_HI / T;
+    return 3.435e-30 * T * pow(l, 1.970) / pow(1.0 + pow(l / 2.250, 0.376), 3.720);
+}
+
+double orc_cool_ci(double T) { return 1.27e-21 * sqrt(T) * exp(-157809.1 / T) / (1.0 + sqrt(T / 1e5)); }
+
+double orc_cool_ce(double T) { return 7.50e-19 * exp(-118348.0 / T) / (1.0 + sqrt(T / 1e5)); }
+
+double orc_cool_ff(double T)
+{
+    const double d = 5.5 - log10(T);
+    return 1.42e-27 * (1.1 + 0.34 * exp(-d * d / 3.0)) * sqrt(T);
+}
+
+/* Compton coefficient per electron, erg/s/K: the cooling is c (T - T_g) n_e */
+double orc_compton_coef(double z, double kB)
+{
+    const double sigma_T = 6.6524587e-25, a_rad = 7.5657e-15, m_e = 9.1093837e-28, c = 2.99792458e10;
+    const double Tg = 2.7255 * (1.0 + z);
+    return 4.0 * sigma_T * a_rad * Tg * Tg * Tg * Tg * kB / (m_e * c);
+}
+
+typedef struct {
+    int on_the_spot;   /* alpha_A = alpha_B, no diffuse field, case-B recombination cooling */
+    int cool_mask;     /* bit 0 recombination, 1 collisional ionization, 2 collisional excitation,
+                          3 free-free, 4 Compton (31: all) */
+    double e_bin[4];   /* mean energy above threshold per photo-ionization in source bin b, erg */
+    double e_diff;     /* the same for the diffuse recombination band, erg */
+    double z;          /* CMB redshift of the Compton term */
+    double kB;         /* Boltzmann constant, erg/K */
+    double T_min, T_max;   /* bracket of the temperature root, K */
+} orc_thermal;
+
+/* Cooling rate C(n, T), erg/s/cm^3, of hydrogen with neutral fraction y. */
+double orc_cooling(const orc_thermal *th, double nH, double y, double T)
+{
+    const double nHI = y * nH, ne = (1.0 - y) * nH, nHII = ne;
+    double c = 0.0;
+    if (th->cool_mask & 1) c += (th->on_the_spot ? orc_cool_rec_B(T) : orc_cool_rec_A(T)) * ne * nHII;
+    if (th->cool_mask & 2) c += orc_cool_ci(T) * ne * nHI;
+    if (th->cool_mask & 4) c += orc_cool_ce(T) * ne * nHI;
+    if (th->cool_mask & 8) c += orc_cool_ff(T) * ne * nHII;
+    if (th->cool_mask & 16) {
+        const double Tg = 2.7255 * (1.0 + th->z);
+        c += orc_compton_coef(th->z, th->kB) * (T - Tg) * ne;
+    }
+    return c;
+}
+
+/* The implicit update of App. C for one cell over dt: the specific energy
+ * u = 3 k_B T (1 + x) n_H / (2 rho) at t + dt solves
+ *   u' = u + (H(n') - C(n', u')) dt / rho,
+ * i.e. with e = rho u = 1.5 k_B T n_H (1 + x) (rho cancels):
+ *   f(T') = 1.5 k_B n_H (1 + x') T' + dt C(n', T') - (e + H' dt) = 0.
+ * The root is bracketed from T (doubling or halving, within [T_min, T_max])
+ * and refined by regula falsi with the Illinois modification (the retained
+ * end's value is halved when the same end is kept twice; Dowell & Jarratt
+ * 1971).  Returns T'. */
+static double energy_f(const orc_thermal *th, double nH, double y1, double A, double B, double dt, double T)
+{
+    return A * T + dt * orc_cooling(th, nH, y1, T) - B;
+}
+
+double orc_energy_step(const orc_thermal *th, double nH, double y0, double T0, double y1, double H1, double dt)
+{
+    const double A = 1.5 * th->kB * nH * (2.0 - y1);
+    const double B = 1.5 * th->kB * nH * (2.0 - y0) * T0 + H1 * dt;
+    double T = T0 < th->T_min ? th->T_min : (T0 > th->T_max ? th->T_max : T0);
+    double f = energy_f(th, nH, y1, A, B, dt, T);
+    if (f == 0.0) return T;
+    double lo, hi, flo, fhi;
+    if (f < 0.0) {
+        lo = T; flo = f; hi = T; fhi = f;
+        while (fhi < 0.0) {
+            if (hi >= th->T_max) return th->T_max;
+            lo = hi; flo = fhi;
+            hi = 2.0 * hi < th->T_max ? 2.0 * hi : th->T_max;
+            fhi = energy_f(th, nH, y1, A, B, dt, hi);
+        }
+    } else {
+        hi = T; fhi = f; lo = T; flo = f;
+        while (flo > 0.0) {
+            if (lo <= th->T_min) return th->T_min;
+            hi = lo; fhi = flo;
+            lo = 0.5 * lo > th->T_min ? 0.5 * lo : th->T_min;
+            flo = energy_f(th, nH, y1, A, B, dt, lo);
+        }
+    }
+    if (flo == 0.0) return lo;
+    if (fhi == 0.0) return hi;
+    int side = 0;
+    double Tm = lo, prev = -1.0;
+    for (int it = 0; it < 200; it++) {
+        Tm = (lo * fhi - hi * flo) / (fhi - flo);
+        if (!(Tm > lo && Tm < hi)) Tm = 0.5 * (lo + hi);
+        if (fabs(Tm - prev) <= 1e-14 * Tm || hi - lo <= 1e-14 * hi) break;
+        prev = Tm;
+        const double fm = energy_f(th, nH, y1, A, B, dt, Tm);
+        if (fm == 0.0) break;
+        if (fm < 0.0) {
+            lo = Tm; flo = fm;
+            if (side == -1) fhi *= 0.5;
+            side = -1;
+        } else {
+            hi = Tm; fhi = fm;
+            if (side == 1) flo *= 0.5;
+            side = 1;
+        }
+    }
+    return Tm;
+}
+
+/* Chemical timestep of App. D at temperature T. */
+static double dtchem_T(double nH, double y, double T, double g, double eps_e, double eps_hi)
+{
+    return dtchem_cell(nH, y, orc_alpha_B(T), orc_gamma_coll(T), g, eps_e, eps_hi);
+}
+
+/* One cell over dt: sub-steps of the chemical timestep; in each, the BDF
+ * update of App. B with alpha_B(T) and Gamma_coll(T) at the sub-step's start,
+ * then the implicit energy update at the new composition.  Heating per
+ * volume H = n_HI (hpt + g_diff e_diff) + (alpha_A - alpha_B)(T) n_e n_HII
+ * e_diff: the photo-heating of the point sources and the plane flux (hpt,
+ * per neutral atom), of the transferred diffuse field, and of the local
+ * recombination photons counted in Gamma^diff by Eq. (gamma_diff). */
+int orc_thermal_cell(const orc_thermal *th, double nH, double y0, double T0, double gpt, double hpt, double gdiff,
+                     double dt, double eps_e, double eps_hi, int max_sub, double *y_out, double *T_out)
+{
+    double y = y0, T = T0, tau = 0.0;
+    int n = 0;
+    const double g = gpt + gdiff;
+    while (tau < dt && n < max_sub) {
+        const double aB = orc_alpha_B(T), gc = orc_gamma_coll(T);
+        const double dal = th->on_the_spot ? 0.0 : orc_alpha_A(T) - aB;
+        const double nHI = y * nH, ne = (1.0 - y) * nH;
+        const double Cc = aB * ne * ne, D = gc * ne + g;
+        double dtc = dtchem_cell(nH, y, aB, gc, g, eps_e, eps_hi);
+        const int last = !(dtc < dt - tau);
+        if (last) dtc = dt - tau;
+        double y1 = (Cc * dtc + nHI) / (1.0 + D * dtc) / nH;
+        if (y1 > 1.0) y1 = 1.0;
+        const double ne1 = (1.0 - y1) * nH;
+        const double H1 = y1 * nH * (hpt + gdiff * th->e_diff) + dal * ne1 * ne1 * th->e_diff;
+        T = orc_energy_step(th, nH, y, T, y1, H1, dtc);
+        y = y1;
+        tau = last ? dt : tau + dtc;
+        n++;
+    }
+    *y_out = y;
+    *T_out = T;
+    return n;
+}
+
+/* Rates of state (y, T): kappa, the emissivity with (alpha_A - alpha_B)(T),
+ * the point sources and plane flux (photo-ionization g and heating h per
+ * neutral atom: the same rates with bin luminosities Q_b E_b), and the
+ * diffuse rate 4 pi G J^in (zero on the spot). */
+static void thermal_rates(const orc_sweep_cfg *cfg, const orc_chem *ch, const orc_thermal *th, const double *nH,
+                          const double *y, const double *T, int nsrc, const double *pos, const double *qb,
+                          const double *qh, int nb, const double *sigma_b, int pl_axis, int pl_dir, double pl_flux,
+                          const double *fb, const double *fh, double G, double *kap, double *kapb, double *eps,
+                          double *gdiff, double *gpt, double *hpt, double *tmp)
+{
+    const long ncell = (long)cfg->nx * cfg->ny * cfg->nz;
+    for (long i = 0; i < ncell; i++) {
+        const double nHI = y[i] * nH[i], ne = (1.0 - y[i]) * nH[i];
+        kap[i] = nHI * ch->sigma0 * ch->dx;
+        const double dal = orc_alpha_A(T[i]) - orc_alpha_B(T[i]);
+        eps[i] = ch->h * ch->nu0 * dal * ne * ne * ch->dx / (4.0 * M_PI * ch->dnu);
+    }
+    if (th->on_the_spot) {
+        for (long i = 0; i < ncell; i++) gdiff[i] = 0.0;
+    } else {
+        orc_sweep_cfg c = *cfg;
+        c.field_form = 1;
+        orc_sweep(&c, kap, eps, gdiff, NULL);
+        for (long i = 0; i < ncell; i++) gdiff[i] *= 4.0 * M_PI * G;
+    }
+    for (int b = 0; b < nb; b++)
+        for (long i = 0; i < ncell; i++) kapb[b * ncell + i] = y[i] * nH[i] * sigma_b[b] * ch->dx;
+    orc_point_sources(cfg->nx, cfg->ny, cfg->nz, nb, kapb, sigma_b, nsrc, pos, qb, ch->dx, cfg->nthreads, gpt);
+    orc_point_sources(cfg->nx, cfg->ny, cfg->nz, nb, kapb, sigma_b, nsrc, pos, qh, ch->dx, cfg->nthreads, hpt);
+    if (pl_flux > 0.0) {
+        orc_plane_source(cfg->nx, cfg->ny, cfg->nz, nb, kapb, sigma_b, pl_axis, pl_dir, fb, tmp);
+        for (long i = 0; i < ncell; i++) gpt[i] += tmp[i];
+        orc_plane_source(cfg->nx, cfg->ny, cfg->nz, nb, kapb, sigma_b, pl_axis, pl_dir, fh, tmp);
+        for (long i = 0; i < ncell; i++) hpt[i] += tmp[i];
+    }
+}
+
+/* Time-dependent mode with the energy equation: as orc_evolve, with the
+ * temperature T carried beside y, the rates and the emissivity taken at
+ * each cell's temperature, and the iteration of every RT step run until
+ * both n_e and u converge (App. D: |x^(i) - x^(i-1)| < eps_iter x^(i) for
+ * x = n_e, u).  Return codes as orc_evolve. */
+int orc_evolve_thermal(const orc_sweep_cfg *cfg, const orc_chem *ch, const orc_thermal *th, const double *nH,
+                       int nsrc, const double *pos, const double *Q, int nb, const double *sigma_b,
+                       const double *frac_b, int pl_axis, int pl_dir, double pl_flux, const orc_evolve_opt *opt,
+                       double t_end, double *y, double *T, int *steps_out, int *iters_out, double *t_out,
+                       double *dt_hist)
+{
+    const long ncell = (long)cfg->nx * cfg->ny * cfg->nz;
+    double *kap = malloc(sizeof(double) * ncell), *kapb = malloc(sizeof(double) * ncell * nb);
+    double *eps = malloc(sizeof(double) * ncell), *gdiff = malloc(sizeof(double) * ncell);
+    double *gpt = malloc(sizeof(double) * ncell), *hpt = malloc(sizeof(double) * ncell);
+    double *tmp = malloc(sizeof(double) * ncell);
+    double *yp = malloc(sizeof(double) * ncell), *Tp = malloc(sizeof(double) * ncell);
+    double *yn = malloc(sizeof(double) * ncell), *Tn = malloc(sizeof(double) * ncell);
+    const int ns = nsrc > 0 ? nsrc : 1;
+    double *qb = malloc(sizeof(double) * ns * nb), *qh = malloc(sizeof(double) * ns * nb);
+    double *fb = malloc(sizeof(double) * nb), *fh = malloc(sizeof(double) * nb);
+    if (!kap || !kapb || !eps || !gdiff || !gpt || !hpt || !tmp || !yp || !Tp || !yn || !Tn || !qb || !qh || !fb ||
+        !fh)
+        return -1;
+    for (int a = 0; a < nsrc; a++)
+        for (int b = 0; b < nb; b++) {
+            qb[a * nb + b] = Q[a] * frac_b[b];
+            qh[a * nb + b] = Q[a] * frac_b[b] * th->e_bin[b];
+        }
+    for (int b = 0; b < nb; b++) {
+        fb[b] = pl_flux * frac_b[b];
+        fh[b] = pl_flux * frac_b[b] * th->e_bin[b];
+    }
+    const double G = orc_band_integral(ch->sigma0, ch->h, ch->nu0, ch->nu0 + ch->dnu);
+    double t = 0.0;
+    int steps = 0, iters = 0, unconverged = 0;
+    while (t < t_end && steps < opt->max_steps) {
+        thermal_rates(cfg, ch, th, nH, y, T, nsrc, pos, qb, qh, nb, sigma_b, pl_axis, pl_dir, pl_flux, fb, fh, G,
+                      kap, kapb, eps, gdiff, gpt, hpt, tmp);
+        double dt;
+        if (opt->dt_fixed > 0.0) {
+            dt = opt->dt_fixed;
+        } else {
+            double m = INFINITY;
+            for (long i = 0; i < ncell; i++) {
+                const double d = dtchem_T(nH[i], y[i], T[i], gpt[i] + gdiff[i], opt->eps_e, opt->eps_hi);
+                if (d < m) m = d;
+            }
+            dt = opt->F * m;
+        }
+        const int last = !(dt < t_end - t);
+        if (last) dt = t_end - t;
+        for (long i = 0; i < ncell; i++) {
+            yp[i] = y[i];
+            Tp[i] = T[i];
+        }
+        int conv = 0;
+        for (int k = 1; k <= opt->max_iter; k++) {
+            iters++;
+            double r = 0.0;
+            for (long i = 0; i < ncell; i++) {
+                orc_thermal_cell(th, nH[i], y[i], T[i], gpt[i], hpt[i], gdiff[i], dt, opt->eps_e, opt->eps_hi,
+                                 opt->max_sub, &yn[i], &Tn[i]);
+                const double ne_new = (1.0 - yn[i]) * nH[i], ne_old = (1.0 - yp[i]) * nH[i];
+                const double re = ne_new > 0.0 ? fabs(ne_new - ne_old) / ne_new : (ne_old > 0.0 ? INFINITY : 0.0);
+                const double u_new = (2.0 - yn[i]) * Tn[i], u_old = (2.0 - yp[i]) * Tp[i];
+                const double ru = fabs(u_new - u_old) / u_new;
+                if (re > r) r = re;
+                if (ru > r) r = ru;
+            }
+            for (long i = 0; i < ncell; i++) {
+                yp[i] = yn[i];
+                Tp[i] = Tn[i];
+            }
+            if (r < opt->eps_iter) {
+                conv = 1;
+                break;
+            }
+            thermal_rates(cfg, ch, th, nH, yp, Tp, nsrc, pos, qb, qh, nb, sigma_b, pl_axis, pl_dir, pl_flux, fb, fh,
+                          G, kap, kapb, eps, gdiff, gpt, hpt, tmp);
+        }
+        if (!conv) unconverged = 1;
+        for (long i = 0; i < ncell; i++) {
+            y[i] = yp[i];
+            T[i] = Tp[i];
+        }
+        if (dt_hist) dt_hist[steps] = dt;
+        t = last ? t_end : t + dt;
+        steps++;
+    }
+    if (steps_out) *steps_out = steps;
+    if (iters_out) *iters_out = iters;
+    if (t_out) *t_out = t;
+    free(kap); free(kapb); free(eps); free(gdiff); free(gpt); free(hpt); free(tmp); free(yp); free(Tp);
+    free(yn); free(Tn); free(qb); free(qh); free(fb); free(fh);
     if (t < t_end) return 2;
     return unconverged ? 1 : 0;
 }
