@@ -510,6 +510,50 @@ def evolve_measure(torch, dev, F=1.0):
     return out
 
 
+def thermal_measure(torch, dev, F=1.0):
+    """Time-dependent mode with the energy equation (App. C) on the paper's
+    Test-1 setup as printed (Sec. 4.1): n_H 1e-3, initial T 100 K, a 1e5 K
+    blackbody source of 5e48 photons/s (4 bins above 13.6 eV) at a corner of a
+    6.6 kpc box, here 64^3 and N_side 4, to 30, 100 and 500 Myr, with the
+    diffuse field and on the spot.  Reports steps, iterations, sweeps, wall
+    time, the ionized-volume radius over R_S and the mean temperature of the
+    ionized gas."""
+    import math
+    from paper_1410_0763_gb300 import art
+    from paper_1410_0763_gb300 import workloads as wl
+    nH0, Q = 1e-3, 5e48
+    case = wl.hii_region(n=64, nside=4, box_kpc=6.6, nH=nH0, Q=Q, source_at="corner")
+    frac, sig, _ = wl.blackbody_bins()
+    dx = case.chem["dx"]
+    rs = 5.4 * wl.KPC                          # the paper's printed Stromgren radius
+    srcs = [(p[0], p[1], p[2], q) for p, q in zip(case.pos, case.Q)]
+    sw = art.ArtSweep(case.nH.shape, case.nside, 1, field_form=art.ART_FIELDS_EPS, dx_cm=dx)
+    sw.set_source_spectrum(sig, frac)
+    nH = torch.as_tensor(case.nH, dtype=torch.float64, device=dev)
+    th = {"e_bin": list(wl.blackbody_heat()), "e_diff": wl.diffuse_band_heat(case.chem)}
+    out = {"workload": "Test-1 setup with the energy equation, 64^3, N_side 4: n_H 1e-3, T0 100 K, 1e5 K "
+                       f"blackbody (4 bins) 5e48 s^-1 at a corner, 6.6 kpc, F = {F}, eps_iter 1e-3"}
+    for label, otsa in (("with_diffuse", 0), ("on_the_spot", 1)):
+        y = torch.as_tensor(case.y0, dtype=torch.float64, device=dev).clone()
+        T = torch.full_like(y, 100.0)
+        t, rows, tot = 0.0, [], {"steps": 0, "iterations": 0, "sweeps": 0, "seconds": 0.0}
+        for t_myr in (30.0, 100.0, 500.0):
+            rep = sw.evolve_thermal(nH, case.chem, dict(th, on_the_spot=otsa), srcs, y, T, t_myr * wl.MYR - t, F=F)
+            t = t_myr * wl.MYR
+            for k in ("steps", "iterations", "sweeps"):
+                tot[k] += int(getattr(rep, k))
+            tot["seconds"] += float(rep.seconds)
+            x = 1 - y
+            vol = 8 * float(torch.sum(x)) * dx ** 3
+            r = (3 * vol / (4 * math.pi)) ** (1 / 3)
+            rows.append({"t_myr": t_myr, "r_ion_over_r_s": round(r / rs, 4),
+                         "mean_T_ionized_K": round(float(torch.sum(T * x) / torch.sum(x)), 1),
+                         "max_T_K": round(float(T.max()), 1)})
+        out[label] = dict(tot, seconds=round(tot["seconds"], 3), radius=rows)
+    sw.close()
+    return out
+
+
 def ablation_measure(torch, dev, reps=3):
     """The paper's ray-grouping comparison (Sec. 5) restated on GB300: the
     thread-per-ray layout of Sec. 3.1 with float atomics against the same
@@ -694,6 +738,7 @@ def run_ours(args, d: Dist):
             extra["rt_ionization_128_plane_flux"] = {"error": str(ex)}
         try:
             extra["time_dependent_64"] = evolve_measure(torch, dev)
+            extra["time_dependent_thermal_64"] = thermal_measure(torch, dev)
         except Exception as ex:  # pragma: no cover
             extra["time_dependent_64"] = {"error": str(ex)}
         try:

@@ -347,7 +347,8 @@ art_status art_iterate_ionization(art_ctx *ctx, const art_chem *chem, const doub
  * non-local rates; the local recombination term of Eq. gamma_diff cancels
  * the ground-state recombinations (alpha_B), and alpha_A == alpha_B is the
  * on-the-spot approximation (no sweep).  The energy equation of App. C is not
- * solved: the temperature stays that of the rate constants.  FP64 chemistry,
+ * solved here: the temperature stays that of the rate constants
+ * (art_evolve_thermal solves it).  FP64 chemistry,
  * one host synchronization per iteration.  nH, y: device [z][y][x] doubles;
  * y is the state at t = 0 on input and at t_end on output.  Errors:
  * ART_E_INVALID, ART_E_NOT_CONVERGED (max_steps before t_end, or a step that
@@ -380,6 +381,66 @@ art_status art_evolve_options_default(art_evolve_options *opt);
 art_status art_evolve_ionization(art_ctx *ctx, const art_chem *chem, const double *nH, const art_source *src,
                                  int n_src, const art_evolve_options *opt, double *y, art_evolve_report *rep,
                                  void *stream);
+
+/*
+ * Energy equation of App. C for the time-dependent mode (art_evolve_thermal).
+ * The paper takes its rate and cooling coefficients from the works of its
+ * rate table without printing them; the library evaluates, T in K,
+ * lambda = 2 * 157807 K / T:
+ *   alpha_A(T), alpha_B(T)       Hui & Gnedin (1997) case-A / case-B fits
+ *   Gamma_coll(T)                Cen (1992) collisional ionization of HI
+ *   recombination cooling        Cen (1992) case A; Hui & Gnedin (1997) case B
+ *   collisional ionization and excitation cooling of HI   Cen (1992)
+ *   free-free cooling            1.42e-27 g_ff sqrt(T) n_e n_HII,
+ *                                g_ff = 1.1 + 0.34 exp(-(5.5 - log10 T)^2 / 3)
+ *   Compton cooling off the CMB  4 sigma_T a T_g^4 k_B (T - T_g) n_e / (m_e c),
+ *                                T_g = 2.7255 (1 + z) K
+ * Photo-heating per volume
+ *   H = n_HI (sum_b Gamma_b e_bin[b] + Gamma^diff_in e_diff)
+ *       + (alpha_A - alpha_B)(T) n_e n_HII e_diff,
+ * the sources' and plane flux's rate per bin times the mean energy above
+ * threshold of a photo-ionization in that bin, the transferred diffuse field,
+ * and the local recombination photons that Eq. gamma_diff counts in
+ * Gamma^diff (their ionizations cancel the ground-state recombinations, their
+ * energy heats).  on_the_spot: alpha_A = alpha_B, no diffuse field and no
+ * diffuse heating, case-B recombination cooling.
+ */
+typedef struct {
+    int32_t on_the_spot;   /* 0 (default): the diffuse field is transferred */
+    int32_t cool_mask;     /* cooling terms on: bit 0 recombination, 1 collisional ionization,
+                              2 collisional excitation, 3 free-free, 4 Compton; default 31 */
+    double e_bin[4];       /* erg per photo-ionization above threshold, per source-spectrum bin */
+    double e_diff;         /* the same for the diffuse recombination band, erg */
+    double z;              /* redshift of the CMB (Compton term), default 0 */
+    double kB;             /* Boltzmann constant, erg/K, default 1.380649e-16 */
+    double T_min, T_max;   /* temperature bracket, K; defaults 10 and 1e9 */
+} art_thermal;
+
+art_status art_thermal_default(art_thermal *th);
+
+/*
+ * The time-dependent mode of art_evolve_ionization with the energy equation
+ * of App. C.  The temperature T (device [z][y][x] doubles, K; the state at
+ * t = 0 on input and at t_end on output) is carried beside y.  In each
+ * chemistry sub-step of a cell: the BDF update of y with alpha_B(T) and
+ * Gamma_coll(T) at the sub-step's start, then the implicit update of the
+ * specific energy u = 3 k_B T (1 + x) n_H / (2 rho) at the new composition,
+ *   u' = u + (H(n') - C(n', u')) dtc / rho
+ * (rho cancels: 1.5 k_B n_H ((1 + x') T' - (1 + x) T) = (H' - C(n', T')) dtc),
+ * whose root T' is bracketed from T within [T_min, T_max] and refined by
+ * regula falsi with the Illinois modification.  The emissivity of the
+ * diffuse field takes (alpha_A - alpha_B)(T) per cell; chem->alphaA,
+ * alphaB and gcoll are not used.  dt_chem is App. D's (n_e and n_HI only);
+ * each RT step iterates until max_cells of |n_e^(i) - n_e^(i-1)| / n_e^(i)
+ * and |u^(i) - u^(i-1)| / u^(i) is below eps_iter (App. D).  Point-source and
+ * plane-flux heating come from the same kernels as their rates (FP32, the
+ * sum over sources in FP64).  Errors: as art_evolve_ionization, and
+ * ART_E_INVALID for a null th or T, kB <= 0, 0 < T_min < T_max violated, a
+ * negative or non-finite energy, or an initial T outside [T_min, T_max].
+ */
+art_status art_evolve_thermal(art_ctx *ctx, const art_chem *chem, const art_thermal *th, const double *nH,
+                              const art_source *src, int n_src, const art_evolve_options *opt, double *y,
+                              double *T, art_evolve_report *rep, void *stream);
 
 /*
  * Source spectrum of art_iterate_ionization on this context (App. A with

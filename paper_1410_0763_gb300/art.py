@@ -60,6 +60,12 @@ class ArtEvolveReport(C.Structure):
                 ("seconds", C.c_double)]
 
 
+class ArtThermal(C.Structure):
+    _fields_ = [("on_the_spot", C.c_int32), ("cool_mask", C.c_int32), ("e_bin", C.c_double * 4),
+                ("e_diff", C.c_double), ("z", C.c_double), ("kB", C.c_double), ("T_min", C.c_double),
+                ("T_max", C.c_double)]
+
+
 class ArtSource(C.Structure):
     _fields_ = [("x", C.c_double), ("y", C.c_double), ("z", C.c_double), ("Q", C.c_double)]
 
@@ -143,6 +149,12 @@ def load() -> C.CDLL:
         lib.art_ablation_sweep.restype = C.c_int
         lib.art_evolve_options_default.argtypes = [C.POINTER(ArtEvolveOptions)]
         lib.art_evolve_options_default.restype = C.c_int
+        lib.art_thermal_default.argtypes = [C.POINTER(ArtThermal)]
+        lib.art_thermal_default.restype = C.c_int
+        lib.art_evolve_thermal.argtypes = [P, C.POINTER(ArtChem), C.POINTER(ArtThermal), P, C.POINTER(ArtSource),
+                                           C.c_int, C.POINTER(ArtEvolveOptions), P, P, C.POINTER(ArtEvolveReport),
+                                           P]
+        lib.art_evolve_thermal.restype = C.c_int
         lib.art_evolve_ionization.argtypes = [P, C.POINTER(ArtChem), P, C.POINTER(ArtSource), C.c_int,
                                               C.POINTER(ArtEvolveOptions), P, C.POINTER(ArtEvolveReport), P]
         lib.art_evolve_ionization.restype = C.c_int
@@ -503,6 +515,42 @@ class ArtSweep:
         ch = self._chem(chem)
         st = load().art_evolve_ionization(self._ctx, C.byref(ch), C.c_void_p(npp), src, len(sources), C.byref(o),
                                           C.c_void_p(yp), C.byref(rep), C.c_void_p(_stream(stream)))
+        _check(self._ctx, st)
+        return rep
+
+    def evolve_thermal(self, nH, chem: dict, thermal: dict, sources, y, T, t_end, stream=None, **opts):
+        """Time-dependent mode with the energy equation (App. B-D); nH, y, T: device FP64 [z][y][x],
+        y and T updated in place.  thermal: on_the_spot, cool_mask, e_bin (list, erg), e_diff (erg), z,
+        kB, T_min, T_max (library defaults for the keys left out).  opts as `evolve`.  Returns the
+        report; raises ArtError unless t_end was reached with every step converged."""
+        npp, nd_, _n = _ptr(nH, np.float64, self.ncell)
+        yp, yd, _y = _ptr(y, np.float64, self.ncell)
+        tp, td, _t = _ptr(T, np.float64, self.ncell)
+        if not (nd_ and yd and td):
+            raise TypeError("evolve_thermal takes device buffers")
+        o = ArtEvolveOptions()
+        load().art_evolve_options_default(C.byref(o))
+        o.t_end = float(t_end)
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, type(getattr(o, k))(v))
+        th = ArtThermal()
+        load().art_thermal_default(C.byref(th))
+        for k, v in thermal.items():
+            if k == "e_bin":
+                e = [float(x) for x in v] + [0.0] * 4
+                th.e_bin = (C.c_double * 4)(*e[:4])
+            elif hasattr(th, k):
+                setattr(th, k, type(getattr(th, k))(v))
+            else:
+                raise TypeError(f"unknown thermal parameter {k}")
+        src = _sources(sources)
+        rep = ArtEvolveReport()
+        ch = self._chem(chem)
+        st = load().art_evolve_thermal(self._ctx, C.byref(ch), C.byref(th), C.c_void_p(npp), src, len(sources),
+                                       C.byref(o), C.c_void_p(yp), C.c_void_p(tp), C.byref(rep),
+                                       C.c_void_p(_stream(stream)))
         _check(self._ctx, st)
         return rep
 

@@ -791,7 +791,8 @@ art_status art_destroy(art_ctx *ctx)
     void *ptrs[] = {ctx->d_field, ctx->d_plane[0], ctx->d_plane[1], ctx->d_jpart, ctx->d_segs, ctx->d_dirs,
                     ctx->d_classes, ctx->d_work, ctx->d_counter, ctx->d_gridinfo, ctx->d_stage, ctx->d_out,
                     ctx->d_flag, ctx->it.nH, ctx->it.y, ctx->it.y0, ctx->it.gpt, ctx->it.kap, ctx->it.eps,
-                    ctx->it.jin, ctx->it.jsur, ctx->it.resid, ctx->it.src, ctx->it.yit, ctx->it.evo};
+                    ctx->it.jin, ctx->it.jsur, ctx->it.resid, ctx->it.src, ctx->it.yit, ctx->it.evo,
+                    ctx->it.hpt, ctx->it.Tit};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *sur[] = {ctx->sur.kc, ctx->sur.ec, ctx->sur.jc, ctx->sur.o, ctx->sur.eref, ctx->sur.nHc, ctx->sur.yc};

@@ -20,6 +20,8 @@ struct art_iter_bufs {
     double *src = nullptr;                                // packed point sources
     double *yit = nullptr;                                // time-dependent mode: the iterate at t + dt
     unsigned long long *evo = nullptr;                    // [3]: residual, min dt_chem (double bits), overflows
+    float *hpt = nullptr;                                 // energy equation: photo-heating per neutral atom
+    double *Tit = nullptr;                                // energy equation: the temperature iterate at t + dt
 };
 
 // One grid of a context (a context holds one grid, or a batch of them).

@@ -1,7 +1,8 @@
 // art_ion.cu -- point sources (long characteristics with the photon-conserving
 // rate of App. A), the FP64 hydrogen ionization balance (App. B, equilibrium
-// limit) and the RT / balance fixed-point iteration (App. D) of Tanaka et al.
-// (2014), on top of the diffuse-radiation sweep.
+// limit), the RT / balance fixed-point iteration (App. D) and the
+// time-dependent mode with and without the energy equation (App. B-D) of
+// Tanaka et al. (2014), on top of the diffuse-radiation sweep.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -61,6 +62,8 @@ struct PtArgs {
     float *gamma;
     int scaled;           // kappa_b = kappa * kscale[b] (one field for all bins, one tau to march)
     float kscale[4];
+    float *heat;          // photo-heating per neutral atom, sum_b Gamma_b ebin[b] (null: not computed)
+    float ebin[4];        // erg above threshold per photo-ionization in bin b
 };
 
 constexpr int kMaxBins = 4;   // point-source kernels are compiled for 1-4 bins
@@ -125,7 +128,7 @@ __global__ void __launch_bounds__(128) point_source_kernel(const PtArgs p)
     const int dims[3] = {p.nx, p.ny, p.nz};
     constexpr int U = PT_UNROLL;
     constexpr int NK = SCALED ? 1 : NB;   // kappa fields marched
-    double g = 0.0;                       // the sum over sources, in index order, in FP64
+    double g = 0.0, h = 0.0;              // the sums over sources, in index order, in FP64
     for (int a = 0; a < p.nsrc; ++a) {
         const PtSrc S = p.src[a];
         // source -> cell centre: integer part exact, plus the fractions
@@ -195,17 +198,21 @@ __global__ void __launch_bounds__(128) point_source_kernel(const PtArgs p)
                 rout = fminf(rout, fmaxf(t1, t2));
             }
             const float den = rout * rout + rout * rin + rin * rin;
-            float ga = 0.0f;
+            float ga = 0.0f, ha = 0.0f;
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
                 const float kb = SCALED ? p.kappa[target] * p.kscale[b] : p.kappa[(long long)b * p.ncell + target];
                 const float tb = SCALED ? tau[0] * p.kscale[b] : tau[b];
-                ga += S.coef[b] * __expf(-tb) * pt_phi(kb * (rout - rin)) / den;
+                const float rb = S.coef[b] * __expf(-tb) * pt_phi(kb * (rout - rin)) / den;
+                ga += rb;
+                ha = fmaf(rb, p.ebin[b], ha);
             }
             g += (double)ga;
+            h += (double)ha;
         }
     }
     p.gamma[target] = (float)g;
+    if (p.heat) p.heat[target] = (float)h;
 }
 
 // ---------------------------------------------------------------------------
@@ -226,8 +233,10 @@ struct PlaneArgs {
     float coef[4];        // F_b sigma_b
     int scaled;
     float kscale[4];
-    int accumulate;       // add to gamma instead of overwriting it
+    int accumulate;       // add to gamma (and heat) instead of overwriting it
     float *gamma;
+    float *heat;          // photo-heating per neutral atom, sum_b Gamma_b ebin[b] (null: not computed)
+    float ebin[4];
 };
 
 template <int NB, bool SCALED> __global__ void __launch_bounds__(128) plane_source_kernel(const PlaneArgs p)
@@ -249,23 +258,29 @@ template <int NB, bool SCALED> __global__ void __launch_bounds__(128) plane_sour
         float kc[NK];
 #pragma unroll
         for (int b = 0; b < NK; ++b) kc[b] = __ldg(p.kappa + (long long)b * p.ncell + ci);
-        float g = 0.0f;
+        float g = 0.0f, h = 0.0f;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             const float kb = SCALED ? kc[0] * p.kscale[b] : kc[b];
             const float tb = SCALED ? tau[0] * p.kscale[b] : tau[b];
-            g += p.coef[b] * __expf(-tb) * pt_phi(kb);
+            const float rb = p.coef[b] * __expf(-tb) * pt_phi(kb);
+            g += rb;
+            h = fmaf(rb, p.ebin[b], h);
         }
 #pragma unroll
         for (int b = 0; b < NK; ++b) tau[b] += kc[b];
         p.gamma[ci] = p.accumulate ? p.gamma[ci] + g : g;
+        if (p.heat) p.heat[ci] = p.accumulate ? p.heat[ci] + h : h;
     }
 }
 
 art_status launch_plane(art_ctx *ctx, const float *kappa, int nbins, int axis, int dir, const double *coef,
-                        float *gamma, int accumulate, cudaStream_t st, const float *kscale = nullptr)
+                        float *gamma, int accumulate, cudaStream_t st, const float *kscale = nullptr,
+                        float *heat = nullptr, const double *ebin = nullptr)
 {
     PlaneArgs a;
+    a.heat = heat;
+    for (int b = 0; b < 4; ++b) a.ebin[b] = heat && b < nbins ? (float)ebin[b] : 0.0f;
     a.kappa = kappa;
     a.ncell = ctx->ncell;
     a.nx = ctx->grid.nx;
@@ -323,7 +338,26 @@ struct BalArgs {
     unsigned long long *resid;
     long long ncell;
     int solve;                  // 0: only derive kappa, eps from y
+    const double *T;            // non-null: eps takes (alpha_A - alpha_B)(T) per cell times eps_base
+    double eps_base;            // G h nu0 dx / dnu
 };
+
+// Temperature fits of the energy equation (App. C), T in K; sources in art.h.
+__device__ __forceinline__ double th_lambda(double T) { return 2.0 * 157807.0 / T; }
+__device__ __forceinline__ double th_alpha_A(double T)
+{
+    const double l = th_lambda(T);
+    return 1.269e-13 * pow(l, 1.503) / pow(1.0 + pow(l / 0.522, 0.470), 1.923);
+}
+__device__ __forceinline__ double th_alpha_B(double T)
+{
+    const double l = th_lambda(T);
+    return 2.753e-14 * pow(l, 1.500) / pow(1.0 + pow(l / 2.740, 0.407), 2.242);
+}
+__device__ __forceinline__ double th_gamma_coll(double T)
+{
+    return 5.85e-11 * sqrt(T) * exp(-157809.1 / T) / (1.0 + sqrt(T / 1e5));
+}
 
 __global__ void balance_kernel(const BalArgs p)
 {
@@ -346,7 +380,8 @@ __global__ void balance_kernel(const BalArgs p)
             p.y[i] = y;
         }
         p.kap[i] = (float)(y * nH * p.kap_coef);
-        p.eps[i] = (float)(p.eps_coef * (x * nH) * (x * nH));
+        const double ec = p.T ? p.eps_base * (th_alpha_A(p.T[i]) - th_alpha_B(p.T[i])) : p.eps_coef;
+        p.eps[i] = (float)(ec * (x * nH) * (x * nH));
     }
     if (!p.solve) return;
     // block max, then one atomic max on the bit pattern (r >= 0)
@@ -440,9 +475,12 @@ template <typename IDX> void launch_points_t(const PtArgs &a, unsigned nb, int n
 // Point-source rates into gamma (device), kappa per bin on the device, or
 // (kscale != null) one kappa field scaled per bin.
 art_status launch_points(art_ctx *ctx, const float *kappa, int nbins, const PtSrc *d_src, int n_src, float *gamma,
-                         cudaStream_t st, const float *kscale = nullptr)
+                         cudaStream_t st, const float *kscale = nullptr, float *heat = nullptr,
+                         const double *ebin = nullptr)
 {
     PtArgs a;
+    a.heat = heat;
+    for (int b = 0; b < 4; ++b) a.ebin[b] = heat && b < nbins ? (float)ebin[b] : 0.0f;
     a.kappa = kappa;
     a.src = d_src;
     a.nsrc = n_src;
@@ -534,6 +572,8 @@ BalArgs balance_args(art_ctx *ctx, const art_chem *ch, const double *nH, double 
     ba.resid = B.resid;
     ba.ncell = ctx->ncell;
     ba.solve = 0;
+    ba.T = nullptr;
+    ba.eps_base = G * ch->h * ch->nu0 * ctx->grid.dx_cm / ch->dnu;
     return ba;
 }
 
@@ -981,6 +1021,337 @@ art_status evolve_impl(art_ctx *ctx, const art_chem *ch, const double *nH, const
     return ART_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Time-dependent mode with the energy equation (App. C).  Per cell and
+// chemistry sub-step: the BDF update of App. B with alpha_B(T), Gamma_coll(T)
+// at the sub-step's start, then the implicit update of the specific energy at
+// the new composition; with e = rho u = 1.5 k_B T n_H (1 + x) it is the root T'
+// of
+//   f(T') = 1.5 k_B n_H (1 + x') T' + dtc C(n', T') - (e + H' dtc),
+// bracketed from T (doubling or halving within [T_min, T_max]) and refined by
+// regula falsi with the Illinois modification (the value kept at an end that
+// survives twice is halved).
+// ---------------------------------------------------------------------------
+struct ThermParams {
+    int otsa, cool_mask;
+    double e_diff, kB, T_min, T_max;
+    double compton, T_g;         // Compton coefficient per electron (erg/s/K) and CMB temperature
+};
+
+__device__ __forceinline__ double th_cooling(const ThermParams &q, double nH, double y, double T)
+{
+    const double nHI = y * nH, ne = (1.0 - y) * nH;
+    const double sT = sqrt(T), cden = 1.0 + sqrt(T / 1e5);
+    double c = 0.0;
+    if (q.cool_mask & 1) {
+        double rc;
+        if (q.otsa) {
+            const double l = th_lambda(T);
+            rc = 3.435e-30 * T * pow(l, 1.970) / pow(1.0 + pow(l / 2.250, 0.376), 3.720);
+        } else {
+            rc = 8.70e-27 * sT * pow(T / 1e3, -0.2) / (1.0 + pow(T / 1e6, 0.7));
+        }
+        c += rc * ne * ne;
+    }
+    if (q.cool_mask & 2) c += 1.27e-21 * sT * exp(-157809.1 / T) / cden * ne * nHI;
+    if (q.cool_mask & 4) c += 7.50e-19 * exp(-118348.0 / T) / cden * ne * nHI;
+    if (q.cool_mask & 8) {
+        const double d = 5.5 - log10(T);
+        c += 1.42e-27 * (1.1 + 0.34 * exp(-d * d / 3.0)) * sT * ne * ne;
+    }
+    if (q.cool_mask & 16) c += q.compton * (T - q.T_g) * ne;
+    return c;
+}
+
+__device__ double th_energy_step(const ThermParams &q, double nH, double y0, double T0, double y1, double H1,
+                                 double dt)
+{
+    const double A = 1.5 * q.kB * nH * (2.0 - y1);
+    const double B = 1.5 * q.kB * nH * (2.0 - y0) * T0 + H1 * dt;
+    auto f = [&](double T) { return A * T + dt * th_cooling(q, nH, y1, T) - B; };
+    const double T = fmin(fmax(T0, q.T_min), q.T_max);
+    const double fT = f(T);
+    if (fT == 0.0) return T;
+    double lo = T, hi = T, flo = fT, fhi = fT;
+    if (fT < 0.0) {
+        while (fhi < 0.0) {   // at most log2(T_max / T_min) doublings
+            if (hi >= q.T_max) return q.T_max;
+            lo = hi;
+            flo = fhi;
+            hi = fmin(2.0 * hi, q.T_max);
+            fhi = f(hi);
+        }
+    } else {
+        while (flo > 0.0) {
+            if (lo <= q.T_min) return q.T_min;
+            hi = lo;
+            fhi = flo;
+            lo = fmax(0.5 * lo, q.T_min);
+            flo = f(lo);
+        }
+    }
+    if (flo == 0.0) return lo;
+    if (fhi == 0.0) return hi;
+    int side = 0;
+    double Tm = lo, prev = -1.0;
+    for (int it = 0; it < 200; ++it) {
+        Tm = (lo * fhi - hi * flo) / (fhi - flo);
+        if (!(Tm > lo && Tm < hi)) Tm = 0.5 * (lo + hi);
+        if (fabs(Tm - prev) <= 1e-14 * Tm || hi - lo <= 1e-14 * hi) break;
+        prev = Tm;
+        const double fm = f(Tm);
+        if (fm == 0.0) break;
+        if (fm < 0.0) {
+            lo = Tm;
+            flo = fm;
+            if (side == -1) fhi *= 0.5;
+            side = -1;
+        } else {
+            hi = Tm;
+            fhi = fm;
+            if (side == 1) flo *= 0.5;
+            side = 1;
+        }
+    }
+    return Tm;
+}
+
+struct ThermArgs {
+    const double *nH;
+    const float *gpt, *hpt, *gdiff;   // rates and heating per neutral atom
+    const double *y_t, *T_t;          // state at t
+    double *y, *T;                    // in: previous iterate at t + dt; out: the new one
+    double dt, eps_e, eps_hi;
+    int max_sub;
+    long long ncell;
+    unsigned long long *evo;          // as ChemArgs
+    int mode;                         // 0: min dt_chem of the state at t; 1: chemistry and energy over dt
+    ThermParams q;
+};
+
+__global__ void __launch_bounds__(256) thermal_kernel(const ThermArgs p)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in = i < p.ncell;
+    if (p.mode == 0) {
+        double d = INFINITY;
+        if (in) {
+            const double T = p.T_t[i];
+            d = dtchem_of(p.nH[i], p.y_t[i], th_alpha_B(T), th_gamma_coll(T), (double)p.gpt[i] + (double)p.gdiff[i],
+                          p.eps_e, p.eps_hi);
+        }
+        block_reduce_bits((unsigned long long)__double_as_longlong(d), false, p.evo + 1);
+        return;
+    }
+    double r = 0.0;
+    if (in) {
+        const double nH = p.nH[i], gd = (double)p.gdiff[i];
+        const double g = (double)p.gpt[i] + gd, hpt = (double)p.hpt[i];
+        double y = p.y_t[i], T = p.T_t[i], tau = 0.0;
+        int n = 0;
+        while (tau < p.dt && n < p.max_sub) {
+            const double aB = th_alpha_B(T), gc = th_gamma_coll(T);
+            const double dal = p.q.otsa ? 0.0 : th_alpha_A(T) - aB;
+            const double nHI = y * nH, ne = (1.0 - y) * nH;
+            const double C = aB * ne * ne, D = gc * ne + g;
+            double dtc = dtchem_of(nH, y, aB, gc, g, p.eps_e, p.eps_hi);
+            const bool last = !(dtc < p.dt - tau);
+            if (last) dtc = p.dt - tau;
+            const double y1 = fmin((C * dtc + nHI) / (1.0 + D * dtc) / nH, 1.0);
+            const double ne1 = (1.0 - y1) * nH;
+            const double H1 = y1 * nH * (hpt + gd * p.q.e_diff) + dal * ne1 * ne1 * p.q.e_diff;
+            T = th_energy_step(p.q, nH, y, T, y1, H1, dtc);
+            y = y1;
+            tau = last ? p.dt : tau + dtc;
+            ++n;
+        }
+        if (tau < p.dt) atomicAdd(p.evo + 2, 1ull);
+        const double ne_new = (1.0 - y) * nH, ne_old = (1.0 - p.y[i]) * nH;
+        const double re = ne_new > 0.0 ? fabs(ne_new - ne_old) / ne_new : (ne_old > 0.0 ? INFINITY : 0.0);
+        const double u_new = (2.0 - y) * T, u_old = (2.0 - p.y[i]) * p.T[i];
+        r = fmax(re, fabs(u_new - u_old) / u_new);
+        p.y[i] = y;
+        p.T[i] = T;
+    }
+    block_reduce_bits((unsigned long long)__double_as_longlong(r), true, p.evo);
+}
+
+__global__ void temperature_check_kernel(const double *__restrict__ T, long long n, double lo, double hi,
+                                         unsigned long long *__restrict__ bad)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && !(T[i] >= lo && T[i] <= hi)) atomicAdd(bad, 1ull);
+}
+
+art_status evolve_thermal_impl(art_ctx *ctx, const art_chem *ch, const art_thermal *th, const double *nH,
+                               const art_source *src, int n_src, const art_evolve_options *o, double *y, double *T,
+                               art_evolve_report *rep, cudaStream_t st)
+{
+    if (!ctx) return ART_E_INVALID;
+    art_status s = check_iteration_context(ctx, ch, "art_evolve_thermal");
+    if (s != ART_OK) return s;
+    if (!nH || !y || !T || !o || !th || (n_src > 0 && !src) || n_src < 0 || !(o->t_end >= 0.0) ||
+        !std::isfinite(o->t_end) || !(o->F > 0.0) || !(o->eps_iter > 0.0) || !(o->eps_e >= 0.0) ||
+        !(o->eps_hi >= 0.0) || !(o->eps_e + o->eps_hi > 0.0) || !(o->dt_fixed >= 0.0) || o->max_steps < 1 ||
+        o->max_iter < 1 || o->max_sub < 1)
+        return art_fail(ctx, ART_E_INVALID, "art_evolve_thermal: bad argument");
+    if (!(th->kB > 0.0) || !(th->T_min > 0.0) || !(th->T_max > th->T_min) || !std::isfinite(th->T_max) ||
+        !(th->e_diff >= 0.0) || !std::isfinite(th->e_diff) || !std::isfinite(th->z) || th->z <= -1.0)
+        return art_fail(ctx, ART_E_INVALID, "art_evolve_thermal: bad thermal parameters");
+    for (int b = 0; b < 4; ++b)
+        if (!(th->e_bin[b] >= 0.0) || !std::isfinite(th->e_bin[b]))
+            return art_fail(ctx, ART_E_INVALID, "art_evolve_thermal: bad bin energy");
+    const auto t0 = std::chrono::steady_clock::now();
+    const long long n = ctx->ncell;
+    art_iter_bufs &B = ctx->it;
+    if ((s = ensure(ctx, &B.gpt, n)) != ART_OK || (s = ensure(ctx, &B.kap, n)) != ART_OK ||
+        (s = ensure(ctx, &B.eps, n)) != ART_OK || (s = ensure(ctx, &B.jin, n)) != ART_OK ||
+        (s = ensure(ctx, &B.yit, n)) != ART_OK || (s = ensure(ctx, &B.evo, 3)) != ART_OK ||
+        (s = ensure(ctx, &B.hpt, n)) != ART_OK || (s = ensure(ctx, &B.Tit, n)) != ART_OK)
+        return s;
+    const int nt = 256;
+    const unsigned nb = (unsigned)((n + nt - 1) / nt);
+    ICK(ctx, cudaMemsetAsync(B.evo, 0, 3 * sizeof(unsigned long long), st));
+    temperature_check_kernel<<<nb, nt, 0, st>>>(T, n, th->T_min, th->T_max, B.evo + 2);
+    ICK(ctx, cudaGetLastError());
+    unsigned long long nbad = 0;
+    ICK(ctx, cudaMemcpyAsync(&nbad, B.evo + 2, sizeof(nbad), cudaMemcpyDeviceToHost, st));
+    ICK(ctx, cudaStreamSynchronize(st));
+    if (nbad) return art_fail(ctx, ART_E_INVALID, "art_evolve_thermal: initial temperature outside [T_min, T_max]");
+
+    const int nbp = ctx->spec_bins > 0 ? ctx->spec_bins : 1;
+    std::vector<double> sig(nbp), frac(nbp), ebin(nbp);
+    std::vector<float> kscale(nbp);
+    for (int b = 0; b < nbp; ++b) {
+        sig[b] = ctx->spec_bins > 0 ? ctx->spec_sigma[b] : ch->sigma0;
+        frac[b] = ctx->spec_bins > 0 ? ctx->spec_frac[b] : 1.0;
+        kscale[b] = (float)(sig[b] / ch->sigma0);
+        ebin[b] = th->e_bin[b];
+    }
+    double plane_coef[4] = {0, 0, 0, 0};
+    for (int b = 0; b < nbp; ++b) plane_coef[b] = ctx->plane_flux * frac[b] * sig[b];
+    std::vector<PtSrc> h_src;
+    if ((s = pack_sources(ctx, src, n_src, nullptr, frac.data(), sig.data(), nbp, h_src)) != ART_OK) return s;
+    if ((s = source_buffer(ctx, n_src)) != ART_OK) return s;
+    const PtSrc *d_src = reinterpret_cast<const PtSrc *>(B.src);
+    ICK(ctx, cudaMemcpyAsync(B.src, h_src.data(), h_src.size() * sizeof(PtSrc), cudaMemcpyHostToDevice, st));
+    const bool otsa = th->on_the_spot != 0;
+    if (otsa) ICK(ctx, cudaMemsetAsync(B.jin, 0, n * sizeof(float), st));
+
+    // rates and heating of state (ys, Ts) into B.gpt, B.hpt (+ plane) and B.jin
+    int sweeps = 0;
+    auto rates = [&](double *ys, double *Ts) -> art_status {
+        BalArgs ba = balance_args(ctx, ch, nH, ys);
+        ba.T = Ts;
+        balance_kernel<<<nb, nt, 0, st>>>(ba);   // kappa, eps of the state
+        ICK(ctx, cudaGetLastError());
+        art_status r = launch_points(ctx, B.kap, nbp, d_src, n_src, B.gpt, st, kscale.data(), B.hpt, ebin.data());
+        if (r != ART_OK) return r;
+        if (ctx->plane_flux > 0.0 &&
+            (r = launch_plane(ctx, B.kap, nbp, ctx->plane_axis, ctx->plane_dir, plane_coef, B.gpt, 1, st,
+                              kscale.data(), B.hpt, ebin.data())) != ART_OK)
+            return r;
+        if (!otsa) {
+            if ((r = art_internal_layout(ctx, B.kap, B.eps, st)) != ART_OK) return r;
+            if ((r = art_internal_sweep(ctx, nullptr, B.jin, nullptr, st)) != ART_OK) return r;
+            ++sweeps;
+        }
+        return ART_OK;
+    };
+    ThermArgs ta;
+    ta.nH = nH;
+    ta.gpt = B.gpt;
+    ta.hpt = B.hpt;
+    ta.gdiff = B.jin;
+    ta.y_t = y;
+    ta.T_t = T;
+    ta.y = B.yit;
+    ta.T = B.Tit;
+    ta.eps_e = o->eps_e;
+    ta.eps_hi = o->eps_hi;
+    ta.max_sub = o->max_sub;
+    ta.ncell = n;
+    ta.evo = B.evo;
+    ta.q.otsa = otsa ? 1 : 0;
+    ta.q.cool_mask = th->cool_mask;
+    ta.q.e_diff = otsa ? 0.0 : th->e_diff;
+    ta.q.kB = th->kB;
+    ta.q.T_min = th->T_min;
+    ta.q.T_max = th->T_max;
+    {
+        // Compton cooling per electron: 4 sigma_T a T_g^4 k_B / (m_e c)
+        const double sigma_T = 6.6524587e-25, a_rad = 7.5657e-15, m_e = 9.1093837e-28, c = 2.99792458e10;
+        ta.q.T_g = 2.7255 * (1.0 + th->z);
+        ta.q.compton = 4.0 * sigma_T * a_rad * std::pow(ta.q.T_g, 4.0) * th->kB / (m_e * c);
+    }
+    double t = 0.0, dt_min = INFINITY, dt_max = 0.0;
+    int steps = 0, iters = 0, unconverged = 0;
+    unsigned long long overflow = 0;
+    while (t < o->t_end && steps < o->max_steps) {
+        if ((s = rates(y, T)) != ART_OK) return s;
+        double dt = o->dt_fixed;
+        if (!(dt > 0.0)) {
+            const unsigned long long inf_bits = 0x7ff0000000000000ull;
+            ICK(ctx, cudaMemcpyAsync(B.evo + 1, &inf_bits, sizeof(inf_bits), cudaMemcpyHostToDevice, st));
+            ta.mode = 0;
+            thermal_kernel<<<nb, nt, 0, st>>>(ta);
+            ICK(ctx, cudaGetLastError());
+            unsigned long long bits = 0;
+            ICK(ctx, cudaMemcpyAsync(&bits, B.evo + 1, sizeof(bits), cudaMemcpyDeviceToHost, st));
+            ICK(ctx, cudaStreamSynchronize(st));
+            double m;
+            std::memcpy(&m, &bits, sizeof(m));
+            dt = o->F * m;
+        }
+        const bool last = !(dt < o->t_end - t);
+        if (last) dt = o->t_end - t;
+        ta.dt = dt;
+        ta.mode = 1;
+        ICK(ctx, cudaMemcpyAsync(B.yit, y, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        ICK(ctx, cudaMemcpyAsync(B.Tit, T, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        int conv = 0;
+        for (int k = 1; k <= o->max_iter; ++k) {
+            ++iters;
+            ICK(ctx, cudaMemsetAsync(B.evo, 0, sizeof(unsigned long long), st));
+            thermal_kernel<<<nb, nt, 0, st>>>(ta);
+            ICK(ctx, cudaGetLastError());
+            unsigned long long bits = 0;
+            ICK(ctx, cudaMemcpyAsync(&bits, B.evo, sizeof(bits), cudaMemcpyDeviceToHost, st));
+            ICK(ctx, cudaStreamSynchronize(st));
+            double r;
+            std::memcpy(&r, &bits, sizeof(r));
+            if (r < o->eps_iter) {
+                conv = 1;
+                break;
+            }
+            if ((s = rates(B.yit, B.Tit)) != ART_OK) return s;
+        }
+        if (!conv) unconverged = 1;
+        ICK(ctx, cudaMemcpyAsync(y, B.yit, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        ICK(ctx, cudaMemcpyAsync(T, B.Tit, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        dt_min = std::min(dt_min, dt);
+        dt_max = std::max(dt_max, dt);
+        t = last ? o->t_end : t + dt;
+        ++steps;
+    }
+    ICK(ctx, cudaMemcpyAsync(&overflow, B.evo + 2, sizeof(overflow), cudaMemcpyDeviceToHost, st));
+    ICK(ctx, cudaStreamSynchronize(st));
+    if (rep) {
+        rep->steps = steps;
+        rep->iterations = iters;
+        rep->sweeps = sweeps;
+        rep->converged = !unconverged;
+        rep->sub_overflow = (long long)overflow;
+        rep->t = t;
+        rep->dt_min = steps ? dt_min : 0.0;
+        rep->dt_max = dt_max;
+        rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (t < o->t_end) return art_fail(ctx, ART_E_NOT_CONVERGED, "art_evolve_thermal: max_steps before t_end");
+    if (unconverged) return art_fail(ctx, ART_E_NOT_CONVERGED, "art_evolve_thermal: a step reached max_iter");
+    return ART_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1013,6 +1384,27 @@ art_status art_evolve_ionization(art_ctx *ctx, const art_chem *ch, const double 
                                  void *stream)
 {
     return evolve_impl(ctx, ch, nH, src, n_src, opt, y, rep, static_cast<cudaStream_t>(stream));
+}
+
+art_status art_thermal_default(art_thermal *th)
+{
+    if (!th) return ART_E_INVALID;
+    th->on_the_spot = 0;
+    th->cool_mask = 31;
+    for (int b = 0; b < 4; ++b) th->e_bin[b] = 0.0;
+    th->e_diff = 0.0;
+    th->z = 0.0;
+    th->kB = 1.380649e-16;
+    th->T_min = 10.0;
+    th->T_max = 1e9;
+    return ART_OK;
+}
+
+art_status art_evolve_thermal(art_ctx *ctx, const art_chem *ch, const art_thermal *th, const double *nH,
+                              const art_source *src, int n_src, const art_evolve_options *opt, double *y, double *T,
+                              art_evolve_report *rep, void *stream)
+{
+    return evolve_thermal_impl(ctx, ch, th, nH, src, n_src, opt, y, T, rep, static_cast<cudaStream_t>(stream));
 }
 
 art_status art_set_plane_source(art_ctx *ctx, int axis, int dir, double flux)

@@ -205,6 +205,28 @@ def blackbody_bins(T: float = 1e5, edges_ev=(13.6, 24.6, 54.4, 100.0, 500.0), n_
     return frac, np.array(sig), nu_edges
 
 
+def blackbody_heat(T: float = 1e5, edges_ev=(13.6, 24.6, 54.4, 100.0, 500.0), n_quad: int = 4000):
+    """Mean energy above the HI threshold (erg) of a photo-ionization by each bin of a
+    blackbody of temperature T (the bins of `blackbody_bins`):
+    e_b = int_b sigma n_nu (h nu - h nu0) / int_b sigma n_nu."""
+    ev = 1.602176634e-12
+    nu_edges = np.array(edges_ev) * ev / H_PLANCK
+    out = []
+    for lo, hi in zip(nu_edges[:-1], nu_edges[1:]):
+        nu = np.linspace(lo, hi, n_quad)
+        w = SIGMA0 * (nu / NU0) ** -3 * nu ** 2 / np.expm1(H_PLANCK * nu / (K_BOLTZ * T))
+        out.append(np.trapezoid(w * H_PLANCK * (nu - NU0), nu) / np.trapezoid(w, nu))
+    return np.array(out)
+
+
+def diffuse_band_heat(chem: dict, n_quad: int = 4000) -> float:
+    """Mean energy above threshold (erg) of a photo-ionization by the recombination
+    band [nu0, nu0 + dnu] with a flat J_nu: int sigma/(h nu) (h nu - h nu0) / int sigma/(h nu)."""
+    nu = np.linspace(chem["nu0"], chem["nu0"] + chem["dnu"], n_quad)
+    w = (nu / chem["nu0"]) ** -3 / nu
+    return float(np.trapezoid(w * chem["h"] * (nu - chem["nu0"]), nu) / np.trapezoid(w, nu))
+
+
 def clumpy(n: int = 256, nside: int = 8, seed: int = 5, sigma: float = 1.5, n_clumps: int = 200,
            overdensity: float = 100.0, n_src: int = 8, Q: float = 5e48, box_kpc: float = 6.6,
            nH_mean: float = 1e-3, x0: float = 1e-4) -> HIICase:

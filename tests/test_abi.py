@@ -90,6 +90,13 @@ def test_null_context_calls_fail_cleanly(lib):
     assert (o.F, o.eps_iter, o.eps_e, o.eps_hi, o.dt_fixed) == (10.0, 1e-3, 0.2, 0.002, 0.0)
     w = art.ArtWarmOptions()
     assert lib.art_warm_options_default(ctypes.byref(w)) == art.ART_OK and w.judge_after == 2
+    assert lib.art_evolve_thermal(None, None, None, None, None, 0, None, None, None, None, None) == \
+        art.ART_E_INVALID
+    assert lib.art_thermal_default(None) == art.ART_E_INVALID
+    th = art.ArtThermal()
+    assert lib.art_thermal_default(ctypes.byref(th)) == art.ART_OK
+    assert (th.on_the_spot, th.cool_mask, list(th.e_bin), th.e_diff, th.z, th.kB, th.T_min, th.T_max) == \
+        (0, 31, [0.0] * 4, 0.0, 0.0, 1.380649e-16, 10.0, 1e9)
     assert lib.art_destroy(None) == art.ART_OK
     assert lib.art_last_error(None) == b"null context"
 
