@@ -554,6 +554,49 @@ def thermal_measure(torch, dev, F=1.0):
     return out
 
 
+def test3_thermal_measure(torch, dev, n=64, nside=4, F=1.0):
+    """The paper's Test 3 as printed (Sec. 4.3), with the energy equation:
+    n_H 2e-4 at 8000 K, a clump of 200x density at 40 K (radius 0.8 kpc, 1.7
+    kpc from the centre along x), a 1e5 K blackbody flux of 1e6 photons/s/cm^2
+    (4 bins) through the x = 0 face, to the paper's 1, 3 and 15 Myr, with the
+    diffuse field and on the spot.  Reports steps, iterations, wall time and y
+    and T at the clump's centre, behind it on its axis, and at the same depth
+    off the shadow."""
+    from paper_1410_0763_gb300 import art
+    from paper_1410_0763_gb300 import workloads as wl
+    case = wl.shadow_clump(n=n, nside=nside)
+    frac, sig, _ = wl.blackbody_bins()
+    sw = art.ArtSweep(case.nH.shape, case.nside, 1, field_form=art.ART_FIELDS_EPS, dx_cm=case.chem["dx"])
+    sw.set_source_spectrum(sig, frac)
+    sw.set_plane_source(*case.plane)
+    nH = torch.as_tensor(case.nH, dtype=torch.float64, device=dev)
+    clump = case.nH > 1.5 * case.nH.min()
+    T0 = np.where(clump, 40.0, 8000.0)
+    th = {"e_bin": list(wl.blackbody_heat()), "e_diff": wl.diffuse_band_heat(case.chem)}
+    mid = n // 2
+    cz, cy, cx = [int(round(v)) for v in np.mean(np.argwhere(clump), axis=0)]
+    cells = {"clump_centre": (cz, cy, cx), "behind_clump": (mid, mid, n - 2), "beside_shadow": (mid, n // 8, n - 2)}
+    out = {"workload": f"Test 3 as printed with the energy equation, {n}^3, N_side {nside}: n_H 2e-4 at 8000 K, "
+                       "clump x200 at 40 K (r 0.8 kpc, 1.7 kpc off centre along x), 1e5 K blackbody flux 1e6 s^-1 "
+                       f"cm^-2 through x = 0 (4 bins), F = {F}, eps_iter 1e-3"}
+    for label, otsa in (("with_diffuse", 0), ("on_the_spot", 1)):
+        y = torch.as_tensor(case.y0, dtype=torch.float64, device=dev).clone()
+        T = torch.as_tensor(T0, dtype=torch.float64, device=dev).clone()
+        t, rows, tot = 0.0, [], {"steps": 0, "iterations": 0, "sweeps": 0, "seconds": 0.0}
+        for t_myr in (1.0, 3.0, 15.0):
+            rep = sw.evolve_thermal(nH, case.chem, dict(th, on_the_spot=otsa), [], y, T, t_myr * wl.MYR - t, F=F)
+            t = t_myr * wl.MYR
+            for k in ("steps", "iterations", "sweeps"):
+                tot[k] += int(getattr(rep, k))
+            tot["seconds"] += float(rep.seconds)
+            yh, Th = y.cpu().numpy(), T.cpu().numpy()
+            rows.append({"t_myr": t_myr, **{f"y_{k}": float(yh[c]) for k, c in cells.items()},
+                         **{f"T_{k}_K": round(float(Th[c]), 1) for k, c in cells.items()}})
+        out[label] = dict(tot, seconds=round(tot["seconds"], 3), at=rows)
+    sw.close()
+    return out
+
+
 def ablation_measure(torch, dev, reps=3):
     """The paper's ray-grouping comparison (Sec. 5) restated on GB300: the
     thread-per-ray layout of Sec. 3.1 with float atomics against the same
@@ -739,6 +782,7 @@ def run_ours(args, d: Dist):
         try:
             extra["time_dependent_64"] = evolve_measure(torch, dev)
             extra["time_dependent_thermal_64"] = thermal_measure(torch, dev)
+            extra["test3_thermal_64"] = test3_thermal_measure(torch, dev)
         except Exception as ex:  # pragma: no cover
             extra["time_dependent_64"] = {"error": str(ex)}
         try:

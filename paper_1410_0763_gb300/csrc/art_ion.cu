@@ -343,17 +343,19 @@ struct BalArgs {
 };
 
 // Temperature fits of the energy equation (App. C), T in K; sources in art.h.
-__device__ __forceinline__ double th_lambda(double T) { return 2.0 * 157807.0 / T; }
-__device__ __forceinline__ double th_alpha_A(double T)
+// The powers of lambda = 2 T_HI / T and of T are taken as exp(a ln .) from one
+// logarithm of T per evaluation.
+constexpr double kLn2THI = 12.662275226919286;   // ln(2 * 157807)
+__device__ __forceinline__ double th_alpha_A_ln(double lnl)
 {
-    const double l = th_lambda(T);
-    return 1.269e-13 * pow(l, 1.503) / pow(1.0 + pow(l / 0.522, 0.470), 1.923);
+    return 1.269e-13 * exp(1.503 * lnl - 1.923 * log1p(exp(0.470 * (lnl - log(0.522)))));
 }
-__device__ __forceinline__ double th_alpha_B(double T)
+__device__ __forceinline__ double th_alpha_B_ln(double lnl)
 {
-    const double l = th_lambda(T);
-    return 2.753e-14 * pow(l, 1.500) / pow(1.0 + pow(l / 2.740, 0.407), 2.242);
+    return 2.753e-14 * exp(1.500 * lnl - 2.242 * log1p(exp(0.407 * (lnl - log(2.740)))));
 }
+__device__ __forceinline__ double th_alpha_A(double T) { return th_alpha_A_ln(kLn2THI - log(T)); }
+__device__ __forceinline__ double th_alpha_B(double T) { return th_alpha_B_ln(kLn2THI - log(T)); }
 __device__ __forceinline__ double th_gamma_coll(double T)
 {
     return 5.85e-11 * sqrt(T) * exp(-157809.1 / T) / (1.0 + sqrt(T / 1e5));
@@ -1041,22 +1043,27 @@ struct ThermParams {
 __device__ __forceinline__ double th_cooling(const ThermParams &q, double nH, double y, double T)
 {
     const double nHI = y * nH, ne = (1.0 - y) * nH;
-    const double sT = sqrt(T), cden = 1.0 + sqrt(T / 1e5);
+    const double lnT = log(T), sT = sqrt(T), cden = 1.0 + sT * 3.1622776601683794e-3;   // 1 + sqrt(T / 1e5)
     double c = 0.0;
     if (q.cool_mask & 1) {
         double rc;
         if (q.otsa) {
-            const double l = th_lambda(T);
-            rc = 3.435e-30 * T * pow(l, 1.970) / pow(1.0 + pow(l / 2.250, 0.376), 3.720);
+            const double lnl = kLn2THI - lnT;
+            rc = 3.435e-30 * T * exp(1.970 * lnl - 3.720 * log1p(exp(0.376 * (lnl - log(2.250)))));
         } else {
-            rc = 8.70e-27 * sT * pow(T / 1e3, -0.2) / (1.0 + pow(T / 1e6, 0.7));
+            // (T / 1e3)^-0.2 / (1 + (T / 1e6)^0.7)
+            rc = 8.70e-27 * sT * exp(-0.2 * (lnT - 6.907755278982137)) /
+                 (1.0 + exp(0.7 * (lnT - 13.815510557964274)));
         }
         c += rc * ne * ne;
     }
-    if (q.cool_mask & 2) c += 1.27e-21 * sT * exp(-157809.1 / T) / cden * ne * nHI;
-    if (q.cool_mask & 4) c += 7.50e-19 * exp(-118348.0 / T) / cden * ne * nHI;
+    if (q.cool_mask & 6) {
+        const double iT = 1.0 / T;
+        if (q.cool_mask & 2) c += 1.27e-21 * sT * exp(-157809.1 * iT) / cden * ne * nHI;
+        if (q.cool_mask & 4) c += 7.50e-19 * exp(-118348.0 * iT) / cden * ne * nHI;
+    }
     if (q.cool_mask & 8) {
-        const double d = 5.5 - log10(T);
+        const double d = 5.5 - lnT * 0.43429448190325176;   // log10 T
         c += 1.42e-27 * (1.1 + 0.34 * exp(-d * d / 3.0)) * sT * ne * ne;
     }
     if (q.cool_mask & 16) c += q.compton * (T - q.T_g) * ne;
@@ -1150,8 +1157,9 @@ __global__ void __launch_bounds__(256) thermal_kernel(const ThermArgs p)
         double y = p.y_t[i], T = p.T_t[i], tau = 0.0;
         int n = 0;
         while (tau < p.dt && n < p.max_sub) {
-            const double aB = th_alpha_B(T), gc = th_gamma_coll(T);
-            const double dal = p.q.otsa ? 0.0 : th_alpha_A(T) - aB;
+            const double lnl = kLn2THI - log(T);
+            const double aB = th_alpha_B_ln(lnl), gc = th_gamma_coll(T);
+            const double dal = p.q.otsa ? 0.0 : th_alpha_A_ln(lnl) - aB;
             const double nHI = y * nH, ne = (1.0 - y) * nH;
             const double C = aB * ne * ne, D = gc * ne + g;
             double dtc = dtchem_of(nH, y, aB, gc, g, p.eps_e, p.eps_hi);
