@@ -502,16 +502,17 @@ art_status art_profile_enable(art_ctx *ctx, int enable);
 art_status art_profile_read(art_ctx *ctx, art_profile *out, int reset);
 
 /*
- * Issue-rate microbenchmark of the current device (about 10 ms): results per
- * clock per SM of MUFU ex2 (the one exponential of each segment), MUFU rcp and
- * FP32 FFMA, from clock64() timings of independent chains with two 1024-thread
- * CTAs per SM: per SM, the window from the earliest start to the latest end of
- * its CTAs; the median over SMs, the better of two runs.  Used to state the
- * sweep's arithmetic roofline.  Errors:
- * ART_E_INVALID (NULL output), ART_E_OOM, ART_E_CUDA.
+ * Issue-rate microbenchmark of the current device (about 15 ms): results per
+ * clock per SM of MUFU ex2 (the one exponential of each segment), MUFU rcp,
+ * scalar FP32 FFMA, and FP32 FMAs issued as packed FP32x2 instructions (two
+ * per instruction, the form of the sweep's pair arithmetic), from clock64()
+ * timings of independent chains with two 1024-thread CTAs per SM: per SM, the
+ * window from the earliest start to the latest end of its CTAs; the median
+ * over SMs, the better of two runs.  Used to state the sweep's arithmetic
+ * roofline.  Errors: ART_E_INVALID (NULL output), ART_E_OOM, ART_E_CUDA.
  */
 art_status art_measure_pipes(double *ex2_per_clk_sm, double *rcp_per_clk_sm,
-                             double *ffma_per_clk_sm);
+                             double *ffma_per_clk_sm, double *ffma2_per_clk_sm);
 
 /*
  * One FP32 sweep (kappa, S inputs, J^in output) that allocates no memory.

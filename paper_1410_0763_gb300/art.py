@@ -161,7 +161,7 @@ def load() -> C.CDLL:
         lib.art_sweep.argtypes = [P, P, P, P, C.c_int, P]
         lib.art_count_segments.argtypes = [C.POINTER(ArtGrid), C.c_int, C.c_double, C.POINTER(C.c_int64)]
         lib.art_band_integral.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_double)]
-        lib.art_measure_pipes.argtypes = [C.POINTER(C.c_double)] * 3
+        lib.art_measure_pipes.argtypes = [C.POINTER(C.c_double)] * 4
         lib.art_point_sources.argtypes = [P, P, C.POINTER(C.c_double), C.POINTER(ArtSource), C.POINTER(C.c_double),
                                           C.c_int, P, P]
         lib.art_iterate_ionization.argtypes = [P, C.POINTER(ArtChem), P, C.POINTER(ArtSource), C.c_int, C.c_double,
@@ -307,12 +307,13 @@ def art_sweep_noalloc(shape, n_side: int, kappa_ptr: int, S_ptr: int, Jin_ptr: i
 
 
 def art_measure_pipes() -> dict:
-    """Results per clock per SM of MUFU ex2, MUFU rcp and FP32 FFMA on the current GPU."""
-    a, b, c = C.c_double(), C.c_double(), C.c_double()
-    st = load().art_measure_pipes(C.byref(a), C.byref(b), C.byref(c))
+    """Results per clock per SM of MUFU ex2, MUFU rcp, scalar FP32 FFMA and FP32 FMAs issued
+    as packed FP32x2 instructions (ffma2, two per instruction) on the current GPU."""
+    a, b, c, d = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+    st = load().art_measure_pipes(C.byref(a), C.byref(b), C.byref(c), C.byref(d))
     if st != ART_OK:
         raise ArtError(st, "art_measure_pipes failed")
-    return {"ex2": a.value, "rcp": b.value, "ffma": c.value}
+    return {"ex2": a.value, "rcp": b.value, "ffma": c.value, "ffma2": d.value}
 
 
 def art_profile_enable(ctx, enable: bool) -> int:
