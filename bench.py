@@ -738,24 +738,36 @@ def run_ours(args, d: Dist):
     peak_gseg = min(peak_mufu, peak_fp32)
     sweep_share = pr.sweep_ms / max(pr.sweep_ms + pr.reduce_ms, 1e-9)
 
-    # end to end through the C ABI with host buffers (pinned), copies included
+    # end to end through the C ABI with host buffers (pinned): every step copies its kappa and
+    # S in and its J out.  art_sweep_stream overlaps those copies with the neighbouring steps'
+    # sweeps; the per-call form (art_set_fields + art_sweep, each synchronous) is reported beside it.
     kh = torch.as_tensor(case.kappa.astype(np.float32)).pin_memory()
     sh = torch.as_tensor(case.src.astype(np.float32)).pin_memory()
-    Jh = torch.empty(k.shape, dtype=torch.float32).pin_memory()
+    Jh = [torch.empty(k.shape, dtype=torch.float32).pin_memory() for _ in range(2)]
     e2e_steps = max(3, min(args.steps, 200))
+    sw.sweep_stream([kh] * 3, [sh] * 3, J=[Jh[i % 2] for i in range(3)])
+    torch.cuda.synchronize()
+    d.barrier()
+    t0 = time.perf_counter()
+    sw.sweep_stream([kh] * e2e_steps, [sh] * e2e_steps, J=[Jh[i % 2] for i in range(e2e_steps)])
+    torch.cuda.synchronize()
+    dt = d.max(time.perf_counter() - t0, dev)
+    e2e = {"value": seg * d.world * e2e_steps / dt, "unit": UNIT,
+           "h2d_bytes_per_step": int(2 * kh.numel() * 4), "d2h_bytes_per_step": int(Jh[0].numel() * 4),
+           "api": "art_sweep_stream (copies overlap the neighbouring steps' sweeps)"}
     for _ in range(3):
         sw.set_fields(kh, sh)
-        sw.sweep(Jh)
+        sw.sweep(Jh[0])
     torch.cuda.synchronize()
     d.barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         sw.set_fields(kh, sh)
-        sw.sweep(Jh)
+        sw.sweep(Jh[0])
     torch.cuda.synchronize()
     dt = d.max(time.perf_counter() - t0, dev)
-    e2e = {"value": seg * d.world * e2e_steps / dt, "unit": UNIT,
-           "h2d_bytes_per_step": int(2 * kh.numel() * 4), "d2h_bytes_per_step": int(Jh.numel() * 4)}
+    e2e["per_call"] = {"value": seg * d.world * e2e_steps / dt, "unit": UNIT,
+                       "api": "art_set_fields + art_sweep per step (each returns synchronized)"}
     sw.close()
 
     extra = {}

@@ -254,6 +254,26 @@ art_status art_band_integral(double sigma0, double h, double nu0, double nu_lo, 
  */
 art_status art_sweep(art_ctx *ctx, void *J, void *J_in, void *gamma, int on_device, void *stream);
 
+/*
+ * The sweeps of n_sets independent field sets held in host memory, streamed
+ * through the device: the host-to-device copy and validation of set k + 1 and
+ * the device-to-host copy of set k - 1 run on the library's own copy streams
+ * while set k is swept on `stream` (double-buffered input staging and output
+ * slots).  kappa[k], src[k]: host arrays as art_set_fields takes them with
+ * on_device = 0; J[k], J_in[k], gamma[k]: host outputs as art_sweep writes
+ * them (any of the three pointer arrays may be NULL: not written).  Page-
+ * locked host memory lets the copies overlap; pageable memory works, slower.
+ * Each set is checked as art_set_fields checks it before it is swept; the
+ * first invalid set ends the call with ART_E_INVALID (the sets before it are
+ * swept and written, the rest are not).  Returns once every output is in host
+ * memory.  The outputs are bit-identical to art_set_fields + art_sweep per
+ * set, and the last set swept remains the context's fields.  Errors:
+ * ART_E_INVALID (null arrays or pointers, n_sets < 0, an invalid set, J on a
+ * direction shard), ART_E_OOM, ART_E_CUDA.
+ */
+art_status art_sweep_stream(art_ctx *ctx, int n_sets, const void *const *kappa, const void *const *src,
+                            void *const *J, void *const *J_in, void *const *gamma, void *stream);
+
 /* Hydrogen rate coefficients at the (fixed) gas temperature and the spectral
  * constants of the recombination radiation (Sec. 2.2, App. B). */
 typedef struct {

@@ -159,6 +159,8 @@ def load() -> C.CDLL:
                                               C.POINTER(ArtEvolveOptions), P, C.POINTER(ArtEvolveReport), P]
         lib.art_evolve_ionization.restype = C.c_int
         lib.art_sweep.argtypes = [P, P, P, P, C.c_int, P]
+        lib.art_sweep_stream.argtypes = [P, C.c_int, P, P, P, P, P, P]
+        lib.art_sweep_stream.restype = C.c_int
         lib.art_count_segments.argtypes = [C.POINTER(ArtGrid), C.c_int, C.c_double, C.POINTER(C.c_int64)]
         lib.art_band_integral.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_double)]
         lib.art_measure_pipes.argtypes = [C.POINTER(C.c_double)] * 4
@@ -697,6 +699,35 @@ class ArtSweep:
         on_dev = kinds.pop() if kinds else 1
         _check(self._ctx, art_sweep(self._ctx, ptrs[0], ptrs[1], ptrs[2], on_dev,
                                     _stream(stream) if on_dev else 0))
+        return J, J_in, gamma
+
+    def sweep_stream(self, kappas, srcs, J=None, J_in=None, gamma=None, stream=None):
+        """Sweeps of len(kappas) field sets held in host memory (art_sweep_stream): the copies of
+        the next and the previous set overlap the current sweep.  kappas, srcs: lists of host
+        arrays as set_fields takes them; J, J_in, gamma: lists of host output arrays, one per set,
+        or None.  Returns (J, J_in, gamma)."""
+        n = len(kappas)
+        if len(srcs) != n:
+            raise ValueError("one source field per kappa field")
+        nf = self.ncell * self.nbins
+        keep = []
+
+        def table(lst, m):
+            if lst is None:
+                return None
+            if len(lst) != n:
+                raise ValueError("one buffer per set")
+            ps = []
+            for a in lst:
+                p, dev, k = _ptr(a, self.dtype, m)
+                if dev:
+                    raise TypeError("sweep_stream takes host buffers")
+                ps.append(p)
+                keep.append(k)
+            return (C.c_void_p * max(n, 1))(*ps)
+
+        tabs = [table(kappas, nf), table(srcs, nf), table(J, nf), table(J_in, nf), table(gamma, self.ncell)]
+        _check(self._ctx, load().art_sweep_stream(self._ctx, n, *tabs, C.c_void_p(_stream(stream))))
         return J, J_in, gamma
 
 

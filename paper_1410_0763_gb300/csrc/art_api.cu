@@ -799,6 +799,19 @@ art_status art_destroy(art_ctx *ctx)
     for (void *p : sur)
         if (p) cudaFree(p);
     art_internal_ablation_free(ctx);
+    {
+        auto &R = ctx->sres;
+        if (R.in) cudaStreamDestroy(R.in);
+        if (R.out) cudaStreamDestroy(R.out);
+        for (int b = 0; b < 2; ++b) {
+            for (cudaEvent_t e : {R.ev_in[b], R.ev_lay[b], R.ev_sw[b], R.ev_out[b]})
+                if (e) cudaEventDestroy(e);
+            if (R.slot[b]) cudaFree(R.slot[b]);
+        }
+        if (R.stage2) cudaFree(R.stage2);
+        if (R.d_flags) cudaFree(R.d_flags);
+        if (R.h_flags) cudaFreeHost(R.h_flags);
+    }
     if (ctx->coarse) art_destroy(ctx->coarse);
     delete ctx;
     return ART_OK;
@@ -886,6 +899,95 @@ art_status art_set_boundary_intensity(art_ctx *ctx, const double *I_bc)
         ctx->gexec = nullptr;
     }
     return ART_OK;
+}
+
+art_status art_sweep_stream(art_ctx *ctx, int n_sets, const void *const *kappa, const void *const *src,
+                            void *const *J, void *const *J_in, void *const *gamma, void *stream)
+{
+    if (!ctx) return ART_E_INVALID;
+    if (n_sets < 0 || (n_sets > 0 && (!kappa || !src)))
+        return fail(ctx, ART_E_INVALID, "art_sweep_stream: bad set count or null input arrays");
+    if (J && ctx->opt.dir_end > ctx->opt.dir_begin)
+        return fail(ctx, ART_E_INVALID, "art_sweep_stream: a direction shard has no J output (sum the J_in shares)");
+    for (int k = 0; k < n_sets; ++k)
+        if (!kappa[k] || !src[k] || (J && !J[k]) || (J_in && !J_in[k]) || (gamma && !gamma[k]))
+            return fail(ctx, ART_E_INVALID, "art_sweep_stream: null field or output pointer");
+    if (n_sets == 0) return ART_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const long long nb = ctx->ncell * ctx->nbins;
+    const size_t rs = ctx->rsz, fbytes = (size_t)nb * rs;
+    const size_t jbytes = fbytes, gbytes = (size_t)ctx->ncell * rs;
+    auto &R = ctx->sres;
+    if (!R.in) {
+        CK(ctx, cudaStreamCreateWithFlags(&R.in, cudaStreamNonBlocking));
+        CK(ctx, cudaStreamCreateWithFlags(&R.out, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; ++b)
+            for (cudaEvent_t *e : {&R.ev_in[b], &R.ev_lay[b], &R.ev_sw[b], &R.ev_out[b]})
+                CK(ctx, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+        const size_t ob = (2 * (size_t)ctx->nbins + 1) * ctx->ncell * rs;
+        CK(ctx, cudaMalloc(&R.stage2, 2 * fbytes));
+        CK(ctx, cudaMalloc(&R.slot[0], ob));
+        CK(ctx, cudaMalloc(&R.slot[1], ob));
+        CK(ctx, cudaMalloc(&R.d_flags, 2 * sizeof(int)));
+        CK(ctx, cudaMallocHost(&R.h_flags, 2 * sizeof(int)));
+        ctx->dev_bytes += (long long)(2 * fbytes + 2 * ob + 2 * sizeof(int));
+    }
+    char *stage[2] = {static_cast<char *>(ctx->d_stage), static_cast<char *>(R.stage2)};
+    char *o = static_cast<char *>(ctx->d_out);
+    void *dJ = J ? o : nullptr, *dJin = J_in ? o + nb * rs : nullptr, *dG = gamma ? o + 2 * nb * rs : nullptr;
+    const int nt = 256;
+    const unsigned vb = (unsigned)std::min<long long>((nb + nt - 1) / nt, 4096);
+    art_status status = ART_OK;
+    int k = 0;
+    for (; k < n_sets; ++k) {
+        const int b = k & 1;
+        // host -> device into stage[b] once the layout of set k - 2 has read it; validate there
+        CK(ctx, cudaStreamWaitEvent(R.in, R.ev_lay[b], 0));
+        CK(ctx, cudaMemcpyAsync(stage[b], kappa[k], fbytes, cudaMemcpyHostToDevice, R.in));
+        CK(ctx, cudaMemcpyAsync(stage[b] + fbytes, src[k], fbytes, cudaMemcpyHostToDevice, R.in));
+        CK(ctx, cudaMemsetAsync(R.d_flags + b, 0, sizeof(int), R.in));
+        if (ctx->prec == ART_FP64)
+            validate_kernel<double><<<vb, nt, 0, R.in>>>(reinterpret_cast<const double *>(stage[b]),
+                                                         reinterpret_cast<const double *>(stage[b] + fbytes), nb,
+                                                         R.d_flags + b);
+        else
+            validate_kernel<float><<<vb, nt, 0, R.in>>>(reinterpret_cast<const float *>(stage[b]),
+                                                        reinterpret_cast<const float *>(stage[b] + fbytes), nb,
+                                                        R.d_flags + b);
+        CK(ctx, cudaGetLastError());
+        CK(ctx, cudaMemcpyAsync(R.h_flags + b, R.d_flags + b, sizeof(int), cudaMemcpyDeviceToHost, R.in));
+        CK(ctx, cudaEventRecord(R.ev_in[b], R.in));
+        // the host waits for this set's copy and check while the sweep of set k - 1 runs
+        CK(ctx, cudaEventSynchronize(R.ev_in[b]));
+        if (R.h_flags[b]) {
+            status = fail(ctx, ART_E_INVALID, "art_sweep_stream: set " + std::to_string(k) +
+                                                  ((R.h_flags[b] & 1) ? ": kappa negative or not finite"
+                                                                      : ": source term not finite"));
+            break;
+        }
+        CK(ctx, cudaStreamWaitEvent(st, R.ev_in[b], 0));
+        if ((status = art_internal_layout(ctx, stage[b], stage[b] + fbytes, st)) != ART_OK) break;
+        CK(ctx, cudaEventRecord(R.ev_lay[b], st));
+        status = (ctx->opt.graph && !ctx->profiling) ? sweep_graph(ctx, dJ, dJin, dG, st)
+                                                     : sweep_launches(ctx, dJ, dJin, dG, st);
+        if (status != ART_OK) break;
+        // results into slot b once the device -> host copy of set k - 2 has read it
+        CK(ctx, cudaStreamWaitEvent(st, R.ev_out[b], 0));
+        char *sl = static_cast<char *>(R.slot[b]);
+        if (J) CK(ctx, cudaMemcpyAsync(sl, dJ, jbytes, cudaMemcpyDeviceToDevice, st));
+        if (J_in) CK(ctx, cudaMemcpyAsync(sl + jbytes, dJin, jbytes, cudaMemcpyDeviceToDevice, st));
+        if (gamma) CK(ctx, cudaMemcpyAsync(sl + 2 * jbytes, dG, gbytes, cudaMemcpyDeviceToDevice, st));
+        CK(ctx, cudaEventRecord(R.ev_sw[b], st));
+        CK(ctx, cudaStreamWaitEvent(R.out, R.ev_sw[b], 0));
+        if (J) CK(ctx, cudaMemcpyAsync(J[k], sl, jbytes, cudaMemcpyDeviceToHost, R.out));
+        if (J_in) CK(ctx, cudaMemcpyAsync(J_in[k], sl + jbytes, jbytes, cudaMemcpyDeviceToHost, R.out));
+        if (gamma) CK(ctx, cudaMemcpyAsync(gamma[k], sl + 2 * jbytes, gbytes, cudaMemcpyDeviceToHost, R.out));
+        CK(ctx, cudaEventRecord(R.ev_out[b], R.out));
+    }
+    CK(ctx, cudaStreamSynchronize(st));
+    CK(ctx, cudaStreamSynchronize(R.out));
+    CK(ctx, cudaStreamSynchronize(R.in));
+    return status;
 }
 
 art_status art_sweep(art_ctx *ctx, void *J, void *J_in, void *gamma, int on_device, void *stream)

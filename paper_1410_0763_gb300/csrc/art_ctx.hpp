@@ -86,6 +86,15 @@ struct art_ctx {
     void *d_stage = nullptr;   // [2][nbins][ncell] real: host-input staging
     void *d_out = nullptr;     // [2 nbins + 1][ncell] real: host-output staging
     int *d_flag = nullptr;
+    // art_sweep_stream: copy streams, the second input staging buffer, two
+    // output slots, per-slot validation flags (device and pinned host), events
+    struct StreamRes {
+        cudaStream_t in = nullptr, out = nullptr;
+        cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_lay[2] = {nullptr, nullptr};
+        cudaEvent_t ev_sw[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+        void *stage2 = nullptr, *slot[2] = {nullptr, nullptr};
+        int *d_flags = nullptr, *h_flags = nullptr;
+    } sres;
     // profiling: event triples (before sweep launches, after them, after reduce)
     bool profiling = false;
     std::vector<cudaEvent_t> ev;
