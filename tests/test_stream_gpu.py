@@ -85,3 +85,33 @@ def test_invalid_set_stops_the_stream():
         sw.sweep(J0)
     assert np.array_equal(J[0], J0)
     assert np.all(np.isnan(J[1])) and np.all(np.isnan(J[2]))
+
+
+@pytest.mark.parametrize("kind", ["fp64", "batch"])
+def test_stream_fp64_and_batch_contexts(kind):
+    if kind == "fp64":
+        shape, nside, kw = (12, 10, 14), 2, dict(precision="fp64")
+        dt = np.float64
+        mk = lambda k: wl.grf(16, 2, seed=50 + k)
+        cut = lambda a: np.ascontiguousarray(a[:12, :10, :14], dtype=dt)
+        fields = [(cut(mk(k).kappa), cut(mk(k).src)) for k in range(3)]
+        n = int(np.prod(shape))
+    else:
+        shape, nside, kw = [(8, 8, 8), (12, 10, 6)], [1, 2], {}
+        dt = np.float32
+        n = sum(int(np.prod(s)) for s in shape)
+        rng = np.random.default_rng(7)
+        fields = [(rng.uniform(0.05, 2.0, n).astype(dt), rng.uniform(0.0, 1.0, n).astype(dt)) for _ in range(3)]
+    want = []
+    with art.ArtSweep(shape, nside, **kw) as sw:
+        for kap, src in fields:
+            sw.set_fields(kap, src)
+            J, Jin = np.empty(n, dt), np.empty(n, dt)
+            sw.sweep(J.reshape(-1), Jin.reshape(-1))
+            want.append((J, Jin))
+    with art.ArtSweep(shape, nside, **kw) as sw:
+        J = [np.empty(n, dt) for _ in fields]
+        Jin = [np.empty(n, dt) for _ in fields]
+        sw.sweep_stream([f[0].reshape(-1) for f in fields], [f[1].reshape(-1) for f in fields], J, Jin)
+    for k in range(len(fields)):
+        assert np.array_equal(J[k], want[k][0]) and np.array_equal(Jin[k], want[k][1])
