@@ -1,7 +1,9 @@
 """Time the point-source rates and one RT / ionization-balance iteration on a
 grid: ``python -m paper_1410_0763_gb300.ionbench --case hii --reps 5`` (128^3
 HII region, one source) or ``--case clumpy`` (256^3 clumpy medium, 8 sources,
-4 bins).  Prints one JSON line."""
+4 bins); or, with ``--case thermal --myr 30``, the time-dependent mode with
+the energy equation on the Test-1 setup (64^3, N_side 4, T0 100 K, a 1e5 K
+blackbody source in 4 bins) to the given time.  Prints one JSON line."""
 from __future__ import annotations
 
 import argparse
@@ -11,9 +13,12 @@ import time
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", choices=("hii", "clumpy"), default="hii")
+    ap.add_argument("--case", choices=("hii", "clumpy", "thermal"), default="hii")
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--myr", type=float, default=30.0, help="thermal case: evolve to this time")
     a = ap.parse_args(argv)
+    if a.case == "thermal":
+        return thermal(a.myr)
     import torch
     from . import art, build
     from . import workloads as wl
@@ -51,6 +56,30 @@ def main(argv=None):
     print(json.dumps({"case": a.case, "n": case.n, "sources": len(srcs),
                       "point_sources_ms_one_bin": round(1e3 * t_pt, 3),
                       "iteration_ms": round(1e3 * t_it, 3)}), flush=True)
+
+
+def thermal(myr: float):
+    import torch
+    from . import art, build
+    from . import workloads as wl
+    build.build()
+    art.load()
+    case = wl.hii_region(n=64, nside=4, box_kpc=6.6, nH=1e-3, Q=5e48, source_at="corner")
+    frac, sig, _ = wl.blackbody_bins()
+    srcs = [(p[0], p[1], p[2], q) for p, q in zip(case.pos, case.Q)]
+    sw = art.ArtSweep(case.nH.shape, case.nside, 1, field_form=art.ART_FIELDS_EPS, dx_cm=case.chem["dx"])
+    sw.set_source_spectrum(sig, frac)
+    th = {"e_bin": list(wl.blackbody_heat()), "e_diff": wl.diffuse_band_heat(case.chem)}
+    nH = torch.as_tensor(case.nH, dtype=torch.float64, device="cuda")
+    y = torch.as_tensor(case.y0, dtype=torch.float64, device="cuda").clone()
+    T = torch.full_like(y, 100.0)
+    rep = sw.evolve_thermal(nH, case.chem, th, srcs, y, T, myr * wl.MYR, F=1.0)
+    sw.close()
+    print(json.dumps({"case": "thermal", "n": case.n, "myr": myr, "steps": int(rep.steps),
+                      "iterations": int(rep.iterations), "sweeps": int(rep.sweeps),
+                      "seconds": round(float(rep.seconds), 4),
+                      "ms_per_iteration": round(1e3 * float(rep.seconds) / max(int(rep.iterations), 1), 3)}),
+          flush=True)
 
 
 if __name__ == "__main__":
