@@ -447,8 +447,10 @@ art_status art_thermal_default(art_thermal *th);
  * specific energy u = 3 k_B T (1 + x) n_H / (2 rho) at the new composition,
  *   u' = u + (H(n') - C(n', u')) dtc / rho
  * (rho cancels: 1.5 k_B n_H ((1 + x') T' - (1 + x) T) = (H' - C(n', T')) dtc),
- * whose root T' is bracketed from T within [T_min, T_max] and refined by
- * regula falsi with the Illinois modification.  The emissivity of the
+ * whose root T' is found by Newton's method from T on the analytic
+ * derivative of the cooling fits, kept inside the bracket its iterates build
+ * within [T_min, T_max] (bisection, or doubling / halving before both ends
+ * are known, when a step leaves it).  The emissivity of the
  * diffuse field takes (alpha_A - alpha_B)(T) per cell; chem->alphaA,
  * alphaB and gcoll are not used.  dt_chem is App. D's (n_e and n_HI only);
  * each RT step iterates until max_cells of |n_e^(i) - n_e^(i-1)| / n_e^(i)

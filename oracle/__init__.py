@@ -117,6 +117,8 @@ def _lib_handle():
             TP = C.POINTER(Thermal)
             lib.orc_cooling.argtypes = [TP, C.c_double, C.c_double, C.c_double]
             lib.orc_cooling.restype = C.c_double
+            lib.orc_cooling_deriv.argtypes = [TP, C.c_double, C.c_double, C.c_double]
+            lib.orc_cooling_deriv.restype = C.c_double
             lib.orc_energy_step.argtypes = [TP] + [C.c_double] * 6
             lib.orc_energy_step.restype = C.c_double
             lib.orc_thermal_cell.argtypes = [TP] + [C.c_double] * 9 + [C.c_int, _D, _D]
@@ -393,6 +395,12 @@ def cooling(th: dict, nH: float, y: float, T: float) -> float:
     """Cooling rate C(n, T) in erg/s/cm^3 (App. C) of hydrogen with neutral fraction y."""
     t = _thermal(th)
     return float(_lib_handle().orc_cooling(C.byref(t), float(nH), float(y), float(T)))
+
+
+def cooling_deriv(th: dict, nH: float, y: float, T: float) -> float:
+    """dC/dT (erg/s/cm^3/K) of `cooling`, from the fits' analytic logarithmic derivatives."""
+    t = _thermal(th)
+    return float(_lib_handle().orc_cooling_deriv(C.byref(t), float(nH), float(y), float(T)))
 
 
 def energy_step(th: dict, nH, y0, T0, y1, H1, dt) -> float:

@@ -1074,15 +1074,54 @@ double orc_cooling(const orc_thermal *th, double nH, double y, double T)
     return c;
 }
 
+/* dC/dT of orc_cooling, from the logarithmic derivative of each fit:
+ *   case-A recombination (Cen)   0.3 - 0.7 u / (1 + u),  u = (T/1e6)^0.7
+ *   case-B recombination (H&G)   1 - 1.970 + 3.720 * 0.376 v / (1 + v),  v = (lambda/2.25)^0.376
+ *   collisional ionization       0.5 + 157809.1/T - 0.5 w / (1 + w),  w = sqrt(T/1e5)
+ *   collisional excitation       118348/T - 0.5 w / (1 + w)
+ *   free-free                    0.5 + 0.34 e^{-d^2/3} (2d / (3 ln 10)) / g_ff,  d = 5.5 - log10 T
+ * (d ln c / d ln T; dc/dT = c (d ln c / d ln T) / T), and the Compton term's
+ * coefficient times n_e. */
+double orc_cooling_deriv(const orc_thermal *th, double nH, double y, double T)
+{
+    const double nHI = y * nH, ne = (1.0 - y) * nH, nHII = ne;
+    const double w = sqrt(T / 1e5);
+    double d = 0.0;
+    if (th->cool_mask & 1) {
+        double c, g;
+        if (th->on_the_spot) {
+            const double v = pow(2.0 * ORC_T_HI / T / 2.250, 0.376);
+            c = orc_cool_rec_B(T);
+            g = 1.0 - 1.970 + 3.720 * 0.376 * v / (1.0 + v);
+        } else {
+            const double u = pow(T / 1e6, 0.7);
+            c = orc_cool_rec_A(T);
+            g = 0.3 - 0.7 * u / (1.0 + u);
+        }
+        d += c * g / T * ne * nHII;
+    }
+    if (th->cool_mask & 2) d += orc_cool_ci(T) * (0.5 + 157809.1 / T - 0.5 * w / (1.0 + w)) / T * ne * nHI;
+    if (th->cool_mask & 4) d += orc_cool_ce(T) * (118348.0 / T - 0.5 * w / (1.0 + w)) / T * ne * nHI;
+    if (th->cool_mask & 8) {
+        const double dd = 5.5 - log10(T), e = 0.34 * exp(-dd * dd / 3.0);
+        d += orc_cool_ff(T) * (0.5 + e * 2.0 * dd / (3.0 * log(10.0)) / (1.1 + e)) / T * ne * nHII;
+    }
+    if (th->cool_mask & 16) d += orc_compton_coef(th->z, th->kB) * ne;
+    return d;
+}
+
 /* The implicit update of App. C for one cell over dt: the specific energy
  * u = 3 k_B T (1 + x) n_H / (2 rho) at t + dt solves
  *   u' = u + (H(n') - C(n', u')) dt / rho,
  * i.e. with e = rho u = 1.5 k_B T n_H (1 + x) (rho cancels):
  *   f(T') = 1.5 k_B n_H (1 + x') T' + dt C(n', T') - (e + H' dt) = 0.
- * The root is bracketed from T (doubling or halving, within [T_min, T_max])
- * and refined by regula falsi with the Illinois modification (the retained
- * end's value is halved when the same end is kept twice; Dowell & Jarratt
- * 1971).  Returns T'. */
+ * Newton's method from T on f' = 1.5 k_B n_H (1 + x') + dt dC/dT, kept
+ * inside the bracket its iterates build (the largest T with f < 0 and the
+ * smallest with f > 0 seen so far, within [T_min, T_max]): a step that leaves
+ * it, or a non-positive f', bisects the bracket once both ends are known and
+ * otherwise doubles or halves T towards the sign change.  Stops when a step
+ * moves T by at most 1e-14 T, at a bound with f of the bound's sign, or after
+ * 100 steps.  Returns T'. */
 static double energy_f(const orc_thermal *th, double nH, double y1, double A, double B, double dt, double T)
 {
     return A * T + dt * orc_cooling(th, nH, y1, T) - B;
@@ -1093,48 +1132,23 @@ double orc_energy_step(const orc_thermal *th, double nH, double y0, double T0, d
     const double A = 1.5 * th->kB * nH * (2.0 - y1);
     const double B = 1.5 * th->kB * nH * (2.0 - y0) * T0 + H1 * dt;
     double T = T0 < th->T_min ? th->T_min : (T0 > th->T_max ? th->T_max : T0);
-    double f = energy_f(th, nH, y1, A, B, dt, T);
-    if (f == 0.0) return T;
-    double lo, hi, flo, fhi;
-    if (f < 0.0) {
-        lo = T; flo = f; hi = T; fhi = f;
-        while (fhi < 0.0) {
-            if (hi >= th->T_max) return th->T_max;
-            lo = hi; flo = fhi;
-            hi = 2.0 * hi < th->T_max ? 2.0 * hi : th->T_max;
-            fhi = energy_f(th, nH, y1, A, B, dt, hi);
+    double lo = th->T_min, hi = th->T_max;
+    int have_lo = 0, have_hi = 0;
+    for (int it = 0; it < 100; it++) {
+        const double f = energy_f(th, nH, y1, A, B, dt, T);
+        if (f == 0.0) return T;
+        if (f < 0.0) { lo = T; have_lo = 1; } else { hi = T; have_hi = 1; }
+        const double fp = A + dt * orc_cooling_deriv(th, nH, y1, T);
+        double Tn = fp > 0.0 ? T - f / fp : -1.0;
+        if (!(Tn > lo && Tn < hi) || !(fp > 0.0)) {
+            if (have_lo && have_hi) Tn = 0.5 * (lo + hi);
+            else if (f < 0.0) Tn = 2.0 * T < th->T_max ? 2.0 * T : th->T_max;
+            else Tn = 0.5 * T > th->T_min ? 0.5 * T : th->T_min;
         }
-    } else {
-        hi = T; fhi = f; lo = T; flo = f;
-        while (flo > 0.0) {
-            if (lo <= th->T_min) return th->T_min;
-            hi = lo; fhi = flo;
-            lo = 0.5 * lo > th->T_min ? 0.5 * lo : th->T_min;
-            flo = energy_f(th, nH, y1, A, B, dt, lo);
-        }
+        if (fabs(Tn - T) <= 1e-14 * T) return Tn;
+        T = Tn;
     }
-    if (flo == 0.0) return lo;
-    if (fhi == 0.0) return hi;
-    int side = 0;
-    double Tm = lo, prev = -1.0;
-    for (int it = 0; it < 200; it++) {
-        Tm = (lo * fhi - hi * flo) / (fhi - flo);
-        if (!(Tm > lo && Tm < hi)) Tm = 0.5 * (lo + hi);
-        if (fabs(Tm - prev) <= 1e-14 * Tm || hi - lo <= 1e-14 * hi) break;
-        prev = Tm;
-        const double fm = energy_f(th, nH, y1, A, B, dt, Tm);
-        if (fm == 0.0) break;
-        if (fm < 0.0) {
-            lo = Tm; flo = fm;
-            if (side == -1) fhi *= 0.5;
-            side = -1;
-        } else {
-            hi = Tm; fhi = fm;
-            if (side == 1) flo *= 0.5;
-            side = 1;
-        }
-    }
-    return Tm;
+    return T;
 }
 
 /* Chemical timestep of App. D at temperature T. */

@@ -1030,9 +1030,7 @@ art_status evolve_impl(art_ctx *ctx, const art_chem *ch, const double *nH, const
 // the new composition; with e = rho u = 1.5 k_B T n_H (1 + x) it is the root T'
 // of
 //   f(T') = 1.5 k_B n_H (1 + x') T' + dtc C(n', T') - (e + H' dtc),
-// bracketed from T (doubling or halving within [T_min, T_max]) and refined by
-// regula falsi with the Illinois modification (the value kept at an end that
-// survives twice is halved).
+// found by a bracket-safeguarded Newton iteration (th_energy_step).
 // ---------------------------------------------------------------------------
 struct ThermParams {
     int otsa, cool_mask;
@@ -1040,87 +1038,94 @@ struct ThermParams {
     double compton, T_g;         // Compton coefficient per electron (erg/s/K) and CMB temperature
 };
 
-__device__ __forceinline__ double th_cooling(const ThermParams &q, double nH, double y, double T)
+// Cooling rate C(n, T) (erg/s/cm^3) and dC/dT, each term's derivative from
+// its logarithmic derivative d ln c / d ln T (rec A: 0.3 - 0.7 u/(1 + u),
+// u = (T/1e6)^0.7; rec B: 1 - 1.970 + 3.720 * 0.376 v/(1 + v),
+// v = (lambda/2.25)^0.376; collisional ionization: 0.5 + 157809.1/T - 0.5 w/(1 + w),
+// w = sqrt(T/1e5); excitation: 118348/T - 0.5 w/(1 + w); free-free:
+// 0.5 + 0.34 e^{-d^2/3} (2d / (3 ln 10)) / g_ff, d = log10 of 10^5.5 / T).
+__device__ __forceinline__ double th_cooling(const ThermParams &q, double nH, double y, double T, double &dC)
 {
     const double nHI = y * nH, ne = (1.0 - y) * nH;
-    const double lnT = log(T), sT = sqrt(T), cden = 1.0 + sT * 3.1622776601683794e-3;   // 1 + sqrt(T / 1e5)
-    double c = 0.0;
+    const double lnT = log(T), iT = 1.0 / T, sT = sqrt(T);
+    const double w = sT * 3.1622776601683794e-3, cden = 1.0 + w;   // sqrt(T / 1e5)
+    double c = 0.0, d = 0.0;
     if (q.cool_mask & 1) {
-        double rc;
+        double rc, g;
         if (q.otsa) {
             const double lnl = kLn2THI - lnT;
-            rc = 3.435e-30 * T * exp(1.970 * lnl - 3.720 * log1p(exp(0.376 * (lnl - log(2.250)))));
+            const double v = exp(0.376 * (lnl - 0.81093021621632877));   // (lambda / 2.25)^0.376
+            rc = 3.435e-30 * T * exp(1.970 * lnl - 3.720 * log1p(v));
+            g = 1.0 - 1.970 + 3.720 * 0.376 * v / (1.0 + v);
         } else {
-            // (T / 1e3)^-0.2 / (1 + (T / 1e6)^0.7)
-            rc = 8.70e-27 * sT * exp(-0.2 * (lnT - 6.907755278982137)) /
-                 (1.0 + exp(0.7 * (lnT - 13.815510557964274)));
+            const double u = exp(0.7 * (lnT - 13.815510557964274));     // (T / 1e6)^0.7
+            rc = 8.70e-27 * sT * exp(-0.2 * (lnT - 6.907755278982137)) / (1.0 + u);
+            g = 0.3 - 0.7 * u / (1.0 + u);
         }
         c += rc * ne * ne;
+        d += rc * g * iT * ne * ne;
     }
-    if (q.cool_mask & 6) {
-        const double iT = 1.0 / T;
-        if (q.cool_mask & 2) c += 1.27e-21 * sT * exp(-157809.1 * iT) / cden * ne * nHI;
-        if (q.cool_mask & 4) c += 7.50e-19 * exp(-118348.0 * iT) / cden * ne * nHI;
+    if (q.cool_mask & 2) {
+        const double r = 1.27e-21 * sT * exp(-157809.1 * iT) / cden;
+        c += r * ne * nHI;
+        d += r * (0.5 + 157809.1 * iT - 0.5 * w / cden) * iT * ne * nHI;
+    }
+    if (q.cool_mask & 4) {
+        const double r = 7.50e-19 * exp(-118348.0 * iT) / cden;
+        c += r * ne * nHI;
+        d += r * (118348.0 * iT - 0.5 * w / cden) * iT * ne * nHI;
     }
     if (q.cool_mask & 8) {
-        const double d = 5.5 - lnT * 0.43429448190325176;   // log10 T
-        c += 1.42e-27 * (1.1 + 0.34 * exp(-d * d / 3.0)) * sT * ne * ne;
+        const double dd = 5.5 - lnT * 0.43429448190325176;   // 5.5 - log10 T
+        const double e = 0.34 * exp(-dd * dd / 3.0), gff = 1.1 + e;
+        const double r = 1.42e-27 * gff * sT;
+        c += r * ne * ne;
+        d += r * (0.5 + e * dd * 0.28952965460216784 / gff) * iT * ne * ne;   // 2 / (3 ln 10)
     }
-    if (q.cool_mask & 16) c += q.compton * (T - q.T_g) * ne;
+    if (q.cool_mask & 16) {
+        c += q.compton * (T - q.T_g) * ne;
+        d += q.compton * ne;
+    }
+    dC = d;
     return c;
 }
 
+// Newton's method from T on f' = 1.5 k_B n_H (1 + x') + dtc dC/dT, kept inside
+// the bracket its iterates build (the largest T with f < 0 and the smallest
+// with f > 0 so far, within [T_min, T_max]): a step that leaves it, or a
+// non-positive f', bisects once both ends are known and otherwise doubles or
+// halves T towards the sign change.  Stops when a step moves T by at most
+// 1e-14 T, at a bound, or after 100 steps.
 __device__ double th_energy_step(const ThermParams &q, double nH, double y0, double T0, double y1, double H1,
                                  double dt)
 {
     const double A = 1.5 * q.kB * nH * (2.0 - y1);
     const double B = 1.5 * q.kB * nH * (2.0 - y0) * T0 + H1 * dt;
-    auto f = [&](double T) { return A * T + dt * th_cooling(q, nH, y1, T) - B; };
-    const double T = fmin(fmax(T0, q.T_min), q.T_max);
-    const double fT = f(T);
-    if (fT == 0.0) return T;
-    double lo = T, hi = T, flo = fT, fhi = fT;
-    if (fT < 0.0) {
-        while (fhi < 0.0) {   // at most log2(T_max / T_min) doublings
-            if (hi >= q.T_max) return q.T_max;
-            lo = hi;
-            flo = fhi;
-            hi = fmin(2.0 * hi, q.T_max);
-            fhi = f(hi);
-        }
-    } else {
-        while (flo > 0.0) {
-            if (lo <= q.T_min) return q.T_min;
-            hi = lo;
-            fhi = flo;
-            lo = fmax(0.5 * lo, q.T_min);
-            flo = f(lo);
-        }
-    }
-    if (flo == 0.0) return lo;
-    if (fhi == 0.0) return hi;
-    int side = 0;
-    double Tm = lo, prev = -1.0;
-    for (int it = 0; it < 200; ++it) {
-        Tm = (lo * fhi - hi * flo) / (fhi - flo);
-        if (!(Tm > lo && Tm < hi)) Tm = 0.5 * (lo + hi);
-        if (fabs(Tm - prev) <= 1e-14 * Tm || hi - lo <= 1e-14 * hi) break;
-        prev = Tm;
-        const double fm = f(Tm);
-        if (fm == 0.0) break;
-        if (fm < 0.0) {
-            lo = Tm;
-            flo = fm;
-            if (side == -1) fhi *= 0.5;
-            side = -1;
+    double T = fmin(fmax(T0, q.T_min), q.T_max);
+    double lo = q.T_min, hi = q.T_max;
+    bool have_lo = false, have_hi = false;
+    for (int it = 0; it < 100; ++it) {
+        double dC;
+        const double f = A * T + dt * th_cooling(q, nH, y1, T, dC) - B;
+        if (f == 0.0) return T;
+        if (f < 0.0) {
+            lo = T;
+            have_lo = true;
         } else {
-            hi = Tm;
-            fhi = fm;
-            if (side == 1) flo *= 0.5;
-            side = 1;
+            hi = T;
+            have_hi = true;
         }
+        const double fp = A + dt * dC;
+        double Tn = fp > 0.0 ? T - f / fp : -1.0;
+        if (!(Tn > lo && Tn < hi) || !(fp > 0.0)) {
+            if (have_lo && have_hi) Tn = 0.5 * (lo + hi);
+            else if (f < 0.0) Tn = fmin(2.0 * T, q.T_max);
+            else Tn = fmax(0.5 * T, q.T_min);
+        }
+        if (fabs(Tn - T) <= 1e-14 * T) return Tn;
+        T = Tn;
     }
-    return Tm;
+    return T;
 }
 
 struct ThermArgs {

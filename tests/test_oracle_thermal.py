@@ -9,10 +9,11 @@ rates, each against something other than the oracle itself.
   1e4 K reproduce the fixed-temperature constants of the equilibrium runs;
   recombination cooling removes 0.5-1.2 k T per recombination, more in case
   A; the free-free Gaunt factor lies in [1.1, 1.44].
-* The implicit energy update: closed forms with no cooling (heat shared by
-  1 + x particles) and with Compton cooling alone (a linear equation); with
-  every term, the root of the implicit equation found by an independent
-  bracketing solver (scipy's brentq).
+* The implicit energy update: the analytic derivative of the cooling rate
+  that its Newton steps use against central differences; closed forms with
+  no cooling (heat shared by 1 + x particles) and with Compton cooling alone
+  (a linear equation); with every term, the root of the implicit equation
+  found by an independent bracketing solver (scipy's brentq).
 * One cell over long times at fixed optically thin rates: ionization
   equilibrium at the final temperature and thermal balance H = C; the
   on-the-spot form (less cooling) ends hotter.
@@ -90,6 +91,18 @@ def _th(**kw):
     d = dict(kB=KB, e_bin=[3 * EV], e_diff=0.5 * EV, z=-1.0, T_min=10.0, T_max=1e9, cool_mask=31)
     d.update(kw)
     return d
+
+
+@pytest.mark.parametrize("otsa", [0, 1])
+def test_cooling_derivative_matches_central_differences(orc, otsa):
+    th = _th(on_the_spot=otsa, z=2.0)
+    for T in np.geomspace(30.0, 3e8, 60):
+        for y in (0.0, 0.3, 0.999):
+            h = 1e-5 * T
+            fd = (orc.cooling(th, 1e-2, y, T + h) - orc.cooling(th, 1e-2, y, T - h)) / (2 * h)
+            d = orc.cooling_deriv(th, 1e-2, y, T)
+            scale = abs(orc.cooling(th, 1e-2, y, T)) / T + 1e-300
+            assert abs(d - fd) <= 1e-6 * max(abs(fd), scale), (T, y, d, fd)
 
 
 def test_energy_step_without_cooling_shares_the_heat(orc):
