@@ -427,6 +427,20 @@ def clumpy_measure(torch, dev, net, tol=1e-6):
                                   converged=bool(wr.total.converged),
                                   speedup_vs_plain=round(out["plain"]["seconds"] / out[label]["seconds"], 3),
                                   max_rel_dy_vs_plain=float(np.max(np.abs(y.cpu().numpy() - y_plain) / y_plain)))
+        # over-relaxed balance update (not in the paper; omega = 1.3), plain and after the coarse solve
+        sw.set_relaxation(1.3)
+        for label, fn in (("plain_relaxed_1.3", lambda y: sw.iterate(nH, case.chem, srcs, y, tol=tol, max_iter=400)),
+                          ("warm_coarse_solve_relaxed_1.3",
+                           lambda y: sw.iterate_warm(None, nH, case.chem, srcs, y, tol=tol, max_iter=400,
+                                                     use_net=False, phase1_max_iter=0))):
+            r2 = run(label, fn)
+            if r2:
+                res, y = r2
+                rep = res[0].total if label.startswith("warm") else res[0]
+                out[label].update(iterations=int(rep.iterations), converged=bool(rep.converged),
+                                  speedup_vs_plain=round(out["plain"]["seconds"] / out[label]["seconds"], 3),
+                                  max_rel_dy_vs_plain=float(np.max(np.abs(y.cpu().numpy() - y_plain) / y_plain)))
+        sw.set_relaxation(1.0)
     sw.close()
     return out
 

@@ -1120,8 +1120,9 @@ double orc_cooling_deriv(const orc_thermal *th, double nH, double y, double T)
  * smallest with f > 0 seen so far, within [T_min, T_max]): a step that leaves
  * it, or a non-positive f', bisects the bracket once both ends are known and
  * otherwise doubles or halves T towards the sign change.  Stops when a step
- * moves T by at most 1e-14 T, at a bound with f of the bound's sign, or after
- * 100 steps.  Returns T'. */
+ * moves T by at most 1e-12 T (Newton's error is then of order the square of
+ * that), at a bound with f of the bound's sign, or after 100 steps.
+ * Returns T'. */
 static double energy_f(const orc_thermal *th, double nH, double y1, double A, double B, double dt, double T)
 {
     return A * T + dt * orc_cooling(th, nH, y1, T) - B;
@@ -1145,7 +1146,7 @@ double orc_energy_step(const orc_thermal *th, double nH, double y0, double T0, d
             else if (f < 0.0) Tn = 2.0 * T < th->T_max ? 2.0 * T : th->T_max;
             else Tn = 0.5 * T > th->T_min ? 0.5 * T : th->T_min;
         }
-        if (fabs(Tn - T) <= 1e-14 * T) return Tn;
+        if (fabs(Tn - T) <= 1e-12 * T) return Tn;   // quadratic: Tn is then exact to rounding
         T = Tn;
     }
     return T;

@@ -145,6 +145,8 @@ def load() -> C.CDLL:
         lib.art_plane_source.restype = C.c_int
         lib.art_set_plane_source.argtypes = [P, C.c_int, C.c_int, C.c_double]
         lib.art_set_plane_source.restype = C.c_int
+        lib.art_set_relaxation.argtypes = [P, C.c_double]
+        lib.art_set_relaxation.restype = C.c_int
         lib.art_ablation_sweep.argtypes = [P, C.c_int, P, P]
         lib.art_ablation_sweep.restype = C.c_int
         lib.art_evolve_options_default.argtypes = [C.POINTER(ArtEvolveOptions)]
@@ -556,6 +558,10 @@ class ArtSweep:
                                        C.c_void_p(_stream(stream)))
         _check(self._ctx, st)
         return rep
+
+    def set_relaxation(self, omega: float):
+        """Over-relaxation factor of the balance update in `iterate` / `iterate_warm` (1: plain)."""
+        _check(self._ctx, load().art_set_relaxation(self._ctx, float(omega)))
 
     def iterate(self, nH, chem: dict, sources, y, tol=1e-6, max_iter=200, stream=None):
         """RT / balance iteration (App. D); nH, y: device FP64 [z][y][x]; y updated in place.

@@ -103,6 +103,7 @@ struct art_ctx {
     double spec_sigma[4] = {0, 0, 0, 0}, spec_frac[4] = {0, 0, 0, 0};
     int plane_axis = 0, plane_dir = 1;   // plane-parallel incident flux of the iteration
     double plane_flux = 0.0;             // photons/s/cm^2 (0: none)
+    double relax = 1.0;                  // over-relaxation factor of the balance update (1: plain)
     art_ctx *coarse = nullptr;  // coarse-mesh sweep of the surrogate
     void *ablation = nullptr;   // thread-per-ray comparison sweep (tables, graphs)
     art_sur_bufs sur;

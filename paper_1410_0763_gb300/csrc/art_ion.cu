@@ -340,6 +340,7 @@ struct BalArgs {
     int solve;                  // 0: only derive kappa, eps from y
     const double *T;            // non-null: eps takes (alpha_A - alpha_B)(T) per cell times eps_base
     double eps_base;            // G h nu0 dx / dnu
+    double relax;               // y <- y_old + relax (y_balance - y_old), clamped to [0, 1]
 };
 
 // Temperature fits of the energy equation (App. C), T in K; sources in art.h.
@@ -377,6 +378,10 @@ __global__ void balance_kernel(const BalArgs p)
             const double den = 2.0 * a + c + g + sq;
             y = den > 0.0 ? 2.0 * a / den : 0.0;
             x = den > 0.0 ? (c + g + sq) / den : 1.0;
+            if (p.relax != 1.0) {
+                y = fmin(fmax(yo + p.relax * (y - yo), 0.0), 1.0);
+                x = 1.0 - y;
+            }
             const double ne_new = x * nH, ne_old = (1.0 - yo) * nH;
             r = ne_new > 0.0 ? fabs(ne_new - ne_old) / ne_new : (ne_old > 0.0 ? INFINITY : 0.0);
             p.y[i] = y;
@@ -576,6 +581,7 @@ BalArgs balance_args(art_ctx *ctx, const art_chem *ch, const double *nH, double 
     ba.solve = 0;
     ba.T = nullptr;
     ba.eps_base = G * ch->h * ch->nu0 * ctx->grid.dx_cm / ch->dnu;
+    ba.relax = ctx->relax;
     return ba;
 }
 
@@ -676,6 +682,7 @@ art_status iterate_impl(art_ctx *ctx, art_net *net, const art_chem *ch, const do
         ctx->coarse->plane_axis = ctx->plane_axis;   // a flux per area: the same on the coarse mesh
         ctx->coarse->plane_dir = ctx->plane_dir;
         ctx->coarse->plane_flux = ctx->plane_flux;
+        ctx->coarse->relax = ctx->relax;
         for (int b = 0; b < 4; ++b) {
             ctx->coarse->spec_sigma[b] = ctx->spec_sigma[b];
             ctx->coarse->spec_frac[b] = ctx->spec_frac[b];
@@ -1095,7 +1102,8 @@ __device__ __forceinline__ double th_cooling(const ThermParams &q, double nH, do
 // with f > 0 so far, within [T_min, T_max]): a step that leaves it, or a
 // non-positive f', bisects once both ends are known and otherwise doubles or
 // halves T towards the sign change.  Stops when a step moves T by at most
-// 1e-14 T, at a bound, or after 100 steps.
+// 1e-12 T (the error is then of order its square), at a bound, or after 100
+// steps.
 __device__ double th_energy_step(const ThermParams &q, double nH, double y0, double T0, double y1, double H1,
                                  double dt)
 {
@@ -1122,7 +1130,7 @@ __device__ double th_energy_step(const ThermParams &q, double nH, double y0, dou
             else if (f < 0.0) Tn = fmin(2.0 * T, q.T_max);
             else Tn = fmax(0.5 * T, q.T_min);
         }
-        if (fabs(Tn - T) <= 1e-14 * T) return Tn;
+        if (fabs(Tn - T) <= 1e-12 * T) return Tn;   // quadratic: Tn is then exact to rounding
         T = Tn;
     }
     return T;
@@ -1418,6 +1426,14 @@ art_status art_evolve_thermal(art_ctx *ctx, const art_chem *ch, const art_therma
                               art_evolve_report *rep, void *stream)
 {
     return evolve_thermal_impl(ctx, ch, th, nH, src, n_src, opt, y, T, rep, static_cast<cudaStream_t>(stream));
+}
+
+art_status art_set_relaxation(art_ctx *ctx, double omega)
+{
+    if (!ctx) return ART_E_INVALID;
+    if (!(omega > 0.0 && omega < 2.0)) return art_fail(ctx, ART_E_INVALID, "art_set_relaxation: 0 < omega < 2");
+    ctx->relax = omega;
+    return ART_OK;
 }
 
 art_status art_set_plane_source(art_ctx *ctx, int axis, int dir, double flux)

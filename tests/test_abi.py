@@ -82,6 +82,7 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.art_set_boundary_intensity(None, None) == art.ART_E_INVALID
     assert lib.art_plane_source(None, None, None, 0, 1, None, None, None) == art.ART_E_INVALID
     assert lib.art_set_plane_source(None, 0, 1, 1.0) == art.ART_E_INVALID
+    assert lib.art_set_relaxation(None, 1.3) == art.ART_E_INVALID
     assert lib.art_evolve_ionization(None, None, None, None, 0, None, None, None, None) == art.ART_E_INVALID
     assert lib.art_evolve_options_default(None) == art.ART_E_INVALID
     assert lib.art_ablation_sweep(None, 0, None, None) == art.ART_E_INVALID

@@ -242,3 +242,26 @@ def test_diffuse_field_enlarges_ionized_region_gpu():
     assert rep_d.converged and rep_o.converged
     assert np.all(y_diff <= y_otsa * (1 + 1e-4))
     assert np.sum(1 - y_diff) > 1.02 * np.sum(1 - y_otsa)
+
+
+@pytest.mark.parametrize("omega", [0.8, 1.3])
+def test_relaxed_iteration_reaches_the_oracle_fixed_point(orc, omega):
+    """Over-relaxation changes the path, not the fixed point: the relaxed GPU
+    iteration, run to 1e-8, ends within 1e-4 of the oracle's plain iteration
+    run to 1e-10."""
+    case = wl.hii_region(n=16, nside=2, box_kpc=1.6)
+    srcs = [(p[0], p[1], p[2], q) for p, q in zip(case.pos, case.Q)]
+    sw = art.ArtSweep(case.nH.shape, case.nside, 1, field_form=art.ART_FIELDS_EPS, dx_cm=case.chem["dx"])
+    sw.set_relaxation(omega)
+    y = torch.as_tensor(case.y0, dtype=torch.float64, device="cuda").clone()
+    rep, _ = sw.iterate(torch.as_tensor(case.nH, dtype=torch.float64, device="cuda"), case.chem, srcs, y, tol=1e-8,
+                        max_iter=400)
+    for bad in (0.0, 2.0, float("nan")):
+        with pytest.raises(art.ArtError) as ex:
+            sw.set_relaxation(bad)
+        assert ex.value.status == art.ART_E_INVALID
+    sw.close()
+    y_orc, it_orc, _, conv = orc.iterate(case.nH, case.nside, case.chem, case.pos, case.Q, case.y0, 1e-10, 400)
+    assert conv and rep.converged
+    yg = y.cpu().numpy()
+    assert rel(yg, y_orc) < 1e-4 and rel(1 - yg, 1 - y_orc) < 1e-4
