@@ -152,8 +152,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
 // accumulators and the group loads (G + 2) 9 tiles instead of 27 G.  Every
 // accumulator still receives its 27 taps in tap order.  The loaded tiles
 // stream through a ring of shared-memory stages; the 27 tap weight blocks
-// stay in shared memory.  One thread issues the MMAs (M = 128, N = COUT,
-// K = 16 per instruction) into double-buffered TMEM accumulators (G per
+// stay in shared memory, ordered by (dy, dx) and then dz = +1, 0, -1, so the
+// blocks a loaded tile needs for outputs j = k - 1, k, k + 1 are adjacent:
+// one MMA (M = 128, N = up to 3 COUT, K = 16 per instruction) covers them,
+// into adjacent columns of the double-buffered TMEM accumulators (G per
 // buffer) that four epilogue warps drain.
 // ---------------------------------------------------------------------------
 template <int CIN, int COUT, int G> struct ConvSmem {
@@ -234,7 +236,9 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
         if (lane == 0) {
             if (!p.test_stall) {
                 mbar_expect_tx(w_bar, L::W_BYTES);
-                for (int t = 0; t < 27; ++t) tma_load_2d(sW + t * L::W_TAP, &wmap, w_bar, 0, t * COUT);
+                // tap t = (dz + 1) 9 + dyx goes to block dyx 3 + (1 - dz)
+                for (int t = 0; t < 27; ++t)
+                    tma_load_2d(sW + ((t % 9) * 3 + 2 - t / 9) * L::W_TAP, &wmap, w_bar, 0, t * COUT);
             }
             int s = 0;
             uint32_t ph = 0;
@@ -273,7 +277,6 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            constexpr uint32_t idesc = mma_idesc(TILE_M, COUT);
             bool ok = mbar_wait(w_bar, 0, abort);
             int s = 0, it = 0;
             uint32_t ph = 0;
@@ -293,17 +296,24 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                     tc_fence_after();
                     const int k = l / 9 - 1, dyx = l % 9;
                     const uint32_t a_base = sA + s * L::A_BYTES;
+                    // outputs j = jlo..jhi take this tile through taps dz = k - j,
+                    // weight blocks dyx 3 + (j - k + 1), adjacent in j
+                    const int jlo = k - 1 < 0 ? 0 : k - 1, jhi = k + 1 > G - 1 ? G - 1 : k + 1;
+                    auto issue = [&](int j0, int j1, int kk, uint32_t acc) {
+                        const uint32_t d = tmem + (uint32_t)((buf * G + j0) * COUT);
+                        const uint32_t b = sW + (dyx * 3 + (j0 - k + 1)) * L::W_TAP + 32 * kk;
+                        mma_bf16(d, smem_desc(a_base + 32 * kk, CIN * 2), smem_desc(b, CIN * 2),
+                                 mma_idesc(TILE_M, (j1 - j0 + 1) * COUT), acc);
+                    };
 #pragma unroll
-                    for (int j = 0; j < G; ++j) {
-                        const int dz = k - j;
-                        if (dz < -1 || dz > 1) continue;
-                        const int t = (dz + 1) * 9 + dyx;
-                        const uint32_t d = tmem + (uint32_t)((buf * G + j) * COUT);
-                        const uint32_t b_base = sW + t * L::W_TAP;
-#pragma unroll
-                        for (int kk = 0; kk < CIN / 16; ++kk)
-                            mma_bf16(d, smem_desc(a_base + 32 * kk, CIN * 2), smem_desc(b_base + 32 * kk, CIN * 2),
-                                     idesc, (t | kk) != 0);
+                    for (int kk = 0; kk < CIN / 16; ++kk) {
+                        if (dyx == 0 && kk == 0 && k + 1 <= jhi) {
+                            // output k + 1 starts here (its first tap, dz = -1, dyx = 0)
+                            if (jlo <= k) issue(jlo, k, 0, 1u);
+                            issue(k + 1, k + 1, 0, 0u);
+                        } else {
+                            issue(jlo, jhi, kk, 1u);
+                        }
                     }
                     mma_commit(empty_bar(s));
                     if (++s == CONV_STAGES) {
