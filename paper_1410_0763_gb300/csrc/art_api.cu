@@ -553,11 +553,12 @@ art_status create_common(const art_grid *grids, const int *n_side, int n_grids, 
         pick = ctx->opt.variant - 1;
         if (pick >= kNumVariants || kVariants[pick].prec != ctx->prec) pick = -2;
     } else {
-        // measured on GB300: the 32 x 8 tile wins for grids below ~100^3
-        // cells (more CTAs per launch), the 32 x 16 tile above
+        // measured on GB300: the 32 x 8 tile with three direction pairs per
+        // exchange (variant 15) wins for grids below ~100^3 cells (more CTAs
+        // per launch), the 32 x 16 tile above
         if (ctx->prec == ART_FP32 && largest < 100LL * 100 * 100 && !ctx->opt.tile_b && !ctx->opt.tile_c &&
             !ctx->opt.slab)
-            pick = 1;
+            pick = 14;
         for (int v = 0; v < kNumVariants && pick == -1; ++v) {
             const KVariant &k = kVariants[v];
             if (k.prec != ctx->prec) continue;

@@ -71,7 +71,7 @@ def test_fp32_ragged_noncubic(orc, tiles):
     assert rel(J, j_o) < 1e-5
 
 
-@pytest.mark.parametrize("variant", [3, 4, 6, 9, 10])
+@pytest.mark.parametrize("variant", [2, 3, 4, 6, 9, 10, 15])
 def test_fp32_ragged_by_variant(orc, variant):
     """Variants that share a tile shape with another (thread count, pairs per
     exchange, CTAs per SM differ), selected by index."""
