@@ -185,6 +185,21 @@ def shadow_clump(n: int = 128, nside: int = 8, box_kpc: float = 6.6, nH: float =
                    np.zeros(0), chem_constants(1e4, dx), 1e-6, box_kpc * KPC, (0, 1, flux))
 
 
+def point_clump(n: int = 128, nside: int = 8, box_kpc: float = 6.6, nH: float = 1e-3, overdensity: float = 200.0,
+                r_kpc: float = 0.56, offset_kpc: float = 0.8, Q: float = 5e48, x0: float = 1e-4) -> HIICase:
+    """The geometry of the paper's Test 2 (Sec. 4.2): a point source of Q
+    photons/s at the box centre, uniform n_H, and a sphere of radius r_kpc at
+    overdensity x n_H centred offset_kpc from the source along +x."""
+    dx = box_kpc * KPC / n
+    c = (np.arange(n) + 0.5) * dx
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    mid = 0.5 * box_kpc * KPC
+    r2 = (x - mid - offset_kpc * KPC) ** 2 + (y - mid) ** 2 + (z - mid) ** 2
+    dens = np.where(r2 <= (r_kpc * KPC) ** 2, overdensity * nH, nH)
+    return HIICase("point_clump", nside, n, dens, np.full((n, n, n), 1.0 - x0), np.array([[n / 2, n / 2, n / 2]]),
+                   np.array([Q]), chem_constants(1e4, dx), 1e-6, box_kpc * KPC)
+
+
 def blackbody_bins(T: float = 1e5, edges_ev=(13.6, 24.6, 54.4, 100.0, 500.0), n_quad: int = 4000):
     """Photon fractions and photon-weighted cross sections of a blackbody of
     temperature T over bins above the HI threshold (hydrogenic sigma0 (nu/nu0)^-3):
