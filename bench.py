@@ -670,6 +670,38 @@ def test2_thermal_measure(torch, dev, n=64, nside=4, F=0.25):
     return out
 
 
+def test2_resolution_measure(torch, dev, n=64, F=0.25, nsides=(1, 2, 4, 8)):
+    """The angular-resolution study of the paper's Test 2 (Sec. 4.2): the
+    setup of test2_thermal_measure with the diffuse field, to 30 Myr, at
+    several N_side.  Reports, per N_side, the mean and the maximum over cells
+    of |y - y_ref| and |T - T_ref| / T_ref against the finest N_side."""
+    from paper_1410_0763_gb300 import art
+    from paper_1410_0763_gb300 import workloads as wl
+    frac, sig, _ = wl.blackbody_bins()
+    res = {}
+    for ns in nsides:
+        case = wl.point_clump(n=n, nside=ns)
+        srcs = [(p[0], p[1], p[2], q) for p, q in zip(case.pos, case.Q)]
+        sw = art.ArtSweep(case.nH.shape, ns, 1, field_form=art.ART_FIELDS_EPS, dx_cm=case.chem["dx"])
+        sw.set_source_spectrum(sig, frac)
+        th = {"e_bin": list(wl.blackbody_heat()), "e_diff": wl.diffuse_band_heat(case.chem)}
+        y = torch.as_tensor(case.y0, dtype=torch.float64, device=dev).clone()
+        T = torch.full_like(y, 100.0)
+        rep = sw.evolve_thermal(torch.as_tensor(case.nH, dtype=torch.float64, device=dev), case.chem, th, srcs, y, T,
+                                30.0 * wl.MYR, F=F, max_iter=300)
+        res[ns] = (y.cpu().numpy(), T.cpu().numpy(), float(rep.seconds), int(rep.iterations))
+        sw.close()
+    yr, Tr = res[nsides[-1]][0], res[nsides[-1]][1]
+    out = {"workload": f"Test 2 with the energy equation and the diffuse field, {n}^3, to 30 Myr, F = {F}; "
+                       f"differences against N_side {nsides[-1]}"}
+    for ns in nsides:
+        yh, Th, sec, it = res[ns]
+        out[f"nside_{ns}"] = {"directions": 12 * ns * ns, "seconds": round(sec, 3), "iterations": it,
+                              "mean_abs_dy": float(np.mean(np.abs(yh - yr))), "max_abs_dy": float(np.max(np.abs(yh - yr))),
+                              "mean_rel_dT": float(np.mean(np.abs(Th - Tr) / Tr))}
+    return out
+
+
 def ablation_measure(torch, dev, reps=3):
     """The paper's ray-grouping comparison (Sec. 5) restated on GB300: the
     thread-per-ray layout of Sec. 3.1 with float atomics against the same
@@ -864,7 +896,8 @@ def run_ours(args, d: Dist):
         except Exception as ex:  # pragma: no cover
             extra["rt_ionization_128_plane_flux"] = {"error": str(ex)}
         for key, fn in (("time_dependent_64", evolve_measure), ("time_dependent_thermal_64", thermal_measure),
-                        ("test3_thermal_64", test3_thermal_measure), ("test2_thermal_64", test2_thermal_measure)):
+                        ("test3_thermal_64", test3_thermal_measure), ("test2_thermal_64", test2_thermal_measure),
+                        ("test2_angular_resolution_64", test2_resolution_measure)):
             try:
                 extra[key] = fn(torch, dev)
             except Exception as ex:  # pragma: no cover
