@@ -451,8 +451,8 @@ art_status art_thermal_default(art_thermal *th);
  * derivative of the cooling fits, kept inside the bracket its iterates build
  * within [T_min, T_max] (bisection, or doubling / halving before both ends
  * are known, when a step leaves it).  The emissivity of the
- * diffuse field takes (alpha_A - alpha_B)(T) per cell; chem->alphaA,
- * alphaB and gcoll are not used.  dt_chem is App. D's (n_e and n_HI only);
+ * diffuse field takes (alpha_A - alpha_B)(T) per cell, evaluated in FP32
+ * like the field it scales; chem->alphaA, alphaB and gcoll are not used.  dt_chem is App. D's (n_e and n_HI only);
  * each RT step iterates until max_cells of |n_e^(i) - n_e^(i-1)| / n_e^(i)
  * and |u^(i) - u^(i-1)| / u^(i) is below eps_iter (App. D).  Point-source and
  * plane-flux heating come from the same kernels as their rates (FP32, the
