@@ -355,7 +355,6 @@ __device__ __forceinline__ double th_alpha_B_ln(double lnl)
 {
     return 2.753e-14 * exp(1.500 * lnl - 2.242 * log1p(exp(0.407 * (lnl - log(2.740)))));
 }
-__device__ __forceinline__ double th_alpha_A(double T) { return th_alpha_A_ln(kLn2THI - log(T)); }
 __device__ __forceinline__ double th_alpha_B(double T) { return th_alpha_B_ln(kLn2THI - log(T)); }
 // alpha_A - alpha_B in FP32, for the emissivity that the FP32 sweep takes (the
 // difference is ~40 % of alpha_A near 1e4 K: no cancellation; ~1e-6 relative)
@@ -1060,89 +1059,101 @@ struct ThermParams {
 // v = (lambda/2.25)^0.376; collisional ionization: 0.5 + 157809.1/T - 0.5 w/(1 + w),
 // w = sqrt(T/1e5); excitation: 118348/T - 0.5 w/(1 + w); free-free:
 // 0.5 + 0.34 e^{-d^2/3} (2d / (3 ln 10)) / g_ff, d = log10 of 10^5.5 / T).
-__device__ __forceinline__ double th_cooling(const ThermParams &q, double nH, double y, double T, double &dC)
+template <typename R>
+__device__ __forceinline__ R th_cooling(const ThermParams &q, R nH, R y, R T, R &dC)
 {
-    const double nHI = y * nH, ne = (1.0 - y) * nH;
-    const double lnT = log(T), iT = 1.0 / T, sT = sqrt(T);
-    const double w = sT * 3.1622776601683794e-3, cden = 1.0 + w;   // sqrt(T / 1e5)
-    double c = 0.0, d = 0.0;
+    const R nHI = y * nH, ne = (R(1) - y) * nH;
+    const R lnT = log(T), iT = R(1) / T, sT = sqrt(T);
+    const R w = sT * R(3.1622776601683794e-3), cden = R(1) + w;   // sqrt(T / 1e5)
+    R c = R(0), d = R(0);
     if (q.cool_mask & 1) {
-        double rc, g;
+        R rc, g;
         if (q.otsa) {
-            const double lnl = kLn2THI - lnT;
-            const double v = exp(0.376 * (lnl - 0.81093021621632877));   // (lambda / 2.25)^0.376
-            rc = 3.435e-30 * T * exp(1.970 * lnl - 3.720 * log1p(v));
-            g = 1.0 - 1.970 + 3.720 * 0.376 * v / (1.0 + v);
+            const R lnl = R(kLn2THI) - lnT;
+            const R v = exp(R(0.376) * (lnl - R(0.81093021621632877)));   // (lambda / 2.25)^0.376
+            rc = R(3.435e-30) * T * exp(R(1.970) * lnl - R(3.720) * log1p(v));
+            g = R(1) - R(1.970) + R(3.720 * 0.376) * v / (R(1) + v);
         } else {
-            const double u = exp(0.7 * (lnT - 13.815510557964274));     // (T / 1e6)^0.7
-            rc = 8.70e-27 * sT * exp(-0.2 * (lnT - 6.907755278982137)) / (1.0 + u);
-            g = 0.3 - 0.7 * u / (1.0 + u);
+            const R u = exp(R(0.7) * (lnT - R(13.815510557964274)));     // (T / 1e6)^0.7
+            rc = R(8.70e-27) * sT * exp(R(-0.2) * (lnT - R(6.907755278982137))) / (R(1) + u);
+            g = R(0.3) - R(0.7) * u / (R(1) + u);
         }
         c += rc * ne * ne;
         d += rc * g * iT * ne * ne;
     }
     if (q.cool_mask & 2) {
-        const double r = 1.27e-21 * sT * exp(-157809.1 * iT) / cden;
+        const R r = R(1.27e-21) * sT * exp(R(-157809.1) * iT) / cden;
         c += r * ne * nHI;
-        d += r * (0.5 + 157809.1 * iT - 0.5 * w / cden) * iT * ne * nHI;
+        d += r * (R(0.5) + R(157809.1) * iT - R(0.5) * w / cden) * iT * ne * nHI;
     }
     if (q.cool_mask & 4) {
-        const double r = 7.50e-19 * exp(-118348.0 * iT) / cden;
+        const R r = R(7.50e-19) * exp(R(-118348.0) * iT) / cden;
         c += r * ne * nHI;
-        d += r * (118348.0 * iT - 0.5 * w / cden) * iT * ne * nHI;
+        d += r * (R(118348.0) * iT - R(0.5) * w / cden) * iT * ne * nHI;
     }
     if (q.cool_mask & 8) {
-        const double dd = 5.5 - lnT * 0.43429448190325176;   // 5.5 - log10 T
-        const double e = 0.34 * exp(-dd * dd / 3.0), gff = 1.1 + e;
-        const double r = 1.42e-27 * gff * sT;
+        const R dd = R(5.5) - lnT * R(0.43429448190325176);   // 5.5 - log10 T
+        const R e = R(0.34) * exp(-dd * dd / R(3)), gff = R(1.1) + e;
+        const R r = R(1.42e-27) * gff * sT;
         c += r * ne * ne;
-        d += r * (0.5 + e * dd * 0.28952965460216784 / gff) * iT * ne * ne;   // 2 / (3 ln 10)
+        d += r * (R(0.5) + e * dd * R(0.28952965460216784) / gff) * iT * ne * ne;   // 2 / (3 ln 10)
     }
     if (q.cool_mask & 16) {
-        c += q.compton * (T - q.T_g) * ne;
-        d += q.compton * ne;
+        c += R(q.compton) * (T - R(q.T_g)) * ne;
+        d += R(q.compton) * ne;
     }
     dC = d;
     return c;
 }
 
-// Newton's method from T on f' = 1.5 k_B n_H (1 + x') + dtc dC/dT, kept inside
-// the bracket its iterates build (the largest T with f < 0 and the smallest
-// with f > 0 so far, within [T_min, T_max]): a step that leaves it, or a
-// non-positive f', bisects once both ends are known and otherwise doubles or
-// halves T towards the sign change.  Stops when a step moves T by at most
-// 1e-12 T (the error is then of order its square), at a bound, or after 100
-// steps.
-__device__ double th_energy_step(const ThermParams &q, double nH, double y0, double T0, double y1, double H1,
-                                 double dt)
+// Newton's method from T on f(T) = A T + dt C(n', T) - B, f' = A + dt dC/dT,
+// kept inside the bracket its iterates build (the largest T with f < 0 and the
+// smallest with f > 0 so far, within [T_min, T_max]): a step that leaves it,
+// or a non-positive f', bisects once both ends are known and otherwise doubles
+// or halves T towards the sign change.  Stops when a step moves T by at most
+// tol T, at a bound, or after max_it steps.
+template <typename R>
+__device__ R th_newton(const ThermParams &q, R nH, R y1, R A, R B, R dt, R T, R tol, int max_it)
 {
-    const double A = 1.5 * q.kB * nH * (2.0 - y1);
-    const double B = 1.5 * q.kB * nH * (2.0 - y0) * T0 + H1 * dt;
-    double T = fmin(fmax(T0, q.T_min), q.T_max);
-    double lo = q.T_min, hi = q.T_max;
+    const R Tmin = R(q.T_min), Tmax = R(q.T_max);
+    T = fmin(fmax(T, Tmin), Tmax);
+    R lo = Tmin, hi = Tmax;
     bool have_lo = false, have_hi = false;
-    for (int it = 0; it < 100; ++it) {
-        double dC;
-        const double f = A * T + dt * th_cooling(q, nH, y1, T, dC) - B;
-        if (f == 0.0) return T;
-        if (f < 0.0) {
+    for (int it = 0; it < max_it; ++it) {
+        R dC;
+        const R f = A * T + dt * th_cooling<R>(q, nH, y1, T, dC) - B;
+        if (f == R(0)) return T;
+        if (f < R(0)) {
             lo = T;
             have_lo = true;
         } else {
             hi = T;
             have_hi = true;
         }
-        const double fp = A + dt * dC;
-        double Tn = fp > 0.0 ? T - f / fp : -1.0;
-        if (!(Tn > lo && Tn < hi) || !(fp > 0.0)) {
-            if (have_lo && have_hi) Tn = 0.5 * (lo + hi);
-            else if (f < 0.0) Tn = fmin(2.0 * T, q.T_max);
-            else Tn = fmax(0.5 * T, q.T_min);
+        const R fp = A + dt * dC;
+        R Tn = fp > R(0) ? T - f / fp : R(-1);
+        if (!(Tn > lo && Tn < hi) || !(fp > R(0))) {
+            if (have_lo && have_hi) Tn = R(0.5) * (lo + hi);
+            else if (f < R(0)) Tn = fmin(R(2) * T, Tmax);
+            else Tn = fmax(R(0.5) * T, Tmin);
         }
-        if (fabs(Tn - T) <= 1e-12 * T) return Tn;   // quadratic: Tn is then exact to rounding
+        if (fabs(Tn - T) <= tol * T) return Tn;
         T = Tn;
     }
     return T;
+}
+
+// The root in FP32 first (to 1e-5 T, ~3 cheap steps), then the FP64 iteration
+// from there, which stops once a step moves T by at most 1e-12 T (Newton's
+// error is then of order its square): usually one or two FP64 cooling
+// evaluations per root instead of ~4.
+__device__ double th_energy_step(const ThermParams &q, double nH, double y0, double T0, double y1, double H1,
+                                 double dt)
+{
+    const double A = 1.5 * q.kB * nH * (2.0 - y1);
+    const double B = 1.5 * q.kB * nH * (2.0 - y0) * T0 + H1 * dt;
+    const float Tf = th_newton<float>(q, (float)nH, (float)y1, (float)A, (float)B, (float)dt, (float)T0, 1e-5f, 50);
+    return th_newton<double>(q, nH, y1, A, B, dt, (double)Tf, 1e-12, 100);
 }
 
 struct ThermArgs {
