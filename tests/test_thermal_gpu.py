@@ -5,9 +5,10 @@ oracle and the invariants its pins use.
   implicit energy solve match the oracle to 1e-9 (FP64 on both sides, no
   FP32 rates involved).
 * Fixed step sequences with a source, on the spot and with the diffuse field
-  transferred, and with a plane flux over 4 blackbody bins: y, 1 - y and T
-  follow the oracle within 1e-4 (the FP32 rates' error, amplified by the
-  chemistry as in the fixed-temperature mode).
+  transferred, with a plane flux over 4 blackbody bins, and in Test 2's
+  geometry (a source beside a dense cold clump): y, 1 - y and T follow the
+  oracle within 1e-4 (the FP32 rates' error, amplified by the chemistry as
+  in the fixed-temperature mode).
 * Neither heating nor cooling: the specific energy (2 - y) T of every cell is
   conserved to rounding.
 * A heated Stromgren region (32^3, on the spot): its volume is the Stromgren
@@ -172,4 +173,29 @@ def test_invalid_thermal_parameters_are_rejected():
         with pytest.raises(art.ArtError) as ex:
             sw.evolve_thermal(nH, case.chem, _th(**bad), _srcs(case), y, T, 1e12)
         assert ex.value.status == art.ART_E_INVALID, bad
+    sw.close()
+
+
+def test_fixed_steps_test2_geometry_match_oracle(orc):
+    """Test 2's geometry (a point source beside a dense cold clump, 4 blackbody
+    bins, the diffuse field transferred) over fixed steps: y, 1 - y and T
+    within 1e-4 of the oracle after every call."""
+    case = wl.point_clump(n=16, nside=2)
+    frac, sig, _ = wl.blackbody_bins()
+    th = _th(e_bin=list(wl.blackbody_heat()), e_diff=wl.diffuse_band_heat(case.chem))
+    T0 = np.full(case.nH.shape, 100.0)
+    dt = 1.0 / (case.chem["alphaB"] * 1e-3) / 800
+    sw = _ctx(case, bins=(frac, sig))
+    nH, y, T = _dev(case.nH), _dev(case.y0), _dev(T0)
+    y_o, T_o = case.y0.copy(), T0.copy()
+    for _ in range(2):
+        rep = sw.evolve_thermal(nH, case.chem, th, _srcs(case), y, T, 3 * dt, dt_fixed=dt, eps_iter=1e-6)
+        assert rep.converged and rep.steps == 3
+        y_o, T_o, steps, *_ = orc.evolve_thermal(case.nH, case.nside, case.chem, th, case.pos, case.Q, y_o, T_o,
+                                                 3 * dt, dt_fixed=dt, eps_iter=1e-9, sigma_bins=sig, frac_bins=frac)
+        yg, Tg = y.cpu().numpy(), T.cpu().numpy()
+        assert rel(yg, y_o) < 1e-4 and rel(1 - yg, 1 - y_o) < 1e-4
+        assert rel(Tg, T_o) < 1e-4
+    clump = case.nH > 1.5e-3
+    assert T_o.max() > 5e3 and np.all(T_o[clump] < 1e3)   # heated near the source, the clump still cold
     sw.close()
