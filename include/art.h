@@ -255,6 +255,29 @@ art_status art_band_integral(double sigma0, double h, double nu0, double nu_lo, 
 art_status art_sweep(art_ctx *ctx, void *J, void *J_in, void *gamma, int on_device, void *stream);
 
 /*
+ * Read and clear the context's sweep error word, synchronizing `stream`.  The
+ * wavefront sweep (the default for FP32 contexts with the paper's averaging)
+ * hands ray intensities between thread blocks through device memory, and
+ * every wait for an upstream block is bounded in time (art_sweep_set_wait);
+ * a wait that runs out ends the sweep early and leaves its outputs invalid.
+ * art_sweep with device outputs returns without waiting, so a caller checks
+ * here; art_sweep with host outputs, art_sweep_stream and the iterations check
+ * on their own.  Returns ART_OK, ART_E_TIMEOUT (a wait ran out) or ART_E_CUDA
+ * (an index check of a checked build failed).  Errors: ART_E_INVALID (NULL).
+ */
+art_status art_sweep_check(art_ctx *ctx, void *stream);
+
+/*
+ * Bound of every wait of the wavefront sweep (seconds, default 2) and a test
+ * hook: stall_unit >= 0 names a unit (CTA tile) that computes but never
+ * publishes its progress, so the tiles downstream of it wait until the bound
+ * and the sweep reports ART_E_TIMEOUT through art_sweep_check; -1 (the
+ * default) disables the hook.  Errors: ART_E_INVALID (NULL ctx, bound not in
+ * (0, 60], stall_unit < -1).
+ */
+art_status art_sweep_set_wait(art_ctx *ctx, double seconds, int stall_unit);
+
+/*
  * The sweeps of n_sets independent field sets held in host memory, streamed
  * through the device: the host-to-device copy and validation of set k + 1 and
  * the device-to-host copy of set k - 1 run on the library's own copy streams

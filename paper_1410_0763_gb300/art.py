@@ -161,6 +161,10 @@ def load() -> C.CDLL:
                                               C.POINTER(ArtEvolveOptions), P, C.POINTER(ArtEvolveReport), P]
         lib.art_evolve_ionization.restype = C.c_int
         lib.art_sweep.argtypes = [P, P, P, P, C.c_int, P]
+        lib.art_sweep_check.argtypes = [P, P]
+        lib.art_sweep_check.restype = C.c_int
+        lib.art_sweep_set_wait.argtypes = [P, C.c_double, C.c_int]
+        lib.art_sweep_set_wait.restype = C.c_int
         lib.art_sweep_stream.argtypes = [P, C.c_int, P, P, P, P, P, P]
         lib.art_sweep_stream.restype = C.c_int
         lib.art_count_segments.argtypes = [C.POINTER(ArtGrid), C.c_int, C.c_double, C.POINTER(C.c_int64)]
@@ -706,6 +710,15 @@ class ArtSweep:
         _check(self._ctx, art_sweep(self._ctx, ptrs[0], ptrs[1], ptrs[2], on_dev,
                                     _stream(stream) if on_dev else 0))
         return J, J_in, gamma
+
+    def check(self, stream=None) -> int:
+        """art_sweep_check: synchronize `stream` and return the status of the sweeps since the last
+        check (ART_OK, ART_E_TIMEOUT when a wait of the wavefront sweep ran out)."""
+        return int(load().art_sweep_check(self._ctx, C.c_void_p(_stream(stream))))
+
+    def set_wait(self, seconds: float = 2.0, stall_unit: int = -1):
+        """art_sweep_set_wait: bound of the wavefront sweep's waits, and the stalled-unit test hook."""
+        _check(self._ctx, load().art_sweep_set_wait(self._ctx, float(seconds), int(stall_unit)))
 
     def sweep_stream(self, kappas, srcs, J=None, J_in=None, gamma=None, stream=None):
         """Sweeps of len(kappas) field sets held in host memory (art_sweep_stream): the copies of

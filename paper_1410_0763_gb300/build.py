@@ -19,9 +19,9 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "lib")
 LIB = os.path.join(OUT_DIR, "libart.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["art_api.cu", "art_sweep_exact.cu", "art_geometry.cpp", "art_probe.cu", "art_noalloc.cu", "art_ion.cu",
+SOURCES = ["art_api.cu", "art_wave.cu", "art_sweep_exact.cu", "art_geometry.cpp", "art_probe.cu", "art_noalloc.cu", "art_ion.cu",
            "art_net.cu", "art_ablation.cu"]
-HEADERS = ["art_kernels.cuh", "art_geometry.hpp", "art_ctx.hpp", "art_net_kernels.cuh", "art_net_internal.hpp",
+HEADERS = ["art_kernels.cuh", "art_wave.cuh", "art_geometry.hpp", "art_ctx.hpp", "art_net_kernels.cuh", "art_net_internal.hpp",
            "art_variants.inc"]
 
 
@@ -47,6 +47,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     obj_dir = os.path.join(OUT_DIR, "obj")
     os.makedirs(obj_dir, exist_ok=True)
     common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC] + ARCH
+    if os.environ.get("ART_WAVE_CHECK") == "1":
+        # the wavefront kernel tests every global index before it is used (slower; for checking runs)
+        common += ["-DART_WAVE_CHECK"]
     if verbose:
         common += ["-Xptxas", "-v"]
 

@@ -298,8 +298,11 @@ template <typename real> art_status upload_gridinfo(art_ctx *ctx)
 
 // Select a kernel variant: build its tables and (re)allocate the buffers that
 // depend on them.  Field, plane and staging buffers do not depend on it.
+art_status setup_wave(art_ctx *ctx, int w);
+
 art_status setup_variant(art_ctx *ctx, int variant)
 {
+    if (variant >= kNumVariants) return setup_wave(ctx, variant - kNumVariants);
     const KVariant &k = kVariants[variant];
     const int per_sm = k.prepare();
     if (per_sm < 1) return fail(ctx, ART_E_CUDA, "sweep kernel variant cannot be launched on this device");
@@ -307,6 +310,7 @@ art_status setup_variant(art_ctx *ctx, int variant)
         cudaGraphExecDestroy(ctx->gexec);
         ctx->gexec = nullptr;
     }
+    art_wave_free(ctx);
     ctx->variant = variant;
     ctx->TB = k.tb;
     ctx->TC = k.tc;
@@ -380,7 +384,88 @@ art_status setup_variant(art_ctx *ctx, int variant)
     CK(ctx, cudaMemcpy(ctx->d_dirs, t.dirs.data(), db, cudaMemcpyHostToDevice));
     CK(ctx, cudaMemcpy(ctx->d_classes, t.classes.data(), cb, cudaMemcpyHostToDevice));
     CK(ctx, cudaMemcpy(ctx->d_work, t.work.data(), wb, cudaMemcpyHostToDevice));
+    // ray-plane buffers of the slab-block launches
+    const size_t pb = (size_t)std::max<long long>(1, ctx->plane_elems) * ctx->rsz;
+    if (ctx->plane_bytes != pb) {
+        dev_free(ctx, ctx->d_plane[0], ctx->plane_bytes_0);
+        dev_free(ctx, ctx->d_plane[1], ctx->plane_bytes_1);
+        if ((s = dev_alloc(ctx, &ctx->d_plane[0], pb)) != ART_OK) return s;
+        ctx->plane_bytes_0 = pb;
+        if ((s = dev_alloc(ctx, &ctx->d_plane[1], pb)) != ART_OK) return s;
+        ctx->plane_bytes_1 = pb;
+        ctx->plane_bytes = pb;
+    }
     return ART_OK;
+}
+
+// Select wave variant w (art_wave.cu): its tables, buffers and J partials; the
+// slab-block tables and planes are released.
+art_status setup_wave(art_ctx *ctx, int w)
+{
+    if (ctx->prec != ART_FP32 || ctx->opt.averaging != ART_AVG_PAPER)
+        return fail(ctx, ART_E_INVALID, "the wavefront sweep is FP32 with the paper's averaging");
+    if (ctx->gexec) {
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+    }
+    dev_free(ctx, ctx->d_jpart, ctx->jpart_bytes);
+    dev_free(ctx, ctx->d_segs, ctx->segs_bytes);
+    dev_free(ctx, ctx->d_dirs, ctx->dirs_bytes);
+    dev_free(ctx, ctx->d_classes, ctx->classes_bytes);
+    dev_free(ctx, ctx->d_work, ctx->work_bytes);
+    dev_free(ctx, ctx->d_counter, ctx->counter_bytes);
+    dev_free(ctx, ctx->d_gridinfo, ctx->gridinfo_bytes);
+    dev_free(ctx, ctx->d_plane[0], ctx->plane_bytes_0);
+    dev_free(ctx, ctx->d_plane[1], ctx->plane_bytes_1);
+    ctx->plane_bytes = 0;
+    art_status s = art_wave_setup(ctx, w);
+    if (s != ART_OK) return s;
+    ctx->variant = kNumVariants + w;
+    ctx->TB = 8 * ctx->wave.wb;
+    ctx->TC = 4 * ctx->wave.wc;
+    ctx->BLK = 0;
+    ctx->KP = 0;
+    ctx->split = 0;
+    ctx->nblocks = 1;
+    ctx->n_work = ctx->wave.n_units;
+    ctx->n_ctas = ctx->wave.n_units;
+    ctx->persistent = 0;
+    ctx->plane_elems = 0;
+    const size_t jb = (size_t)std::max<long long>(1, ctx->wave.jpart_floats) * sizeof(float);
+    if ((s = dev_alloc(ctx, &ctx->d_jpart, jb)) != ART_OK) return s;
+    ctx->jpart_bytes = jb;
+    const size_t gb = ctx->grids.size() * sizeof(GridDev<double>);
+    if ((s = dev_alloc(ctx, &ctx->d_gridinfo, gb)) != ART_OK) return s;
+    ctx->gridinfo_bytes = gb;
+    return upload_gridinfo<float>(ctx);
+}
+
+// The wave variant for the context's largest class: the fewest direction
+// slots that hold it, else the most (classes split into groups); -1 if the
+// context cannot use the wavefront sweep.
+int pick_wave(const art_ctx *ctx)
+{
+    if (ctx->prec != ART_FP32 || ctx->opt.averaging != ART_AVG_PAPER) return -1;
+    int maxc = 0;
+    for (const art_grid_host &g : ctx->grids) {
+        std::vector<double> xyz;
+        healpix_directions(g.nside, xyz);
+        int cnt[24] = {0};
+        const bool ranged = ctx->opt.dir_end > ctx->opt.dir_begin;
+        for (int d = 0; d < g.nd; ++d)
+            if (!ranged || (d >= ctx->opt.dir_begin && d < ctx->opt.dir_end))
+                ++cnt[frame_of(&xyz[3 * d], ctx->opt.tie_tol).cls];
+        for (int c = 0; c < 24; ++c) maxc = std::max(maxc, cnt[c]);
+    }
+    int best = -1;
+    for (int w = 0; w < art_wave_variants(); ++w) {
+        const int dm = art_wave_dmax(w);
+        if (dm >= maxc && (best < 0 || dm < art_wave_dmax(best))) best = w;
+    }
+    if (best < 0)
+        for (int w = 0; w < art_wave_variants(); ++w)
+            if (best < 0 || art_wave_dmax(w) > art_wave_dmax(best)) best = w;
+    return best;
 }
 
 template <typename real> art_status do_sweep(art_ctx *ctx, real *J, real *Jin, real *gam, cudaStream_t st)
@@ -415,7 +500,13 @@ template <typename real> art_status do_sweep(art_ctx *ctx, real *J, real *Jin, r
         }
         if (ctx->persistent) CK(ctx, cudaMemsetAsync(ctx->d_counter, 0, ctx->counter_bytes, st));
         if (ctx->profiling) CK(ctx, cudaEventRecord(e0, st));
-        for (int k = 0; k < ctx->nblocks; ++k) {
+        if (ctx->wave.on) {
+            art_status ws = art_wave_launch(ctx, reinterpret_cast<const float2 *>(a.field0),
+                                            reinterpret_cast<const float2 *>(a.field1),
+                                            reinterpret_cast<const float2 *>(a.field2), float(ctx->i_bc[b]), st);
+            if (ws != ART_OK) return ws;
+        }
+        for (int k = 0; k < ctx->nblocks && !ctx->wave.on; ++k) {
             a.kblock = k;
             a.plane_in = planes[k & 1];
             a.plane_out = planes[(k + 1) & 1];
@@ -549,9 +640,18 @@ art_status create_common(const art_grid *grids, const int *n_side, int n_grids, 
     ctx->early_launch = ctx->opt.early_launch >= 0;
 
     int pick = -1;
-    if (ctx->opt.variant > 0) {
+    if (ctx->opt.variant > kNumVariants) {
+        pick = ctx->opt.variant - 1;
+        if (pick - kNumVariants >= art_wave_variants() || ctx->prec != ART_FP32 ||
+            ctx->opt.averaging != ART_AVG_PAPER)
+            pick = -2;
+    } else if (ctx->opt.variant > 0) {
         pick = ctx->opt.variant - 1;
         if (pick >= kNumVariants || kVariants[pick].prec != ctx->prec) pick = -2;
+    } else if (!ctx->opt.tile_b && !ctx->opt.tile_c && !ctx->opt.slab && !ctx->opt.dir_split &&
+               ctx->opt.persistent == 0 && pick_wave(ctx) >= 0) {
+        // the wavefront sweep, unless the options ask for a slab-block shape
+        pick = kNumVariants + pick_wave(ctx);
     } else {
         // measured on GB300: the 32 x 8 tile with three direction pairs per
         // exchange (variant 15) wins for grids below ~100^3 cells (more CTAs
@@ -586,8 +686,6 @@ art_status create_common(const art_grid *grids, const int *n_side, int n_grids, 
         }                                                       \
     } while (0)
     ALLOC(ctx->d_field, 3 * (size_t)nu_bins * n * 2 * rs);
-    ALLOC(ctx->d_plane[0], (size_t)ctx->plane_elems * rs);
-    ALLOC(ctx->d_plane[1], (size_t)ctx->plane_elems * rs);
     ALLOC(ctx->d_stage, 2 * (size_t)nu_bins * n * rs);
     ALLOC(ctx->d_out, (2 * (size_t)nu_bins + 1) * n * rs);
     ALLOC(ctx->d_flag, sizeof(int));
@@ -680,11 +778,14 @@ art_status art_autotune(art_ctx *ctx, int reps, int *best_variant, void *stream)
     // launch forms tried: both unless the options fixed one
     const int forms[2] = {1, 0};
     const int nforms = ctx->opt.persistent == 0 ? 2 : 1;
-    for (int v = 0; v < kNumVariants && s == ART_OK; ++v) {
-        if (kVariants[v].prec != ctx->prec || kVariants[v].prepare() < 1) continue;
+    const bool wave_ok = ctx->prec == ART_FP32 && ctx->opt.averaging == ART_AVG_PAPER;
+    const int nv = kNumVariants + (wave_ok ? art_wave_variants() : 0);
+    for (int v = 0; v < nv && s == ART_OK; ++v) {
+        const bool wave = v >= kNumVariants;
+        if (!wave && (kVariants[v].prec != ctx->prec || kVariants[v].prepare() < 1)) continue;
         if ((s = setup_variant(ctx, v)) != ART_OK) break;
-        for (int f = 0; f < nforms && s == ART_OK; ++f) {
-            if (nforms == 2) ctx->persistent = forms[f];
+        for (int f = 0; f < (wave ? 1 : nforms) && s == ART_OK; ++f) {
+            if (nforms == 2 && !wave) ctx->persistent = forms[f];
             if ((s = sweep_launches(ctx, nullptr, jin, nullptr, st)) != ART_OK) break;   // warm-up
             if (cudaEventRecord(e0, st) != cudaSuccess) {
                 s = fail(ctx, ART_E_CUDA, "art_autotune: cudaEventRecord failed");
@@ -708,9 +809,9 @@ art_status art_autotune(art_ctx *ctx, int reps, int *best_variant, void *stream)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->profiling = keep_prof;
-    ctx->persistent = best_pers;
     if (s != ART_OK) return s;
     if ((s = setup_variant(ctx, best)) != ART_OK) return s;
+    if (best < kNumVariants) ctx->persistent = best_pers;
     if (best_variant) *best_variant = best + 1;
     return ART_OK;
 }
@@ -796,6 +897,7 @@ art_status art_destroy(art_ctx *ctx)
                     ctx->it.hpt, ctx->it.Tit};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    art_wave_free(ctx);
     void *sur[] = {ctx->sur.kc, ctx->sur.ec, ctx->sur.jc, ctx->sur.o, ctx->sur.eref, ctx->sur.nHc, ctx->sur.yc};
     for (void *p : sur)
         if (p) cudaFree(p);
@@ -826,7 +928,7 @@ art_status art_get_stats(const art_ctx *ctx, art_sweep_stats *s)
     s->segments = ctx->seg_count * ctx->nbins;
     s->n_dirs = ctx->nd;
     s->n_classes = ctx->n_classes;
-    s->launches = ctx->nblocks + 1;
+    s->launches = ctx->wave.on ? 2 : ctx->nblocks + 1;
     s->ctas_per_launch = ctx->persistent ? ctx->n_ctas : ctx->n_work;
     s->tile_b = ctx->TB;
     s->tile_c = ctx->TC;
@@ -834,7 +936,7 @@ art_status art_get_stats(const art_ctx *ctx, art_sweep_stats *s)
     s->dir_split = ctx->split;
     s->device_bytes = ctx->dev_bytes;
     s->variant = ctx->variant + 1;
-    s->group = 2 * ctx->KP;
+    s->group = ctx->wave.on ? ctx->wave.dmax : 2 * ctx->KP;
     s->n_grids = (int32_t)ctx->grids.size();
     s->work_items = ctx->n_work;
     s->persistent = ctx->persistent;
@@ -1015,6 +1117,28 @@ art_status art_sweep(art_ctx *ctx, void *J, void *J_in, void *gamma, int on_devi
         if (J_in) CK(ctx, cudaMemcpyAsync(J_in, dJin, nb * rs, cudaMemcpyDeviceToHost, st));
         if (gamma) CK(ctx, cudaMemcpyAsync(gamma, dG, ctx->ncell * rs, cudaMemcpyDeviceToHost, st));
         CK(ctx, cudaStreamSynchronize(st));
+        return art_wave_status(ctx, st);
+    }
+    return ART_OK;
+}
+
+art_status art_sweep_check(art_ctx *ctx, void *stream)
+{
+    if (!ctx) return ART_E_INVALID;
+    return art_wave_status(ctx, static_cast<cudaStream_t>(stream));
+}
+
+art_status art_sweep_set_wait(art_ctx *ctx, double seconds, int stall_unit)
+{
+    if (!ctx) return ART_E_INVALID;
+    if (!(seconds > 0.0) || seconds > 60.0)
+        return fail(ctx, ART_E_INVALID, "art_sweep_set_wait: the bound must be in (0, 60] seconds");
+    if (stall_unit < -1) return fail(ctx, ART_E_INVALID, "art_sweep_set_wait: stall_unit must be >= -1");
+    ctx->wave.wait_ns = (long long)(seconds * 1e9);
+    ctx->wave.stall_unit = stall_unit;
+    if (ctx->gexec) {   // the captured launch holds the old values
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
     }
     return ART_OK;
 }

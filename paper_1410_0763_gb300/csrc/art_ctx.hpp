@@ -45,6 +45,19 @@ struct art_sur_bufs {
     double *nHc = nullptr, *yc = nullptr;   // coarse-mesh solve of the warm start
 };
 
+// Wavefront sweep (art_wave.cuh): tables and buffers of the selected shape.
+struct art_wave_state {
+    bool on = false;
+    int variant = 0, wb = 0, wc = 0, dmax = 0, n_units = 0;
+    void *units = nullptr, *classes = nullptr, *segs = nullptr, *seg_off = nullptr;
+    float *edge = nullptr;      // edge intensities handed between CTA tiles
+    int *flags = nullptr;       // [0] error word, [1] ticket, then per-unit progress flags
+    size_t flag_bytes = 0;
+    long long edge_floats = 0, jpart_floats = 0, bytes = 0;
+    long long wait_ns = 2000000000LL;   // bound of every wait in the kernel
+    int stall_unit = -1;                 // test hook (see art_wave_test_stall)
+};
+
 struct art_ctx {
     art_grid grid{};           // first grid (the only one outside batches)
     int nside = 0, nbins = 0;
@@ -76,6 +89,7 @@ struct art_ctx {
     // device memory
     void *d_field = nullptr;   // [3][nbins][ncell] vec2
     void *d_plane[2] = {nullptr, nullptr};
+    size_t plane_bytes = 0, plane_bytes_0 = 0, plane_bytes_1 = 0;
     void *d_jpart = nullptr;   // [n_part][ncell] real, natural layout
     void *d_segs = nullptr;
     art::DirDev *d_dirs = nullptr;
@@ -107,6 +121,7 @@ struct art_ctx {
     art_ctx *coarse = nullptr;  // coarse-mesh sweep of the surrogate
     void *ablation = nullptr;   // thread-per-ray comparison sweep (tables, graphs)
     art_sur_bufs sur;
+    art_wave_state wave;
 };
 
 
@@ -115,3 +130,12 @@ art_status art_fail(art_ctx *ctx, art_status st, const std::string &msg);
 void art_internal_ablation_free(art_ctx *ctx);
 art_status art_internal_sweep(art_ctx *ctx, void *J, void *J_in, void *gamma, cudaStream_t st);
 art_status art_internal_layout(art_ctx *ctx, const void *kappa, const void *src, cudaStream_t st);
+// wavefront sweep (art_wave.cu)
+int art_wave_variants();
+int art_wave_dmax(int w);
+void art_wave_free(art_ctx *ctx);
+art_status art_wave_setup(art_ctx *ctx, int w);
+art_status art_wave_launch(art_ctx *ctx, const float2 *f0, const float2 *f1, const float2 *f2, float i_bc,
+                           cudaStream_t st);
+art_status art_wave_status(art_ctx *ctx, cudaStream_t st);
+art_status art_wave_status_async(art_ctx *ctx, int *host, cudaStream_t st);

@@ -1,0 +1,401 @@
+// art_wave.cu -- host side of the wavefront sweep (art_wave.cuh): the unit,
+// class and direction tables of a context, its device buffers, the launch of
+// one bin, and the compiled kernel shapes.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "art.h"
+#include "art_ctx.hpp"
+#include "art_geometry.hpp"
+#include "art_wave.cuh"
+
+using namespace art;
+
+namespace {
+
+#define WCK(ctx, call)                                                                            \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return art_fail(ctx, e_ == cudaErrorMemoryAllocation ? ART_E_OOM : ART_E_CUDA,        \
+                            std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+    } while (0)
+
+template <int WB, int WC, int DMAX, int MINB>
+cudaError_t wave_launch(const WaveArgs &a, int n_units, cudaStream_t st)
+{
+    using Sh = WaveShape<WB, WC, DMAX>;
+    wave_kernel<WB, WC, DMAX, MINB, 4><<<(unsigned)n_units, Sh::NT, Sh::bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Shared-memory attribute; returns resident CTAs per SM (0 on error).
+template <int WB, int WC, int DMAX, int MINB> int wave_prepare()
+{
+    using Sh = WaveShape<WB, WC, DMAX>;
+    auto kern = wave_kernel<WB, WC, DMAX, MINB, 4>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Sh::NT, Sh::bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm;
+}
+
+struct WVariant {
+    int wb, wc, dmax, minb;
+    cudaError_t (*launch)(const WaveArgs &, int, cudaStream_t);
+    int (*prepare)();
+};
+
+#define ART_WV(wb, wc, dm, mb) {wb, wc, dm, mb, &wave_launch<wb, wc, dm, mb>, &wave_prepare<wb, wc, dm, mb>}
+// Compiled shapes: warps along b and c (a warp tile is 8 x 4 columns), the
+// direction slots of a unit (classes with more directions are split into
+// groups), min CTAs per SM.
+const WVariant kWave[] = {
+    ART_WV(2, 4, 40, 2),   // N_side 8 (26-37 directions per class)
+    ART_WV(2, 4, 12, 3),   // N_side 3-4 (3-11)
+    ART_WV(2, 4, 4, 3),    // N_side 1-2 (1-4)
+    ART_WV(4, 4, 40, 1),   // 32 x 16 columns, N_side 8
+};
+#undef ART_WV
+const int kNumWave = int(sizeof(kWave) / sizeof(kWave[0]));
+
+struct WaveHost {
+    std::vector<WaveClass> classes;
+    std::vector<WaveUnit> units;   // ticket order
+    std::vector<float4> segs;
+    std::vector<long long> seg_off;
+    std::vector<art_grid_host> grids;
+    long long edge_floats = 0, jpart_floats = 0;
+    int max_class = 0;
+};
+
+// A path length with a flag in its sign bit (-0 where the length is 0).
+float signed_len(double ds, bool neg) { return std::copysign(std::fabs(float(ds)), neg ? -1.0f : 1.0f); }
+
+void build_wave(const art_ctx *ctx, const WVariant &v, WaveHost &t)
+{
+    const int TB = 8 * v.wb, TC = 4 * v.wc;
+    long long jpart_off = 0, cell_off = 0;
+    struct Raw {
+        WaveUnit u;
+        int ib, ic, grid, key;
+        long long cost;
+    };
+    std::vector<Raw> raw;
+    for (const art_grid_host &gin : ctx->grids) {
+        art_grid_host gh = gin;
+        const int dims[3] = {gh.g.nx, gh.g.ny, gh.g.nz};
+        const long long strides[3] = {1, (long long)dims[0], (long long)dims[0] * dims[1]};
+        std::vector<double> xyz;
+        healpix_directions(gh.nside, xyz);
+        std::vector<Frame> fr(gh.nd);
+        for (int d = 0; d < gh.nd; ++d) fr[d] = frame_of(&xyz[3 * d], ctx->opt.tie_tol);
+        const bool ranged = ctx->opt.dir_end > ctx->opt.dir_begin;
+        auto in_shard = [&](int d) { return !ranged || (d >= ctx->opt.dir_begin && d < ctx->opt.dir_end); };
+        gh.cell_off = cell_off;
+        gh.jpart_off = jpart_off;
+        gh.seg_count = 0;
+        gh.nblocks = 1;
+        int part = 0;
+        for (int cls = 0; cls < 24; ++cls) {
+            std::vector<int> members;
+            for (int d = 0; d < gh.nd; ++d)
+                if (fr[d].cls == cls && in_shard(d)) members.push_back(d);
+            if (members.empty()) continue;
+            const int n = (int)members.size();
+            t.max_class = std::max(t.max_class, n);
+            const Frame &f0 = fr[members[0]];
+            WaveClass C{};
+            C.a = f0.a;
+            C.sa = f0.sa;
+            C.sb = f0.sb;
+            C.sc = f0.sc;
+            C.Na = dims[f0.a];
+            C.Nb = dims[f0.b];
+            C.Nc = dims[f0.c];
+            C.cell_off = gh.cell_off;
+            C.stride_a = strides[f0.a];
+            C.stride_b = strides[f0.b];
+            C.stride_c = strides[f0.c];
+            const int ci = (int)t.classes.size();
+            t.classes.push_back(C);
+            const int G = (n + v.dmax - 1) / v.dmax;
+            for (int g = 0; g < G; ++g) {
+                const int lo = (int)((long long)n * g / G), hi = (int)((long long)n * (g + 1) / G);
+                const int d0 = (int)t.seg_off.size();
+                for (int i = lo; i < hi; ++i) {
+                    const Frame &f = fr[members[i]];
+                    std::vector<SlabGeom> geo;
+                    slab_geometry(f, C.Na, geo);
+                    t.seg_off.push_back((long long)t.segs.size());
+                    for (const SlabGeom &s : geo) {
+                        const bool firstc = s.nseg == 2 ? s.shc != 0 : (s.nseg == 3 && s.cfirst);
+                        float4 e;
+                        e.x = signed_len(s.ds[0], firstc);
+                        e.y = signed_len(s.ds[1], s.nseg >= 2);
+                        e.z = signed_len(s.ds[2], s.nseg == 3);
+                        e.w = float(f.na);
+                        t.segs.push_back(e);
+                        gh.seg_count += (long long)s.nonzero * C.Nb * C.Nc;
+                    }
+                }
+                const long long jp = gh.jpart_off + (long long)part * gh.ncell;
+                ++part;
+                const int nib = (C.Nb + TB - 1) / TB, nic = (C.Nc + TC - 1) / TC;
+                for (int ic = 0; ic < nic; ++ic)
+                    for (int ib = 0; ib < nib; ++ib) {
+                        Raw r{};
+                        r.u.cls = ci;
+                        r.u.d0 = d0;
+                        r.u.nd = hi - lo;
+                        r.u.tb = ib * TB;
+                        r.u.tc = ic * TC;
+                        r.u.jpart = jp;
+                        // output buffers only where a downstream tile reads them
+                        r.u.eb = ib + 1 < nib ? 0 : -1;
+                        r.u.ec = ic + 1 < nic ? 0 : -1;
+                        r.ib = ib;
+                        r.ic = ic;
+                        r.grid = (int)t.grids.size();
+                        r.key = (int)raw.size();
+                        r.cost = (long long)C.Na * (hi - lo);
+                        raw.push_back(r);
+                    }
+            }
+        }
+        gh.n_part = part;
+        jpart_off += (long long)part * gh.ncell;
+        cell_off += gh.ncell;
+        t.grids.push_back(gh);
+    }
+    t.jpart_floats = jpart_off;
+    // Ticket order: by tile diagonal, so both upstream tiles of a unit come
+    // first; within a diagonal the costliest units first.
+    std::vector<int> idx(raw.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+        const int dx = raw[x].ib + raw[x].ic, dy = raw[y].ib + raw[y].ic;
+        if (dx != dy) return dx < dy;
+        return raw[x].cost > raw[y].cost;
+    });
+    // raw units are laid out tile-row by tile-row per (class, group): the
+    // upstream tiles are at key - 1 (along b) and key - nib (along c)
+    std::vector<int> pos(raw.size());
+    for (size_t i = 0; i < idx.size(); ++i) pos[idx[i]] = (int)i;
+    t.units.resize(raw.size());
+    long long eoff = 0;
+    for (size_t i = 0; i < idx.size(); ++i) {
+        const Raw &r = raw[idx[i]];
+        WaveUnit u = r.u;
+        const WaveClass &C = t.classes[u.cls];
+        const int nib = (C.Nb + TB - 1) / TB;
+        u.up_b = r.ib > 0 ? pos[r.key - 1] : -1;
+        u.up_c = r.ic > 0 ? pos[r.key - nib] : -1;
+        if (u.eb >= 0) {
+            u.eb = eoff;
+            eoff += (long long)C.Na * v.wc * v.dmax * 4;
+        }
+        if (u.ec >= 0) {
+            u.ec = eoff;
+            eoff += (long long)C.Na * v.wb * v.dmax * 8;
+        }
+        t.units[i] = u;
+    }
+    t.edge_floats = eoff;
+}
+
+// Invariants the kernel relies on: every upstream unit has a smaller ticket
+// (so a wait is always on a unit that has started), the upstream tiles are the
+// neighbours of the same (class, group), and every buffer range lies inside
+// its allocation.
+bool wave_tables_ok(const WaveHost &t, const WVariant &v, std::string &why)
+{
+    const int TB = 8 * v.wb, TC = 4 * v.wc;
+    for (size_t i = 0; i < t.units.size(); ++i) {
+        const WaveUnit &u = t.units[i];
+        if (u.cls < 0 || u.cls >= (int)t.classes.size() || u.nd < 1 || u.nd > v.dmax || u.d0 < 0 ||
+            u.d0 + u.nd > (int)t.seg_off.size()) {
+            why = "unit " + std::to_string(i) + ": class or direction range";
+            return false;
+        }
+        const WaveClass &C = t.classes[u.cls];
+        for (int d = u.d0; d < u.d0 + u.nd; ++d)
+            if (t.seg_off[d] < 0 || t.seg_off[d] + C.Na > (long long)t.segs.size()) {
+                why = "unit " + std::to_string(i) + ": segment table range";
+                return false;
+            }
+        const int ups[2] = {u.up_b, u.up_c};
+        for (int k = 0; k < 2; ++k) {
+            const int q = ups[k];
+            const bool edge = k == 0 ? u.tb == 0 : u.tc == 0;
+            if (edge != (q < 0) || q >= (int)i) {
+                why = "unit " + std::to_string(i) + ": upstream ticket order";
+                return false;
+            }
+            if (q < 0) continue;
+            const WaveUnit &w = t.units[q];
+            const bool nb = k == 0 ? (w.tb + TB == u.tb && w.tc == u.tc) : (w.tc + TC == u.tc && w.tb == u.tb);
+            const long long o = k == 0 ? w.eb : w.ec;
+            const long long len = k == 0 ? (long long)C.Na * v.wc * v.dmax * 4 : (long long)C.Na * v.wb * v.dmax * 8;
+            if (!nb || w.cls != u.cls || w.d0 != u.d0 || w.nd != u.nd || o < 0 || o % 4 || o + len > t.edge_floats) {
+                why = "unit " + std::to_string(i) + ": upstream tile or its buffer";
+                return false;
+            }
+        }
+        const long long ncell = (long long)C.Na * C.Nb * C.Nc;
+        if (u.jpart < 0 || u.jpart + ncell > t.jpart_floats) {
+            why = "unit " + std::to_string(i) + ": J partial range";
+            return false;
+        }
+    }
+    return true;
+}
+
+}  // namespace
+
+int art_wave_variants() { return kNumWave; }
+
+// Direction slots of wave variant w (0 if out of range).
+int art_wave_dmax(int w) { return w >= 0 && w < kNumWave ? kWave[w].dmax : 0; }
+
+void art_wave_free(art_ctx *ctx)
+{
+    art_wave_state &W = ctx->wave;
+    void *ptrs[] = {W.units, W.classes, W.segs, W.seg_off, W.edge, W.flags};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    ctx->dev_bytes -= W.bytes;
+    const long long wait_ns = W.wait_ns;
+    const int stall = W.stall_unit;
+    W = art_wave_state{};
+    W.wait_ns = wait_ns;
+    W.stall_unit = stall;
+}
+
+// Build the tables of wave variant w for the context's grids and allocate
+// its buffers (the J partials are the context's d_jpart).
+art_status art_wave_setup(art_ctx *ctx, int w)
+{
+    if (w < 0 || w >= kNumWave) return art_fail(ctx, ART_E_INVALID, "wave variant out of range");
+    const WVariant &v = kWave[w];
+    if (v.prepare() < 1) return art_fail(ctx, ART_E_CUDA, "wave kernel variant cannot be launched on this device");
+    art_wave_free(ctx);
+    WaveHost t;
+    build_wave(ctx, v, t);
+    std::string why;
+    if (!wave_tables_ok(t, v, why)) return art_fail(ctx, ART_E_CUDA, "wave sweep tables inconsistent: " + why);
+    art_wave_state &W = ctx->wave;
+    W.variant = w;
+    W.wb = v.wb;
+    W.wc = v.wc;
+    W.dmax = v.dmax;
+    W.n_units = (int)t.units.size();
+    W.edge_floats = t.edge_floats;
+    W.jpart_floats = t.jpart_floats;
+    ctx->grids = t.grids;
+    ctx->n_classes = (int)t.classes.size();
+    ctx->n_part = 0;
+    ctx->seg_count = 0;
+    for (const art_grid_host &g : ctx->grids) {
+        ctx->n_part += g.n_part;
+        ctx->seg_count += g.seg_count;
+    }
+    const size_t ub = t.units.size() * sizeof(WaveUnit), cb = t.classes.size() * sizeof(WaveClass);
+    const size_t sb = std::max<size_t>(16, t.segs.size() * sizeof(float4));
+    const size_t ob = std::max<size_t>(16, t.seg_off.size() * sizeof(long long));
+    const size_t eb = std::max<size_t>(16, (size_t)t.edge_floats * sizeof(float));
+    const size_t fb = (size_t(W.n_units) * (v.wb + v.wc) + 2) * sizeof(int);
+    struct {
+        void **p;
+        size_t b;
+    } al[] = {{&W.units, ub}, {&W.classes, cb}, {&W.segs, sb}, {&W.seg_off, ob},
+              {reinterpret_cast<void **>(&W.edge), eb}, {reinterpret_cast<void **>(&W.flags), fb}};
+    for (auto &a : al) {
+        const cudaError_t e = cudaMalloc(a.p, a.b ? a.b : 16);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return art_fail(ctx, e == cudaErrorMemoryAllocation ? ART_E_OOM : ART_E_CUDA,
+                            "wave sweep buffers (" + std::to_string(a.b) + " bytes): " + cudaGetErrorString(e));
+        }
+        W.bytes += (long long)a.b;
+        ctx->dev_bytes += (long long)a.b;
+    }
+    W.flag_bytes = fb;
+    WCK(ctx, cudaMemcpy(W.units, t.units.data(), ub, cudaMemcpyHostToDevice));
+    WCK(ctx, cudaMemcpy(W.classes, t.classes.data(), cb, cudaMemcpyHostToDevice));
+    if (!t.segs.empty()) WCK(ctx, cudaMemcpy(W.segs, t.segs.data(), t.segs.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    if (!t.seg_off.empty())
+        WCK(ctx, cudaMemcpy(W.seg_off, t.seg_off.data(), t.seg_off.size() * sizeof(long long), cudaMemcpyHostToDevice));
+    WCK(ctx, cudaMemset(W.flags, 0, fb));
+    W.on = true;
+    return ART_OK;
+}
+
+// One bin's wavefront sweep into the context's J partials: clear the ticket
+// and progress flags (the error word, flags[0], is kept until read), launch.
+art_status art_wave_launch(art_ctx *ctx, const float2 *f0, const float2 *f1, const float2 *f2, float i_bc,
+                           cudaStream_t st)
+{
+    art_wave_state &W = ctx->wave;
+    const WVariant &v = kWave[W.variant];
+    WCK(ctx, cudaMemsetAsync(W.flags + 1, 0, W.flag_bytes - sizeof(int), st));
+    WaveArgs a{};
+    a.field0 = f0;
+    a.field1 = f1;
+    a.field2 = f2;
+    a.segs = static_cast<const float4 *>(W.segs);
+    a.seg_off = static_cast<const long long *>(W.seg_off);
+    a.units = static_cast<const WaveUnit *>(W.units);
+    a.classes = static_cast<const WaveClass *>(W.classes);
+    a.jpart = static_cast<float *>(ctx->d_jpart);
+    a.edge = W.edge;
+    a.err = W.flags;
+    a.ticket = W.flags + 1;
+    a.flags = W.flags + 2;
+    a.n_units = W.n_units;
+    a.field_form = ctx->opt.field_form;
+    a.i_bc = i_bc;
+    a.stall_unit = W.stall_unit;
+    a.wait_ns = W.wait_ns;
+    a.edge_floats = W.edge_floats;
+    a.jpart_floats = W.jpart_floats;
+    if (W.n_units == 0) return ART_OK;
+    WCK(ctx, v.launch(a, W.n_units, st));
+    return ART_OK;
+}
+
+// Read and clear the error word (synchronizes the stream).
+art_status art_wave_status(art_ctx *ctx, cudaStream_t st)
+{
+    art_wave_state &W = ctx->wave;
+    if (!W.on) return ART_OK;
+    int err = 0;
+    WCK(ctx, cudaMemcpyAsync(&err, W.flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    WCK(ctx, cudaStreamSynchronize(st));
+    if (err) WCK(ctx, cudaMemsetAsync(W.flags, 0, sizeof(int), st));
+    if (err & 2) return art_fail(ctx, ART_E_CUDA, "wave sweep: an index check failed (checked build)");
+    if (err & 1) return art_fail(ctx, ART_E_TIMEOUT, "wave sweep: a wait for an upstream tile ran out");
+    return ART_OK;
+}
+
+// Enqueue a copy of the error word to host memory (read after the stream's
+// next synchronization).
+art_status art_wave_status_async(art_ctx *ctx, int *host, cudaStream_t st)
+{
+    art_wave_state &W = ctx->wave;
+    *host = 0;
+    if (!W.on) return ART_OK;
+    WCK(ctx, cudaMemcpyAsync(host, W.flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    return ART_OK;
+}

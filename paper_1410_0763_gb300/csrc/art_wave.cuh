@@ -1,0 +1,535 @@
+// art_wave.cuh -- wavefront sweep kernel (FP32, the paper's cell average).
+//
+// The same discretization as the slab-block kernel of art_kernels.cuh (Sec. 2.2:
+// per direction the family of parallel rays one cell apart, Eq. (rt) per
+// segment, the Delta-tau (= Delta-s) weighted cell average of
+// Eq. (averaged_intensity), the angle average of Eq. (mean_intensity)), laid out
+// as a wavefront so that no ray segment is computed twice and one launch covers
+// the whole sweep of a bin:
+//
+//  * Directions are grouped into octant-axis classes; in a class's canonical
+//    frame (axes mirrored so that every component is >= 0) rays advance in +a
+//    (slab by slab), +b and +c.  Slab m of a direction cuts every ray into the
+//    same 1-3 segments, so a cell receives at most one segment of each kind:
+//    kind 1 from the ray that enters the slab in its own column, kind 2 from
+//    the ray one column upstream along the axis crossed first, kind 3 from the
+//    diagonal neighbour.
+//  * Lane = ray column.  A warp owns an 8 (b) x 4 (c) tile of columns and, at
+//    each step, one slab of it: every lane computes its cell's segments for
+//    every direction of the unit, holding the intensity of the ray that sits
+//    in its column in a register per direction.  The intensity handed from a
+//    column to its downstream neighbour inside the warp moves by a warp
+//    shuffle; at the warp's edges it goes through shared memory, and at the
+//    CTA's edges through global memory.
+//  * A CTA owns WB x WC warp tiles.  Warp (wb, wc) handles slab t - wb - wc at
+//    step t, so everything it receives from the warps upstream of it was
+//    written one step earlier (double-buffered by step parity): one barrier
+//    per step, and every segment is computed once.
+//  * A unit of work is (grid, class, direction group, CTA tile) over all slabs.
+//    Units are numbered in an order in which every unit comes after the two
+//    units upstream of it (the tile diagonal), and a CTA takes the next number
+//    from a ticket counter when it starts.  A CTA waits only on units with
+//    smaller tickets, which are running or done, so the waits always end.
+//    The downstream CTA polls per-warp-row progress flags (release / acquire at
+//    GPU scope) before it copies an upstream slab's edge intensities; every
+//    wait is bounded in time, and a wait that runs out sets an error word,
+//    after which every CTA leaves its loop at the next step.
+//  * Each unit writes the J partial of its (class, direction group) once per
+//    cell; reduce_kernel sums the partials in fixed order with Kahan.  Within a
+//    unit a cell's direction sum is Kahan-compensated per group of KG
+//    directions.  Results are deterministic.
+//  * Arithmetic per (warp, slab), chosen by ballot over the warp's 32 cells:
+//    every kappa below KAP_THIN (series only), every kappa at or above
+//    KAP_THICK (hardware exponential only), else both with a per-segment
+//    select (series below x = 1/4).  The series path deposits ds phi(x)
+//    directly, so kappa = 0 needs no special case; the exponential path
+//    deposits 1 - e^-x and the cell's sum is scaled by 1/kappa once.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace art {
+
+// A (grid, class) of the wavefront: canonical frame and natural strides.
+struct WaveClass {
+    int a, sa, sb, sc;
+    int Na, Nb, Nc;
+    int pad;
+    long long cell_off;       // first cell of the grid in the concatenated field arrays
+    long long stride_a, stride_b, stride_c;   // natural-layout strides of axes a, b, c
+};
+
+// A unit of the wavefront: one CTA tile of one (grid, class, direction group).
+struct WaveUnit {
+    int cls;                  // WaveClass index
+    int d0, nd;               // first entry in the direction table, count (<= DMAX)
+    int tb, tc;               // tile origin in canonical columns
+    int up_b, up_c;           // unit index of the upstream tiles along b and c; -1 at the box edge
+    int pad;
+    long long jpart;          // first element of the J partial this unit writes
+    long long eb, ec;         // first float of its B-face and C-face output buffers
+};
+
+struct WaveArgs {
+    const float2 *field0, *field1, *field2;   // (kappa, S or eps), sweep-axis layouts, one bin
+    const float4 *segs;       // per (direction, slab): +-ds1, +-ds2, +-ds3, |n_a| (sign bits: code)
+    const long long *seg_off; // per direction: first entry of its slab table
+    const WaveUnit *units;    // in ticket order
+    const WaveClass *classes;
+    float *jpart;
+    float *edge;              // B-face [Na][WC][DMAX][4] and C-face [Na][WB][DMAX][8] per unit
+    int *flags;               // per unit: WC B-face then WB C-face progress counters (slabs published)
+    int *ticket;              // next unit to take (0 before the launch)
+    int *err;                 // bit 0: a wait ran out; bit 1: check failure (checked builds)
+    int n_units;
+    int field_form;           // 0: S, 1: eps
+    float i_bc;               // intensity of every ray where it enters the box
+    int stall_unit;           // test hook: this unit never publishes its progress (-1: none)
+    long long wait_ns;        // bound of every wait
+    long long edge_floats;    // size of the edge buffer (checked builds)
+    long long jpart_floats;   // size of the partials (checked builds)
+};
+
+// Thresholds of the per-warp arithmetic choice.  Series of phi(x) =
+// (1 - e^-x)/x: to x^4 in the thin path (x <= sqrt(3) KAP_THIN = 0.173,
+// truncation < 2.2e-7 relative), to x^5 in the mixed path below x = 1/4
+// (< 6e-8).  Exponential path: 1 - ex2.approx(-x log2 e), whose absolute error
+// (~2^-22) is below 2e-6 of a cell's deposit when kappa >= KAP_THICK.
+constexpr float KAP_THIN = 0.1f;
+constexpr float KAP_THICK = 0.5f;
+constexpr float X_SERIES = 0.25f;
+constexpr int MODE_THIN = 0, MODE_MIXED = 1, MODE_THICK = 2;
+
+__device__ __forceinline__ float wv_ex2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float wv_rcp(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ long long wv_now()
+{
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int wv_ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int wv_ld_relaxed(const int *p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void wv_st_release(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned wv_smem(const void *p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+// Asynchronous global -> shared copies (L2 only for 16 bytes), completed by
+// wv_cp_wait before the step's barrier.
+__device__ __forceinline__ void wv_cp16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(wv_smem(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void wv_cp8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(wv_smem(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void wv_cp_wait()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Poll a progress flag until it reaches `target` or the wait runs out (or
+// another CTA reported an error).  Returns 1 when the flag is reached.
+__device__ __forceinline__ int wv_wait(const int *flag, int target, const WaveArgs &p)
+{
+    if (wv_ld_acquire(flag) >= target) return 1;
+    const long long t0 = wv_now();
+    for (;;) {
+        __nanosleep(64);
+        if (wv_ld_acquire(flag) >= target) return 1;
+        if (wv_ld_relaxed(p.err) != 0 || wv_now() - t0 > p.wait_ns) return 0;
+    }
+}
+
+// Checked builds (ART_WAVE_CHECK) test every global index against its buffer
+// before the access, record a failure in bit 1 of the error word and skip the
+// access; plain builds compile the test away.
+__device__ __forceinline__ bool wv_ok(bool cond, int *err)
+{
+#ifdef ART_WAVE_CHECK
+    if (!cond) atomicOr(err, 2);
+    return cond;
+#else
+    (void)err;
+    return true;
+#endif
+}
+
+// Cell values of one lane for the current slab.
+struct WvCell {
+    float kap;   // kappa per cell width (0 outside the box)
+    float E;     // kappa S (S inputs) or eps: emission per unit length
+    float S;     // source function (exponential path only; kappa > 0 there)
+    float k2;    // -kappa log2 e
+    float rk;    // 1/kappa (0 where kappa = 0)
+};
+
+// One segment of length ds with incoming intensity I: accumulates the deposit
+// into A and returns the outgoing intensity.  Thin / mixed deposits are
+// ds phi(x); the thick path deposits 1 - e^-x (scaled by 1/kappa per cell).
+template <int MODE, bool FIRST>
+__device__ __forceinline__ float wv_seg(const WvCell &c, float I, float ds, float &A)
+{
+    if (MODE == MODE_THICK) {
+        const float h = 1.0f - wv_ex2(c.k2 * ds);
+        A = FIRST ? I * h : fmaf(I, h, A);
+        return fmaf(c.S - I, h, I);
+    }
+    const float x = c.kap * ds;
+    float g;
+    if (MODE == MODE_THIN) {
+        float q = fmaf(x, 1.0f / 120.0f, -1.0f / 24.0f);
+        q = fmaf(x, q, 1.0f / 6.0f);
+        q = fmaf(x, q, -0.5f);
+        q = fmaf(x, q, 1.0f);
+        g = ds * q;
+    } else {
+        float q = fmaf(x, -1.0f / 720.0f, 1.0f / 120.0f);
+        q = fmaf(x, q, -1.0f / 24.0f);
+        q = fmaf(x, q, 1.0f / 6.0f);
+        q = fmaf(x, q, -0.5f);
+        q = fmaf(x, q, 1.0f);
+        const float gs = ds * q;
+        const float gm = (1.0f - wv_ex2(c.k2 * ds)) * c.rk;
+        g = x < X_SERIES ? gs : gm;
+    }
+    A = FIRST ? I * g : fmaf(I, g, A);
+    // I_out = I + (S - I)(1 - e^-x) = I + (eps - kappa I) ds phi(x)
+    return fmaf(fmaf(-c.kap, I, c.E), g, I);
+}
+
+__device__ __forceinline__ void wv_sts(unsigned a, float v) { asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory"); }
+__device__ __forceinline__ float wv_lds(unsigned a)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+    return v;
+}
+
+// Per-lane exchange state of one step: shared-window byte addresses of this
+// lane's slots for direction 0 (direction d is 16 d bytes further along B,
+// 32 d along C).
+struct WvXch {
+    unsigned bo, bi;   // B-face output / input slot
+    unsigned co, ci;   // C-face output / input slot
+    bool b0, b7, c0, c3;
+};
+
+// Hand the intensity v (leaving this lane's column across a b-plane) to the
+// downstream neighbour; return the intensity arriving from upstream.
+__device__ __forceinline__ float wv_xb(const WvXch &x, float v, int d)
+{
+    const float n = __shfl_up_sync(0xffffffffu, v, 1);
+    if (x.b7) wv_sts(x.bo + 16 * d, v);
+    const float in = wv_lds(x.bi + 16 * d);
+    return x.b0 ? in : n;
+}
+
+__device__ __forceinline__ float wv_xc(const WvXch &x, float v, int d)
+{
+    const float n = __shfl_up_sync(0xffffffffu, v, 8);
+    if (x.c3) wv_sts(x.co + 32 * d, v);
+    const float in = wv_lds(x.ci + 32 * d);
+    return x.c0 ? in : n;
+}
+
+// All directions of the unit for one slab: ray states R are updated in place,
+// the cell's direction sum returned in (js, jc) (Kahan).
+template <int MODE, int DMAX, int KG>
+__device__ __forceinline__ void wv_dirs(const WvCell &c, float (&R)[DMAX], const float4 *__restrict__ tab, int nd,
+                                        const WvXch &x, float &js, float &jc)
+{
+    js = 0.0f;
+    jc = 0.0f;
+#pragma unroll
+    for (int d0 = 0; d0 < DMAX; d0 += KG) {
+        if (d0 >= nd) break;
+        float acc = 0.0f;
+#pragma unroll
+        for (int q = 0; q < KG; ++q) {
+            const int d = d0 + q;
+            if (d < nd) {
+                const float4 e = tab[d];
+                const unsigned c1 = __float_as_uint(e.x) >> 31;   // first hand-off along c
+                const unsigned c2 = __float_as_uint(e.y) >> 31;   // two or more segments
+                const unsigned c3 = __float_as_uint(e.z) >> 31;   // three segments
+                float A;
+                float o = wv_seg<MODE, true>(c, R[d], fabsf(e.x), A);
+                if (c2) {
+                    if (c1) {
+                        const float v = wv_xc(x, o, d);
+                        o = wv_seg<MODE, false>(c, v, fabsf(e.y), A);
+                        if (c3) {
+                            const float w = wv_xb(x, o, d);
+                            o = wv_seg<MODE, false>(c, w, fabsf(e.z), A);
+                        }
+                    } else {
+                        const float v = wv_xb(x, o, d);
+                        o = wv_seg<MODE, false>(c, v, fabsf(e.y), A);
+                        if (c3) {
+                            const float w = wv_xc(x, o, d);
+                            o = wv_seg<MODE, false>(c, w, fabsf(e.z), A);
+                        }
+                    }
+                }
+                R[d] = o;
+                acc = fmaf(A, e.w, acc);
+            }
+        }
+        const float y = acc - jc;
+        const float t = js + y;
+        jc = (t - js) - y;
+        js = t;
+    }
+}
+
+template <int WB, int WC, int DMAX> struct WaveShape {
+    static constexpr int NT = 32 * WB * WC;
+    static constexpr int TB = 8 * WB, TC = 4 * WC;
+    static constexpr int RT = (WB + WC <= 4) ? 4 : ((WB + WC <= 8) ? 8 : 16);   // table ring (slabs)
+    static constexpr int XB_PAR = (WB + 1) * WC * DMAX * 4;   // floats per parity
+    static constexpr int XC_PAR = (WC + 1) * WB * DMAX * 8;
+    static constexpr size_t off_xb = size_t(RT) * DMAX * 16;
+    static constexpr size_t off_xc = off_xb + size_t(2) * XB_PAR * 4;
+    static constexpr size_t off_fs = off_xc + size_t(2) * XC_PAR * 4;
+    static constexpr size_t bytes = off_fs + size_t(2) * NT * 8;
+    static constexpr long long edge_b(int Na) { return (long long)Na * WC * DMAX * 4; }
+    static constexpr long long edge_c(int Na) { return (long long)Na * WB * DMAX * 8; }
+};
+
+template <int WB, int WC, int DMAX, int MINB, int KG>
+__global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs p)
+{
+    using Sh = WaveShape<WB, WC, DMAX>;
+    constexpr int NT = Sh::NT, RT = Sh::RT;
+    extern __shared__ __align__(16) unsigned char wsm[];
+    float4 *tab = reinterpret_cast<float4 *>(wsm);                  // [RT][DMAX]
+    float *XB = reinterpret_cast<float *>(wsm + Sh::off_xb);        // [2][WB+1][WC][DMAX][4]
+    float *XC = reinterpret_cast<float *>(wsm + Sh::off_xc);        // [2][WC+1][WB][DMAX][8]
+    float2 *FS = reinterpret_cast<float2 *>(wsm + Sh::off_fs);      // [2][NT]
+    __shared__ int s_unit;
+    __shared__ long long s_seg[DMAX];   // first table entry of each direction of the unit
+    __shared__ long long s_up[2];       // output buffers of the upstream units (B, C)
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wb = warp % WB, wc = warp / WB;
+    const int bl = lane & 7, cl = lane >> 3;
+    if (tid == 0) s_unit = atomicAdd(p.ticket, 1);
+    __syncthreads();
+    const int u = s_unit;
+    if (u >= p.n_units) return;
+    const WaveUnit U = p.units[u];
+    const WaveClass C = p.classes[U.cls];
+    const int Na = C.Na, nd = U.nd;
+    const int j = U.tb + 8 * wb + bl, k = U.tc + 4 * wc + cl;   // canonical column
+    const bool in_box = j < C.Nb && k < C.Nc;
+    const int pb = C.sb > 0 ? j : C.Nb - 1 - j, pc = C.sc > 0 ? k : C.Nc - 1 - k;
+    // the lane's column in the axis-a field layout [a][c][b], and its cell of
+    // slab m in the natural layout of the J partial: Jl[m * jstep]
+    const float2 *Fl = (C.a == 0 ? p.field0 : (C.a == 1 ? p.field1 : p.field2)) + C.cell_off +
+                       (in_box ? (long long)pc * C.Nb + pb : 0);
+    const int fslab = C.Nb * C.Nc;
+    const long long jbase = (C.sa > 0 ? 0 : (long long)(Na - 1) * C.stride_a) + (long long)pb * C.stride_b +
+                            (long long)pc * C.stride_c;
+    const int jstep = (int)(C.sa > 0 ? C.stride_a : -C.stride_a);
+    float *Jl = p.jpart + U.jpart + (in_box ? jbase : 0);
+    const bool jl_ok = wv_ok(!in_box || (U.jpart + jbase >= 0 && U.jpart + jbase < p.jpart_floats &&
+                                         U.jpart + jbase + (long long)(Na - 1) * jstep >= 0 &&
+                                         U.jpart + jbase + (long long)(Na - 1) * jstep < p.jpart_floats),
+                             p.err);
+    const bool stalled = u == p.stall_unit;
+
+    if (tid < nd) s_seg[tid] = p.seg_off[U.d0 + tid];
+    if (tid == 0) s_up[0] = U.up_b >= 0 ? p.units[U.up_b].eb : -1;
+    if (tid == 1) s_up[1] = U.up_c >= 0 ? p.units[U.up_c].ec : -1;
+
+    // box-edge inputs carry the boundary intensity in both parities
+    if (U.up_b < 0)
+        for (int e = tid; e < WC * DMAX * 4; e += NT) {
+            XB[e] = p.i_bc;
+            XB[Sh::XB_PAR + e] = p.i_bc;
+        }
+    if (U.up_c < 0)
+        for (int e = tid; e < WB * DMAX * 8; e += NT) {
+            XC[e] = p.i_bc;
+            XC[Sh::XC_PAR + e] = p.i_bc;
+        }
+
+    float R[DMAX];
+#pragma unroll
+    for (int d = 0; d < DMAX; ++d) R[d] = p.i_bc;
+
+    // Stage what step t + 1 reads: the table of slab t + 1, this lane's field
+    // of its next slab, and (warps on the CTA's upstream edges) the upstream
+    // CTA's edge intensities, into the parity that step t + 1 reads (t & 1).
+    // Returns 0 if a wait ran out.
+    auto stage = [&](int t) -> int {
+        const int s1 = t + 1, rp = t & 1;
+        if (tid < nd && s1 < Na) wv_cp16(tab + (s1 & (RT - 1)) * DMAX + tid, p.segs + s_seg[tid] + s1);
+        const int mn = s1 - wb - wc;
+        if (in_box && mn >= 0 && mn < Na) {
+            const int pa = C.sa > 0 ? mn : Na - 1 - mn;
+            wv_cp8(FS + (s1 & 1) * NT + tid, Fl + (long long)pa * fslab);   // read at step s1 as FS[s1 & 1]
+        }
+        int ok = 1;
+        if (wb == 0 && U.up_b >= 0) {
+            const int s = s1 - wc;
+            if (s >= 0 && s < Na) {
+                const int *fl = p.flags + (long long)U.up_b * (WB + WC) + wc;
+                if (lane == 0) ok = wv_wait(fl, s + 1, p);
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (ok) {
+                    (void)wv_ld_acquire(fl);
+                    const long long eb_up = s_up[0];
+                    for (int dd = lane; dd < nd; dd += 32) {
+                        const long long o = eb_up + (((long long)s * WC + wc) * DMAX + dd) * 4;
+                        if (wv_ok(eb_up >= 0 && o + 4 <= p.edge_floats, p.err))
+                            wv_cp16(XB + rp * Sh::XB_PAR + (wc * DMAX + dd) * 4, p.edge + o);
+                    }
+                }
+            }
+        }
+        if (wc == 0 && U.up_c >= 0) {
+            const int s = s1 - wb;
+            if (s >= 0 && s < Na) {
+                const int *fl = p.flags + (long long)U.up_c * (WB + WC) + WC + wb;
+                int okc = 1;
+                if (lane == 0) okc = wv_wait(fl, s + 1, p);
+                okc = __shfl_sync(0xffffffffu, okc, 0);
+                if (okc) {
+                    (void)wv_ld_acquire(fl);
+                    const long long ec_up = s_up[1];
+                    for (int dd = lane; dd < nd; dd += 32) {
+                        const long long o = ec_up + (((long long)s * WB + wb) * DMAX + dd) * 8;
+                        if (wv_ok(ec_up >= 0 && o + 8 <= p.edge_floats, p.err)) {
+                            float *dst = XC + rp * Sh::XC_PAR + (wb * DMAX + dd) * 8;
+                            wv_cp16(dst, p.edge + o);
+                            wv_cp16(dst + 4, p.edge + o + 4);
+                        }
+                    }
+                }
+                ok &= okc;
+            }
+        }
+        return ok;
+    };
+
+    __syncthreads();   // s_seg
+    // A wait that ran out ends the unit: the decision is taken by the barrier
+    // itself (__syncthreads_or), so every thread leaves the loop at the same step.
+    int bad = stage(-1) ? 0 : 1;
+    wv_cp_wait();
+    int abort_ = __syncthreads_or(bad);
+
+    const int T = Na + WB + WC - 2;
+    const bool b_out = wb == WB - 1, c_out = wc == WC - 1;
+    const int fl_b = u * (WB + WC) + wc, fl_c = u * (WB + WC) + WC + wb;
+    const unsigned xb0 = wv_smem(XB), xc0 = wv_smem(XC);
+    for (int t = 0; t < T && !abort_; ++t) {
+        const int m = t - wb - wc;
+        // progress of the slab written to global memory in the previous step
+        if (lane == 0 && !stalled && m - 1 >= 0 && m - 1 < Na) {
+            if (b_out) wv_st_release(p.flags + fl_b, m);
+            if (c_out) wv_st_release(p.flags + fl_c, m);
+        }
+        if (!stage(t)) bad = 1;
+        if (m >= 0 && m < Na) {
+            const int par = t & 1;
+            const float2 f = FS[par * NT + tid];
+            WvCell c;
+            c.kap = in_box ? f.x : 0.0f;
+            const float src = in_box ? f.y : 0.0f;
+            c.rk = c.kap > 0.0f ? wv_rcp(c.kap) : 0.0f;
+            c.E = p.field_form ? src : c.kap * src;
+            c.S = p.field_form ? src * c.rk : src;
+            c.k2 = -1.4426950408889634f * c.kap;
+            WvXch x;
+            x.bo = xb0 + 4 * (par * Sh::XB_PAR + ((wb + 1) * WC + wc) * DMAX * 4 + cl);
+            x.bi = xb0 + 4 * ((par ^ 1) * Sh::XB_PAR + (wb * WC + wc) * DMAX * 4 + cl);
+            x.co = xc0 + 4 * (par * Sh::XC_PAR + ((wc + 1) * WB + wb) * DMAX * 8 + bl);
+            x.ci = xc0 + 4 * ((par ^ 1) * Sh::XC_PAR + (wc * WB + wb) * DMAX * 8 + bl);
+            x.b0 = bl == 0;
+            x.b7 = bl == 7;
+            x.c0 = cl == 0;
+            x.c3 = cl == 3;
+            const float4 *tb = tab + (m & (RT - 1)) * DMAX;
+            const unsigned thin = __ballot_sync(0xffffffffu, c.kap < KAP_THIN);
+            const unsigned thick = __ballot_sync(0xffffffffu, c.kap >= KAP_THICK);
+            float js, jc;
+            if (thin == 0xffffffffu)
+                wv_dirs<MODE_THIN, DMAX, KG>(c, R, tb, nd, x, js, jc);
+            else if (thick == 0xffffffffu)
+                wv_dirs<MODE_THICK, DMAX, KG>(c, R, tb, nd, x, js, jc);
+            else
+                wv_dirs<MODE_MIXED, DMAX, KG>(c, R, tb, nd, x, js, jc);
+            if (in_box && jl_ok) {
+                const float scale = thick == 0xffffffffu ? c.rk : 1.0f;
+                Jl[m * jstep] = (js - jc) * scale;
+            }
+            // edge intensities of this slab to the downstream CTAs
+            if ((b_out && U.eb >= 0) || (c_out && U.ec >= 0)) {
+                __syncwarp();
+                if (b_out && U.eb >= 0)
+                    for (int dd = lane; dd < nd; dd += 32) {
+                        const float4 v = *reinterpret_cast<const float4 *>(
+                            XB + par * Sh::XB_PAR + ((wb + 1) * WC + wc) * DMAX * 4 + dd * 4);
+                        const long long o = U.eb + (((long long)m * WC + wc) * DMAX + dd) * 4;
+                        if (wv_ok(o + 4 <= p.edge_floats, p.err)) *reinterpret_cast<float4 *>(p.edge + o) = v;
+                    }
+                if (c_out && U.ec >= 0)
+                    for (int dd = lane; dd < nd; dd += 32) {
+                        const float *srcs = XC + par * Sh::XC_PAR + ((wc + 1) * WB + wb) * DMAX * 8 + dd * 8;
+                        const long long o = U.ec + (((long long)m * WB + wb) * DMAX + dd) * 8;
+                        if (wv_ok(o + 8 <= p.edge_floats, p.err)) {
+                            *reinterpret_cast<float4 *>(p.edge + o) = *reinterpret_cast<const float4 *>(srcs);
+                            *reinterpret_cast<float4 *>(p.edge + o + 4) = *reinterpret_cast<const float4 *>(srcs + 4);
+                        }
+                    }
+            }
+        }
+        wv_cp_wait();
+        abort_ = __syncthreads_or(bad);
+    }
+    if (abort_) {
+        if (tid == 0) atomicOr(p.err, 1);
+        return;
+    }
+    if (lane == 0 && !stalled) {
+        if (b_out) wv_st_release(p.flags + fl_b, Na);
+        if (c_out) wv_st_release(p.flags + fl_c, Na);
+    }
+}
+
+}  // namespace art

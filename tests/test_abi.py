@@ -95,6 +95,8 @@ def test_null_context_calls_fail_cleanly(lib):
         art.ART_E_INVALID
     assert lib.art_thermal_default(None) == art.ART_E_INVALID
     assert lib.art_sweep_stream(None, 1, None, None, None, None, None, None) == art.ART_E_INVALID
+    assert lib.art_sweep_check(None, None) == art.ART_E_INVALID
+    assert lib.art_sweep_set_wait(None, 1.0, -1) == art.ART_E_INVALID
     th = art.ArtThermal()
     assert lib.art_thermal_default(ctypes.byref(th)) == art.ART_OK
     assert (th.on_the_spot, th.cool_mask, list(th.e_bin), th.e_diff, th.z, th.kB, th.T_min, th.T_max) == \

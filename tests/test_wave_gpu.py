@@ -1,0 +1,211 @@
+"""GPU parity of the wavefront sweep (the default FP32 sweep with the paper's
+cell average) against the FP64 oracle, through the C ABI.
+
+Bar: 1e-5 relative per cell on J and J^in (the FP32 target), as for the
+slab-block kernels.  Every compiled wavefront shape (art_options.variant 16-19:
+8 x 4-column warp tiles, 2 x 4 or 4 x 4 warps per CTA, 40 / 12 / 4 direction
+slots) runs on ragged grids that span several CTA tiles along both transverse
+axes, with classes split into direction groups where they exceed the slots.
+The bounded waits are checked by stalling one tile on purpose: the tiles
+downstream of it give up after the bound and the sweep reports ART_E_TIMEOUT,
+after which the context sweeps correctly again.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1410_0763_gb300 import art, build
+from paper_1410_0763_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+WAVE0 = 16   # art_options.variant of the first wavefront shape
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    art.load()
+
+
+def f32(x):
+    return np.asarray(x, dtype=np.float32).astype(np.float64)
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)))
+
+
+def run(kap, src, nside, form=0, nbins=1, i_bc=None, check=True, **kw):
+    shape = kap.shape[-3:]
+    k = torch.as_tensor(np.ascontiguousarray(kap), dtype=torch.float32, device="cuda")
+    s = torch.as_tensor(np.ascontiguousarray(src), dtype=torch.float32, device="cuda")
+    sw = art.ArtSweep(shape, nside, nbins, field_form=form, **kw)
+    if i_bc is not None:
+        sw.set_boundary_intensity(i_bc)
+    J = torch.empty_like(k)
+    Jin = torch.empty_like(k)
+    sw.set_fields(k, s)
+    sw.sweep(J, Jin)
+    torch.cuda.synchronize()
+    st = sw.check()
+    stats = sw.stats
+    sw.close()
+    if check:
+        assert st == art.ART_OK
+    return J.cpu().numpy().astype(np.float64), Jin.cpu().numpy().astype(np.float64), stats
+
+
+def lognormal(shape, seed, scale=0.5):
+    rng = np.random.default_rng(seed)
+    return f32(scale * np.exp(rng.standard_normal(shape))), f32(rng.random(shape))
+
+
+def test_default_fp32_context_uses_the_wavefront_sweep():
+    kap, S = lognormal((12, 14, 16), 1)
+    _, _, st = run(kap, S, 2)
+    assert st.variant >= WAVE0 and st.launches == 2 and st.ctas_per_launch > 0
+
+
+@pytest.mark.parametrize("variant,nside", [(WAVE0, 8), (WAVE0 + 1, 4), (WAVE0 + 1, 3), (WAVE0 + 2, 2),
+                                           (WAVE0 + 2, 1), (WAVE0 + 3, 8), (WAVE0 + 2, 4), (WAVE0 + 1, 8)])
+def test_ragged_grids_every_shape(orc, variant, nside):
+    """Ragged against every tile (16 x 16 and 32 x 16 columns); shapes with fewer slots than a
+    class's directions split it into groups."""
+    shape = (21, 26, 37) if nside < 8 else (19, 23, 34)
+    kap, S = lognormal(shape, 7 + nside)
+    jin_o, j_o, _ = orc.sweep(kap, S, nside)
+    J, Jin, st = run(kap, S, nside, variant=variant)
+    assert st.variant == variant
+    assert rel(Jin, jin_o) < 1e-5
+    assert rel(J, j_o) < 1e-5
+
+
+@pytest.mark.parametrize("scale", [0.02, 0.3, 3.0])
+def test_thin_mixed_and_thick_media(orc, scale):
+    """Media whose warps take the series path, both paths, or the exponential path."""
+    kap, S = lognormal((20, 24, 28), 11, scale)
+    jin_o, j_o, _ = orc.sweep(kap, S, 4)
+    J, Jin, _ = run(kap, S, 4)
+    assert rel(Jin, jin_o) < 1e-5
+    assert rel(J, j_o) < 1e-5
+
+
+def test_grf_64_nside4(orc):
+    c = wl.grf(64, 4)
+    kap, S = f32(c.kappa), f32(c.src)
+    jin_o, j_o, _ = orc.sweep(kap, S, 4)
+    J, Jin, _ = run(kap, S, 4)
+    assert rel(Jin, jin_o) < 1e-5
+    assert rel(J, j_o) < 1e-5
+
+
+def test_emissivity_form_with_transparent_cells(orc):
+    rng = np.random.default_rng(9)
+    shape = (18, 22, 17)
+    kap = 0.3 * np.exp(rng.standard_normal(shape))
+    kap[rng.random(shape) < 0.3] = 0.0
+    kap = f32(kap)
+    eps = f32(rng.random(shape))
+    jin_o, j_o, _ = orc.sweep(kap, eps, 3, field_form=1)
+    J, Jin, _ = run(kap, eps, 3, form=1)
+    assert rel(Jin, jin_o) < 1e-5
+    assert rel(J, j_o) < 1e-5
+
+
+def test_boundary_intensity(orc):
+    kap, S = lognormal((17, 20, 23), 12)
+    jin_o, j_o, _ = orc.sweep(kap, S, 2, i_bc=0.8)
+    J, Jin, _ = run(kap, S, 2, i_bc=[0.8])
+    assert rel(Jin, jin_o) < 1e-5
+    assert rel(J, j_o) < 1e-5
+
+
+def test_multiple_bins(orc):
+    shape = (12, 14, 16)
+    rng = np.random.default_rng(5)
+    kap = f32(0.4 * np.exp(rng.standard_normal((3,) + shape)))
+    S = f32(rng.random((3,) + shape))
+    J, Jin, _ = run(kap, S, 3, nbins=3)
+    for b in range(3):
+        jin_o, j_o, _ = orc.sweep(kap[b], S[b], 3)
+        assert rel(Jin[b], jin_o) < 1e-5
+        assert rel(J[b], j_o) < 1e-5
+
+
+def test_direction_shards_add_up(orc):
+    kap, S = lognormal((14, 15, 16), 13)
+    nd = 12 * 3 * 3
+    full = np.zeros(kap.shape)
+    cuts = [0, 31, 70, nd]
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        _, jin, st = run(kap, S, 3, dir_range=(a, b))
+        assert st.variant >= WAVE0
+        full += jin
+    jin_o, _, _ = orc.sweep(kap, S, 3)
+    assert rel(full, jin_o) < 1e-5
+
+
+def test_deterministic_bitwise():
+    kap, S = lognormal((24, 20, 28), 14)
+    a = run(kap, S, 4)[1]
+    b = run(kap, S, 4)[1]
+    assert np.array_equal(a, b)
+
+
+def test_batch_of_uneven_grids_matches_single_contexts(orc):
+    shapes = [(9, 11, 13), (20, 16, 18), (12, 12, 12)]
+    nsides = [2, 4, 3]
+    rng = np.random.default_rng(15)
+    ks = [f32(0.5 * np.exp(rng.standard_normal(s))) for s in shapes]
+    ss = [f32(rng.random(s)) for s in shapes]
+    kap = np.concatenate([k.ravel() for k in ks])
+    src = np.concatenate([s.ravel() for s in ss])
+    sw = art.ArtSweep(shapes, nsides, 1)
+    assert sw.stats.variant >= WAVE0
+    k = torch.as_tensor(kap, dtype=torch.float32, device="cuda")
+    s = torch.as_tensor(src, dtype=torch.float32, device="cuda")
+    Jin = torch.empty_like(k)
+    sw.set_fields(k, s)
+    sw.sweep(None, Jin)
+    assert sw.check() == art.ART_OK
+    sw.close()
+    got = Jin.cpu().numpy().astype(np.float64)
+    off = 0
+    for kk, s_, ns in zip(ks, ss, nsides):
+        n = kk.size
+        jin_o, _, _ = orc.sweep(kk, s_, ns)
+        assert rel(got[off:off + n].reshape(kk.shape), jin_o) < 1e-5
+        single = run(kk, s_, ns)[1]
+        assert np.array_equal(got[off:off + n].reshape(kk.shape), single)
+        off += n
+
+
+def test_graph_replay_matches_plain_launches():
+    kap, S = lognormal((16, 18, 20), 16)
+    a = run(kap, S, 4)[1]
+    b = run(kap, S, 4, graph=True)[1]
+    assert np.array_equal(a, b)
+
+
+def test_a_stalled_tile_times_out_and_the_context_recovers(orc):
+    """A unit that never publishes its progress: the tiles downstream of it wait until the
+    bound (0.2 s), the sweep reports ART_E_TIMEOUT, and the next sweep is correct."""
+    kap, S = lognormal((40, 36, 44), 17)
+    k = torch.as_tensor(kap, dtype=torch.float32, device="cuda")
+    s = torch.as_tensor(S, dtype=torch.float32, device="cuda")
+    sw = art.ArtSweep(kap.shape, 2, 1)
+    sw.set_fields(k, s)
+    Jin = torch.empty_like(k)
+    sw.set_wait(0.2, 0)   # unit 0 starts a tile diagonal: every class has tiles downstream of it
+    sw.sweep(None, Jin)
+    assert sw.check() == art.ART_E_TIMEOUT
+    sw.set_wait(2.0, -1)
+    sw.sweep(None, Jin)
+    assert sw.check() == art.ART_OK
+    sw.close()
+    jin_o, _, _ = orc.sweep(kap, S, 2)
+    assert rel(Jin.cpu().numpy().astype(np.float64), jin_o) < 1e-5
