@@ -46,7 +46,8 @@ def run(kap, src, nside, form=0, nbins=1, i_bc=None, check=True, **kw):
     sw = art.ArtSweep(shape, nside, nbins, field_form=form, **kw)
     if i_bc is not None:
         sw.set_boundary_intensity(i_bc)
-    J = torch.empty_like(k)
+    shard = kw.get("dir_range") is not None
+    J = None if shard else torch.empty_like(k)   # a direction shard has J^in only
     Jin = torch.empty_like(k)
     sw.set_fields(k, s)
     sw.sweep(J, Jin)
@@ -56,7 +57,8 @@ def run(kap, src, nside, form=0, nbins=1, i_bc=None, check=True, **kw):
     sw.close()
     if check:
         assert st == art.ART_OK
-    return J.cpu().numpy().astype(np.float64), Jin.cpu().numpy().astype(np.float64), stats
+    Jh = None if shard else J.cpu().numpy().astype(np.float64)
+    return Jh, Jin.cpu().numpy().astype(np.float64), stats
 
 
 def lognormal(shape, seed, scale=0.5):
