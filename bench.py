@@ -716,7 +716,7 @@ def ablation_measure(torch, dev, reps=3):
         c = wl.grf(n, nside)
         k = torch.as_tensor(c.kappa, dtype=torch.float32, device=dev)
         s = torch.as_tensor(c.src, dtype=torch.float32, device=dev)
-        sw = art.ArtSweep(k.shape, nside, 1, graph=True)
+        sw = art.ArtSweep(k.shape, nside, 1, graph=True, variant=1)   # the slab-block tables it marches
         sw.set_fields(k, s)
         j = torch.empty_like(k)
 

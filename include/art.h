@@ -212,7 +212,10 @@ art_status art_set_band(art_ctx *ctx, const double *G);
  * and output pointer) and replayed on an internal stream ordered with
  * `stream`.  J_in: device [z][y][x] floats, overwritten with J^in.  Single
  * grid, FP32, one bin, ART_FIELDS_S, all directions, vacuum boundary, after
- * art_set_fields.  Errors: ART_E_INVALID, ART_E_STATE, ART_E_CUDA.
+ * art_set_fields, on a context created with a slab-block kernel variant
+ * (art_options.variant 1-15: it marches that kernel's segment tables).
+ * Errors: ART_E_INVALID, ART_E_STATE (no fields, or a wavefront context),
+ * ART_E_CUDA.
  */
 art_status art_ablation_sweep(art_ctx *ctx, int mode, float *J_in, void *stream);
 
@@ -314,6 +317,9 @@ typedef struct {
     double Q;
 } art_source;
 
+/* Starts of art_iterate_ionization. */
+enum { ART_WARM_NONE = 0, ART_WARM_COARSE = 1, ART_WARM_SURROGATE = 2 };
+
 typedef struct {
     int32_t iterations;     /* iterations run */
     int32_t converged;      /* 1 if the residual fell below tol */
@@ -367,12 +373,27 @@ art_status art_point_sources(art_ctx *ctx, const float *kappa, const double *sig
  * array (src[i].Q photons/s, monochromatic at nu0 unless
  * art_set_source_spectrum gave bins); resid_hist: host array of max_iter
  * doubles or NULL; rep: may be NULL.  One host synchronization per iteration
- * (the residual).  Errors: ART_E_INVALID, ART_E_NOT_CONVERGED (y holds the
- * last iterate), ART_E_OOM, ART_E_CUDA.
+ * (the residual).
+ * warm_start (not in the paper, which iterates from its initial state):
+ *   ART_WARM_NONE       the plain iteration from y;
+ *   ART_WARM_COARSE     first solve the same problem on the mesh coarsened by
+ *                       4 (N_side 4; n_H and y block means) to 1e-4 and start
+ *                       from its neutral fraction;
+ *   ART_WARM_SURROGATE  the coarse start, then early iterations take J^in
+ *                       from the context's surrogate network (trained by
+ *                       art_surrogate_train, art_net.h) until the residual
+ *                       falls below 1e-3, judged against full sweeps and
+ *                       abandoned for the coarse start if its error exceeds
+ *                       0.3 (art_iterate_ionization_warm gives every option).
+ * All three stop by the same rule at the same fixed point.  The warm starts
+ * need grid dimensions divisible by 4.  Errors: ART_E_INVALID,
+ * ART_E_STATE (ART_WARM_SURROGATE before art_surrogate_train),
+ * ART_E_NOT_CONVERGED (y holds the last iterate), ART_E_OOM, ART_E_CUDA,
+ * ART_E_TIMEOUT (a bounded wait of the sweep ran out).
  */
 art_status art_iterate_ionization(art_ctx *ctx, const art_chem *chem, const double *nH, const art_source *src,
-                                  int n_src, double tol, int max_iter, double *y, double *resid_hist,
-                                  art_iter_report *rep, void *stream);
+                                  int n_src, double tol, int max_iter, int warm_start, double *y,
+                                  double *resid_hist, art_iter_report *rep, void *stream);
 
 /*
  * Time-dependent mode (App. B-D) for hydrogen at the fixed temperature of

@@ -209,6 +209,52 @@ art_status art_iterate_ionization_warm(art_ctx *ctx, art_net *net, const art_che
                                        const art_warm_options *wopt, double *y, double *resid_hist,
                                        art_warm_report *rep, void *stream);
 
+/* Training samples on a context's grid: X [n_samples][4][V], t and w
+ * [n_samples][V] device floats (w may be NULL: weights 1), V = nx ny nz, as
+ * art_surrogate_collect writes them. */
+typedef struct {
+    int nx, ny, nz;
+    int n_samples;
+    const float *X, *t, *w;
+} art_dataset;
+
+typedef struct {
+    int steps;                /* Adam steps, one sample per step; default 0 = 8 epochs */
+    uint64_t seed;            /* permutation seed of the epochs, default 1 */
+    int reset;                /* 1: start from freshly initialised weights (net options) */
+    art_net_options net;      /* network of the first call or of a reset (defaults as art_net_options_default) */
+    void *stream;             /* cudaStream_t of the training launches, NULL = legacy default */
+} art_train_opts;
+
+typedef struct {
+    int32_t steps;            /* steps run */
+    double first_epoch_loss;  /* mean loss of the first min(n_samples, steps) steps */
+    double last_epoch_loss;   /* mean loss of the last min(n_samples, steps) steps */
+    double seconds;           /* wall time */
+} art_train_report;
+
+/* Defaults of art_train_opts.  Never fails for a non-NULL pointer. */
+art_status art_train_opts_default(art_train_opts *opt);
+
+/*
+ * Train the context's surrogate network (the one ART_WARM_SURROGATE of
+ * art_iterate_ionization uses) on a dataset of its grid: art_net_train's
+ * seeded Adam epochs on a network the context owns, created by the first
+ * call (or by reset) with opt->net.  The paper has no surrogate; this is the
+ * warm start's learned part.  opt may be NULL (defaults), rep may be NULL.
+ * Synchronizes opt->stream once.  Errors: ART_E_INVALID (NULL ctx or data,
+ * a grid other than the context's, n_samples < 1, NULL X or t, steps < 0),
+ * ART_E_OOM, ART_E_CUDA, ART_E_TIMEOUT (a bounded wait of the convolution
+ * kernels ran out).
+ */
+art_status art_surrogate_train(art_ctx *ctx, const art_dataset *data, const art_train_opts *opt,
+                               art_train_report *rep);
+
+/* The context's surrogate network (owned by the context; NULL before
+ * art_surrogate_train), e.g. to read or set its parameters.  Errors:
+ * ART_E_INVALID (NULL ctx or out). */
+art_status art_surrogate_network(art_ctx *ctx, art_net **out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -100,6 +100,24 @@ ART_NET_PARAMS = 59713
 NET_LAYERS = [(4, 32), (32, 32), (32, 32), (32, 1)]   # (c_in, c_out)
 
 
+class ArtDataset(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("n_samples", C.c_int),
+                ("X", C.c_void_p), ("t", C.c_void_p), ("w", C.c_void_p)]
+
+
+class ArtTrainOpts(C.Structure):
+    _fields_ = [("steps", C.c_int), ("seed", C.c_uint64), ("reset", C.c_int), ("net", ArtNetOptions),
+                ("stream", C.c_void_p)]
+
+
+class ArtTrainReport(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("first_epoch_loss", C.c_double), ("last_epoch_loss", C.c_double),
+                ("seconds", C.c_double)]
+
+
+ART_WARM_NONE, ART_WARM_COARSE, ART_WARM_SURROGATE = 0, 1, 2
+
+
 class ArtError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{_STATUS.get(status, status)}: {msg}")
@@ -173,7 +191,15 @@ def load() -> C.CDLL:
         lib.art_point_sources.argtypes = [P, P, C.POINTER(C.c_double), C.POINTER(ArtSource), C.POINTER(C.c_double),
                                           C.c_int, P, P]
         lib.art_iterate_ionization.argtypes = [P, C.POINTER(ArtChem), P, C.POINTER(ArtSource), C.c_int, C.c_double,
-                                               C.c_int, P, C.POINTER(C.c_double), C.POINTER(ArtIterReport), P]
+                                               C.c_int, C.c_int, P, C.POINTER(C.c_double), C.POINTER(ArtIterReport),
+                                               P]
+        lib.art_train_opts_default.argtypes = [C.POINTER(ArtTrainOpts)]
+        lib.art_train_opts_default.restype = C.c_int
+        lib.art_surrogate_train.argtypes = [P, C.POINTER(ArtDataset), C.POINTER(ArtTrainOpts),
+                                            C.POINTER(ArtTrainReport)]
+        lib.art_surrogate_train.restype = C.c_int
+        lib.art_surrogate_network.argtypes = [P, C.POINTER(P)]
+        lib.art_surrogate_network.restype = C.c_int
         lib.art_sweep_noalloc.argtypes = [C.POINTER(ArtGrid), C.c_int, P, P, P, P, C.c_char_p, C.c_size_t]
         lib.art_profile_enable.argtypes = [P, C.c_int]
         lib.art_profile_read.argtypes = [P, C.POINTER(ArtProfile), C.c_int]
@@ -567,8 +593,9 @@ class ArtSweep:
         """Over-relaxation factor of the balance update in `iterate` / `iterate_warm` (1: plain)."""
         _check(self._ctx, load().art_set_relaxation(self._ctx, float(omega)))
 
-    def iterate(self, nH, chem: dict, sources, y, tol=1e-6, max_iter=200, stream=None):
+    def iterate(self, nH, chem: dict, sources, y, tol=1e-6, max_iter=200, stream=None, warm_start=ART_WARM_NONE):
         """RT / balance iteration (App. D); nH, y: device FP64 [z][y][x]; y updated in place.
+        warm_start: ART_WARM_NONE, ART_WARM_COARSE or ART_WARM_SURROGATE (after surrogate_train).
         Returns (report, residual history); raises ArtError unless converged."""
         npp, nd_, _n = _ptr(nH, np.float64, self.ncell)
         yp, yd, _y = _ptr(y, np.float64, self.ncell)
@@ -580,12 +607,31 @@ class ArtSweep:
         hist = (C.c_double * max_iter)()
         rep = ArtIterReport()
         st = load().art_iterate_ionization(self._ctx, C.byref(ch), C.c_void_p(npp), src, len(sources), float(tol),
-                                           int(max_iter), C.c_void_p(yp), hist, C.byref(rep),
+                                           int(max_iter), int(warm_start), C.c_void_p(yp), hist, C.byref(rep),
                                            C.c_void_p(_stream(stream)))
         n = max(0, min(rep.iterations, max_iter))
         if st != ART_OK:
             raise ArtError(st, art_last_error(self._ctx))
         return rep, np.array(hist[:n])
+
+    def surrogate_train(self, X, t, w, n_samples, steps=0, seed=1, reset=False, stream=None):
+        """art_surrogate_train: train the context's surrogate network on samples of its grid (device
+        arrays as surrogate_collect fills them; w may be None).  Returns the ArtTrainReport."""
+        nz, ny, nx = self.shape
+        V = nx * ny * nz
+        xp, xd, _x = _ptr(X, np.float32, 4 * V * n_samples)
+        tp, td, _t = _ptr(t, np.float32, V * n_samples)
+        wp, wd, _w = _ptr(w, np.float32, V * n_samples)
+        if not (xd and td and (w is None or wd)):
+            raise TypeError("surrogate_train takes device buffers")
+        data = ArtDataset(nx, ny, nz, int(n_samples), C.c_void_p(xp), C.c_void_p(tp), C.c_void_p(wp or None))
+        o = ArtTrainOpts()
+        load().art_train_opts_default(C.byref(o))
+        o.steps, o.seed, o.reset = int(steps), int(seed), 1 if reset else 0
+        o.stream = C.c_void_p(_stream(stream))
+        rep = ArtTrainReport()
+        _check(self._ctx, load().art_surrogate_train(self._ctx, C.byref(data), C.byref(o), C.byref(rep)))
+        return rep
 
     def set_source_spectrum(self, sigma=None, frac=None):
         """Point-source bins of the iteration: cross sections sigma[b] (cm^2), photon fractions frac[b];

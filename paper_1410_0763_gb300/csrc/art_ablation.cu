@@ -227,6 +227,10 @@ extern "C" art_status art_ablation_sweep(art_ctx *ctx, int mode, float *J_in, vo
                         "art_ablation_sweep: single-grid FP32 contexts, one bin, ART_FIELDS_S, the paper's averaging, "
                         "all directions");
     if (!ctx->have_fields) return art_fail(ctx, ART_E_STATE, "art_ablation_sweep: call art_set_fields first");
+    if (ctx->wave.on)
+        return art_fail(ctx, ART_E_STATE,
+                        "art_ablation_sweep: needs a slab-block context (art_options.variant 1-15), whose segment "
+                        "tables it marches; this context uses the wavefront sweep");
     for (double v : ctx->i_bc)
         if (v != 0.0) return art_fail(ctx, ART_E_INVALID, "art_ablation_sweep: vacuum boundary only");
     AblationPlan *P = static_cast<AblationPlan *>(ctx->ablation);

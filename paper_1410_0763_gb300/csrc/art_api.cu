@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "art.h"
+#include "art_net.h"
 #include "art_geometry.hpp"
 #include "art_kernels.cuh"
 
@@ -422,7 +423,7 @@ art_status setup_wave(art_ctx *ctx, int w)
     if (s != ART_OK) return s;
     ctx->variant = kNumVariants + w;
     ctx->TB = 8 * ctx->wave.wb;
-    ctx->TC = 4 * ctx->wave.wc;
+    ctx->TC = 8 * ctx->wave.wc;
     ctx->BLK = 0;
     ctx->KP = 0;
     ctx->split = 0;
@@ -916,6 +917,7 @@ art_status art_destroy(art_ctx *ctx)
         if (R.h_flags) cudaFreeHost(R.h_flags);
     }
     if (ctx->coarse) art_destroy(ctx->coarse);
+    if (ctx->net) art_net_destroy(ctx->net);
     delete ctx;
     return ART_OK;
 }

@@ -8,6 +8,8 @@
 #include "art.h"
 #include "art_kernels.cuh"
 
+struct art_net;
+
 // Device buffers of the RT / ionization-balance iteration (allocated on the
 // first art_iterate_ionization call).
 struct art_iter_bufs {
@@ -122,6 +124,7 @@ struct art_ctx {
     void *ablation = nullptr;   // thread-per-ray comparison sweep (tables, graphs)
     art_sur_bufs sur;
     art_wave_state wave;
+    art_net *net = nullptr;     // the context's surrogate (art_surrogate_train)
 };
 
 

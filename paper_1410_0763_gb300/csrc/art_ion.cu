@@ -1398,11 +1398,28 @@ art_status evolve_thermal_impl(art_ctx *ctx, const art_chem *ch, const art_therm
 extern "C" {
 
 art_status art_iterate_ionization(art_ctx *ctx, const art_chem *ch, const double *nH, const art_source *src,
-                                  int n_src, double tol, int max_iter, double *y, double *resid_hist,
-                                  art_iter_report *rep, void *stream)
+                                  int n_src, double tol, int max_iter, int warm_start, double *y,
+                                  double *resid_hist, art_iter_report *rep, void *stream)
 {
-    return iterate_impl(ctx, nullptr, ch, nH, src, n_src, tol, max_iter, nullptr, y, resid_hist, rep, nullptr,
-                        static_cast<cudaStream_t>(stream));
+    if (!ctx) return ART_E_INVALID;
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (warm_start == ART_WARM_NONE)
+        return iterate_impl(ctx, nullptr, ch, nH, src, n_src, tol, max_iter, nullptr, y, resid_hist, rep, nullptr, st);
+    if (warm_start != ART_WARM_COARSE && warm_start != ART_WARM_SURROGATE)
+        return art_fail(ctx, ART_E_INVALID, "art_iterate_ionization: warm_start must be ART_WARM_NONE, "
+                                            "ART_WARM_COARSE or ART_WARM_SURROGATE");
+    if (warm_start == ART_WARM_SURROGATE && !ctx->net)
+        return art_fail(ctx, ART_E_STATE, "art_iterate_ionization: train the context's surrogate "
+                                          "(art_surrogate_train) before ART_WARM_SURROGATE");
+    art_warm_options w;
+    art_warm_options_default(&w);
+    if (warm_start == ART_WARM_COARSE) {
+        w.use_net = 0;
+        w.phase1_max_iter = 0;   // the coarse-mesh start, then plain iterations
+    }
+    art_warm_report wr{};
+    return iterate_impl(ctx, warm_start == ART_WARM_SURROGATE ? ctx->net : nullptr, ch, nH, src, n_src, tol,
+                        max_iter, &w, y, resid_hist, rep, &wr, st);
 }
 
 art_status art_evolve_options_default(art_evolve_options *o)

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -729,6 +730,70 @@ art_status art_net_train_step(art_net *n, int nx, int ny, int nz, const float *X
         NCK(n, cudaMemcpyAsync(loss, n->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
         return check_err(n, st);
     }
+    return ART_OK;
+}
+
+
+art_status art_train_opts_default(art_train_opts *o)
+{
+    if (!o) return ART_E_INVALID;
+    std::memset(o, 0, sizeof(*o));
+    o->steps = 0;
+    o->seed = 1;
+    o->reset = 0;
+    art_net_options_default(&o->net);
+    o->stream = nullptr;
+    return ART_OK;
+}
+
+art_status art_surrogate_train(art_ctx *ctx, const art_dataset *data, const art_train_opts *opt,
+                               art_train_report *rep)
+{
+    if (!ctx) return ART_E_INVALID;
+    if (!data || !data->X || !data->t || data->n_samples < 1)
+        return art_fail(ctx, ART_E_INVALID, "art_surrogate_train: null dataset, no samples or null X / t");
+    if (ctx->grids.size() != 1 || data->nx != ctx->grid.nx || data->ny != ctx->grid.ny || data->nz != ctx->grid.nz)
+        return art_fail(ctx, ART_E_INVALID, "art_surrogate_train: the samples must be on the context's grid");
+    art_train_opts o;
+    if (opt) o = *opt;
+    else art_train_opts_default(&o);
+    if (o.steps < 0) return art_fail(ctx, ART_E_INVALID, "art_surrogate_train: steps must be >= 0");
+    const int steps = o.steps > 0 ? o.steps : 8 * data->n_samples;
+    const auto t0 = std::chrono::steady_clock::now();
+    if (ctx->net && o.reset) {
+        art_net_destroy(ctx->net);
+        ctx->net = nullptr;
+    }
+    if (!ctx->net) {
+        art_net *n = nullptr;
+        const art_status s = art_net_create(&o.net, &n);
+        if (s != ART_OK) return art_fail(ctx, s, "art_surrogate_train: network creation failed");
+        ctx->net = n;
+    }
+    std::vector<double> hist(steps);
+    art_status s = art_net_train(ctx->net, data->nx, data->ny, data->nz, data->n_samples, data->X, data->t, data->w,
+                                 steps, o.seed, hist.data(), o.stream);
+    if (s == ART_OK) s = art_net_check(ctx->net, o.stream);
+    if (s != ART_OK) return art_fail(ctx, s, std::string("art_surrogate_train: ") + art_net_last_error(ctx->net));
+    if (rep) {
+        rep->steps = steps;
+        const int ep = std::min(steps, data->n_samples);
+        double m0 = 0.0, m1 = 0.0;
+        for (int i = 0; i < ep; ++i) {
+            m0 += hist[i];
+            m1 += hist[steps - ep + i];
+        }
+        rep->first_epoch_loss = ep ? m0 / ep : 0.0;
+        rep->last_epoch_loss = ep ? m1 / ep : 0.0;
+        rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return ART_OK;
+}
+
+art_status art_surrogate_network(art_ctx *ctx, art_net **out)
+{
+    if (!ctx || !out) return ART_E_INVALID;
+    *out = ctx->net;
     return ART_OK;
 }
 

@@ -30,7 +30,7 @@ template <int WB, int WC, int DMAX, int MINB>
 cudaError_t wave_launch(const WaveArgs &a, int n_units, cudaStream_t st)
 {
     using Sh = WaveShape<WB, WC, DMAX>;
-    wave_kernel<WB, WC, DMAX, MINB, 4><<<(unsigned)n_units, Sh::NT, Sh::bytes, st>>>(a);
+    wave_kernel<WB, WC, DMAX, MINB><<<(unsigned)n_units, Sh::NT, Sh::bytes, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -38,7 +38,7 @@ cudaError_t wave_launch(const WaveArgs &a, int n_units, cudaStream_t st)
 template <int WB, int WC, int DMAX, int MINB> int wave_prepare()
 {
     using Sh = WaveShape<WB, WC, DMAX>;
-    auto kern = wave_kernel<WB, WC, DMAX, MINB, 4>;
+    auto kern = wave_kernel<WB, WC, DMAX, MINB>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::bytes) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -58,14 +58,15 @@ struct WVariant {
 };
 
 #define ART_WV(wb, wc, dm, mb) {wb, wc, dm, mb, &wave_launch<wb, wc, dm, mb>, &wave_prepare<wb, wc, dm, mb>}
-// Compiled shapes: warps along b and c (a warp tile is 8 x 4 columns), the
+// Compiled shapes: warps along b and c (a warp tile is 8 x 8 columns), the
 // direction slots of a unit (classes with more directions are split into
 // groups), min CTAs per SM.
 const WVariant kWave[] = {
-    ART_WV(2, 4, 40, 2),   // N_side 8 (26-37 directions per class)
-    ART_WV(2, 4, 12, 3),   // N_side 3-4 (3-11)
-    ART_WV(2, 4, 4, 3),    // N_side 1-2 (1-4)
-    ART_WV(4, 4, 40, 1),   // 32 x 16 columns, N_side 8
+    ART_WV(2, 2, 16, 6),   // 16 x 16 columns; N_side 8 (26-37 directions per class: 2-3 groups)
+    ART_WV(2, 2, 12, 6),   // N_side 3-4 (3-11)
+    ART_WV(2, 2, 4, 6),    // N_side 1-2 (1-4)
+    ART_WV(2, 4, 16, 3),   // 16 x 32 columns
+    ART_WV(4, 2, 16, 3),   // 32 x 16 columns
 };
 #undef ART_WV
 const int kNumWave = int(sizeof(kWave) / sizeof(kWave[0]));
@@ -85,7 +86,7 @@ float signed_len(double ds, bool neg) { return std::copysign(std::fabs(float(ds)
 
 void build_wave(const art_ctx *ctx, const WVariant &v, WaveHost &t)
 {
-    const int TB = 8 * v.wb, TC = 4 * v.wc;
+    const int TB = 8 * v.wb, TC = 8 * v.wc;
     long long jpart_off = 0, cell_off = 0;
     struct Raw {
         WaveUnit u;
@@ -204,7 +205,7 @@ void build_wave(const art_ctx *ctx, const WVariant &v, WaveHost &t)
         u.up_c = r.ic > 0 ? pos[r.key - nib] : -1;
         if (u.eb >= 0) {
             u.eb = eoff;
-            eoff += (long long)C.Na * v.wc * v.dmax * 4;
+            eoff += (long long)C.Na * v.wc * v.dmax * 8;
         }
         if (u.ec >= 0) {
             u.ec = eoff;
@@ -221,7 +222,7 @@ void build_wave(const art_ctx *ctx, const WVariant &v, WaveHost &t)
 // its allocation.
 bool wave_tables_ok(const WaveHost &t, const WVariant &v, std::string &why)
 {
-    const int TB = 8 * v.wb, TC = 4 * v.wc;
+    const int TB = 8 * v.wb, TC = 8 * v.wc;
     for (size_t i = 0; i < t.units.size(); ++i) {
         const WaveUnit &u = t.units[i];
         if (u.cls < 0 || u.cls >= (int)t.classes.size() || u.nd < 1 || u.nd > v.dmax || u.d0 < 0 ||
@@ -247,7 +248,7 @@ bool wave_tables_ok(const WaveHost &t, const WVariant &v, std::string &why)
             const WaveUnit &w = t.units[q];
             const bool nb = k == 0 ? (w.tb + TB == u.tb && w.tc == u.tc) : (w.tc + TC == u.tc && w.tb == u.tb);
             const long long o = k == 0 ? w.eb : w.ec;
-            const long long len = k == 0 ? (long long)C.Na * v.wc * v.dmax * 4 : (long long)C.Na * v.wb * v.dmax * 8;
+            const long long len = (long long)C.Na * (k == 0 ? v.wc : v.wb) * v.dmax * 8;
             if (!nb || w.cls != u.cls || w.d0 != u.d0 || w.nd != u.nd || o < 0 || o % 4 || o + len > t.edge_floats) {
                 why = "unit " + std::to_string(i) + ": upstream tile or its buffer";
                 return false;

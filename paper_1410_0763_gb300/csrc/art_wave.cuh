@@ -14,13 +14,14 @@
 //    kind 1 from the ray that enters the slab in its own column, kind 2 from
 //    the ray one column upstream along the axis crossed first, kind 3 from the
 //    diagonal neighbour.
-//  * Lane = ray column.  A warp owns an 8 (b) x 4 (c) tile of columns and, at
-//    each step, one slab of it: every lane computes its cell's segments for
-//    every direction of the unit, holding the intensity of the ray that sits
-//    in its column in a register per direction.  The intensity handed from a
-//    column to its downstream neighbour inside the warp moves by a warp
-//    shuffle; at the warp's edges it goes through shared memory, and at the
-//    CTA's edges through global memory.
+//  * A warp owns an 8 (b) x 8 (c) tile of ray columns and, at each step, one
+//    slab of it; a lane owns two columns (two neighbouring c rows), so it
+//    marches two independent cells per direction.  The intensity handed from a
+//    column to its downstream neighbour moves inside the lane (between its two
+//    rows), by a warp shuffle, through shared memory at the warp's edges, or
+//    through global memory at the CTA's edges.  The intensity of the ray that
+//    sits in each column, per direction, is kept in shared memory between
+//    slabs, so the direction loop stays rolled (small code).
 //  * A CTA owns WB x WC warp tiles.  Warp (wb, wc) handles slab t - wb - wc at
 //    step t, so everything it receives from the warps upstream of it was
 //    written one step earlier (double-buffered by step parity): one barrier
@@ -30,15 +31,16 @@
 //    units upstream of it (the tile diagonal), and a CTA takes the next number
 //    from a ticket counter when it starts.  A CTA waits only on units with
 //    smaller tickets, which are running or done, so the waits always end.
-//    The downstream CTA polls per-warp-row progress flags (release / acquire at
-//    GPU scope) before it copies an upstream slab's edge intensities; every
-//    wait is bounded in time, and a wait that runs out sets an error word,
+//    Each warp row on a CTA's downstream faces publishes its progress every
+//    PUB slabs (release at GPU scope); the downstream warp polls only when
+//    the last value it saw does not cover the slab it needs (then acquires).
+//    Every wait is bounded in time; one that runs out sets an error word,
 //    after which every CTA leaves its loop at the next step.
 //  * Each unit writes the J partial of its (class, direction group) once per
 //    cell; reduce_kernel sums the partials in fixed order with Kahan.  Within a
-//    unit a cell's direction sum is Kahan-compensated per group of KG
-//    directions.  Results are deterministic.
-//  * Arithmetic per (warp, slab), chosen by ballot over the warp's 32 cells:
+//    unit a cell's direction sum is Kahan-compensated every 8 directions.
+//    Results are deterministic.
+//  * Arithmetic per (warp, slab), chosen by ballot over the warp's 64 cells:
 //    every kappa below KAP_THIN (series only), every kappa at or above
 //    KAP_THICK (hardware exponential only), else both with a per-segment
 //    select (series below x = 1/4).  The series path deposits ds phi(x)
@@ -121,13 +123,6 @@ __device__ __forceinline__ long long wv_now()
     return t;
 }
 
-__device__ __forceinline__ int wv_ld_acquire(const int *p)
-{
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 __device__ __forceinline__ int wv_ld_relaxed(const int *p)
 {
     int v;
@@ -160,17 +155,23 @@ __device__ __forceinline__ void wv_cp_wait()
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// Poll a progress flag until it reaches `target` or the wait runs out (or
-// another CTA reported an error).  Returns 1 when the flag is reached.
+// Poll a progress flag (relaxed loads) until it reaches `target` or the wait
+// runs out (or another CTA reported an error); a fence then makes it an
+// acquire.  Returns the value seen, or -1 if the wait ran out.
 __device__ __forceinline__ int wv_wait(const int *flag, int target, const WaveArgs &p)
 {
-    if (wv_ld_acquire(flag) >= target) return 1;
-    const long long t0 = wv_now();
-    for (;;) {
-        __nanosleep(64);
-        if (wv_ld_acquire(flag) >= target) return 1;
-        if (wv_ld_relaxed(p.err) != 0 || wv_now() - t0 > p.wait_ns) return 0;
+    int v = wv_ld_relaxed(flag);
+    if (v < target) {
+        const long long t0 = wv_now();
+        for (;;) {
+            __nanosleep(64);
+            v = wv_ld_relaxed(flag);
+            if (v >= target) break;
+            if (wv_ld_relaxed(p.err) != 0 || wv_now() - t0 > p.wait_ns) return -1;
+        }
     }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    return v;
 }
 
 // Checked builds (ART_WAVE_CHECK) test every global index against its buffer
@@ -237,108 +238,144 @@ __device__ __forceinline__ float wv_lds(unsigned a)
     asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
     return v;
 }
+__device__ __forceinline__ void wv_sts2(unsigned a, float x, float y)
+{
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(x), "f"(y) : "memory");
+}
+__device__ __forceinline__ float2 wv_lds2(unsigned a)
+{
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+    return v;
+}
 
 // Per-lane exchange state of one step: shared-window byte addresses of this
-// lane's slots for direction 0 (direction d is 16 d bytes further along B,
-// 32 d along C).
+// lane's slots for direction 0 (direction d is 32 d bytes further).  B-face
+// slots hold the lane's two rows (2 cl, 2 cl + 1), C-face slots its column bl.
 struct WvXch {
-    unsigned bo, bi;   // B-face output / input slot
-    unsigned co, ci;   // C-face output / input slot
+    unsigned bo, bi;   // B-face output / input pair
+    unsigned co, ci;   // C-face output / input
     bool b0, b7, c0, c3;
 };
 
-// Hand the intensity v (leaving this lane's column across a b-plane) to the
-// downstream neighbour; return the intensity arriving from upstream.
-__device__ __forceinline__ float wv_xb(const WvXch &x, float v, int d)
+// Hand-off across a b-plane: each of the lane's rows takes the intensity that
+// leaves the column one step upstream along b (the lane to the left, or the
+// B-face input at bl = 0); lanes at bl = 7 write theirs to the B-face output.
+__device__ __forceinline__ void wv_xb(const WvXch &x, float &v0, float &v1, int d)
 {
-    const float n = __shfl_up_sync(0xffffffffu, v, 1);
-    if (x.b7) wv_sts(x.bo + 16 * d, v);
-    const float in = wv_lds(x.bi + 16 * d);
-    return x.b0 ? in : n;
+    const float n0 = __shfl_up_sync(0xffffffffu, v0, 1);
+    const float n1 = __shfl_up_sync(0xffffffffu, v1, 1);
+    if (x.b7) wv_sts2(x.bo + 32 * d, v0, v1);
+    const float2 in = wv_lds2(x.bi + 32 * d);
+    v0 = x.b0 ? in.x : n0;
+    v1 = x.b0 ? in.y : n1;
 }
 
-__device__ __forceinline__ float wv_xc(const WvXch &x, float v, int d)
+// Hand-off across a c-plane: the lane's second row takes its first row's
+// intensity; the first row takes the second row of the lane one step upstream
+// along c (or the C-face input at cl = 0); lanes at cl = 3 write their second
+// row to the C-face output.
+__device__ __forceinline__ void wv_xc(const WvXch &x, float &v0, float &v1, int d)
 {
-    const float n = __shfl_up_sync(0xffffffffu, v, 8);
-    if (x.c3) wv_sts(x.co + 32 * d, v);
+    const float n = __shfl_up_sync(0xffffffffu, v1, 8);
+    if (x.c3) wv_sts(x.co + 32 * d, v1);
     const float in = wv_lds(x.ci + 32 * d);
-    return x.c0 ? in : n;
+    v1 = v0;
+    v0 = x.c0 ? in : n;
 }
 
-// All directions of the unit for one slab: ray states R are updated in place,
-// the cell's direction sum returned in (js, jc) (Kahan).
-template <int MODE, int DMAX, int KG>
-__device__ __forceinline__ void wv_dirs(const WvCell &c, float (&R)[DMAX], const float4 *__restrict__ tab, int nd,
-                                        const WvXch &x, float &js, float &jc)
+// All directions of the unit for one slab, for the lane's two cells: the ray
+// states (shared memory, pairs at rs + 8 NT d) are updated in place; the
+// cells' direction sums are returned in (js, jc) (Kahan every 8 directions).
+template <int MODE, int NT>
+__device__ __forceinline__ void wv_dirs(const WvCell &c0, const WvCell &c1, unsigned rs, unsigned tab, int nd,
+                                        const WvXch &x, float &js0, float &jc0, float &js1, float &jc1)
 {
-    js = 0.0f;
-    jc = 0.0f;
-#pragma unroll
-    for (int d0 = 0; d0 < DMAX; d0 += KG) {
-        if (d0 >= nd) break;
-        float acc = 0.0f;
-#pragma unroll
-        for (int q = 0; q < KG; ++q) {
-            const int d = d0 + q;
-            if (d < nd) {
-                const float4 e = tab[d];
-                const unsigned c1 = __float_as_uint(e.x) >> 31;   // first hand-off along c
-                const unsigned c2 = __float_as_uint(e.y) >> 31;   // two or more segments
-                const unsigned c3 = __float_as_uint(e.z) >> 31;   // three segments
-                float A;
-                float o = wv_seg<MODE, true>(c, R[d], fabsf(e.x), A);
-                if (c2) {
-                    if (c1) {
-                        const float v = wv_xc(x, o, d);
-                        o = wv_seg<MODE, false>(c, v, fabsf(e.y), A);
-                        if (c3) {
-                            const float w = wv_xb(x, o, d);
-                            o = wv_seg<MODE, false>(c, w, fabsf(e.z), A);
-                        }
-                    } else {
-                        const float v = wv_xb(x, o, d);
-                        o = wv_seg<MODE, false>(c, v, fabsf(e.y), A);
-                        if (c3) {
-                            const float w = wv_xc(x, o, d);
-                            o = wv_seg<MODE, false>(c, w, fabsf(e.z), A);
-                        }
-                    }
-                }
-                R[d] = o;
-                acc = fmaf(A, e.w, acc);
+    js0 = jc0 = js1 = jc1 = 0.0f;
+    float acc0 = 0.0f, acc1 = 0.0f;
+    float4 e;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(e.x), "=f"(e.y), "=f"(e.z), "=f"(e.w) : "r"(tab));
+    float2 R = wv_lds2(rs);
+#pragma unroll 1
+    for (int d = 0; d < nd; ++d) {
+        // next direction's table entry and ray states (the last iteration reloads its own)
+        const int dn = d + 1 < nd ? d + 1 : d;
+        float4 en;
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(en.x), "=f"(en.y), "=f"(en.z), "=f"(en.w)
+                     : "r"(tab + 16 * dn));
+        const float2 Rn = wv_lds2(rs + 8 * NT * dn);
+        const unsigned f1 = __float_as_uint(e.x) >> 31;   // first hand-off along c
+        const unsigned f2 = __float_as_uint(e.y) >> 31;   // two or more segments
+        const unsigned f3 = __float_as_uint(e.z) >> 31;   // three segments
+        float A0, A1;
+        float o0 = wv_seg<MODE, true>(c0, R.x, fabsf(e.x), A0);
+        float o1 = wv_seg<MODE, true>(c1, R.y, fabsf(e.x), A1);
+        if (f2) {
+            if (f1) wv_xc(x, o0, o1, d);
+            else wv_xb(x, o0, o1, d);
+            o0 = wv_seg<MODE, false>(c0, o0, fabsf(e.y), A0);
+            o1 = wv_seg<MODE, false>(c1, o1, fabsf(e.y), A1);
+            if (f3) {
+                if (f1) wv_xb(x, o0, o1, d);
+                else wv_xc(x, o0, o1, d);
+                o0 = wv_seg<MODE, false>(c0, o0, fabsf(e.z), A0);
+                o1 = wv_seg<MODE, false>(c1, o1, fabsf(e.z), A1);
             }
         }
-        const float y = acc - jc;
-        const float t = js + y;
-        jc = (t - js) - y;
-        js = t;
+        wv_sts2(rs + 8 * NT * d, o0, o1);
+        acc0 = fmaf(A0, e.w, acc0);
+        acc1 = fmaf(A1, e.w, acc1);
+        if ((d & 7) == 7) {
+            float y = acc0 - jc0, t = js0 + y;
+            jc0 = (t - js0) - y;
+            js0 = t;
+            y = acc1 - jc1;
+            t = js1 + y;
+            jc1 = (t - js1) - y;
+            js1 = t;
+            acc0 = acc1 = 0.0f;
+        }
+        e = en;
+        R = Rn;
     }
+    float y = acc0 - jc0, t = js0 + y;
+    jc0 = (t - js0) - y;
+    js0 = t;
+    y = acc1 - jc1;
+    t = js1 + y;
+    jc1 = (t - js1) - y;
+    js1 = t;
 }
 
 template <int WB, int WC, int DMAX> struct WaveShape {
     static constexpr int NT = 32 * WB * WC;
-    static constexpr int TB = 8 * WB, TC = 4 * WC;
+    static constexpr int TB = 8 * WB, TC = 8 * WC;
     static constexpr int RT = (WB + WC <= 4) ? 4 : ((WB + WC <= 8) ? 8 : 16);   // table ring (slabs)
-    static constexpr int XB_PAR = (WB + 1) * WC * DMAX * 4;   // floats per parity
+    static constexpr int XB_PAR = (WB + 1) * WC * DMAX * 8;   // floats per parity
     static constexpr int XC_PAR = (WC + 1) * WB * DMAX * 8;
     static constexpr size_t off_xb = size_t(RT) * DMAX * 16;
     static constexpr size_t off_xc = off_xb + size_t(2) * XB_PAR * 4;
     static constexpr size_t off_fs = off_xc + size_t(2) * XC_PAR * 4;
-    static constexpr size_t bytes = off_fs + size_t(2) * NT * 8;
-    static constexpr long long edge_b(int Na) { return (long long)Na * WC * DMAX * 4; }
+    static constexpr size_t off_rs = off_fs + size_t(2) * NT * 16;
+    static constexpr size_t bytes = off_rs + size_t(DMAX) * NT * 8;
+    static constexpr long long edge_b(int Na) { return (long long)Na * WC * DMAX * 8; }
     static constexpr long long edge_c(int Na) { return (long long)Na * WB * DMAX * 8; }
 };
 
-template <int WB, int WC, int DMAX, int MINB, int KG>
+constexpr int WAVE_PUB = 4;   // slabs between progress publications
+
+template <int WB, int WC, int DMAX, int MINB>
 __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs p)
 {
     using Sh = WaveShape<WB, WC, DMAX>;
     constexpr int NT = Sh::NT, RT = Sh::RT;
     extern __shared__ __align__(16) unsigned char wsm[];
     float4 *tab = reinterpret_cast<float4 *>(wsm);                  // [RT][DMAX]
-    float *XB = reinterpret_cast<float *>(wsm + Sh::off_xb);        // [2][WB+1][WC][DMAX][4]
+    float *XB = reinterpret_cast<float *>(wsm + Sh::off_xb);        // [2][WB+1][WC][DMAX][8]
     float *XC = reinterpret_cast<float *>(wsm + Sh::off_xc);        // [2][WC+1][WB][DMAX][8]
-    float2 *FS = reinterpret_cast<float2 *>(wsm + Sh::off_fs);      // [2][NT]
+    float4 *FS = reinterpret_cast<float4 *>(wsm + Sh::off_fs);      // [2][NT]: (kappa, src) of the two cells
+    float2 *RS = reinterpret_cast<float2 *>(wsm + Sh::off_rs);      // [DMAX][NT]: ray states of the two columns
     __shared__ int s_unit;
     __shared__ long long s_seg[DMAX];   // first table entry of each direction of the unit
     __shared__ long long s_up[2];       // output buffers of the upstream units (B, C)
@@ -353,31 +390,37 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
     const WaveUnit U = p.units[u];
     const WaveClass C = p.classes[U.cls];
     const int Na = C.Na, nd = U.nd;
-    const int j = U.tb + 8 * wb + bl, k = U.tc + 4 * wc + cl;   // canonical column
-    const bool in_box = j < C.Nb && k < C.Nc;
-    const int pb = C.sb > 0 ? j : C.Nb - 1 - j, pc = C.sc > 0 ? k : C.Nc - 1 - k;
-    // the lane's column in the axis-a field layout [a][c][b], and its cell of
-    // slab m in the natural layout of the J partial: Jl[m * jstep]
-    const float2 *Fl = (C.a == 0 ? p.field0 : (C.a == 1 ? p.field1 : p.field2)) + C.cell_off +
-                       (in_box ? (long long)pc * C.Nb + pb : 0);
+    const int j = U.tb + 8 * wb + bl;                          // canonical b column
+    const int k0 = U.tc + 8 * wc + 2 * cl;                      // canonical c rows k0, k0 + 1
+    const bool in0 = j < C.Nb && k0 < C.Nc, in1 = j < C.Nb && k0 + 1 < C.Nc;
+    const int pb = C.sb > 0 ? j : C.Nb - 1 - j;
+    const int pc0 = C.sc > 0 ? k0 : C.Nc - 1 - k0, pc1 = C.sc > 0 ? k0 + 1 : C.Nc - 2 - k0;
+    // the lane's two columns in the axis-a field layout [a][c][b], and its
+    // cells of slab m in the natural layout of the J partial: Jl[m * jstep]
+    const float2 *Fb = (C.a == 0 ? p.field0 : (C.a == 1 ? p.field1 : p.field2)) + C.cell_off;
+    const float2 *F0 = Fb + (in0 ? (long long)pc0 * C.Nb + pb : 0);
+    const float2 *F1 = Fb + (in1 ? (long long)pc1 * C.Nb + pb : 0);
     const int fslab = C.Nb * C.Nc;
-    const long long jbase = (C.sa > 0 ? 0 : (long long)(Na - 1) * C.stride_a) + (long long)pb * C.stride_b +
-                            (long long)pc * C.stride_c;
+    const long long ja = C.sa > 0 ? 0 : (long long)(Na - 1) * C.stride_a;
+    const long long jb0 = ja + (long long)pb * C.stride_b + (long long)pc0 * C.stride_c;
+    const long long jb1 = ja + (long long)pb * C.stride_b + (long long)pc1 * C.stride_c;
     const int jstep = (int)(C.sa > 0 ? C.stride_a : -C.stride_a);
-    float *Jl = p.jpart + U.jpart + (in_box ? jbase : 0);
-    const bool jl_ok = wv_ok(!in_box || (U.jpart + jbase >= 0 && U.jpart + jbase < p.jpart_floats &&
-                                         U.jpart + jbase + (long long)(Na - 1) * jstep >= 0 &&
-                                         U.jpart + jbase + (long long)(Na - 1) * jstep < p.jpart_floats),
-                             p.err);
+    auto jrange_ok = [&](bool in, long long jb) {
+        return !in || (U.jpart + jb >= 0 && U.jpart + jb < p.jpart_floats &&
+                       U.jpart + jb + (long long)(Na - 1) * jstep >= 0 &&
+                       U.jpart + jb + (long long)(Na - 1) * jstep < p.jpart_floats);
+    };
+    const bool jl_ok = wv_ok(jrange_ok(in0, jb0) && jrange_ok(in1, jb1), p.err);
+    float *J0 = p.jpart + U.jpart + (in0 ? jb0 : 0);
+    float *J1 = p.jpart + U.jpart + (in1 ? jb1 : 0);
     const bool stalled = u == p.stall_unit;
 
     if (tid < nd) s_seg[tid] = p.seg_off[U.d0 + tid];
     if (tid == 0) s_up[0] = U.up_b >= 0 ? p.units[U.up_b].eb : -1;
     if (tid == 1) s_up[1] = U.up_c >= 0 ? p.units[U.up_c].ec : -1;
-
     // box-edge inputs carry the boundary intensity in both parities
     if (U.up_b < 0)
-        for (int e = tid; e < WC * DMAX * 4; e += NT) {
+        for (int e = tid; e < WC * DMAX * 8; e += NT) {
             XB[e] = p.i_bc;
             XB[Sh::XB_PAR + e] = p.i_bc;
         }
@@ -386,12 +429,13 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
             XC[e] = p.i_bc;
             XC[Sh::XC_PAR + e] = p.i_bc;
         }
+    // every ray enters the box with the boundary intensity
+    for (int d = 0; d < nd; ++d) RS[d * NT + tid] = make_float2(p.i_bc, p.i_bc);
 
-    float R[DMAX];
-#pragma unroll
-    for (int d = 0; d < DMAX; ++d) R[d] = p.i_bc;
+    // progress of the upstream warps last seen by this warp (uniform)
+    int seen_b = 0, seen_c = 0;
 
-    // Stage what step t + 1 reads: the table of slab t + 1, this lane's field
+    // Stage what step t + 1 reads: the table of slab t + 1, this lane's fields
     // of its next slab, and (warps on the CTA's upstream edges) the upstream
     // CTA's edge intensities, into the parity that step t + 1 reads (t & 1).
     // Returns 0 if a wait ran out.
@@ -399,24 +443,32 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
         const int s1 = t + 1, rp = t & 1;
         if (tid < nd && s1 < Na) wv_cp16(tab + (s1 & (RT - 1)) * DMAX + tid, p.segs + s_seg[tid] + s1);
         const int mn = s1 - wb - wc;
-        if (in_box && mn >= 0 && mn < Na) {
-            const int pa = C.sa > 0 ? mn : Na - 1 - mn;
-            wv_cp8(FS + (s1 & 1) * NT + tid, Fl + (long long)pa * fslab);   // read at step s1 as FS[s1 & 1]
+        if (mn >= 0 && mn < Na) {
+            const long long pa = (C.sa > 0 ? mn : Na - 1 - mn) * (long long)fslab;
+            float2 *dst = reinterpret_cast<float2 *>(FS + (s1 & 1) * NT + tid);   // read at step s1
+            if (in0) wv_cp8(dst, F0 + pa);
+            if (in1) wv_cp8(dst + 1, F1 + pa);
         }
         int ok = 1;
         if (wb == 0 && U.up_b >= 0) {
             const int s = s1 - wc;
             if (s >= 0 && s < Na) {
-                const int *fl = p.flags + (long long)U.up_b * (WB + WC) + wc;
-                if (lane == 0) ok = wv_wait(fl, s + 1, p);
-                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (s + 1 > seen_b) {
+                    int v = 0;
+                    if (lane == 0) v = wv_wait(p.flags + (long long)U.up_b * (WB + WC) + wc, s + 1, p);
+                    v = __shfl_sync(0xffffffffu, v, 0);
+                    if (v < 0) ok = 0;
+                    else seen_b = v;
+                }
                 if (ok) {
-                    (void)wv_ld_acquire(fl);
                     const long long eb_up = s_up[0];
                     for (int dd = lane; dd < nd; dd += 32) {
-                        const long long o = eb_up + (((long long)s * WC + wc) * DMAX + dd) * 4;
-                        if (wv_ok(eb_up >= 0 && o + 4 <= p.edge_floats, p.err))
-                            wv_cp16(XB + rp * Sh::XB_PAR + (wc * DMAX + dd) * 4, p.edge + o);
+                        const long long o = eb_up + (((long long)s * WC + wc) * DMAX + dd) * 8;
+                        if (wv_ok(eb_up >= 0 && o + 8 <= p.edge_floats, p.err)) {
+                            float *dst = XB + rp * Sh::XB_PAR + (wc * DMAX + dd) * 8;
+                            wv_cp16(dst, p.edge + o);
+                            wv_cp16(dst + 4, p.edge + o + 4);
+                        }
                     }
                 }
             }
@@ -424,12 +476,15 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
         if (wc == 0 && U.up_c >= 0) {
             const int s = s1 - wb;
             if (s >= 0 && s < Na) {
-                const int *fl = p.flags + (long long)U.up_c * (WB + WC) + WC + wb;
                 int okc = 1;
-                if (lane == 0) okc = wv_wait(fl, s + 1, p);
-                okc = __shfl_sync(0xffffffffu, okc, 0);
+                if (s + 1 > seen_c) {
+                    int v = 0;
+                    if (lane == 0) v = wv_wait(p.flags + (long long)U.up_c * (WB + WC) + WC + wb, s + 1, p);
+                    v = __shfl_sync(0xffffffffu, v, 0);
+                    if (v < 0) okc = 0;
+                    else seen_c = v;
+                }
                 if (okc) {
-                    (void)wv_ld_acquire(fl);
                     const long long ec_up = s_up[1];
                     for (int dd = lane; dd < nd; dd += 32) {
                         const long long o = ec_up + (((long long)s * WB + wb) * DMAX + dd) * 8;
@@ -446,7 +501,7 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
         return ok;
     };
 
-    __syncthreads();   // s_seg
+    __syncthreads();   // s_seg, s_up, ray states
     // A wait that ran out ends the unit: the decision is taken by the barrier
     // itself (__syncthreads_or), so every thread leaves the loop at the same step.
     int bad = stage(-1) ? 0 : 1;
@@ -457,56 +512,65 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
     const bool b_out = wb == WB - 1, c_out = wc == WC - 1;
     const int fl_b = u * (WB + WC) + wc, fl_c = u * (WB + WC) + WC + wb;
     const unsigned xb0 = wv_smem(XB), xc0 = wv_smem(XC);
+    const unsigned rs0 = wv_smem(RS) + 8 * tid, tab0 = wv_smem(tab);
     for (int t = 0; t < T && !abort_; ++t) {
         const int m = t - wb - wc;
-        // progress of the slab written to global memory in the previous step
-        if (lane == 0 && !stalled && m - 1 >= 0 && m - 1 < Na) {
+        // progress of the slabs written to global memory in earlier steps
+        if (lane == 0 && !stalled && m - 1 >= 0 && m - 1 < Na && m % WAVE_PUB == 0) {
             if (b_out) wv_st_release(p.flags + fl_b, m);
             if (c_out) wv_st_release(p.flags + fl_c, m);
         }
         if (!stage(t)) bad = 1;
         if (m >= 0 && m < Na) {
             const int par = t & 1;
-            const float2 f = FS[par * NT + tid];
-            WvCell c;
-            c.kap = in_box ? f.x : 0.0f;
-            const float src = in_box ? f.y : 0.0f;
-            c.rk = c.kap > 0.0f ? wv_rcp(c.kap) : 0.0f;
-            c.E = p.field_form ? src : c.kap * src;
-            c.S = p.field_form ? src * c.rk : src;
-            c.k2 = -1.4426950408889634f * c.kap;
+            const float4 f = FS[par * NT + tid];
+            WvCell c0, c1;
+            c0.kap = in0 ? f.x : 0.0f;
+            c1.kap = in1 ? f.z : 0.0f;
+            const float src0 = in0 ? f.y : 0.0f, src1 = in1 ? f.w : 0.0f;
+            c0.rk = c0.kap > 0.0f ? wv_rcp(c0.kap) : 0.0f;
+            c1.rk = c1.kap > 0.0f ? wv_rcp(c1.kap) : 0.0f;
+            c0.E = p.field_form ? src0 : c0.kap * src0;
+            c1.E = p.field_form ? src1 : c1.kap * src1;
+            c0.S = p.field_form ? src0 * c0.rk : src0;
+            c1.S = p.field_form ? src1 * c1.rk : src1;
+            c0.k2 = -1.4426950408889634f * c0.kap;
+            c1.k2 = -1.4426950408889634f * c1.kap;
             WvXch x;
-            x.bo = xb0 + 4 * (par * Sh::XB_PAR + ((wb + 1) * WC + wc) * DMAX * 4 + cl);
-            x.bi = xb0 + 4 * ((par ^ 1) * Sh::XB_PAR + (wb * WC + wc) * DMAX * 4 + cl);
+            x.bo = xb0 + 4 * (par * Sh::XB_PAR + ((wb + 1) * WC + wc) * DMAX * 8 + 2 * cl);
+            x.bi = xb0 + 4 * ((par ^ 1) * Sh::XB_PAR + (wb * WC + wc) * DMAX * 8 + 2 * cl);
             x.co = xc0 + 4 * (par * Sh::XC_PAR + ((wc + 1) * WB + wb) * DMAX * 8 + bl);
             x.ci = xc0 + 4 * ((par ^ 1) * Sh::XC_PAR + (wc * WB + wb) * DMAX * 8 + bl);
             x.b0 = bl == 0;
             x.b7 = bl == 7;
             x.c0 = cl == 0;
             x.c3 = cl == 3;
-            const float4 *tb = tab + (m & (RT - 1)) * DMAX;
-            const unsigned thin = __ballot_sync(0xffffffffu, c.kap < KAP_THIN);
-            const unsigned thick = __ballot_sync(0xffffffffu, c.kap >= KAP_THICK);
-            float js, jc;
+            const unsigned tb = tab0 + 16 * (m & (RT - 1)) * DMAX;
+            const unsigned thin = __ballot_sync(0xffffffffu, c0.kap < KAP_THIN && c1.kap < KAP_THIN);
+            const unsigned thick = __ballot_sync(0xffffffffu, c0.kap >= KAP_THICK && c1.kap >= KAP_THICK);
+            float js0, jc0, js1, jc1;
             if (thin == 0xffffffffu)
-                wv_dirs<MODE_THIN, DMAX, KG>(c, R, tb, nd, x, js, jc);
+                wv_dirs<MODE_THIN, NT>(c0, c1, rs0, tb, nd, x, js0, jc0, js1, jc1);
             else if (thick == 0xffffffffu)
-                wv_dirs<MODE_THICK, DMAX, KG>(c, R, tb, nd, x, js, jc);
+                wv_dirs<MODE_THICK, NT>(c0, c1, rs0, tb, nd, x, js0, jc0, js1, jc1);
             else
-                wv_dirs<MODE_MIXED, DMAX, KG>(c, R, tb, nd, x, js, jc);
-            if (in_box && jl_ok) {
-                const float scale = thick == 0xffffffffu ? c.rk : 1.0f;
-                Jl[m * jstep] = (js - jc) * scale;
+                wv_dirs<MODE_MIXED, NT>(c0, c1, rs0, tb, nd, x, js0, jc0, js1, jc1);
+            if (jl_ok) {
+                const bool thk = thick == 0xffffffffu;
+                if (in0) J0[m * jstep] = (js0 - jc0) * (thk ? c0.rk : 1.0f);
+                if (in1) J1[m * jstep] = (js1 - jc1) * (thk ? c1.rk : 1.0f);
             }
             // edge intensities of this slab to the downstream CTAs
             if ((b_out && U.eb >= 0) || (c_out && U.ec >= 0)) {
                 __syncwarp();
                 if (b_out && U.eb >= 0)
                     for (int dd = lane; dd < nd; dd += 32) {
-                        const float4 v = *reinterpret_cast<const float4 *>(
-                            XB + par * Sh::XB_PAR + ((wb + 1) * WC + wc) * DMAX * 4 + dd * 4);
-                        const long long o = U.eb + (((long long)m * WC + wc) * DMAX + dd) * 4;
-                        if (wv_ok(o + 4 <= p.edge_floats, p.err)) *reinterpret_cast<float4 *>(p.edge + o) = v;
+                        const float *srcs = XB + par * Sh::XB_PAR + ((wb + 1) * WC + wc) * DMAX * 8 + dd * 8;
+                        const long long o = U.eb + (((long long)m * WC + wc) * DMAX + dd) * 8;
+                        if (wv_ok(o + 8 <= p.edge_floats, p.err)) {
+                            *reinterpret_cast<float4 *>(p.edge + o) = *reinterpret_cast<const float4 *>(srcs);
+                            *reinterpret_cast<float4 *>(p.edge + o + 4) = *reinterpret_cast<const float4 *>(srcs + 4);
+                        }
                     }
                 if (c_out && U.ec >= 0)
                     for (int dd = lane; dd < nd; dd += 32) {

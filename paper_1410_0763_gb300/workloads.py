@@ -242,6 +242,22 @@ def diffuse_band_heat(chem: dict, n_quad: int = 4000) -> float:
     return float(np.trapezoid(w * chem["h"] * (nu - chem["nu0"]), nu) / np.trapezoid(w, nu))
 
 
+def clumpy_sweep(n: int = 256, nside: int = 8, seed: int = 5, tau_box: float = 10.0, nbins: int = 4) -> SweepCase:
+    """Sweep input on the clumpy medium of `clumpy` (lognormal sigma 1.5, P(k) ~ k^-3, plus 200
+    spheres at 100x the mean density; seed 5), in the 4 bins of a 1e5 K blackbody above 13.6 eV:
+    kappa_b = rho/<rho> * tau_box/N * sigma_b/sigma_0 (the grf recipe's box optical depth 10 in
+    the first bin, sigma_b the bins' photon-weighted cross sections) and S_b = rho/<rho> in every
+    bin.  Arrays are [bin][z][y][x]."""
+    case = clumpy(n=n, nside=nside, seed=seed)
+    rho = case.nH / case.nH.mean()
+    _, sig, _ = blackbody_bins()
+    sig = sig[:nbins]
+    kappa = np.stack([rho * (tau_box / n) * (s / SIGMA0) for s in sig])
+    src = np.stack([rho] * nbins)
+    return SweepCase("clumpy_sweep", nside, kappa, src, 0, dict(seed=seed, n=n, tau_box=tau_box, nbins=nbins,
+                                                                 sigma_ratio=[float(s / SIGMA0) for s in sig]))
+
+
 def clumpy(n: int = 256, nside: int = 8, seed: int = 5, sigma: float = 1.5, n_clumps: int = 200,
            overdensity: float = 100.0, n_src: int = 8, Q: float = 5e48, box_kpc: float = 6.6,
            nH_mean: float = 1e-3, x0: float = 1e-4) -> HIICase:

@@ -96,6 +96,14 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.art_thermal_default(None) == art.ART_E_INVALID
     assert lib.art_sweep_stream(None, 1, None, None, None, None, None, None) == art.ART_E_INVALID
     assert lib.art_sweep_check(None, None) == art.ART_E_INVALID
+    assert lib.art_iterate_ionization(None, None, None, None, 0, 1e-6, 10, art.ART_WARM_SURROGATE, None, None,
+                                      None, None) == art.ART_E_INVALID
+    assert lib.art_surrogate_train(None, None, None, None) == art.ART_E_INVALID
+    assert lib.art_surrogate_network(None, None) == art.ART_E_INVALID
+    assert lib.art_train_opts_default(None) == art.ART_E_INVALID
+    to = art.ArtTrainOpts()
+    assert lib.art_train_opts_default(ctypes.byref(to)) == art.ART_OK
+    assert (to.steps, to.seed, to.reset, list(to.net.dilation)) == (0, 1, 0, [1, 2, 4, 8])
     assert lib.art_sweep_set_wait(None, 1.0, -1) == art.ART_E_INVALID
     th = art.ArtThermal()
     assert lib.art_thermal_default(ctypes.byref(th)) == art.ART_OK

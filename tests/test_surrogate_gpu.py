@@ -152,3 +152,38 @@ def test_trained_network_beats_the_coarse_sweep_on_held_out_states():
     assert after < before
     assert after < 0.8 * coarse_err, (after, coarse_err)
     net.close()
+
+
+def test_c_abi_surrogate_train_and_the_warm_start_argument():
+    """The boundary's own calls: art_surrogate_train trains the network the context owns on
+    samples of its grid, and art_iterate_ionization's warm_start argument selects the plain,
+    coarse-mesh and surrogate starts; all three reach the same fixed point.  Before training,
+    the surrogate start is a state error."""
+    n, nside, NIT = 32, 2, 8
+    case = wl.hii_region(n=n, nside=nside, box_kpc=1.6)
+    sw = art.ArtSweep((n, n, n), nside, 1, field_form=art.ART_FIELDS_EPS, dx_cm=case.chem["dx"])
+    nH = torch.as_tensor(case.nH, dtype=torch.float64, device="cuda")
+    y_plain, rep_plain = _plain(case, sw, nH)
+    fresh = lambda: torch.as_tensor(case.y0, dtype=torch.float64, device="cuda").clone()
+    with pytest.raises(art.ArtError) as e:
+        sw.iterate(nH, case.chem, srcs(case), fresh(), tol=1e-6, max_iter=300, warm_start=art.ART_WARM_SURROGATE)
+    assert e.value.status == art.ART_E_STATE
+    tr = wl.hii_random(n, nside, seed=300, box_kpc=1.6)
+    V = n ** 3
+    X = torch.empty((NIT, 4, V), device="cuda")
+    T = torch.empty((NIT, V), device="cuda")
+    W = torch.empty((NIT, V), device="cuda")
+    ytr = torch.as_tensor(tr.y0, dtype=torch.float64, device="cuda").clone()
+    sw.surrogate_collect(torch.as_tensor(tr.nH, device="cuda"), tr.chem, srcs(tr), ytr, X, T, NIT, w=W,
+                         coarse_factor=4, coarse_nside=4)
+    rep = sw.surrogate_train(X, T, W, NIT, steps=6 * NIT, seed=2)
+    assert rep.steps == 6 * NIT and np.isfinite(rep.first_epoch_loss)
+    assert rep.last_epoch_loss < rep.first_epoch_loss
+    for ws in (art.ART_WARM_NONE, art.ART_WARM_COARSE, art.ART_WARM_SURROGATE):
+        y = fresh()
+        r, hist = sw.iterate(nH, case.chem, srcs(case), y, tol=1e-6, max_iter=300, warm_start=ws)
+        assert r.converged and hist[-1] < 1e-6
+        yw = y.cpu().numpy()
+        assert np.max(np.abs(yw - y_plain) / y_plain) < 1e-4
+        assert np.max(np.abs((1 - yw) - (1 - y_plain)) / (1 - y_plain)) < 1e-4
+    sw.close()
