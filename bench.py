@@ -37,6 +37,10 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 WORKLOADS = {
+    "clumpy4": dict(n=256, nside=8, seed=5, bins=4, kind="clumpy", steps=12,
+                    desc="256^3 clumpy medium (lognormal sigma 1.5, P(k)~k^-3, + 200 spheres x100), N_side 8 "
+                         "(768 dirs), 4 bins of a 1e5 K blackbody (kappa_b ~ rho sigma_b, box tau 10 in bin 0; "
+                         "S_b ~ rho)"),
     "grf64": dict(n=64, nside=4, seed=2, sigma=1.0,
                   desc="64^3 lognormal GRF (sigma 1, P(k)~k^-3, box tau 10), N_side 4 (192 dirs), 1 bin"),
     "grf128": dict(n=128, nside=8, seed=3, sigma=1.0,
@@ -67,16 +71,21 @@ def measured_bf16_peak():
         return 1700.0
 
 
+def kernel_source(variant: int) -> str:
+    """The source file of the sweep kernel that a variant runs (wavefront variants are 16 and up)."""
+    name = "art_wave.cuh" if variant >= 16 else "art_kernels.cuh"
+    return os.path.join(HERE, "paper_1410_0763_gb300", "csrc", name)
+
+
 def recorded_traffic(workload: str, variant: int, persistent: int):
     """DRAM bytes per sweep launch from the committed ncu summary, if it was
     taken on this workload, kernel variant and launch form with the kernel
     source as it is now; else None."""
     import hashlib
-    path = os.path.join(HERE, "profiles", f"traffic_sweep_block_{workload}.txt")
-    src = os.path.join(HERE, "paper_1410_0763_gb300", "csrc", "art_kernels.cuh")
+    path = os.path.join(HERE, "profiles", f"traffic_sweep_{workload}.txt")
     try:
         rec = dict(line.split(": ", 1) for line in open(path).read().splitlines() if ": " in line)
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        digest = hashlib.sha256(open(kernel_source(variant), "rb").read()).hexdigest()
     except OSError:
         return None
     if rec.get("kernel_source_sha256") != digest or int(rec.get("variant", -1)) != variant or \
@@ -88,15 +97,32 @@ def recorded_traffic(workload: str, variant: int, persistent: int):
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=2000)
-    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--steps", type=int, default=None, help="timed steps (default: per workload)")
+    p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=sorted(WORKLOADS), default="grf64")
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default="clumpy4")
+    p.add_argument("--paper-tests", action="store_true",
+                   help="also run the paper's test problems as printed (Tests 1-3 with the energy equation, "
+                        "Test 2's angular-resolution study) and the ray-grouping ablation")
+    p.add_argument("--profile-case", choices=["sweep", "net", "hii", "clumpy", "thermal"], default=None,
+                   help="run one small case for a profiler (ncu) instead of the benchmark")
+    p.add_argument("--n", type=int, default=None, help="--profile-case: cells per axis")
+    p.add_argument("--nside", type=int, default=None, help="--profile-case sweep: N_side")
+    p.add_argument("--variant", type=int, default=0, help="--profile-case sweep: kernel variant (0: default)")
+    p.add_argument("--reps", type=int, default=3, help="--profile-case: repetitions")
+    p.add_argument("--train", action="store_true", help="--profile-case net: also time training steps")
+    p.add_argument("--myr", type=float, default=30.0, help="--profile-case thermal: evolve to this time")
     p.add_argument("--no-autotune", action="store_true", help="keep the default kernel variant")
     p.add_argument("--no-graph", action="store_true", help="plain launches instead of CUDA-graph replay")
     p.add_argument("--no-extra", action="store_true", help="skip the side measurements (128^3, 256^3, 48-grid batch, 128^3 ionization solve)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    return p.parse_args()
+    p.add_argument("--shard", action="store_true",
+                   help="strong scaling: one grid, its directions split over the ranks, the shares combined by "
+                        "the rank-ordered reduce-scatter inside the timed region")
+    a = p.parse_args()
+    if a.steps is None:
+        a.steps = WORKLOADS[a.workload].get("steps", 200)
+    return a
 
 
 # ---------------------------------------------------------------------------
@@ -187,16 +213,28 @@ class ClockSampler:
 # our arm
 # ---------------------------------------------------------------------------
 def make_case(wl_name: str, rank: int):
+    """The workload's seeded input (a different seed per rank: independent grids)."""
     from paper_1410_0763_gb300 import workloads as wl
     w = WORKLOADS[wl_name]
+    if w.get("kind") == "clumpy":
+        return wl.clumpy_sweep(w["n"], w["nside"], seed=w["seed"] + 1000 * rank, nbins=w["bins"])
     return wl.grf(w["n"], w["nside"], seed=w["seed"] + 1000 * rank, sigma=w["sigma"])
 
 
-def band_G():
+def case_bins(case) -> int:
+    return 1 if case.kappa.ndim == 3 else int(case.kappa.shape[0])
+
+
+def band_G(nbins: int = 1):
+    """Band integrals of the Gamma epilogue: the recombination band [nu0, nu0 + k T / h] for one bin;
+    for the blackbody bins of the clumpy workload, the integral over each bin."""
     from paper_1410_0763_gb300 import art
     from paper_1410_0763_gb300 import workloads as wl
     c = wl.chem_constants()
-    return art.art_band_integral(c["sigma0"], c["h"], c["nu0"], c["nu0"], c["nu0"] + c["dnu"])
+    if nbins == 1:
+        return [art.art_band_integral(c["sigma0"], c["h"], c["nu0"], c["nu0"], c["nu0"] + c["dnu"])]
+    _, _, edges = wl.blackbody_bins()
+    return [art.art_band_integral(c["sigma0"], c["h"], c["nu0"], edges[b], edges[b + 1]) for b in range(nbins)]
 
 
 def time_device(sw, J, Jin, gam, steps, flush, torch):
@@ -212,20 +250,21 @@ def time_device(sw, J, Jin, gam, steps, flush, torch):
     return [a.elapsed_time(b) for a, b in evs]
 
 
-def side_measure(wl_name, torch, dev, G, steps=5):
+def side_measure(wl_name, torch, dev, steps=5):
     from paper_1410_0763_gb300 import art
     c = make_case(wl_name, 0)
     k = torch.as_tensor(c.kappa, dtype=torch.float32, device=dev)
     s = torch.as_tensor(c.src, dtype=torch.float32, device=dev)
-    sw = art.ArtSweep(k.shape, c.nside)
+    sw = art.ArtSweep(c.shape, c.nside, case_bins(c))
     sw.set_fields(k, s)
-    sw.set_band([G])
-    J, Jin, gam = torch.empty_like(k), torch.empty_like(k), torch.empty_like(k)
+    sw.set_band(band_G(case_bins(c)))
+    J, Jin, gam = torch.empty_like(k), torch.empty_like(k), torch.empty(c.shape, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     for _ in range(2):
         sw.sweep(J, Jin, gam)
     ms = time_device(sw, J, Jin, gam, steps, flush, torch)
     seg = sw.stats.segments
+    assert sw.check() == art.ART_OK
     sw.close()
     t = statistics.median(ms)
     return {"workload": WORKLOADS[wl_name]["desc"], "ms_per_step": round(t, 4),
@@ -745,38 +784,105 @@ def ablation_measure(torch, dev, reps=3):
     return out
 
 
-def cpu_baseline(case, seg_per_sweep: int, budget_s: float = 12.0) -> dict:
+def cpu_baseline(case, seg_per_step: int, budget_s: float = 12.0) -> dict:
+    """The FP64 oracle on the host cores: as many full sweeps of the workload as fit in budget_s
+    when one takes less than that; else a bounded sample of directions (the oracle's cost is per
+    segment, so segments per second carry over to the whole step)."""
     import oracle
     oracle.build()
     nt = oracle.default_threads()
-    k = case.kappa.astype(np.float32).astype(np.float64)
-    s = case.src.astype(np.float32).astype(np.float64)
+    kap = case.kappa.astype(np.float32).astype(np.float64)
+    src = case.src.astype(np.float32).astype(np.float64)
+    k, s_ = (kap, src) if kap.ndim == 3 else (kap[0], src[0])
     nd = 12 * case.nside * case.nside
+    # directions per chunk so that one chunk takes about a second
     t0 = time.perf_counter()
-    segs = 0
-    sweeps = 0
+    oracle.sweep_range_count(k, s_, case.nside, 0, min(nd, nt), nthreads=nt)
+    per_dir = (time.perf_counter() - t0) / min(nd, nt)
+    chunk = int(max(1, min(nd, 1.0 / max(per_dir, 1e-9))))
+    t0 = time.perf_counter()
+    segs, d0 = 0, 0
     while True:
-        _, n = oracle.sweep_range_count(k, s, case.nside, 0, nd, nthreads=nt)
+        d1 = min(nd, d0 + chunk)
+        _, n = oracle.sweep_range_count(k, s_, case.nside, d0, d1, nthreads=nt)
         segs += n
-        sweeps += 1
+        d0 = d1 % nd
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    # one core: a bounded sample of directions (the oracle's cost is per segment)
-    d1 = max(1, nd // 16)
+    d1 = max(1, nd // 64)
     t1 = time.perf_counter()
     segs1 = 0
     while True:
-        _, n1 = oracle.sweep_range_count(k, s, case.nside, 0, d1, nthreads=1)
+        _, n1 = oracle.sweep_range_count(k, s_, case.nside, 0, d1, nthreads=1)
         segs1 += n1
         if time.perf_counter() - t1 > budget_s / 4:
             break
     dt1 = time.perf_counter() - t1
     return {"value": segs / dt, "unit": UNIT, "cores": nt, "kind": "oracle",
-            "sample": f"{sweeps} full FP64 oracle sweeps of the same workload ({segs} segments, {dt:.1f} s)",
+            "sample": f"bin 0 of the workload, {segs} segments in chunks of {chunk} of its {nd} directions "
+                      f"({dt:.1f} s, FP64 oracle, OpenMP over directions); one step is {seg_per_step} segments",
             "single_core": {"value": segs1 / dt1, "unit": UNIT, "cores": 1,
-                            "sample": f"directions 0-{d1 - 1} of the same workload repeated ({segs1} segments, "
-                                      f"{dt1:.1f} s)"}}
+                            "sample": f"directions 0-{d1 - 1} of bin 0 repeated ({segs1} segments, {dt1:.1f} s)"}}
+
+
+def run_shard(args, d: Dist):
+    """The workload's sweep with its directions split over the ranks (Sec. 3.2): each step is this
+    rank's share (its RING-index block, all bins) and the rank-ordered reduce-scatter + all-gather
+    that gives every rank J^in.  Strong scaling: the total work is fixed."""
+    import torch
+    from paper_1410_0763_gb300 import art
+    from paper_1410_0763_gb300 import build as libbuild
+    from paper_1410_0763_gb300 import dist as adist
+    dev = torch.device("cuda", d.local)
+    torch.cuda.set_device(dev)
+    if d.rank == 0:
+        libbuild.build()
+    d.barrier()
+    art.load()
+    case = make_case(args.workload, 0)          # the same grid on every rank
+    nb = case_bins(case)
+    k = torch.as_tensor(case.kappa, dtype=torch.float32, device=dev)
+    s = torch.as_tensor(case.src, dtype=torch.float32, device=dev)
+    sh = adist.ShardedSweep(case.shape, case.nside, nb, group=None)
+    sh.set_fields(k, s)
+    seg_total = int(art.art_count_segments(case.shape, case.nside)) * nb
+    part = torch.empty_like(k)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        jin = sh.jin(sh.share(part))
+    torch.cuda.synchronize()
+    if sh.check() != art.ART_OK:
+        raise RuntimeError("sweep reported an error")
+    clocks = ClockSampler(d.local)
+    clocks.start()
+    d.barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in evs:
+        flush.zero_()
+        a.record(stream)
+        jin = sh.jin(sh.share(part))
+        b.record(stream)
+    torch.cuda.synchronize()
+    d.barrier()
+    ck = clocks.stop()
+    total_ms = d.max(sum(a.elapsed_time(b) for a, b in evs), dev)
+    sh.close()
+    out = {
+        "metric": METRIC, "value": seg_total * args.steps / (total_ms * 1e-3), "unit": UNIT, "n_gpus": d.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload]["desc"], "n": int(case.shape[0]), "nside": case.nside,
+                   "bins": nb, "segments_per_step": seg_total,
+                   "parallelism": f"directions split over {d.world} ranks; rank-ordered reduce-scatter "
+                                  f"(point-to-point) + all-gather of J^in"},
+        "clocks": ck,
+        "gpu_launches": int(args.steps * 3 * nb),
+    }
+    if d.rank == 0:
+        print(json.dumps(out), flush=True)
 
 
 def run_ours(args, d: Dist):
@@ -791,17 +897,20 @@ def run_ours(args, d: Dist):
     d.barrier()
     art.load()
     case = make_case(args.workload, d.rank)
-    G = band_G()
+    nb = case_bins(case)
     k = torch.as_tensor(case.kappa, dtype=torch.float32, device=dev)
     s = torch.as_tensor(case.src, dtype=torch.float32, device=dev)
-    sw = art.ArtSweep(k.shape, case.nside, graph=not args.no_graph)
+    sw = art.ArtSweep(case.shape, case.nside, nb, graph=not args.no_graph)
     sw.set_fields(k, s)
-    sw.set_band([G])
+    sw.set_band(band_G(nb))
+    t0 = time.perf_counter()
     if not args.no_autotune:
-        sw.autotune(3)          # untimed: the library's own variant / launch-form choice
+        sw.autotune(1)          # untimed: the library's own variant / launch-form choice
+    tune_s = time.perf_counter() - t0
     st = sw.stats
-    seg = int(st.segments)
-    J, Jin, gam = torch.empty_like(k), torch.empty_like(k), torch.empty_like(k)
+    seg = int(st.segments)       # all bins
+    J, Jin = torch.empty_like(k), torch.empty_like(k)
+    gam = torch.empty(case.shape, dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     clocks = ClockSampler(d.local)
@@ -809,17 +918,22 @@ def run_ours(args, d: Dist):
     for _ in range(args.warmup):
         sw.sweep(J, Jin, gam)
     torch.cuda.synchronize()
+    if sw.check() != art.ART_OK:
+        raise RuntimeError("sweep reported an error: " + art.art_last_error(sw._ctx))
     d.barrier()
     torch.cuda.synchronize()
     ms = time_device(sw, J, Jin, gam, args.steps, flush, torch)
     torch.cuda.synchronize()
     d.barrier()
     ck = clocks.stop()
+    if sw.check() != art.ART_OK:
+        raise RuntimeError("sweep reported an error: " + art.art_last_error(sw._ctx))
     total_ms = d.max(sum(ms), dev)
     value = seg * d.world * args.steps / (total_ms * 1e-3)
 
-    # kernel-level roofline: same steps with per-kernel events inside the library
-    prof_steps = min(args.steps, 200)
+    # kernel-level roofline: the same steps with per-kernel events inside the library
+    # (events around each bin's sweep launch and around its reduction)
+    prof_steps = min(args.steps, 50)
     sw.profile(True)
     time_device(sw, J, Jin, gam, prof_steps, flush, torch)
     sw.profile(False)
@@ -842,6 +956,8 @@ def run_ours(args, d: Dist):
     peak_fp32 = ffma / FP32_OPS_PER_SEG * n_sm * sm_mhz * 1e6 / 1e9
     peak_gseg = min(peak_mufu, peak_fp32)
     sweep_share = pr.sweep_ms / max(pr.sweep_ms + pr.reduce_ms, 1e-9)
+    wave = st.variant >= 16
+    kname = "wave_kernel" if wave else ("sweep_queue_kernel" if st.persistent else "sweep_block_kernel")
 
     # end to end through the C ABI with host buffers (pinned): every step copies its kappa and
     # S in and its J out.  art_sweep_stream overlaps those copies with the neighbouring steps'
@@ -849,8 +965,8 @@ def run_ours(args, d: Dist):
     kh = torch.as_tensor(case.kappa.astype(np.float32)).pin_memory()
     sh = torch.as_tensor(case.src.astype(np.float32)).pin_memory()
     Jh = [torch.empty(k.shape, dtype=torch.float32).pin_memory() for _ in range(2)]
-    e2e_steps = max(3, min(args.steps, 200))
-    sw.sweep_stream([kh] * 3, [sh] * 3, J=[Jh[i % 2] for i in range(3)])
+    e2e_steps = max(3, min(args.steps, 50))
+    sw.sweep_stream([kh] * 2, [sh] * 2, J=[Jh[i % 2] for i in range(2)])
     torch.cuda.synchronize()
     d.barrier()
     t0 = time.perf_counter()
@@ -860,27 +976,27 @@ def run_ours(args, d: Dist):
     e2e = {"value": seg * d.world * e2e_steps / dt, "unit": UNIT,
            "h2d_bytes_per_step": int(2 * kh.numel() * 4), "d2h_bytes_per_step": int(Jh[0].numel() * 4),
            "api": "art_sweep_stream (copies overlap the neighbouring steps' sweeps)"}
-    for _ in range(3):
-        sw.set_fields(kh, sh)
-        sw.sweep(Jh[0])
+    pc_steps = max(2, min(e2e_steps, 10))
+    sw.set_fields(kh, sh)
+    sw.sweep(Jh[0])
     torch.cuda.synchronize()
     d.barrier()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    for _ in range(pc_steps):
         sw.set_fields(kh, sh)
         sw.sweep(Jh[0])
     torch.cuda.synchronize()
     dt = d.max(time.perf_counter() - t0, dev)
-    e2e["per_call"] = {"value": seg * d.world * e2e_steps / dt, "unit": UNIT,
+    e2e["per_call"] = {"value": seg * d.world * pc_steps / dt, "unit": UNIT,
                        "api": "art_set_fields + art_sweep per step (each returns synchronized)"}
     sw.close()
 
     extra = {}
     if d.rank == 0 and d.world == 1 and not args.no_extra:
-        for name in ("grf128", "grf256"):
+        for name in ("grf64", "grf128", "grf256"):
             if name != args.workload:
                 try:
-                    extra[name] = side_measure(name, torch, dev, G)
+                    extra[name] = side_measure(name, torch, dev)
                 except Exception as ex:  # pragma: no cover
                     extra[name] = {"error": str(ex)}
         try:
@@ -891,21 +1007,22 @@ def run_ours(args, d: Dist):
             extra["rt_ionization_128"], extra["rt_ionization_256_clumpy"] = ionization_measure(torch, dev)
         except Exception as ex:  # pragma: no cover
             extra["rt_ionization_128"] = {"error": str(ex)}
-        try:
-            extra["rt_ionization_128_plane_flux"] = shadow_measure(torch, dev)
-        except Exception as ex:  # pragma: no cover
-            extra["rt_ionization_128_plane_flux"] = {"error": str(ex)}
-        for key, fn in (("time_dependent_64", evolve_measure), ("time_dependent_thermal_64", thermal_measure),
-                        ("test3_thermal_64", test3_thermal_measure), ("test2_thermal_64", test2_thermal_measure),
-                        ("test2_angular_resolution_64", test2_resolution_measure)):
+        if args.paper_tests:
             try:
-                extra[key] = fn(torch, dev)
+                extra["rt_ionization_128_plane_flux"] = shadow_measure(torch, dev)
             except Exception as ex:  # pragma: no cover
-                extra[key] = {"error": str(ex)}
-        try:
-            extra["ablation_ray_grouping"] = ablation_measure(torch, dev)
-        except Exception as ex:  # pragma: no cover
-            extra["ablation_ray_grouping"] = {"error": str(ex)}
+                extra["rt_ionization_128_plane_flux"] = {"error": str(ex)}
+            for key, fn in (("time_dependent_64", evolve_measure), ("time_dependent_thermal_64", thermal_measure),
+                            ("test3_thermal_64", test3_thermal_measure), ("test2_thermal_64", test2_thermal_measure),
+                            ("test2_angular_resolution_64", test2_resolution_measure)):
+                try:
+                    extra[key] = fn(torch, dev)
+                except Exception as ex:  # pragma: no cover
+                    extra[key] = {"error": str(ex)}
+            try:
+                extra["ablation_ray_grouping"] = ablation_measure(torch, dev)
+            except Exception as ex:  # pragma: no cover
+                extra["ablation_ray_grouping"] = {"error": str(ex)}
 
     cpu = None
     if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
@@ -916,17 +1033,20 @@ def run_ours(args, d: Dist):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload]["desc"], "n": int(case.shape[0]),
-                   "nside": case.nside, "bins": 1, "segments_per_step": seg,
-                   "kernel": f"slab-block sweep, tile {st.tile_b}x{st.tile_c}, slab {st.slab}, "
-                             f"dir groups {st.dir_split}, {st.ctas_per_launch} CTAs x {st.launches - 1} launches",
-                   "l2": "flushed between timed steps (256 MiB write)",
+                   "nside": case.nside, "bins": nb, "segments_per_step": seg,
+                   "kernel": (f"wavefront sweep, CTA tile {st.tile_b}x{st.tile_c} columns, "
+                              f"{st.group} direction slots, {st.ctas_per_launch} units, one launch per bin"
+                              if wave else
+                              f"slab-block sweep, tile {st.tile_b}x{st.tile_c}, slab {st.slab}, "
+                              f"dir groups {st.dir_split}, {st.ctas_per_launch} CTAs x {st.launches - 1} launches"),
+                   "variant": int(st.variant), "autotune_s": round(tune_s, 2),
+                   "l2": "inputs larger than L2; L2 also flushed between timed steps (256 MiB write)",
                    "parallelism": f"weak x{d.world} (independent grid per GPU)"},
         "roofline": {"bound": "alu", "achieved": achieved_gseg, "peak": peak_gseg, "unit": "Gseg/s",
                      "frac": achieved_gseg / peak_gseg,
                      "traffic": recorded_traffic(args.workload, int(st.variant), int(st.persistent)),
-                     "traffic_unit": "DRAM bytes per sweep launch (ncu, cold L2)",
-                     "kernel": ("sweep_queue_kernel" if st.persistent else "sweep_block_kernel") +
-                               f" variant {st.variant} (tile {st.tile_b}x{st.tile_c}, slab {st.slab})",
+                     "traffic_unit": "DRAM bytes per sweep launch (ncu)",
+                     "kernel": f"{kname} variant {st.variant} (tile {st.tile_b}x{st.tile_c})",
                      "kernel_share_of_step": sweep_share,
                      "peak_basis": f"binding roof = min(FP32: {ffma}/clk/SM (measured FMAs, scalar or packed FP32x2) / "
                                    f"{FP32_OPS_PER_SEG} ops per segment = {peak_fp32:.0f} Gseg/s, "
@@ -935,7 +1055,7 @@ def run_ours(args, d: Dist):
                      "peak_fp32_gseg": peak_fp32, "peak_mufu_gseg": peak_mufu,
                      "pipes_per_clk_sm": pipes},
         "e2e": e2e,
-        "gpu_launches": int(args.steps * st.launches),
+        "gpu_launches": int(args.steps * st.launches * nb),
         "clocks": ck,
         "cpu_baseline": cpu,
     }
@@ -954,25 +1074,29 @@ def run_reference(args, d: Dist):
     import oracle
     oracle.build()
     case = make_case(args.workload, 0)
+    nb = case_bins(case)
     nt = oracle.default_threads()
-    k = case.kappa.astype(np.float32).astype(np.float64)
-    s = case.src.astype(np.float32).astype(np.float64)
+    kap = case.kappa.astype(np.float32).astype(np.float64)
+    src = case.src.astype(np.float32).astype(np.float64)
     nd = 12 * case.nside * case.nside
-    # each step: a block of directions sized so that warmup + steps fit in ~3 minutes
-    _, n1 = oracle.sweep_range_count(k, s, case.nside, 0, 1, nthreads=1)
+    # each step: a block of directions of one bin (bins in turn), sized so that warmup + steps
+    # fit in about 2.5 minutes; the oracle's cost is per segment
+    k0, s0 = (kap, src) if nb == 1 else (kap[0], src[0])
     t0 = time.perf_counter()
-    oracle.sweep_range_count(k, s, case.nside, 0, min(nd, nt), nthreads=nt)
+    oracle.sweep_range_count(k0, s0, case.nside, 0, min(nd, nt), nthreads=nt)
     per_dir = (time.perf_counter() - t0) / min(nd, nt)
     budget = 150.0 / max(args.steps + args.warmup, 1)
     ndir = int(max(1, min(nd, budget / max(per_dir, 1e-9))))
     pos = 0
     segs, tsum = 0, 0.0
     for i in range(args.warmup + args.steps):
+        b = i % nb
+        kb, sb = (kap, src) if nb == 1 else (kap[b], src[b])
         d0 = pos % nd
         d1 = min(nd, d0 + ndir)
         pos = d1
         t0 = time.perf_counter()
-        _, n = oracle.sweep_range_count(k, s, case.nside, d0, d1, nthreads=nt)
+        _, n = oracle.sweep_range_count(kb, sb, case.nside, d0, d1, nthreads=nt)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             segs += n
@@ -984,17 +1108,139 @@ def run_reference(args, d: Dist):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload]["desc"], "n": int(case.shape[0]),
-                   "nside": case.nside, "bins": 1},
+                   "nside": case.nside, "bins": nb},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle",
-                         "sample": f"each step: {ndir} of {nd} directions of the workload (FP64 oracle)"},
+                         "sample": f"each step: {ndir} of the {nd} directions of one bin of the workload "
+                                   f"(bins in turn; FP64 oracle)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# small cases for a profiler (ncu): one JSON line each, no benchmark line
+# ---------------------------------------------------------------------------
+def profile_case(args):
+    import torch
+    from paper_1410_0763_gb300 import art
+    from paper_1410_0763_gb300 import build as libbuild
+    from paper_1410_0763_gb300 import workloads as wl
+    libbuild.build()
+    art.load()
+    out = {"profile_case": args.profile_case}
+    if args.profile_case == "sweep":
+        # a few sweeps of one workload: the GRF recipe at n^3 and N_side (one bin), or with
+        # --workload given explicitly, that benchmark workload (all its bins); the kernel variant given
+        if "--workload" in sys.argv:
+            c = make_case(args.workload, 0)
+            n, nside, nb = c.shape[0], c.nside, case_bins(c)
+        else:
+            n, nside, nb = args.n or 128, args.nside or 8, 1
+            c = wl.grf(n, nside, seed=3)
+        k = torch.as_tensor(c.kappa.astype(np.float32), device="cuda")
+        s = torch.as_tensor(c.src.astype(np.float32), device="cuda")
+        sw = art.ArtSweep(c.shape, nside, nb, variant=args.variant)
+        sw.set_fields(k, s)
+        Jin = torch.empty_like(k)
+        for _ in range(args.reps):
+            sw.sweep(None, Jin)
+        torch.cuda.synchronize()
+        if sw.check() != art.ART_OK:
+            raise RuntimeError("sweep reported an error")
+        st = sw.stats
+        out.update(n=n, nside=nside, variant=int(st.variant), units=int(st.ctas_per_launch),
+                   segments=int(st.segments))
+        sw.close()
+    elif args.profile_case == "net":
+        # the surrogate network on one grid: forward passes (and training steps)
+        n = args.n or 128
+        V = n ** 3
+        g = torch.Generator(device="cuda").manual_seed(0)
+        X = torch.randn(4 * V, device="cuda", generator=g)
+        t = torch.randn(V, device="cuda", generator=g)
+        o = torch.empty(V, device="cuda")
+        net = art.ArtNet()
+        shape = (n, n, n)
+        for _ in range(3):
+            net.forward(X, o, shape)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.reps):
+            net.forward(X, o, shape)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.reps
+        flops = 2.0 * 27 * V * (4 * 32 + 32 * 32 * 2 + 32 * 1)
+        out.update(n=n, forward_ms=round(ms, 4), forward_tflops_algorithmic=round(flops / ms / 1e9, 1))
+        if args.train:
+            for _ in range(2):
+                net.train_step(X, t, shape, want_loss=False)
+            e0.record()
+            for _ in range(args.reps):
+                net.train_step(X, t, shape, want_loss=False)
+            e1.record()
+            torch.cuda.synchronize()
+            out["train_step_ms"] = round(e0.elapsed_time(e1) / args.reps, 4)
+        net.close()
+    elif args.profile_case in ("hii", "clumpy"):
+        # point-source rates and RT / ionization-balance iterations
+        case = wl.hii_region() if args.profile_case == "hii" else wl.clumpy()
+        srcs = [(p[0], p[1], p[2], q) for p, q in zip(case.pos, case.Q)]
+        sw = art.ArtSweep(case.nH.shape, case.nside, 1, field_form=art.ART_FIELDS_EPS, dx_cm=case.chem["dx"])
+        if args.profile_case == "clumpy":
+            frac, sig, _ = wl.blackbody_bins()
+            sw.set_source_spectrum(sig, frac)
+        V = case.n ** 3
+        kap = torch.as_tensor((case.y0 * case.nH * case.chem["sigma0"] * case.chem["dx"]).ravel(),
+                              dtype=torch.float32, device="cuda")
+        g = torch.empty(V, device="cuda")
+        for _ in range(2):
+            sw.point_sources(kap, [case.chem["sigma0"]], srcs, g)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.reps):
+            sw.point_sources(kap, [case.chem["sigma0"]], srcs, g)
+        torch.cuda.synchronize()
+        t_pt = (time.perf_counter() - t0) / args.reps
+        nH = torch.as_tensor(case.nH, dtype=torch.float64, device="cuda")
+        y = torch.as_tensor(case.y0, dtype=torch.float64, device="cuda").clone()
+        t0 = time.perf_counter()
+        try:
+            sw.iterate(nH, case.chem, srcs, y, tol=1e-300, max_iter=args.reps)
+        except art.ArtError as ex:
+            if ex.status != art.ART_E_NOT_CONVERGED:
+                raise
+        torch.cuda.synchronize()
+        t_it = (time.perf_counter() - t0) / args.reps
+        sw.close()
+        out.update(n=case.n, sources=len(srcs), point_sources_ms_one_bin=round(1e3 * t_pt, 3),
+                   iteration_ms=round(1e3 * t_it, 3))
+    else:
+        # the time-dependent mode with the energy equation on the Test-1 setup (64^3, N_side 4,
+        # T0 100 K, a 1e5 K blackbody source in 4 bins) to args.myr
+        case = wl.hii_region(n=64, nside=4, box_kpc=6.6, nH=1e-3, Q=5e48, source_at="corner")
+        frac, sig, _ = wl.blackbody_bins()
+        srcs = [(p[0], p[1], p[2], q) for p, q in zip(case.pos, case.Q)]
+        sw = art.ArtSweep(case.nH.shape, case.nside, 1, field_form=art.ART_FIELDS_EPS, dx_cm=case.chem["dx"])
+        sw.set_source_spectrum(sig, frac)
+        th = {"e_bin": list(wl.blackbody_heat()), "e_diff": wl.diffuse_band_heat(case.chem)}
+        nH = torch.as_tensor(case.nH, dtype=torch.float64, device="cuda")
+        y = torch.as_tensor(case.y0, dtype=torch.float64, device="cuda").clone()
+        T = torch.full_like(y, 100.0)
+        rep = sw.evolve_thermal(nH, case.chem, th, srcs, y, T, args.myr * wl.MYR, F=1.0)
+        sw.close()
+        out.update(n=case.n, myr=args.myr, steps=int(rep.steps), iterations=int(rep.iterations),
+                   sweeps=int(rep.sweeps), seconds=round(float(rep.seconds), 4),
+                   ms_per_iteration=round(1e3 * float(rep.seconds) / max(int(rep.iterations), 1), 3))
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        profile_case(args)
+        return
     if args.impl == "reference":
         d = Dist("gloo")
         try:
@@ -1004,7 +1250,7 @@ def main():
         return
     d = Dist("nccl")
     try:
-        run_ours(args, d)
+        (run_shard if args.shard else run_ours)(args, d)
     finally:
         d.close()
 

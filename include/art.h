@@ -610,11 +610,16 @@ art_status art_measure_pipes(double *ex2_per_clk_sm, double *rcp_per_clk_sm,
  * the grid's tables must fit the 12 MiB; otherwise ART_E_INVALID and a message
  * in errbuf (if errbuf != NULL, errlen bytes).  Inputs are not validated.
  *
- * The first call on each device looks up the device address of the scratch
- * array (cudaGetSymbolAddress); make that first call before any stream
- * capture.  The call copies its tables with cudaMemcpyAsync and synchronizes
- * `stream` once before launching its kernels on it; it returns without waiting
- * for them.  Every call uses the same scratch array and the array keeps the
+ * The library's device code is loaded lazily: the first call on each device
+ * loads the module that holds the scratch array (looking up its address with
+ * cudaGetSymbolAddress), and only then are its 12 MiB reserved.  A caller that
+ * reserves the device's memory for itself should therefore make a first call
+ * (a 1 x 1 x 1 grid will do) before it does; a load that runs out of memory
+ * returns ART_E_OOM.  The call copies its tables with cudaMemcpyAsync and
+ * synchronizes `stream` once before launching its kernels on it (it returns
+ * without waiting for them), so it must never be called on a stream that is
+ * being captured: it checks, and returns ART_E_INVALID before queuing anything,
+ * leaving the capture valid.  Every call uses the same scratch array and the array keeps the
  * last call's contents (nothing is carried over: each call writes every
  * element it reads), so calls that overlap on the GPU -- from several threads
  * or streams -- race and must be serialized by the caller.

@@ -281,7 +281,7 @@ std::vector<SegEntry<real>> pack_segs(const std::vector<SlabGeom> &geo, const st
             e.ds1 = real(g.ds[0]);
             e.ds2 = real(g.ds[1]);
             e.ds3 = real(g.ds[2]);
-            e.code = (g.nseg - 1) | (g.cfirst << 2) | (g.shb << 3) | (g.shc << 4) | (rb << 5) | (rc << 9);
+            e.code = slab_code(g, rb, rc);
         }
         base += n;
     }

@@ -15,9 +15,14 @@ static const double kPi = 3.14159265358979323846;
 // Sec. 4: equal-area, iso-latitude pixels).
 void healpix_directions(int nside, std::vector<double> &xyz)
 {
+    xyz.assign(36u * nside * nside, 0.0);
+    healpix_directions_into(nside, xyz.data());
+}
+
+void healpix_directions_into(int nside, double *xyz)
+{
     const int N = nside;
-    xyz.clear();
-    xyz.reserve(36u * N * N);
+    long long p = 0;
     for (int r = 1; r <= 4 * N - 1; ++r) {
         double z, dphi, off;
         int count;
@@ -39,11 +44,11 @@ void healpix_directions(int nside, std::vector<double> &xyz)
             off = 0.5;
         }
         const double st = std::sqrt((1.0 - z) * (1.0 + z));
-        for (int j = 1; j <= count; ++j) {
+        for (int j = 1; j <= count; ++j, ++p) {
             const double ph = dphi * (j - off);
-            xyz.push_back(st * std::cos(ph));
-            xyz.push_back(st * std::sin(ph));
-            xyz.push_back(z);
+            xyz[3 * p] = st * std::cos(ph);
+            xyz[3 * p + 1] = st * std::sin(ph);
+            xyz[3 * p + 2] = z;
         }
     }
 }
@@ -88,6 +93,11 @@ static double snap(double u)
 void slab_geometry(const Frame &f, int Na, std::vector<SlabGeom> &out)
 {
     out.resize(Na);
+    slab_geometry_into(f, Na, out.data());
+}
+
+void slab_geometry_into(const Frame &f, int Na, SlabGeom *out)
+{
     for (int m = 0; m < Na; ++m) {
         SlabGeom g{};
         const double fb0 = std::floor(0.5 + f.qb * m), fb1 = std::floor(0.5 + f.qb * (m + 1));

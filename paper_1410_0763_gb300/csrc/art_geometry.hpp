@@ -37,6 +37,8 @@ struct SlabGeom {
 
 // HEALPix RING pixel centres, 12 nside^2 unit vectors (x, y, z), RING order.
 void healpix_directions(int nside, std::vector<double> &xyz);
+// The same into a caller array of 36 nside^2 doubles (no allocation).
+void healpix_directions_into(int nside, double *xyz);
 
 // Frame of direction n; a = the lowest axis whose |n_i| is within tie_tol
 // (relative) of the largest component.
@@ -44,5 +46,15 @@ Frame frame_of(const double n[3], double tie_tol);
 
 // Segments of every slab 0 <= m < Na of a direction in its canonical frame.
 void slab_geometry(const Frame &f, int Na, std::vector<SlabGeom> &out);
+// The same into a caller array of Na entries (no allocation).
+void slab_geometry_into(const Frame &f, int Na, SlabGeom *out);
+
+// Code word of a slab-block segment-table entry: bits 0-1 nseg - 1, 2 the
+// c-plane first, 3 b-shift, 4 c-shift, 5-8 and 9-12 the b- and c-shifts from
+// this slab to the end of its slab block (rb, rc; this slab included).
+inline int slab_code(const SlabGeom &g, int rb, int rc)
+{
+    return (g.nseg - 1) | (g.cfirst << 2) | (g.shb << 3) | (g.shc << 4) | (rb << 5) | (rc << 9);
+}
 
 }  // namespace art

@@ -756,8 +756,11 @@ art_status iterate_impl(art_ctx *ctx, art_net *net, const art_chem *ch, const do
         balance_kernel<<<nb, nt, 0, st>>>(ba);
         ICK(ctx, cudaGetLastError());
         unsigned long long bits = 0;
+        int werr = 0;
         ICK(ctx, cudaMemcpyAsync(&bits, B.resid, sizeof(bits), cudaMemcpyDeviceToHost, st));
+        if ((s = art_wave_status_async(ctx, &werr, st)) != ART_OK) return s;
         ICK(ctx, cudaStreamSynchronize(st));
+        if (werr && (s = art_wave_status(ctx, st)) != ART_OK) return s;
         std::memcpy(&r, &bits, sizeof(r));
         if (resid_hist) resid_hist[it - 1] = r;
         if (!phase1 && r < tol) {
@@ -1003,8 +1006,17 @@ art_status evolve_impl(art_ctx *ctx, const art_chem *ch, const double *nH, const
             chem_kernel<<<nb, nt, 0, st>>>(ca);
             ICK(ctx, cudaGetLastError());
             unsigned long long bits = 0;
+            int werr = 0;
             ICK(ctx, cudaMemcpyAsync(&bits, B.evo, sizeof(bits), cudaMemcpyDeviceToHost, st));
+            {
+                const art_status ws = art_wave_status_async(ctx, &werr, st);
+                if (ws != ART_OK) return ws;
+            }
             ICK(ctx, cudaStreamSynchronize(st));
+            if (werr) {
+                const art_status ws = art_wave_status(ctx, st);
+                if (ws != ART_OK) return ws;
+            }
             double r;
             std::memcpy(&r, &bits, sizeof(r));
             if (r < o->eps_iter) {
@@ -1357,8 +1369,17 @@ art_status evolve_thermal_impl(art_ctx *ctx, const art_chem *ch, const art_therm
             thermal_kernel<<<nb, nt, 0, st>>>(ta);
             ICK(ctx, cudaGetLastError());
             unsigned long long bits = 0;
+            int werr = 0;
             ICK(ctx, cudaMemcpyAsync(&bits, B.evo, sizeof(bits), cudaMemcpyDeviceToHost, st));
+            {
+                const art_status ws = art_wave_status_async(ctx, &werr, st);
+                if (ws != ART_OK) return ws;
+            }
             ICK(ctx, cudaStreamSynchronize(st));
+            if (werr) {
+                const art_status ws = art_wave_status(ctx, st);
+                if (ws != ART_OK) return ws;
+            }
             double r;
             std::memcpy(&r, &bits, sizeof(r));
             if (r < o->eps_iter) {

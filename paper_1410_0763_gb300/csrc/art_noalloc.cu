@@ -38,6 +38,7 @@ static double g_xyz[3 * kMaxDirs];
 static Frame g_frame[kMaxDirs];
 static int g_order[kMaxDirs];
 static SegEntry<float> g_segs[kMaxSlabs];
+static SlabGeom g_geo[kMaxDim];
 static DirDev g_dirs[kMaxDirs];
 static ClassDev g_classes[24];
 static WorkItem g_work[kMaxWork];
@@ -49,78 +50,6 @@ art_status reject(char *errbuf, size_t errlen, art_status st, const char *msg)
 {
     if (errbuf && errlen) std::snprintf(errbuf, errlen, "%s", msg);
     return st;
-}
-
-// HEALPix RING pixel centres written into a caller array (no allocation).
-void directions_into(int N, double *xyz)
-{
-    const double pi = 3.14159265358979323846;
-    int p = 0;
-    for (int r = 1; r <= 4 * N - 1; ++r) {
-        double z, dphi, off;
-        int count;
-        if (r < N) {
-            z = 1.0 - double(r) * r / (3.0 * N * N);
-            count = 4 * r;
-            dphi = pi / (2.0 * r);
-            off = 0.5;
-        } else if (r <= 3 * N) {
-            z = 2.0 * double(2 * N - r) / (3.0 * N);
-            count = 4 * N;
-            dphi = pi / (2.0 * N);
-            off = ((r - N + 1) & 1) ? 0.5 : 0.0;
-        } else {
-            const int rs = 4 * N - r;
-            z = -(1.0 - double(rs) * rs / (3.0 * N * N));
-            count = 4 * rs;
-            dphi = pi / (2.0 * rs);
-            off = 0.5;
-        }
-        const double st = std::sqrt((1.0 - z) * (1.0 + z));
-        for (int j = 1; j <= count; ++j, ++p) {
-            xyz[3 * p] = st * std::cos(dphi * (j - off));
-            xyz[3 * p + 1] = st * std::sin(dphi * (j - off));
-            xyz[3 * p + 2] = z;
-        }
-    }
-}
-
-// Segment table of one direction (same rules as the context path: crossings
-// from the integer parts of the column offset, ties within 1e-12 merged).
-void slabs_into(const Frame &f, int Na, SegEntry<float> *out)
-{
-    const double tie = 1e-12;
-    auto snap = [&](double u) { return u <= tie ? 0.0 : (u >= 1.0 - tie ? 1.0 : u); };
-    for (int m = 0; m < Na; ++m) {
-        const double fb0 = std::floor(0.5 + f.qb * m), fb1 = std::floor(0.5 + f.qb * (m + 1));
-        const double fc0 = std::floor(0.5 + f.qc * m), fc1 = std::floor(0.5 + f.qc * (m + 1));
-        const int shb = fb1 > fb0, shc = fc1 > fc0;
-        double ub = 2.0, uc = 2.0;
-        if (shb) ub = snap((fb1 - 0.5 - f.qb * m) / f.qb);
-        if (shc) uc = snap((fc1 - 0.5 - f.qc * m) / f.qc);
-        if (shb && shc && std::fabs(ub - uc) <= tie) uc = ub;
-        const double inv = 1.0 / f.na;
-        const int nseg = 1 + shb + shc;
-        double ds[3] = {0.0, 0.0, 0.0};
-        int cf = 0;
-        if (nseg == 1) {
-            ds[0] = inv;
-        } else if (nseg == 2) {
-            const double u = shb ? ub : uc;
-            ds[0] = u * inv;
-            ds[1] = (1.0 - u) * inv;
-        } else {
-            cf = uc < ub;
-            const double u1 = ub < uc ? ub : uc, u2 = ub < uc ? uc : ub;
-            ds[0] = u1 * inv;
-            ds[1] = (u2 - u1) * inv;
-            ds[2] = (1.0 - u2) * inv;
-        }
-        out[m].ds1 = float(ds[0]);
-        out[m].ds2 = float(ds[1]);
-        out[m].ds3 = float(ds[2]);
-        out[m].code = (nseg - 1) | (cf << 2) | (shb << 3) | (shc << 4);
-    }
 }
 
 }  // namespace
@@ -140,7 +69,21 @@ extern "C" art_status art_sweep_noalloc(const art_grid *grid, int n_side, const 
                       "(each axis <= 64 cells, <= 32768 cells, n_side <= 4); use art_create/art_sweep");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
+    // The call synchronizes the stream after copying its tables, which a stream
+    // capture does not allow: refuse before anything is queued, so that the
+    // caller's capture stays valid.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return reject(errbuf, errlen, ART_E_CUDA, "art_sweep_noalloc: cudaStreamIsCapturing failed");
+    }
+    if (cap != cudaStreamCaptureStatusNone)
+        return reject(errbuf, errlen, ART_E_INVALID,
+                      "art_sweep_noalloc: the stream is being captured; call it outside stream capture");
+
     // Device set-up, once per device: the device address of the scratch array.
+    // The device module holding the array is loaded here, on the first call
+    // (lazy loading), which is when its 12 MiB are reserved.
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return reject(errbuf, errlen, ART_E_CUDA, "art_sweep_noalloc: no usable current device");
@@ -149,7 +92,15 @@ extern "C" art_status art_sweep_noalloc(const art_grid *grid, int n_side, const 
         const cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
         if (e != cudaSuccess || !ptr) {
             cudaGetLastError();
-            return reject(errbuf, errlen, ART_E_CUDA, "art_sweep_noalloc: cudaGetSymbolAddress of the scratch array failed");
+            if (e == cudaErrorMemoryAllocation)
+                return reject(errbuf, errlen, ART_E_OOM,
+                              "art_sweep_noalloc: loading the library's device module (with its 12 MiB scratch "
+                              "array) ran out of device memory; make the first call on each device before "
+                              "reserving the device's memory");
+            char msg[256];
+            std::snprintf(msg, sizeof(msg), "art_sweep_noalloc: loading the device module / scratch address failed: %s",
+                          cudaGetErrorString(e));
+            return reject(errbuf, errlen, ART_E_CUDA, msg);
         }
         g_scratch_dev[dev] = ptr;
     }
@@ -157,7 +108,7 @@ extern "C" art_status art_sweep_noalloc(const art_grid *grid, int n_side, const 
 
     // Host tables: classes of directions, drift-sorted, with segment tables.
     const int nd = 12 * n_side * n_side;
-    directions_into(n_side, g_xyz);
+    healpix_directions_into(n_side, g_xyz);
     for (int d = 0; d < nd; ++d) g_frame[d] = frame_of(&g_xyz[3 * d], 1e-12);
     int ncls = 0, nslab = 0, nwork = 0, ndir = 0;
     long long plane_elems = 0;
@@ -204,15 +155,17 @@ extern "C" art_status art_sweep_noalloc(const art_grid *grid, int n_side, const 
             D.plane_off = plane_elems;
             D.na = g_frame[g_order[i]].na;
             g_dirs[ndir++] = D;
-            slabs_into(g_frame[g_order[i]], C.Na, g_segs + nslab);
-            // remaining column shifts to the end of each slab block (read by the kernel)
+            slab_geometry_into(g_frame[g_order[i]], C.Na, g_geo);
+            // entries with the remaining column shifts to the end of each slab block (read by the kernel)
             for (int m = C.Na - 1; m >= 0; --m) {
+                const SlabGeom &g = g_geo[m];
                 SegEntry<float> &e = g_segs[nslab + m];
                 const bool last = (m + 1) % kBLK == 0 || m + 1 == C.Na;
                 const int nxt = last ? 0 : g_segs[nslab + m + 1].code;
-                const int rb = ((e.code >> 3) & 1) + ((nxt >> 5) & 15);
-                const int rc = ((e.code >> 4) & 1) + ((nxt >> 9) & 15);
-                e.code = (e.code & 31) | (rb << 5) | (rc << 9);
+                e.ds1 = float(g.ds[0]);
+                e.ds2 = float(g.ds[1]);
+                e.ds3 = float(g.ds[2]);
+                e.code = slab_code(g, g.shb + ((nxt >> 5) & 15), g.shc + ((nxt >> 9) & 15));
             }
             nslab += C.Na;
             plane_elems += (long long)C.Nb * C.Nc;

@@ -62,11 +62,12 @@ struct WVariant {
 // direction slots of a unit (classes with more directions are split into
 // groups), min CTAs per SM.
 const WVariant kWave[] = {
-    ART_WV(2, 2, 16, 6),   // 16 x 16 columns; N_side 8 (26-37 directions per class: 2-3 groups)
-    ART_WV(2, 2, 12, 6),   // N_side 3-4 (3-11)
-    ART_WV(2, 2, 4, 6),    // N_side 1-2 (1-4)
+    ART_WV(2, 2, 16, 6),   // 16 x 16 columns; N_side 8 (26-37 directions per class: 3 groups)
+    ART_WV(2, 2, 12, 8),   // N_side 3-4 (3-11 directions per class)
+    ART_WV(2, 2, 4, 8),    // N_side 1-2 (1-4)
     ART_WV(2, 4, 16, 3),   // 16 x 32 columns
     ART_WV(4, 2, 16, 3),   // 32 x 16 columns
+    ART_WV(2, 4, 12, 4),   // 16 x 32 columns, 12 slots (more CTAs per SM)
 };
 #undef ART_WV
 const int kNumWave = int(sizeof(kWave) / sizeof(kWave[0]));

@@ -37,9 +37,11 @@
 //    Every wait is bounded in time; one that runs out sets an error word,
 //    after which every CTA leaves its loop at the next step.
 //  * Each unit writes the J partial of its (class, direction group) once per
-//    cell; reduce_kernel sums the partials in fixed order with Kahan.  Within a
-//    unit a cell's direction sum is Kahan-compensated every 8 directions.
+//    cell: the FP32 sum over its directions (at most 16, in table order).
+//    reduce_kernel sums the partials in fixed order with Kahan compensation.
 //    Results are deterministic.
+//  * The lane's two cells share every segment length and every branch, so the
+//    arithmetic of Eq. (rt) runs as packed FP32x2 instructions on both.
 //  * Arithmetic per (warp, slab), chosen by ballot over the warp's 64 cells:
 //    every kappa below KAP_THIN (series only), every kappa at or above
 //    KAP_THICK (hardware exponential only), else both with a per-segment
@@ -155,12 +157,12 @@ __device__ __forceinline__ void wv_cp_wait()
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// Poll a progress flag (relaxed loads) until it reaches `target` or the wait
-// runs out (or another CTA reported an error); a fence then makes it an
-// acquire.  Returns the value seen, or -1 if the wait ran out.
-__device__ __forceinline__ int wv_wait(const int *flag, int target, const WaveArgs &p)
+// Poll a progress flag (relaxed loads), starting from the value v read
+// earlier, until it reaches `target` or the wait runs out (or another CTA
+// reported an error); a fence then makes the read that saw it an acquire.
+// Returns the value seen, or -1 if the wait ran out.
+__device__ __forceinline__ int wv_wait(const int *flag, int target, int v, const WaveArgs &p)
 {
-    int v = wv_ld_relaxed(flag);
     if (v < target) {
         const long long t0 = wv_now();
         for (;;) {
@@ -188,47 +190,60 @@ __device__ __forceinline__ bool wv_ok(bool cond, int *err)
 #endif
 }
 
-// Cell values of one lane for the current slab.
-struct WvCell {
-    float kap;   // kappa per cell width (0 outside the box)
-    float E;     // kappa S (S inputs) or eps: emission per unit length
-    float S;     // source function (exponential path only; kappa > 0 there)
-    float k2;    // -kappa log2 e
-    float rk;    // 1/kappa (0 where kappa = 0)
+// Values of the lane's two cells (x: the first row, y: the second) for the
+// current slab.  The two cells see the same segment lengths, so each FP32
+// operation of Eq. (rt) runs on both at once as one packed FP32x2 instruction.
+struct WvCell2 {
+    float2 nkap;  // -kappa per cell width (0 outside the box)
+    float2 kap;   // kappa
+    float2 E;     // kappa S (S inputs) or eps: emission per unit length
+    float2 S;     // source function (exponential path only; kappa > 0 there)
+    float2 k2;    // -kappa log2 e
+    float2 rk;    // 1/kappa (0 where kappa = 0)
 };
 
-// One segment of length ds with incoming intensity I: accumulates the deposit
-// into A and returns the outgoing intensity.  Thin / mixed deposits are
-// ds phi(x); the thick path deposits 1 - e^-x (scaled by 1/kappa per cell).
+__device__ __forceinline__ float2 f2s(float v) { return make_float2(v, v); }
+
+// One segment of length ds with incoming intensities I (both cells):
+// accumulates the deposits into A and returns the outgoing intensities.
+// Thin / mixed deposits are ds phi(x); the thick path deposits 1 - e^-x
+// (scaled by 1/kappa per cell).
 template <int MODE, bool FIRST>
-__device__ __forceinline__ float wv_seg(const WvCell &c, float I, float ds, float &A)
+__device__ __forceinline__ float2 wv_seg(const WvCell2 &c, float2 I, float ds, float2 &A)
 {
+    const float2 dsv = f2s(ds);
     if (MODE == MODE_THICK) {
-        const float h = 1.0f - wv_ex2(c.k2 * ds);
-        A = FIRST ? I * h : fmaf(I, h, A);
-        return fmaf(c.S - I, h, I);
+        const float2 arg = __fmul2_rn(c.k2, dsv);
+        const float2 e = make_float2(wv_ex2(arg.x), wv_ex2(arg.y));
+        const float2 h = __ffma2_rn(e, f2s(-1.0f), f2s(1.0f));
+        A = FIRST ? __fmul2_rn(I, h) : __ffma2_rn(I, h, A);
+        // I_out = I + (S - I)(1 - e^-x)
+        return __ffma2_rn(__ffma2_rn(I, f2s(-1.0f), c.S), h, I);
     }
-    const float x = c.kap * ds;
-    float g;
+    const float2 x = __fmul2_rn(c.kap, dsv);
+    float2 g;
     if (MODE == MODE_THIN) {
-        float q = fmaf(x, 1.0f / 120.0f, -1.0f / 24.0f);
-        q = fmaf(x, q, 1.0f / 6.0f);
-        q = fmaf(x, q, -0.5f);
-        q = fmaf(x, q, 1.0f);
-        g = ds * q;
+        float2 q = __ffma2_rn(x, f2s(1.0f / 120.0f), f2s(-1.0f / 24.0f));
+        q = __ffma2_rn(x, q, f2s(1.0f / 6.0f));
+        q = __ffma2_rn(x, q, f2s(-0.5f));
+        q = __ffma2_rn(x, q, f2s(1.0f));
+        g = __fmul2_rn(dsv, q);
     } else {
-        float q = fmaf(x, -1.0f / 720.0f, 1.0f / 120.0f);
-        q = fmaf(x, q, -1.0f / 24.0f);
-        q = fmaf(x, q, 1.0f / 6.0f);
-        q = fmaf(x, q, -0.5f);
-        q = fmaf(x, q, 1.0f);
-        const float gs = ds * q;
-        const float gm = (1.0f - wv_ex2(c.k2 * ds)) * c.rk;
-        g = x < X_SERIES ? gs : gm;
+        float2 q = __ffma2_rn(x, f2s(-1.0f / 720.0f), f2s(1.0f / 120.0f));
+        q = __ffma2_rn(x, q, f2s(-1.0f / 24.0f));
+        q = __ffma2_rn(x, q, f2s(1.0f / 6.0f));
+        q = __ffma2_rn(x, q, f2s(-0.5f));
+        q = __ffma2_rn(x, q, f2s(1.0f));
+        const float2 gs = __fmul2_rn(dsv, q);
+        const float2 arg = __fmul2_rn(c.k2, dsv);
+        const float2 e = make_float2(wv_ex2(arg.x), wv_ex2(arg.y));
+        const float2 gm = __fmul2_rn(__ffma2_rn(e, f2s(-1.0f), f2s(1.0f)), c.rk);
+        g.x = x.x < X_SERIES ? gs.x : gm.x;
+        g.y = x.y < X_SERIES ? gs.y : gm.y;
     }
-    A = FIRST ? I * g : fmaf(I, g, A);
+    A = FIRST ? __fmul2_rn(I, g) : __ffma2_rn(I, g, A);
     // I_out = I + (S - I)(1 - e^-x) = I + (eps - kappa I) ds phi(x)
-    return fmaf(fmaf(-c.kap, I, c.E), g, I);
+    return __ffma2_rn(__ffma2_rn(c.nkap, I, c.E), g, I);
 }
 
 __device__ __forceinline__ void wv_sts(unsigned a, float v) { asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory"); }
@@ -261,91 +276,62 @@ struct WvXch {
 // Hand-off across a b-plane: each of the lane's rows takes the intensity that
 // leaves the column one step upstream along b (the lane to the left, or the
 // B-face input at bl = 0); lanes at bl = 7 write theirs to the B-face output.
-__device__ __forceinline__ void wv_xb(const WvXch &x, float &v0, float &v1, int d)
+__device__ __forceinline__ void wv_xb(const WvXch &x, float2 &v, int d)
 {
-    const float n0 = __shfl_up_sync(0xffffffffu, v0, 1);
-    const float n1 = __shfl_up_sync(0xffffffffu, v1, 1);
-    if (x.b7) wv_sts2(x.bo + 32 * d, v0, v1);
+    const float n0 = __shfl_up_sync(0xffffffffu, v.x, 1);
+    const float n1 = __shfl_up_sync(0xffffffffu, v.y, 1);
+    if (x.b7) wv_sts2(x.bo + 32 * d, v.x, v.y);
     const float2 in = wv_lds2(x.bi + 32 * d);
-    v0 = x.b0 ? in.x : n0;
-    v1 = x.b0 ? in.y : n1;
+    v.x = x.b0 ? in.x : n0;
+    v.y = x.b0 ? in.y : n1;
 }
 
 // Hand-off across a c-plane: the lane's second row takes its first row's
 // intensity; the first row takes the second row of the lane one step upstream
 // along c (or the C-face input at cl = 0); lanes at cl = 3 write their second
 // row to the C-face output.
-__device__ __forceinline__ void wv_xc(const WvXch &x, float &v0, float &v1, int d)
+__device__ __forceinline__ void wv_xc(const WvXch &x, float2 &v, int d)
 {
-    const float n = __shfl_up_sync(0xffffffffu, v1, 8);
-    if (x.c3) wv_sts(x.co + 32 * d, v1);
+    const float n = __shfl_up_sync(0xffffffffu, v.y, 8);
+    if (x.c3) wv_sts(x.co + 32 * d, v.y);
     const float in = wv_lds(x.ci + 32 * d);
-    v1 = v0;
-    v0 = x.c0 ? in : n;
+    v.y = v.x;
+    v.x = x.c0 ? in : n;
 }
 
 // All directions of the unit for one slab, for the lane's two cells: the ray
-// states (shared memory, pairs at rs + 8 NT d) are updated in place; the
-// cells' direction sums are returned in (js, jc) (Kahan every 8 directions).
+// states (shared memory, pairs at rs + 8 NT d) are updated in place; returns
+// the cells' sums over the unit's directions of |n_a| times the deposits
+// (at most 16 directions per unit, summed in FP32 in table order; the units'
+// partials are summed with Kahan compensation by the reduction).
 template <int MODE, int NT>
-__device__ __forceinline__ void wv_dirs(const WvCell &c0, const WvCell &c1, unsigned rs, unsigned tab, int nd,
-                                        const WvXch &x, float &js0, float &jc0, float &js1, float &jc1)
+__device__ __forceinline__ float2 wv_dirs(const WvCell2 &c, unsigned rs, unsigned tab, int nd, const WvXch &x)
 {
-    js0 = jc0 = js1 = jc1 = 0.0f;
-    float acc0 = 0.0f, acc1 = 0.0f;
-    float4 e;
-    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(e.x), "=f"(e.y), "=f"(e.z), "=f"(e.w) : "r"(tab));
-    float2 R = wv_lds2(rs);
+    float2 acc = f2s(0.0f);
 #pragma unroll 1
     for (int d = 0; d < nd; ++d) {
-        // next direction's table entry and ray states (the last iteration reloads its own)
-        const int dn = d + 1 < nd ? d + 1 : d;
-        float4 en;
+        float4 e;
         asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                     : "=f"(en.x), "=f"(en.y), "=f"(en.z), "=f"(en.w)
-                     : "r"(tab + 16 * dn));
-        const float2 Rn = wv_lds2(rs + 8 * NT * dn);
-        const unsigned f1 = __float_as_uint(e.x) >> 31;   // first hand-off along c
-        const unsigned f2 = __float_as_uint(e.y) >> 31;   // two or more segments
-        const unsigned f3 = __float_as_uint(e.z) >> 31;   // three segments
-        float A0, A1;
-        float o0 = wv_seg<MODE, true>(c0, R.x, fabsf(e.x), A0);
-        float o1 = wv_seg<MODE, true>(c1, R.y, fabsf(e.x), A1);
-        if (f2) {
-            if (f1) wv_xc(x, o0, o1, d);
-            else wv_xb(x, o0, o1, d);
-            o0 = wv_seg<MODE, false>(c0, o0, fabsf(e.y), A0);
-            o1 = wv_seg<MODE, false>(c1, o1, fabsf(e.y), A1);
-            if (f3) {
-                if (f1) wv_xb(x, o0, o1, d);
-                else wv_xc(x, o0, o1, d);
-                o0 = wv_seg<MODE, false>(c0, o0, fabsf(e.z), A0);
-                o1 = wv_seg<MODE, false>(c1, o1, fabsf(e.z), A1);
+                     : "=f"(e.x), "=f"(e.y), "=f"(e.z), "=f"(e.w)
+                     : "r"(tab + 16 * d));
+        const float2 R = wv_lds2(rs + 8 * NT * d);
+        float2 A;
+        float2 o = wv_seg<MODE, true>(c, R, fabsf(e.x), A);
+        if (__float_as_int(e.y) < 0) {            // two or more segments
+            const bool fc = __float_as_int(e.x) < 0;   // first hand-off along c
+            if (fc) wv_xc(x, o, d);
+            else wv_xb(x, o, d);
+            o = wv_seg<MODE, false>(c, o, fabsf(e.y), A);
+            if (__float_as_int(e.z) < 0) {        // three segments
+                if (fc) wv_xb(x, o, d);
+                else wv_xc(x, o, d);
+                o = wv_seg<MODE, false>(c, o, fabsf(e.z), A);
             }
         }
-        wv_sts2(rs + 8 * NT * d, o0, o1);
-        acc0 = fmaf(A0, e.w, acc0);
-        acc1 = fmaf(A1, e.w, acc1);
-        if ((d & 7) == 7) {
-            float y = acc0 - jc0, t = js0 + y;
-            jc0 = (t - js0) - y;
-            js0 = t;
-            y = acc1 - jc1;
-            t = js1 + y;
-            jc1 = (t - js1) - y;
-            js1 = t;
-            acc0 = acc1 = 0.0f;
-        }
-        e = en;
-        R = Rn;
+        wv_sts2(rs + 8 * NT * d, o.x, o.y);
+        acc = __ffma2_rn(A, f2s(e.w), acc);
     }
-    float y = acc0 - jc0, t = js0 + y;
-    jc0 = (t - js0) - y;
-    js0 = t;
-    y = acc1 - jc1;
-    t = js1 + y;
-    jc1 = (t - js1) - y;
-    js1 = t;
+    return acc;
 }
 
 template <int WB, int WC, int DMAX> struct WaveShape {
@@ -432,8 +418,11 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
     // every ray enters the box with the boundary intensity
     for (int d = 0; d < nd; ++d) RS[d * NT + tid] = make_float2(p.i_bc, p.i_bc);
 
-    // progress of the upstream warps last seen by this warp (uniform)
-    int seen_b = 0, seen_c = 0;
+    // progress of the upstream warps last seen by this warp (uniform), and the
+    // flag values lane 0 read in the previous step (used before polling again)
+    int seen_b = 0, seen_c = 0, pref_b = 0, pref_c = 0;
+    const int *up_flag_b = U.up_b >= 0 ? p.flags + (long long)U.up_b * (WB + WC) + wc : nullptr;
+    const int *up_flag_c = U.up_c >= 0 ? p.flags + (long long)U.up_c * (WB + WC) + WC + wb : nullptr;
 
     // Stage what step t + 1 reads: the table of slab t + 1, this lane's fields
     // of its next slab, and (warps on the CTA's upstream edges) the upstream
@@ -455,11 +444,13 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
             if (s >= 0 && s < Na) {
                 if (s + 1 > seen_b) {
                     int v = 0;
-                    if (lane == 0) v = wv_wait(p.flags + (long long)U.up_b * (WB + WC) + wc, s + 1, p);
+                    if (lane == 0) v = wv_wait(up_flag_b, s + 1, pref_b, p);
                     v = __shfl_sync(0xffffffffu, v, 0);
                     if (v < 0) ok = 0;
                     else seen_b = v;
                 }
+                // read ahead: the value is used by the next step that needs more than seen_b
+                if (lane == 0 && seen_b < Na) pref_b = wv_ld_relaxed(up_flag_b);
                 if (ok) {
                     const long long eb_up = s_up[0];
                     for (int dd = lane; dd < nd; dd += 32) {
@@ -479,11 +470,12 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
                 int okc = 1;
                 if (s + 1 > seen_c) {
                     int v = 0;
-                    if (lane == 0) v = wv_wait(p.flags + (long long)U.up_c * (WB + WC) + WC + wb, s + 1, p);
+                    if (lane == 0) v = wv_wait(up_flag_c, s + 1, pref_c, p);
                     v = __shfl_sync(0xffffffffu, v, 0);
                     if (v < 0) okc = 0;
                     else seen_c = v;
                 }
+                if (lane == 0 && seen_c < Na) pref_c = wv_ld_relaxed(up_flag_c);
                 if (okc) {
                     const long long ec_up = s_up[1];
                     for (int dd = lane; dd < nd; dd += 32) {
@@ -524,18 +516,14 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
         if (m >= 0 && m < Na) {
             const int par = t & 1;
             const float4 f = FS[par * NT + tid];
-            WvCell c0, c1;
-            c0.kap = in0 ? f.x : 0.0f;
-            c1.kap = in1 ? f.z : 0.0f;
-            const float src0 = in0 ? f.y : 0.0f, src1 = in1 ? f.w : 0.0f;
-            c0.rk = c0.kap > 0.0f ? wv_rcp(c0.kap) : 0.0f;
-            c1.rk = c1.kap > 0.0f ? wv_rcp(c1.kap) : 0.0f;
-            c0.E = p.field_form ? src0 : c0.kap * src0;
-            c1.E = p.field_form ? src1 : c1.kap * src1;
-            c0.S = p.field_form ? src0 * c0.rk : src0;
-            c1.S = p.field_form ? src1 * c1.rk : src1;
-            c0.k2 = -1.4426950408889634f * c0.kap;
-            c1.k2 = -1.4426950408889634f * c1.kap;
+            WvCell2 c;
+            c.kap = make_float2(in0 ? f.x : 0.0f, in1 ? f.z : 0.0f);
+            const float2 src = make_float2(in0 ? f.y : 0.0f, in1 ? f.w : 0.0f);
+            c.nkap = make_float2(-c.kap.x, -c.kap.y);
+            c.rk = make_float2(c.kap.x > 0.0f ? wv_rcp(c.kap.x) : 0.0f, c.kap.y > 0.0f ? wv_rcp(c.kap.y) : 0.0f);
+            c.E = p.field_form ? src : __fmul2_rn(c.kap, src);
+            c.S = p.field_form ? __fmul2_rn(src, c.rk) : src;
+            c.k2 = __fmul2_rn(c.kap, f2s(-1.4426950408889634f));
             WvXch x;
             x.bo = xb0 + 4 * (par * Sh::XB_PAR + ((wb + 1) * WC + wc) * DMAX * 8 + 2 * cl);
             x.bi = xb0 + 4 * ((par ^ 1) * Sh::XB_PAR + (wb * WC + wc) * DMAX * 8 + 2 * cl);
@@ -546,19 +534,18 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
             x.c0 = cl == 0;
             x.c3 = cl == 3;
             const unsigned tb = tab0 + 16 * (m & (RT - 1)) * DMAX;
-            const unsigned thin = __ballot_sync(0xffffffffu, c0.kap < KAP_THIN && c1.kap < KAP_THIN);
-            const unsigned thick = __ballot_sync(0xffffffffu, c0.kap >= KAP_THICK && c1.kap >= KAP_THICK);
-            float js0, jc0, js1, jc1;
+            const unsigned thin = __ballot_sync(0xffffffffu, c.kap.x < KAP_THIN && c.kap.y < KAP_THIN);
+            const unsigned thick = __ballot_sync(0xffffffffu, c.kap.x >= KAP_THICK && c.kap.y >= KAP_THICK);
+            float2 js;
             if (thin == 0xffffffffu)
-                wv_dirs<MODE_THIN, NT>(c0, c1, rs0, tb, nd, x, js0, jc0, js1, jc1);
+                js = wv_dirs<MODE_THIN, NT>(c, rs0, tb, nd, x);
             else if (thick == 0xffffffffu)
-                wv_dirs<MODE_THICK, NT>(c0, c1, rs0, tb, nd, x, js0, jc0, js1, jc1);
+                js = __fmul2_rn(wv_dirs<MODE_THICK, NT>(c, rs0, tb, nd, x), c.rk);
             else
-                wv_dirs<MODE_MIXED, NT>(c0, c1, rs0, tb, nd, x, js0, jc0, js1, jc1);
+                js = wv_dirs<MODE_MIXED, NT>(c, rs0, tb, nd, x);
             if (jl_ok) {
-                const bool thk = thick == 0xffffffffu;
-                if (in0) J0[m * jstep] = (js0 - jc0) * (thk ? c0.rk : 1.0f);
-                if (in1) J1[m * jstep] = (js1 - jc1) * (thk ? c1.rk : 1.0f);
+                if (in0) J0[m * jstep] = js.x;
+                if (in1) J1[m * jstep] = js.y;
             }
             // edge intensities of this slab to the downstream CTAs
             if ((b_out && U.eb >= 0) || (c_out && U.ec >= 0)) {

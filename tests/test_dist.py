@@ -1,7 +1,10 @@
-"""Direction-sharded sweep over ranks: the partition of the RING indices,
-the rank-order gather and the rank-order combination, run as world-size-2
-gloo process groups on CPU (each rank's share computed by the oracle, since
-this host has no GPU), against the unsharded oracle sweep."""
+"""Direction-sharded sweep over ranks: the partition of the RING indices and
+of the cells, the rank-ordered reduce-scatter (point-to-point exchange of cell
+blocks, rank-order Kahan sum of each block, all-gather of the summed blocks),
+run as world-size-2 and -3 gloo process groups on CPU (each rank's share
+computed by the oracle, since this host has no GPU; the block sum, which the
+library does on the GPU, is written here in numpy), against the unsharded
+oracle sweep."""
 import os
 
 import numpy as np
@@ -27,6 +30,26 @@ def test_direction_blocks_partition_the_sphere():
         adist.direction_block(1, 2, 2)
 
 
+def test_cell_blocks_partition_the_cells():
+    for n in (1, 7, 1000, 4096 * 3 + 1):
+        for world in (1, 2, 3, 8):
+            blocks = [adist.cell_block(n, r, world) for r in range(world)]
+            assert blocks[0][0] == 0 and blocks[-1][1] == n
+            assert all(blocks[i][1] == blocks[i + 1][0] for i in range(world - 1))
+
+
+def kahan_rows(parts: np.ndarray) -> np.ndarray:
+    """Rank-order Kahan sum of the rows (what art_sum_partials computes on the GPU)."""
+    s = np.zeros(parts.shape[1:], dtype=parts.dtype)
+    c = np.zeros_like(s)
+    for p in parts:
+        y = p - c
+        t = s + y
+        c = (t - s) - y
+        s = t
+    return s
+
+
 def _rank_main(rank, world, port, out_dir):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -38,8 +61,12 @@ def _rank_main(rank, world, port, out_dir):
     b, e = adist.direction_block(nside, rank, world)
     acc, _ = oracle.sweep_range(case.kappa, case.src, nside, b, e, nthreads=1)
     share = torch.as_tensor(acc / (12 * nside * nside))
-    parts = adist.gather_in_rank_order(share)
-    jin = adist.combine_in_rank_order(parts.numpy())
+    pieces = adist.exchange_blocks(share.reshape(-1))
+    n = share.numel()
+    b, e = adist.cell_block(n, rank, world)
+    assert pieces.shape == (world, e - b)
+    mine = torch.as_tensor(kahan_rows(pieces.numpy()))
+    jin = adist.gather_blocks(mine, n).reshape(share.shape).numpy()
     np.save(os.path.join(out_dir, f"jin_{rank}.npy"), jin)
     np.save(os.path.join(out_dir, f"share_{rank}.npy"), share.numpy())
     dist.destroy_process_group()
@@ -66,6 +93,6 @@ def test_gloo_ranks_reproduce_the_full_sweep(tmp_path, world):
     for r in range(1, world):
         assert np.array_equal(results[r], results[0])      # every rank holds the same combination
     assert np.allclose(results[0], want, rtol=1e-13, atol=0)
-    # the combination is the rank-order sum of the shares
+    # the combination is the rank-order Kahan sum of the shares, cell by cell
     shares = np.stack([np.load(tmp_path / f"share_{r}.npy") for r in range(world)])
-    assert np.allclose(results[0], shares.sum(axis=0), rtol=1e-14)
+    assert np.array_equal(results[0], kahan_rows(shares))

@@ -74,3 +74,43 @@ def test_shard_rejects_J_output():
         sw.sweep(J=torch.empty_like(k), J_in=torch.empty_like(k))
     assert e.value.status == art.ART_E_INVALID
     sw.close()
+
+
+def _one_rank_sharded(q):
+    import os
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    import socket
+    with socket.socket() as s_:
+        s_.bind(("127.0.0.1", 0))
+        os.environ["MASTER_PORT"] = str(s_.getsockname()[1])
+    dist.init_process_group("nccl", rank=0, world_size=1)
+    try:
+        build.build()
+        art.load()
+        c = wl.grf(24, 3, seed=11)
+        k = torch.as_tensor(c.kappa, dtype=torch.float32, device="cuda")
+        s = torch.as_tensor(c.src, dtype=torch.float32, device="cuda")
+        sh = adist.ShardedSweep(c.kappa.shape, 3, 1)
+        sh.set_fields(k, s)
+        jin = sh.jin(sh.share(torch.empty_like(k))).cpu().numpy()
+        jin2 = sh.jin(sh.share(torch.empty_like(k))).cpu().numpy()
+        sh.close()
+        full, _ = share(c.kappa, c.src, 3, None)
+        q.put((bool(np.array_equal(jin, full.cpu().numpy().reshape(jin.shape))), bool(np.array_equal(jin, jin2))))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_sweep_on_one_rank_equals_the_full_sweep():
+    """ShardedSweep (the multi-GPU path of bench.py --shard) on a one-rank NCCL group: the
+    context kept across calls, the exchange and the rank-order sum reduce to the full sweep,
+    bit for bit, call after call."""
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_one_rank_sharded, args=(q,))
+    p.start()
+    p.join(300)
+    assert p.exitcode == 0
+    assert q.get(timeout=5) == (True, True)
