@@ -423,7 +423,7 @@ art_status setup_wave(art_ctx *ctx, int w)
     if (s != ART_OK) return s;
     ctx->variant = kNumVariants + w;
     ctx->TB = 8 * ctx->wave.wb;
-    ctx->TC = 8 * ctx->wave.wc;
+    ctx->TC = 8 * ctx->wave.np * ctx->wave.wc;
     ctx->BLK = 0;
     ctx->KP = 0;
     ctx->split = 0;

@@ -50,7 +50,7 @@ struct art_sur_bufs {
 // Wavefront sweep (art_wave.cuh): tables and buffers of the selected shape.
 struct art_wave_state {
     bool on = false;
-    int variant = 0, wb = 0, wc = 0, dmax = 0, n_units = 0;
+    int variant = 0, wb = 0, wc = 0, dmax = 0, np = 1, n_units = 0;
     void *units = nullptr, *classes = nullptr, *segs = nullptr, *seg_off = nullptr;
     float *edge = nullptr;      // edge intensities handed between CTA tiles
     int *flags = nullptr;       // [0] error word, [1] ticket, then per-unit progress flags

@@ -26,19 +26,19 @@ namespace {
                             std::string(#call) + ": " + cudaGetErrorString(e_));                  \
     } while (0)
 
-template <int WB, int WC, int DMAX, int MINB>
+template <int WB, int WC, int DMAX, int NP, int MINB>
 cudaError_t wave_launch(const WaveArgs &a, int n_units, cudaStream_t st)
 {
-    using Sh = WaveShape<WB, WC, DMAX>;
-    wave_kernel<WB, WC, DMAX, MINB><<<(unsigned)n_units, Sh::NT, Sh::bytes, st>>>(a);
+    using Sh = WaveShape<WB, WC, DMAX, NP>;
+    wave_kernel<WB, WC, DMAX, NP, MINB><<<(unsigned)n_units, Sh::NT, Sh::bytes, st>>>(a);
     return cudaGetLastError();
 }
 
 // Shared-memory attribute; returns resident CTAs per SM (0 on error).
-template <int WB, int WC, int DMAX, int MINB> int wave_prepare()
+template <int WB, int WC, int DMAX, int NP, int MINB> int wave_prepare()
 {
-    using Sh = WaveShape<WB, WC, DMAX>;
-    auto kern = wave_kernel<WB, WC, DMAX, MINB>;
+    using Sh = WaveShape<WB, WC, DMAX, NP>;
+    auto kern = wave_kernel<WB, WC, DMAX, NP, MINB>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::bytes) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -52,23 +52,27 @@ template <int WB, int WC, int DMAX, int MINB> int wave_prepare()
 }
 
 struct WVariant {
-    int wb, wc, dmax, minb;
+    int wb, wc, dmax, np, minb;   // np: pairs of rows per lane (a warp tile is 8 x 8 np columns)
     cudaError_t (*launch)(const WaveArgs &, int, cudaStream_t);
     int (*prepare)();
 };
 
-#define ART_WV(wb, wc, dm, mb) {wb, wc, dm, mb, &wave_launch<wb, wc, dm, mb>, &wave_prepare<wb, wc, dm, mb>}
-// Compiled shapes: warps along b and c (a warp tile is 8 x 8 columns), the
-// direction slots of a unit (classes with more directions are split into
-// groups), min CTAs per SM.
+#define ART_WV(wb, wc, dm, np, mb) \
+    {wb, wc, dm, np, mb, &wave_launch<wb, wc, dm, np, mb>, &wave_prepare<wb, wc, dm, np, mb>}
+// Compiled shapes: warps along b and c, direction slots of a unit (classes
+// with more directions are split into groups), pairs of rows per lane (a warp
+// tile is 8 x 8 np columns), min CTAs per SM.
 const WVariant kWave[] = {
-    ART_WV(2, 2, 16, 6),   // 16 x 16 columns; N_side 8 (26-37 directions per class: 3 groups)
-    ART_WV(2, 2, 12, 8),   // N_side 3-4 (3-11 directions per class)
-    ART_WV(2, 2, 4, 8),    // N_side 1-2 (1-4)
-    ART_WV(2, 4, 16, 3),   // 16 x 32 columns
-    ART_WV(4, 2, 16, 3),   // 32 x 16 columns
-    ART_WV(2, 4, 12, 4),   // 16 x 32 columns, 12 slots (more CTAs per SM)
-    ART_WV(2, 2, 20, 5),   // 16 x 16 columns, 20 slots: N_side 8 classes in 2 groups
+    ART_WV(2, 2, 16, 1, 6),   // 16 x 16 columns; N_side 8 (26-37 directions per class: 3 groups)
+    ART_WV(2, 2, 12, 1, 8),   // N_side 3-4 (3-11 directions per class)
+    ART_WV(2, 2, 4, 1, 8),    // N_side 1-2 (1-4)
+    ART_WV(2, 4, 16, 1, 3),   // 16 x 32 columns
+    ART_WV(4, 2, 16, 1, 3),   // 32 x 16 columns
+    ART_WV(2, 4, 12, 1, 4),   // 16 x 32 columns, 12 slots (more CTAs per SM)
+    ART_WV(2, 2, 20, 1, 5),   // 16 x 16 columns, 20 slots: N_side 8 classes in 2 groups
+    ART_WV(2, 2, 16, 2, 4),   // four rows per lane: 16 x 32 columns, 4 warps
+    ART_WV(2, 1, 16, 2, 8),   // four rows per lane: 16 x 16 columns, 2 warps
+    ART_WV(2, 2, 12, 2, 4),   // four rows per lane, 12 slots
 };
 #undef ART_WV
 const int kNumWave = int(sizeof(kWave) / sizeof(kWave[0]));
@@ -88,7 +92,7 @@ float signed_len(double ds, bool neg) { return std::copysign(std::fabs(float(ds)
 
 void build_wave(const art_ctx *ctx, const WVariant &v, WaveHost &t)
 {
-    const int TB = 8 * v.wb, TC = 8 * v.wc;
+    const int TB = 8 * v.wb, TC = 8 * v.np * v.wc;
     long long jpart_off = 0, cell_off = 0;
     struct Raw {
         WaveUnit u;
@@ -211,7 +215,7 @@ void build_wave(const art_ctx *ctx, const WVariant &v, WaveHost &t)
         u.up_c = r.ic > 0 ? pos[r.key - nib] : -1;
         if (u.eb >= 0) {
             u.eb = eoff;
-            eoff += (long long)C.Na * v.wc * v.dmax * 8;
+            eoff += (long long)C.Na * v.wc * v.dmax * 8 * v.np;
         }
         if (u.ec >= 0) {
             u.ec = eoff;
@@ -228,7 +232,7 @@ void build_wave(const art_ctx *ctx, const WVariant &v, WaveHost &t)
 // its allocation.
 bool wave_tables_ok(const WaveHost &t, const WVariant &v, std::string &why)
 {
-    const int TB = 8 * v.wb, TC = 8 * v.wc;
+    const int TB = 8 * v.wb, TC = 8 * v.np * v.wc;
     for (size_t i = 0; i < t.units.size(); ++i) {
         const WaveUnit &u = t.units[i];
         if (u.cls < 0 || u.cls >= (int)t.classes.size() || u.nd < 1 || u.nd > v.dmax || u.d0 < 0 ||
@@ -254,7 +258,7 @@ bool wave_tables_ok(const WaveHost &t, const WVariant &v, std::string &why)
             const WaveUnit &w = t.units[q];
             const bool nb = k == 0 ? (w.tb + TB == u.tb && w.tc == u.tc) : (w.tc + TC == u.tc && w.tb == u.tb);
             const long long o = k == 0 ? w.eb : w.ec;
-            const long long len = (long long)C.Na * (k == 0 ? v.wc : v.wb) * v.dmax * 8;
+            const long long len = (long long)C.Na * (k == 0 ? v.wc * 8 * v.np : v.wb * 8) * v.dmax;
             if (!nb || w.cls != u.cls || w.d0 != u.d0 || w.nd != u.nd || o < 0 || o % 4 || o + len > t.edge_floats) {
                 why = "unit " + std::to_string(i) + ": upstream tile or its buffer";
                 return false;
@@ -307,6 +311,7 @@ art_status art_wave_setup(art_ctx *ctx, int w)
     W.wb = v.wb;
     W.wc = v.wc;
     W.dmax = v.dmax;
+    W.np = v.np;
     W.n_units = (int)t.units.size();
     W.edge_floats = t.edge_floats;
     W.jpart_floats = t.jpart_floats;

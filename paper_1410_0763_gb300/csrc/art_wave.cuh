@@ -264,104 +264,160 @@ __device__ __forceinline__ float2 wv_lds2(unsigned a)
     return v;
 }
 
+// The lane's rows in pairs (rows 2i, 2i + 1 in p[i]): each packed FP32x2
+// instruction of a segment works on one pair.
+template <int NP> struct WvRows {
+    static_assert(NP == 1 || NP == 2, "two or four rows per lane");
+    float2 p[NP];
+};
+
 // Per-lane exchange state of one step: shared-window byte addresses of this
-// lane's slots for direction 0 (direction d is 32 d bytes further).  B-face
-// slots hold the lane's two rows (2 cl, 2 cl + 1), C-face slots its column bl.
+// lane's slots for direction 0.  B-face slots hold the lane's 2 NP rows (the
+// warp's 4 lanes of a column: 32 NP bytes per direction), C-face slots its
+// column bl (8 lanes: 32 bytes per direction).
 struct WvXch {
-    unsigned bo, bi;   // B-face output / input pair
+    unsigned bo, bi;   // B-face output / input rows
     unsigned co, ci;   // C-face output / input
     bool b0, b7, c0, c3;
 };
 
+template <int NP> __device__ __forceinline__ void wv_sts_rows(unsigned a, const WvRows<NP> &v)
+{
+    if (NP == 1) {
+        wv_sts2(a, v.p[0].x, v.p[0].y);
+    } else {
+        asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.p[0].x), "f"(v.p[0].y),
+                     "f"(v.p[NP - 1].x), "f"(v.p[NP - 1].y)
+                     : "memory");
+    }
+}
+
+template <int NP> __device__ __forceinline__ WvRows<NP> wv_lds_rows(unsigned a)
+{
+    WvRows<NP> v;
+    if (NP == 1) {
+        v.p[0] = wv_lds2(a);
+    } else {
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(v.p[0].x), "=f"(v.p[0].y), "=f"(v.p[NP - 1].x), "=f"(v.p[NP - 1].y)
+                     : "r"(a)
+                     : "memory");
+    }
+    return v;
+}
+
 // Hand-off across a b-plane: each of the lane's rows takes the intensity that
 // leaves the column one step upstream along b (the lane to the left, or the
 // B-face input at bl = 0); lanes at bl = 7 write theirs to the B-face output.
-__device__ __forceinline__ void wv_xb(const WvXch &x, float2 &v, int d)
+template <int NP> __device__ __forceinline__ void wv_xb(const WvXch &x, WvRows<NP> &v, int d)
 {
-    const float n0 = __shfl_up_sync(0xffffffffu, v.x, 1);
-    const float n1 = __shfl_up_sync(0xffffffffu, v.y, 1);
-    if (x.b7) wv_sts2(x.bo + 32 * d, v.x, v.y);
-    const float2 in = wv_lds2(x.bi + 32 * d);
-    v.x = x.b0 ? in.x : n0;
-    v.y = x.b0 ? in.y : n1;
+    constexpr unsigned XBD = 4 * 4 * 2 * NP;   // bytes per direction: 4 lanes x 2 NP rows
+    WvRows<NP> n;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        n.p[i].x = __shfl_up_sync(0xffffffffu, v.p[i].x, 1);
+        n.p[i].y = __shfl_up_sync(0xffffffffu, v.p[i].y, 1);
+    }
+    if (x.b7) wv_sts_rows<NP>(x.bo + XBD * d, v);
+    const WvRows<NP> in = wv_lds_rows<NP>(x.bi + XBD * d);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        v.p[i].x = x.b0 ? in.p[i].x : n.p[i].x;
+        v.p[i].y = x.b0 ? in.p[i].y : n.p[i].y;
+    }
 }
 
-// Hand-off across a c-plane: the lane's second row takes its first row's
-// intensity; the first row takes the second row of the lane one step upstream
-// along c (or the C-face input at cl = 0); lanes at cl = 3 write their second
-// row to the C-face output.
-__device__ __forceinline__ void wv_xc(const WvXch &x, float2 &v, int d)
+// Hand-off across a c-plane: each row after the lane's first takes the row
+// before it (registers); the first row takes the last row of the lane one step
+// upstream along c (or the C-face input at cl = 0); lanes at cl = 3 write
+// their last row to the C-face output.
+template <int NP> __device__ __forceinline__ void wv_xc(const WvXch &x, WvRows<NP> &v, int d)
 {
-    const float n = __shfl_up_sync(0xffffffffu, v.y, 8);
-    if (x.c3) wv_sts(x.co + 32 * d, v.y);
+    const float last = v.p[NP - 1].y;
+    const float n = __shfl_up_sync(0xffffffffu, last, 8);
+    if (x.c3) wv_sts(x.co + 32 * d, last);
     const float in = wv_lds(x.ci + 32 * d);
-    v.y = v.x;
-    v.x = x.c0 ? in : n;
+#pragma unroll
+    for (int i = NP - 1; i >= 0; --i) {
+        v.p[i].y = v.p[i].x;
+        v.p[i].x = i > 0 ? v.p[i - 1].y : (x.c0 ? in : n);
+    }
 }
 
-// All directions of the unit for one slab, for the lane's two cells: the ray
-// states (shared memory, pairs at rs + 8 NT d) are updated in place; returns
-// the cells' sums over the unit's directions of |n_a| times the deposits
-// (at most 16 directions per unit, summed in FP32 in table order; the units'
+// All directions of the unit for one slab, for the lane's 2 NP cells: the ray
+// states (shared memory, rows at rs + 8 NP NT d) are updated in place; returns
+// the cells' sums over the unit's directions of |n_a| times the deposits (at
+// most DMAX directions per unit, summed in FP32 in table order; the units'
 // partials are summed with Kahan compensation by the reduction).
-template <int MODE, int NT>
-__device__ __forceinline__ float2 wv_dirs(const WvCell2 &c, unsigned rs, unsigned tab, int nd, const WvXch &x)
+template <int MODE, int NT, int NP>
+__device__ __forceinline__ WvRows<NP> wv_dirs(const WvCell2 (&c)[NP], unsigned rs, unsigned tab, int nd,
+                                              const WvXch &x)
 {
-    float2 acc = f2s(0.0f);
+    WvRows<NP> acc;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) acc.p[i] = f2s(0.0f);
 #pragma unroll 1
     for (int d = 0; d < nd; ++d) {
         float4 e;
         asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                      : "=f"(e.x), "=f"(e.y), "=f"(e.z), "=f"(e.w)
                      : "r"(tab + 16 * d));
-        const float2 R = wv_lds2(rs + 8 * NT * d);
-        float2 A;
-        float2 o = wv_seg<MODE, true>(c, R, fabsf(e.x), A);
-        if (__float_as_int(e.y) < 0) {            // two or more segments
+        WvRows<NP> o = wv_lds_rows<NP>(rs + 8 * NP * NT * d);
+        WvRows<NP> A;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) o.p[i] = wv_seg<MODE, true>(c[i], o.p[i], fabsf(e.x), A.p[i]);
+        if (__float_as_int(e.y) < 0) {                 // two or more segments
             const bool fc = __float_as_int(e.x) < 0;   // first hand-off along c
-            if (fc) wv_xc(x, o, d);
-            else wv_xb(x, o, d);
-            o = wv_seg<MODE, false>(c, o, fabsf(e.y), A);
-            if (__float_as_int(e.z) < 0) {        // three segments
-                if (fc) wv_xb(x, o, d);
-                else wv_xc(x, o, d);
-                o = wv_seg<MODE, false>(c, o, fabsf(e.z), A);
+            if (fc) wv_xc<NP>(x, o, d);
+            else wv_xb<NP>(x, o, d);
+#pragma unroll
+            for (int i = 0; i < NP; ++i) o.p[i] = wv_seg<MODE, false>(c[i], o.p[i], fabsf(e.y), A.p[i]);
+            if (__float_as_int(e.z) < 0) {             // three segments
+                if (fc) wv_xb<NP>(x, o, d);
+                else wv_xc<NP>(x, o, d);
+#pragma unroll
+                for (int i = 0; i < NP; ++i) o.p[i] = wv_seg<MODE, false>(c[i], o.p[i], fabsf(e.z), A.p[i]);
             }
         }
-        wv_sts2(rs + 8 * NT * d, o.x, o.y);
-        acc = __ffma2_rn(A, f2s(e.w), acc);
+        wv_sts_rows<NP>(rs + 8 * NP * NT * d, o);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) acc.p[i] = __ffma2_rn(A.p[i], f2s(e.w), acc.p[i]);
     }
     return acc;
 }
 
-template <int WB, int WC, int DMAX> struct WaveShape {
+// Shared-memory and edge-buffer shape of a kernel: WB x WC warps, each an
+// 8 (b) x 4 R (c) tile of columns with R = 2 NP rows per lane.
+template <int WB, int WC, int DMAX, int NP> struct WaveShape {
     static constexpr int NT = 32 * WB * WC;
-    static constexpr int TB = 8 * WB, TC = 8 * WC;
+    static constexpr int R = 2 * NP;                          // rows per lane
+    static constexpr int TB = 8 * WB, TC = 4 * R * WC;
     static constexpr int RT = (WB + WC <= 4) ? 4 : ((WB + WC <= 8) ? 8 : 16);   // table ring (slabs)
-    static constexpr int XB_PAR = (WB + 1) * WC * DMAX * 8;   // floats per parity
+    static constexpr int XBW = 4 * R;                         // B-face floats per warp and direction
+    static constexpr int XB_PAR = (WB + 1) * WC * DMAX * XBW; // floats per parity
     static constexpr int XC_PAR = (WC + 1) * WB * DMAX * 8;
     static constexpr size_t off_xb = size_t(RT) * DMAX * 16;
     static constexpr size_t off_xc = off_xb + size_t(2) * XB_PAR * 4;
     static constexpr size_t off_fs = off_xc + size_t(2) * XC_PAR * 4;
-    static constexpr size_t off_rs = off_fs + size_t(2) * NT * 16;
-    static constexpr size_t bytes = off_rs + size_t(DMAX) * NT * 8;
-    static constexpr long long edge_b(int Na) { return (long long)Na * WC * DMAX * 8; }
+    static constexpr size_t off_rs = off_fs + size_t(2) * NT * R * 8;
+    static constexpr size_t bytes = off_rs + size_t(DMAX) * NT * R * 4;
+    static constexpr long long edge_b(int Na) { return (long long)Na * WC * DMAX * XBW; }
     static constexpr long long edge_c(int Na) { return (long long)Na * WB * DMAX * 8; }
 };
 
 constexpr int WAVE_PUB = 4;   // slabs between progress publications
 
-template <int WB, int WC, int DMAX, int MINB>
+template <int WB, int WC, int DMAX, int NP, int MINB>
 __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs p)
 {
-    using Sh = WaveShape<WB, WC, DMAX>;
-    constexpr int NT = Sh::NT, RT = Sh::RT;
+    using Sh = WaveShape<WB, WC, DMAX, NP>;
+    constexpr int NT = Sh::NT, RT = Sh::RT, R = Sh::R, XBW = Sh::XBW;
     extern __shared__ __align__(16) unsigned char wsm[];
     float4 *tab = reinterpret_cast<float4 *>(wsm);                  // [RT][DMAX]
-    float *XB = reinterpret_cast<float *>(wsm + Sh::off_xb);        // [2][WB+1][WC][DMAX][8]
+    float *XB = reinterpret_cast<float *>(wsm + Sh::off_xb);        // [2][WB+1][WC][DMAX][XBW]
     float *XC = reinterpret_cast<float *>(wsm + Sh::off_xc);        // [2][WC+1][WB][DMAX][8]
-    float4 *FS = reinterpret_cast<float4 *>(wsm + Sh::off_fs);      // [2][NT]: (kappa, src) of the two cells
-    float2 *RS = reinterpret_cast<float2 *>(wsm + Sh::off_rs);      // [DMAX][NT]: ray states of the two columns
+    float2 *FS = reinterpret_cast<float2 *>(wsm + Sh::off_fs);      // [2][NT][R]: (kappa, src) of the lane's cells
+    float *RS = reinterpret_cast<float *>(wsm + Sh::off_rs);        // [DMAX][NT][R]: ray states of its columns
     __shared__ int s_unit;
     __shared__ long long s_seg[DMAX];   // first table entry of each direction of the unit
     __shared__ long long s_up[2];       // output buffers of the upstream units (B, C)
@@ -377,28 +433,32 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
     const WaveClass C = p.classes[U.cls];
     const int Na = C.Na, nd = U.nd;
     const int j = U.tb + 8 * wb + bl;                          // canonical b column
-    const int k0 = U.tc + 8 * wc + 2 * cl;                      // canonical c rows k0, k0 + 1
-    const bool in0 = j < C.Nb && k0 < C.Nc, in1 = j < C.Nb && k0 + 1 < C.Nc;
+    const int k0 = U.tc + 4 * R * wc + R * cl;                  // canonical c rows k0 .. k0 + R - 1
     const int pb = C.sb > 0 ? j : C.Nb - 1 - j;
-    const int pc0 = C.sc > 0 ? k0 : C.Nc - 1 - k0, pc1 = C.sc > 0 ? k0 + 1 : C.Nc - 2 - k0;
-    // the lane's two columns in the axis-a field layout [a][c][b], and its
-    // cells of slab m in the natural layout of the J partial: Jl[m * jstep]
+    const int pc0 = C.sc > 0 ? k0 : C.Nc - 1 - k0;
+    const int dpc = C.sc > 0 ? 1 : -1;                          // physical c step from one row to the next
+    unsigned inmask = 0;                                        // rows of the lane inside the box
+#pragma unroll
+    for (int r = 0; r < R; ++r) inmask |= (j < C.Nb && k0 + r < C.Nc) ? 1u << r : 0u;
+    // the lane's columns in the axis-a field layout [a][c][b] (row r at
+    // F0 + r dpc Nb), and its cells of slab m in the natural layout of the J
+    // partial (row r at J0 + r dpc stride_c + m jstep)
     const float2 *Fb = (C.a == 0 ? p.field0 : (C.a == 1 ? p.field1 : p.field2)) + C.cell_off;
-    const float2 *F0 = Fb + (in0 ? (long long)pc0 * C.Nb + pb : 0);
-    const float2 *F1 = Fb + (in1 ? (long long)pc1 * C.Nb + pb : 0);
-    const int fslab = C.Nb * C.Nc;
+    const long long f0 = (long long)pc0 * C.Nb + pb;
+    const int fslab = C.Nb * C.Nc, frow = dpc * C.Nb;
     const long long ja = C.sa > 0 ? 0 : (long long)(Na - 1) * C.stride_a;
     const long long jb0 = ja + (long long)pb * C.stride_b + (long long)pc0 * C.stride_c;
-    const long long jb1 = ja + (long long)pb * C.stride_b + (long long)pc1 * C.stride_c;
+    const int jrow = (int)(dpc * C.stride_c);
     const int jstep = (int)(C.sa > 0 ? C.stride_a : -C.stride_a);
-    auto jrange_ok = [&](bool in, long long jb) {
-        return !in || (U.jpart + jb >= 0 && U.jpart + jb < p.jpart_floats &&
-                       U.jpart + jb + (long long)(Na - 1) * jstep >= 0 &&
-                       U.jpart + jb + (long long)(Na - 1) * jstep < p.jpart_floats);
-    };
-    const bool jl_ok = wv_ok(jrange_ok(in0, jb0) && jrange_ok(in1, jb1), p.err);
-    float *J0 = p.jpart + U.jpart + (in0 ? jb0 : 0);
-    float *J1 = p.jpart + U.jpart + (in1 ? jb1 : 0);
+    bool jl_ok = true;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (inmask >> r & 1) {
+            const long long j1 = U.jpart + jb0 + (long long)r * jrow, j2 = j1 + (long long)(Na - 1) * jstep;
+            jl_ok = jl_ok && j1 >= 0 && j1 < p.jpart_floats && j2 >= 0 && j2 < p.jpart_floats;
+        }
+    jl_ok = wv_ok(jl_ok, p.err);
+    float *J0 = p.jpart + U.jpart + (inmask ? jb0 : 0);
     const bool stalled = u == p.stall_unit;
 
     if (tid < nd) s_seg[tid] = p.seg_off[U.d0 + tid];
@@ -406,7 +466,7 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
     if (tid == 1) s_up[1] = U.up_c >= 0 ? p.units[U.up_c].ec : -1;
     // box-edge inputs carry the boundary intensity in both parities
     if (U.up_b < 0)
-        for (int e = tid; e < WC * DMAX * 8; e += NT) {
+        for (int e = tid; e < WC * DMAX * XBW; e += NT) {
             XB[e] = p.i_bc;
             XB[Sh::XB_PAR + e] = p.i_bc;
         }
@@ -416,7 +476,9 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
             XC[Sh::XC_PAR + e] = p.i_bc;
         }
     // every ray enters the box with the boundary intensity
-    for (int d = 0; d < nd; ++d) RS[d * NT + tid] = make_float2(p.i_bc, p.i_bc);
+    for (int d = 0; d < nd; ++d)
+#pragma unroll
+        for (int r = 0; r < R; ++r) RS[(d * NT + tid) * R + r] = p.i_bc;
 
     // progress of the upstream warps last seen by this warp (uniform), and the
     // flag values lane 0 read in the previous step (used before polling again)
@@ -433,10 +495,11 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
         if (tid < nd && s1 < Na) wv_cp16(tab + (s1 & (RT - 1)) * DMAX + tid, p.segs + s_seg[tid] + s1);
         const int mn = s1 - wb - wc;
         if (mn >= 0 && mn < Na) {
-            const long long pa = (C.sa > 0 ? mn : Na - 1 - mn) * (long long)fslab;
-            float2 *dst = reinterpret_cast<float2 *>(FS + (s1 & 1) * NT + tid);   // read at step s1
-            if (in0) wv_cp8(dst, F0 + pa);
-            if (in1) wv_cp8(dst + 1, F1 + pa);
+            const long long fa = f0 + (long long)(C.sa > 0 ? mn : Na - 1 - mn) * fslab;
+            float2 *dst = FS + ((s1 & 1) * NT + tid) * R;   // read at step s1
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (inmask >> r & 1) wv_cp8(dst + r, Fb + fa + (long long)r * frow);
         }
         int ok = 1;
         if (wb == 0 && U.up_b >= 0) {
@@ -454,11 +517,11 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
                 if (ok) {
                     const long long eb_up = s_up[0];
                     for (int dd = lane; dd < nd; dd += 32) {
-                        const long long o = eb_up + (((long long)s * WC + wc) * DMAX + dd) * 8;
-                        if (wv_ok(eb_up >= 0 && o + 8 <= p.edge_floats, p.err)) {
-                            float *dst = XB + rp * Sh::XB_PAR + (wc * DMAX + dd) * 8;
-                            wv_cp16(dst, p.edge + o);
-                            wv_cp16(dst + 4, p.edge + o + 4);
+                        const long long o = eb_up + (((long long)s * WC + wc) * DMAX + dd) * XBW;
+                        if (wv_ok(eb_up >= 0 && o + XBW <= p.edge_floats, p.err)) {
+                            float *dst = XB + rp * Sh::XB_PAR + (wc * DMAX + dd) * XBW;
+#pragma unroll
+                            for (int q = 0; q < XBW; q += 4) wv_cp16(dst + q, p.edge + o + q);
                         }
                     }
                 }
@@ -504,7 +567,7 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
     const bool b_out = wb == WB - 1, c_out = wc == WC - 1;
     const int fl_b = u * (WB + WC) + wc, fl_c = u * (WB + WC) + WC + wb;
     const unsigned xb0 = wv_smem(XB), xc0 = wv_smem(XC);
-    const unsigned rs0 = wv_smem(RS) + 8 * tid, tab0 = wv_smem(tab);
+    const unsigned rs0 = wv_smem(RS) + 4 * R * tid, tab0 = wv_smem(tab);
     for (int t = 0; t < T && !abort_; ++t) {
         const int m = t - wb - wc;
         // progress of the slabs written to global memory in earlier steps
@@ -515,18 +578,26 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
         if (!stage(t)) bad = 1;
         if (m >= 0 && m < Na) {
             const int par = t & 1;
-            const float4 f = FS[par * NT + tid];
-            WvCell2 c;
-            c.kap = make_float2(in0 ? f.x : 0.0f, in1 ? f.z : 0.0f);
-            const float2 src = make_float2(in0 ? f.y : 0.0f, in1 ? f.w : 0.0f);
-            c.nkap = make_float2(-c.kap.x, -c.kap.y);
-            c.rk = make_float2(c.kap.x > 0.0f ? wv_rcp(c.kap.x) : 0.0f, c.kap.y > 0.0f ? wv_rcp(c.kap.y) : 0.0f);
-            c.E = p.field_form ? src : __fmul2_rn(c.kap, src);
-            c.S = p.field_form ? __fmul2_rn(src, c.rk) : src;
-            c.k2 = __fmul2_rn(c.kap, f2s(-1.4426950408889634f));
+            WvCell2 c[NP];
+            bool thin = true, thick = true;
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                const float4 f = reinterpret_cast<const float4 *>(FS + (par * NT + tid) * R)[i];
+                const bool i0 = inmask >> (2 * i) & 1, i1 = inmask >> (2 * i + 1) & 1;
+                c[i].kap = make_float2(i0 ? f.x : 0.0f, i1 ? f.z : 0.0f);
+                const float2 src = make_float2(i0 ? f.y : 0.0f, i1 ? f.w : 0.0f);
+                c[i].nkap = make_float2(-c[i].kap.x, -c[i].kap.y);
+                c[i].rk = make_float2(c[i].kap.x > 0.0f ? wv_rcp(c[i].kap.x) : 0.0f,
+                                      c[i].kap.y > 0.0f ? wv_rcp(c[i].kap.y) : 0.0f);
+                c[i].E = p.field_form ? src : __fmul2_rn(c[i].kap, src);
+                c[i].S = p.field_form ? __fmul2_rn(src, c[i].rk) : src;
+                c[i].k2 = __fmul2_rn(c[i].kap, f2s(-1.4426950408889634f));
+                thin = thin && c[i].kap.x < KAP_THIN && c[i].kap.y < KAP_THIN;
+                thick = thick && c[i].kap.x >= KAP_THICK && c[i].kap.y >= KAP_THICK;
+            }
             WvXch x;
-            x.bo = xb0 + 4 * (par * Sh::XB_PAR + ((wb + 1) * WC + wc) * DMAX * 8 + 2 * cl);
-            x.bi = xb0 + 4 * ((par ^ 1) * Sh::XB_PAR + (wb * WC + wc) * DMAX * 8 + 2 * cl);
+            x.bo = xb0 + 4 * (par * Sh::XB_PAR + ((wb + 1) * WC + wc) * DMAX * XBW + R * cl);
+            x.bi = xb0 + 4 * ((par ^ 1) * Sh::XB_PAR + (wb * WC + wc) * DMAX * XBW + R * cl);
             x.co = xc0 + 4 * (par * Sh::XC_PAR + ((wc + 1) * WB + wb) * DMAX * 8 + bl);
             x.ci = xc0 + 4 * ((par ^ 1) * Sh::XC_PAR + (wc * WB + wb) * DMAX * 8 + bl);
             x.b0 = bl == 0;
@@ -534,30 +605,37 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
             x.c0 = cl == 0;
             x.c3 = cl == 3;
             const unsigned tb = tab0 + 16 * (m & (RT - 1)) * DMAX;
-            const unsigned thin = __ballot_sync(0xffffffffu, c.kap.x < KAP_THIN && c.kap.y < KAP_THIN);
-            const unsigned thick = __ballot_sync(0xffffffffu, c.kap.x >= KAP_THICK && c.kap.y >= KAP_THICK);
-            float2 js;
-            if (thin == 0xffffffffu)
-                js = wv_dirs<MODE_THIN, NT>(c, rs0, tb, nd, x);
-            else if (thick == 0xffffffffu)
-                js = __fmul2_rn(wv_dirs<MODE_THICK, NT>(c, rs0, tb, nd, x), c.rk);
-            else
-                js = wv_dirs<MODE_MIXED, NT>(c, rs0, tb, nd, x);
+            const bool all_thin = __all_sync(0xffffffffu, thin), all_thick = __all_sync(0xffffffffu, thick);
+            WvRows<NP> js;
+            if (all_thin) {
+                js = wv_dirs<MODE_THIN, NT, NP>(c, rs0, tb, nd, x);
+            } else if (all_thick) {
+                js = wv_dirs<MODE_THICK, NT, NP>(c, rs0, tb, nd, x);
+#pragma unroll
+                for (int i = 0; i < NP; ++i) js.p[i] = __fmul2_rn(js.p[i], c[i].rk);
+            } else {
+                js = wv_dirs<MODE_MIXED, NT, NP>(c, rs0, tb, nd, x);
+            }
             if (jl_ok) {
-                if (in0) J0[m * jstep] = js.x;
-                if (in1) J1[m * jstep] = js.y;
+                float *Jm = J0 + (long long)m * jstep;
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    if (inmask >> (2 * i) & 1) Jm[(2 * i) * jrow] = js.p[i].x;
+                    if (inmask >> (2 * i + 1) & 1) Jm[(2 * i + 1) * jrow] = js.p[i].y;
+                }
             }
             // edge intensities of this slab to the downstream CTAs
             if ((b_out && U.eb >= 0) || (c_out && U.ec >= 0)) {
                 __syncwarp();
                 if (b_out && U.eb >= 0)
                     for (int dd = lane; dd < nd; dd += 32) {
-                        const float *srcs = XB + par * Sh::XB_PAR + ((wb + 1) * WC + wc) * DMAX * 8 + dd * 8;
-                        const long long o = U.eb + (((long long)m * WC + wc) * DMAX + dd) * 8;
-                        if (wv_ok(o + 8 <= p.edge_floats, p.err)) {
-                            *reinterpret_cast<float4 *>(p.edge + o) = *reinterpret_cast<const float4 *>(srcs);
-                            *reinterpret_cast<float4 *>(p.edge + o + 4) = *reinterpret_cast<const float4 *>(srcs + 4);
-                        }
+                        const float *srcs = XB + par * Sh::XB_PAR + ((wb + 1) * WC + wc) * DMAX * XBW + dd * XBW;
+                        const long long o = U.eb + (((long long)m * WC + wc) * DMAX + dd) * XBW;
+                        if (wv_ok(o + XBW <= p.edge_floats, p.err))
+#pragma unroll
+                            for (int q = 0; q < XBW; q += 4)
+                                *reinterpret_cast<float4 *>(p.edge + o + q) =
+                                    *reinterpret_cast<const float4 *>(srcs + q);
                     }
                 if (c_out && U.ec >= 0)
                     for (int dd = lane; dd < nd; dd += 32) {

@@ -2,8 +2,9 @@
 cell average) against the FP64 oracle, through the C ABI.
 
 Bar: 1e-5 relative per cell on J and J^in (the FP32 target), as for the
-slab-block kernels.  Every compiled wavefront shape (art_options.variant 16-22:
-8 x 8-column warp tiles, 2 x 2, 2 x 4 or 4 x 2 warps per CTA, 20 / 16 / 12 / 4
+slab-block kernels.  Every compiled wavefront shape (art_options.variant 16-25:
+8 x 8- or 8 x 16-column warp tiles (two or four rows per lane), 2 x 1, 2 x 2,
+2 x 4 or 4 x 2 warps per CTA, 20 / 16 / 12 / 4
 direction slots) runs on ragged grids that span several CTA tiles along both
 transverse axes, with classes split into direction groups where they exceed
 the slots.  The bounded waits are checked by stalling one tile on purpose: the
@@ -75,7 +76,9 @@ def test_default_fp32_context_uses_the_wavefront_sweep():
 @pytest.mark.parametrize("variant,nside", [(WAVE0, 8), (WAVE0 + 1, 4), (WAVE0 + 1, 3), (WAVE0 + 2, 2),
                                            (WAVE0 + 2, 1), (WAVE0 + 3, 8), (WAVE0 + 4, 8), (WAVE0 + 2, 4),
                                            (WAVE0 + 1, 8), (WAVE0 + 3, 2), (WAVE0 + 4, 3),
-                                           (WAVE0 + 5, 8), (WAVE0 + 5, 4), (WAVE0 + 6, 8), (WAVE0 + 6, 2)])
+                                           (WAVE0 + 5, 8), (WAVE0 + 5, 4), (WAVE0 + 6, 8), (WAVE0 + 6, 2),
+                                           (WAVE0 + 7, 8), (WAVE0 + 7, 3), (WAVE0 + 8, 8), (WAVE0 + 8, 1),
+                                           (WAVE0 + 9, 4)])
 def test_ragged_grids_every_shape(orc, variant, nside):
     """Ragged against every tile (16 x 16 and 32 x 16 columns); shapes with fewer slots than a
     class's directions split it into groups."""
@@ -89,11 +92,12 @@ def test_ragged_grids_every_shape(orc, variant, nside):
 
 
 @pytest.mark.parametrize("scale", [0.02, 0.3, 3.0])
-def test_thin_mixed_and_thick_media(orc, scale):
+@pytest.mark.parametrize("variant", [0, WAVE0 + 7])
+def test_thin_mixed_and_thick_media(orc, scale, variant):
     """Media whose warps take the series path, both paths, or the exponential path."""
     kap, S = lognormal((20, 24, 28), 11, scale)
     jin_o, j_o, _ = orc.sweep(kap, S, 4)
-    J, Jin, _ = run(kap, S, 4)
+    J, Jin, _ = run(kap, S, 4, variant=variant)
     assert rel(Jin, jin_o) < 1e-5
     assert rel(J, j_o) < 1e-5
 
