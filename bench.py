@@ -1131,10 +1131,17 @@ def profile_case(args):
     out = {"profile_case": args.profile_case}
     if args.profile_case == "sweep":
         # a few sweeps of one workload: the GRF recipe at n^3 and N_side (one bin), or with
-        # --workload given explicitly, that benchmark workload (all its bins); the kernel variant given
+        # --workload given explicitly, that benchmark workload (all its bins; the clumpy medium at
+        # n^3 when --n is given too, with the full workload's optical depth per cell); the kernel
+        # variant given
         if "--workload" in sys.argv:
-            c = make_case(args.workload, 0)
-            n, nside, nb = c.shape[0], c.nside, case_bins(c)
+            w = WORKLOADS[args.workload]
+            if args.n and w.get("kind") == "clumpy":
+                c = wl.clumpy_sweep(args.n, args.nside or w["nside"], seed=w["seed"], nbins=w["bins"],
+                                    tau_box=10.0 * args.n / w["n"])
+            else:
+                c = make_case(args.workload, 0)
+            n, nside, nb = c.shape[-1], c.nside, case_bins(c)
         else:
             n, nside, nb = args.n or 128, args.nside or 8, 1
             c = wl.grf(n, nside, seed=3)

@@ -51,7 +51,8 @@ struct art_sur_bufs {
 struct art_wave_state {
     bool on = false;
     int variant = 0, wb = 0, wc = 0, dmax = 0, np = 1, n_units = 0;
-    void *units = nullptr, *classes = nullptr, *segs = nullptr, *seg_off = nullptr;
+    void *units = nullptr, *classes = nullptr, *rtab = nullptr;   // rtab: run tables of the direction groups
+    long long rtab_len = 0;     // float4 count
     float *edge = nullptr;      // edge intensities handed between CTA tiles
     int *flags = nullptr;       // [0] error word, [1] ticket, then per-unit progress flags
     size_t flag_bytes = 0;

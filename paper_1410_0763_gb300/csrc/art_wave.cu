@@ -80,15 +80,57 @@ const int kNumWave = int(sizeof(kWave) / sizeof(kWave[0]));
 struct WaveHost {
     std::vector<WaveClass> classes;
     std::vector<WaveUnit> units;   // ticket order
-    std::vector<float4> segs;
-    std::vector<long long> seg_off;
+    std::vector<float4> rtab;      // run tables of the direction groups
+    int n_groups = 0;
     std::vector<art_grid_host> grids;
     long long edge_floats = 0, jpart_floats = 0;
     int max_class = 0;
 };
 
-// A path length with a flag in its sign bit (-0 where the length is 0).
-float signed_len(double ds, bool neg) { return std::copysign(std::fabs(float(ds)), neg ? -1.0f : 1.0f); }
+float int_bits(int v)
+{
+    float f;
+    std::memcpy(&f, &v, sizeof f);
+    return f;
+}
+
+// Segment pattern of a slab, the run it belongs to: 0 one segment; 1 / 2 two
+// segments, hand-off along b / c; 3 / 4 three segments, b / c crossed first.
+int run_of(const SlabGeom &g)
+{
+    if (g.nseg == 1) return 0;
+    if (g.nseg == 2) return g.shc ? 2 : 1;
+    return g.cfirst ? 4 : 3;
+}
+
+// Run table of one direction group (members' frames f[0..nd)): per slab the
+// header of run ends and the entries sorted by run (stable: slot order within
+// a run).
+void build_run_table(const std::vector<const Frame *> &f, int Na, std::vector<float4> &out)
+{
+    const int nd = (int)f.size();
+    std::vector<std::vector<SlabGeom>> geo(nd);
+    for (int i = 0; i < nd; ++i) slab_geometry(*f[i], Na, geo[i]);
+    std::vector<int> order(nd);
+    for (int m = 0; m < Na; ++m) {
+        int ends[5] = {0, 0, 0, 0, 0};
+        for (int i = 0; i < nd; ++i) ++ends[run_of(geo[i][m])];
+        for (int k = 1; k < 5; ++k) ends[k] += ends[k - 1];
+        for (int i = 0; i < nd; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int x, int y) { return run_of(geo[x][m]) < run_of(geo[y][m]); });
+        out.push_back(make_float4(int_bits(ends[0]), int_bits(ends[1]), int_bits(ends[2]), int_bits(ends[3])));
+        for (int i : order) {
+            const SlabGeom &g = geo[i][m];
+            for (int k = 0; k < 3; ++k) {
+                const float ds = k < g.nseg ? float(g.ds[k]) : 0.0f;
+                out.push_back(make_float4(ds, ds, ds * ds, ds * ds));
+            }
+            const float na = float(f[i]->na);
+            out.push_back(make_float4(na, na, int_bits(i), 0.0f));
+        }
+    }
+}
 
 void build_wave(const art_ctx *ctx, const WVariant &v, WaveHost &t)
 {
@@ -140,23 +182,16 @@ void build_wave(const art_ctx *ctx, const WVariant &v, WaveHost &t)
             const int G = (n + v.dmax - 1) / v.dmax;
             for (int g = 0; g < G; ++g) {
                 const int lo = (int)((long long)n * g / G), hi = (int)((long long)n * (g + 1) / G);
-                const int d0 = (int)t.seg_off.size();
+                const int grp = t.n_groups++;
+                const long long gtab = (long long)t.rtab.size();
+                std::vector<const Frame *> gf;
                 for (int i = lo; i < hi; ++i) {
-                    const Frame &f = fr[members[i]];
+                    gf.push_back(&fr[members[i]]);
                     std::vector<SlabGeom> geo;
-                    slab_geometry(f, C.Na, geo);
-                    t.seg_off.push_back((long long)t.segs.size());
-                    for (const SlabGeom &s : geo) {
-                        const bool firstc = s.nseg == 2 ? s.shc != 0 : (s.nseg == 3 && s.cfirst);
-                        float4 e;
-                        e.x = signed_len(s.ds[0], firstc);
-                        e.y = signed_len(s.ds[1], s.nseg >= 2);
-                        e.z = signed_len(s.ds[2], s.nseg == 3);
-                        e.w = float(f.na);
-                        t.segs.push_back(e);
-                        gh.seg_count += (long long)s.nonzero * C.Nb * C.Nc;
-                    }
+                    slab_geometry(fr[members[i]], C.Na, geo);
+                    for (const SlabGeom &s : geo) gh.seg_count += (long long)s.nonzero * C.Nb * C.Nc;
                 }
+                build_run_table(gf, C.Na, t.rtab);
                 const long long jp = gh.jpart_off + (long long)part * gh.ncell;
                 ++part;
                 const int nib = (C.Nb + TB - 1) / TB, nic = (C.Nc + TC - 1) / TC;
@@ -164,8 +199,9 @@ void build_wave(const art_ctx *ctx, const WVariant &v, WaveHost &t)
                     for (int ib = 0; ib < nib; ++ib) {
                         Raw r{};
                         r.u.cls = ci;
-                        r.u.d0 = d0;
+                        r.u.grp = grp;
                         r.u.nd = hi - lo;
+                        r.u.tab = gtab;
                         r.u.tb = ib * TB;
                         r.u.tc = ic * TC;
                         r.u.jpart = jp;
@@ -226,26 +262,62 @@ void build_wave(const art_ctx *ctx, const WVariant &v, WaveHost &t)
     t.edge_floats = eoff;
 }
 
+int bits_int(float f)
+{
+    int v;
+    std::memcpy(&v, &f, sizeof v);
+    return v;
+}
+
+// A run table block per slab: run ends in order and at most nd, the slots of
+// its entries a permutation of 0 .. nd - 1 (the kernel indexes shared memory
+// with both unchecked).
+bool run_table_ok(const std::vector<float4> &rt, long long tab, int nd, int Na)
+{
+    std::vector<char> seen(nd);
+    for (int m = 0; m < Na; ++m) {
+        const long long b = tab + (long long)m * wv_block(nd);
+        const float4 h = rt[b];
+        const int e[6] = {0, bits_int(h.x), bits_int(h.y), bits_int(h.z), bits_int(h.w), nd};
+        for (int k = 0; k < 5; ++k)
+            if (e[k] > e[k + 1]) return false;
+        std::fill(seen.begin(), seen.end(), 0);
+        for (int i = 0; i < nd; ++i) {
+            const int slot = bits_int(rt[b + 1 + (long long)WV_ENT * i + 3].z);
+            if (slot < 0 || slot >= nd || seen[slot]) return false;
+            seen[slot] = 1;
+        }
+    }
+    return true;
+}
+
 // Invariants the kernel relies on: every upstream unit has a smaller ticket
 // (so a wait is always on a unit that has started), the upstream tiles are the
-// neighbours of the same (class, group), and every buffer range lies inside
-// its allocation.
+// neighbours of the same (class, group), every buffer range lies inside its
+// allocation, and the run tables are well formed.
 bool wave_tables_ok(const WaveHost &t, const WVariant &v, std::string &why)
 {
     const int TB = 8 * v.wb, TC = 8 * v.np * v.wc;
+    std::vector<char> group_ok(t.n_groups, 0);
     for (size_t i = 0; i < t.units.size(); ++i) {
         const WaveUnit &u = t.units[i];
-        if (u.cls < 0 || u.cls >= (int)t.classes.size() || u.nd < 1 || u.nd > v.dmax || u.d0 < 0 ||
-            u.d0 + u.nd > (int)t.seg_off.size()) {
+        if (u.cls < 0 || u.cls >= (int)t.classes.size() || u.nd < 1 || u.nd > v.dmax || u.grp < 0 ||
+            u.grp >= t.n_groups) {
             why = "unit " + std::to_string(i) + ": class or direction range";
             return false;
         }
         const WaveClass &C = t.classes[u.cls];
-        for (int d = u.d0; d < u.d0 + u.nd; ++d)
-            if (t.seg_off[d] < 0 || t.seg_off[d] + C.Na > (long long)t.segs.size()) {
-                why = "unit " + std::to_string(i) + ": segment table range";
+        if (u.tab < 0 || u.tab + (long long)C.Na * wv_block(u.nd) > (long long)t.rtab.size()) {
+            why = "unit " + std::to_string(i) + ": run table range";
+            return false;
+        }
+        if (!group_ok[u.grp]) {
+            if (!run_table_ok(t.rtab, u.tab, u.nd, C.Na)) {
+                why = "unit " + std::to_string(i) + ": run table contents";
                 return false;
             }
+            group_ok[u.grp] = 1;
+        }
         const int ups[2] = {u.up_b, u.up_c};
         for (int k = 0; k < 2; ++k) {
             const int q = ups[k];
@@ -259,7 +331,7 @@ bool wave_tables_ok(const WaveHost &t, const WVariant &v, std::string &why)
             const bool nb = k == 0 ? (w.tb + TB == u.tb && w.tc == u.tc) : (w.tc + TC == u.tc && w.tb == u.tb);
             const long long o = k == 0 ? w.eb : w.ec;
             const long long len = (long long)C.Na * (k == 0 ? v.wc * 8 * v.np : v.wb * 8) * v.dmax;
-            if (!nb || w.cls != u.cls || w.d0 != u.d0 || w.nd != u.nd || o < 0 || o % 4 || o + len > t.edge_floats) {
+            if (!nb || w.cls != u.cls || w.grp != u.grp || w.nd != u.nd || o < 0 || o % 4 || o + len > t.edge_floats) {
                 why = "unit " + std::to_string(i) + ": upstream tile or its buffer";
                 return false;
             }
@@ -283,7 +355,7 @@ int art_wave_dmax(int w) { return w >= 0 && w < kNumWave ? kWave[w].dmax : 0; }
 void art_wave_free(art_ctx *ctx)
 {
     art_wave_state &W = ctx->wave;
-    void *ptrs[] = {W.units, W.classes, W.segs, W.seg_off, W.edge, W.flags};
+    void *ptrs[] = {W.units, W.classes, W.rtab, W.edge, W.flags};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     ctx->dev_bytes -= W.bytes;
@@ -324,14 +396,13 @@ art_status art_wave_setup(art_ctx *ctx, int w)
         ctx->seg_count += g.seg_count;
     }
     const size_t ub = t.units.size() * sizeof(WaveUnit), cb = t.classes.size() * sizeof(WaveClass);
-    const size_t sb = std::max<size_t>(16, t.segs.size() * sizeof(float4));
-    const size_t ob = std::max<size_t>(16, t.seg_off.size() * sizeof(long long));
+    const size_t sb = std::max<size_t>(16, t.rtab.size() * sizeof(float4));
     const size_t eb = std::max<size_t>(16, (size_t)t.edge_floats * sizeof(float));
     const size_t fb = (size_t(W.n_units) * (v.wb + v.wc) + 2) * sizeof(int);
     struct {
         void **p;
         size_t b;
-    } al[] = {{&W.units, ub}, {&W.classes, cb}, {&W.segs, sb}, {&W.seg_off, ob},
+    } al[] = {{&W.units, ub}, {&W.classes, cb}, {&W.rtab, sb},
               {reinterpret_cast<void **>(&W.edge), eb}, {reinterpret_cast<void **>(&W.flags), fb}};
     for (auto &a : al) {
         const cudaError_t e = cudaMalloc(a.p, a.b ? a.b : 16);
@@ -346,9 +417,8 @@ art_status art_wave_setup(art_ctx *ctx, int w)
     W.flag_bytes = fb;
     WCK(ctx, cudaMemcpy(W.units, t.units.data(), ub, cudaMemcpyHostToDevice));
     WCK(ctx, cudaMemcpy(W.classes, t.classes.data(), cb, cudaMemcpyHostToDevice));
-    if (!t.segs.empty()) WCK(ctx, cudaMemcpy(W.segs, t.segs.data(), t.segs.size() * sizeof(float4), cudaMemcpyHostToDevice));
-    if (!t.seg_off.empty())
-        WCK(ctx, cudaMemcpy(W.seg_off, t.seg_off.data(), t.seg_off.size() * sizeof(long long), cudaMemcpyHostToDevice));
+    if (!t.rtab.empty()) WCK(ctx, cudaMemcpy(W.rtab, t.rtab.data(), t.rtab.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    W.rtab_len = (long long)t.rtab.size();
     WCK(ctx, cudaMemset(W.flags, 0, fb));
     W.on = true;
     return ART_OK;
@@ -366,8 +436,8 @@ art_status art_wave_launch(art_ctx *ctx, const float2 *f0, const float2 *f1, con
     a.field0 = f0;
     a.field1 = f1;
     a.field2 = f2;
-    a.segs = static_cast<const float4 *>(W.segs);
-    a.seg_off = static_cast<const long long *>(W.seg_off);
+    a.rtab = static_cast<const float4 *>(W.rtab);
+    a.rtab_len = W.rtab_len;
     a.units = static_cast<const WaveUnit *>(W.units);
     a.classes = static_cast<const WaveClass *>(W.classes);
     a.jpart = static_cast<float *>(ctx->d_jpart);

@@ -36,14 +36,19 @@
 //    the last value it saw does not cover the slab it needs (then acquires).
 //    Every wait is bounded in time; one that runs out sets an error word,
 //    after which every CTA leaves its loop at the next step.
+//  * Per slab, the directions of a group are listed in five runs by segment
+//    pattern (one segment; two, hand-off along b or c; three, b or c crossed
+//    first), so each run is a branch-free loop; the entry's slot names the
+//    direction's ray states and hand-off buffers.
 //  * Each unit writes the J partial of its (class, direction group) once per
-//    cell: the FP32 sum over its directions (at most 16, in table order).
+//    cell: the FP32 sum over its directions (at most DMAX, in run order).
 //    reduce_kernel sums the partials in fixed order with Kahan compensation.
 //    Results are deterministic.
 //  * The lane's two cells share every segment length and every branch, so the
 //    arithmetic of Eq. (rt) runs as packed FP32x2 instructions on both.
 //  * Arithmetic per (warp, slab), chosen by ballot over the warp's 64 cells:
-//    every kappa below KAP_THIN (series only), every kappa at or above
+//    every kappa below KAP_THIN (series only, as a polynomial in the segment
+//    length with per-cell coefficients), every kappa at or above
 //    KAP_THICK (hardware exponential only), else both with a per-segment
 //    select (series below x = 1/4).  The series path deposits ds phi(x)
 //    directly, so kappa = 0 needs no special case; the exponential path
@@ -66,18 +71,30 @@ struct WaveClass {
 // A unit of the wavefront: one CTA tile of one (grid, class, direction group).
 struct WaveUnit {
     int cls;                  // WaveClass index
-    int d0, nd;               // first entry in the direction table, count (<= DMAX)
+    int grp, nd;              // direction group (index over all classes), its directions (<= DMAX)
     int tb, tc;               // tile origin in canonical columns
     int up_b, up_c;           // unit index of the upstream tiles along b and c; -1 at the box edge
     int pad;
+    long long tab;            // first float4 of the group's run table
     long long jpart;          // first element of the J partial this unit writes
     long long eb, ec;         // first float of its B-face and C-face output buffers
 };
 
+// Run table of a direction group: per slab a block of 1 + 4 nd float4.  The
+// header (int4) holds the ends of five runs of entries, by segment pattern:
+// one segment; two with the hand-off along b; two along c; three, b first;
+// three, c first.  Entry = 4 float4: (ds_k, ds_k, ds_k^2, ds_k^2) for the
+// segments k = 1..3 (zero past the pattern's count), then (|n_a|, |n_a|,
+// direction slot as int bits, 0).  Packed pairs load straight into the
+// register pairs of the FP32x2 arithmetic.
+constexpr int WV_ENT = 4;   // float4 per entry
+
+__host__ __device__ constexpr int wv_block(int nd) { return 1 + WV_ENT * nd; }
+
 struct WaveArgs {
     const float2 *field0, *field1, *field2;   // (kappa, S or eps), sweep-axis layouts, one bin
-    const float4 *segs;       // per (direction, slab): +-ds1, +-ds2, +-ds3, |n_a| (sign bits: code)
-    const long long *seg_off; // per direction: first entry of its slab table
+    const float4 *rtab;       // run tables of the direction groups
+    long long rtab_len;       // float4 count (checked builds)
     const WaveUnit *units;    // in ticket order
     const WaveClass *classes;
     float *jpart;
@@ -190,9 +207,24 @@ __device__ __forceinline__ bool wv_ok(bool cond, int *err)
 #endif
 }
 
-// Values of the lane's two cells (x: the first row, y: the second) for the
-// current slab.  The two cells see the same segment lengths, so each FP32
-// operation of Eq. (rt) runs on both at once as one packed FP32x2 instruction.
+__device__ __forceinline__ float2 f2s(float v) { return make_float2(v, v); }
+
+// Per-cell values of a pair of the lane's cells (x: the first row, y: the
+// second) for the current slab.  The two cells see the same segment lengths,
+// so each FP32 operation of Eq. (rt) runs on both at once as one packed FP32x2
+// instruction.
+//
+// Thin path (every kappa < KAP_THIN): the deposit coefficient of a segment,
+// ds phi(kappa ds) with phi to x^4, written as a polynomial in ds whose
+// coefficients are the cell's: ds + ds^2 (c1 + ds (c2 + ds (c3 + ds c4))),
+// c1 = -kappa/2, c2 = kappa^2/6, c3 = -kappa^3/24, c4 = kappa^4/120.
+struct WvThin {
+    float2 c1, c2, c3, c4;
+    float2 nkap;   // -kappa
+    float2 E;      // kappa S (S inputs) or eps: emission per unit length
+};
+
+// Mixed and thick paths.
 struct WvCell2 {
     float2 nkap;  // -kappa per cell width (0 outside the box)
     float2 kap;   // kappa
@@ -202,49 +234,75 @@ struct WvCell2 {
     float2 rk;    // 1/kappa (0 where kappa = 0)
 };
 
-__device__ __forceinline__ float2 f2s(float v) { return make_float2(v, v); }
-
-// One segment of length ds with incoming intensities I (both cells):
-// accumulates the deposits into A and returns the outgoing intensities.
-// Thin / mixed deposits are ds phi(x); the thick path deposits 1 - e^-x
-// (scaled by 1/kappa per cell).
-template <int MODE, bool FIRST>
-__device__ __forceinline__ float2 wv_seg(const WvCell2 &c, float2 I, float ds, float2 &A)
+// Coefficient of one segment for both cells, from its table pair w = (ds, ds,
+// ds^2, ds^2); independent of the intensities, so the coefficients of a
+// direction's segments are evaluated side by side.  Thin and mixed paths:
+// ds phi(x); thick path: 1 - e^-x (the cell's deposits are scaled by 1/kappa
+// at the end).
+__device__ __forceinline__ float2 wv_coef(const WvThin &c, const float4 &w)
 {
-    const float2 dsv = f2s(ds);
+    const float2 ds = make_float2(w.x, w.y), ds2 = make_float2(w.z, w.w);
+    float2 q = __ffma2_rn(c.c4, ds, c.c3);
+    q = __ffma2_rn(q, ds, c.c2);
+    q = __ffma2_rn(q, ds, c.c1);
+    return __ffma2_rn(q, ds2, ds);
+}
+
+template <int MODE> __device__ __forceinline__ float2 wv_coef(const WvCell2 &c, const float4 &w)
+{
+    const float2 dsv = make_float2(w.x, w.y);
     if (MODE == MODE_THICK) {
         const float2 arg = __fmul2_rn(c.k2, dsv);
         const float2 e = make_float2(wv_ex2(arg.x), wv_ex2(arg.y));
-        const float2 h = __ffma2_rn(e, f2s(-1.0f), f2s(1.0f));
-        A = FIRST ? __fmul2_rn(I, h) : __ffma2_rn(I, h, A);
-        // I_out = I + (S - I)(1 - e^-x)
-        return __ffma2_rn(__ffma2_rn(I, f2s(-1.0f), c.S), h, I);
+        return __ffma2_rn(e, f2s(-1.0f), f2s(1.0f));
     }
     const float2 x = __fmul2_rn(c.kap, dsv);
-    float2 g;
-    if (MODE == MODE_THIN) {
-        float2 q = __ffma2_rn(x, f2s(1.0f / 120.0f), f2s(-1.0f / 24.0f));
-        q = __ffma2_rn(x, q, f2s(1.0f / 6.0f));
-        q = __ffma2_rn(x, q, f2s(-0.5f));
-        q = __ffma2_rn(x, q, f2s(1.0f));
-        g = __fmul2_rn(dsv, q);
-    } else {
-        float2 q = __ffma2_rn(x, f2s(-1.0f / 720.0f), f2s(1.0f / 120.0f));
-        q = __ffma2_rn(x, q, f2s(-1.0f / 24.0f));
-        q = __ffma2_rn(x, q, f2s(1.0f / 6.0f));
-        q = __ffma2_rn(x, q, f2s(-0.5f));
-        q = __ffma2_rn(x, q, f2s(1.0f));
-        const float2 gs = __fmul2_rn(dsv, q);
-        const float2 arg = __fmul2_rn(c.k2, dsv);
-        const float2 e = make_float2(wv_ex2(arg.x), wv_ex2(arg.y));
-        const float2 gm = __fmul2_rn(__ffma2_rn(e, f2s(-1.0f), f2s(1.0f)), c.rk);
-        g.x = x.x < X_SERIES ? gs.x : gm.x;
-        g.y = x.y < X_SERIES ? gs.y : gm.y;
-    }
+    float2 q = __ffma2_rn(x, f2s(-1.0f / 720.0f), f2s(1.0f / 120.0f));
+    q = __ffma2_rn(x, q, f2s(-1.0f / 24.0f));
+    q = __ffma2_rn(x, q, f2s(1.0f / 6.0f));
+    q = __ffma2_rn(x, q, f2s(-0.5f));
+    q = __ffma2_rn(x, q, f2s(1.0f));
+    const float2 gs = __fmul2_rn(dsv, q);
+    const float2 arg = __fmul2_rn(c.k2, dsv);
+    const float2 e = make_float2(wv_ex2(arg.x), wv_ex2(arg.y));
+    const float2 gm = __fmul2_rn(__ffma2_rn(e, f2s(-1.0f), f2s(1.0f)), c.rk);
+    return make_float2(x.x < X_SERIES ? gs.x : gm.x, x.y < X_SERIES ? gs.y : gm.y);
+}
+
+// One segment with coefficient g and incoming intensities I (both cells):
+// accumulates the deposits I g into A and returns the outgoing intensities,
+// I + (eps - kappa I) ds phi(x) = I + (S - I)(1 - e^-x).
+template <bool FIRST>
+__device__ __forceinline__ float2 wv_seg(const WvThin &c, float2 I, float2 g, float2 &A)
+{
     A = FIRST ? __fmul2_rn(I, g) : __ffma2_rn(I, g, A);
-    // I_out = I + (S - I)(1 - e^-x) = I + (eps - kappa I) ds phi(x)
     return __ffma2_rn(__ffma2_rn(c.nkap, I, c.E), g, I);
 }
+
+template <int MODE, bool FIRST>
+__device__ __forceinline__ float2 wv_seg(const WvCell2 &c, float2 I, float2 g, float2 &A)
+{
+    A = FIRST ? __fmul2_rn(I, g) : __ffma2_rn(I, g, A);
+    if (MODE == MODE_THICK) return __ffma2_rn(__ffma2_rn(I, f2s(-1.0f), c.S), g, I);
+    return __ffma2_rn(__ffma2_rn(c.nkap, I, c.E), g, I);
+}
+
+// Mode dispatch of the two helpers above (the thin path has its own type).
+template <int MODE, class CO> struct WvOps;
+template <> struct WvOps<MODE_THIN, WvThin> {
+    static __device__ __forceinline__ float2 coef(const WvThin &c, const float4 &w) { return wv_coef(c, w); }
+    template <bool F> static __device__ __forceinline__ float2 seg(const WvThin &c, float2 I, float2 g, float2 &A)
+    {
+        return wv_seg<F>(c, I, g, A);
+    }
+};
+template <int MODE> struct WvOps<MODE, WvCell2> {
+    static __device__ __forceinline__ float2 coef(const WvCell2 &c, const float4 &w) { return wv_coef<MODE>(c, w); }
+    template <bool F> static __device__ __forceinline__ float2 seg(const WvCell2 &c, float2 I, float2 g, float2 &A)
+    {
+        return wv_seg<MODE, F>(c, I, g, A);
+    }
+};
 
 __device__ __forceinline__ void wv_sts(unsigned a, float v) { asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory"); }
 __device__ __forceinline__ float wv_lds(unsigned a)
@@ -279,6 +337,8 @@ struct WvXch {
     unsigned bo, bi;   // B-face output / input rows
     unsigned co, ci;   // C-face output / input
     bool b0, b7, c0, c3;
+    int nslot;         // direction slots (checked builds test table slots against it)
+    int *err;
 };
 
 template <int NP> __device__ __forceinline__ void wv_sts_rows(unsigned a, const WvRows<NP> &v)
@@ -308,8 +368,9 @@ template <int NP> __device__ __forceinline__ WvRows<NP> wv_lds_rows(unsigned a)
 
 // Hand-off across a b-plane: each of the lane's rows takes the intensity that
 // leaves the column one step upstream along b (the lane to the left, or the
-// B-face input at bl = 0); lanes at bl = 7 write theirs to the B-face output.
-template <int NP> __device__ __forceinline__ void wv_xb(const WvXch &x, WvRows<NP> &v, int d)
+// B-face input `in` at bl = 0, loaded beforehand); lanes at bl = 7 write
+// theirs to the B-face output.
+template <int NP> __device__ __forceinline__ void wv_xb(const WvXch &x, WvRows<NP> &v, int d, const WvRows<NP> &in)
 {
     constexpr unsigned XBD = 4 * 4 * 2 * NP;   // bytes per direction: 4 lanes x 2 NP rows
     WvRows<NP> n;
@@ -319,7 +380,6 @@ template <int NP> __device__ __forceinline__ void wv_xb(const WvXch &x, WvRows<N
         n.p[i].y = __shfl_up_sync(0xffffffffu, v.p[i].y, 1);
     }
     if (x.b7) wv_sts_rows<NP>(x.bo + XBD * d, v);
-    const WvRows<NP> in = wv_lds_rows<NP>(x.bi + XBD * d);
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
         v.p[i].x = x.b0 ? in.p[i].x : n.p[i].x;
@@ -329,14 +389,13 @@ template <int NP> __device__ __forceinline__ void wv_xb(const WvXch &x, WvRows<N
 
 // Hand-off across a c-plane: each row after the lane's first takes the row
 // before it (registers); the first row takes the last row of the lane one step
-// upstream along c (or the C-face input at cl = 0); lanes at cl = 3 write
-// their last row to the C-face output.
-template <int NP> __device__ __forceinline__ void wv_xc(const WvXch &x, WvRows<NP> &v, int d)
+// upstream along c (or the C-face input `in` at cl = 0, loaded beforehand);
+// lanes at cl = 3 write their last row to the C-face output.
+template <int NP> __device__ __forceinline__ void wv_xc(const WvXch &x, WvRows<NP> &v, int d, float in)
 {
     const float last = v.p[NP - 1].y;
     const float n = __shfl_up_sync(0xffffffffu, last, 8);
     if (x.c3) wv_sts(x.co + 32 * d, last);
-    const float in = wv_lds(x.ci + 32 * d);
 #pragma unroll
     for (int i = NP - 1; i >= 0; --i) {
         v.p[i].y = v.p[i].x;
@@ -344,45 +403,98 @@ template <int NP> __device__ __forceinline__ void wv_xc(const WvXch &x, WvRows<N
     }
 }
 
-// All directions of the unit for one slab, for the lane's 2 NP cells: the ray
-// states (shared memory, rows at rs + 8 NP NT d) are updated in place; returns
-// the cells' sums over the unit's directions of |n_a| times the deposits (at
-// most DMAX directions per unit, summed in FP32 in table order; the units'
-// partials are summed with Kahan compensation by the reduction).
-template <int MODE, int NT, int NP>
-__device__ __forceinline__ WvRows<NP> wv_dirs(const WvCell2 (&c)[NP], unsigned rs, unsigned tab, int nd,
-                                              const WvXch &x)
+template <int NP> __device__ __forceinline__ WvRows<NP> wv_ld_xb(const WvXch &x, int d)
+{
+    return wv_lds_rows<NP>(x.bi + 4 * 4 * 2 * NP * d);
+}
+__device__ __forceinline__ float wv_ld_xc(const WvXch &x, int d) { return wv_lds(x.ci + 32 * d); }
+
+__device__ __forceinline__ float4 wv_lds4(unsigned a)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
+
+// One run of a slab's table: entries [d, d1), all with NS segments and, for
+// NS >= 2, the first hand-off along c (FC) or b.  Each entry's ray states
+// (shared memory, rows at rs + 8 NP NT slot) are updated in place and its
+// |n_a|-weighted deposits added to acc.  The segment coefficients come first
+// (they do not depend on the intensities), then the chain of intensity
+// updates and hand-offs.
+template <int MODE, int NT, int NP, int NS, bool FC, class CO>
+__device__ __forceinline__ void wv_run(const CO (&c)[NP], unsigned rs, unsigned ent, int d, int d1,
+                                       const WvXch &x, WvRows<NP> &acc)
+{
+    using Op = WvOps<MODE, CO>;
+    constexpr unsigned RSD = 8 * NP * NT;   // ray-state bytes per direction slot
+#pragma unroll 1
+    for (; d < d1; ++d) {
+        const unsigned e = ent + 16 * WV_ENT * d;
+        const float4 w3 = wv_lds4(e + 48);
+        int slot = __float_as_int(w3.z);
+#ifdef ART_WAVE_CHECK
+        if (!wv_ok(slot >= 0 && slot < x.nslot, x.err)) slot = 0;
+#endif
+        const float4 w0 = wv_lds4(e);
+        float4 w1 = w0, w2 = w0;
+        if (NS >= 2) w1 = wv_lds4(e + 16);
+        if (NS >= 3) w2 = wv_lds4(e + 32);
+        WvRows<NP> o = wv_lds_rows<NP>(rs + RSD * slot);
+        WvRows<NP> inb;
+        float inc = 0.0f;
+        if (NS == 3 || (NS == 2 && !FC)) inb = wv_ld_xb<NP>(x, slot);
+        if (NS == 3 || (NS == 2 && FC)) inc = wv_ld_xc(x, slot);
+        float2 g1[NP], g2[NP], g3[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            g1[i] = Op::coef(c[i], w0);
+            if (NS >= 2) g2[i] = Op::coef(c[i], w1);
+            if (NS >= 3) g3[i] = Op::coef(c[i], w2);
+        }
+        WvRows<NP> A;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) o.p[i] = Op::template seg<true>(c[i], o.p[i], g1[i], A.p[i]);
+        if (NS >= 2) {
+            if (FC) wv_xc<NP>(x, o, slot, inc);
+            else wv_xb<NP>(x, o, slot, inb);
+#pragma unroll
+            for (int i = 0; i < NP; ++i) o.p[i] = Op::template seg<false>(c[i], o.p[i], g2[i], A.p[i]);
+        }
+        if (NS >= 3) {
+            if (FC) wv_xb<NP>(x, o, slot, inb);
+            else wv_xc<NP>(x, o, slot, inc);
+#pragma unroll
+            for (int i = 0; i < NP; ++i) o.p[i] = Op::template seg<false>(c[i], o.p[i], g3[i], A.p[i]);
+        }
+        wv_sts_rows<NP>(rs + RSD * slot, o);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) acc.p[i] = __ffma2_rn(A.p[i], make_float2(w3.x, w3.y), acc.p[i]);
+    }
+}
+
+// All directions of the unit for one slab (table block at tb), for the lane's
+// 2 NP cells: returns the cells' sums over the unit's directions of |n_a|
+// times the deposits (at most DMAX directions, summed in FP32 in run order;
+// the units' partials are summed with Kahan compensation by the reduction).
+template <int MODE, int NT, int NP, class CO>
+__device__ __forceinline__ WvRows<NP> wv_dirs(const CO (&c)[NP], unsigned rs, unsigned tb, int nd, const WvXch &x)
 {
     WvRows<NP> acc;
 #pragma unroll
     for (int i = 0; i < NP; ++i) acc.p[i] = f2s(0.0f);
-#pragma unroll 1
-    for (int d = 0; d < nd; ++d) {
-        float4 e;
-        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                     : "=f"(e.x), "=f"(e.y), "=f"(e.z), "=f"(e.w)
-                     : "r"(tab + 16 * d));
-        WvRows<NP> o = wv_lds_rows<NP>(rs + 8 * NP * NT * d);
-        WvRows<NP> A;
-#pragma unroll
-        for (int i = 0; i < NP; ++i) o.p[i] = wv_seg<MODE, true>(c[i], o.p[i], fabsf(e.x), A.p[i]);
-        if (__float_as_int(e.y) < 0) {                 // two or more segments
-            const bool fc = __float_as_int(e.x) < 0;   // first hand-off along c
-            if (fc) wv_xc<NP>(x, o, d);
-            else wv_xb<NP>(x, o, d);
-#pragma unroll
-            for (int i = 0; i < NP; ++i) o.p[i] = wv_seg<MODE, false>(c[i], o.p[i], fabsf(e.y), A.p[i]);
-            if (__float_as_int(e.z) < 0) {             // three segments
-                if (fc) wv_xb<NP>(x, o, d);
-                else wv_xc<NP>(x, o, d);
-#pragma unroll
-                for (int i = 0; i < NP; ++i) o.p[i] = wv_seg<MODE, false>(c[i], o.p[i], fabsf(e.z), A.p[i]);
-            }
-        }
-        wv_sts_rows<NP>(rs + 8 * NP * NT * d, o);
-#pragma unroll
-        for (int i = 0; i < NP; ++i) acc.p[i] = __ffma2_rn(A.p[i], f2s(e.w), acc.p[i]);
-    }
+    const float4 hf = wv_lds4(tb);
+    int e1 = __float_as_int(hf.x), e2 = __float_as_int(hf.y), e3 = __float_as_int(hf.z), e4 = __float_as_int(hf.w);
+#ifdef ART_WAVE_CHECK
+    if (!wv_ok(0 <= e1 && e1 <= e2 && e2 <= e3 && e3 <= e4 && e4 <= nd && nd <= x.nslot, x.err))
+        e1 = e2 = e3 = e4 = nd = 0;
+#endif
+    const unsigned ent = tb + 16;
+    wv_run<MODE, NT, NP, 1, false>(c, rs, ent, 0, e1, x, acc);
+    wv_run<MODE, NT, NP, 2, false>(c, rs, ent, e1, e2, x, acc);
+    wv_run<MODE, NT, NP, 2, true>(c, rs, ent, e2, e3, x, acc);
+    wv_run<MODE, NT, NP, 3, false>(c, rs, ent, e3, e4, x, acc);
+    wv_run<MODE, NT, NP, 3, true>(c, rs, ent, e4, nd, x, acc);
     return acc;
 }
 
@@ -396,7 +508,8 @@ template <int WB, int WC, int DMAX, int NP> struct WaveShape {
     static constexpr int XBW = 4 * R;                         // B-face floats per warp and direction
     static constexpr int XB_PAR = (WB + 1) * WC * DMAX * XBW; // floats per parity
     static constexpr int XC_PAR = (WC + 1) * WB * DMAX * 8;
-    static constexpr size_t off_xb = size_t(RT) * DMAX * 16;
+    static constexpr int TABS = wv_block(DMAX);               // float4 per slab of the table ring
+    static constexpr size_t off_xb = size_t(RT) * TABS * 16;
     static constexpr size_t off_xc = off_xb + size_t(2) * XB_PAR * 4;
     static constexpr size_t off_fs = off_xc + size_t(2) * XC_PAR * 4;
     static constexpr size_t off_rs = off_fs + size_t(2) * NT * R * 8;
@@ -405,7 +518,13 @@ template <int WB, int WC, int DMAX, int NP> struct WaveShape {
     static constexpr long long edge_c(int Na) { return (long long)Na * WB * DMAX * 8; }
 };
 
-constexpr int WAVE_PUB = 4;   // slabs between progress publications
+// Slabs between progress publications (each costs the publishing warp a
+// GPU-scope release, and its consumer an acquire).
+#ifndef ART_WAVE_PUB
+#define ART_WAVE_PUB 4
+#endif
+constexpr int WAVE_PUB = ART_WAVE_PUB;
+static_assert(WAVE_PUB >= 1, "publication interval");
 
 template <int WB, int WC, int DMAX, int NP, int MINB>
 __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs p)
@@ -413,13 +532,12 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
     using Sh = WaveShape<WB, WC, DMAX, NP>;
     constexpr int NT = Sh::NT, RT = Sh::RT, R = Sh::R, XBW = Sh::XBW;
     extern __shared__ __align__(16) unsigned char wsm[];
-    float4 *tab = reinterpret_cast<float4 *>(wsm);                  // [RT][DMAX]
+    float4 *tab = reinterpret_cast<float4 *>(wsm);                  // [RT][TABS]: run-table blocks
     float *XB = reinterpret_cast<float *>(wsm + Sh::off_xb);        // [2][WB+1][WC][DMAX][XBW]
     float *XC = reinterpret_cast<float *>(wsm + Sh::off_xc);        // [2][WC+1][WB][DMAX][8]
     float2 *FS = reinterpret_cast<float2 *>(wsm + Sh::off_fs);      // [2][NT][R]: (kappa, src) of the lane's cells
     float *RS = reinterpret_cast<float *>(wsm + Sh::off_rs);        // [DMAX][NT][R]: ray states of its columns
     __shared__ int s_unit;
-    __shared__ long long s_seg[DMAX];   // first table entry of each direction of the unit
     __shared__ long long s_up[2];       // output buffers of the upstream units (B, C)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -461,7 +579,6 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
     float *J0 = p.jpart + U.jpart + (inmask ? jb0 : 0);
     const bool stalled = u == p.stall_unit;
 
-    if (tid < nd) s_seg[tid] = p.seg_off[U.d0 + tid];
     if (tid == 0) s_up[0] = U.up_b >= 0 ? p.units[U.up_b].eb : -1;
     if (tid == 1) s_up[1] = U.up_c >= 0 ? p.units[U.up_c].ec : -1;
     // box-edge inputs carry the boundary intensity in both parities
@@ -492,7 +609,11 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
     // Returns 0 if a wait ran out.
     auto stage = [&](int t) -> int {
         const int s1 = t + 1, rp = t & 1;
-        if (tid < nd && s1 < Na) wv_cp16(tab + (s1 & (RT - 1)) * DMAX + tid, p.segs + s_seg[tid] + s1);
+        if (s1 < Na) {
+            const long long src = U.tab + (long long)s1 * wv_block(nd);
+            for (int q = tid; q < wv_block(nd); q += NT)
+                if (wv_ok(src + q < p.rtab_len, p.err)) wv_cp16(tab + (s1 & (RT - 1)) * Sh::TABS + q, p.rtab + src + q);
+        }
         const int mn = s1 - wb - wc;
         if (mn >= 0 && mn < Na) {
             const long long fa = f0 + (long long)(C.sa > 0 ? mn : Na - 1 - mn) * fslab;
@@ -556,7 +677,7 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
         return ok;
     };
 
-    __syncthreads();   // s_seg, s_up, ray states
+    __syncthreads();   // s_up, ray states
     // A wait that ran out ends the unit: the decision is taken by the barrier
     // itself (__syncthreads_or), so every thread leaves the loop at the same step.
     int bad = stage(-1) ? 0 : 1;
@@ -578,22 +699,16 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
         if (!stage(t)) bad = 1;
         if (m >= 0 && m < Na) {
             const int par = t & 1;
-            WvCell2 c[NP];
+            float2 kap[NP], src[NP];
             bool thin = true, thick = true;
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
                 const float4 f = reinterpret_cast<const float4 *>(FS + (par * NT + tid) * R)[i];
                 const bool i0 = inmask >> (2 * i) & 1, i1 = inmask >> (2 * i + 1) & 1;
-                c[i].kap = make_float2(i0 ? f.x : 0.0f, i1 ? f.z : 0.0f);
-                const float2 src = make_float2(i0 ? f.y : 0.0f, i1 ? f.w : 0.0f);
-                c[i].nkap = make_float2(-c[i].kap.x, -c[i].kap.y);
-                c[i].rk = make_float2(c[i].kap.x > 0.0f ? wv_rcp(c[i].kap.x) : 0.0f,
-                                      c[i].kap.y > 0.0f ? wv_rcp(c[i].kap.y) : 0.0f);
-                c[i].E = p.field_form ? src : __fmul2_rn(c[i].kap, src);
-                c[i].S = p.field_form ? __fmul2_rn(src, c[i].rk) : src;
-                c[i].k2 = __fmul2_rn(c[i].kap, f2s(-1.4426950408889634f));
-                thin = thin && c[i].kap.x < KAP_THIN && c[i].kap.y < KAP_THIN;
-                thick = thick && c[i].kap.x >= KAP_THICK && c[i].kap.y >= KAP_THICK;
+                kap[i] = make_float2(i0 ? f.x : 0.0f, i1 ? f.z : 0.0f);
+                src[i] = make_float2(i0 ? f.y : 0.0f, i1 ? f.w : 0.0f);
+                thin = thin && kap[i].x < KAP_THIN && kap[i].y < KAP_THIN;
+                thick = thick && kap[i].x >= KAP_THICK && kap[i].y >= KAP_THICK;
             }
             WvXch x;
             x.bo = xb0 + 4 * (par * Sh::XB_PAR + ((wb + 1) * WC + wc) * DMAX * XBW + R * cl);
@@ -604,17 +719,43 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
             x.b7 = bl == 7;
             x.c0 = cl == 0;
             x.c3 = cl == 3;
-            const unsigned tb = tab0 + 16 * (m & (RT - 1)) * DMAX;
+            x.nslot = DMAX;
+            x.err = p.err;
+            const unsigned tb = tab0 + 16 * (m & (RT - 1)) * Sh::TABS;
             const bool all_thin = __all_sync(0xffffffffu, thin), all_thick = __all_sync(0xffffffffu, thick);
             WvRows<NP> js;
             if (all_thin) {
-                js = wv_dirs<MODE_THIN, NT, NP>(c, rs0, tb, nd, x);
-            } else if (all_thick) {
-                js = wv_dirs<MODE_THICK, NT, NP>(c, rs0, tb, nd, x);
+                WvThin c[NP];
 #pragma unroll
-                for (int i = 0; i < NP; ++i) js.p[i] = __fmul2_rn(js.p[i], c[i].rk);
+                for (int i = 0; i < NP; ++i) {
+                    const float2 k = kap[i], kk = __fmul2_rn(k, k);
+                    c[i].c1 = __fmul2_rn(k, f2s(-0.5f));
+                    c[i].c2 = __fmul2_rn(kk, f2s(1.0f / 6.0f));
+                    c[i].c3 = __fmul2_rn(__fmul2_rn(kk, k), f2s(-1.0f / 24.0f));
+                    c[i].c4 = __fmul2_rn(__fmul2_rn(kk, kk), f2s(1.0f / 120.0f));
+                    c[i].nkap = make_float2(-k.x, -k.y);
+                    c[i].E = p.field_form ? src[i] : __fmul2_rn(k, src[i]);
+                }
+                js = wv_dirs<MODE_THIN, NT, NP>(c, rs0, tb, nd, x);
             } else {
-                js = wv_dirs<MODE_MIXED, NT, NP>(c, rs0, tb, nd, x);
+                WvCell2 c[NP];
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    c[i].kap = kap[i];
+                    c[i].nkap = make_float2(-kap[i].x, -kap[i].y);
+                    c[i].rk = make_float2(kap[i].x > 0.0f ? wv_rcp(kap[i].x) : 0.0f,
+                                          kap[i].y > 0.0f ? wv_rcp(kap[i].y) : 0.0f);
+                    c[i].E = p.field_form ? src[i] : __fmul2_rn(kap[i], src[i]);
+                    c[i].S = p.field_form ? __fmul2_rn(src[i], c[i].rk) : src[i];
+                    c[i].k2 = __fmul2_rn(kap[i], f2s(-1.4426950408889634f));
+                }
+                if (all_thick) {
+                    js = wv_dirs<MODE_THICK, NT, NP>(c, rs0, tb, nd, x);
+#pragma unroll
+                    for (int i = 0; i < NP; ++i) js.p[i] = __fmul2_rn(js.p[i], c[i].rk);
+                } else {
+                    js = wv_dirs<MODE_MIXED, NT, NP>(c, rs0, tb, nd, x);
+                }
             }
             if (jl_ok) {
                 float *Jm = J0 + (long long)m * jstep;
