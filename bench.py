@@ -110,6 +110,7 @@ def parse():
     p.add_argument("--nside", type=int, default=None, help="--profile-case sweep: N_side")
     p.add_argument("--variant", type=int, default=0, help="--profile-case sweep: kernel variant (0: default)")
     p.add_argument("--reps", type=int, default=3, help="--profile-case: repetitions")
+    p.add_argument("--bin", type=int, default=None, help="--profile-case sweep: one bin of a multi-bin workload")
     p.add_argument("--train", action="store_true", help="--profile-case net: also time training steps")
     p.add_argument("--myr", type=float, default=30.0, help="--profile-case thermal: evolve to this time")
     p.add_argument("--no-autotune", action="store_true", help="keep the default kernel variant")
@@ -1145,8 +1146,11 @@ def profile_case(args):
         else:
             n, nside, nb = args.n or 128, args.nside or 8, 1
             c = wl.grf(n, nside, seed=3)
-        k = torch.as_tensor(c.kappa.astype(np.float32), device="cuda")
-        s = torch.as_tensor(c.src.astype(np.float32), device="cuda")
+        kap, src = c.kappa, c.src
+        if args.bin is not None and nb > 1:   # one bin of a multi-bin workload
+            kap, src, nb = kap[args.bin], src[args.bin], 1
+        k = torch.as_tensor(kap.astype(np.float32), device="cuda")
+        s = torch.as_tensor(src.astype(np.float32), device="cuda")
         sw = art.ArtSweep(c.shape, nside, nb, variant=args.variant)
         sw.set_fields(k, s)
         Jin = torch.empty_like(k)
@@ -1156,8 +1160,14 @@ def profile_case(args):
         if sw.check() != art.ART_OK:
             raise RuntimeError("sweep reported an error")
         st = sw.stats
-        out.update(n=n, nside=nside, variant=int(st.variant), units=int(st.ctas_per_launch),
+        out.update(n=n, nside=nside, bins=nb, variant=int(st.variant), units=int(st.ctas_per_launch),
                    segments=int(st.segments))
+        if int(st.variant) >= 16:
+            cnt = sw.wave_counters()   # nonzero in ART_WAVE_STATS builds only
+            if cnt["unit_cycles"]:
+                out.update(barrier_fraction=round(cnt["barrier_cycles"] / cnt["unit_cycles"], 4),
+                           poll_fraction=round(cnt["poll_cycles"] / cnt["unit_cycles"], 4),
+                           polls=cnt["polls"])
         sw.close()
     elif args.profile_case == "net":
         # the surrogate network on one grid: forward passes (and training steps)

@@ -766,6 +766,18 @@ class ArtSweep:
         """art_sweep_set_wait: bound of the wavefront sweep's waits, and the stalled-unit test hook."""
         _check(self._ctx, load().art_sweep_set_wait(self._ctx, float(seconds), int(stall_unit)))
 
+    def wave_counters(self) -> dict:
+        """Counters of a library built with ART_WAVE_STATS=1 (a profiling aid): warp cycles at the
+        wavefront sweep's step barriers and in its units, lane-0 cycles in the poll loops and the
+        number of polls, summed since the last call (all zero in other builds)."""
+        lib = load()
+        lib.art_wave_counters.argtypes = [C.c_void_p, C.POINTER(C.c_longlong)]
+        lib.art_wave_counters.restype = C.c_int
+        out = (C.c_longlong * 4)()
+        _check(self._ctx, lib.art_wave_counters(self._ctx, out))
+        return dict(barrier_cycles=int(out[0]), unit_cycles=int(out[1]), poll_cycles=int(out[2]),
+                    polls=int(out[3]))
+
     def sweep_stream(self, kappas, srcs, J=None, J_in=None, gamma=None, stream=None):
         """Sweeps of len(kappas) field sets held in host memory (art_sweep_stream): the copies of
         the next and the previous set overlap the current sweep.  kappas, srcs: lists of host

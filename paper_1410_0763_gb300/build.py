@@ -50,6 +50,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if os.environ.get("ART_WAVE_CHECK") == "1":
         # the wavefront kernel tests every global index before it is used (slower; for checking runs)
         common += ["-DART_WAVE_CHECK"]
+    if os.environ.get("ART_WAVE_STATS") == "1":
+        # the wavefront kernel counts its barrier and poll cycles (art_wave_counters; for profiling runs)
+        common += ["-DART_WAVE_STATS"]
     # extra preprocessor definitions for tuning builds (e.g. "-DART_WAVE_PUB=8")
     common += [d for d in os.environ.get("ART_NVCC_DEFINES", "").split() if d.startswith("-D")]
     if verbose:

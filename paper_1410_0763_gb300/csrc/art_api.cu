@@ -458,15 +458,7 @@ int pick_wave(const art_ctx *ctx)
                 ++cnt[frame_of(&xyz[3 * d], ctx->opt.tie_tol).cls];
         for (int c = 0; c < 24; ++c) maxc = std::max(maxc, cnt[c]);
     }
-    int best = -1;
-    for (int w = 0; w < art_wave_variants(); ++w) {
-        const int dm = art_wave_dmax(w);
-        if (dm >= maxc && (best < 0 || dm < art_wave_dmax(best))) best = w;
-    }
-    if (best < 0)
-        for (int w = 0; w < art_wave_variants(); ++w)
-            if (best < 0 || art_wave_dmax(w) > art_wave_dmax(best)) best = w;
-    return best;
+    return art_wave_default(maxc);
 }
 
 template <typename real> art_status do_sweep(art_ctx *ctx, real *J, real *Jin, real *gam, cudaStream_t st)

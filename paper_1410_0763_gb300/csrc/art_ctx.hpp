@@ -55,6 +55,7 @@ struct art_wave_state {
     long long rtab_len = 0;     // float4 count
     float *edge = nullptr;      // edge intensities handed between CTA tiles
     int *flags = nullptr;       // [0] error word, [1] ticket, then per-unit progress flags
+    long long *stats = nullptr; // inside the flags allocation: counters of ART_WAVE_STATS builds
     size_t flag_bytes = 0;
     long long edge_floats = 0, jpart_floats = 0, bytes = 0;
     long long wait_ns = 2000000000LL;   // bound of every wait in the kernel
@@ -137,6 +138,7 @@ art_status art_internal_layout(art_ctx *ctx, const void *kappa, const void *src,
 // wavefront sweep (art_wave.cu)
 int art_wave_variants();
 int art_wave_dmax(int w);
+int art_wave_default(int maxc);   // default shape for classes of at most maxc directions
 void art_wave_free(art_ctx *ctx);
 art_status art_wave_setup(art_ctx *ctx, int w);
 art_status art_wave_launch(art_ctx *ctx, const float2 *f0, const float2 *f1, const float2 *f2, float i_bc,

@@ -72,7 +72,8 @@ const WVariant kWave[] = {
     ART_WV(2, 2, 20, 1, 5),   // 16 x 16 columns, 20 slots: N_side 8 classes in 2 groups
     ART_WV(2, 2, 16, 2, 4),   // four rows per lane: 16 x 32 columns, 4 warps
     ART_WV(2, 1, 16, 2, 8),   // four rows per lane: 16 x 16 columns, 2 warps
-    ART_WV(2, 2, 12, 2, 4),   // four rows per lane, 12 slots
+    ART_WV(2, 2, 12, 2, 4),   // four rows per lane, 12 slots (the default from N_side 3 up)
+    ART_WV(2, 2, 17, 2, 3),   // four rows per lane, 17 slots: N_side 8 classes in 2 groups
 };
 #undef ART_WV
 const int kNumWave = int(sizeof(kWave) / sizeof(kWave[0]));
@@ -173,6 +174,8 @@ void build_wave(const art_ctx *ctx, const WVariant &v, WaveHost &t)
             C.Na = dims[f0.a];
             C.Nb = dims[f0.b];
             C.Nc = dims[f0.c];
+            C.pub = 1;
+            while (C.pub * 2 <= std::min(WAVE_PUB, C.Na / 16)) C.pub *= 2;
             C.cell_off = gh.cell_off;
             C.stride_a = strides[f0.a];
             C.stride_b = strides[f0.b];
@@ -307,6 +310,10 @@ bool wave_tables_ok(const WaveHost &t, const WVariant &v, std::string &why)
             return false;
         }
         const WaveClass &C = t.classes[u.cls];
+        if (C.pub < 1 || (C.pub & (C.pub - 1)) || C.pub > WAVE_PUB) {
+            why = "unit " + std::to_string(i) + ": publication interval";
+            return false;
+        }
         if (u.tab < 0 || u.tab + (long long)C.Na * wv_block(u.nd) > (long long)t.rtab.size()) {
             why = "unit " + std::to_string(i) + ": run table range";
             return false;
@@ -348,6 +355,17 @@ bool wave_tables_ok(const WaveHost &t, const WVariant &v, std::string &why)
 }  // namespace
 
 int art_wave_variants() { return kNumWave; }
+
+// Default shape for classes of at most maxc directions: 2 x 2 warps with four
+// rows per lane and 12 slots (the fastest measured on GB300 at N_side 4 and
+// 8), or with 4 slots and two rows per lane when no class has more than 4.
+int art_wave_default(int maxc)
+{
+    const int want_dmax = maxc <= 4 ? 4 : 12, want_np = maxc <= 4 ? 1 : 2;
+    for (int w = 0; w < kNumWave; ++w)
+        if (kWave[w].wb == 2 && kWave[w].wc == 2 && kWave[w].dmax == want_dmax && kWave[w].np == want_np) return w;
+    return 0;
+}
 
 // Direction slots of wave variant w (0 if out of range).
 int art_wave_dmax(int w) { return w >= 0 && w < kNumWave ? kWave[w].dmax : 0; }
@@ -398,7 +416,8 @@ art_status art_wave_setup(art_ctx *ctx, int w)
     const size_t ub = t.units.size() * sizeof(WaveUnit), cb = t.classes.size() * sizeof(WaveClass);
     const size_t sb = std::max<size_t>(16, t.rtab.size() * sizeof(float4));
     const size_t eb = std::max<size_t>(16, (size_t)t.edge_floats * sizeof(float));
-    const size_t fb = (size_t(W.n_units) * (v.wb + v.wc) + 2) * sizeof(int);
+    // error word, ticket, progress flags, then (8-byte aligned) four counters of ART_WAVE_STATS builds
+    const size_t fb = ((size_t(W.n_units) * (v.wb + v.wc) + 2) * sizeof(int) + 7) / 8 * 8 + 4 * sizeof(long long);
     struct {
         void **p;
         size_t b;
@@ -414,7 +433,8 @@ art_status art_wave_setup(art_ctx *ctx, int w)
         W.bytes += (long long)a.b;
         ctx->dev_bytes += (long long)a.b;
     }
-    W.flag_bytes = fb;
+    W.flag_bytes = fb - 4 * sizeof(long long);   // cleared before every launch (the counters are not)
+    W.stats = reinterpret_cast<long long *>(reinterpret_cast<char *>(W.flags) + W.flag_bytes);
     WCK(ctx, cudaMemcpy(W.units, t.units.data(), ub, cudaMemcpyHostToDevice));
     WCK(ctx, cudaMemcpy(W.classes, t.classes.data(), cb, cudaMemcpyHostToDevice));
     if (!t.rtab.empty()) WCK(ctx, cudaMemcpy(W.rtab, t.rtab.data(), t.rtab.size() * sizeof(float4), cudaMemcpyHostToDevice));
@@ -452,6 +472,7 @@ art_status art_wave_launch(art_ctx *ctx, const float2 *f0, const float2 *f1, con
     a.wait_ns = W.wait_ns;
     a.edge_floats = W.edge_floats;
     a.jpart_floats = W.jpart_floats;
+    a.stats = W.stats;
     if (W.n_units == 0) return ART_OK;
     WCK(ctx, v.launch(a, W.n_units, st));
     return ART_OK;
@@ -479,5 +500,21 @@ art_status art_wave_status_async(art_ctx *ctx, int *host, cudaStream_t st)
     *host = 0;
     if (!W.on) return ART_OK;
     WCK(ctx, cudaMemcpyAsync(host, W.flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    return ART_OK;
+}
+
+// Counters of a build with ART_WAVE_STATS (a profiling aid, not part of the
+// C ABI): cycles warps spent at the step barriers, cycles in their units,
+// cycles of lane 0 in the poll loops and the number of polls, summed over the
+// launches since the last call; read and cleared.  Zeros in other builds.
+extern "C" art_status art_wave_counters(art_ctx *ctx, long long *out)
+{
+    if (!ctx || !out) return ART_E_INVALID;
+    for (int i = 0; i < 4; ++i) out[i] = 0;
+    art_wave_state &W = ctx->wave;
+    if (!W.on) return ART_OK;
+    WCK(ctx, cudaDeviceSynchronize());
+    WCK(ctx, cudaMemcpy(out, W.stats, 4 * sizeof(long long), cudaMemcpyDeviceToHost));
+    WCK(ctx, cudaMemset(W.stats, 0, 4 * sizeof(long long)));
     return ART_OK;
 }

@@ -14,13 +14,13 @@
 //    kind 1 from the ray that enters the slab in its own column, kind 2 from
 //    the ray one column upstream along the axis crossed first, kind 3 from the
 //    diagonal neighbour.
-//  * A warp owns an 8 (b) x 8 (c) tile of ray columns and, at each step, one
-//    slab of it; a lane owns two columns (two neighbouring c rows), so it
-//    marches two independent cells per direction.  The intensity handed from a
-//    column to its downstream neighbour moves inside the lane (between its two
-//    rows), by a warp shuffle, through shared memory at the warp's edges, or
-//    through global memory at the CTA's edges.  The intensity of the ray that
-//    sits in each column, per direction, is kept in shared memory between
+//  * A warp owns an 8 (b) x 8 NP (c) tile of ray columns and, at each step,
+//    one slab of it; a lane owns 2 NP columns (neighbouring c rows, in NP
+//    pairs), so it marches 2 NP cells per direction.  The intensity handed
+//    from a column to its downstream neighbour moves inside the lane (between
+//    its rows), by a warp shuffle, through shared memory at the warp's edges,
+//    or through global memory at the CTA's edges.  The intensity of the ray
+//    that sits in each column, per direction, is kept in shared memory between
 //    slabs, so the direction loop stays rolled (small code).
 //  * A CTA owns WB x WC warp tiles.  Warp (wb, wc) handles slab t - wb - wc at
 //    step t, so everything it receives from the warps upstream of it was
@@ -44,9 +44,9 @@
 //    cell: the FP32 sum over its directions (at most DMAX, in run order).
 //    reduce_kernel sums the partials in fixed order with Kahan compensation.
 //    Results are deterministic.
-//  * The lane's two cells share every segment length and every branch, so the
-//    arithmetic of Eq. (rt) runs as packed FP32x2 instructions on both.
-//  * Arithmetic per (warp, slab), chosen by ballot over the warp's 64 cells:
+//  * The two cells of a pair share every segment length, so the arithmetic of
+//    Eq. (rt) runs as packed FP32x2 instructions on both.
+//  * Arithmetic per (warp, slab), chosen by ballot over the warp's cells:
 //    every kappa below KAP_THIN (series only, as a polynomial in the segment
 //    length with per-cell coefficients), every kappa at or above
 //    KAP_THICK (hardware exponential only), else both with a per-segment
@@ -63,7 +63,7 @@ namespace art {
 struct WaveClass {
     int a, sa, sb, sc;
     int Na, Nb, Nc;
-    int pad;
+    int pub;                  // slabs between progress publications (a power of two)
     long long cell_off;       // first cell of the grid in the concatenated field arrays
     long long stride_a, stride_b, stride_c;   // natural-layout strides of axes a, b, c
 };
@@ -109,14 +109,17 @@ struct WaveArgs {
     long long wait_ns;        // bound of every wait
     long long edge_floats;    // size of the edge buffer (checked builds)
     long long jpart_floats;   // size of the partials (checked builds)
+    long long *stats;         // counters of ART_WAVE_STATS builds: barrier, unit, poll-loop cycles, polls
 };
 
 // Thresholds of the per-warp arithmetic choice.  Series of phi(x) =
 // (1 - e^-x)/x: to x^4 in the thin path (x <= sqrt(3) KAP_THIN = 0.173,
-// truncation < 2.2e-7 relative), to x^5 in the mixed path below x = 1/4
+// truncation < 2.2e-7 relative), to x^6 in the second thin path (x <= sqrt(3)
+// KAP_THIN6 = 0.433: < 7.1e-8), to x^5 in the mixed path below x = 1/4
 // (< 6e-8).  Exponential path: 1 - ex2.approx(-x log2 e), whose absolute error
 // (~2^-22) is below 2e-6 of a cell's deposit when kappa >= KAP_THICK.
 constexpr float KAP_THIN = 0.1f;
+constexpr float KAP_THIN6 = 0.25f;
 constexpr float KAP_THICK = 0.5f;
 constexpr float X_SERIES = 0.25f;
 constexpr int MODE_THIN = 0, MODE_MIXED = 1, MODE_THICK = 2;
@@ -178,17 +181,27 @@ __device__ __forceinline__ void wv_cp_wait()
 // earlier, until it reaches `target` or the wait runs out (or another CTA
 // reported an error); a fence then makes the read that saw it an acquire.
 // Returns the value seen, or -1 if the wait ran out.
-__device__ __forceinline__ int wv_wait(const int *flag, int target, int v, const WaveArgs &p)
+__device__ __forceinline__ int wv_wait(const int *flag, int target, int v, const WaveArgs &p, long long *st)
 {
     if (v < target) {
         const long long t0 = wv_now();
+#ifdef ART_WAVE_STATS
+        const long long c0 = clock64();
+#endif
         for (;;) {
             __nanosleep(64);
+#ifdef ART_WAVE_STATS
+            ++st[1];
+#endif
             v = wv_ld_relaxed(flag);
             if (v >= target) break;
             if (wv_ld_relaxed(p.err) != 0 || wv_now() - t0 > p.wait_ns) return -1;
         }
+#ifdef ART_WAVE_STATS
+        st[0] += clock64() - c0;
+#endif
     }
+    (void)st;
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
     return v;
 }
@@ -214,12 +227,12 @@ __device__ __forceinline__ float2 f2s(float v) { return make_float2(v, v); }
 // so each FP32 operation of Eq. (rt) runs on both at once as one packed FP32x2
 // instruction.
 //
-// Thin path (every kappa < KAP_THIN): the deposit coefficient of a segment,
-// ds phi(kappa ds) with phi to x^4, written as a polynomial in ds whose
-// coefficients are the cell's: ds + ds^2 (c1 + ds (c2 + ds (c3 + ds c4))),
-// c1 = -kappa/2, c2 = kappa^2/6, c3 = -kappa^3/24, c4 = kappa^4/120.
-struct WvThin {
-    float2 c1, c2, c3, c4;
+// Thin paths (every kappa < KAP_THIN, K = 4; every kappa < KAP_THIN6, K = 6):
+// the deposit coefficient of a segment, ds phi(kappa ds) with phi to x^K,
+// written as a polynomial in ds whose coefficients are the cell's:
+// ds + ds^2 (c_1 + ds (c_2 + ... + ds c_K)), c_k = (-kappa)^k / (k + 1)!.
+template <int K> struct WvThin {
+    float2 c[K];   // c_1 .. c_K
     float2 nkap;   // -kappa
     float2 E;      // kappa S (S inputs) or eps: emission per unit length
 };
@@ -239,13 +252,31 @@ struct WvCell2 {
 // direction's segments are evaluated side by side.  Thin and mixed paths:
 // ds phi(x); thick path: 1 - e^-x (the cell's deposits are scaled by 1/kappa
 // at the end).
-__device__ __forceinline__ float2 wv_coef(const WvThin &c, const float4 &w)
+template <int K> __device__ __forceinline__ float2 wv_coef(const WvThin<K> &c, const float4 &w)
 {
     const float2 ds = make_float2(w.x, w.y), ds2 = make_float2(w.z, w.w);
-    float2 q = __ffma2_rn(c.c4, ds, c.c3);
-    q = __ffma2_rn(q, ds, c.c2);
-    q = __ffma2_rn(q, ds, c.c1);
+    float2 q = __ffma2_rn(c.c[K - 1], ds, c.c[K - 2]);
+#pragma unroll
+    for (int k = K - 3; k >= 0; --k) q = __ffma2_rn(q, ds, c.c[k]);
     return __ffma2_rn(q, ds2, ds);
+}
+
+// The coefficients c_1 .. c_K of a pair of cells.
+template <int K> __device__ __forceinline__ WvThin<K> wv_thin(float2 k, float2 src, int field_form)
+{
+    constexpr float inv_fact[7] = {1.0f, 0.5f, 1.0f / 6.0f, 1.0f / 24.0f, 1.0f / 120.0f, 1.0f / 720.0f,
+                                   1.0f / 5040.0f};   // 1 / (j + 1)!
+    WvThin<K> c;
+    const float2 nk = make_float2(-k.x, -k.y);
+    float2 pw = nk;   // (-kappa)^j
+#pragma unroll
+    for (int j = 1; j <= K; ++j) {
+        c.c[j - 1] = __fmul2_rn(pw, f2s(inv_fact[j]));
+        pw = __fmul2_rn(pw, nk);
+    }
+    c.nkap = nk;
+    c.E = field_form ? src : __fmul2_rn(k, src);
+    return c;
 }
 
 template <int MODE> __device__ __forceinline__ float2 wv_coef(const WvCell2 &c, const float4 &w)
@@ -272,8 +303,8 @@ template <int MODE> __device__ __forceinline__ float2 wv_coef(const WvCell2 &c, 
 // One segment with coefficient g and incoming intensities I (both cells):
 // accumulates the deposits I g into A and returns the outgoing intensities,
 // I + (eps - kappa I) ds phi(x) = I + (S - I)(1 - e^-x).
-template <bool FIRST>
-__device__ __forceinline__ float2 wv_seg(const WvThin &c, float2 I, float2 g, float2 &A)
+template <bool FIRST, int K>
+__device__ __forceinline__ float2 wv_seg(const WvThin<K> &c, float2 I, float2 g, float2 &A)
 {
     A = FIRST ? __fmul2_rn(I, g) : __ffma2_rn(I, g, A);
     return __ffma2_rn(__ffma2_rn(c.nkap, I, c.E), g, I);
@@ -289,9 +320,10 @@ __device__ __forceinline__ float2 wv_seg(const WvCell2 &c, float2 I, float2 g, f
 
 // Mode dispatch of the two helpers above (the thin path has its own type).
 template <int MODE, class CO> struct WvOps;
-template <> struct WvOps<MODE_THIN, WvThin> {
-    static __device__ __forceinline__ float2 coef(const WvThin &c, const float4 &w) { return wv_coef(c, w); }
-    template <bool F> static __device__ __forceinline__ float2 seg(const WvThin &c, float2 I, float2 g, float2 &A)
+template <int K> struct WvOps<MODE_THIN, WvThin<K>> {
+    static __device__ __forceinline__ float2 coef(const WvThin<K> &c, const float4 &w) { return wv_coef(c, w); }
+    template <bool F>
+    static __device__ __forceinline__ float2 seg(const WvThin<K> &c, float2 I, float2 g, float2 &A)
     {
         return wv_seg<F>(c, I, g, A);
     }
@@ -352,6 +384,27 @@ template <int NP> __device__ __forceinline__ void wv_sts_rows(unsigned a, const 
     }
 }
 
+// The same stores, made by the lanes whose flag is set (a predicated store:
+// no branch in the direction loop).
+template <int NP> __device__ __forceinline__ void wv_sts_rows_if(bool f, unsigned a, const WvRows<NP> &v)
+{
+    if (NP == 1) {
+        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q st.shared.v2.f32 [%1], {%2, %3};\n\t}"
+                     ::"r"((int)f), "r"(a), "f"(v.p[0].x), "f"(v.p[0].y)
+                     : "memory");
+    } else {
+        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q st.shared.v4.f32 [%1], {%2, %3, %4, %5};\n\t}"
+                     ::"r"((int)f), "r"(a), "f"(v.p[0].x), "f"(v.p[0].y), "f"(v.p[NP - 1].x), "f"(v.p[NP - 1].y)
+                     : "memory");
+    }
+}
+__device__ __forceinline__ void wv_sts_if(bool f, unsigned a, float v)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q st.shared.f32 [%1], %2;\n\t}"
+                 ::"r"((int)f), "r"(a), "f"(v)
+                 : "memory");
+}
+
 template <int NP> __device__ __forceinline__ WvRows<NP> wv_lds_rows(unsigned a)
 {
     WvRows<NP> v;
@@ -379,7 +432,11 @@ template <int NP> __device__ __forceinline__ void wv_xb(const WvXch &x, WvRows<N
         n.p[i].x = __shfl_up_sync(0xffffffffu, v.p[i].x, 1);
         n.p[i].y = __shfl_up_sync(0xffffffffu, v.p[i].y, 1);
     }
-    if (x.b7) wv_sts_rows<NP>(x.bo + XBD * d, v);
+    if (NP == 1) {   // (the predicated form costs these shapes registers)
+        if (x.b7) wv_sts_rows<NP>(x.bo + XBD * d, v);
+    } else {
+        wv_sts_rows_if<NP>(x.b7, x.bo + XBD * d, v);
+    }
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
         v.p[i].x = x.b0 ? in.p[i].x : n.p[i].x;
@@ -395,7 +452,11 @@ template <int NP> __device__ __forceinline__ void wv_xc(const WvXch &x, WvRows<N
 {
     const float last = v.p[NP - 1].y;
     const float n = __shfl_up_sync(0xffffffffu, last, 8);
-    if (x.c3) wv_sts(x.co + 32 * d, last);
+    if (NP == 1) {
+        if (x.c3) wv_sts(x.co + 32 * d, last);
+    } else {
+        wv_sts_if(x.c3, x.co + 32 * d, last);
+    }
 #pragma unroll
     for (int i = NP - 1; i >= 0; --i) {
         v.p[i].y = v.p[i].x;
@@ -416,60 +477,98 @@ __device__ __forceinline__ float4 wv_lds4(unsigned a)
     return v;
 }
 
-// One run of a slab's table: entries [d, d1), all with NS segments and, for
-// NS >= 2, the first hand-off along c (FC) or b.  Each entry's ray states
-// (shared memory, rows at rs + 8 NP NT slot) are updated in place and its
-// |n_a|-weighted deposits added to acc.  The segment coefficients come first
-// (they do not depend on the intensities), then the chain of intensity
-// updates and hand-offs.
+// What one entry of a run needs from shared memory: its segment pairs, its
+// |n_a| pair and slot, the ray states of the slot and the hand-off inputs.
+template <int NP> struct WvEnt {
+    float4 w0, w1, w2;
+    float2 na;
+    int slot;
+    WvRows<NP> o, inb;
+    float inc;
+};
+
+template <int NT, int NP, int NS, bool FC>
+__device__ __forceinline__ WvEnt<NP> wv_ld_ent(unsigned rs, unsigned ent, int d, const WvXch &x)
+{
+    constexpr unsigned RSD = 8 * NP * NT;   // ray-state bytes per direction slot
+    WvEnt<NP> E;
+    const unsigned e = ent + 16 * WV_ENT * d;
+    const float4 w3 = wv_lds4(e + 48);
+    E.slot = __float_as_int(w3.z);
+#ifdef ART_WAVE_CHECK
+    if (!wv_ok(E.slot >= 0 && E.slot < x.nslot, x.err)) E.slot = 0;
+#endif
+    E.na = make_float2(w3.x, w3.y);
+    E.w0 = wv_lds4(e);
+    E.w1 = E.w2 = E.w0;
+    if (NS >= 2) E.w1 = wv_lds4(e + 16);
+    if (NS >= 3) E.w2 = wv_lds4(e + 32);
+    E.o = wv_lds_rows<NP>(rs + RSD * E.slot);
+    E.inc = 0.0f;
+    if (NS == 3 || (NS == 2 && !FC)) E.inb = wv_ld_xb<NP>(x, E.slot);
+    if (NS == 3 || (NS == 2 && FC)) E.inc = wv_ld_xc(x, E.slot);
+    return E;
+}
+
+// One entry: the segment coefficients first (they do not depend on the
+// intensities), then the chain of intensity updates and hand-offs; the ray
+// states go back to the slot and the |n_a|-weighted deposits into acc.
 template <int MODE, int NT, int NP, int NS, bool FC, class CO>
+__device__ __forceinline__ void wv_ent(const CO (&c)[NP], unsigned rs, WvEnt<NP> &E, const WvXch &x,
+                                       WvRows<NP> &acc)
+{
+    using Op = WvOps<MODE, CO>;
+    constexpr unsigned RSD = 8 * NP * NT;
+    float2 g1[NP], g2[NP], g3[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        g1[i] = Op::coef(c[i], E.w0);
+        if (NS >= 2) g2[i] = Op::coef(c[i], E.w1);
+        if (NS >= 3) g3[i] = Op::coef(c[i], E.w2);
+    }
+    WvRows<NP> A;
+    WvRows<NP> &o = E.o;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) o.p[i] = Op::template seg<true>(c[i], o.p[i], g1[i], A.p[i]);
+    if (NS >= 2) {
+        if (FC) wv_xc<NP>(x, o, E.slot, E.inc);
+        else wv_xb<NP>(x, o, E.slot, E.inb);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) o.p[i] = Op::template seg<false>(c[i], o.p[i], g2[i], A.p[i]);
+    }
+    if (NS >= 3) {
+        if (FC) wv_xb<NP>(x, o, E.slot, E.inb);
+        else wv_xc<NP>(x, o, E.slot, E.inc);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) o.p[i] = Op::template seg<false>(c[i], o.p[i], g3[i], A.p[i]);
+    }
+    wv_sts_rows<NP>(rs + RSD * E.slot, o);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) acc.p[i] = __ffma2_rn(A.p[i], E.na, acc.p[i]);
+}
+
+// One run of a slab's table: entries [d, d1), all with NS segments and, for
+// NS >= 2, the first hand-off along c (FC) or b.  (Loading the next entry
+// while computing the current one, in register-rich shapes, measured no
+// faster.)
+template <int MODE, int NT, int NP, int NS, bool FC, bool TWO, class CO>
 __device__ __forceinline__ void wv_run(const CO (&c)[NP], unsigned rs, unsigned ent, int d, int d1,
                                        const WvXch &x, WvRows<NP> &acc)
 {
-    using Op = WvOps<MODE, CO>;
-    constexpr unsigned RSD = 8 * NP * NT;   // ray-state bytes per direction slot
+    if (TWO) {
+        // two entries side by side (independent chains for the scheduler)
+#pragma unroll 1
+        for (; d + 1 < d1; d += 2) {
+            WvEnt<NP> E0 = wv_ld_ent<NT, NP, NS, FC>(rs, ent, d, x);
+            WvEnt<NP> E1 = wv_ld_ent<NT, NP, NS, FC>(rs, ent, d + 1, x);
+            wv_ent<MODE, NT, NP, NS, FC>(c, rs, E0, x, acc);
+            wv_ent<MODE, NT, NP, NS, FC>(c, rs, E1, x, acc);
+        }
+    }
 #pragma unroll 1
     for (; d < d1; ++d) {
-        const unsigned e = ent + 16 * WV_ENT * d;
-        const float4 w3 = wv_lds4(e + 48);
-        int slot = __float_as_int(w3.z);
-#ifdef ART_WAVE_CHECK
-        if (!wv_ok(slot >= 0 && slot < x.nslot, x.err)) slot = 0;
-#endif
-        const float4 w0 = wv_lds4(e);
-        float4 w1 = w0, w2 = w0;
-        if (NS >= 2) w1 = wv_lds4(e + 16);
-        if (NS >= 3) w2 = wv_lds4(e + 32);
-        WvRows<NP> o = wv_lds_rows<NP>(rs + RSD * slot);
-        WvRows<NP> inb;
-        float inc = 0.0f;
-        if (NS == 3 || (NS == 2 && !FC)) inb = wv_ld_xb<NP>(x, slot);
-        if (NS == 3 || (NS == 2 && FC)) inc = wv_ld_xc(x, slot);
-        float2 g1[NP], g2[NP], g3[NP];
-#pragma unroll
-        for (int i = 0; i < NP; ++i) {
-            g1[i] = Op::coef(c[i], w0);
-            if (NS >= 2) g2[i] = Op::coef(c[i], w1);
-            if (NS >= 3) g3[i] = Op::coef(c[i], w2);
-        }
-        WvRows<NP> A;
-#pragma unroll
-        for (int i = 0; i < NP; ++i) o.p[i] = Op::template seg<true>(c[i], o.p[i], g1[i], A.p[i]);
-        if (NS >= 2) {
-            if (FC) wv_xc<NP>(x, o, slot, inc);
-            else wv_xb<NP>(x, o, slot, inb);
-#pragma unroll
-            for (int i = 0; i < NP; ++i) o.p[i] = Op::template seg<false>(c[i], o.p[i], g2[i], A.p[i]);
-        }
-        if (NS >= 3) {
-            if (FC) wv_xb<NP>(x, o, slot, inb);
-            else wv_xc<NP>(x, o, slot, inc);
-#pragma unroll
-            for (int i = 0; i < NP; ++i) o.p[i] = Op::template seg<false>(c[i], o.p[i], g3[i], A.p[i]);
-        }
-        wv_sts_rows<NP>(rs + RSD * slot, o);
-#pragma unroll
-        for (int i = 0; i < NP; ++i) acc.p[i] = __ffma2_rn(A.p[i], make_float2(w3.x, w3.y), acc.p[i]);
+        WvEnt<NP> E = wv_ld_ent<NT, NP, NS, FC>(rs, ent, d, x);
+        wv_ent<MODE, NT, NP, NS, FC>(c, rs, E, x, acc);
     }
 }
 
@@ -477,7 +576,7 @@ __device__ __forceinline__ void wv_run(const CO (&c)[NP], unsigned rs, unsigned 
 // 2 NP cells: returns the cells' sums over the unit's directions of |n_a|
 // times the deposits (at most DMAX directions, summed in FP32 in run order;
 // the units' partials are summed with Kahan compensation by the reduction).
-template <int MODE, int NT, int NP, class CO>
+template <int MODE, int NT, int NP, bool TWO, class CO>
 __device__ __forceinline__ WvRows<NP> wv_dirs(const CO (&c)[NP], unsigned rs, unsigned tb, int nd, const WvXch &x)
 {
     WvRows<NP> acc;
@@ -490,11 +589,11 @@ __device__ __forceinline__ WvRows<NP> wv_dirs(const CO (&c)[NP], unsigned rs, un
         e1 = e2 = e3 = e4 = nd = 0;
 #endif
     const unsigned ent = tb + 16;
-    wv_run<MODE, NT, NP, 1, false>(c, rs, ent, 0, e1, x, acc);
-    wv_run<MODE, NT, NP, 2, false>(c, rs, ent, e1, e2, x, acc);
-    wv_run<MODE, NT, NP, 2, true>(c, rs, ent, e2, e3, x, acc);
-    wv_run<MODE, NT, NP, 3, false>(c, rs, ent, e3, e4, x, acc);
-    wv_run<MODE, NT, NP, 3, true>(c, rs, ent, e4, nd, x, acc);
+    wv_run<MODE, NT, NP, 1, false, TWO && MODE == MODE_THIN>(c, rs, ent, 0, e1, x, acc);
+    wv_run<MODE, NT, NP, 2, false, TWO && MODE == MODE_THIN>(c, rs, ent, e1, e2, x, acc);
+    wv_run<MODE, NT, NP, 2, true, TWO && MODE == MODE_THIN>(c, rs, ent, e2, e3, x, acc);
+    wv_run<MODE, NT, NP, 3, false, TWO && MODE == MODE_THIN>(c, rs, ent, e3, e4, x, acc);
+    wv_run<MODE, NT, NP, 3, true, TWO && MODE == MODE_THIN>(c, rs, ent, e4, nd, x, acc);
     return acc;
 }
 
@@ -518,19 +617,25 @@ template <int WB, int WC, int DMAX, int NP> struct WaveShape {
     static constexpr long long edge_c(int Na) { return (long long)Na * WB * DMAX * 8; }
 };
 
-// Slabs between progress publications (each costs the publishing warp a
-// GPU-scope release, and its consumer an acquire).
+// Longest interval between progress publications, in slabs (each costs the
+// publishing warp a GPU-scope release, and its consumer an acquire; a class
+// publishes every Na/16 slabs, a power of two between 1 and this).
 #ifndef ART_WAVE_PUB
-#define ART_WAVE_PUB 4
+#define ART_WAVE_PUB 16
 #endif
 constexpr int WAVE_PUB = ART_WAVE_PUB;
-static_assert(WAVE_PUB >= 1, "publication interval");
+static_assert(WAVE_PUB >= 1 && (WAVE_PUB & (WAVE_PUB - 1)) == 0, "publication interval");
 
 template <int WB, int WC, int DMAX, int NP, int MINB>
 __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs p)
 {
     using Sh = WaveShape<WB, WC, DMAX, NP>;
     constexpr int NT = Sh::NT, RT = Sh::RT, R = Sh::R, XBW = Sh::XBW;
+    // shapes with at least 160 registers a thread take two thin-path entries at a time
+    constexpr bool TWO = 65536 / (MINB * NT) >= 160;
+    // the second thin path (kappa < KAP_THIN6) in shapes with at least 96 registers a thread
+    // (the others take the mixed path there)
+    constexpr bool THIN6 = 65536 / (MINB * NT) >= 96;
     extern __shared__ __align__(16) unsigned char wsm[];
     float4 *tab = reinterpret_cast<float4 *>(wsm);                  // [RT][TABS]: run-table blocks
     float *XB = reinterpret_cast<float *>(wsm + Sh::off_xb);        // [2][WB+1][WC][DMAX][XBW]
@@ -578,6 +683,20 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
     jl_ok = wv_ok(jl_ok, p.err);
     float *J0 = p.jpart + U.jpart + (inmask ? jb0 : 0);
     const bool stalled = u == p.stall_unit;
+    // ART_WAVE_STATS builds: cycles in the poll loops and polls (lane 0), cycles at the step
+    // barriers and in the unit (every warp), added to p.stats when the unit ends
+    long long st_poll[2] = {0, 0}, st_bar = 0;
+#ifdef ART_WAVE_STATS
+    const long long st_t0 = clock64();
+    auto stats_out = [&]() {
+        if (lane == 0 && p.stats) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(p.stats + 0), (unsigned long long)st_bar);
+            atomicAdd(reinterpret_cast<unsigned long long *>(p.stats + 1), (unsigned long long)(clock64() - st_t0));
+            atomicAdd(reinterpret_cast<unsigned long long *>(p.stats + 2), (unsigned long long)st_poll[0]);
+            atomicAdd(reinterpret_cast<unsigned long long *>(p.stats + 3), (unsigned long long)st_poll[1]);
+        }
+    };
+#endif
 
     if (tid == 0) s_up[0] = U.up_b >= 0 ? p.units[U.up_b].eb : -1;
     if (tid == 1) s_up[1] = U.up_c >= 0 ? p.units[U.up_c].ec : -1;
@@ -628,7 +747,7 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
             if (s >= 0 && s < Na) {
                 if (s + 1 > seen_b) {
                     int v = 0;
-                    if (lane == 0) v = wv_wait(up_flag_b, s + 1, pref_b, p);
+                    if (lane == 0) v = wv_wait(up_flag_b, s + 1, pref_b, p, st_poll);
                     v = __shfl_sync(0xffffffffu, v, 0);
                     if (v < 0) ok = 0;
                     else seen_b = v;
@@ -654,7 +773,7 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
                 int okc = 1;
                 if (s + 1 > seen_c) {
                     int v = 0;
-                    if (lane == 0) v = wv_wait(up_flag_c, s + 1, pref_c, p);
+                    if (lane == 0) v = wv_wait(up_flag_c, s + 1, pref_c, p, st_poll);
                     v = __shfl_sync(0xffffffffu, v, 0);
                     if (v < 0) okc = 0;
                     else seen_c = v;
@@ -692,7 +811,7 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
     for (int t = 0; t < T && !abort_; ++t) {
         const int m = t - wb - wc;
         // progress of the slabs written to global memory in earlier steps
-        if (lane == 0 && !stalled && m - 1 >= 0 && m - 1 < Na && m % WAVE_PUB == 0) {
+        if (lane == 0 && !stalled && m - 1 >= 0 && m - 1 < Na && (m & (C.pub - 1)) == 0) {
             if (b_out) wv_st_release(p.flags + fl_b, m);
             if (c_out) wv_st_release(p.flags + fl_c, m);
         }
@@ -700,7 +819,7 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
         if (m >= 0 && m < Na) {
             const int par = t & 1;
             float2 kap[NP], src[NP];
-            bool thin = true, thick = true;
+            bool thin = true, thin6 = true, thick = true;
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
                 const float4 f = reinterpret_cast<const float4 *>(FS + (par * NT + tid) * R)[i];
@@ -708,6 +827,7 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
                 kap[i] = make_float2(i0 ? f.x : 0.0f, i1 ? f.z : 0.0f);
                 src[i] = make_float2(i0 ? f.y : 0.0f, i1 ? f.w : 0.0f);
                 thin = thin && kap[i].x < KAP_THIN && kap[i].y < KAP_THIN;
+                thin6 = thin6 && kap[i].x < KAP_THIN6 && kap[i].y < KAP_THIN6;
                 thick = thick && kap[i].x >= KAP_THICK && kap[i].y >= KAP_THICK;
             }
             WvXch x;
@@ -723,20 +843,18 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
             x.err = p.err;
             const unsigned tb = tab0 + 16 * (m & (RT - 1)) * Sh::TABS;
             const bool all_thin = __all_sync(0xffffffffu, thin), all_thick = __all_sync(0xffffffffu, thick);
+            const bool all_thin6 = THIN6 && __all_sync(0xffffffffu, thin6);
             WvRows<NP> js;
             if (all_thin) {
-                WvThin c[NP];
+                WvThin<4> c[NP];
 #pragma unroll
-                for (int i = 0; i < NP; ++i) {
-                    const float2 k = kap[i], kk = __fmul2_rn(k, k);
-                    c[i].c1 = __fmul2_rn(k, f2s(-0.5f));
-                    c[i].c2 = __fmul2_rn(kk, f2s(1.0f / 6.0f));
-                    c[i].c3 = __fmul2_rn(__fmul2_rn(kk, k), f2s(-1.0f / 24.0f));
-                    c[i].c4 = __fmul2_rn(__fmul2_rn(kk, kk), f2s(1.0f / 120.0f));
-                    c[i].nkap = make_float2(-k.x, -k.y);
-                    c[i].E = p.field_form ? src[i] : __fmul2_rn(k, src[i]);
-                }
-                js = wv_dirs<MODE_THIN, NT, NP>(c, rs0, tb, nd, x);
+                for (int i = 0; i < NP; ++i) c[i] = wv_thin<4>(kap[i], src[i], p.field_form);
+                js = wv_dirs<MODE_THIN, NT, NP, TWO>(c, rs0, tb, nd, x);
+            } else if (THIN6 && all_thin6) {
+                WvThin<6> c[NP];
+#pragma unroll
+                for (int i = 0; i < NP; ++i) c[i] = wv_thin<6>(kap[i], src[i], p.field_form);
+                js = wv_dirs<MODE_THIN, NT, NP, false>(c, rs0, tb, nd, x);   // (code size: one entry at a time)
             } else {
                 WvCell2 c[NP];
 #pragma unroll
@@ -750,11 +868,11 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
                     c[i].k2 = __fmul2_rn(kap[i], f2s(-1.4426950408889634f));
                 }
                 if (all_thick) {
-                    js = wv_dirs<MODE_THICK, NT, NP>(c, rs0, tb, nd, x);
+                    js = wv_dirs<MODE_THICK, NT, NP, TWO>(c, rs0, tb, nd, x);
 #pragma unroll
                     for (int i = 0; i < NP; ++i) js.p[i] = __fmul2_rn(js.p[i], c[i].rk);
                 } else {
-                    js = wv_dirs<MODE_MIXED, NT, NP>(c, rs0, tb, nd, x);
+                    js = wv_dirs<MODE_MIXED, NT, NP, TWO>(c, rs0, tb, nd, x);
                 }
             }
             if (jl_ok) {
@@ -790,8 +908,18 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
             }
         }
         wv_cp_wait();
+#ifdef ART_WAVE_STATS
+        const long long tb0 = clock64();
+#endif
         abort_ = __syncthreads_or(bad);
+#ifdef ART_WAVE_STATS
+        st_bar += clock64() - tb0;
+#endif
     }
+#ifdef ART_WAVE_STATS
+    stats_out();
+#endif
+    (void)st_bar;
     if (abort_) {
         if (tid == 0) atomicOr(p.err, 1);
         return;

@@ -2,9 +2,9 @@
 cell average) against the FP64 oracle, through the C ABI.
 
 Bar: 1e-5 relative per cell on J and J^in (the FP32 target), as for the
-slab-block kernels.  Every compiled wavefront shape (art_options.variant 16-25:
+slab-block kernels.  Every compiled wavefront shape (art_options.variant 16-26:
 8 x 8- or 8 x 16-column warp tiles (two or four rows per lane), 2 x 1, 2 x 2,
-2 x 4 or 4 x 2 warps per CTA, 20 / 16 / 12 / 4
+2 x 4 or 4 x 2 warps per CTA, 20 / 17 / 16 / 12 / 4
 direction slots) runs on ragged grids that span several CTA tiles along both
 transverse axes, with classes split into direction groups where they exceed
 the slots.  The bounded waits are checked by stalling one tile on purpose: the
@@ -78,7 +78,7 @@ def test_default_fp32_context_uses_the_wavefront_sweep():
                                            (WAVE0 + 1, 8), (WAVE0 + 3, 2), (WAVE0 + 4, 3),
                                            (WAVE0 + 5, 8), (WAVE0 + 5, 4), (WAVE0 + 6, 8), (WAVE0 + 6, 2),
                                            (WAVE0 + 7, 8), (WAVE0 + 7, 3), (WAVE0 + 8, 8), (WAVE0 + 8, 1),
-                                           (WAVE0 + 9, 4)])
+                                           (WAVE0 + 9, 4), (WAVE0 + 9, 8), (WAVE0 + 10, 8), (WAVE0 + 10, 2), (WAVE0 + 10, 4)])
 def test_ragged_grids_every_shape(orc, variant, nside):
     """Ragged against every tile (16 x 16 and 32 x 16 columns); shapes with fewer slots than a
     class's directions split it into groups."""
@@ -92,10 +92,25 @@ def test_ragged_grids_every_shape(orc, variant, nside):
 
 
 @pytest.mark.parametrize("scale", [0.02, 0.3, 3.0])
-@pytest.mark.parametrize("variant", [0, WAVE0 + 7])
+@pytest.mark.parametrize("variant", [0, WAVE0 + 1, WAVE0 + 10])
 def test_thin_mixed_and_thick_media(orc, scale, variant):
     """Media whose warps take the series path, both paths, or the exponential path."""
     kap, S = lognormal((20, 24, 28), 11, scale)
+    jin_o, j_o, _ = orc.sweep(kap, S, 4)
+    J, Jin, _ = run(kap, S, 4, variant=variant)
+    assert rel(Jin, jin_o) < 1e-5
+    assert rel(J, j_o) < 1e-5
+
+
+@pytest.mark.parametrize("variant", [0, WAVE0 + 6, WAVE0 + 10])
+@pytest.mark.parametrize("hi", [0.099, 0.249])
+def test_second_thin_path(orc, variant, hi):
+    """kappa uniform in [0, hi): every warp below 0.1 takes the x^4 series, below 0.25 the x^6
+    series (in shapes with the registers for it; the mixed path in the others), with segments
+    up to x = 0.43."""
+    rng = np.random.default_rng(19)
+    shape = (22, 27, 35)
+    kap, S = f32(hi * rng.random(shape)), f32(rng.random(shape))
     jin_o, j_o, _ = orc.sweep(kap, S, 4)
     J, Jin, _ = run(kap, S, 4, variant=variant)
     assert rel(Jin, jin_o) < 1e-5
@@ -217,3 +232,59 @@ def test_a_stalled_tile_times_out_and_the_context_recovers(orc):
     sw.close()
     jin_o, _, _ = orc.sweep(kap, S, 2)
     assert rel(Jin.cpu().numpy().astype(np.float64), jin_o) < 1e-5
+
+
+def clump_boundary_cells(rho, rng, count):
+    """Cells of the clumpy medium whose density differs from a face neighbour's by more than
+    10x (the surfaces of the overdense spheres), `count` of them at random."""
+    jump = np.zeros(rho.shape, dtype=bool)
+    for ax in range(3):
+        hi = np.maximum(rho, np.roll(rho, 1, ax)) > 10.0 * np.minimum(rho, np.roll(rho, 1, ax))
+        edge = [slice(None)] * 3
+        edge[ax] = 0
+        hi[tuple(edge)] = False            # no wrap-around across the box faces
+        jump |= hi
+    idx = np.flatnonzero(jump)
+    return rng.choice(idx, min(count, idx.size), replace=False)
+
+
+def test_clumpy_256_four_bins_sampled_cells(orc):
+    """The headline workload at full size (256^3 clumpy medium, N_side 8, 4 bins), in the launch
+    configuration the benchmark times (all bins in one context, autotuned variant): J^in of
+    1000 cells per bin against the oracle, computed cell by cell -- 400 on the clumps'
+    surfaces, the 8 corners, cells on every face and the rest uniform.  FP32 bar at 256^3:
+    1e-4 relative per cell."""
+    c = wl.clumpy_sweep()
+    kap, S = f32(c.kappa), f32(c.src)
+    nb, n = kap.shape[0], kap.shape[-1]
+    k = torch.as_tensor(np.ascontiguousarray(kap), dtype=torch.float32, device="cuda")
+    s = torch.as_tensor(np.ascontiguousarray(S), dtype=torch.float32, device="cuda")
+    sw = art.ArtSweep((n, n, n), 8, nb)
+    sw.set_fields(k, s)
+    sw.autotune(1)
+    Jin = torch.empty_like(k)
+    sw.sweep(None, Jin)
+    torch.cuda.synchronize()
+    assert sw.check() == art.ART_OK
+    variant = sw.stats.variant
+    sw.close()
+    Jin = Jin.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(12)
+    rho = S[0]
+    corners = [z * n * n + y * n + x for z in (0, n - 1) for y in (0, n - 1) for x in (0, n - 1)]
+    faces = []
+    for ax in range(3):
+        for side in (0, n - 1):
+            p = rng.integers(0, n, size=(10, 3))
+            p[:, ax] = side
+            faces += list(p[:, 0] * n * n + p[:, 1] * n + p[:, 2])
+    edge = clump_boundary_cells(rho, rng, 400)
+    rest = rng.choice(n ** 3, 1000 - len(corners) - len(faces) - edge.size, replace=False)
+    cells = np.unique(np.concatenate([corners, faces, edge, rest]).astype(np.int64))
+    assert cells.size >= 990 and edge.size == 400
+    for b in range(nb):
+        ref = orc.jin_cells(kap[b], S[b], 8, cells, nthreads=orc.default_threads())
+        got = Jin[b].ravel()[cells]
+        assert np.all(ref > 0)
+        err = np.abs(got - ref) / ref
+        assert err.max() < 1e-4, (b, variant, float(err.max()), int(cells[np.argmax(err)]))
