@@ -448,6 +448,7 @@ int pick_wave(const art_ctx *ctx)
 {
     if (ctx->prec != ART_FP32 || ctx->opt.averaging != ART_AVG_PAPER) return -1;
     int maxc = 0;
+    long long largest = 0;
     for (const art_grid_host &g : ctx->grids) {
         std::vector<double> xyz;
         healpix_directions(g.nside, xyz);
@@ -457,8 +458,9 @@ int pick_wave(const art_ctx *ctx)
             if (!ranged || (d >= ctx->opt.dir_begin && d < ctx->opt.dir_end))
                 ++cnt[frame_of(&xyz[3 * d], ctx->opt.tie_tol).cls];
         for (int c = 0; c < 24; ++c) maxc = std::max(maxc, cnt[c]);
+        largest = std::max(largest, (long long)g.g.nx * g.g.ny * g.g.nz);
     }
-    return art_wave_default(maxc);
+    return art_wave_default(maxc, largest);
 }
 
 template <typename real> art_status do_sweep(art_ctx *ctx, real *J, real *Jin, real *gam, cudaStream_t st)

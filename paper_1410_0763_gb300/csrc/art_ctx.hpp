@@ -138,7 +138,7 @@ art_status art_internal_layout(art_ctx *ctx, const void *kappa, const void *src,
 // wavefront sweep (art_wave.cu)
 int art_wave_variants();
 int art_wave_dmax(int w);
-int art_wave_default(int maxc);   // default shape for classes of at most maxc directions
+int art_wave_default(int maxc, long long cells);   // default shape: class size, largest grid
 void art_wave_free(art_ctx *ctx);
 art_status art_wave_setup(art_ctx *ctx, int w);
 art_status art_wave_launch(art_ctx *ctx, const float2 *f0, const float2 *f1, const float2 *f2, float i_bc,

@@ -356,14 +356,20 @@ bool wave_tables_ok(const WaveHost &t, const WVariant &v, std::string &why)
 
 int art_wave_variants() { return kNumWave; }
 
-// Default shape for classes of at most maxc directions: 2 x 2 warps with four
-// rows per lane and 12 slots (the fastest measured on GB300 at N_side 4 and
-// 8), or with 4 slots and two rows per lane when no class has more than 4.
-int art_wave_default(int maxc)
+// Default shape for classes of at most maxc directions and a largest grid of
+// `cells` cells (measured on GB300): 2 x 2 warps throughout; with 4 slots and
+// two rows per lane when no class has more than 4 directions; below 100^3
+// cells two rows per lane and 20 slots (more, smaller tiles); above, four rows
+// per lane with 17 slots where classes exceed 12 directions (N_side 8: two
+// groups per class), else 12.
+int art_wave_default(int maxc, long long cells)
 {
-    const int want_dmax = maxc <= 4 ? 4 : 12, want_np = maxc <= 4 ? 1 : 2;
+    int dmax = 17, np = 2;
+    if (maxc <= 4) dmax = 4, np = 1;
+    else if (cells < 100LL * 100 * 100) dmax = 20, np = 1;
+    else if (maxc <= 12) dmax = 12;
     for (int w = 0; w < kNumWave; ++w)
-        if (kWave[w].wb == 2 && kWave[w].wc == 2 && kWave[w].dmax == want_dmax && kWave[w].np == want_np) return w;
+        if (kWave[w].wb == 2 && kWave[w].wc == 2 && kWave[w].dmax == dmax && kWave[w].np == np) return w;
     return 0;
 }
 
