@@ -187,3 +187,56 @@ def test_c_abi_surrogate_train_and_the_warm_start_argument():
         assert np.max(np.abs(yw - y_plain) / y_plain) < 1e-4
         assert np.max(np.abs((1 - yw) - (1 - y_plain)) / (1 - y_plain)) < 1e-4
     sw.close()
+
+
+def test_network_phase_against_the_run_without_it():
+    """The warm start's claim, measured on a held-out setup at 64^3: the run with the trained
+    network's phase against the same run without the network (coarse-mesh start, then plain
+    iterations), both to 1e-6.  The design bounds the network's cost -- at most one full
+    sweep more than without it (the judge's), surrogate iterations within the phase limit --
+    and both reach the same fixed point.  The seconds and sweep counts of both are printed:
+    after the coarse start the network does not remove full sweeps (its J^in error is at the
+    level of the residual it starts from)."""
+    import time
+    n, nside, NIT = 64, 4, 16
+    V = n ** 3
+    X = torch.empty((4 * NIT, 4, V), device="cuda")
+    T = torch.empty((4 * NIT, V), device="cuda")
+    W = torch.empty((4 * NIT, V), device="cuda")
+    for k in range(4):
+        c = wl.hii_random(n, nside, seed=400 + k, box_kpc=3.3)
+        sk = art.ArtSweep(c.nH.shape, c.nside, 1, field_form=art.ART_FIELDS_EPS, dx_cm=c.chem["dx"])
+        yk = torch.as_tensor(c.y0, dtype=torch.float64, device="cuda").clone()
+        sk.surrogate_collect(torch.as_tensor(c.nH, device="cuda"), c.chem, srcs(c), yk, X[k * NIT:(k + 1) * NIT],
+                             T[k * NIT:(k + 1) * NIT], NIT, w=W[k * NIT:(k + 1) * NIT], coarse_nside=2)
+        sk.close()
+    net = art.ArtNet(dilation=(1, 2, 4, 8), lr=3e-4, seed=3)
+    net.train(X, T, (n, n, n), X.shape[0], 600, w=W, seed=1)
+    del X, T, W
+    held = wl.hii_region(n=n, nside=nside, box_kpc=3.3)
+    sw = art.ArtSweep((n, n, n), nside, 1, field_form=art.ART_FIELDS_EPS, dx_cm=held.chem["dx"])
+    nH = torch.as_tensor(held.nH, dtype=torch.float64, device="cuda")
+    res = {}
+    for label, netp, kw in (("without", None, dict(use_net=False, phase1_max_iter=0)), ("with", net, {})):
+        best = None
+        for _ in range(2):
+            y = torch.as_tensor(held.y0, dtype=torch.float64, device="cuda").clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rep, hist = sw.iterate_warm(netp, nH, held.chem, srcs(held), y, tol=1e-6, max_iter=300,
+                                        coarse_nside=2, **kw)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        assert rep.total.converged and hist[-1] < 1e-6
+        res[label] = (rep, best, y.cpu().numpy())
+    (r0, t0_, y0), (r1, t1_, y1) = res["without"], res["with"]
+    print(f"\nWARM START 64^3: without the network {r0.total.iterations} iterations, {r0.plain_sweeps} full sweeps, "
+          f"{t0_:.4f} s; with it {r1.total.iterations} iterations ({r1.surrogate_iterations} surrogate), "
+          f"{r1.plain_sweeps} full sweeps, {t1_:.4f} s, judge error {r1.judge_error:.3f}")
+    assert r1.surrogate_iterations >= 1 and not r1.fell_back
+    assert r1.plain_sweeps <= r0.plain_sweeps + 1
+    assert np.max(np.abs(y1 - y0) / y0) < 1e-4
+    assert np.max(np.abs((1 - y1) - (1 - y0)) / (1 - y0)) < 1e-4
+    net.close()
+    sw.close()
