@@ -74,7 +74,6 @@ const WVariant kWave[] = {
     ART_WV(2, 1, 16, 2, 8),   // four rows per lane: 16 x 16 columns, 2 warps
     ART_WV(2, 2, 12, 2, 4),   // four rows per lane, 12 slots (the default from N_side 3 up)
     ART_WV(2, 2, 17, 2, 3),   // four rows per lane, 17 slots: N_side 8 classes in 2 groups
-    ART_WV(2, 1, 17, 2, 6),   // the same with 2 x 1 warps (a two-warp step barrier), 6 CTAs per SM
 };
 #undef ART_WV
 const int kNumWave = int(sizeof(kWave) / sizeof(kWave[0]));

@@ -279,6 +279,37 @@ template <int K> __device__ __forceinline__ WvThin<K> wv_thin(float2 k, float2 s
     return c;
 }
 
+// Mixed path: per cell and segment, the x^5 series of the thin path (per-cell
+// coefficients) for segments with x = kappa ds below X_SERIES, i.e. ds below
+// the cell's threshold X_SERIES / kappa, else the exponential path.
+struct WvMixed {
+    WvThin<5> t;     // c_1 .. c_5, -kappa, emission
+    float2 k2;       // -kappa log2 e
+    float2 rk, nrk;  // 1/kappa, -1/kappa (0 where kappa = 0)
+    float2 th;       // X_SERIES / kappa (+inf where kappa = 0)
+};
+
+__device__ __forceinline__ WvMixed wv_mixed(float2 k, float2 src, int field_form)
+{
+    WvMixed c;
+    c.t = wv_thin<5>(k, src, field_form);
+    c.k2 = __fmul2_rn(k, f2s(-1.4426950408889634f));
+    c.rk = make_float2(k.x > 0.0f ? wv_rcp(k.x) : 0.0f, k.y > 0.0f ? wv_rcp(k.y) : 0.0f);
+    c.nrk = make_float2(-c.rk.x, -c.rk.y);
+    c.th = make_float2(k.x > 0.0f ? X_SERIES * c.rk.x : __int_as_float(0x7f800000),
+                       k.y > 0.0f ? X_SERIES * c.rk.y : __int_as_float(0x7f800000));
+    return c;
+}
+
+__device__ __forceinline__ float2 wv_coef(const WvMixed &c, const float4 &w)
+{
+    const float2 gs = wv_coef(c.t, w);
+    const float2 arg = __fmul2_rn(c.k2, make_float2(w.x, w.y));
+    const float2 e = make_float2(wv_ex2(arg.x), wv_ex2(arg.y));
+    const float2 gm = __ffma2_rn(e, c.nrk, c.rk);   // (1 - e^-x) / kappa
+    return make_float2(w.x < c.th.x ? gs.x : gm.x, w.y < c.th.y ? gs.y : gm.y);
+}
+
 template <int MODE> __device__ __forceinline__ float2 wv_coef(const WvCell2 &c, const float4 &w)
 {
     const float2 dsv = make_float2(w.x, w.y);
@@ -326,6 +357,14 @@ template <int K> struct WvOps<MODE_THIN, WvThin<K>> {
     static __device__ __forceinline__ float2 seg(const WvThin<K> &c, float2 I, float2 g, float2 &A)
     {
         return wv_seg<F>(c, I, g, A);
+    }
+};
+template <> struct WvOps<MODE_MIXED, WvMixed> {
+    static __device__ __forceinline__ float2 coef(const WvMixed &c, const float4 &w) { return wv_coef(c, w); }
+    template <bool F>
+    static __device__ __forceinline__ float2 seg(const WvMixed &c, float2 I, float2 g, float2 &A)
+    {
+        return wv_seg<F>(c.t, I, g, A);
     }
 };
 template <int MODE> struct WvOps<MODE, WvCell2> {
@@ -855,6 +894,11 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
 #pragma unroll
                 for (int i = 0; i < NP; ++i) c[i] = wv_thin<6>(kap[i], src[i], p.field_form);
                 js = wv_dirs<MODE_THIN, NT, NP, false>(c, rs0, tb, nd, x);   // (code size: one entry at a time)
+            } else if (THIN6 && !all_thick) {   // (the coefficient form needs the registers of THIN6 shapes)
+                WvMixed c[NP];
+#pragma unroll
+                for (int i = 0; i < NP; ++i) c[i] = wv_mixed(kap[i], src[i], p.field_form);
+                js = wv_dirs<MODE_MIXED, NT, NP, false>(c, rs0, tb, nd, x);
             } else {
                 WvCell2 c[NP];
 #pragma unroll
@@ -868,11 +912,11 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
                     c[i].k2 = __fmul2_rn(kap[i], f2s(-1.4426950408889634f));
                 }
                 if (all_thick) {
-                    js = wv_dirs<MODE_THICK, NT, NP, TWO>(c, rs0, tb, nd, x);
+                    js = wv_dirs<MODE_THICK, NT, NP, false>(c, rs0, tb, nd, x);
 #pragma unroll
                     for (int i = 0; i < NP; ++i) js.p[i] = __fmul2_rn(js.p[i], c[i].rk);
                 } else {
-                    js = wv_dirs<MODE_MIXED, NT, NP, TWO>(c, rs0, tb, nd, x);
+                    js = wv_dirs<MODE_MIXED, NT, NP, false>(c, rs0, tb, nd, x);
                 }
             }
             if (jl_ok) {

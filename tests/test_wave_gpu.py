@@ -2,7 +2,7 @@
 cell average) against the FP64 oracle, through the C ABI.
 
 Bar: 1e-5 relative per cell on J and J^in (the FP32 target), as for the
-slab-block kernels.  Every compiled wavefront shape (art_options.variant 16-27:
+slab-block kernels.  Every compiled wavefront shape (art_options.variant 16-26:
 8 x 8- or 8 x 16-column warp tiles (two or four rows per lane), 2 x 1, 2 x 2,
 2 x 4 or 4 x 2 warps per CTA, 20 / 17 / 16 / 12 / 4
 direction slots) runs on ragged grids that span several CTA tiles along both
@@ -78,8 +78,7 @@ def test_default_fp32_context_uses_the_wavefront_sweep():
                                            (WAVE0 + 1, 8), (WAVE0 + 3, 2), (WAVE0 + 4, 3),
                                            (WAVE0 + 5, 8), (WAVE0 + 5, 4), (WAVE0 + 6, 8), (WAVE0 + 6, 2),
                                            (WAVE0 + 7, 8), (WAVE0 + 7, 3), (WAVE0 + 8, 8), (WAVE0 + 8, 1),
-                                           (WAVE0 + 9, 4), (WAVE0 + 9, 8), (WAVE0 + 10, 8), (WAVE0 + 10, 2), (WAVE0 + 10, 4),
-                                           (WAVE0 + 11, 8), (WAVE0 + 11, 3)])
+                                           (WAVE0 + 9, 4), (WAVE0 + 9, 8), (WAVE0 + 10, 8), (WAVE0 + 10, 2), (WAVE0 + 10, 4)])
 def test_ragged_grids_every_shape(orc, variant, nside):
     """Ragged against every tile (16 x 16 and 32 x 16 columns); shapes with fewer slots than a
     class's directions split it into groups."""
@@ -189,7 +188,8 @@ def test_batch_of_uneven_grids_matches_single_contexts(orc):
     kap = np.concatenate([k.ravel() for k in ks])
     src = np.concatenate([s.ravel() for s in ss])
     sw = art.ArtSweep(shapes, nsides, 1)
-    assert sw.stats.variant >= WAVE0
+    variant = sw.stats.variant
+    assert variant >= WAVE0
     k = torch.as_tensor(kap, dtype=torch.float32, device="cuda")
     s = torch.as_tensor(src, dtype=torch.float32, device="cuda")
     Jin = torch.empty_like(k)
@@ -203,7 +203,7 @@ def test_batch_of_uneven_grids_matches_single_contexts(orc):
         n = kk.size
         jin_o, _, _ = orc.sweep(kk, s_, ns)
         assert rel(got[off:off + n].reshape(kk.shape), jin_o) < 1e-5
-        single = run(kk, s_, ns)[1]
+        single = run(kk, s_, ns, variant=variant)[1]   # the same kernel shape: the same arithmetic
         assert np.array_equal(got[off:off + n].reshape(kk.shape), single)
         off += n
 
