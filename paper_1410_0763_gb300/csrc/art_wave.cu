@@ -73,7 +73,8 @@ const WVariant kWave[] = {
     ART_WV(2, 2, 16, 2, 4),   // four rows per lane: 16 x 32 columns, 4 warps
     ART_WV(2, 1, 16, 2, 8),   // four rows per lane: 16 x 16 columns, 2 warps
     ART_WV(2, 2, 12, 2, 4),   // four rows per lane, 12 slots (the default from N_side 3 up)
-    ART_WV(2, 2, 17, 2, 3),   // four rows per lane, 17 slots: N_side 8 classes in 2 groups
+    ART_WV(2, 2, 17, 2, 3),   // four rows per lane, 17 slots: N_side 8 classes of up to 34 in 2 groups
+    ART_WV(2, 2, 19, 2, 3),   // four rows per lane, 19 slots: every N_side 8 class (up to 37) in 2 groups
 };
 #undef ART_WV
 const int kNumWave = int(sizeof(kWave) / sizeof(kWave[0]));
@@ -360,14 +361,15 @@ int art_wave_variants() { return kNumWave; }
 // `cells` cells (measured on GB300): 2 x 2 warps throughout; with 4 slots and
 // two rows per lane when no class has more than 4 directions; below 100^3
 // cells two rows per lane and 20 slots (more, smaller tiles); above, four rows
-// per lane with 17 slots where classes exceed 12 directions (N_side 8: two
-// groups per class), else 12.
+// per lane with 12 slots up to 12 directions per class, 17 up to 17, else 19
+// (N_side 8, classes of 26-37: two groups each).
 int art_wave_default(int maxc, long long cells)
 {
-    int dmax = 17, np = 2;
+    int dmax = 19, np = 2;
     if (maxc <= 4) dmax = 4, np = 1;
     else if (cells < 100LL * 100 * 100) dmax = 20, np = 1;
     else if (maxc <= 12) dmax = 12;
+    else if (maxc <= 17) dmax = 17;
     for (int w = 0; w < kNumWave; ++w)
         if (kWave[w].wb == 2 && kWave[w].wc == 2 && kWave[w].dmax == dmax && kWave[w].np == np) return w;
     return 0;

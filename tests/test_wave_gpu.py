@@ -2,9 +2,9 @@
 cell average) against the FP64 oracle, through the C ABI.
 
 Bar: 1e-5 relative per cell on J and J^in (the FP32 target), as for the
-slab-block kernels.  Every compiled wavefront shape (art_options.variant 16-26:
+slab-block kernels.  Every compiled wavefront shape (art_options.variant 16-27:
 8 x 8- or 8 x 16-column warp tiles (two or four rows per lane), 2 x 1, 2 x 2,
-2 x 4 or 4 x 2 warps per CTA, 20 / 17 / 16 / 12 / 4
+2 x 4 or 4 x 2 warps per CTA, 20 / 19 / 17 / 16 / 12 / 4
 direction slots) runs on ragged grids that span several CTA tiles along both
 transverse axes, with classes split into direction groups where they exceed
 the slots.  The bounded waits are checked by stalling one tile on purpose: the
@@ -78,7 +78,8 @@ def test_default_fp32_context_uses_the_wavefront_sweep():
                                            (WAVE0 + 1, 8), (WAVE0 + 3, 2), (WAVE0 + 4, 3),
                                            (WAVE0 + 5, 8), (WAVE0 + 5, 4), (WAVE0 + 6, 8), (WAVE0 + 6, 2),
                                            (WAVE0 + 7, 8), (WAVE0 + 7, 3), (WAVE0 + 8, 8), (WAVE0 + 8, 1),
-                                           (WAVE0 + 9, 4), (WAVE0 + 9, 8), (WAVE0 + 10, 8), (WAVE0 + 10, 2), (WAVE0 + 10, 4)])
+                                           (WAVE0 + 9, 4), (WAVE0 + 9, 8), (WAVE0 + 10, 8), (WAVE0 + 10, 2), (WAVE0 + 10, 4),
+                                           (WAVE0 + 11, 8), (WAVE0 + 11, 3)])
 def test_ragged_grids_every_shape(orc, variant, nside):
     """Ragged against every tile (16 x 16 and 32 x 16 columns); shapes with fewer slots than a
     class's directions split it into groups."""
