@@ -586,6 +586,66 @@ __device__ __forceinline__ void wv_ent(const CO (&c)[NP], unsigned rs, WvEnt<NP>
     for (int i = 0; i < NP; ++i) acc.p[i] = __ffma2_rn(A.p[i], E.na, acc.p[i]);
 }
 
+// Two entries of one run in lockstep, statement by statement, so that their
+// independent chains sit side by side for the scheduler; the same arithmetic
+// and the same order of the deposit sums as two calls of wv_ent.
+template <int MODE, int NT, int NP, int NS, bool FC, class CO>
+__device__ __forceinline__ void wv_ent2(const CO (&c)[NP], unsigned rs, WvEnt<NP> &E, WvEnt<NP> &F,
+                                        const WvXch &x, WvRows<NP> &acc)
+{
+    using Op = WvOps<MODE, CO>;
+    constexpr unsigned RSD = 8 * NP * NT;
+    float2 g1[NP], g2[NP], g3[NP], h1[NP], h2[NP], h3[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        g1[i] = Op::coef(c[i], E.w0);
+        h1[i] = Op::coef(c[i], F.w0);
+        if (NS >= 2) g2[i] = Op::coef(c[i], E.w1);
+        if (NS >= 2) h2[i] = Op::coef(c[i], F.w1);
+        if (NS >= 3) g3[i] = Op::coef(c[i], E.w2);
+        if (NS >= 3) h3[i] = Op::coef(c[i], F.w2);
+    }
+    WvRows<NP> A, B;
+    WvRows<NP> &o = E.o, &q = F.o;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        o.p[i] = Op::template seg<true>(c[i], o.p[i], g1[i], A.p[i]);
+        q.p[i] = Op::template seg<true>(c[i], q.p[i], h1[i], B.p[i]);
+    }
+    if (NS >= 2) {
+        if (FC) {
+            wv_xc<NP>(x, o, E.slot, E.inc);
+            wv_xc<NP>(x, q, F.slot, F.inc);
+        } else {
+            wv_xb<NP>(x, o, E.slot, E.inb);
+            wv_xb<NP>(x, q, F.slot, F.inb);
+        }
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            o.p[i] = Op::template seg<false>(c[i], o.p[i], g2[i], A.p[i]);
+            q.p[i] = Op::template seg<false>(c[i], q.p[i], h2[i], B.p[i]);
+        }
+    }
+    if (NS >= 3) {
+        if (FC) {
+            wv_xb<NP>(x, o, E.slot, E.inb);
+            wv_xb<NP>(x, q, F.slot, F.inb);
+        } else {
+            wv_xc<NP>(x, o, E.slot, E.inc);
+            wv_xc<NP>(x, q, F.slot, F.inc);
+        }
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            o.p[i] = Op::template seg<false>(c[i], o.p[i], g3[i], A.p[i]);
+            q.p[i] = Op::template seg<false>(c[i], q.p[i], h3[i], B.p[i]);
+        }
+    }
+    wv_sts_rows<NP>(rs + RSD * E.slot, o);
+    wv_sts_rows<NP>(rs + RSD * F.slot, q);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) acc.p[i] = __ffma2_rn(B.p[i], F.na, __ffma2_rn(A.p[i], E.na, acc.p[i]));
+}
+
 // One run of a slab's table: entries [d, d1), all with NS segments and, for
 // NS >= 2, the first hand-off along c (FC) or b.  (Loading the next entry
 // while computing the current one, in register-rich shapes, measured no
@@ -600,8 +660,7 @@ __device__ __forceinline__ void wv_run(const CO (&c)[NP], unsigned rs, unsigned 
         for (; d + 1 < d1; d += 2) {
             WvEnt<NP> E0 = wv_ld_ent<NT, NP, NS, FC>(rs, ent, d, x);
             WvEnt<NP> E1 = wv_ld_ent<NT, NP, NS, FC>(rs, ent, d + 1, x);
-            wv_ent<MODE, NT, NP, NS, FC>(c, rs, E0, x, acc);
-            wv_ent<MODE, NT, NP, NS, FC>(c, rs, E1, x, acc);
+            wv_ent2<MODE, NT, NP, NS, FC>(c, rs, E0, E1, x, acc);
         }
     }
 #pragma unroll 1
