@@ -1036,7 +1036,8 @@ def run_ours(args, d: Dist):
         "config": {"workload": WORKLOADS[args.workload]["desc"], "n": int(case.shape[0]),
                    "nside": case.nside, "bins": nb, "segments_per_step": seg,
                    "kernel": (f"wavefront sweep, CTA tile {st.tile_b}x{st.tile_c} columns, "
-                              f"{st.group} direction slots, {st.ctas_per_launch} units, one launch per bin"
+                              f"{st.group} direction slots, {st.ctas_per_launch} units per bin, "
+                              f"{st.bins_per_launch} bin(s) per launch"
                               if wave else
                               f"slab-block sweep, tile {st.tile_b}x{st.tile_c}, slab {st.slab}, "
                               f"dir groups {st.dir_split}, {st.ctas_per_launch} CTAs x {st.launches - 1} launches"),
@@ -1056,7 +1057,8 @@ def run_ours(args, d: Dist):
                      "peak_fp32_gseg": peak_fp32, "peak_mufu_gseg": peak_mufu,
                      "pipes_per_clk_sm": pipes},
         "e2e": e2e,
-        "gpu_launches": int(args.steps * st.launches * nb),
+        # per step: one reduction per bin, one sweep launch per bins_per_launch bins
+        "gpu_launches": int(args.steps * (nb + (st.launches - 1) * nb // max(1, int(st.bins_per_launch)))),
         "clocks": ck,
         "cpu_baseline": cpu,
     }

@@ -96,7 +96,8 @@ typedef struct {
     int64_t segments;        /* exact number of (ray, cell) pairs with ds > 0, all bins */
     int32_t n_dirs;          /* 12 N_side^2 */
     int32_t n_classes;       /* non-empty (dominant axis, octant) classes */
-    int32_t launches;        /* kernel launches per sweep and bin (sweep + reduce) */
+    int32_t launches;        /* kernel launches per sweep and bin (sweep + reduce); a sweep launch
+                                covers bins_per_launch bins */
     int32_t ctas_per_launch; /* CTAs of one slab-block launch */
     int32_t tile_b, tile_c, slab, dir_split;
     int64_t device_bytes;    /* device memory owned by the context */
@@ -105,6 +106,9 @@ typedef struct {
     int32_t n_grids;         /* grids in the context (1 outside batches) */
     int32_t work_items;      /* (class, tile, direction group) items per slab-block launch */
     int32_t persistent;      /* 1 if launches take work items from a queue */
+    int32_t bins_per_launch; /* bins one sweep launch covers: the wavefront sweep takes all bins
+                                in one launch when their buffers fit in a quarter of the free
+                                device memory at setup (at most 8), else 1 */
 } art_sweep_stats;
 
 /* Fill `opt` with defaults (FP32, paper averaging, (kappa, S) inputs, auto

@@ -40,7 +40,8 @@ class ArtSweepStats(C.Structure):
                 ("launches", C.c_int32), ("ctas_per_launch", C.c_int32), ("tile_b", C.c_int32),
                 ("tile_c", C.c_int32), ("slab", C.c_int32), ("dir_split", C.c_int32),
                 ("device_bytes", C.c_int64), ("variant", C.c_int32), ("group", C.c_int32),
-                ("n_grids", C.c_int32), ("work_items", C.c_int32), ("persistent", C.c_int32)]
+                ("n_grids", C.c_int32), ("work_items", C.c_int32), ("persistent", C.c_int32),
+                ("bins_per_launch", C.c_int32)]
 
 
 class ArtChem(C.Structure):

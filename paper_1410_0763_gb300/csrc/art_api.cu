@@ -432,7 +432,8 @@ art_status setup_wave(art_ctx *ctx, int w)
     ctx->n_ctas = ctx->wave.n_units;
     ctx->persistent = 0;
     ctx->plane_elems = 0;
-    const size_t jb = (size_t)std::max<long long>(1, ctx->wave.jpart_floats) * sizeof(float);
+    const size_t jb =
+        (size_t)std::max<long long>(1, ctx->wave.jpart_floats) * ctx->wave.bins_per_launch * sizeof(float);
     if ((s = dev_alloc(ctx, &ctx->d_jpart, jb)) != ART_OK) return s;
     ctx->jpart_bytes = jb;
     const size_t gb = ctx->grids.size() * sizeof(GridDev<double>);
@@ -495,10 +496,12 @@ template <typename real> art_status do_sweep(art_ctx *ctx, real *J, real *Jin, r
         }
         if (ctx->persistent) CK(ctx, cudaMemsetAsync(ctx->d_counter, 0, ctx->counter_bytes, st));
         if (ctx->profiling) CK(ctx, cudaEventRecord(e0, st));
-        if (ctx->wave.on) {
+        // the wavefront sweeps bins_per_launch bins per launch (all of them, or one)
+        const int wnb = ctx->wave.on ? ctx->wave.bins_per_launch : 1;
+        if (ctx->wave.on && b % wnb == 0) {
             art_status ws = art_wave_launch(ctx, reinterpret_cast<const float2 *>(a.field0),
                                             reinterpret_cast<const float2 *>(a.field1),
-                                            reinterpret_cast<const float2 *>(a.field2), float(ctx->i_bc[b]), st);
+                                            reinterpret_cast<const float2 *>(a.field2), n, b, st);
             if (ws != ART_OK) return ws;
         }
         for (int k = 0; k < ctx->nblocks && !ctx->wave.on; ++k) {
@@ -512,7 +515,8 @@ template <typename real> art_status do_sweep(art_ctx *ctx, real *J, real *Jin, r
         }
         if (ctx->profiling) CK(ctx, cudaEventRecord(e1, st));
         ReduceArgs<real> r{};
-        r.jpart = static_cast<const real *>(ctx->d_jpart);
+        r.jpart = static_cast<const real *>(ctx->d_jpart) +
+                  (ctx->wave.on ? (long long)(b % wnb) * ctx->wave.jpart_floats : 0LL);
         r.field_nat = fields + (2LL * ctx->nbins + b) * n;
         r.grids = static_cast<const GridDev<real> *>(ctx->d_gridinfo);
         r.n_grids = (int)ctx->grids.size();
@@ -936,6 +940,7 @@ art_status art_get_stats(const art_ctx *ctx, art_sweep_stats *s)
     s->n_grids = (int32_t)ctx->grids.size();
     s->work_items = ctx->n_work;
     s->persistent = ctx->persistent;
+    s->bins_per_launch = ctx->wave.on ? ctx->wave.bins_per_launch : 1;
     return ART_OK;
 }
 

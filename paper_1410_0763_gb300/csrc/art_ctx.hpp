@@ -51,6 +51,7 @@ struct art_sur_bufs {
 struct art_wave_state {
     bool on = false;
     int variant = 0, wb = 0, wc = 0, dmax = 0, np = 1, n_units = 0;
+    int bins_per_launch = 1;    // all of a sweep's bins in one launch when their buffers fit
     void *units = nullptr, *classes = nullptr, *rtab = nullptr;   // rtab: run tables of the direction groups
     long long rtab_len = 0;     // float4 count
     float *edge = nullptr;      // edge intensities handed between CTA tiles
@@ -141,7 +142,7 @@ int art_wave_dmax(int w);
 int art_wave_default(int maxc, long long cells);   // default shape: class size, largest grid
 void art_wave_free(art_ctx *ctx);
 art_status art_wave_setup(art_ctx *ctx, int w);
-art_status art_wave_launch(art_ctx *ctx, const float2 *f0, const float2 *f1, const float2 *f2, float i_bc,
-                           cudaStream_t st);
+art_status art_wave_launch(art_ctx *ctx, const float2 *f0, const float2 *f1, const float2 *f2,
+                           long long bin_cells, int b0, cudaStream_t st);
 art_status art_wave_status(art_ctx *ctx, cudaStream_t st);
 art_status art_wave_status_async(art_ctx *ctx, int *host, cudaStream_t st);

@@ -421,11 +421,27 @@ art_status art_wave_setup(art_ctx *ctx, int w)
         ctx->n_part += g.n_part;
         ctx->seg_count += g.seg_count;
     }
+    // All bins in one launch (the units of bin b after those of bin b - 1, so
+    // no launch drains between bins) when their edge buffers and J partials
+    // fit in a quarter of the free device memory; else one launch per bin.
+    int nb = 1;
+    if (ctx->nbins > 1 && ctx->nbins <= WV_MAXB) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+            const double extra = double(ctx->nbins - 1) * double(t.edge_floats + t.jpart_floats) * sizeof(float);
+            if (extra <= 0.25 * double(fr)) nb = ctx->nbins;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    W.bins_per_launch = nb;
     const size_t ub = t.units.size() * sizeof(WaveUnit), cb = t.classes.size() * sizeof(WaveClass);
     const size_t sb = std::max<size_t>(16, t.rtab.size() * sizeof(float4));
-    const size_t eb = std::max<size_t>(16, (size_t)t.edge_floats * sizeof(float));
-    // error word, ticket, progress flags, then (8-byte aligned) four counters of ART_WAVE_STATS builds
-    const size_t fb = ((size_t(W.n_units) * (v.wb + v.wc) + 2) * sizeof(int) + 7) / 8 * 8 + 4 * sizeof(long long);
+    const size_t eb = std::max<size_t>(16, (size_t)t.edge_floats * nb * sizeof(float));
+    // error word, ticket, progress flags of every bin, then (8-byte aligned) four counters of
+    // ART_WAVE_STATS builds
+    const size_t fb =
+        ((size_t(W.n_units) * (v.wb + v.wc) * nb + 2) * sizeof(int) + 7) / 8 * 8 + 4 * sizeof(long long);
     struct {
         void **p;
         size_t b;
@@ -452,18 +468,26 @@ art_status art_wave_setup(art_ctx *ctx, int w)
     return ART_OK;
 }
 
-// One bin's wavefront sweep into the context's J partials: clear the ticket
-// and progress flags (the error word, flags[0], is kept until read), launch.
-art_status art_wave_launch(art_ctx *ctx, const float2 *f0, const float2 *f1, const float2 *f2, float i_bc,
-                           cudaStream_t st)
+// The wavefront sweep of bins b0 .. b0 + bins_per_launch - 1 (fields of bin
+// b0 at f0, f1, f2, the next bins bin_cells elements further) into the
+// context's J partials (bin b0 + k at k jpart_floats): clear the ticket and
+// progress flags (the error word, flags[0], is kept until read), launch.
+art_status art_wave_launch(art_ctx *ctx, const float2 *f0, const float2 *f1, const float2 *f2,
+                           long long bin_cells, int b0, cudaStream_t st)
 {
     art_wave_state &W = ctx->wave;
     const WVariant &v = kWave[W.variant];
+    const int nb = W.bins_per_launch;
+    if (nb < 1 || nb > WV_MAXB || b0 < 0 || b0 + nb > ctx->nbins)
+        return art_fail(ctx, ART_E_INVALID, "wave sweep: bins of a launch out of range");
     WCK(ctx, cudaMemsetAsync(W.flags + 1, 0, W.flag_bytes - sizeof(int), st));
     WaveArgs a{};
     a.field0 = f0;
     a.field1 = f1;
     a.field2 = f2;
+    a.n_bins = nb;
+    a.bin_cells = bin_cells;
+    for (int k = 0; k < nb; ++k) a.i_bc[k] = float(ctx->i_bc[b0 + k]);
     a.rtab = static_cast<const float4 *>(W.rtab);
     a.rtab_len = W.rtab_len;
     a.units = static_cast<const WaveUnit *>(W.units);
@@ -475,14 +499,13 @@ art_status art_wave_launch(art_ctx *ctx, const float2 *f0, const float2 *f1, con
     a.flags = W.flags + 2;
     a.n_units = W.n_units;
     a.field_form = ctx->opt.field_form;
-    a.i_bc = i_bc;
     a.stall_unit = W.stall_unit;
     a.wait_ns = W.wait_ns;
     a.edge_floats = W.edge_floats;
     a.jpart_floats = W.jpart_floats;
     a.stats = W.stats;
     if (W.n_units == 0) return ART_OK;
-    WCK(ctx, v.launch(a, W.n_units, st));
+    WCK(ctx, v.launch(a, W.n_units * nb, st));
     return ART_OK;
 }
 

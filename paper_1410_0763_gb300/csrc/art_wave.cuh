@@ -91,6 +91,8 @@ constexpr int WV_ENT = 4;   // float4 per entry
 
 __host__ __device__ constexpr int wv_block(int nd) { return 1 + WV_ENT * nd; }
 
+constexpr int WV_MAXB = 8;   // bins one launch can hold
+
 struct WaveArgs {
     const float2 *field0, *field1, *field2;   // (kappa, S or eps), sweep-axis layouts, one bin
     const float4 *rtab;       // run tables of the direction groups
@@ -104,11 +106,13 @@ struct WaveArgs {
     int *err;                 // bit 0: a wait ran out; bit 1: check failure (checked builds)
     int n_units;
     int field_form;           // 0: S, 1: eps
-    float i_bc;               // intensity of every ray where it enters the box
+    int n_bins;               // bins in this launch (units of bin b take tickets b n_units ..)
+    long long bin_cells;      // field elements from one bin to the next
+    float i_bc[WV_MAXB];      // intensity of every ray where it enters the box, per bin
     int stall_unit;           // test hook: this unit never publishes its progress (-1: none)
     long long wait_ns;        // bound of every wait
-    long long edge_floats;    // size of the edge buffer (checked builds)
-    long long jpart_floats;   // size of the partials (checked builds)
+    long long edge_floats;    // edge buffer of one bin (the bins' buffers follow each other)
+    long long jpart_floats;   // J partials of one bin (likewise)
     long long *stats;         // counters of ART_WAVE_STATS builds: barrier, unit, poll-loop cycles, polls
 };
 
@@ -748,8 +752,14 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
     const int bl = lane & 7, cl = lane >> 3;
     if (tid == 0) s_unit = atomicAdd(p.ticket, 1);
     __syncthreads();
-    const int u = s_unit;
-    if (u >= p.n_units) return;
+    const int ticket = s_unit;
+    if (ticket >= p.n_units * p.n_bins) return;
+    // all bins' units in one launch, bin by bin in ticket order: the units of
+    // a bin wait only on units of the same bin, which have smaller tickets
+    const int bin = ticket / p.n_units, u = ticket - bin * p.n_units;
+    const float i_bc = p.i_bc[bin];
+    float *const edge = p.edge + bin * p.edge_floats;
+    int *const flags = p.flags + (long long)bin * p.n_units * (WB + WC);
     const WaveUnit U = p.units[u];
     const WaveClass C = p.classes[U.cls];
     const int Na = C.Na, nd = U.nd;
@@ -764,7 +774,7 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
     // the lane's columns in the axis-a field layout [a][c][b] (row r at
     // F0 + r dpc Nb), and its cells of slab m in the natural layout of the J
     // partial (row r at J0 + r dpc stride_c + m jstep)
-    const float2 *Fb = (C.a == 0 ? p.field0 : (C.a == 1 ? p.field1 : p.field2)) + C.cell_off;
+    const float2 *Fb = (C.a == 0 ? p.field0 : (C.a == 1 ? p.field1 : p.field2)) + bin * p.bin_cells + C.cell_off;
     const long long f0 = (long long)pc0 * C.Nb + pb;
     const int fslab = C.Nb * C.Nc, frow = dpc * C.Nb;
     const long long ja = C.sa > 0 ? 0 : (long long)(Na - 1) * C.stride_a;
@@ -779,8 +789,8 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
             jl_ok = jl_ok && j1 >= 0 && j1 < p.jpart_floats && j2 >= 0 && j2 < p.jpart_floats;
         }
     jl_ok = wv_ok(jl_ok, p.err);
-    float *J0 = p.jpart + U.jpart + (inmask ? jb0 : 0);
-    const bool stalled = u == p.stall_unit;
+    float *J0 = p.jpart + bin * p.jpart_floats + U.jpart + (inmask ? jb0 : 0);
+    const bool stalled = ticket == p.stall_unit;
     // ART_WAVE_STATS builds: cycles in the poll loops and polls (lane 0), cycles at the step
     // barriers and in the unit (every warp), added to p.stats when the unit ends
     long long st_poll[2] = {0, 0}, st_bar = 0;
@@ -801,24 +811,24 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
     // box-edge inputs carry the boundary intensity in both parities
     if (U.up_b < 0)
         for (int e = tid; e < WC * DMAX * XBW; e += NT) {
-            XB[e] = p.i_bc;
-            XB[Sh::XB_PAR + e] = p.i_bc;
+            XB[e] = i_bc;
+            XB[Sh::XB_PAR + e] = i_bc;
         }
     if (U.up_c < 0)
         for (int e = tid; e < WB * DMAX * 8; e += NT) {
-            XC[e] = p.i_bc;
-            XC[Sh::XC_PAR + e] = p.i_bc;
+            XC[e] = i_bc;
+            XC[Sh::XC_PAR + e] = i_bc;
         }
     // every ray enters the box with the boundary intensity
     for (int d = 0; d < nd; ++d)
 #pragma unroll
-        for (int r = 0; r < R; ++r) RS[(d * NT + tid) * R + r] = p.i_bc;
+        for (int r = 0; r < R; ++r) RS[(d * NT + tid) * R + r] = i_bc;
 
     // progress of the upstream warps last seen by this warp (uniform), and the
     // flag values lane 0 read in the previous step (used before polling again)
     int seen_b = 0, seen_c = 0, pref_b = 0, pref_c = 0;
-    const int *up_flag_b = U.up_b >= 0 ? p.flags + (long long)U.up_b * (WB + WC) + wc : nullptr;
-    const int *up_flag_c = U.up_c >= 0 ? p.flags + (long long)U.up_c * (WB + WC) + WC + wb : nullptr;
+    const int *up_flag_b = U.up_b >= 0 ? flags + (long long)U.up_b * (WB + WC) + wc : nullptr;
+    const int *up_flag_c = U.up_c >= 0 ? flags + (long long)U.up_c * (WB + WC) + WC + wb : nullptr;
 
     // Stage what step t + 1 reads: the table of slab t + 1, this lane's fields
     // of its next slab, and (warps on the CTA's upstream edges) the upstream
@@ -859,7 +869,7 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
                         if (wv_ok(eb_up >= 0 && o + XBW <= p.edge_floats, p.err)) {
                             float *dst = XB + rp * Sh::XB_PAR + (wc * DMAX + dd) * XBW;
 #pragma unroll
-                            for (int q = 0; q < XBW; q += 4) wv_cp16(dst + q, p.edge + o + q);
+                            for (int q = 0; q < XBW; q += 4) wv_cp16(dst + q, edge + o + q);
                         }
                     }
                 }
@@ -883,8 +893,8 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
                         const long long o = ec_up + (((long long)s * WB + wb) * DMAX + dd) * 8;
                         if (wv_ok(ec_up >= 0 && o + 8 <= p.edge_floats, p.err)) {
                             float *dst = XC + rp * Sh::XC_PAR + (wb * DMAX + dd) * 8;
-                            wv_cp16(dst, p.edge + o);
-                            wv_cp16(dst + 4, p.edge + o + 4);
+                            wv_cp16(dst, edge + o);
+                            wv_cp16(dst + 4, edge + o + 4);
                         }
                     }
                 }
@@ -910,8 +920,8 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
         const int m = t - wb - wc;
         // progress of the slabs written to global memory in earlier steps
         if (lane == 0 && !stalled && m - 1 >= 0 && m - 1 < Na && (m & (C.pub - 1)) == 0) {
-            if (b_out) wv_st_release(p.flags + fl_b, m);
-            if (c_out) wv_st_release(p.flags + fl_c, m);
+            if (b_out) wv_st_release(flags + fl_b, m);
+            if (c_out) wv_st_release(flags + fl_c, m);
         }
         if (!stage(t)) bad = 1;
         if (m >= 0 && m < Na) {
@@ -996,7 +1006,7 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
                         if (wv_ok(o + XBW <= p.edge_floats, p.err))
 #pragma unroll
                             for (int q = 0; q < XBW; q += 4)
-                                *reinterpret_cast<float4 *>(p.edge + o + q) =
+                                *reinterpret_cast<float4 *>(edge + o + q) =
                                     *reinterpret_cast<const float4 *>(srcs + q);
                     }
                 if (c_out && U.ec >= 0)
@@ -1004,8 +1014,8 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
                         const float *srcs = XC + par * Sh::XC_PAR + ((wc + 1) * WB + wb) * DMAX * 8 + dd * 8;
                         const long long o = U.ec + (((long long)m * WB + wb) * DMAX + dd) * 8;
                         if (wv_ok(o + 8 <= p.edge_floats, p.err)) {
-                            *reinterpret_cast<float4 *>(p.edge + o) = *reinterpret_cast<const float4 *>(srcs);
-                            *reinterpret_cast<float4 *>(p.edge + o + 4) = *reinterpret_cast<const float4 *>(srcs + 4);
+                            *reinterpret_cast<float4 *>(edge + o) = *reinterpret_cast<const float4 *>(srcs);
+                            *reinterpret_cast<float4 *>(edge + o + 4) = *reinterpret_cast<const float4 *>(srcs + 4);
                         }
                     }
             }
@@ -1028,8 +1038,8 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
         return;
     }
     if (lane == 0 && !stalled) {
-        if (b_out) wv_st_release(p.flags + fl_b, Na);
-        if (c_out) wv_st_release(p.flags + fl_c, Na);
+        if (b_out) wv_st_release(flags + fl_b, Na);
+        if (c_out) wv_st_release(flags + fl_c, Na);
     }
 }
 

@@ -148,14 +148,30 @@ def test_boundary_intensity(orc):
     assert rel(J, j_o) < 1e-5
 
 
-def test_multiple_bins(orc):
+@pytest.mark.parametrize("nbins,boundary", [(3, 0.0), (3, 0.7), (9, 0.0)])
+def test_multiple_bins(orc, nbins, boundary):
+    """Up to 8 bins go through one launch (their units in bin order under one ticket counter,
+    each bin with its fields, boundary intensity, edge buffers, flags and J partials); more
+    bins through one launch each.  Every bin against the oracle."""
     shape = (12, 14, 16)
-    rng = np.random.default_rng(5)
-    kap = f32(0.4 * np.exp(rng.standard_normal((3,) + shape)))
-    S = f32(rng.random((3,) + shape))
-    J, Jin, _ = run(kap, S, 3, nbins=3)
-    for b in range(3):
-        jin_o, j_o, _ = orc.sweep(kap[b], S[b], 3)
+    rng = np.random.default_rng(5 + nbins)
+    kap = f32((0.1 + 0.1 * np.arange(nbins))[:, None, None, None] * np.exp(rng.standard_normal((nbins,) + shape)))
+    S = f32(rng.random((nbins,) + shape))
+    sw = art.ArtSweep(shape, 3, nbins)
+    if boundary:
+        sw.set_boundary_intensity([boundary * (b + 1) for b in range(nbins)])
+    k = torch.as_tensor(np.ascontiguousarray(kap), dtype=torch.float32, device="cuda")
+    s = torch.as_tensor(np.ascontiguousarray(S), dtype=torch.float32, device="cuda")
+    J, Jin = torch.empty_like(k), torch.empty_like(k)
+    sw.set_fields(k, s)
+    sw.sweep(J, Jin)
+    assert sw.check() == art.ART_OK
+    st = sw.stats
+    sw.close()
+    assert st.variant >= WAVE0 and st.bins_per_launch == (nbins if nbins <= 8 else 1)
+    J, Jin = J.cpu().numpy().astype(np.float64), Jin.cpu().numpy().astype(np.float64)
+    for b in range(nbins):
+        jin_o, j_o, _ = orc.sweep(kap[b], S[b], 3, i_bc=boundary * (b + 1))
         assert rel(Jin[b], jin_o) < 1e-5
         assert rel(J[b], j_o) < 1e-5
 
