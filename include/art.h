@@ -277,7 +277,9 @@ art_status art_sweep_check(art_ctx *ctx, void *stream);
 /*
  * Bound of every wait of the wavefront sweep (seconds, default 2) and a test
  * hook: stall_unit >= 0 names a unit (CTA tile) that computes but never
- * publishes its progress, so the tiles downstream of it wait until the bound
+ * publishes its progress (by its ticket: unit u of bin b of a launch that
+ * holds several bins is b * ctas_per_launch + u, art_sweep_stats), so the
+ * tiles downstream of it wait until the bound
  * and the sweep reports ART_E_TIMEOUT through art_sweep_check; -1 (the
  * default) disables the hook.  Errors: ART_E_INVALID (NULL ctx, bound not in
  * (0, 60], stall_unit < -1).

@@ -5,7 +5,7 @@
 // segment, the Delta-tau (= Delta-s) weighted cell average of
 // Eq. (averaged_intensity), the angle average of Eq. (mean_intensity)), laid out
 // as a wavefront so that no ray segment is computed twice and one launch covers
-// the whole sweep of a bin:
+// the whole sweep of a bin, or of every bin when their buffers fit:
 //
 //  * Directions are grouped into octant-axis classes; in a class's canonical
 //    frame (axes mirrored so that every component is >= 0) rays advance in +a
@@ -26,13 +26,13 @@
 //    step t, so everything it receives from the warps upstream of it was
 //    written one step earlier (double-buffered by step parity): one barrier
 //    per step, and every segment is computed once.
-//  * A unit of work is (grid, class, direction group, CTA tile) over all slabs.
-//    Units are numbered in an order in which every unit comes after the two
-//    units upstream of it (the tile diagonal), and a CTA takes the next number
-//    from a ticket counter when it starts.  A CTA waits only on units with
+//  * A unit of work is (grid, class, direction group, CTA tile) over all slabs,
+//    for one bin.  Units are numbered in an order in which every unit comes
+//    after the two units upstream of it (the tile diagonal; bin by bin), and
+//    a CTA takes the next number from a ticket counter when it starts.  A CTA waits only on units with
 //    smaller tickets, which are running or done, so the waits always end.
 //    Each warp row on a CTA's downstream faces publishes its progress every
-//    PUB slabs (release at GPU scope); the downstream warp polls only when
+//    C.pub slabs (release at GPU scope); the downstream warp polls only when
 //    the last value it saw does not cover the slab it needs (then acquires).
 //    Every wait is bounded in time; one that runs out sets an error word,
 //    after which every CTA leaves its loop at the next step.
@@ -47,12 +47,12 @@
 //  * The two cells of a pair share every segment length, so the arithmetic of
 //    Eq. (rt) runs as packed FP32x2 instructions on both.
 //  * Arithmetic per (warp, slab), chosen by ballot over the warp's cells:
-//    every kappa below KAP_THIN (series only, as a polynomial in the segment
-//    length with per-cell coefficients), every kappa at or above
-//    KAP_THICK (hardware exponential only), else both with a per-segment
-//    select (series below x = 1/4).  The series path deposits ds phi(x)
-//    directly, so kappa = 0 needs no special case; the exponential path
-//    deposits 1 - e^-x and the cell's sum is scaled by 1/kappa once.
+//    every kappa below KAP_THIN, or KAP_THIN6 (series only, to x^4 or x^6, as
+//    a polynomial in the segment length with per-cell coefficients), every
+//    kappa at or above KAP_THICK (hardware exponential only), else both with a
+//    per-segment select (series below x = 1/4).  The series path deposits
+//    ds phi(x) directly, so kappa = 0 needs no special case; the exponential
+//    path deposits 1 - e^-x and the cell's sum is scaled by 1/kappa once.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>

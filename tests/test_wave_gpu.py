@@ -252,6 +252,34 @@ def test_a_stalled_tile_times_out_and_the_context_recovers(orc):
     assert rel(Jin.cpu().numpy().astype(np.float64), jin_o) < 1e-5
 
 
+def test_a_stalled_tile_of_a_later_bin_times_out_and_the_context_recovers(orc):
+    """The same with 3 bins in one launch: the stalled unit is the first of the last bin (its
+    ticket follows all units of the earlier bins); the context recovers and every bin is
+    correct afterwards."""
+    rng = np.random.default_rng(23)
+    shape = (40, 36, 44)
+    kap = f32(0.3 * np.exp(rng.standard_normal((3,) + shape)))
+    S = f32(rng.random((3,) + shape))
+    k = torch.as_tensor(kap, dtype=torch.float32, device="cuda")
+    s = torch.as_tensor(S, dtype=torch.float32, device="cuda")
+    sw = art.ArtSweep(shape, 2, 3)
+    st = sw.stats
+    assert st.bins_per_launch == 3
+    sw.set_fields(k, s)
+    Jin = torch.empty_like(k)
+    sw.set_wait(0.2, 2 * st.ctas_per_launch)   # ticket of unit 0 of bin 2
+    sw.sweep(None, Jin)
+    assert sw.check() == art.ART_E_TIMEOUT
+    sw.set_wait(2.0, -1)
+    sw.sweep(None, Jin)
+    assert sw.check() == art.ART_OK
+    sw.close()
+    got = Jin.cpu().numpy().astype(np.float64)
+    for b in range(3):
+        jin_o, _, _ = orc.sweep(kap[b], S[b], 2)
+        assert rel(got[b], jin_o) < 1e-5
+
+
 def clump_boundary_cells(rho, rng, count):
     """Cells of the clumpy medium whose density differs from a face neighbour's by more than
     10x (the surfaces of the overdense spheres), `count` of them at random."""
