@@ -47,10 +47,10 @@
 //  * The two cells of a pair share every segment length, so the arithmetic of
 //    Eq. (rt) runs as packed FP32x2 instructions on both.
 //  * Arithmetic per (warp, slab), chosen by ballot over the warp's cells:
-//    every kappa below KAP_THIN, or KAP_THIN6 (series only, to x^4 or x^6, as
-//    a polynomial in the segment length with per-cell coefficients), every
-//    kappa at or above KAP_THICK (hardware exponential only), else both with a
-//    per-segment select (series below x = 1/4).  The series path deposits
+//    every kappa below KAP_THIN2, KAP_THIN or KAP_THIN6 (series only, to x^2,
+//    x^4 or x^6, as a polynomial in the segment length with per-cell
+//    coefficients), every kappa at or above KAP_THICK (hardware exponential
+//    only), else both with a per-segment select (series below x = 1/4).  The series path deposits
 //    ds phi(x) directly, so kappa = 0 needs no special case; the exponential
 //    path deposits 1 - e^-x and the cell's sum is scaled by 1/kappa once.
 #pragma once
@@ -122,6 +122,7 @@ struct WaveArgs {
 // KAP_THIN6 = 0.433: < 7.1e-8), to x^5 in the mixed path below x = 1/4
 // (< 6e-8).  Exponential path: 1 - ex2.approx(-x log2 e), whose absolute error
 // (~2^-22) is below 2e-6 of a cell's deposit when kappa >= KAP_THICK.
+constexpr float KAP_THIN2 = 0.01f;   // x^2 path: x <= 0.0174, truncation < 2.2e-7
 constexpr float KAP_THIN = 0.1f;
 constexpr float KAP_THIN6 = 0.25f;
 constexpr float KAP_THICK = 0.5f;
@@ -231,7 +232,8 @@ __device__ __forceinline__ float2 f2s(float v) { return make_float2(v, v); }
 // so each FP32 operation of Eq. (rt) runs on both at once as one packed FP32x2
 // instruction.
 //
-// Thin paths (every kappa < KAP_THIN, K = 4; every kappa < KAP_THIN6, K = 6):
+// Thin paths (every kappa below KAP_THIN2, KAP_THIN or KAP_THIN6: K = 2, 4 or
+// 6, each within the same truncation bound):
 // the deposit coefficient of a segment, ds phi(kappa ds) with phi to x^K,
 // written as a polynomial in ds whose coefficients are the cell's:
 // ds + ds^2 (c_1 + ds (c_2 + ... + ds c_K)), c_k = (-kappa)^k / (k + 1)!.
@@ -733,7 +735,7 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
 {
     using Sh = WaveShape<WB, WC, DMAX, NP>;
     constexpr int NT = Sh::NT, RT = Sh::RT, R = Sh::R, XBW = Sh::XBW;
-    // shapes with at least 160 registers a thread take two thin-path entries at a time
+    // shapes with at least 160 registers a thread take two x^2-path entries at a time
     constexpr bool TWO = 65536 / (MINB * NT) >= 160;
     // the second thin path (kappa < KAP_THIN6) in shapes with at least 96 registers a thread
     // (the others take the mixed path there)
@@ -927,17 +929,18 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
         if (m >= 0 && m < Na) {
             const int par = t & 1;
             float2 kap[NP], src[NP];
-            bool thin = true, thin6 = true, thick = true;
+            float kmax = 0.0f, kmin = __int_as_float(0x7f800000);
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
                 const float4 f = reinterpret_cast<const float4 *>(FS + (par * NT + tid) * R)[i];
                 const bool i0 = inmask >> (2 * i) & 1, i1 = inmask >> (2 * i + 1) & 1;
                 kap[i] = make_float2(i0 ? f.x : 0.0f, i1 ? f.z : 0.0f);
                 src[i] = make_float2(i0 ? f.y : 0.0f, i1 ? f.w : 0.0f);
-                thin = thin && kap[i].x < KAP_THIN && kap[i].y < KAP_THIN;
-                thin6 = thin6 && kap[i].x < KAP_THIN6 && kap[i].y < KAP_THIN6;
-                thick = thick && kap[i].x >= KAP_THICK && kap[i].y >= KAP_THICK;
+                kmax = fmaxf(kmax, fmaxf(kap[i].x, kap[i].y));
+                kmin = fminf(kmin, fminf(kap[i].x, kap[i].y));
             }
+            // the mode of the warp, by vote on its cells' largest and smallest kappa
+            const bool all_thin2 = THIN6 && __all_sync(0xffffffffu, kmax < KAP_THIN2);
             WvXch x;
             x.bo = xb0 + 4 * (par * Sh::XB_PAR + ((wb + 1) * WC + wc) * DMAX * XBW + R * cl);
             x.bi = xb0 + 4 * ((par ^ 1) * Sh::XB_PAR + (wb * WC + wc) * DMAX * XBW + R * cl);
@@ -950,19 +953,28 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
             x.nslot = DMAX;
             x.err = p.err;
             const unsigned tb = tab0 + 16 * (m & (RT - 1)) * Sh::TABS;
-            const bool all_thin = __all_sync(0xffffffffu, thin), all_thick = __all_sync(0xffffffffu, thick);
-            const bool all_thin6 = THIN6 && __all_sync(0xffffffffu, thin6);
+            const bool all_thin = __all_sync(0xffffffffu, kmax < KAP_THIN);
+            const bool all_thick = __all_sync(0xffffffffu, kmin >= KAP_THICK);
+            const bool all_thin6 = THIN6 && __all_sync(0xffffffffu, kmax < KAP_THIN6);
             WvRows<NP> js;
-            if (all_thin) {
+            // (code size decides which paths take two entries at a time: with the
+            // x^2 path's loop doubled and the others single, the modes of a mixed
+            // bin still fit the instruction cache)
+            if (THIN6 && all_thin2) {   // (the x^2 and x^6 paths: shapes with >= 96 registers)
+                WvThin<2> c[NP];
+#pragma unroll
+                for (int i = 0; i < NP; ++i) c[i] = wv_thin<2>(kap[i], src[i], p.field_form);
+                js = wv_dirs<MODE_THIN, NT, NP, TWO>(c, rs0, tb, nd, x);
+            } else if (all_thin) {
                 WvThin<4> c[NP];
 #pragma unroll
                 for (int i = 0; i < NP; ++i) c[i] = wv_thin<4>(kap[i], src[i], p.field_form);
-                js = wv_dirs<MODE_THIN, NT, NP, TWO>(c, rs0, tb, nd, x);
+                js = wv_dirs<MODE_THIN, NT, NP, false>(c, rs0, tb, nd, x);
             } else if (THIN6 && all_thin6) {
                 WvThin<6> c[NP];
 #pragma unroll
                 for (int i = 0; i < NP; ++i) c[i] = wv_thin<6>(kap[i], src[i], p.field_form);
-                js = wv_dirs<MODE_THIN, NT, NP, false>(c, rs0, tb, nd, x);   // (code size: one entry at a time)
+                js = wv_dirs<MODE_THIN, NT, NP, false>(c, rs0, tb, nd, x);
             } else if (THIN6 && !all_thick) {   // (the coefficient form needs the registers of THIN6 shapes)
                 WvMixed c[NP];
 #pragma unroll
