@@ -130,14 +130,19 @@ def parse():
 # distributed plumbing
 # ---------------------------------------------------------------------------
 class Dist:
-    def __init__(self, backend: str):
+    def __init__(self, backend: str, always: bool = False):
+        """One process per GPU (torchrun's environment); a process group when there are several
+        ranks, or always (the sharded sweep's collectives run on a one-rank group too)."""
         self.world = int(os.environ.get("WORLD_SIZE", "1"))
         self.rank = int(os.environ.get("RANK", "0"))
         self.local = int(os.environ.get("LOCAL_RANK", "0"))
         self.dist = None
-        if self.world > 1:
+        if self.world > 1 or always:
             import torch.distributed as dist
             os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            os.environ.setdefault("MASTER_PORT", "29517")
+            os.environ.setdefault("WORLD_SIZE", str(self.world))
+            os.environ.setdefault("RANK", str(self.rank))
             dist.init_process_group(backend)
             self.dist = dist
 
@@ -870,6 +875,10 @@ def run_shard(args, d: Dist):
     d.barrier()
     ck = clocks.stop()
     total_ms = d.max(sum(a.elapsed_time(b) for a, b in evs), dev)
+    st = sh.sw.stats if sh.sw is not None else None
+    # per step: the sweep launches (one per bins_per_launch bins), one reduction per bin, the
+    # rank-ordered sum of the exchanged blocks
+    launches = (nb // max(1, int(st.bins_per_launch)) + nb + 1) if st is not None else 1
     sh.close()
     out = {
         "metric": METRIC, "value": seg_total * args.steps / (total_ms * 1e-3), "unit": UNIT, "n_gpus": d.world,
@@ -880,7 +889,7 @@ def run_shard(args, d: Dist):
                    "parallelism": f"directions split over {d.world} ranks; rank-ordered reduce-scatter "
                                   f"(point-to-point) + all-gather of J^in"},
         "clocks": ck,
-        "gpu_launches": int(args.steps * 3 * nb),
+        "gpu_launches": int(args.steps * launches),
     }
     if d.rank == 0:
         print(json.dumps(out), flush=True)
@@ -1267,7 +1276,7 @@ def main():
         finally:
             d.close()
         return
-    d = Dist("nccl")
+    d = Dist("nccl", always=args.shard)
     try:
         (run_shard if args.shard else run_ours)(args, d)
     finally:
