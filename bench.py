@@ -62,6 +62,15 @@ FP32_OPS_PER_SEG = 7
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
+def measured_hbm_gbs():
+    """Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json), else the fallback."""
+    try:
+        with open(os.path.join(HERE, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
 def measured_bf16_peak():
     """Sustained dense BF16 TFLOP/s measured on this machine (MEASURED_PEAKS.json), else the fallback."""
     try:
@@ -966,6 +975,12 @@ def run_ours(args, d: Dist):
     peak_fp32 = ffma / FP32_OPS_PER_SEG * n_sm * sm_mhz * 1e6 / 1e9
     peak_gseg = min(peak_mufu, peak_fp32)
     sweep_share = pr.sweep_ms / max(pr.sweep_ms + pr.reduce_ms, 1e-9)
+    # the DRAM side of the same kernel: recorded ncu bytes per launch over the live launch time
+    traffic = recorded_traffic(args.workload, int(st.variant), int(st.persistent))
+    launches_per_step = max(1, nb // max(1, int(st.bins_per_launch))) if st.variant >= 16 else st.launches - 1
+    launch_ms = pr.sweep_ms / (prof_steps * max(1, launches_per_step))
+    hbm = measured_hbm_gbs()
+    dram_gbs = traffic / (launch_ms * 1e-3) / 1e9 if traffic else None
     wave = st.variant >= 16
     kname = "wave_kernel" if wave else ("sweep_queue_kernel" if st.persistent else "sweep_block_kernel")
 
@@ -1055,8 +1070,10 @@ def run_ours(args, d: Dist):
                    "parallelism": f"weak x{d.world} (independent grid per GPU)"},
         "roofline": {"bound": "alu", "achieved": achieved_gseg, "peak": peak_gseg, "unit": "Gseg/s",
                      "frac": achieved_gseg / peak_gseg,
-                     "traffic": recorded_traffic(args.workload, int(st.variant), int(st.persistent)),
+                     "traffic": traffic,
                      "traffic_unit": "DRAM bytes per sweep launch (ncu)",
+                     "dram_gbs": dram_gbs, "hbm_frac": dram_gbs / hbm if dram_gbs else None,
+                     "hbm_peak_gbs": hbm, "binding": "FP32 pipe" if peak_fp32 <= peak_mufu else "MUFU",
                      "kernel": f"{kname} variant {st.variant} (tile {st.tile_b}x{st.tile_c})",
                      "kernel_share_of_step": sweep_share,
                      "peak_basis": f"binding roof = min(FP32: {ffma}/clk/SM (measured FMAs, scalar or packed FP32x2) / "
