@@ -287,6 +287,18 @@ art_status art_sweep_check(art_ctx *ctx, void *stream);
 art_status art_sweep_set_wait(art_ctx *ctx, double seconds, int stall_unit);
 
 /*
+ * Profiling counters of the wavefront sweep (a library built with
+ * ART_WAVE_STATS=1; zeros in other builds and in contexts that use the
+ * slab-block sweep).  out[4] receives, summed over the sweep launches since
+ * the last call: out[0] warp cycles spent at the per-step block barriers,
+ * out[1] warp cycles in the units (tiles), out[2] cycles lane 0 spent polling
+ * upstream progress flags, out[3] the number of those polls; the counters are
+ * then cleared.  Synchronizes the device.  Errors: ART_E_INVALID (NULL),
+ * ART_E_CUDA.
+ */
+art_status art_wave_counters(art_ctx *ctx, long long *out);
+
+/*
  * The sweeps of n_sets independent field sets held in host memory, streamed
  * through the device: the host-to-device copy and validation of set k + 1 and
  * the device-to-host copy of set k - 1 run on the library's own copy streams

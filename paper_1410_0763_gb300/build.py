@@ -32,8 +32,29 @@ def nvcc_path() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libart")
 
 
+def _defines() -> list[str]:
+    """Preprocessor definitions chosen by the environment (checked, profiling and tuning builds)."""
+    d = []
+    if os.environ.get("ART_WAVE_CHECK") == "1":
+        # the wavefront kernel tests every global index before it is used (slower; for checking runs)
+        d.append("-DART_WAVE_CHECK")
+    if os.environ.get("ART_WAVE_STATS") == "1":
+        # the wavefront kernel counts its barrier and poll cycles (art_wave_counters; for profiling runs)
+        d.append("-DART_WAVE_STATS")
+    # extra definitions for tuning builds (e.g. "-DART_WAVE_PUB=8")
+    d += [x for x in os.environ.get("ART_NVCC_DEFINES", "").split() if x.startswith("-D")]
+    return d
+
+
 def _stale() -> bool:
+    """The library is missing, older than a source, or built with other definitions."""
     if not os.path.exists(LIB):
+        return True
+    try:
+        with open(LIB + ".defines") as f:
+            if f.read().split() != _defines():
+                return True
+    except OSError:
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(INCLUDE, h) for h in ("art.h", "art_net.h")] + [__file__]
@@ -46,15 +67,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = nvcc_path()
     obj_dir = os.path.join(OUT_DIR, "obj")
     os.makedirs(obj_dir, exist_ok=True)
-    common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC] + ARCH
-    if os.environ.get("ART_WAVE_CHECK") == "1":
-        # the wavefront kernel tests every global index before it is used (slower; for checking runs)
-        common += ["-DART_WAVE_CHECK"]
-    if os.environ.get("ART_WAVE_STATS") == "1":
-        # the wavefront kernel counts its barrier and poll cycles (art_wave_counters; for profiling runs)
-        common += ["-DART_WAVE_STATS"]
-    # extra preprocessor definitions for tuning builds (e.g. "-DART_WAVE_PUB=8")
-    common += [d for d in os.environ.get("ART_NVCC_DEFINES", "").split() if d.startswith("-D")]
+    defines = _defines()
+    common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC] + ARCH + defines
     if verbose:
         common += ["-Xptxas", "-v"]
 
@@ -76,6 +90,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(LIB + ".defines", "w") as f:
+        f.write(" ".join(defines) + "\n")
     return LIB
 
 

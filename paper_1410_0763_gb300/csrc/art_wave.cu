@@ -534,10 +534,10 @@ art_status art_wave_status_async(art_ctx *ctx, int *host, cudaStream_t st)
     return ART_OK;
 }
 
-// Counters of a build with ART_WAVE_STATS (a profiling aid, not part of the
-// C ABI): cycles warps spent at the step barriers, cycles in their units,
-// cycles of lane 0 in the poll loops and the number of polls, summed over the
-// launches since the last call; read and cleared.  Zeros in other builds.
+// Counters of a build with ART_WAVE_STATS (a profiling aid): cycles warps
+// spent at the step barriers, cycles in their units, cycles of lane 0 in the
+// poll loops and the number of polls, summed over the launches since the last
+// call; read and cleared.  Zeros in other builds.
 extern "C" art_status art_wave_counters(art_ctx *ctx, long long *out)
 {
     if (!ctx || !out) return ART_E_INVALID;

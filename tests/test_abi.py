@@ -96,6 +96,7 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.art_thermal_default(None) == art.ART_E_INVALID
     assert lib.art_sweep_stream(None, 1, None, None, None, None, None, None) == art.ART_E_INVALID
     assert lib.art_sweep_check(None, None) == art.ART_E_INVALID
+    assert lib.art_wave_counters(None, None) == art.ART_E_INVALID
     assert lib.art_iterate_ionization(None, None, None, None, 0, 1e-6, 10, art.ART_WARM_SURROGATE, None, None,
                                       None, None) == art.ART_E_INVALID
     assert lib.art_surrogate_train(None, None, None, None) == art.ART_E_INVALID

@@ -176,6 +176,28 @@ def test_multiple_bins(orc, nbins, boundary):
         assert rel(J[b], j_o) < 1e-5
 
 
+def test_wave_counters():
+    """art_wave_counters: zeros unless the library was built with ART_WAVE_STATS=1; there, the
+    warp cycles at the step barriers are a part of the cycles in the units, and a second read
+    (after the clear) is zero."""
+    import os
+    shape = (20, 22, 24)
+    kap, S = lognormal(shape, 3)
+    sw = art.ArtSweep(shape, 4)
+    k = torch.as_tensor(np.ascontiguousarray(kap), dtype=torch.float32, device="cuda")
+    s = torch.as_tensor(np.ascontiguousarray(S), dtype=torch.float32, device="cuda")
+    sw.set_fields(k, s)
+    sw.sweep(None, torch.empty_like(k))
+    assert sw.check() == art.ART_OK
+    c1, c2 = sw.wave_counters(), sw.wave_counters()
+    sw.close()
+    assert all(v == 0 for v in c2.values())
+    if os.environ.get("ART_WAVE_STATS") == "1":
+        assert 0 < c1["barrier_cycles"] < c1["unit_cycles"]
+    else:
+        assert all(v == 0 for v in c1.values())
+
+
 def test_direction_shards_add_up(orc):
     kap, S = lognormal((14, 15, 16), 13)
     nd = 12 * 3 * 3
