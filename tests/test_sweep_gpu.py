@@ -97,6 +97,26 @@ def test_fp64_ragged_direction_groups(orc, split):
     assert rel(J, j_o) < 1e-12
 
 
+@pytest.mark.parametrize("shape", [(1, 1, 1), (2, 2, 2), (1, 5, 7), (9, 1, 1), (3, 40, 1), (70, 3, 2)])
+@pytest.mark.parametrize("precision,averaging,nside", [("fp64", 0, 1), ("fp64", 0, 4), ("fp32", 1, 2)])
+def test_degenerate_grids_slab_blocks(orc, shape, precision, averaging, nside):
+    """The slab-block kernels (FP64, and FP32 with the exact path average) on a single cell, a
+    2^3 cube, planes, lines and a bar longer than a slab block."""
+    rng = np.random.default_rng(23)
+    kap = 0.6 * np.exp(rng.standard_normal(shape))
+    S = rng.random(shape)
+    if precision == "fp32":
+        kap, S = f32(kap), f32(S)
+    jin_o, j_o, _ = orc.sweep(kap, S, nside, averaging=averaging)
+    J, Jin = run(kap, S, nside, precision, averaging=averaging)
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    assert rel(J, j_o) < tol
+    if averaging:   # (J^in = J - S can cross zero)
+        assert np.max(np.abs(Jin - jin_o)) < tol * np.max(np.abs(j_o))
+    else:
+        assert rel(Jin, jin_o) < tol
+
+
 def test_fp32_grf_64_nside4(orc):
     c = wl.grf(64, 4)
     kap, S = f32(c.kappa), f32(c.src)

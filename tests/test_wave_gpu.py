@@ -140,6 +140,24 @@ def test_emissivity_form_with_transparent_cells(orc):
     assert rel(J, j_o) < 1e-5
 
 
+@pytest.mark.parametrize("shape", [(1, 1, 1), (2, 2, 2), (1, 5, 7), (9, 1, 1), (1, 1, 13), (3, 40, 1), (1, 37, 41),
+                                   (257, 6, 5), (5, 9, 257)])
+@pytest.mark.parametrize("variant,nside,i_bc", [(0, 1, None), (0, 2, 0.8), (0, 4, None), (WAVE0 + 11, 4, 0.5)])
+def test_degenerate_grids(orc, shape, variant, nside, i_bc):
+    """A single cell, a 2^3 cube, planes, lines, thin slabs and long bars (every transverse tile
+    ragged or of one column; sweeps of one to 257 slabs), with and without a boundary intensity;
+    the default shape and the four-row shape.  With vacuum boundaries a single cell receives no
+    intensity (J^in = 0 exactly)."""
+    kap, S = lognormal(shape, 21)
+    jin_o, j_o, _ = orc.sweep(kap, S, nside, i_bc=0.0 if i_bc is None else i_bc)
+    J, Jin, st = run(kap, S, nside, i_bc=None if i_bc is None else [i_bc], variant=variant)
+    assert st.variant >= WAVE0
+    assert rel(Jin, jin_o) < 1e-5
+    assert rel(J, j_o) < 1e-5
+    if shape == (1, 1, 1) and i_bc is None:
+        assert Jin[0, 0, 0] == 0.0
+
+
 def test_boundary_intensity(orc):
     kap, S = lognormal((17, 20, 23), 12)
     jin_o, j_o, _ = orc.sweep(kap, S, 2, i_bc=0.8)
