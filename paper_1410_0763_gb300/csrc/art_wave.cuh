@@ -47,10 +47,11 @@
 //  * The two cells of a pair share every segment length, so the arithmetic of
 //    Eq. (rt) runs as packed FP32x2 instructions on both.
 //  * Arithmetic per (warp, slab), chosen by ballot over the warp's cells:
-//    every kappa below KAP_THIN2, KAP_THIN or KAP_THIN6 (series only, to x^2,
-//    x^4 or x^6, as a polynomial in the segment length with per-cell
-//    coefficients), every kappa at or above KAP_THICK (hardware exponential
-//    only), else both with a per-segment select (series below x = 1/4).  The series path deposits
+//    every kappa below KAP_THIN2, KAP_THIN or KAP_THIN5 (series only, of
+//    degree 2, 3 or 5 with economized coefficients, as a polynomial in the
+//    segment length with per-cell coefficients), every kappa at or above
+//    KAP_THICK (hardware exponential only), else both with a per-segment
+//    select (series below x = 1/4).  The series path deposits
 //    ds phi(x) directly, so kappa = 0 needs no special case; the exponential
 //    path deposits 1 - e^-x and the cell's sum is scaled by 1/kappa once.
 #pragma once
@@ -116,15 +117,20 @@ struct WaveArgs {
     long long *stats;         // counters of ART_WAVE_STATS builds: barrier, unit, poll-loop cycles, polls
 };
 
-// Thresholds of the per-warp arithmetic choice.  Series of phi(x) =
-// (1 - e^-x)/x: to x^4 in the thin path (x <= sqrt(3) KAP_THIN = 0.173,
-// truncation < 2.2e-7 relative), to x^6 in the second thin path (x <= sqrt(3)
-// KAP_THIN6 = 0.433: < 7.1e-8), to x^5 in the mixed path below x = 1/4
-// (< 6e-8).  Exponential path: 1 - ex2.approx(-x log2 e), whose absolute error
-// (~2^-22) is below 2e-6 of a cell's deposit when kappa >= KAP_THICK.
-constexpr float KAP_THIN2 = 0.01f;   // x^2 path: x <= 0.0174, truncation < 2.2e-7
-constexpr float KAP_THIN = 0.1f;
-constexpr float KAP_THIN6 = 0.25f;
+// Thresholds of the per-warp arithmetic choice.  The series paths replace
+// phi(x) = (1 - e^-x)/x by a polynomial of degree K whose coefficients are
+// economized (Chebyshev) on the path's whole range x <= sqrt(3) kappa_max
+// (wv_beta): degree 2 to KAP_THIN2 (x <= 0.0329), degree 3 to KAP_THIN (x <=
+// 0.165), degree 5 to KAP_THIN5 (x <= 0.866); each approximation is within
+// 2e-7 relative of phi there (with FP32 rounding of the coefficient
+// polynomial, 2.8e-7 for degree 5; the plain Taylor series would reach only
+// x = 0.017, 0.071 and 0.32 with the same degrees).  The mixed path takes the
+// degree-5 series below x = 1/4.  Exponential path: 1 - ex2.approx(-x log2 e),
+// whose absolute error (~2^-22) is below 2e-6 of a cell's deposit when
+// kappa >= KAP_THICK.
+constexpr float KAP_THIN2 = 0.019f;
+constexpr float KAP_THIN = 0.095f;
+constexpr float KAP_THIN5 = 0.5f;
 constexpr float KAP_THICK = 0.5f;
 constexpr float X_SERIES = 0.25f;
 constexpr int MODE_THIN = 0, MODE_MIXED = 1, MODE_THICK = 2;
@@ -232,11 +238,11 @@ __device__ __forceinline__ float2 f2s(float v) { return make_float2(v, v); }
 // so each FP32 operation of Eq. (rt) runs on both at once as one packed FP32x2
 // instruction.
 //
-// Thin paths (every kappa below KAP_THIN2, KAP_THIN or KAP_THIN6: K = 2, 4 or
-// 6, each within the same truncation bound):
-// the deposit coefficient of a segment, ds phi(kappa ds) with phi to x^K,
-// written as a polynomial in ds whose coefficients are the cell's:
-// ds + ds^2 (c_1 + ds (c_2 + ... + ds c_K)), c_k = (-kappa)^k / (k + 1)!.
+// Thin paths (every kappa below KAP_THIN2, KAP_THIN or KAP_THIN5: K = 2, 3 or
+// 5): the deposit coefficient of a segment, ds phi(kappa ds) with phi to
+// degree K, written as a polynomial in ds whose coefficients are the cell's:
+// ds + ds^2 (c_1 + ds (c_2 + ... + ds c_K)), c_k = (-kappa)^k beta_k, where
+// beta_k = 1/(k + 1)! for the Taylor series and wv_beta<K>(k) economized.
 template <int K> struct WvThin {
     float2 c[K];   // c_1 .. c_K
     float2 nkap;   // -kappa
@@ -267,17 +273,36 @@ template <int K> __device__ __forceinline__ float2 wv_coef(const WvThin<K> &c, c
     return __ffma2_rn(q, ds2, ds);
 }
 
+// Economized coefficients beta_k (k = 1 .. K; c_k = (-kappa)^k beta_k) of the
+// series paths: the Taylor series of psi(x) = (phi(x) - 1)/x, whose x^(k-1)
+// coefficient is (-1)^k/(k + 1)!, taken to degree K + 7, rewritten in the
+// Chebyshev polynomials of the path's range [0, h], h = sqrt(3) kappa_max,
+// and truncated to degree K - 1 (Chebyshev economization; each beta_k lies
+// just below its Taylor value 1/(k + 1)!).  Rounded to FP32.
+template <int K> __host__ __device__ constexpr float wv_beta(int k);
+template <> __host__ __device__ constexpr float wv_beta<2>(int k)   // h = sqrt(3) KAP_THIN2
+{
+    return k == 1 ? 0.499994397f : 0.165303871f;
+}
+template <> __host__ __device__ constexpr float wv_beta<3>(int k)   // h = sqrt(3) KAP_THIN
+{
+    return k == 1 ? 0.499998897f : (k == 2 ? 0.166545019f : 0.0396740399f);
+}
+template <> __host__ __device__ constexpr float wv_beta<5>(int k)   // h = sqrt(3) KAP_THIN5
+{
+    return k == 1 ? 0.499999851f
+                  : (k == 2 ? 0.166658416f : (k == 3 ? 0.0415891334f : (k == 4 ? 0.00807498395f : 0.00102687033f)));
+}
+
 // The coefficients c_1 .. c_K of a pair of cells.
 template <int K> __device__ __forceinline__ WvThin<K> wv_thin(float2 k, float2 src, int field_form)
 {
-    constexpr float inv_fact[7] = {1.0f, 0.5f, 1.0f / 6.0f, 1.0f / 24.0f, 1.0f / 120.0f, 1.0f / 720.0f,
-                                   1.0f / 5040.0f};   // 1 / (j + 1)!
     WvThin<K> c;
     const float2 nk = make_float2(-k.x, -k.y);
     float2 pw = nk;   // (-kappa)^j
 #pragma unroll
     for (int j = 1; j <= K; ++j) {
-        c.c[j - 1] = __fmul2_rn(pw, f2s(inv_fact[j]));
+        c.c[j - 1] = __fmul2_rn(pw, f2s(wv_beta<K>(j)));
         pw = __fmul2_rn(pw, nk);
     }
     c.nkap = nk;
@@ -285,9 +310,10 @@ template <int K> __device__ __forceinline__ WvThin<K> wv_thin(float2 k, float2 s
     return c;
 }
 
-// Mixed path: per cell and segment, the x^5 series of the thin path (per-cell
-// coefficients) for segments with x = kappa ds below X_SERIES, i.e. ds below
-// the cell's threshold X_SERIES / kappa, else the exponential path.
+// Mixed path: per cell and segment, the degree-5 series (per-cell
+// coefficients; its range x <= 0.866 covers X_SERIES) for segments with
+// x = kappa ds below X_SERIES, i.e. ds below the cell's threshold
+// X_SERIES / kappa, else the exponential path.
 struct WvMixed {
     WvThin<5> t;     // c_1 .. c_5, -kappa, emission
     float2 k2;       // -kappa log2 e
@@ -735,11 +761,12 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
 {
     using Sh = WaveShape<WB, WC, DMAX, NP>;
     constexpr int NT = Sh::NT, RT = Sh::RT, R = Sh::R, XBW = Sh::XBW;
-    // shapes with at least 160 registers a thread take two x^2-path entries at a time
+    // shapes with at least 160 registers a thread take two degree-2-path entries at a time
     constexpr bool TWO = 65536 / (MINB * NT) >= 160;
-    // the second thin path (kappa < KAP_THIN6) in shapes with at least 96 registers a thread
-    // (the others take the mixed path there)
-    constexpr bool THIN6 = 65536 / (MINB * NT) >= 96;
+    // the degree-2 and degree-5 series paths (kappa < KAP_THIN2, KAP_THIN5) and the coefficient
+    // form of the mixed path in shapes with at least 96 registers a thread (the others take the
+    // degree-3 path below KAP_THIN and the mixed path in x above it)
+    constexpr bool THIN5 = 65536 / (MINB * NT) >= 96;
     extern __shared__ __align__(16) unsigned char wsm[];
     float4 *tab = reinterpret_cast<float4 *>(wsm);                  // [RT][TABS]: run-table blocks
     float *XB = reinterpret_cast<float *>(wsm + Sh::off_xb);        // [2][WB+1][WC][DMAX][XBW]
@@ -940,7 +967,7 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
                 kmin = fminf(kmin, fminf(kap[i].x, kap[i].y));
             }
             // the mode of the warp, by vote on its cells' largest and smallest kappa
-            const bool all_thin2 = THIN6 && __all_sync(0xffffffffu, kmax < KAP_THIN2);
+            const bool all_thin2 = THIN5 && __all_sync(0xffffffffu, kmax < KAP_THIN2);
             WvXch x;
             x.bo = xb0 + 4 * (par * Sh::XB_PAR + ((wb + 1) * WC + wc) * DMAX * XBW + R * cl);
             x.bi = xb0 + 4 * ((par ^ 1) * Sh::XB_PAR + (wb * WC + wc) * DMAX * XBW + R * cl);
@@ -955,27 +982,27 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
             const unsigned tb = tab0 + 16 * (m & (RT - 1)) * Sh::TABS;
             const bool all_thin = __all_sync(0xffffffffu, kmax < KAP_THIN);
             const bool all_thick = __all_sync(0xffffffffu, kmin >= KAP_THICK);
-            const bool all_thin6 = THIN6 && __all_sync(0xffffffffu, kmax < KAP_THIN6);
+            const bool all_thin5 = THIN5 && __all_sync(0xffffffffu, kmax < KAP_THIN5);
             WvRows<NP> js;
             // (code size decides which paths take two entries at a time: with the
-            // x^2 path's loop doubled and the others single, the modes of a mixed
+            // degree-2 path's loop doubled and the others single, the modes of a mixed
             // bin still fit the instruction cache)
-            if (THIN6 && all_thin2) {   // (the x^2 and x^6 paths: shapes with >= 96 registers)
+            if (THIN5 && all_thin2) {   // (the degree-2 and degree-5 paths: shapes with >= 96 registers)
                 WvThin<2> c[NP];
 #pragma unroll
                 for (int i = 0; i < NP; ++i) c[i] = wv_thin<2>(kap[i], src[i], p.field_form);
                 js = wv_dirs<MODE_THIN, NT, NP, TWO>(c, rs0, tb, nd, x);
             } else if (all_thin) {
-                WvThin<4> c[NP];
+                WvThin<3> c[NP];
 #pragma unroll
-                for (int i = 0; i < NP; ++i) c[i] = wv_thin<4>(kap[i], src[i], p.field_form);
+                for (int i = 0; i < NP; ++i) c[i] = wv_thin<3>(kap[i], src[i], p.field_form);
                 js = wv_dirs<MODE_THIN, NT, NP, false>(c, rs0, tb, nd, x);
-            } else if (THIN6 && all_thin6) {
-                WvThin<6> c[NP];
+            } else if (THIN5 && all_thin5) {
+                WvThin<5> c[NP];
 #pragma unroll
-                for (int i = 0; i < NP; ++i) c[i] = wv_thin<6>(kap[i], src[i], p.field_form);
+                for (int i = 0; i < NP; ++i) c[i] = wv_thin<5>(kap[i], src[i], p.field_form);
                 js = wv_dirs<MODE_THIN, NT, NP, false>(c, rs0, tb, nd, x);
-            } else if (THIN6 && !all_thick) {   // (the coefficient form needs the registers of THIN6 shapes)
+            } else if (THIN5 && !all_thick) {   // (the coefficient form needs the registers of THIN5 shapes)
                 WvMixed c[NP];
 #pragma unroll
                 for (int i = 0; i < NP; ++i) c[i] = wv_mixed(kap[i], src[i], p.field_form);
