@@ -47,8 +47,8 @@
 //  * The two cells of a pair share every segment length, so the arithmetic of
 //    Eq. (rt) runs as packed FP32x2 instructions on both.
 //  * Arithmetic per (warp, slab), chosen by ballot over the warp's cells:
-//    every kappa below KAP_THIN2, KAP_THIN or KAP_THIN6 (series only, of
-//    degree 2, 3 or 6 with economized coefficients, as a polynomial in the
+//    every kappa below KAP_THIN2, KAP_THIN or KAP_THIN5 (series only, of
+//    degree 2, 3 or 5 with economized coefficients, as a polynomial in the
 //    segment length with per-cell coefficients), every kappa at or above
 //    KAP_THICK (hardware exponential only), else both with a per-segment
 //    select (series below x = 1/4).  The series path deposits
@@ -121,17 +121,17 @@ struct WaveArgs {
 // phi(x) = (1 - e^-x)/x by a polynomial of degree K whose coefficients are
 // economized (Chebyshev) on the path's whole range x <= sqrt(3) kappa_max
 // (wv_beta): degree 2 to KAP_THIN2 (x <= 0.0329), degree 3 to KAP_THIN (x <=
-// 0.165), degree 6 to KAP_THIN6 (x <= 1.386); each approximation is within
-// 2e-7 relative of phi there (2.4e-7 with the FP32 rounding of the
-// coefficient polynomial; the plain Taylor series would reach only x = 0.017,
-// 0.071 and 0.50 with the same degrees).  The mixed path takes a degree-5
-// series (economized on x <= 0.866) below x = 1/4.  Exponential path:
-// 1 - ex2.approx(-x log2 e), whose absolute error (~2^-22) is below 2e-6 of a
-// cell's deposit when kappa >= KAP_THICK.
+// 0.165), degree 5 to KAP_THIN5 (x <= 0.866); each approximation is within
+// 2e-7 relative of phi there (with FP32 rounding of the coefficient
+// polynomial, 2.8e-7 for degree 5; the plain Taylor series would reach only
+// x = 0.017, 0.071 and 0.32 with the same degrees).  The mixed path takes the
+// degree-5 series below x = 1/4.  Exponential path: 1 - ex2.approx(-x log2 e),
+// whose absolute error (~2^-22) is below 2e-6 of a cell's deposit when
+// kappa >= KAP_THICK.
 constexpr float KAP_THIN2 = 0.019f;
 constexpr float KAP_THIN = 0.095f;
-constexpr float KAP_THIN6 = 0.8f;
-constexpr float KAP_THICK = 0.8f;
+constexpr float KAP_THIN5 = 0.5f;
+constexpr float KAP_THICK = 0.5f;
 constexpr float X_SERIES = 0.25f;
 constexpr int MODE_THIN = 0, MODE_MIXED = 1, MODE_THICK = 2;
 
@@ -238,8 +238,8 @@ __device__ __forceinline__ float2 f2s(float v) { return make_float2(v, v); }
 // so each FP32 operation of Eq. (rt) runs on both at once as one packed FP32x2
 // instruction.
 //
-// Thin paths (every kappa below KAP_THIN2, KAP_THIN or KAP_THIN6: K = 2, 3 or
-// 6): the deposit coefficient of a segment, ds phi(kappa ds) with phi to
+// Thin paths (every kappa below KAP_THIN2, KAP_THIN or KAP_THIN5: K = 2, 3 or
+// 5): the deposit coefficient of a segment, ds phi(kappa ds) with phi to
 // degree K, written as a polynomial in ds whose coefficients are the cell's:
 // ds + ds^2 (c_1 + ds (c_2 + ... + ds c_K)), c_k = (-kappa)^k beta_k, where
 // beta_k = 1/(k + 1)! for the Taylor series and wv_beta<K>(k) economized.
@@ -288,13 +288,7 @@ template <> __host__ __device__ constexpr float wv_beta<3>(int k)   // h = sqrt(
 {
     return k == 1 ? 0.499998897f : (k == 2 ? 0.166545019f : 0.0396740399f);
 }
-template <> __host__ __device__ constexpr float wv_beta<6>(int k)   // h = sqrt(3) KAP_THIN6
-{
-    return k == 1 ? 0.49999994f
-                  : (k == 2 ? 0.166663885f
-                            : (k == 3 ? 0.0416428f : (k == 4 ? 0.00825761817f : (k == 5 ? 0.00127810426f : 0.000119953038f))));
-}
-template <> __host__ __device__ constexpr float wv_beta<5>(int k)   // h = sqrt(3) 0.5 (mixed path, x < X_SERIES)
+template <> __host__ __device__ constexpr float wv_beta<5>(int k)   // h = sqrt(3) KAP_THIN5
 {
     return k == 1 ? 0.499999851f
                   : (k == 2 ? 0.166658416f : (k == 3 ? 0.0415891334f : (k == 4 ? 0.00807498395f : 0.00102687033f)));
@@ -316,7 +310,7 @@ template <int K> __device__ __forceinline__ WvThin<K> wv_thin(float2 k, float2 s
     return c;
 }
 
-// Mixed path: per cell and segment, a degree-5 series (per-cell
+// Mixed path: per cell and segment, the degree-5 series (per-cell
 // coefficients; its range x <= 0.866 covers X_SERIES) for segments with
 // x = kappa ds below X_SERIES, i.e. ds below the cell's threshold
 // X_SERIES / kappa, else the exponential path.
@@ -769,10 +763,10 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
     constexpr int NT = Sh::NT, RT = Sh::RT, R = Sh::R, XBW = Sh::XBW;
     // shapes with at least 160 registers a thread take two degree-2-path entries at a time
     constexpr bool TWO = 65536 / (MINB * NT) >= 160;
-    // the degree-2 and degree-6 series paths (kappa < KAP_THIN2, KAP_THIN6) and the coefficient
+    // the degree-2 and degree-5 series paths (kappa < KAP_THIN2, KAP_THIN5) and the coefficient
     // form of the mixed path in shapes with at least 96 registers a thread (the others take the
     // degree-3 path below KAP_THIN and the mixed path in x above it)
-    constexpr bool THIN6 = 65536 / (MINB * NT) >= 96;
+    constexpr bool THIN5 = 65536 / (MINB * NT) >= 96;
     extern __shared__ __align__(16) unsigned char wsm[];
     float4 *tab = reinterpret_cast<float4 *>(wsm);                  // [RT][TABS]: run-table blocks
     float *XB = reinterpret_cast<float *>(wsm + Sh::off_xb);        // [2][WB+1][WC][DMAX][XBW]
@@ -973,7 +967,7 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
                 kmin = fminf(kmin, fminf(kap[i].x, kap[i].y));
             }
             // the mode of the warp, by vote on its cells' largest and smallest kappa
-            const bool all_thin2 = THIN6 && __all_sync(0xffffffffu, kmax < KAP_THIN2);
+            const bool all_thin2 = THIN5 && __all_sync(0xffffffffu, kmax < KAP_THIN2);
             WvXch x;
             x.bo = xb0 + 4 * (par * Sh::XB_PAR + ((wb + 1) * WC + wc) * DMAX * XBW + R * cl);
             x.bi = xb0 + 4 * ((par ^ 1) * Sh::XB_PAR + (wb * WC + wc) * DMAX * XBW + R * cl);
@@ -988,12 +982,12 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
             const unsigned tb = tab0 + 16 * (m & (RT - 1)) * Sh::TABS;
             const bool all_thin = __all_sync(0xffffffffu, kmax < KAP_THIN);
             const bool all_thick = __all_sync(0xffffffffu, kmin >= KAP_THICK);
-            const bool all_thin6 = THIN6 && __all_sync(0xffffffffu, kmax < KAP_THIN6);
+            const bool all_thin5 = THIN5 && __all_sync(0xffffffffu, kmax < KAP_THIN5);
             WvRows<NP> js;
             // (code size decides which paths take two entries at a time: with the
             // degree-2 path's loop doubled and the others single, the modes of a mixed
             // bin still fit the instruction cache)
-            if (THIN6 && all_thin2) {   // (the degree-2 and degree-6 paths: shapes with >= 96 registers)
+            if (THIN5 && all_thin2) {   // (the degree-2 and degree-5 paths: shapes with >= 96 registers)
                 WvThin<2> c[NP];
 #pragma unroll
                 for (int i = 0; i < NP; ++i) c[i] = wv_thin<2>(kap[i], src[i], p.field_form);
@@ -1003,12 +997,12 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
 #pragma unroll
                 for (int i = 0; i < NP; ++i) c[i] = wv_thin<3>(kap[i], src[i], p.field_form);
                 js = wv_dirs<MODE_THIN, NT, NP, false>(c, rs0, tb, nd, x);
-            } else if (THIN6 && all_thin6) {
-                WvThin<6> c[NP];
+            } else if (THIN5 && all_thin5) {
+                WvThin<5> c[NP];
 #pragma unroll
-                for (int i = 0; i < NP; ++i) c[i] = wv_thin<6>(kap[i], src[i], p.field_form);
+                for (int i = 0; i < NP; ++i) c[i] = wv_thin<5>(kap[i], src[i], p.field_form);
                 js = wv_dirs<MODE_THIN, NT, NP, false>(c, rs0, tb, nd, x);
-            } else if (THIN6 && !all_thick) {   // (the coefficient form needs the registers of THIN6 shapes)
+            } else if (THIN5 && !all_thick) {   // (the coefficient form needs the registers of THIN5 shapes)
                 WvMixed c[NP];
 #pragma unroll
                 for (int i = 0; i < NP; ++i) c[i] = wv_mixed(kap[i], src[i], p.field_form);

@@ -104,10 +104,10 @@ def test_thin_mixed_and_thick_media(orc, scale, variant):
 
 
 @pytest.mark.parametrize("variant", [0, WAVE0 + 6, WAVE0 + 10])
-@pytest.mark.parametrize("hi", [0.0099, 0.0189, 0.094, 0.499, 0.799])
+@pytest.mark.parametrize("hi", [0.0099, 0.0189, 0.094, 0.249, 0.499])
 def test_second_thin_path(orc, variant, hi):
-    """kappa uniform in [0, hi): a warp whose kappa stay below 0.019, 0.095 or 0.8 takes the
-    economized series of degree 2, 3 or 6 (degrees 2 and 6 in shapes with the registers for
+    """kappa uniform in [0, hi): a warp whose kappa stay below 0.019, 0.095 or 0.5 takes the
+    economized series of degree 2, 3 or 5 (degrees 2 and 5 in shapes with the registers for
     them; the degree-3 and mixed paths in the others), each up to the top of its range,
     x = sqrt(3) hi."""
     rng = np.random.default_rng(19)

@@ -20,8 +20,6 @@ def source():
 
 
 def threshold(name):
-    if not isinstance(name, str):
-        return float(np.float32(name))
     m = re.search(r"constexpr float %s = ([0-9.eE+-]+)f;" % name, source())
     assert m, name
     return float(np.float32(float(m.group(1))))
@@ -53,9 +51,7 @@ def g_fp32(beta, kap, ds):
     return (q * ds2 + ds).astype(f).astype(np.float64)
 
 
-# (degree, top of its kappa range): the three series paths, and the mixed path's degree-5
-# series, economized on kappa < 0.5 (it serves x < X_SERIES)
-PATHS = [(2, "KAP_THIN2"), (3, "KAP_THIN"), (6, "KAP_THIN6"), (5, 0.5)]
+PATHS = [(2, "KAP_THIN2"), (3, "KAP_THIN"), (5, "KAP_THIN5")]
 
 
 @pytest.mark.parametrize("K,name", PATHS)
@@ -64,10 +60,10 @@ def test_economized_series_within_its_bound(K, name):
     kmax = threshold(name)
     h = math.sqrt(3.0) * kmax
     # each coefficient sits below its Taylor value 1/(k+1)!, the lower ones just below (the
-    # highest two absorb most of the dropped terms); a transposed or missing coefficient fails
+    # highest absorbs most of the dropped terms); a transposed or missing coefficient fails here
     for k, b in enumerate(beta, start=1):
         t = 1.0 / math.factorial(k + 1)
-        assert {K: 0.5, K - 1: 0.85}.get(k, 0.95) * t < b <= t
+        assert (0.5 if k == K else 0.95) * t < b <= t
     x = np.linspace(0.0, h, 400001)[1:]
     phi = -np.expm1(-x) / x
     a = [(-1) ** k * b for k, b in enumerate(beta, start=1)]   # psi(x) ~ sum a_k x^(k-1)
@@ -91,6 +87,6 @@ def test_economized_series_in_fp32(K, name):
 
 def test_thresholds_order():
     """The series paths cover nested ranges up to the exponential-only path."""
-    assert threshold("KAP_THIN2") < threshold("KAP_THIN") < threshold("KAP_THIN6") <= threshold("KAP_THICK")
-    # the mixed path's series (degree 5, economized on kappa < 0.5) covers its range x < X_SERIES
-    assert threshold("X_SERIES") <= math.sqrt(3.0) * 0.5
+    assert threshold("KAP_THIN2") < threshold("KAP_THIN") < threshold("KAP_THIN5") <= threshold("KAP_THICK")
+    # the mixed path's series (degree 5) covers its own range x < X_SERIES
+    assert threshold("X_SERIES") <= math.sqrt(3.0) * threshold("KAP_THIN5")
