@@ -124,15 +124,18 @@ struct WaveArgs {
 // 0.165), degree 5 to KAP_THIN5 (x <= 0.866); each approximation is within
 // 2e-7 relative of phi there (with FP32 rounding of the coefficient
 // polynomial, 2.8e-7 for degree 5; the plain Taylor series would reach only
-// x = 0.017, 0.071 and 0.32 with the same degrees).  The mixed path takes the
-// degree-5 series below x = 1/4.  Exponential path: 1 - ex2.approx(-x log2 e),
-// whose absolute error (~2^-22) is below 2e-6 of a cell's deposit when
-// kappa >= KAP_THICK.
+// x = 0.017, 0.071 and 0.32 with the same degrees).  The mixed path takes a
+// degree-4 series economized on x < X_SERIES (within 1.2e-7, 1.8e-7 with FP32
+// rounding; shapes without the registers for it keep the x^5 Taylor series
+// in x below X_SERIES_X, < 6e-8).  Exponential path: 1 - ex2.approx(-x log2
+// e), whose absolute error (~2^-22) is below 2e-6 of a cell's deposit when
+// kappa >= KAP_THICK, and below 5e-7 of a segment's deposit for x >= X_SERIES.
 constexpr float KAP_THIN2 = 0.019f;
 constexpr float KAP_THIN = 0.095f;
 constexpr float KAP_THIN5 = 0.5f;
 constexpr float KAP_THICK = 0.5f;
-constexpr float X_SERIES = 0.25f;
+constexpr float X_SERIES = 0.4f;
+constexpr float X_SERIES_X = 0.25f;
 constexpr int MODE_THIN = 0, MODE_MIXED = 1, MODE_THICK = 2;
 
 __device__ __forceinline__ float wv_ex2(float x)
@@ -288,6 +291,10 @@ template <> __host__ __device__ constexpr float wv_beta<3>(int k)   // h = sqrt(
 {
     return k == 1 ? 0.499998897f : (k == 2 ? 0.166545019f : 0.0396740399f);
 }
+template <> __host__ __device__ constexpr float wv_beta<4>(int k)   // h = X_SERIES (mixed path)
+{
+    return k == 1 ? 0.499999762f : (k == 2 ? 0.166646942f : (k == 3 ? 0.0414167084f : 0.00730631594f));
+}
 template <> __host__ __device__ constexpr float wv_beta<5>(int k)   // h = sqrt(3) KAP_THIN5
 {
     return k == 1 ? 0.499999851f
@@ -310,12 +317,12 @@ template <int K> __device__ __forceinline__ WvThin<K> wv_thin(float2 k, float2 s
     return c;
 }
 
-// Mixed path: per cell and segment, the degree-5 series (per-cell
-// coefficients; its range x <= 0.866 covers X_SERIES) for segments with
+// Mixed path: per cell and segment, the degree-4 series (per-cell
+// coefficients, economized on x < X_SERIES) for segments with
 // x = kappa ds below X_SERIES, i.e. ds below the cell's threshold
 // X_SERIES / kappa, else the exponential path.
 struct WvMixed {
-    WvThin<5> t;     // c_1 .. c_5, -kappa, emission
+    WvThin<4> t;     // c_1 .. c_4, -kappa, emission
     float2 k2;       // -kappa log2 e
     float2 rk, nrk;  // 1/kappa, -1/kappa (0 where kappa = 0)
     float2 th;       // X_SERIES / kappa (+inf where kappa = 0)
@@ -324,7 +331,7 @@ struct WvMixed {
 __device__ __forceinline__ WvMixed wv_mixed(float2 k, float2 src, int field_form)
 {
     WvMixed c;
-    c.t = wv_thin<5>(k, src, field_form);
+    c.t = wv_thin<4>(k, src, field_form);
     c.k2 = __fmul2_rn(k, f2s(-1.4426950408889634f));
     c.rk = make_float2(k.x > 0.0f ? wv_rcp(k.x) : 0.0f, k.y > 0.0f ? wv_rcp(k.y) : 0.0f);
     c.nrk = make_float2(-c.rk.x, -c.rk.y);
@@ -360,7 +367,7 @@ template <int MODE> __device__ __forceinline__ float2 wv_coef(const WvCell2 &c, 
     const float2 arg = __fmul2_rn(c.k2, dsv);
     const float2 e = make_float2(wv_ex2(arg.x), wv_ex2(arg.y));
     const float2 gm = __fmul2_rn(__ffma2_rn(e, f2s(-1.0f), f2s(1.0f)), c.rk);
-    return make_float2(x.x < X_SERIES ? gs.x : gm.x, x.y < X_SERIES ? gs.y : gm.y);
+    return make_float2(x.x < X_SERIES_X ? gs.x : gm.x, x.y < X_SERIES_X ? gs.y : gm.y);
 }
 
 // One segment with coefficient g and incoming intensities I (both cells):

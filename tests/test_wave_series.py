@@ -20,6 +20,8 @@ def source():
 
 
 def threshold(name):
+    if not isinstance(name, str):
+        return float(np.float32(name))
     m = re.search(r"constexpr float %s = ([0-9.eE+-]+)f;" % name, source())
     assert m, name
     return float(np.float32(float(m.group(1))))
@@ -51,7 +53,9 @@ def g_fp32(beta, kap, ds):
     return (q * ds2 + ds).astype(f).astype(np.float64)
 
 
-PATHS = [(2, "KAP_THIN2"), (3, "KAP_THIN"), (5, "KAP_THIN5")]
+# (degree, top of its kappa range): the three series paths, and the mixed path's degree-4
+# series, economized on x < X_SERIES (kappa up to X_SERIES / sqrt(3) with segments up to sqrt(3))
+PATHS = [(2, "KAP_THIN2"), (3, "KAP_THIN"), (5, "KAP_THIN5"), (4, threshold("X_SERIES") / math.sqrt(3.0))]
 
 
 @pytest.mark.parametrize("K,name", PATHS)
@@ -88,5 +92,6 @@ def test_economized_series_in_fp32(K, name):
 def test_thresholds_order():
     """The series paths cover nested ranges up to the exponential-only path."""
     assert threshold("KAP_THIN2") < threshold("KAP_THIN") < threshold("KAP_THIN5") <= threshold("KAP_THICK")
-    # the mixed path's series (degree 5) covers its own range x < X_SERIES
-    assert threshold("X_SERIES") <= math.sqrt(3.0) * threshold("KAP_THIN5")
+    # the mixed path switches to the exponential where the series' range ends; the x-form mixed
+    # path of the smaller shapes (the x^5 Taylor series) stops earlier
+    assert threshold("X_SERIES_X") <= threshold("X_SERIES")
