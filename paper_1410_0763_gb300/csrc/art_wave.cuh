@@ -125,9 +125,10 @@ struct WaveArgs {
 // 2e-7 relative of phi there (with FP32 rounding of the coefficient
 // polynomial, 2.8e-7 for degree 5; the plain Taylor series would reach only
 // x = 0.017, 0.071 and 0.32 with the same degrees).  The mixed path takes a
-// degree-4 series economized on x < X_SERIES (within 1.2e-7, 1.8e-7 with FP32
-// rounding; shapes without the registers for it keep the x^5 Taylor series
-// in x below X_SERIES_X, < 6e-8).  Exponential path: 1 - ex2.approx(-x log2
+// series below x = X_SERIES: of degree 4 economized on that range in the
+// four-row shapes (within 1.2e-7, 1.8e-7 with FP32 rounding), the degree-5
+// one in the two-row shapes; shapes with fewer than 96 registers a thread
+// keep the x^5 Taylor series in x below X_SERIES_X (< 6e-8).  Exponential path: 1 - ex2.approx(-x log2
 // e), whose absolute error (~2^-22) is below 2e-6 of a cell's deposit when
 // kappa >= KAP_THICK, and below 5e-7 of a segment's deposit for x >= X_SERIES.
 constexpr float KAP_THIN2 = 0.019f;
@@ -317,21 +318,23 @@ template <int K> __device__ __forceinline__ WvThin<K> wv_thin(float2 k, float2 s
     return c;
 }
 
-// Mixed path: per cell and segment, the degree-4 series (per-cell
-// coefficients, economized on x < X_SERIES) for segments with
-// x = kappa ds below X_SERIES, i.e. ds below the cell's threshold
-// X_SERIES / kappa, else the exponential path.
-struct WvMixed {
-    WvThin<4> t;     // c_1 .. c_4, -kappa, emission
+// Mixed path: per cell and segment, a series of degree K (per-cell
+// coefficients; degree 4 economized on x < X_SERIES, or degree 5, economized
+// on a range that covers it) for segments with x = kappa ds below X_SERIES,
+// i.e. ds below the cell's threshold X_SERIES / kappa, else the exponential
+// path.  (Four-row shapes take degree 4; in the two-row shapes degree 4
+// spills registers, so they keep degree 5.)
+template <int K> struct WvMixed {
+    WvThin<K> t;     // c_1 .. c_K, -kappa, emission
     float2 k2;       // -kappa log2 e
     float2 rk, nrk;  // 1/kappa, -1/kappa (0 where kappa = 0)
     float2 th;       // X_SERIES / kappa (+inf where kappa = 0)
 };
 
-__device__ __forceinline__ WvMixed wv_mixed(float2 k, float2 src, int field_form)
+template <int K> __device__ __forceinline__ WvMixed<K> wv_mixed(float2 k, float2 src, int field_form)
 {
-    WvMixed c;
-    c.t = wv_thin<4>(k, src, field_form);
+    WvMixed<K> c;
+    c.t = wv_thin<K>(k, src, field_form);
     c.k2 = __fmul2_rn(k, f2s(-1.4426950408889634f));
     c.rk = make_float2(k.x > 0.0f ? wv_rcp(k.x) : 0.0f, k.y > 0.0f ? wv_rcp(k.y) : 0.0f);
     c.nrk = make_float2(-c.rk.x, -c.rk.y);
@@ -340,7 +343,7 @@ __device__ __forceinline__ WvMixed wv_mixed(float2 k, float2 src, int field_form
     return c;
 }
 
-__device__ __forceinline__ float2 wv_coef(const WvMixed &c, const float4 &w)
+template <int K> __device__ __forceinline__ float2 wv_coef(const WvMixed<K> &c, const float4 &w)
 {
     const float2 gs = wv_coef(c.t, w);
     const float2 arg = __fmul2_rn(c.k2, make_float2(w.x, w.y));
@@ -398,10 +401,10 @@ template <int K> struct WvOps<MODE_THIN, WvThin<K>> {
         return wv_seg<F>(c, I, g, A);
     }
 };
-template <> struct WvOps<MODE_MIXED, WvMixed> {
-    static __device__ __forceinline__ float2 coef(const WvMixed &c, const float4 &w) { return wv_coef(c, w); }
+template <int K> struct WvOps<MODE_MIXED, WvMixed<K>> {
+    static __device__ __forceinline__ float2 coef(const WvMixed<K> &c, const float4 &w) { return wv_coef(c, w); }
     template <bool F>
-    static __device__ __forceinline__ float2 seg(const WvMixed &c, float2 I, float2 g, float2 &A)
+    static __device__ __forceinline__ float2 seg(const WvMixed<K> &c, float2 I, float2 g, float2 &A)
     {
         return wv_seg<F>(c.t, I, g, A);
     }
@@ -1010,9 +1013,10 @@ __global__ void __launch_bounds__(32 * WB * WC, MINB) wave_kernel(const WaveArgs
                 for (int i = 0; i < NP; ++i) c[i] = wv_thin<5>(kap[i], src[i], p.field_form);
                 js = wv_dirs<MODE_THIN, NT, NP, false>(c, rs0, tb, nd, x);
             } else if (THIN5 && !all_thick) {   // (the coefficient form needs the registers of THIN5 shapes)
-                WvMixed c[NP];
+                constexpr int KM = NP == 2 ? 4 : 5;   // the mixed path's series degree
+                WvMixed<KM> c[NP];
 #pragma unroll
-                for (int i = 0; i < NP; ++i) c[i] = wv_mixed(kap[i], src[i], p.field_form);
+                for (int i = 0; i < NP; ++i) c[i] = wv_mixed<KM>(kap[i], src[i], p.field_form);
                 js = wv_dirs<MODE_MIXED, NT, NP, false>(c, rs0, tb, nd, x);
             } else {
                 WvCell2 c[NP];
